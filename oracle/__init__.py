@@ -1,0 +1,279 @@
+"""FP64 CPU oracle for the PAM fitting path -- test infrastructure only.
+
+Only the tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
+``bench.py`` may import this package. The product path (the CUDA library and
+its Python binding) never imports, links or calls anything here, and the two
+share no code.
+
+The arithmetic lives in ``pam_oracle.c`` (plain C, binary64, no fused
+multiply-add); this module compiles it with gcc on first use and wraps each
+function with numpy marshalling. Which paper passage each function follows is
+stated beside it in the C source.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "pam_oracle.c")
+_LIB = os.path.join(_HERE, "_build", "libpam_oracle.so")
+_lock = threading.Lock()
+_lib = None
+
+NINFO = 8  # per-subdomain diagnostics, see orc_fit_subdomain
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle shared library (gcc, -O2, OpenMP, no FMA contraction)."""
+    os.makedirs(os.path.dirname(_LIB), exist_ok=True)
+    stale = (not os.path.exists(_LIB)) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)
+    if force or stale:
+        tmp = _LIB + f".{os.getpid()}.tmp"
+        cmd = ["gcc", "-O2", "-std=c11", "-fPIC", "-shared", "-fopenmp",
+               "-ffp-contract=off", "-fno-fast-math", _SRC, "-o", tmp, "-lm"]
+        subprocess.run(cmd, check=True)
+        os.replace(tmp, _LIB)
+    return _LIB
+
+
+def lib():
+    global _lib
+    with _lock:
+        if _lib is None:
+            build()
+            L = C.CDLL(_LIB)
+            i32p = np.ctypeslib.ndpointer(np.int32, flags="C_CONTIGUOUS")
+            f64p = np.ctypeslib.ndpointer(np.float64, flags="C_CONTIGUOUS")
+            L.orc_partition.argtypes = [C.c_int, i32p, i32p, C.c_int, i32p]
+            L.orc_partition.restype = C.c_int
+            L.orc_box_cells.argtypes = [C.c_int, i32p, i32p, i32p, f64p, f64p, f64p, f64p]
+            L.orc_box_cells.restype = C.c_int64
+            L.orc_initial_dictionary.argtypes = [C.c_int, i32p, i32p, i32p, i32p, f64p]
+            L.orc_initial_dictionary.restype = C.c_int
+            L.orc_assemble.argtypes = [C.c_int, C.c_int64, f64p, C.c_int, f64p, f64p]
+            L.orc_assemble.restype = None
+            L.orc_gram.argtypes = [C.c_int64, C.c_int, f64p, f64p, f64p, f64p]
+            L.orc_gram.restype = None
+            L.orc_enet.argtypes = [C.c_int, f64p, f64p, C.c_double, C.c_double, f64p,
+                                   C.c_int, f64p]
+            L.orc_enet.restype = C.c_int
+            L.orc_enet_objective.argtypes = [C.c_int, f64p, f64p, C.c_double, C.c_double,
+                                             C.c_double, f64p]
+            L.orc_enet_objective.restype = C.c_double
+            L.orc_residual.argtypes = [C.c_int64, C.c_int, f64p, f64p, f64p, C.c_double, f64p]
+            L.orc_residual.restype = None
+            L.orc_mark.argtypes = [C.c_int64, f64p, C.c_double, C.c_int, i32p]
+            L.orc_mark.restype = C.c_int
+            L.orc_enrich.argtypes = [C.c_int, C.c_int, f64p, C.c_int, i32p, f64p, f64p,
+                                     f64p, C.c_double, C.c_int]
+            L.orc_enrich.restype = C.c_int
+            L.orc_fit_all.argtypes = [C.c_int, i32p, f64p, C.c_int, i32p, i32p,
+                                      C.c_void_p, C.c_int, C.c_void_p, C.c_int,
+                                      f64p, f64p, f64p]
+            L.orc_fit_all.restype = C.c_int
+            L.orc_eval.argtypes = [C.c_int, i32p, i32p, C.c_int, i32p, f64p, f64p,
+                                   C.c_int64, f64p, C.c_int, f64p, C.c_void_p]
+            L.orc_eval.restype = None
+            L.orc_errors.argtypes = [C.c_int, i32p, i32p, C.c_int, i32p, f64p, f64p,
+                                     f64p, f64p]
+            L.orc_errors.restype = None
+            _lib = L
+    return _lib
+
+
+class _Params(C.Structure):
+    _fields_ = [("lambda1_hat", C.c_double), ("lambda2_hat", C.c_double),
+                ("eps_tol_rel", C.c_double), ("eta", C.c_double),
+                ("k_top", C.c_int), ("m_max", C.c_int), ("levels", C.c_int),
+                ("max_sweeps", C.c_int)]
+
+
+def _i32(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.int32))
+
+
+def _f64(a):
+    return np.ascontiguousarray(np.asarray(a, dtype=np.float64))
+
+
+def _pad3(v, fill):
+    v = list(v)
+    return _i32(v + [fill] * (3 - len(v)))
+
+
+# --------------------------------------------------------------------------
+# Step 1
+# --------------------------------------------------------------------------
+
+def partition(n_cells, n_sub, overlap=0):
+    """Core/patch boxes, int32 [S, 12] (core_lo, core_hi, patch_lo, patch_hi)."""
+    dim = len(n_cells)
+    S = int(np.prod(n_sub))
+    boxes = np.zeros((S, 12), dtype=np.int32)
+    lib().orc_partition(dim, _pad3(n_cells, 1), _pad3(n_sub, 1), int(overlap), boxes)
+    return boxes
+
+
+def box_cells(n_cells, lo, hi, K):
+    """(x [N,3], y = ln K [N], K [N]) of the cells of box [lo, hi), x fastest."""
+    dim = len(n_cells)
+    lo, hi = _pad3(list(lo)[:3], 0), _pad3(list(hi)[:3], 1)
+    N = int(np.prod(hi - lo))
+    x = np.zeros((N, 3)); y = np.zeros(N); kv = np.zeros(N)
+    lib().orc_box_cells(dim, _pad3(n_cells, 1), lo, hi, _f64(K).reshape(-1), x, y, kv)
+    return x, y, kv
+
+
+def initial_dictionary(n_cells, core_lo, core_hi, g):
+    """Uniform cell-centred lattice over the core box: [M, 4] = (c, sigma)."""
+    dim = len(n_cells)
+    M = int(np.prod(g))
+    c = np.zeros((M, 4))
+    lib().orc_initial_dictionary(dim, _pad3(n_cells, 1), _pad3(list(core_lo)[:3], 0),
+                                 _pad3(list(core_hi)[:3], 1), _pad3(g, 1), c)
+    return c
+
+
+# --------------------------------------------------------------------------
+# Step 2
+# --------------------------------------------------------------------------
+
+def assemble(dim, x, c):
+    """Shepard-normalised feature matrix W [N, M] (x: [N,3] or [N,dim])."""
+    x = _f64(x)
+    if x.shape[1] != 3:
+        x = _f64(np.concatenate([x, np.zeros((x.shape[0], 3 - x.shape[1]))], axis=1))
+    c = _f64(c)
+    W = np.zeros((x.shape[0], c.shape[0]))
+    lib().orc_assemble(dim, x.shape[0], x, c.shape[0], c, W)
+    return W
+
+
+def gram(W, y):
+    W = _f64(W); y = _f64(y)
+    n, m = W.shape
+    G = np.zeros((m, m)); b = np.zeros(m)
+    lib().orc_gram(n, m, W, y, G, b)
+    return G, b
+
+
+def enet(G, b, lam1, lam2, beta0=None, max_sweeps=200000):
+    """Elastic Net minimiser of Eq. (2) given G = W^T W, b = W^T y.
+
+    Returns (beta, info) with info = dict(sweeps, attempts, margin,
+    certified, support).
+    """
+    G = _f64(G); b = _f64(b)
+    m = b.shape[0]
+    beta = np.zeros(m) if beta0 is None else _f64(beta0).copy()
+    info = np.zeros(5)
+    lib().orc_enet(m, G, b, float(lam1), float(lam2), beta, int(max_sweeps), info)
+    return beta, dict(sweeps=int(info[0]), attempts=int(info[1]), margin=float(info[2]),
+                      certified=bool(info[3]), support=int(info[4]))
+
+
+def enet_objective(G, b, yty, lam1, lam2, beta):
+    return lib().orc_enet_objective(b.shape[0], _f64(G), _f64(b), float(yty), float(lam1),
+                                    float(lam2), _f64(beta))
+
+
+# --------------------------------------------------------------------------
+# Step 3
+# --------------------------------------------------------------------------
+
+def residual(W, beta, kv, vol):
+    W = _f64(W)
+    R = np.zeros(W.shape[0])
+    lib().orc_residual(W.shape[0], W.shape[1], W, _f64(beta), _f64(kv), float(vol), R)
+    return R
+
+
+def mark(R, eps_tol, k_top):
+    R = _f64(R)
+    out = np.zeros(max(int(k_top), 1), dtype=np.int32)
+    n = lib().orc_mark(R.shape[0], R, float(eps_tol), int(k_top), out)
+    return out[:n].copy()
+
+
+def enrich(dim, c, marked, x, ext_lo, ext_hi, eta, m_limit):
+    """Append the new centres of the marked cells; returns the grown [M', 4]."""
+    c = _f64(c)
+    m = c.shape[0]
+    cap = max(int(m_limit), m)
+    buf = np.zeros((cap, 4))
+    buf[:m] = c
+    x = _f64(x)
+    if x.shape[1] != 3:
+        x = _f64(np.concatenate([x, np.zeros((x.shape[0], 3 - x.shape[1]))], axis=1))
+    lo = _f64(list(ext_lo) + [0.0] * (3 - len(ext_lo)))
+    hi = _f64(list(ext_hi) + [0.0] * (3 - len(ext_hi)))
+    mk = _i32(marked)
+    mm = lib().orc_enrich(dim, m, buf, mk.shape[0], mk, x, lo, hi, float(eta), cap)
+    return buf[:mm].copy()
+
+
+# --------------------------------------------------------------------------
+# Algorithm 1 on all subdomains, and Step 4
+# --------------------------------------------------------------------------
+
+def default_params(**kw):
+    p = dict(lambda1_hat=4.59e-4, lambda2_hat=4.64e-6, eps_tol_rel=1e-3, eta=0.5,
+             k_top=37, m_max=1 << 30, levels=3, max_sweeps=200000)
+    p.update(kw)
+    return p
+
+
+def m_capacity(g, dim, k_top, levels, m_max):
+    m0 = int(np.prod(g))
+    return int(min(m0 + levels * (dim + 1) * k_top, m0 + m_max))
+
+
+def fit_all(K, n_cells, n_sub, overlap, g, params, which=None, m_cap=None):
+    """Algorithm 1 on every subdomain (or the subset ``which``).
+
+    Returns dict(boxes, M, c [S, m_cap, 4], beta [S, m_cap], info [S, NINFO],
+    m_cap, failed). Subdomains not in ``which`` are left empty (M = 0).
+    """
+    dim = len(n_cells)
+    boxes = partition(n_cells, n_sub, overlap)
+    S = boxes.shape[0]
+    P = _Params(**{k: params[k] for k, _ in _Params._fields_})
+    if m_cap is None:
+        m_cap = m_capacity(g, dim, params["k_top"], params["levels"], params["m_max"])
+    c = np.zeros((S, m_cap, 4)); beta = np.zeros((S, m_cap)); info = np.zeros((S, NINFO))
+    wh = None if which is None else _i32(which)
+    failed = lib().orc_fit_all(dim, _pad3(n_cells, 1), _f64(K).reshape(-1), S, boxes,
+                               _pad3(g, 1), C.byref(P), int(m_cap),
+                               None if wh is None else wh.ctypes.data, 0 if wh is None else wh.shape[0],
+                               c, beta, info)
+    M = info[:, 0].astype(np.int32)
+    return dict(boxes=boxes, M=M, c=c, beta=beta, info=info, m_cap=int(m_cap), failed=int(failed),
+                n_cells=tuple(n_cells), n_sub=tuple(n_sub))
+
+
+def evaluate(model, pts, log_space=False, return_owner=False):
+    """K*(x) (or its log) at points [n, dim] from a fitted model (Step 4)."""
+    n_cells, n_sub = model["n_cells"], model["n_sub"]
+    dim = len(n_cells)
+    pts = _f64(pts).reshape(-1, dim)
+    out = np.zeros(pts.shape[0])
+    own = np.zeros(pts.shape[0], dtype=np.int32)
+    lib().orc_eval(dim, _pad3(n_cells, 1), _pad3(n_sub, 1), int(model["m_cap"]), _i32(model["M"]),
+                   _f64(model["c"]), _f64(model["beta"]), pts.shape[0], pts, int(bool(log_space)),
+                   out, own.ctypes.data)
+    return (out, own) if return_owner else out
+
+
+def errors(model, K):
+    """dict(l1, l2, l1_log, max_log10) of the reconstruction over the source cells."""
+    n_cells, n_sub = model["n_cells"], model["n_sub"]
+    dim = len(n_cells)
+    err = np.zeros(4)
+    lib().orc_errors(dim, _pad3(n_cells, 1), _pad3(n_sub, 1), int(model["m_cap"]), _i32(model["M"]),
+                     _f64(model["c"]), _f64(model["beta"]), _f64(K).reshape(-1), err)
+    return dict(l1=err[0], l2=err[1], l1_log=err[2], max_log10=err[3])
