@@ -1,0 +1,218 @@
+/*
+ * pam.h -- C ABI of libpam, the GB300 (sm_103a) implementation of the PAM
+ * fitting path: Parallel and Adaptive Mesh-free approximation of cellwise
+ * constant coefficient data by Shepard-normalised Gaussian RBFs, fitted per
+ * subdomain by an Elastic Net with residual-driven refinement.
+ *
+ * The calls follow the paper's statement of the method (section 2):
+ *   pam_partition        Step 1   split the grid into subdomains
+ *   pam_fit_subdomains   Step 2   assemble, Gram products, Elastic Net solve
+ *   pam_refine           Step 3   indicators, marking, enrichment, re-solve
+ *                                 (Algorithm 1, repeated n_levels times)
+ *   pam_eval             Step 4   evaluate the piecewise surrogate anywhere
+ *   pam_errors                    relative L1/L2 errors over the source cells
+ *
+ * Conventions shared by every call:
+ *  - Grid: dim in {1,2,3}; n_cells[a] cells per axis (axes >= dim are 1);
+ *    isotropic cells of side h = 1/max_a n_cells[a]; cell (i,j,k) has the
+ *    centroid ((i+1/2)h, (j+1/2)h, (k+1/2)h) and global index
+ *    i + n_x (j + n_y k) (x fastest). Field arrays follow that order.
+ *  - Pointers named d_* are DEVICE pointers, h_* HOST pointers. Every
+ *    buffer is owned by the caller; the library allocates no memory.
+ *    Scratch comes from a caller workspace of pam_plan.workspace_bytes.
+ *  - Device work is enqueued on `stream` (a cudaStream_t, NULL = legacy
+ *    default stream). Calls that return device-side status synchronise
+ *    that stream once before returning; this is stated per call.
+ *  - Errors: arguments are validated on the host before any launch; an
+ *    invalid one returns PAM_ERR_INVALID_ARG and enqueues nothing. Device
+ *    code never traps: per-subdomain problems are reported in the info
+ *    array of the model (PAM_FLAG_*), and input faults through the status.
+ *  - Thread safety: calls on different workspaces/models may run
+ *    concurrently on different streams; calls sharing a workspace must be
+ *    ordered on one stream.
+ */
+#ifndef PAM_H
+#define PAM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define PAM_MAX_DIM 3
+#define PAM_MAX_M 1024         /* largest dictionary capacity per subdomain */
+#define PAM_INFO_N 8           /* int32 entries per subdomain in pam_model.info */
+
+typedef enum {
+    PAM_OK = 0,
+    PAM_ERR_INVALID_ARG = 1,   /* bad pointer, size, or parameter */
+    PAM_ERR_NONPOSITIVE_K = 2, /* a cell value is <= 0, NaN or Inf (the paper assumes 0 < K_min) */
+    PAM_ERR_CUDA = 3,          /* a CUDA runtime call failed */
+    PAM_ERR_WORKSPACE = 4,     /* workspace smaller than pam_plan.workspace_bytes */
+    PAM_ERR_NOT_CONVERGED = 5, /* some subdomain's solve was not certified (see info) */
+    PAM_ERR_UNSUPPORTED = 6    /* valid request this build does not serve */
+} pam_status;
+
+typedef enum {
+    PAM_PREC_FP64 = 0,   /* plain form: every step in binary64 */
+    PAM_PREC_MIXED = 1   /* Gram on tensor cores (bf16 hi/lo split, fp32 accumulate),
+                            fp32 active-set solve with iterative refinement,
+                            fp64 residual and error accumulation */
+} pam_precision;
+
+/* Per-subdomain info entries (pam_model.info[s * PAM_INFO_N + k]). */
+enum {
+    PAM_INFO_M = 0,        /* current dictionary size M_i */
+    PAM_INFO_SUPPORT = 1,  /* nonzero coefficients */
+    PAM_INFO_LEVELS = 2,   /* enrichment rounds done */
+    PAM_INFO_ITERS = 3,    /* active-set iterations of the last solve */
+    PAM_INFO_FLAGS = 4,    /* PAM_FLAG_* bits */
+    PAM_INFO_STOPPED = 5,  /* 1 once Algorithm 1 stopped for this subdomain */
+    PAM_INFO_N_CELLS = 6,  /* patch cells N_i */
+    PAM_INFO_MARKED = 7    /* cells marked in the last round */
+};
+
+enum {
+    PAM_FLAG_NOT_CERTIFIED = 1, /* the last solve did not pass the optimality check */
+    PAM_FLAG_CHOLESKY = 2,      /* a non-positive pivot (never expected: lambda2 > 0) */
+    PAM_FLAG_REFINE_DIVERGED = 4/* mixed form: refinement stalled; solved in fp64 instead */
+};
+
+/* The problem: grid, decomposition and initial dictionary (section 2 Step 1;
+ * Algorithm 1 inputs). */
+typedef struct {
+    int dim;
+    int n_cells[PAM_MAX_DIM];
+    int n_sub[PAM_MAX_DIM];   /* subdomains per axis; cores split axis a as
+                                 [floor(j n / p), floor((j+1) n / p)) */
+    int overlap;              /* patch = core grown by `overlap` cells, clipped */
+    int g_init[PAM_MAX_DIM];  /* initial uniform lattice per subdomain core */
+} pam_problem;
+
+/* Algorithm 1 parameters. */
+typedef struct {
+    double lambda1_hat;  /* Elastic Net weights per sample: lambda_k = N_i * lambda_k_hat */
+    double lambda2_hat;  /*   (Eq. (2); Example 2 prints 4.59e-4 and 4.64e-6) */
+    double eps_tol_rel;  /* eps_tol = |T| (eps_tol_rel * max_{T in patch} K_T)^2;
+                            negative: no tolerance, always mark k_top cells */
+    double eta;          /* width ratio of new centres, in (0,1) (section 3.4) */
+    int k_top;           /* cells marked per round (Algorithm 1 K_top) */
+    int m_max;           /* at most m_max centres added per subdomain (M_max) */
+    int levels;          /* enrichment rounds planned (sizes the capacity) */
+    int max_iters;       /* active-set iteration cap per solve (0: default 64) */
+    int precision;       /* pam_precision */
+} pam_params;
+
+/* Sizes derived from a problem and parameters by pam_plan_create. */
+typedef struct {
+    int n_subdomains;
+    int max_patch_cells;     /* max_i N_i */
+    int m0;                  /* initial dictionary size prod g_init */
+    int m_cap;               /* dictionary capacity per subdomain (<= PAM_MAX_M) */
+    int64_t n_grid_cells;
+    size_t workspace_bytes;  /* device scratch the fit/refine/error calls need */
+} pam_plan;
+
+/* Device model, caller-owned (sizes from pam_plan):
+ *   boxes   int32  [S][12]  core_lo[3], core_hi[3], patch_lo[3], patch_hi[3]
+ *   centres double [S][m_cap][4]  (c_x, c_y, c_z, sigma); unused axes 0
+ *   beta    double [S][m_cap]     coefficients (log space), zero past M_i
+ *   info    int32  [S][PAM_INFO_N]  */
+typedef struct {
+    int32_t *boxes;
+    double *centres;
+    double *beta;
+    int32_t *info;
+} pam_model;
+
+/* Library version string (static storage). */
+const char *pam_version(void);
+
+/* Human-readable name of a status (static storage). */
+const char *pam_status_string(pam_status s);
+
+/*
+ * Sizes for `prob` and `par` (host only, no device work).
+ * m_cap = min(prod g_init + levels (dim+1) k_top, prod g_init + m_max),
+ * rounded up to a multiple of 32; PAM_ERR_UNSUPPORTED if it exceeds
+ * PAM_MAX_M. Returns PAM_ERR_INVALID_ARG for an inconsistent problem
+ * (dim outside 1..3, n_sub[a] outside 1..n_cells[a], overlap < 0,
+ * g_init < 1, lambda's < 0 or lambda2_hat == 0, eta outside (0,1),
+ * k_top < 0, m_max < 0, levels < 0, precision unknown).
+ */
+pam_status pam_plan_create(const pam_problem *prob, const pam_params *par, pam_plan *out);
+
+/*
+ * Step 1 (section 2) on the host: core and patch boxes of every subdomain,
+ * h_boxes [S][12] (layout of pam_model.boxes). Cores are non-overlapping and
+ * every cell belongs to exactly one (the half-open decomposition of
+ * Experiment 1.2); patches add `overlap` cells of fit data around a core.
+ */
+pam_status pam_partition(const pam_problem *prob, int32_t *h_boxes);
+
+/*
+ * Step 2 (section 2) for every subdomain: copy the partition into
+ * model->boxes, lay down the initial dictionary (uniform g_init lattice over
+ * each core box, cell-centred, sigma = lattice spacing), then assemble the
+ * Shepard-normalised feature matrix W (Eq. (10)) of the Gaussians (Eq. (6))
+ * at the patch centroids, form G = W^T W and b = W^T ln K, and solve the
+ * Elastic Net (Eq. (2)) on ln K (Remark on log K, section 3.3) from beta = 0.
+ * d_K: device double [n_grid_cells], the cell values, all > 0 and finite.
+ * Synchronises `stream` once (to read the input check and the certificates).
+ * Returns PAM_ERR_NONPOSITIVE_K if some K_T <= 0, NaN or Inf (nothing is
+ * fitted then), PAM_ERR_NOT_CONVERGED if a subdomain's solve was not
+ * certified (its info carries PAM_FLAG_NOT_CERTIFIED), else PAM_OK.
+ */
+pam_status pam_fit_subdomains(const pam_problem *prob, const pam_params *par,
+                              const pam_plan *plan, const double *d_K,
+                              pam_model *model, void *d_workspace,
+                              size_t workspace_bytes, void *stream);
+
+/*
+ * Step 3 (section 2; Algorithm 1 (2)-(5)) n_levels times on every
+ * subdomain still running: residual indicators R_T (Eq. (4), midpoint
+ * rule), marking of the k_top largest R_T >= eps_tol, d+1 new centres per
+ * marked cell at width eta * sigma_parent, zero extension of beta, and the
+ * re-assembly and re-solve on the enlarged dictionary. A subdomain stops
+ * when nothing is marked or its size reaches m0 + m_max (info STOPPED).
+ * Must follow pam_fit_subdomains on the same model, workspace and d_K.
+ * Synchronises `stream` once; returns as pam_fit_subdomains.
+ */
+pam_status pam_refine(const pam_problem *prob, const pam_params *par,
+                      const pam_plan *plan, const double *d_K, pam_model *model,
+                      int n_levels, void *d_workspace, size_t workspace_bytes,
+                      void *stream);
+
+/*
+ * Step 4 (section 2): K*(x) = exp(sum_m beta_m w_m(x)) with the Shepard
+ * weights w_m (Eq. (9)) over the whole dictionary of the subdomain whose
+ * core contains x (half-open cores, outer face of the grid closed).
+ * d_pts: device double [n_pts][dim]; d_out: device double [n_pts], K*(x),
+ * or the log-space value when log_space != 0; NaN for points outside the
+ * grid. precision PAM_PREC_MIXED evaluates the Gaussians in fp32.
+ * Asynchronous (no synchronisation); n_pts == 0 is a no-op.
+ */
+pam_status pam_eval(const pam_problem *prob, const pam_plan *plan,
+                    const pam_model *model, const double *d_pts, int64_t n_pts,
+                    double *d_out, int log_space, int precision, void *stream);
+
+/*
+ * Relative errors of the reconstruction over the source cells, each cell
+ * measured with its owner's surrogate at its centroid:
+ * d_err[0] = sum |K_T - K*| / sum |K_T|, d_err[1] = (Eq. (12))
+ * (sum (K_T - K*)^2 / sum K_T^2)^(1/2), d_err[2] = sum |ln K_T - ln K*| /
+ * sum |ln K_T|, d_err[3] = max_T |log10 K_T - log10 K*(x_T)|; fp64
+ * accumulation. d_err: device double [4]. Uses the workspace.
+ * Asynchronous.
+ */
+pam_status pam_errors(const pam_problem *prob, const pam_plan *plan,
+                      const pam_model *model, const double *d_K, double *d_err,
+                      void *d_workspace, size_t workspace_bytes, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PAM_H */

@@ -1,0 +1,300 @@
+// pam_api.cu -- host side of libpam: argument validation, sizes, workspace
+// carve-up and the order of the launches of each C-ABI entry point.
+#include <cmath>
+#include <cstring>
+
+#include "pam_internal.cuh"
+
+namespace pam {
+
+static size_t align_up(size_t v, size_t a) { return (v + a - 1) / a * a; }
+
+static int64_t prod3(const int v[3]) { return (int64_t)v[0] * v[1] * v[2]; }
+
+// Validates a problem/parameter pair and fills the kernel-side view.
+// `par` may be NULL (calls that need only the geometry).
+bool make_geo(const pam_problem *prob, const pam_params *par, Geo *g, Par *p, pam_status *st) {
+    *st = PAM_ERR_INVALID_ARG;
+    if (!prob) return false;
+    memset(g, 0, sizeof(*g));
+    if (prob->dim < 1 || prob->dim > 3) return false;
+    g->dim = prob->dim;
+    int64_t S = 1, nmax = 1;
+    for (int a = 0; a < 3; ++a) {
+        bool used = a < prob->dim;
+        g->n[a] = used ? prob->n_cells[a] : 1;
+        g->p[a] = used ? prob->n_sub[a] : 1;
+        g->g[a] = used ? prob->g_init[a] : 1;
+        if (g->n[a] < 1 || g->n[a] > (1 << 24)) return false;
+        if (g->p[a] < 1 || g->p[a] > g->n[a]) return false;
+        if (g->g[a] < 1) return false;
+        S *= g->p[a];
+        if (g->n[a] > nmax) nmax = g->n[a];
+    }
+    if (prob->overlap < 0) return false;
+    if (S > 65535) return false;
+    if (prod3(g->n) > ((int64_t)1 << 40)) return false;
+    g->overlap = prob->overlap;
+    g->S = (int)S;
+    g->nmax = (int)nmax;
+    g->h = 1.0 / (double)nmax;
+    g->vol = 1.0;
+    for (int a = 0; a < g->dim; ++a) g->vol *= g->h;
+    // largest patch: the widest core along each axis grown by the overlap
+    int64_t nm = 1;
+    for (int a = 0; a < 3; ++a) {
+        int widest = 0;
+        for (int j = 0; j < g->p[a]; ++j) {
+            int64_t lo = ((int64_t)j * g->n[a]) / g->p[a], hi = ((int64_t)(j + 1) * g->n[a]) / g->p[a];
+            int64_t plo = lo - (a < g->dim ? g->overlap : 0), phi = hi + (a < g->dim ? g->overlap : 0);
+            if (plo < 0) plo = 0;
+            if (phi > g->n[a]) phi = g->n[a];
+            if (phi - plo > widest) widest = (int)(phi - plo);
+        }
+        nm *= widest;
+    }
+    if (nm > (1 << 20)) { *st = PAM_ERR_UNSUPPORTED; return false; }
+    g->n_max = (int)align_up((size_t)nm, 32);
+    g->m0 = (int)prod3(g->g);
+    if (g->m0 > PAM_MAX_M) { *st = PAM_ERR_UNSUPPORTED; return false; }
+    g->m_cap = (int)align_up((size_t)g->m0, 64);
+    if (par) {
+        if (!(par->lambda1_hat >= 0.0) || !(par->lambda2_hat > 0.0)) return false;
+        if (!std::isfinite(par->lambda1_hat) || !std::isfinite(par->lambda2_hat)) return false;
+        if (!(par->eta > 0.0 && par->eta < 1.0)) return false;
+        if (std::isnan(par->eps_tol_rel)) return false;
+        if (par->k_top < 0 || par->m_max < 0 || par->levels < 0 || par->max_iters < 0) return false;
+        if (par->precision != PAM_PREC_FP64 && par->precision != PAM_PREC_MIXED) return false;
+        if (par->precision == PAM_PREC_MIXED) { *st = PAM_ERR_UNSUPPORTED; return false; }
+        int64_t add = (int64_t)par->levels * (g->dim + 1) * par->k_top;
+        if (add > par->m_max) add = par->m_max;
+        int64_t cap = (int64_t)g->m0 + add;
+        cap = (int64_t)align_up((size_t)cap, 64);
+        if (cap > PAM_MAX_M) { *st = PAM_ERR_UNSUPPORTED; return false; }
+        g->m_cap = (int)cap;
+        if (p) {
+            p->lam1_hat = par->lambda1_hat;
+            p->lam2_hat = par->lambda2_hat;
+            p->eps_tol_rel = par->eps_tol_rel;
+            p->eta = par->eta;
+            p->k_top = par->k_top;
+            p->m_max = par->m_max;
+            p->levels = par->levels;
+            p->max_iters = par->max_iters > 0 ? par->max_iters : 64;
+        }
+    }
+    *st = PAM_OK;
+    return true;
+}
+
+// Region sizes. Small regions come first so that calls which use only them
+// (errors) agree with the fit calls on where they live.
+static size_t carve(const Geo &g, char *base, Ws *w) {
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> char * {
+        char *p = base ? base + off : nullptr;
+        off = align_up(off + bytes, 256);
+        return p;
+    };
+    const size_t S = (size_t)g.S, nm = (size_t)g.n_max, mc = (size_t)g.m_cap;
+    w->status = (int32_t *)take(8 * sizeof(int32_t));
+    w->kmax_bits = (unsigned long long *)take(S * sizeof(unsigned long long));
+    w->err_part = (double *)take((size_t)kErrBlocks * 4 * sizeof(double));
+    w->y = (double *)take(S * nm * sizeof(double));
+    w->kv = (double *)take(S * nm * sizeof(double));
+    w->inv_s = (double *)take(S * nm * sizeof(double));
+    w->R = (double *)take(S * nm * sizeof(double));
+    w->rowmax = (float *)take(S * nm * sizeof(float));
+    w->rowinv = (float *)take(S * nm * sizeof(float));
+    w->b = (double *)take(S * mc * sizeof(double));
+    w->L = (double *)take(S * (mc * (mc + 1) / 2) * sizeof(double));
+    w->G = (double *)take(S * mc * mc * sizeof(double));
+    w->Gf = (float *)w->G;  // the mixed form keeps its fp32 Gram in the same region
+    w->E = (double *)take(S * mc * nm * sizeof(double));
+    w->bytes = off;
+    return off;
+}
+
+Ws carve_workspace(const Geo &g, void *base) {
+    Ws w;
+    carve(g, (char *)base, &w);
+    return w;
+}
+
+}  // namespace pam
+
+using namespace pam;
+
+extern "C" {
+
+const char *pam_version(void) { return "libpam 0.1 (sm_103a)"; }
+
+const char *pam_status_string(pam_status s) {
+    switch (s) {
+        case PAM_OK: return "ok";
+        case PAM_ERR_INVALID_ARG: return "invalid argument";
+        case PAM_ERR_NONPOSITIVE_K: return "cell value <= 0, NaN or Inf";
+        case PAM_ERR_CUDA: return "CUDA runtime error";
+        case PAM_ERR_WORKSPACE: return "workspace too small";
+        case PAM_ERR_NOT_CONVERGED: return "a subdomain solve was not certified";
+        case PAM_ERR_UNSUPPORTED: return "unsupported size";
+    }
+    return "unknown status";
+}
+
+pam_status pam_plan_create(const pam_problem *prob, const pam_params *par, pam_plan *out) {
+    if (!prob || !par || !out) return PAM_ERR_INVALID_ARG;
+    Geo g;
+    Par p;
+    pam_status st;
+    if (!make_geo(prob, par, &g, &p, &st)) return st;
+    Ws w;
+    out->n_subdomains = g.S;
+    out->max_patch_cells = g.n_max;
+    out->m0 = g.m0;
+    out->m_cap = g.m_cap;
+    out->n_grid_cells = prod3(g.n);
+    out->workspace_bytes = carve(g, nullptr, &w);
+    return PAM_OK;
+}
+
+pam_status pam_partition(const pam_problem *prob, int32_t *h_boxes) {
+    if (!prob || !h_boxes) return PAM_ERR_INVALID_ARG;
+    Geo g;
+    pam_status st;
+    if (!make_geo(prob, nullptr, &g, nullptr, &st)) return st;
+    for (int s = 0; s < g.S; ++s) {
+        int j[3] = {s % g.p[0], (s / g.p[0]) % g.p[1], s / (g.p[0] * g.p[1])};
+        for (int a = 0; a < 3; ++a) {
+            int lo = (int)(((int64_t)j[a] * g.n[a]) / g.p[a]);
+            int hi = (int)(((int64_t)(j[a] + 1) * g.n[a]) / g.p[a]);
+            int ov = a < g.dim ? g.overlap : 0;
+            h_boxes[s * 12 + a] = lo;
+            h_boxes[s * 12 + 3 + a] = hi;
+            h_boxes[s * 12 + 6 + a] = lo - ov < 0 ? 0 : lo - ov;
+            h_boxes[s * 12 + 9 + a] = hi + ov > g.n[a] ? g.n[a] : hi + ov;
+        }
+    }
+    return PAM_OK;
+}
+
+static bool model_ok(const pam_model *m) {
+    return m && m->boxes && m->centres && m->beta && m->info;
+}
+
+static pam_status check_plan(const Geo &g, const pam_plan *plan) {
+    if (!plan) return PAM_ERR_INVALID_ARG;
+    if (plan->n_subdomains != g.S || plan->m_cap < g.m_cap || plan->max_patch_cells != g.n_max ||
+        plan->m_cap > PAM_MAX_M || plan->m_cap % 64 != 0)
+        return PAM_ERR_INVALID_ARG;
+    return PAM_OK;
+}
+
+// Reads the device status words after the enqueued work (one sync).
+static pam_status read_status(const Ws &w, cudaStream_t st, int32_t host[8]) {
+    PAM_CUDA_TRY(cudaMemcpyAsync(host, w.status, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, st));
+    PAM_CUDA_TRY(cudaStreamSynchronize(st));
+    return PAM_OK;
+}
+
+pam_status pam_fit_subdomains(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                              const double *d_K, pam_model *model, void *d_workspace,
+                              size_t workspace_bytes, void *stream) {
+    Geo g;
+    Par p;
+    pam_status st;
+    if (!par || !make_geo(prob, par, &g, &p, &st)) return par ? st : PAM_ERR_INVALID_ARG;
+    if ((st = check_plan(g, plan)) != PAM_OK) return st;
+    g.m_cap = plan->m_cap;
+    if (!d_K || !model_ok(model) || !d_workspace) return PAM_ERR_INVALID_ARG;
+    Ws w = carve_workspace(g, d_workspace);
+    if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 8 * sizeof(int32_t), s));
+    launch_partition(g, model->boxes, s);
+    launch_prepare(g, model->boxes, d_K, w, s);
+    PAM_CUDA_TRY(cudaGetLastError());
+    int32_t hs[8];
+    if ((st = read_status(w, s, hs)) != PAM_OK) return st;
+    if (hs[kStBadK]) return PAM_ERR_NONPOSITIVE_K;
+    launch_init_dictionary(g, model->boxes, model->centres, model->beta, model->info, s);
+    if (par->precision == PAM_PREC_MIXED)
+        launch_solve_level_mixed(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
+    else
+        launch_solve_level_f64(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
+    PAM_CUDA_TRY(cudaGetLastError());
+    if ((st = read_status(w, s, hs)) != PAM_OK) return st;
+    return hs[kStUncertified] ? PAM_ERR_NOT_CONVERGED : PAM_OK;
+}
+
+pam_status pam_refine(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                      const double *d_K, pam_model *model, int n_levels, void *d_workspace,
+                      size_t workspace_bytes, void *stream) {
+    Geo g;
+    Par p;
+    pam_status st;
+    if (!par || !make_geo(prob, par, &g, &p, &st)) return par ? st : PAM_ERR_INVALID_ARG;
+    if ((st = check_plan(g, plan)) != PAM_OK) return st;
+    g.m_cap = plan->m_cap;
+    if (!d_K || !model_ok(model) || !d_workspace || n_levels < 0) return PAM_ERR_INVALID_ARG;
+    Ws w = carve_workspace(g, d_workspace);
+    if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 8 * sizeof(int32_t), s));
+    for (int lv = 0; lv < n_levels; ++lv) {
+        launch_refine_round(g, p, par->precision, model->boxes, model->centres, model->beta,
+                            model->info, w, s);
+        if (par->precision == PAM_PREC_MIXED)
+            launch_solve_level_mixed(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
+        else
+            launch_solve_level_f64(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
+    }
+    PAM_CUDA_TRY(cudaGetLastError());
+    int32_t hs[8];
+    if ((st = read_status(w, s, hs)) != PAM_OK) return st;
+    return hs[kStUncertified] ? PAM_ERR_NOT_CONVERGED : PAM_OK;
+}
+
+pam_status pam_eval(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
+                    const double *d_pts, int64_t n_pts, double *d_out, int log_space, int precision,
+                    void *stream) {
+    Geo g;
+    pam_status st;
+    if (!make_geo(prob, nullptr, &g, nullptr, &st)) return st;
+    if (!plan || plan->n_subdomains != g.S || plan->m_cap > PAM_MAX_M || plan->m_cap < 1)
+        return PAM_ERR_INVALID_ARG;
+    g.m_cap = plan->m_cap;
+    g.n_max = plan->max_patch_cells;
+    if (n_pts < 0 || !model_ok(model)) return PAM_ERR_INVALID_ARG;
+    if (precision != PAM_PREC_FP64 && precision != PAM_PREC_MIXED) return PAM_ERR_INVALID_ARG;
+    if (precision == PAM_PREC_MIXED) return PAM_ERR_UNSUPPORTED;
+    if (n_pts == 0) return PAM_OK;
+    if (!d_pts || !d_out) return PAM_ERR_INVALID_ARG;
+    launch_eval(g, model->boxes, model->centres, model->beta, model->info, d_pts, n_pts, d_out,
+                log_space, precision, (cudaStream_t)stream);
+    PAM_CUDA_TRY(cudaGetLastError());
+    return PAM_OK;
+}
+
+pam_status pam_errors(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
+                      const double *d_K, double *d_err, void *d_workspace, size_t workspace_bytes,
+                      void *stream) {
+    Geo g;
+    pam_status st;
+    if (!make_geo(prob, nullptr, &g, nullptr, &st)) return st;
+    if (!plan || plan->n_subdomains != g.S || plan->m_cap > PAM_MAX_M || plan->m_cap < 1)
+        return PAM_ERR_INVALID_ARG;
+    g.m_cap = plan->m_cap;
+    g.n_max = plan->max_patch_cells;
+    if (!model_ok(model) || !d_K || !d_err || !d_workspace) return PAM_ERR_INVALID_ARG;
+    Ws w = carve_workspace(g, d_workspace);
+    if (workspace_bytes < (size_t)((char *)w.err_part - (char *)d_workspace) +
+                              (size_t)kErrBlocks * 4 * sizeof(double))
+        return PAM_ERR_WORKSPACE;
+    launch_errors(g, model->boxes, model->centres, model->beta, model->info, d_K, d_err, w,
+                  (cudaStream_t)stream);
+    PAM_CUDA_TRY(cudaGetLastError());
+    return PAM_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,786 @@
+// pam_f64.cu -- the plain (binary64) form of the PAM fitting path on sm_103a,
+// plus the precision-independent kernels (partition, cell preparation,
+// dictionary set-up, marking/enrichment, evaluation, errors).
+//
+// Data layout in HBM (per subdomain s, strides from the plan):
+//   cells:   y = ln K, kv = K, inv_s, R  [S][n_max]   (patch order, x fastest)
+//   E        [S][m_cap][n_max]  exp(l_jm - l_j*), transposed so that the
+//            cell index is contiguous (coalesced along threads = cells)
+//   G        [S][m_cap][m_cap]  W^T W, both triangles
+//   b        [S][m_cap]         W^T y
+//   model    centres [S][m_cap][4] = (c, sigma), beta [S][m_cap]
+#include <cfloat>
+#include <cmath>
+
+#include "pam_internal.cuh"
+
+namespace pam {
+
+// --------------------------------------------------------------------------
+// Step 1 on the device: core and patch boxes (same rule as pam_partition).
+// --------------------------------------------------------------------------
+__global__ void k_partition(Geo g, int32_t *boxes) {
+    int s = blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= g.S) return;
+    int j[3] = {s % g.p[0], (s / g.p[0]) % g.p[1], s / (g.p[0] * g.p[1])};
+    for (int a = 0; a < 3; ++a) {
+        int lo = (int)(((int64_t)j[a] * g.n[a]) / g.p[a]);
+        int hi = (int)(((int64_t)(j[a] + 1) * g.n[a]) / g.p[a]);
+        int ov = a < g.dim ? g.overlap : 0;
+        boxes[s * 12 + a] = lo;
+        boxes[s * 12 + 3 + a] = hi;
+        boxes[s * 12 + 6 + a] = lo - ov < 0 ? 0 : lo - ov;
+        boxes[s * 12 + 9 + a] = hi + ov > g.n[a] ? g.n[a] : hi + ov;
+    }
+}
+
+void launch_partition(const Geo &g, int32_t *boxes, cudaStream_t st) {
+    k_partition<<<(g.S + 127) / 128, 128, 0, st>>>(g, boxes);
+}
+
+// --------------------------------------------------------------------------
+// Patch cell data: y = ln K (Remark on log K, section 3.3), K, the patch
+// maximum of K, and the input check K > 0 finite.
+// --------------------------------------------------------------------------
+__global__ void k_prepare(Geo g, const int32_t *boxes, const double *K, Ws w) {
+    int s = blockIdx.y;
+    const int32_t *box = boxes + s * 12;
+    int ext[3];
+    patch_extent(box, ext);
+    int N = ext[0] * ext[1] * ext[2];
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double kmax = 0.0;
+    if (t < g.n_max) {
+        size_t o = (size_t)s * g.n_max + t;
+        if (t < N) {
+            double x[3];
+            int64_t gi;
+            patch_cell(g, box, t, x, &gi);
+            double k = K[gi];
+            if (!(k > 0.0) || !(k <= DBL_MAX)) {
+                atomicAdd(&w.status[kStBadK], 1);
+                k = 1.0;
+            }
+            w.y[o] = log(k);
+            w.kv[o] = k;
+            kmax = k;
+        } else {
+            w.y[o] = 0.0;
+            w.kv[o] = 0.0;
+        }
+    }
+    // positive doubles order like their bit patterns
+    double m = warp_max(kmax);
+    if ((threadIdx.x & 31) == 0 && m > 0.0)
+        atomicMax(&w.kmax_bits[s], (unsigned long long)__double_as_longlong(m));
+}
+
+void launch_prepare(const Geo &g, const int32_t *boxes, const double *K, const Ws &w,
+                    cudaStream_t st) {
+    cudaMemsetAsync(w.kmax_bits, 0, sizeof(unsigned long long) * g.S, st);
+    dim3 grid((g.n_max + 255) / 256, g.S);
+    k_prepare<<<grid, 256, 0, st>>>(g, boxes, K, w);
+}
+
+// --------------------------------------------------------------------------
+// Initial dictionary (Algorithm 1 input): a uniform g lattice over each core
+// box, cell-centred, sigma = the lattice spacing (largest over the axes).
+// --------------------------------------------------------------------------
+__global__ void k_init_dictionary(Geo g, const int32_t *boxes, double *centres, double *beta,
+                                  int32_t *info) {
+    int s = blockIdx.y;
+    int m = blockIdx.x * blockDim.x + threadIdx.x;
+    const int32_t *box = boxes + s * 12;
+    if (m < g.m_cap) {
+        double lo[3] = {0, 0, 0}, sp[3] = {0, 0, 0};
+        double sigma = 0.0;
+        for (int a = 0; a < g.dim; ++a) {
+            lo[a] = __dmul_rn((double)box[a], g.h);
+            sp[a] = __ddiv_rn(__dmul_rn((double)(box[3 + a] - box[a]), g.h), (double)g.g[a]);
+            sigma = fmax(sigma, sp[a]);
+        }
+        double *c = centres + ((size_t)s * g.m_cap + m) * 4;
+        if (m < g.m0) {
+            int idx[3] = {m % g.g[0], (m / g.g[0]) % g.g[1], m / (g.g[0] * g.g[1])};
+            for (int a = 0; a < 3; ++a)
+                c[a] = a < g.dim ? __dadd_rn(lo[a], __dmul_rn((double)idx[a] + 0.5, sp[a])) : 0.0;
+            c[3] = sigma;
+        } else {
+            c[0] = c[1] = c[2] = c[3] = 0.0;
+        }
+        beta[(size_t)s * g.m_cap + m] = 0.0;
+    }
+    if (m == 0) {
+        int ext[3];
+        patch_extent(box, ext);
+        int32_t *inf = info + s * kInfoN;
+        inf[PAM_INFO_M] = g.m0;
+        inf[PAM_INFO_SUPPORT] = 0;
+        inf[PAM_INFO_LEVELS] = 0;
+        inf[PAM_INFO_ITERS] = 0;
+        inf[PAM_INFO_FLAGS] = 0;
+        inf[PAM_INFO_STOPPED] = 0;
+        inf[PAM_INFO_N_CELLS] = ext[0] * ext[1] * ext[2];
+        inf[PAM_INFO_MARKED] = 0;
+    }
+}
+
+void launch_init_dictionary(const Geo &g, const int32_t *boxes, double *centres, double *beta,
+                            int32_t *info, cudaStream_t st) {
+    dim3 grid((g.m_cap + 127) / 128, g.S);
+    k_init_dictionary<<<grid, 128, 0, st>>>(g, boxes, centres, beta, info);
+}
+
+// --------------------------------------------------------------------------
+// Assembly, Eq. (6) and (10): E_jm = exp(l_jm - l_j*), inv_s_j = 1 / sum_m E_jm,
+// so that W_jm = E_jm inv_s_j; l_jm = -|x_j - c_m|^2 / (2 sigma_m^2).
+// One thread per patch cell, the dictionary staged in shared memory.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_assemble_f64(Geo g, const int32_t *boxes,
+                                                      const double *centres, const int32_t *info,
+                                                      Ws w) {
+    int s = blockIdx.y;
+    const int32_t *inf = info + s * kInfoN;
+    if (inf[PAM_INFO_STOPPED]) return;
+    int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
+    extern __shared__ dvec4 sc[];  // (c_x, c_y, c_z, -1/(2 sigma^2))
+    const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        dvec4 c = cg[m];
+        c.w = -1.0 / (2.0 * c.w * c.w);
+        sc[m] = c;
+    }
+    __syncthreads();
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    double x[3];
+    int64_t gi;
+    patch_cell(g, boxes + s * 12, t, x, &gi);
+    double lmax = -INFINITY;
+    for (int m = 0; m < M; ++m) {
+        dvec4 c = sc[m];
+        double d0 = x[0] - c.x, d1 = x[1] - c.y, d2 = x[2] - c.z;
+        double l = (d0 * d0 + d1 * d1 + d2 * d2) * c.w;
+        lmax = fmax(lmax, l);
+    }
+    double sum = 0.0;
+    double *E = w.E + (size_t)s * g.m_cap * g.n_max + t;
+    for (int m = 0; m < M; ++m) {
+        dvec4 c = sc[m];
+        double d0 = x[0] - c.x, d1 = x[1] - c.y, d2 = x[2] - c.z;
+        double e = exp((d0 * d0 + d1 * d1 + d2 * d2) * c.w - lmax);
+        E[(size_t)m * g.n_max] = e;
+        sum += e;
+    }
+    w.inv_s[(size_t)s * g.n_max + t] = 1.0 / sum;
+}
+
+// b_m = sum_j W_jm y_j, one warp per (subdomain, centre).
+__global__ void k_bvec_f64(Geo g, const int32_t *info, Ws w) {
+    int s = blockIdx.y;
+    const int32_t *inf = info + s * kInfoN;
+    if (inf[PAM_INFO_STOPPED]) return;
+    int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
+    int m = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
+    int lane = threadIdx.x & 31;
+    if (m >= M) return;
+    const double *E = w.E + ((size_t)s * g.m_cap + m) * g.n_max;
+    const double *iv = w.inv_s + (size_t)s * g.n_max;
+    const double *y = w.y + (size_t)s * g.n_max;
+    double acc = 0.0;
+    for (int t = lane; t < N; t += 32) acc += E[t] * iv[t] * y[t];
+    acc = warp_sum(acc);
+    if (lane == 0) w.b[(size_t)s * g.m_cap + m] = acc;
+}
+
+// G = W^T W on 64 x 64 tiles of the upper triangle, mirrored; fp64 FMA.
+constexpr int kGT = 64, kGK = 16;
+__global__ void __launch_bounds__(256) k_gram_f64(Geo g, const int32_t *info, Ws w) {
+    int s = blockIdx.y;
+    const int32_t *inf = info + s * kInfoN;
+    if (inf[PAM_INFO_STOPPED]) return;
+    int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
+    int T = g.m_cap / kGT;
+    int u = blockIdx.x, ti = 0;
+    while (u >= T - ti) { u -= T - ti; ++ti; }
+    int tj = ti + u;
+    int I0 = ti * kGT, J0 = tj * kGT;
+    if (I0 >= M || J0 >= M) return;
+    __shared__ double As[kGK][kGT + 1], Bs[kGK][kGT + 1];
+    const double *E = w.E + (size_t)s * g.m_cap * g.n_max;
+    const double *iv = w.inv_s + (size_t)s * g.n_max;
+    int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
+    double acc[4][4] = {};
+    for (int t0 = 0; t0 < N; t0 += kGK) {
+        for (int e = tid; e < kGT * kGK; e += 256) {
+            int row = e / kGK, kk = e % kGK, t = t0 + kk;
+            double sc = t < N ? iv[t] : 0.0;
+            double a = (t < N && I0 + row < M) ? E[(size_t)(I0 + row) * g.n_max + t] * sc : 0.0;
+            double b = (t < N && J0 + row < M) ? E[(size_t)(J0 + row) * g.n_max + t] * sc : 0.0;
+            As[kk][row] = a;
+            Bs[kk][row] = b;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int kk = 0; kk < kGK; ++kk) {
+            double av[4], bv[4];
+#pragma unroll
+            for (int q = 0; q < 4; ++q) { av[q] = As[kk][ty + 16 * q]; bv[q] = Bs[kk][tx + 16 * q]; }
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+#pragma unroll
+                for (int j = 0; j < 4; ++j) acc[i][j] = fma(av[i], bv[j], acc[i][j]);
+        }
+        __syncthreads();
+    }
+    double *G = w.G + (size_t)s * g.m_cap * g.m_cap;
+    for (int i = 0; i < 4; ++i)
+        for (int j = 0; j < 4; ++j) {
+            int r = I0 + ty + 16 * i, c = J0 + tx + 16 * j;
+            if (r < M && c < M) {
+                G[(size_t)r * g.m_cap + c] = acc[i][j];
+                G[(size_t)c * g.m_cap + r] = acc[i][j];
+            }
+        }
+}
+
+// --------------------------------------------------------------------------
+// Elastic Net, Eq. (2), in normal-equation form: primal-dual active-set
+// iterations. For a guess of the support S and signs s_S, the stationarity
+// condition on S is the SPD system (G_SS + lambda2 I) x_S = b_S - lambda1 s_S
+// (Cholesky). The guess is corrected until the optimality conditions hold:
+// sign(x_S) = s_S and |b_j - G_jS x_S| <= lambda1 (1 + 1e-9) off S, which
+// certify the unique minimiser (strict convexity for lambda2 > 0).
+// One block per subdomain; the warm start is the previous coefficients
+// extended by zeros (Algorithm 1 (5)). After 16 full corrections the
+// corrections go one index at a time.
+// --------------------------------------------------------------------------
+constexpr int kSolveThreads = 256;
+constexpr int kFactorSmemBytes = 80 * 1024;
+
+struct SolveShared {
+    int cnt, bad, viol, flag, worst;
+    double worst_v;
+};
+
+// Packed lower-triangular index.
+__device__ __forceinline__ size_t tri(int p, int q) { return (size_t)p * (p + 1) / 2 + q; }
+
+__device__ void compact_active(const int *sg, int M, int *idx, int *cnt) {
+    // warp 0 scans in chunks of 32 (ascending j)
+    if (threadIdx.x < 32) {
+        int lane = threadIdx.x, base = 0;
+        for (int j0 = 0; j0 < M; j0 += 32) {
+            int j = j0 + lane;
+            bool on = j < M && sg[j] != 0;
+            unsigned bal = __ballot_sync(0xffffffffu, on);
+            if (on) idx[base + __popc(bal & ((1u << lane) - 1u))] = j;
+            base += __popc(bal);
+        }
+        if (lane == 0) *cnt = base;
+    }
+    __syncthreads();
+}
+
+// In-place Cholesky of the packed s x s matrix A; sets *flag on a
+// non-positive pivot.
+__device__ void cholesky_packed(double *A, int s, int *flag, double *inv_piv) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < s; ++k) {
+        if (tid == 0) {
+            double d = A[tri(k, k)];
+            if (!(d > 0.0)) { *flag = 1; d = 1.0; }
+            double l = sqrt(d);
+            A[tri(k, k)] = l;
+            *inv_piv = 1.0 / l;
+        }
+        __syncthreads();
+        double iv = *inv_piv;
+        for (int i = k + 1 + tid; i < s; i += blockDim.x) A[tri(i, k)] *= iv;
+        __syncthreads();
+        for (int i = k + 1 + warp; i < s; i += nw) {
+            double lik = A[tri(i, k)];
+            double *row = A + tri(i, 0);
+            for (int j = k + 1 + lane; j <= i; j += 32) row[j] -= lik * A[tri(j, k)];
+        }
+        __syncthreads();
+    }
+}
+
+// Solves L L^T z = r in place (packed L), by warp 0.
+__device__ void cholesky_solve_packed(const double *A, int s, double *r) {
+    if (threadIdx.x < 32) {
+        int lane = threadIdx.x;
+        for (int q = 0; q < s; ++q) {
+            double v = r[q] / A[tri(q, q)];
+            __syncwarp();
+            if (lane == 0) r[q] = v;
+            for (int p = q + 1 + lane; p < s; p += 32) r[p] -= A[tri(p, q)] * v;
+            __syncwarp();
+        }
+        for (int q = s - 1; q >= 0; --q) {
+            double v = r[q] / A[tri(q, q)];
+            __syncwarp();
+            if (lane == 0) r[q] = v;
+            const double *row = A + tri(q, 0);
+            for (int p = lane; p < q; p += 32) r[p] -= row[p] * v;
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kSolveThreads) k_solve_f64(Geo g, Par p, double *beta,
+                                                             int32_t *info, Ws w) {
+    const int s = blockIdx.x;
+    int32_t *inf = info + s * kInfoN;
+    if (inf[PAM_INFO_STOPPED]) return;
+    const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS], mc = g.m_cap;
+    const double lam1 = (double)N * p.lam1_hat, lam2 = (double)N * p.lam2_hat;
+    const double viol_tol = lam1 * (1.0 + 1e-9);
+    extern __shared__ double sm[];
+    double *x = sm;          // [mc] full coefficient vector of the current iterate
+    double *gr = x + mc;     // [mc] b - G x
+    double *bv = gr + mc;    // [mc]
+    double *rhs = bv + mc;   // [mc] system on the active list
+    int *sg = (int *)(rhs + mc);  // [mc] sign of active coefficients, 0 off the support
+    int *idx = sg + mc;           // [mc] active list (ascending)
+    double *Asm = (double *)(idx + mc);
+    __shared__ SolveShared sh;
+    __shared__ double inv_piv;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const double *G = w.G + (size_t)s * mc * mc;
+    const size_t smem_factor_elems = kFactorSmemBytes / sizeof(double);
+
+    for (int j = tid; j < mc; j += blockDim.x) {
+        double b0 = j < M ? beta[(size_t)s * mc + j] : 0.0;
+        x[j] = b0;
+        bv[j] = j < M ? w.b[(size_t)s * mc + j] : 0.0;
+        sg[j] = (j < M) ? ((b0 > 0.0) - (b0 < 0.0)) : 0;
+    }
+    if (tid == 0) { sh.flag = 0; }
+    __syncthreads();
+
+    int it = 0, certified = 0, scnt = 0;
+    for (; it < p.max_iters; ++it) {
+        compact_active(sg, M, idx, &sh.cnt);
+        scnt = sh.cnt;
+        double *A = (tri(scnt, 0) <= smem_factor_elems) ? Asm
+                                                      : w.L + (size_t)s * ((size_t)mc * (mc + 1) / 2);
+        // A = G_SS + lambda2 I (packed lower), rhs = b_S - lambda1 s_S
+        for (int pp = warp; pp < scnt; pp += nw) {
+            const double *Gr = G + (size_t)idx[pp] * mc;
+            for (int q = lane; q <= pp; q += 32)
+                A[tri(pp, q)] = Gr[idx[q]] + (q == pp ? lam2 : 0.0);
+            if (lane == 0) rhs[pp] = bv[idx[pp]] - lam1 * (double)sg[idx[pp]];
+        }
+        __syncthreads();
+        cholesky_packed(A, scnt, &sh.flag, &inv_piv);
+        if (sh.flag) break;
+        cholesky_solve_packed(A, scnt, rhs);
+        for (int j = tid; j < M; j += blockDim.x) x[j] = 0.0;
+        __syncthreads();
+        for (int pp = tid; pp < scnt; pp += blockDim.x) x[idx[pp]] = rhs[pp];
+        __syncthreads();
+        // gradient b - G_{:,S} x_S over every centre
+        for (int j = warp; j < M; j += nw) {
+            const double *Gr = G + (size_t)j * mc;
+            double acc = 0.0;
+            for (int pp = lane; pp < scnt; pp += 32) acc += Gr[idx[pp]] * rhs[pp];
+            acc = warp_sum(acc);
+            if (lane == 0) gr[j] = bv[j] - acc;
+        }
+        if (tid == 0) { sh.bad = 0; sh.viol = 0; sh.worst = -1; sh.worst_v = 0.0; }
+        __syncthreads();
+        int my_bad = 0, my_viol = 0;
+        for (int j = tid; j < M; j += blockDim.x) {
+            if (sg[j] != 0) my_bad += !(x[j] * (double)sg[j] > 0.0);
+            else my_viol += fabs(gr[j]) > viol_tol;
+        }
+        if (my_bad) atomicAdd(&sh.bad, my_bad);
+        if (my_viol) atomicAdd(&sh.viol, my_viol);
+        __syncthreads();
+        if (sh.bad == 0 && sh.viol == 0) { certified = 1; break; }
+        const bool one_at_a_time = it >= 16;
+        if (one_at_a_time && sh.bad == 0) {
+            // add only the largest violation (ties to the lower index)
+            if (tid == 0) {
+                double best = -1.0;
+                int bj = -1;
+                for (int j = 0; j < M; ++j)
+                    if (sg[j] == 0 && fabs(gr[j]) > viol_tol && fabs(gr[j]) > best) {
+                        best = fabs(gr[j]);
+                        bj = j;
+                    }
+                sh.worst = bj;
+            }
+            __syncthreads();
+            if (tid == 0 && sh.worst >= 0) sg[sh.worst] = gr[sh.worst] > 0.0 ? 1 : -1;
+        } else {
+            for (int j = tid; j < M; j += blockDim.x) {
+                if (sg[j] != 0) {
+                    if (!(x[j] * (double)sg[j] > 0.0)) sg[j] = 0;
+                } else if (!one_at_a_time && fabs(gr[j]) > viol_tol) {
+                    sg[j] = gr[j] > 0.0 ? 1 : -1;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    for (int j = tid; j < M; j += blockDim.x) beta[(size_t)s * mc + j] = x[j];
+    if (tid == 0) {
+        int flags = inf[PAM_INFO_FLAGS] & ~(PAM_FLAG_NOT_CERTIFIED | PAM_FLAG_CHOLESKY);
+        if (!certified) {
+            flags |= PAM_FLAG_NOT_CERTIFIED;
+            atomicAdd(&w.status[kStUncertified], 1);
+        }
+        if (sh.flag) flags |= PAM_FLAG_CHOLESKY;
+        inf[PAM_INFO_FLAGS] = flags;
+        inf[PAM_INFO_SUPPORT] = scnt;
+        inf[PAM_INFO_ITERS] = it + (certified ? 1 : 0);
+    }
+}
+
+static size_t solve_smem_bytes(int mc) {
+    return (size_t)mc * (4 * sizeof(double) + 2 * sizeof(int)) + kFactorSmemBytes;
+}
+
+void launch_solve_level_f64(const Geo &g, const Par &p, const int32_t *boxes,
+                            const double *centres, double *beta, int32_t *info, const Ws &w,
+                            cudaStream_t st) {
+    size_t asm_smem = (size_t)g.m_cap * sizeof(dvec4);
+    cudaFuncSetAttribute(k_assemble_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_smem);
+    dim3 ga((g.n_max + 127) / 128, g.S);
+    k_assemble_f64<<<ga, 128, asm_smem, st>>>(g, boxes, centres, info, w);
+    dim3 gb((g.m_cap + 7) / 8, g.S);
+    k_bvec_f64<<<gb, 256, 0, st>>>(g, info, w);
+    int T = g.m_cap / kGT;
+    dim3 gg(T * (T + 1) / 2, g.S);
+    k_gram_f64<<<gg, 256, 0, st>>>(g, info, w);
+    size_t ss = solve_smem_bytes(g.m_cap);
+    cudaFuncSetAttribute(k_solve_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    k_solve_f64<<<g.S, kSolveThreads, ss, st>>>(g, p, beta, info, w);
+}
+
+// --------------------------------------------------------------------------
+// Step 3: residual indicators (Eq. (4), midpoint rule, K space),
+// R_T = |T| (exp(sum_m W_Tm beta_m) - K_T)^2.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_residual_f64(Geo g, const double *beta,
+                                                      const int32_t *info, Ws w) {
+    int s = blockIdx.y;
+    const int32_t *inf = info + s * kInfoN;
+    if (inf[PAM_INFO_STOPPED]) return;
+    int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
+    extern __shared__ double sb[];
+    for (int m = threadIdx.x; m < M; m += blockDim.x) sb[m] = beta[(size_t)s * g.m_cap + m];
+    __syncthreads();
+    int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    const double *E = w.E + (size_t)s * g.m_cap * g.n_max + t;
+    double acc = 0.0;
+    for (int m = 0; m < M; ++m) acc += E[(size_t)m * g.n_max] * sb[m];
+    size_t o = (size_t)s * g.n_max + t;
+    double e = exp(acc * w.inv_s[o]) - w.kv[o];
+    w.R[o] = g.vol * (e * e);
+}
+
+// --------------------------------------------------------------------------
+// Algorithm 1 (3)-(5): mark the k_top cells with the largest R_T >= eps_tol
+// (ranked by R_T rounded to binary32, ties to the lower cell index), then
+// add d+1 centres per marked cell: at x_T + eta sigma_p u_q on the vertices
+// u_q of a regular simplex, p the current centre nearest to x_T (ties to the
+// lower index), clipped to the patch, width eta sigma_p; beta is extended by
+// zeros. The geometric decisions use unfused binary64 operations.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ void simplex_dir(int dim, int q, double u[3]) {
+    u[0] = u[1] = u[2] = 0.0;
+    if (dim == 1) {
+        u[0] = q == 0 ? 1.0 : -1.0;
+    } else if (dim == 2) {
+        const double c30 = 0.86602540378443864676;  // sqrt(3)/2
+        if (q == 0) { u[0] = -c30; u[1] = -0.5; }
+        else if (q == 1) { u[0] = c30; u[1] = -0.5; }
+        else { u[1] = 1.0; }
+    } else {
+        const double r3 = 0.57735026918962576451;  // 1/sqrt(3)
+        const int sgn[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
+        for (int a = 0; a < 3; ++a) u[a] = (double)sgn[q][a] * r3;
+    }
+}
+
+constexpr int kMarkThreads = 256;
+constexpr int kMaxKTop = 1024;
+
+__global__ void __launch_bounds__(kMarkThreads) k_mark_enrich(Geo g, Par p, const int32_t *boxes,
+                                                              double *centres, double *beta,
+                                                              int32_t *info, Ws w) {
+    const int s = blockIdx.x;
+    int32_t *inf = info + s * kInfoN;
+    if (inf[PAM_INFO_STOPPED]) return;
+    const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS], L = inf[PAM_INFO_LEVELS];
+    int64_t lim = (int64_t)g.m0 + p.m_max;
+    const int m_limit = (int)(lim < g.m_cap ? lim : g.m_cap);
+    const int tid = threadIdx.x;
+    __shared__ int marked[kMaxKTop];
+    __shared__ unsigned long long wbest[kMarkThreads / 32];
+    __shared__ int n_marked;
+    extern __shared__ unsigned long long keys[];  // [n_max]
+    if (L >= p.levels || M >= m_limit) {
+        if (tid == 0) inf[PAM_INFO_STOPPED] = 1;
+        return;
+    }
+    double kmax = __longlong_as_double((long long)w.kmax_bits[s]);
+    double eps;
+    if (p.eps_tol_rel < 0.0) {
+        eps = -INFINITY;
+    } else {
+        double a = p.eps_tol_rel * kmax;
+        eps = g.vol * (a * a);
+    }
+    const float ek = (float)eps;
+    const double *R = w.R + (size_t)s * g.n_max;
+    for (int t = tid; t < N; t += blockDim.x) {
+        float key = (float)R[t];
+        keys[t] = (key >= ek) ? (((unsigned long long)(__float_as_uint(key) + 1u) << 32) |
+                                 (unsigned long long)(0xffffffffu - (unsigned)t))
+                              : 0ull;
+    }
+    if (tid == 0) n_marked = 0;
+    __syncthreads();
+    const int k_top = p.k_top < kMaxKTop ? p.k_top : kMaxKTop;
+    for (int r = 0; r < k_top; ++r) {
+        unsigned long long best = 0;
+        for (int t = tid; t < N; t += blockDim.x) best = keys[t] > best ? keys[t] : best;
+        for (int o = 16; o > 0; o >>= 1) {
+            unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
+            best = v > best ? v : best;
+        }
+        if ((tid & 31) == 0) wbest[tid >> 5] = best;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long b = 0;
+            for (int q = 0; q < kMarkThreads / 32; ++q) b = wbest[q] > b ? wbest[q] : b;
+            if (b != 0) {
+                int t = (int)(0xffffffffu - (unsigned)(b & 0xffffffffull));
+                marked[n_marked++] = t;
+                keys[t] = 0ull;
+            }
+        }
+        __syncthreads();
+        if (n_marked <= r) break;
+    }
+    const int nm = n_marked;
+    if (nm == 0) {
+        if (tid == 0) { inf[PAM_INFO_STOPPED] = 1; inf[PAM_INFO_MARKED] = 0; }
+        return;
+    }
+    const int per = g.dim + 1;
+    int add = nm * per;
+    if (add > m_limit - M) add = m_limit - M;
+    double *cs = centres + (size_t)s * g.m_cap * 4;
+    const int32_t *box = boxes + s * 12;
+    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
+    for (int a = 0; a < g.dim; ++a) {
+        lo[a] = __dmul_rn((double)box[6 + a], g.h);
+        hi[a] = __dmul_rn((double)box[9 + a], g.h);
+    }
+    for (int r = tid; r < nm; r += blockDim.x) {
+        if (r * per >= add) continue;
+        double xt[3];
+        int64_t gi;
+        patch_cell(g, box, marked[r], xt, &gi);
+        int bestm = 0;
+        double bd = INFINITY;
+        for (int m = 0; m < M; ++m) {
+            double d2 = 0.0;
+            for (int a = 0; a < g.dim; ++a) {
+                double d = __dsub_rn(xt[a], cs[(size_t)m * 4 + a]);
+                d2 = __dadd_rn(d2, __dmul_rn(d, d));
+            }
+            if (d2 < bd) { bd = d2; bestm = m; }
+        }
+        double sn = __dmul_rn(p.eta, cs[(size_t)bestm * 4 + 3]);
+        for (int q = 0; q < per; ++q) {
+            int slot = r * per + q;
+            if (slot >= add) break;
+            double u[3];
+            simplex_dir(g.dim, q, u);
+            double *c = cs + (size_t)(M + slot) * 4;
+            for (int a = 0; a < 3; ++a) {
+                double v = 0.0;
+                if (a < g.dim) {
+                    v = __dadd_rn(xt[a], __dmul_rn(sn, u[a]));
+                    if (v < lo[a]) v = lo[a];
+                    if (v > hi[a]) v = hi[a];
+                }
+                c[a] = v;
+            }
+            c[3] = sn;
+            beta[(size_t)s * g.m_cap + M + slot] = 0.0;
+        }
+    }
+    if (tid == 0) {
+        inf[PAM_INFO_M] = M + add;
+        inf[PAM_INFO_LEVELS] = L + 1;
+        inf[PAM_INFO_MARKED] = nm;
+        if (add == 0) inf[PAM_INFO_STOPPED] = 1;
+    }
+}
+
+void launch_mark_enrich(const Geo &g, const Par &p, const int32_t *boxes, double *centres,
+                        double *beta, int32_t *info, const Ws &w, cudaStream_t st) {
+    size_t sm = (size_t)g.n_max * sizeof(unsigned long long);
+    cudaFuncSetAttribute(k_mark_enrich, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_mark_enrich<<<g.S, kMarkThreads, sm, st>>>(g, p, boxes, centres, beta, info, w);
+}
+
+void launch_residual_f64(const Geo &g, const double *beta, const int32_t *info, const Ws &w,
+                         cudaStream_t st) {
+    size_t sm = (size_t)g.m_cap * sizeof(double);
+    dim3 grid((g.n_max + 127) / 128, g.S);
+    k_residual_f64<<<grid, 128, sm, st>>>(g, beta, info, w);
+}
+
+// --------------------------------------------------------------------------
+// Step 4: evaluation of the piecewise surrogate, and the error measures.
+// --------------------------------------------------------------------------
+// Shepard value sum_m beta_m w_m(x) of subdomain s at x (two passes: the
+// maximum logit, then the normalised sum), binary64.
+__device__ double shepard_value_f64(const Geo &g, const double *centres, const double *beta,
+                                    int s, int M, const double x[3]) {
+    const dvec4 *cs = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
+    const double *bs = beta + (size_t)s * g.m_cap;
+    double lmax = -INFINITY;
+    for (int m = 0; m < M; ++m) {
+        dvec4 c = cs[m];
+        double d0 = x[0] - c.x, d1 = x[1] - c.y, d2 = x[2] - c.z;
+        double l = -(d0 * d0 + d1 * d1 + d2 * d2) / (2.0 * c.w * c.w);
+        lmax = fmax(lmax, l);
+    }
+    double num = 0.0, den = 0.0;
+    for (int m = 0; m < M; ++m) {
+        dvec4 c = cs[m];
+        double d0 = x[0] - c.x, d1 = x[1] - c.y, d2 = x[2] - c.z;
+        double e = exp(-(d0 * d0 + d1 * d1 + d2 * d2) / (2.0 * c.w * c.w) - lmax);
+        num += bs[m] * e;
+        den += e;
+    }
+    return num / den;
+}
+
+__global__ void k_eval_f64(Geo g, const double *centres, const double *beta, const int32_t *info,
+                           const double *pts, int64_t n_pts, double *out, int log_space) {
+    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (q >= n_pts) return;
+    double x[3] = {0, 0, 0};
+    for (int a = 0; a < g.dim; ++a) x[a] = pts[q * g.dim + a];
+    int s = owner_of_point(g, x);
+    if (s < 0) { out[q] = nan(""); return; }
+    int M = info[s * kInfoN + PAM_INFO_M];
+    double v = shepard_value_f64(g, centres, beta, s, M, x);
+    out[q] = log_space ? v : exp(v);
+}
+
+void launch_eval_mixed(const Geo &g, const int32_t *boxes, const double *centres,
+                       const double *beta, const int32_t *info, const double *pts, int64_t n_pts,
+                       double *out, int log_space, cudaStream_t st);
+
+void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
+                 const int32_t *info, const double *pts, int64_t n_pts, double *out, int log_space,
+                 int precision, cudaStream_t st) {
+    if (precision == PAM_PREC_MIXED) {
+        launch_eval_mixed(g, boxes, centres, beta, info, pts, n_pts, out, log_space, st);
+        return;
+    }
+    int64_t blocks = (n_pts + 127) / 128;
+    k_eval_f64<<<(unsigned)blocks, 128, 0, st>>>(g, centres, beta, info, pts, n_pts, out, log_space);
+}
+
+// Per-block partial sums over the grid cells, in a fixed order:
+// [0] sum |K - K*|, [1] sum |K|, [2] sum (K - K*)^2, [3] sum K^2 -> err_part
+// [4] sum |ln K - ln K*|, [5] sum |ln K|, [6] max |ln K - ln K*|
+constexpr int kErrThreads = 256;
+__global__ void __launch_bounds__(kErrThreads) k_errors_partial(Geo g, const double *centres,
+                                                                const double *beta,
+                                                                const int32_t *info,
+                                                                const double *K, double *part) {
+    const int64_t total = (int64_t)g.n[0] * g.n[1] * g.n[2];
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
+         c += (int64_t)gridDim.x * blockDim.x) {
+        int64_t i = c % g.n[0], j = (c / g.n[0]) % g.n[1], k = c / ((int64_t)g.n[0] * g.n[1]);
+        int idx[3] = {(int)i, (int)j, (int)k};
+        double x[3] = {0, 0, 0};
+        int js[3] = {0, 0, 0};
+        for (int a = 0; a < g.dim; ++a) {
+            x[a] = __dmul_rn((double)idx[a] + 0.5, g.h);
+            js[a] = core_of(idx[a], g.n[a], g.p[a]);
+        }
+        int s = js[0] + g.p[0] * (js[1] + g.p[1] * js[2]);
+        int M = info[s * kInfoN + PAM_INFO_M];
+        double v = shepard_value_f64(g, centres, beta, s, M, x);
+        double kk = K[c], ks = exp(v), lk = log(kk);
+        acc[0] += fabs(kk - ks);
+        acc[1] += fabs(kk);
+        acc[2] += (kk - ks) * (kk - ks);
+        acc[3] += kk * kk;
+        acc[4] += fabs(lk - v);
+        acc[5] += fabs(lk);
+        acc[6] = fmax(acc[6], fabs(lk - v));
+    }
+    __shared__ double red[kErrThreads / 32][7];
+    for (int q = 0; q < 7; ++q) {
+        double v = acc[q];
+        if (q == 6) v = warp_max(v);
+        else v = warp_sum(v);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 7) {
+        int q = threadIdx.x;
+        double v = 0.0;
+        for (int wdx = 0; wdx < kErrThreads / 32; ++wdx)
+            v = (q == 6) ? fmax(v, red[wdx][q]) : v + red[wdx][q];
+        part[(size_t)blockIdx.x * 8 + q] = v;
+    }
+}
+
+__global__ void k_errors_final(const double *part, int nblocks, double *err) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int b = 0; b < nblocks; ++b)
+        for (int q = 0; q < 7; ++q)
+            a[q] = (q == 6) ? fmax(a[q], part[(size_t)b * 8 + q]) : a[q] + part[(size_t)b * 8 + q];
+    err[0] = a[0] / a[1];
+    err[1] = sqrt(a[2] / a[3]);
+    err[2] = a[5] > 0.0 ? a[4] / a[5] : a[4];
+    err[3] = a[6] / log(10.0);
+}
+
+void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
+                   const int32_t *info, const double *K, double *err, const Ws &w,
+                   cudaStream_t st) {
+    (void)boxes;
+    int nb = kErrBlocks / 2;  // err_part holds kErrBlocks*4 doubles = nb rows of 8
+    k_errors_partial<<<nb, kErrThreads, 0, st>>>(g, centres, beta, info, K, w.err_part);
+    k_errors_final<<<1, 32, 0, st>>>(w.err_part, nb, err);
+}
+
+// --------------------------------------------------------------------------
+// One refinement round: residuals of the current fit, then mark + enrich.
+// --------------------------------------------------------------------------
+void launch_residual_mixed(const Geo &g, const int32_t *boxes, const double *centres,
+                           const double *beta, const int32_t *info, const Ws &w, cudaStream_t st);
+
+void launch_refine_round(const Geo &g, const Par &p, int precision, const int32_t *boxes,
+                         double *centres, double *beta, int32_t *info, const Ws &w,
+                         cudaStream_t st) {
+    if (precision == PAM_PREC_MIXED)
+        launch_residual_mixed(g, boxes, centres, beta, info, w, st);
+    else
+        launch_residual_f64(g, beta, info, w, st);
+    launch_mark_enrich(g, p, boxes, centres, beta, info, w, st);
+}
+
+}  // namespace pam

@@ -1,0 +1,145 @@
+// pam_internal.cuh -- declarations shared by libpam's translation units:
+// workspace layout, the kernel-side view of a problem, and small device
+// helpers. Internal to the library (the public ABI is include/pam.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "pam.h"
+
+namespace pam {
+
+constexpr int kInfoN = PAM_INFO_N;
+
+// 32-byte aligned four-double vector (a centre: c_x, c_y, c_z, sigma).
+using dvec4 = double4_32a;
+
+// Kernel-side copy of the problem and parameters (passed by value).
+struct Geo {
+    int dim;
+    int n[3];       // cells per axis (unused axes 1)
+    int p[3];       // subdomains per axis (unused axes 1)
+    int overlap;
+    int g[3];       // initial lattice (unused axes 1)
+    int nmax;       // max_a n[a]
+    double h;       // 1 / nmax
+    double vol;     // h^dim
+    int S;          // subdomains
+    int n_max;      // max patch cells (padded stride of per-cell arrays)
+    int m0, m_cap;
+};
+
+struct Par {
+    double lam1_hat, lam2_hat, eps_tol_rel, eta;
+    int k_top, m_max, levels, max_iters;
+};
+
+// Workspace carve-up. Every region is 256-byte aligned.
+struct Ws {
+    double *y;        // [S][n_max]   ln K of patch cells (row-major over the patch)
+    double *kv;       // [S][n_max]   K of patch cells
+    double *inv_s;    // [S][n_max]   1 / Shepard sum of the max-shifted exps of each row
+    double *E;        // [S][m_cap][n_max] exp(l - l*) (fp64 form; W = E * inv_s)
+    double *G;        // [S][m_cap][m_cap] Gram W^T W (fp64 form)
+    double *b;        // [S][m_cap]   W^T y
+    double *R;        // [S][n_max]   residual indicators
+    double *L;        // [S][m_cap (m_cap+1)/2] packed Cholesky factor when it exceeds shared memory
+    float *Gf;        // [S][m_cap][m_cap] Gram in fp32 (mixed form)
+    float *rowmax;    // [S][n_max]   row maximum of the logits (mixed form)
+    float *rowinv;    // [S][n_max]   1 / Shepard sum (mixed form)
+    double *err_part; // [err_blocks][4] per-block partial sums of the error measures
+    unsigned long long *kmax_bits; // [S] max K of each patch as ordered bits
+    int32_t *status;  // [8] device status words
+    size_t bytes;
+};
+
+enum StatusWord { kStBadK = 0, kStUncertified = 1, kStCholesky = 2 };
+
+constexpr int kErrBlocks = 1024;
+
+Ws carve_workspace(const Geo &g, void *base);
+bool make_geo(const pam_problem *prob, const pam_params *par, Geo *g, Par *p, pam_status *st);
+
+// Launchers implemented in the kernel translation units.
+void launch_partition(const Geo &g, int32_t *boxes, cudaStream_t st);
+void launch_prepare(const Geo &g, const int32_t *boxes, const double *K, const Ws &w, cudaStream_t st);
+void launch_init_dictionary(const Geo &g, const int32_t *boxes, double *centres, double *beta,
+                            int32_t *info, cudaStream_t st);
+void launch_solve_level_f64(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
+                            double *beta, int32_t *info, const Ws &w, cudaStream_t st);
+void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
+                              double *beta, int32_t *info, const Ws &w, cudaStream_t st);
+void launch_refine_round(const Geo &g, const Par &p, int precision, const int32_t *boxes,
+                         double *centres, double *beta, int32_t *info, const Ws &w, cudaStream_t st);
+void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
+                 const int32_t *info, const double *pts, int64_t n_pts, double *out, int log_space,
+                 int precision, cudaStream_t st);
+void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
+                   const int32_t *info, const double *K, double *err, const Ws &w, cudaStream_t st);
+
+// ---------------------------------------------------------------- device ---
+
+// Patch extent w[a] = patch_hi - patch_lo of subdomain s.
+__device__ __forceinline__ void patch_extent(const int32_t *box, int w[3]) {
+    w[0] = box[9] - box[6];
+    w[1] = box[10] - box[7];
+    w[2] = box[11] - box[8];
+}
+
+// Centroid of local patch cell t (row-major over the patch, x fastest).
+// (i + 1/2) h is one exact add and one rounded multiply, no contraction.
+__device__ __forceinline__ void patch_cell(const Geo &g, const int32_t *box, int t, double x[3],
+                                          int64_t *gidx) {
+    int w[3];
+    patch_extent(box, w);
+    int i = box[6] + t % w[0];
+    int j = box[7] + (t / w[0]) % w[1];
+    int k = box[8] + t / (w[0] * w[1]);
+    x[0] = __dmul_rn((double)i + 0.5, g.h);
+    x[1] = g.dim > 1 ? __dmul_rn((double)j + 0.5, g.h) : 0.0;
+    x[2] = g.dim > 2 ? __dmul_rn((double)k + 0.5, g.h) : 0.0;
+    *gidx = (int64_t)i + (int64_t)g.n[0] * ((int64_t)j + (int64_t)g.n[1] * (int64_t)k);
+}
+
+// Index of the core interval [floor(j n / p), floor((j+1) n / p)) holding
+// cell index i along an axis.
+__device__ __forceinline__ int core_of(int i, int n, int p) {
+    int j = (int)(((int64_t)i * p) / n);
+    if (j + 1 < p && (((int64_t)(j + 1) * n) / p) <= i) ++j;
+    return j;
+}
+
+// Owner subdomain of a point (half-open cores, outer face closed), -1 outside.
+__device__ __forceinline__ int owner_of_point(const Geo &g, const double x[3]) {
+    int j[3] = {0, 0, 0};
+    for (int a = 0; a < g.dim; ++a) {
+        double u = x[a] * (double)g.nmax;
+        if (!(u >= 0.0) || u > (double)g.n[a]) return -1;
+        int i = (int)floor(u);
+        if (i >= g.n[a]) i = g.n[a] - 1;
+        j[a] = core_of(i, g.n[a], g.p[a]);
+    }
+    return j[0] + g.p[0] * (j[1] + g.p[1] * j[2]);
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ float warp_sumf(float v) {
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+    for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+}  // namespace pam
+
+#define PAM_CUDA_TRY(expr)                                      \
+    do {                                                        \
+        cudaError_t e_ = (expr);                                \
+        if (e_ != cudaSuccess) return PAM_ERR_CUDA;             \
+    } while (0)

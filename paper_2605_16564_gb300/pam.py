@@ -1,0 +1,256 @@
+"""Thin Python binding of libpam (include/pam.h), argument marshalling only.
+
+Every step of the fitting path runs in the CUDA library; this module turns
+torch tensors into device pointers, fills the C structs and checks status
+codes. PyTorch supplies the device memory (model arrays, workspace) and the
+stream. If the library was not built, importing works but every call raises
+``RuntimeError`` -- there is no other implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+from dataclasses import dataclass, field
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "_build", "libpam.so")
+
+PAM_MAX_DIM = 3
+PAM_INFO_N = 8
+PAM_PREC_FP64 = 0
+PAM_PREC_MIXED = 1
+
+INFO_M, INFO_SUPPORT, INFO_LEVELS, INFO_ITERS, INFO_FLAGS, INFO_STOPPED, INFO_N_CELLS, INFO_MARKED = range(8)
+FLAG_NOT_CERTIFIED, FLAG_CHOLESKY, FLAG_REFINE_DIVERGED = 1, 2, 4
+
+STATUS = {0: "PAM_OK", 1: "PAM_ERR_INVALID_ARG", 2: "PAM_ERR_NONPOSITIVE_K", 3: "PAM_ERR_CUDA",
+          4: "PAM_ERR_WORKSPACE", 5: "PAM_ERR_NOT_CONVERGED", 6: "PAM_ERR_UNSUPPORTED"}
+
+EXPORTED = ["pam_version", "pam_status_string", "pam_plan_create", "pam_partition",
+            "pam_fit_subdomains", "pam_refine", "pam_eval", "pam_errors"]
+
+
+class PamError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {STATUS.get(code, code)}")
+
+
+class pam_problem(C.Structure):
+    _fields_ = [("dim", C.c_int), ("n_cells", C.c_int * 3), ("n_sub", C.c_int * 3),
+                ("overlap", C.c_int), ("g_init", C.c_int * 3)]
+
+
+class pam_params(C.Structure):
+    _fields_ = [("lambda1_hat", C.c_double), ("lambda2_hat", C.c_double),
+                ("eps_tol_rel", C.c_double), ("eta", C.c_double), ("k_top", C.c_int),
+                ("m_max", C.c_int), ("levels", C.c_int), ("max_iters", C.c_int),
+                ("precision", C.c_int)]
+
+
+class pam_plan(C.Structure):
+    _fields_ = [("n_subdomains", C.c_int), ("max_patch_cells", C.c_int), ("m0", C.c_int),
+                ("m_cap", C.c_int), ("n_grid_cells", C.c_int64), ("workspace_bytes", C.c_size_t)]
+
+
+class pam_model(C.Structure):
+    _fields_ = [("boxes", C.c_void_p), ("centres", C.c_void_p), ("beta", C.c_void_p),
+                ("info", C.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """The loaded libpam (raises if it was not built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"libpam is not built ({LIB_PATH} missing): run "
+                               "__graft_entry__.build() or python paper_2605_16564_gb300/build.py")
+        L = C.CDLL(LIB_PATH)
+        P = C.POINTER
+        L.pam_version.restype = C.c_char_p
+        L.pam_status_string.restype = C.c_char_p
+        L.pam_status_string.argtypes = [C.c_int]
+        L.pam_plan_create.argtypes = [P(pam_problem), P(pam_params), P(pam_plan)]
+        L.pam_partition.argtypes = [P(pam_problem), C.c_void_p]
+        L.pam_fit_subdomains.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), C.c_void_p,
+                                         P(pam_model), C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_refine.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), C.c_void_p,
+                                 P(pam_model), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_eval.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_int64,
+                               C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+        L.pam_errors.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_void_p,
+                                 C.c_void_p, C.c_size_t, C.c_void_p]
+        for name in ("pam_plan_create", "pam_partition", "pam_fit_subdomains", "pam_refine",
+                     "pam_eval", "pam_errors"):
+            getattr(L, name).restype = C.c_int
+        _lib = L
+    return _lib
+
+
+def _check(code, where):
+    if code != 0:
+        raise PamError(code, where)
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _stream(stream):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+def make_problem(n_cells, n_sub, overlap, g_init):
+    dim = len(n_cells)
+    pad = lambda v, f: list(v) + [f] * (3 - len(v))
+    pr = pam_problem()
+    pr.dim = dim
+    pr.n_cells[:] = pad(n_cells, 1)
+    pr.n_sub[:] = pad(n_sub, 1)
+    pr.overlap = overlap
+    pr.g_init[:] = pad(g_init, 1)
+    return pr
+
+
+def make_params(lambda1_hat=4.59e-4, lambda2_hat=4.64e-6, eps_tol_rel=1e-3, eta=0.5, k_top=37,
+                m_max=1 << 30, levels=3, max_iters=0, precision=PAM_PREC_FP64):
+    p = pam_params()
+    p.lambda1_hat, p.lambda2_hat, p.eps_tol_rel, p.eta = lambda1_hat, lambda2_hat, eps_tol_rel, eta
+    p.k_top, p.m_max, p.levels, p.max_iters, p.precision = k_top, min(m_max, (1 << 31) - 1), levels, \
+        max_iters, precision
+    return p
+
+
+# ------------------------------------------------------------ entry points --
+
+def pam_version():
+    return lib().pam_version().decode()
+
+
+def pam_plan_create(problem, params):
+    plan = pam_plan()
+    _check(lib().pam_plan_create(C.byref(problem), C.byref(params), C.byref(plan)), "pam_plan_create")
+    return plan
+
+
+def pam_partition(problem):
+    S = int(np.prod(list(problem.n_sub)[:problem.dim]))
+    boxes = np.zeros((S, 12), dtype=np.int32)
+    _check(lib().pam_partition(C.byref(problem), boxes.ctypes.data), "pam_partition")
+    return boxes
+
+
+def pam_fit_subdomains(problem, params, plan, K, model, workspace, stream=None, check=True):
+    code = lib().pam_fit_subdomains(C.byref(problem), C.byref(params), C.byref(plan), _ptr(K),
+                                    C.byref(model.c_struct()), _ptr(workspace),
+                                    workspace.numel() * workspace.element_size(), _stream(stream))
+    if check:
+        _check(code, "pam_fit_subdomains")
+    return code
+
+
+def pam_refine(problem, params, plan, K, model, n_levels, workspace, stream=None, check=True):
+    code = lib().pam_refine(C.byref(problem), C.byref(params), C.byref(plan), _ptr(K),
+                            C.byref(model.c_struct()), int(n_levels), _ptr(workspace),
+                            workspace.numel() * workspace.element_size(), _stream(stream))
+    if check:
+        _check(code, "pam_refine")
+    return code
+
+
+def pam_eval(problem, plan, model, pts, out, log_space=False, precision=PAM_PREC_FP64, stream=None):
+    n = pts.shape[0] if pts is not None else 0
+    _check(lib().pam_eval(C.byref(problem), C.byref(plan), C.byref(model.c_struct()), _ptr(pts),
+                          int(n), _ptr(out), int(bool(log_space)), int(precision), _stream(stream)),
+           "pam_eval")
+
+
+def pam_errors(problem, plan, model, K, err, workspace, stream=None):
+    _check(lib().pam_errors(C.byref(problem), C.byref(plan), C.byref(model.c_struct()), _ptr(K),
+                            _ptr(err), _ptr(workspace), workspace.numel() * workspace.element_size(),
+                            _stream(stream)), "pam_errors")
+
+
+# ------------------------------------------------------------------ helpers --
+
+@dataclass
+class Model:
+    """Device arrays of a fitted model (torch tensors, caller-owned)."""
+    boxes: "object"
+    centres: "object"
+    beta: "object"
+    info: "object"
+    _c: pam_model = field(default=None, repr=False)
+
+    def c_struct(self):
+        self._c = pam_model(self.boxes.data_ptr(), self.centres.data_ptr(), self.beta.data_ptr(),
+                            self.info.data_ptr())
+        return self._c
+
+    def to_host(self, n_cells, n_sub, m_cap):
+        """The model as the numpy dict the oracle's evaluation takes."""
+        info = self.info.cpu().numpy()
+        return dict(boxes=self.boxes.cpu().numpy(), M=info[:, INFO_M].astype(np.int32),
+                    c=self.centres.cpu().numpy(), beta=self.beta.cpu().numpy(), info=info,
+                    m_cap=int(m_cap), n_cells=tuple(n_cells), n_sub=tuple(n_sub))
+
+
+def alloc_model(plan, device="cuda"):
+    import torch
+    S, mc = plan.n_subdomains, plan.m_cap
+    return Model(boxes=torch.zeros((S, 12), dtype=torch.int32, device=device),
+                 centres=torch.zeros((S, mc, 4), dtype=torch.float64, device=device),
+                 beta=torch.zeros((S, mc), dtype=torch.float64, device=device),
+                 info=torch.zeros((S, PAM_INFO_N), dtype=torch.int32, device=device))
+
+
+def alloc_workspace(plan, device="cuda"):
+    import torch
+    return torch.empty(int(plan.workspace_bytes), dtype=torch.uint8, device=device)
+
+
+class Fitter:
+    """A problem, its parameters and plan, with the device buffers they need."""
+
+    def __init__(self, n_cells, n_sub, overlap, g_init, device="cuda", **params):
+        self.n_cells, self.n_sub = tuple(n_cells), tuple(n_sub)
+        self.problem = make_problem(n_cells, n_sub, overlap, g_init)
+        self.params = make_params(**params)
+        self.plan = pam_plan_create(self.problem, self.params)
+        self.device = device
+        self.model = alloc_model(self.plan, device)
+        self.workspace = alloc_workspace(self.plan, device)
+
+    def fit(self, K, levels=None, stream=None, check=True):
+        """Step 2, then `levels` rounds of Step 3 (default: the planned levels)."""
+        lv = self.params.levels if levels is None else levels
+        c1 = pam_fit_subdomains(self.problem, self.params, self.plan, K, self.model, self.workspace,
+                                stream, check)
+        c2 = pam_refine(self.problem, self.params, self.plan, K, self.model, lv, self.workspace,
+                        stream, check) if lv > 0 else 0
+        return c1 or c2
+
+    def eval(self, pts, out=None, log_space=False, precision=None, stream=None):
+        import torch
+        if out is None:
+            out = torch.empty(pts.shape[0], dtype=torch.float64, device=pts.device)
+        prec = self.params.precision if precision is None else precision
+        pam_eval(self.problem, self.plan, self.model, pts, out, log_space, prec, stream)
+        return out
+
+    def errors(self, K, stream=None):
+        import torch
+        err = torch.zeros(4, dtype=torch.float64, device=K.device)
+        pam_errors(self.problem, self.plan, self.model, K, err, self.workspace, stream)
+        e = err.cpu().numpy()
+        return dict(l1=e[0], l2=e[1], l1_log=e[2], max_log10=e[3])
+
+    def host_model(self):
+        return self.model.to_host(self.n_cells, self.n_sub, self.plan.m_cap)

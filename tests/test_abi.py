@@ -1,0 +1,101 @@
+"""The C ABI without a GPU: the library builds, loads, exports every entry
+point include/pam.h declares, and its host-only calls (sizes, partition,
+argument checks) behave as documented."""
+import os
+import re
+
+import numpy as np
+import pytest
+
+import oracle
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def pam():
+    from paper_2605_16564_gb300 import build
+    build.build()
+    from paper_2605_16564_gb300 import pam as p
+    p.lib()
+    return p
+
+
+def _declared_functions():
+    names = []
+    for h in sorted(os.listdir(os.path.join(ROOT, "include"))):
+        if h.endswith(".h"):
+            src = open(os.path.join(ROOT, "include", h)).read()
+            src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+            names += re.findall(r"\b(pam_\w+)\s*\(", src)
+    return sorted(set(names))
+
+
+def test_library_exports_every_declared_entry_point(pam):
+    declared = _declared_functions()
+    assert "pam_fit_subdomains" in declared and "pam_eval" in declared
+    L = pam.lib()
+    for name in declared:
+        assert hasattr(L, name), name
+    assert set(pam.EXPORTED) <= set(declared)
+    assert "sm_103a" in pam.pam_version()
+
+
+@pytest.mark.parametrize("n_cells,n_sub,overlap", [
+    ((256, 256), (8, 8), 2), ((60, 220, 85), (6, 22, 17), 1), ((37, 23), (4, 3), 3), ((50,), (7,), 2)])
+def test_partition_matches_the_oracle(pam, n_cells, n_sub, overlap):
+    pr = pam.make_problem(n_cells, n_sub, overlap, (2,) * len(n_cells))
+    np.testing.assert_array_equal(pam.pam_partition(pr), oracle.partition(n_cells, n_sub, overlap))
+
+
+def test_plan_sizes(pam):
+    pr = pam.make_problem((60, 220, 85), (6, 22, 17), 1, (4, 4, 2))
+    plan = pam.pam_plan_create(pr, pam.make_params(k_top=30, levels=3))
+    assert plan.n_subdomains == 2244 and plan.m0 == 32
+    assert plan.m_cap == 448 and plan.m_cap >= 32 + 3 * 4 * 30
+    assert plan.max_patch_cells >= 12 * 12 * 7 and plan.max_patch_cells % 32 == 0
+    assert plan.n_grid_cells == 60 * 220 * 85
+    assert plan.workspace_bytes > 0
+    # the m_max cap bounds the capacity
+    plan2 = pam.pam_plan_create(pr, pam.make_params(k_top=30, levels=3, m_max=10))
+    assert plan2.m_cap == 64
+
+
+@pytest.mark.parametrize("bad", [
+    dict(problem=dict(n_cells=(0, 8), n_sub=(1, 1))),
+    dict(problem=dict(n_cells=(8, 8), n_sub=(9, 1))),
+    dict(problem=dict(overlap=-1)),
+    dict(problem=dict(g_init=(0, 2))),
+    dict(params=dict(lambda2_hat=0.0)),
+    dict(params=dict(lambda1_hat=-1.0)),
+    dict(params=dict(eta=1.0)),
+    dict(params=dict(k_top=-1)),
+    dict(params=dict(precision=7)),
+])
+def test_invalid_arguments_are_rejected(pam, bad):
+    base = dict(n_cells=(8, 8), n_sub=(2, 2), overlap=1, g_init=(2, 2))
+    base.update(bad.get("problem", {}))
+    pr = pam.make_problem(base["n_cells"], base["n_sub"], base["overlap"], base["g_init"])
+    par = pam.make_params(**bad.get("params", {}))
+    with pytest.raises(pam.PamError) as e:
+        pam.pam_plan_create(pr, par)
+    assert e.value.code == 1
+
+
+def test_oversized_dictionary_is_unsupported(pam):
+    pr = pam.make_problem((64, 64), (1, 1), 0, (40, 40))
+    with pytest.raises(pam.PamError) as e:
+        pam.pam_plan_create(pr, pam.make_params())
+    assert e.value.code == 6
+
+
+def test_null_arguments_are_rejected(pam):
+    import ctypes as C
+    L = pam.lib()
+    assert L.pam_plan_create(None, None, None) == 1
+    assert L.pam_partition(None, None) == 1
+    pr = pam.make_problem((8, 8), (2, 2), 1, (2, 2))
+    par = pam.make_params()
+    plan = pam.pam_plan_create(pr, par)
+    assert L.pam_fit_subdomains(C.byref(pr), C.byref(par), C.byref(plan), None, None, None, 0, None) == 1
+    assert L.pam_eval(C.byref(pr), C.byref(plan), None, None, 0, None, 0, 0, None) == 1
