@@ -1,0 +1,441 @@
+"""Benchmark of the PAM fitting path on GB300.
+
+One step = the whole path on one synthetic field: partition, Step 2 fit,
+three refinement levels (Algorithm 1), evaluation of the surrogate on the
+2x refined target mesh, and the error reduction. Workload (default): the
+60 x 220 x 85 layered field (1,122,000 cells), 6 x 22 x 17 subdomains with a
+1-cell overlap, 4 x 4 x 2 initial centres, 3 levels, evaluated on the
+120 x 440 x 170 cell-centred mesh (8,976,000 points).
+
+Prints ONE JSON line (rank 0). `value` = source cells fitted and evaluated
+per second, whole job, inputs resident in HBM; `e2e` = the same through the
+C ABI from pinned host buffers, copies included. Multi-GPU: every rank fits
+its own field (weak scaling, no collective on the data path); the step time
+is the maximum over ranks.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl pam|reference]
+                  [--precision auto|fp64|mixed] [--workload layered3d|voronoi2d|...]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2605_16564_gb300 import fields  # noqa: E402
+
+METRIC = "cells fit/s & eval pts/s, chosen vs plain GPU form at equal L1 error"
+
+WORKLOADS = {
+    # name: (shape, n_sub, overlap, g_init, params, eval mesh counts, field maker)
+    "layered3d": dict(shape=(60, 220, 85), n_sub=(6, 22, 17), overlap=1, g=(4, 4, 2),
+                      params=dict(k_top=30, levels=3), eval_counts=(120, 440, 170),
+                      field=lambda seed: fields.layered_field((60, 220, 85), seed=seed), seed=5),
+    "channel2d": dict(shape=(1024, 1024), n_sub=(32, 32), overlap=2, g=(8, 8),
+                      params=dict(k_top=37, levels=3), eval_counts=(1536, 1536),
+                      field=lambda seed: fields.channel_field(1024, seed=seed), seed=3),
+    "voronoi2d": dict(shape=(256, 256), n_sub=(8, 8), overlap=2, g=(8, 8),
+                      params=dict(k_top=37, levels=3), eval_counts=(384, 384),
+                      field=lambda seed: fields.voronoi_field(256, seed=seed), seed=2),
+    "disc2d": dict(shape=(64, 64), n_sub=(1, 1), overlap=0, g=(16, 16),
+                   params=dict(k_top=51, levels=2), eval_counts=(97, 97),
+                   field=lambda seed: fields.disc_field(64), seed=0),
+}
+
+PHASES = ["prepare", "assemble", "gram", "solve", "residual", "mark", "eval", "errors", "stats",
+          "gram_tc", "refine"]
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    return rank, ws
+
+
+def max_over_ranks(x: float, ws: int, device=None) -> float:
+    """Maximum of a scalar over ranks (timing only; no data-path exchange)."""
+    if ws == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(ws: int):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def shard_seed(base_seed: int, rank: int) -> int:
+    """Each rank fits its own field: weak scaling over independent problems."""
+    return base_seed + 1000 * rank
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.Q}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], 0.0, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx = max(mx, float(parts[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(n)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx or None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        with open(p) as f:
+            d = json.load(f)
+        return d, "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+# Nominal FP64 rate of GB300 (dense, per GPU), the peak of the binary64 path.
+FP64_NOMINAL_TFLOPS = 1.25
+
+
+def accounting(fit, Kd, levels, pam):
+    """Algorithmic work of one step, counted from the dictionary sizes each
+    solve actually had: Gram flops sum 2 N_i M_i^2 and assembly exps
+    sum N_i M_i over every (subdomain, solve). Runs the fit level by level
+    (outside the timed region) and reads the sizes after each level."""
+    gram, exps = 0.0, 0.0
+    fit_levels = [0] + [1] * levels
+    for r, lv in enumerate(fit_levels):
+        if r == 0:
+            pam.pam_fit_subdomains(fit.problem, fit.params, fit.plan, Kd, fit.model, fit.workspace)
+        else:
+            pam.pam_refine(fit.problem, fit.params, fit.plan, Kd, fit.model, 1, fit.workspace)
+        info = fit.model.info.cpu().numpy()
+        solved = info[:, pam.INFO_STOPPED] == 0 if r > 0 else np.ones(len(info), bool)
+        n = info[solved, pam.INFO_N_CELLS].astype(float)
+        m = info[solved, pam.INFO_M].astype(float)
+        gram += float(np.sum(2.0 * n * m * m))
+        exps += float(np.sum(n * m))
+    return gram, exps
+
+
+def run_pam(args, rank, ws):
+    import torch
+    from paper_2605_16564_gb300 import build, pam
+
+    build.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    W = WORKLOADS[args.workload]
+    K = W["field"](shard_seed(W["seed"], rank))
+    shape = W["shape"]
+    h = fields.cell_size(shape)
+    extent = [n * h for n in shape]
+    pts = fields.cell_centred_points(W["eval_counts"], extent)
+    n_cells = int(np.prod(shape))
+    n_pts = pts.shape[0]
+
+    prec_name = args.precision
+    if prec_name == "auto":
+        prec_name = "mixed" if _mixed_available(pam) else "fp64"
+    prec = pam.PAM_PREC_MIXED if prec_name == "mixed" else pam.PAM_PREC_FP64
+
+    fit = pam.Fitter(shape, W["n_sub"], W["overlap"], W["g"], device=dev, precision=prec, **W["params"])
+    Kd = torch.from_numpy(np.ascontiguousarray(K)).to(dev)
+    ptsd = torch.from_numpy(pts).to(dev)
+    out = torch.empty(n_pts, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        fit.fit(Kd)
+        fit.eval(ptsd, out=out)
+        return fit.errors(Kd)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+
+    L = pam.lib()
+    L.pam_timing_reset()
+    L.pam_timing_enable(1)
+    launches0 = L.pam_kernel_launches()
+    times = []
+    barrier(ws)
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)  # L2 flush between timed steps (outside the events)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            err = step()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            times.append(e0.elapsed_time(e1))
+    barrier(ws)
+    launches = L.pam_kernel_launches() - launches0
+    L.pam_timing_enable(0)
+    phase_ms = {}
+    for i, name in enumerate(PHASES):
+        import ctypes as C
+        tot, cnt = C.c_double(0), C.c_int(0)
+        L.pam_timing_read(i, C.byref(tot), C.byref(cnt))
+        if cnt.value:
+            phase_ms[name] = (tot.value / args.steps, cnt.value // args.steps)
+    L.pam_timing_reset()
+
+    step_ms = max_over_ranks(sum(times) / len(times), ws, dev)
+    value = n_cells * ws / (step_ms / 1e3)
+    info = fit.model.info.cpu().numpy()
+
+    # --- end to end through the C ABI from pinned host buffers -------------
+    Kh = torch.from_numpy(np.ascontiguousarray(K)).pin_memory()
+    ptsh = torch.from_numpy(pts).pin_memory()
+    outh = torch.empty(n_pts, dtype=torch.float64).pin_memory()
+    e2e_times = []
+    for it in range(args.warmup + args.steps):
+        torch.cuda.synchronize()
+        flush.fill_(1)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Kd.copy_(Kh, non_blocking=True)
+        ptsd.copy_(ptsh, non_blocking=True)
+        fit.fit(Kd)
+        fit.eval(ptsd, out=out)
+        errh = fit.errors(Kd)
+        outh.copy_(out, non_blocking=True)
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_times.append(time.perf_counter() - t0)
+    e2e_s = max_over_ranks(sum(e2e_times) / len(e2e_times), ws, dev)
+    h2d = Kh.numel() * 8 + ptsh.numel() * 8
+    d2h = outh.numel() * 8 + 4 * 8
+
+    # --- the plain binary64 form, for the chosen-vs-plain ratio -------------
+    plain = None
+    if prec == pam.PAM_PREC_MIXED and not args.skip_plain:
+        pf = pam.Fitter(shape, W["n_sub"], W["overlap"], W["g"], device=dev,
+                        precision=pam.PAM_PREC_FP64, **W["params"])
+        pf.fit(Kd)
+        torch.cuda.synchronize()
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        flush.fill_(1)
+        e0.record(stream)
+        pf.fit(Kd)
+        pf.eval(ptsd, out=out)
+        perr = pf.errors(Kd)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        pms = e0.elapsed_time(e1)
+        plain = {"ms_per_step": pms, "cells_per_s": n_cells / (pms / 1e3), "l1": perr["l1"],
+                 "speedup_chosen_over_plain": pms / step_ms,
+                 "l1_ratio_chosen_over_plain": err["l1"] / perr["l1"]}
+        del pf
+
+    # --- roofline of the dominant kernel family -----------------------------
+    peaks, peak_src = _peaks()
+    gram_flops, exps = accounting(fit, Kd, W["params"]["levels"], pam)
+    dom = max(phase_ms.items(), key=lambda kv: kv[1][0]) if phase_ms else ("none", (0.0, 0))
+    roof = None
+    if dom[0] in ("gram", "gram_tc"):
+        if prec == pam.PAM_PREC_MIXED:
+            peak = peaks.get("bf16_tflops", 1900.0)
+            ach = gram_flops / (dom[1][0] / 1e3) / 1e12
+            roof = {"kernel": "gram_tc", "bound": "tensor", "achieved": ach, "peak": peak,
+                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
+                    "peak_source": f"bf16_tflops of {peak_src}"}
+        else:
+            ach = gram_flops / (dom[1][0] / 1e3) / 1e12
+            roof = {"kernel": "gram_f64", "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS,
+                    "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None,
+                    "peak_source": "nominal GB300 FP64 dense rate"}
+    else:
+        roof = {"kernel": dom[0], "bound": "alu", "achieved": None, "peak": None, "unit": None,
+                "frac": None, "traffic": None}
+
+    return dict(value=value, step_ms=step_ms, times=times, err=err, phase_ms=phase_ms, launches=launches,
+                clocks=clk.summary(), e2e_s=e2e_s, h2d=h2d, d2h=d2h, plain=plain, roof=roof,
+                prec_name=prec_name, n_cells=n_cells, n_pts=n_pts, info=info, gram_flops=gram_flops,
+                exps=exps)
+
+
+def _mixed_available(pam):
+    try:
+        pr = pam.make_problem((8, 8), (1, 1), 0, (2, 2))
+        pam.pam_plan_create(pr, pam.make_params(precision=pam.PAM_PREC_MIXED))
+        return True
+    except pam.PamError:
+        return False
+
+
+def oracle_sample(workload: str, n_sub_sample: int, seed_offset=0):
+    """Time the FP64 oracle on a bounded, evenly spaced sample of subdomains of
+    the workload (fit + evaluation of the target points inside their cores)."""
+    import oracle
+    W = WORKLOADS[workload]
+    K = W["field"](W["seed"] + seed_offset)
+    shape = W["shape"]
+    S = int(np.prod(W["n_sub"]))
+    which = np.unique(np.linspace(0, S - 1, min(n_sub_sample, S)).astype(np.int32))
+    boxes = oracle.partition(shape, W["n_sub"], W["overlap"])
+    h = fields.cell_size(shape)
+    ratio = [c / n for c, n in zip(W["eval_counts"], shape)]
+    pts = []
+    for s in which:
+        lo, hi = boxes[s, :3], boxes[s, 3:6]
+        axes = []
+        for a in range(len(shape)):
+            ia = np.arange(int(lo[a] * ratio[a]), int(hi[a] * ratio[a]))
+            axes.append((ia + 0.5) * h / ratio[a])
+        g = np.meshgrid(*reversed(axes), indexing="ij")
+        pts.append(np.stack([x.reshape(-1) for x in reversed(g)], axis=1))
+    pts = np.concatenate(pts)
+    cells = int(np.prod(boxes[which, 3:6] - boxes[which, 0:3], axis=1).sum())
+    t0 = time.perf_counter()
+    model = oracle.fit_all(K, shape, W["n_sub"], W["overlap"], W["g"],
+                           oracle.default_params(**W["params"]), which=which)
+    oracle.evaluate(model, pts)
+    dt = time.perf_counter() - t0
+    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
+    return dict(cells=cells, seconds=dt, cores=cores, n_sub=len(which), n_pts=len(pts))
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="pam", choices=["pam", "reference"])
+    ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
+    ap.add_argument("--workload", default="layered3d", choices=sorted(WORKLOADS))
+    ap.add_argument("--cpu-sample", type=int, default=192, help="subdomains in the oracle baseline sample")
+    ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--skip-cpu", action="store_true")
+    args = ap.parse_args()
+    rank, ws = _dist()
+    W = WORKLOADS[args.workload]
+    cfg = {"workload": f"{args.workload} {'x'.join(map(str, W['shape']))} cells, "
+                       f"{'x'.join(map(str, W['n_sub']))} subdomains, overlap {W['overlap']}, "
+                       f"{'x'.join(map(str, W['g']))} initial centres, {W['params']['levels']} levels, "
+                       f"eval {'x'.join(map(str, W['eval_counts']))}",
+           "cells_per_step": int(np.prod(W["shape"])), "eval_pts_per_step": int(np.prod(W["eval_counts"])),
+           "l2_flush": "256 MB buffer written between timed steps", "parallelism": f"replicas{ws}"}
+
+    if ws > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "pam" else "gloo"
+        dist.init_process_group(backend=backend)
+
+    if args.impl == "reference":
+        if rank != 0:
+            return
+        per_step = max(8, args.cpu_sample // 8)
+        vals = []
+        for i in range(args.warmup + args.steps):
+            r = oracle_sample(args.workload, per_step)
+            if i >= args.warmup:
+                vals.append(r)
+        secs = sum(v["seconds"] for v in vals) / len(vals)
+        cells = vals[0]["cells"]
+        value = cells / secs
+        line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "cells/s", "n_gpus": args.gpus,
+                "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs * 1e3,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+                "data": "synthetic", "config": cfg,
+                "cpu_baseline": {"value": value, "unit": "cells/s", "cores": vals[0]["cores"], "kind": "oracle",
+                                 "sample": f"{vals[0]['n_sub']} evenly spaced subdomains per step "
+                                           f"({cells} core cells, {vals[0]['n_pts']} eval points)"},
+                "e2e": {"value": value, "unit": "cells/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+        print(json.dumps(line))
+        return
+
+    r = run_pam(args, rank, ws)
+    if rank != 0:
+        return
+    cpu = None
+    if not args.skip_cpu:
+        o = oracle_sample(args.workload, args.cpu_sample)
+        cpu = {"value": o["cells"] / o["seconds"], "unit": "cells/s", "cores": o["cores"], "kind": "oracle",
+               "sample": f"{o['n_sub']} evenly spaced subdomains of the workload: Algorithm 1 fit + "
+                         f"evaluation of their {o['n_pts']} target points ({o['cells']} core cells, "
+                         f"{o['seconds']:.1f} s)"}
+    step_s = r["step_ms"] / 1e3
+    eval_ms = r["phase_ms"].get("eval", (None,))[0]
+    line = {
+        "metric": METRIC, "value": r["value"], "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": r["step_ms"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if r["prec_name"] == "fp64" else "bf16x3+f32+f64",
+        "data": "synthetic", "config": dict(cfg, precision=r["prec_name"]),
+        "eval_pts_per_s": r["n_pts"] * ws / (eval_ms / 1e3) if eval_ms else None,
+        "fit_cells_per_s": None,
+        "l1_rel": r["err"]["l1"], "l2_rel": r["err"]["l2"],
+        "roofline": r["roof"],
+        "cpu_baseline": cpu,
+        "e2e": {"value": r["n_cells"] * ws / r["e2e_s"], "unit": "cells/s",
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+        "gpu_launches": r["launches"],
+        "clocks": r["clocks"],
+        "phase_ms_per_step": {k: round(v[0], 4) for k, v in r["phase_ms"].items()},
+        "plain_fp64": r["plain"],
+    }
+    fit_ms = sum(v[0] for k, v in r["phase_ms"].items() if k not in ("eval", "errors"))
+    line["fit_cells_per_s"] = r["n_cells"] * ws / (fit_ms / 1e3) if fit_ms else None
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -211,6 +211,25 @@ pam_status pam_errors(const pam_problem *prob, const pam_plan *plan,
                       const pam_model *model, const double *d_K, double *d_err,
                       void *d_workspace, size_t workspace_bytes, void *stream);
 
+/*
+ * Optional kernel timing. When enabled, every kernel family below records a
+ * CUDA event pair around its launches on the caller's stream; reading sums
+ * the elapsed times per family (and synchronises on the recorded events).
+ * Families: PAM_PHASE_* (prepare, assemble, gram, solve, residual, mark,
+ * eval, errors, stats, gram_tc, refine). Not thread-safe against concurrent
+ * enable/reset; intended for benchmarks. No counterpart in the paper.
+ */
+enum {
+    PAM_PHASE_PREPARE = 0, PAM_PHASE_ASSEMBLE, PAM_PHASE_GRAM, PAM_PHASE_SOLVE,
+    PAM_PHASE_RESIDUAL, PAM_PHASE_MARK, PAM_PHASE_EVAL, PAM_PHASE_ERRORS,
+    PAM_PHASE_STATS, PAM_PHASE_GRAM_TC, PAM_PHASE_REFINE, PAM_PHASE_COUNT
+};
+void pam_timing_enable(int on);
+/* Kernels this library has launched since it was loaded (host-side count). */
+long long pam_kernel_launches(void);
+void pam_timing_reset(void);
+pam_status pam_timing_read(int phase, double *h_total_ms, int *h_count);
+
 #ifdef __cplusplus
 }
 #endif

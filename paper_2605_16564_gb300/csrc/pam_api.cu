@@ -2,6 +2,9 @@
 // carve-up and the order of the launches of each C-ABI entry point.
 #include <cmath>
 #include <cstring>
+#include <atomic>
+#include <mutex>
+#include <vector>
 
 #include "pam_internal.cuh"
 
@@ -115,6 +118,37 @@ static size_t carve(const Geo &g, char *base, Ws *w) {
     return off;
 }
 
+// ---------------------------------------------------------------- timing ---
+// Event pairs recorded on the launching stream; read back (with one
+// synchronisation) by pam_timing_read.
+namespace {
+struct Pair {
+    int phase;
+    cudaEvent_t a, b;
+};
+bool g_timing = false;
+std::atomic<long long> g_launches{0};
+std::vector<Pair> g_pairs;
+std::mutex g_mu;
+}  // namespace
+
+void count_launches(int n) { g_launches += n; }
+
+PhaseScope::PhaseScope(int phase, cudaStream_t st) : phase_(phase), st_(st), stop_(nullptr), on_(g_timing) {
+    if (!on_) return;
+    cudaEvent_t a, b;
+    cudaEventCreate(&a);
+    cudaEventCreate(&b);
+    cudaEventRecord(a, st);
+    stop_ = b;
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_pairs.push_back({phase, a, b});
+}
+
+PhaseScope::~PhaseScope() {
+    if (on_) cudaEventRecord(stop_, st_);
+}
+
 Ws carve_workspace(const Geo &g, void *base) {
     Ws w;
     carve(g, (char *)base, &w);
@@ -128,6 +162,37 @@ using namespace pam;
 extern "C" {
 
 const char *pam_version(void) { return "libpam 0.1 (sm_103a)"; }
+
+void pam_timing_enable(int on) { g_timing = on != 0; }
+
+long long pam_kernel_launches(void) { return g_launches.load(); }
+
+void pam_timing_reset(void) {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto &p : g_pairs) {
+        cudaEventDestroy(p.a);
+        cudaEventDestroy(p.b);
+    }
+    g_pairs.clear();
+}
+
+pam_status pam_timing_read(int phase, double *h_total_ms, int *h_count) {
+    if (!h_total_ms || !h_count || phase < 0 || phase >= PAM_PHASE_COUNT) return PAM_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> lk(g_mu);
+    double tot = 0.0;
+    int cnt = 0;
+    for (auto &p : g_pairs) {
+        if (p.phase != phase) continue;
+        if (cudaEventSynchronize(p.b) != cudaSuccess) return PAM_ERR_CUDA;
+        float ms = 0.0f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) != cudaSuccess) return PAM_ERR_CUDA;
+        tot += ms;
+        ++cnt;
+    }
+    *h_total_ms = tot;
+    *h_count = cnt;
+    return PAM_OK;
+}
 
 const char *pam_status_string(pam_status s) {
     switch (s) {

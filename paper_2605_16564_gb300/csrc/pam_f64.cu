@@ -36,6 +36,7 @@ __global__ void k_partition(Geo g, int32_t *boxes) {
 
 void launch_partition(const Geo &g, int32_t *boxes, cudaStream_t st) {
     k_partition<<<(g.S + 127) / 128, 128, 0, st>>>(g, boxes);
+    count_launches(1);
 }
 
 // --------------------------------------------------------------------------
@@ -77,9 +78,11 @@ __global__ void k_prepare(Geo g, const int32_t *boxes, const double *K, Ws w) {
 
 void launch_prepare(const Geo &g, const int32_t *boxes, const double *K, const Ws &w,
                     cudaStream_t st) {
+    PhaseScope ps(kPhPrepare, st);
     cudaMemsetAsync(w.kmax_bits, 0, sizeof(unsigned long long) * g.S, st);
     dim3 grid((g.n_max + 255) / 256, g.S);
     k_prepare<<<grid, 256, 0, st>>>(g, boxes, K, w);
+    count_launches(1);
 }
 
 // --------------------------------------------------------------------------
@@ -129,6 +132,7 @@ void launch_init_dictionary(const Geo &g, const int32_t *boxes, double *centres,
                             int32_t *info, cudaStream_t st) {
     dim3 grid((g.m_cap + 127) / 128, g.S);
     k_init_dictionary<<<grid, 128, 0, st>>>(g, boxes, centres, beta, info);
+    count_launches(1);
 }
 
 // --------------------------------------------------------------------------
@@ -450,16 +454,29 @@ void launch_solve_level_f64(const Geo &g, const Par &p, const int32_t *boxes,
                             cudaStream_t st) {
     size_t asm_smem = (size_t)g.m_cap * sizeof(dvec4);
     cudaFuncSetAttribute(k_assemble_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_smem);
-    dim3 ga((g.n_max + 127) / 128, g.S);
-    k_assemble_f64<<<ga, 128, asm_smem, st>>>(g, boxes, centres, info, w);
-    dim3 gb((g.m_cap + 7) / 8, g.S);
-    k_bvec_f64<<<gb, 256, 0, st>>>(g, info, w);
-    int T = g.m_cap / kGT;
-    dim3 gg(T * (T + 1) / 2, g.S);
-    k_gram_f64<<<gg, 256, 0, st>>>(g, info, w);
     size_t ss = solve_smem_bytes(g.m_cap);
     cudaFuncSetAttribute(k_solve_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    k_solve_f64<<<g.S, kSolveThreads, ss, st>>>(g, p, beta, info, w);
+    {
+        PhaseScope ps(kPhAssemble, st);
+        dim3 ga((g.n_max + 127) / 128, g.S);
+        k_assemble_f64<<<ga, 128, asm_smem, st>>>(g, boxes, centres, info, w);
+        count_launches(1);
+        dim3 gb((g.m_cap + 7) / 8, g.S);
+        k_bvec_f64<<<gb, 256, 0, st>>>(g, info, w);
+        count_launches(1);
+    }
+    {
+        PhaseScope ps(kPhGram, st);
+        int T = g.m_cap / kGT;
+        dim3 gg(T * (T + 1) / 2, g.S);
+        k_gram_f64<<<gg, 256, 0, st>>>(g, info, w);
+        count_launches(1);
+    }
+    {
+        PhaseScope ps(kPhSolve, st);
+        k_solve_f64<<<g.S, kSolveThreads, ss, st>>>(g, p, beta, info, w);
+        count_launches(1);
+    }
 }
 
 // --------------------------------------------------------------------------
@@ -632,14 +649,18 @@ void launch_mark_enrich(const Geo &g, const Par &p, const int32_t *boxes, double
                         double *beta, int32_t *info, const Ws &w, cudaStream_t st) {
     size_t sm = (size_t)g.n_max * sizeof(unsigned long long);
     cudaFuncSetAttribute(k_mark_enrich, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    PhaseScope ps(kPhMark, st);
     k_mark_enrich<<<g.S, kMarkThreads, sm, st>>>(g, p, boxes, centres, beta, info, w);
+    count_launches(1);
 }
 
 void launch_residual_f64(const Geo &g, const double *beta, const int32_t *info, const Ws &w,
                          cudaStream_t st) {
     size_t sm = (size_t)g.m_cap * sizeof(double);
     dim3 grid((g.n_max + 127) / 128, g.S);
+    PhaseScope ps(kPhResidual, st);
     k_residual_f64<<<grid, 128, sm, st>>>(g, beta, info, w);
+    count_launches(1);
 }
 
 // --------------------------------------------------------------------------
@@ -694,7 +715,9 @@ void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, cons
         return;
     }
     int64_t blocks = (n_pts + 127) / 128;
+    PhaseScope ps(kPhEval, st);
     k_eval_f64<<<(unsigned)blocks, 128, 0, st>>>(g, centres, beta, info, pts, n_pts, out, log_space);
+    count_launches(1);
 }
 
 // Per-block partial sums over the grid cells, in a fixed order:
@@ -763,8 +786,11 @@ void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, co
                    cudaStream_t st) {
     (void)boxes;
     int nb = kErrBlocks / 2;  // err_part holds kErrBlocks*4 doubles = nb rows of 8
+    PhaseScope ps(kPhErrors, st);
     k_errors_partial<<<nb, kErrThreads, 0, st>>>(g, centres, beta, info, K, w.err_part);
+    count_launches(1);
     k_errors_final<<<1, 32, 0, st>>>(w.err_part, nb, err);
+    count_launches(1);
 }
 
 // --------------------------------------------------------------------------

@@ -78,6 +78,26 @@ void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, cons
 void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
                    const int32_t *info, const double *K, double *err, const Ws &w, cudaStream_t st);
 
+// Kernel families timed by the optional event profiler (pam_timing_*).
+enum Phase {
+    kPhPrepare = 0, kPhAssemble, kPhGram, kPhSolve, kPhResidual, kPhMark, kPhEval, kPhErrors,
+    kPhStats, kPhGramTC, kPhRefine, kPhCount
+};
+
+// Counts kernel launches issued by the library (host side).
+void count_launches(int n);
+
+// Records a CUDA event pair around the launches of its scope on `st` when
+// the profiler is on (one pair per scope); a no-op otherwise.
+struct PhaseScope {
+    PhaseScope(int phase, cudaStream_t st);
+    ~PhaseScope();
+    int phase_;
+    cudaStream_t st_;
+    cudaEvent_t stop_;
+    bool on_;
+};
+
 // ---------------------------------------------------------------- device ---
 
 // Patch extent w[a] = patch_hi - patch_lo of subdomain s.
