@@ -152,8 +152,9 @@ FP64_NOMINAL_TFLOPS = 1.25
 
 def accounting(fit, Kd, levels, pam):
     """Algorithmic work of one step, counted from the dictionary sizes each
-    solve actually had: Gram flops sum 2 N_i M_i^2 and assembly exps
-    sum N_i M_i over every (subdomain, solve). Runs the fit level by level
+    solve actually had: Gram flops sum N_i M_i (M_i + 1) (the multiply-adds
+    of the upper triangle of the symmetric W^T W, two flops each) and
+    assembly exps sum N_i M_i over every (subdomain, solve). Runs the fit level by level
     (outside the timed region) and reads the sizes after each level."""
     gram, exps = 0.0, 0.0
     fit_levels = [0] + [1] * levels
@@ -166,7 +167,7 @@ def accounting(fit, Kd, levels, pam):
         solved = info[:, pam.INFO_STOPPED] == 0 if r > 0 else np.ones(len(info), bool)
         n = info[solved, pam.INFO_N_CELLS].astype(float)
         m = info[solved, pam.INFO_M].astype(float)
-        gram += float(np.sum(2.0 * n * m * m))
+        gram += float(np.sum(n * m * (m + 1.0)))
         exps += float(np.sum(n * m))
     return gram, exps
 
