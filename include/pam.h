@@ -212,6 +212,28 @@ pam_status pam_errors(const pam_problem *prob, const pam_plan *plan,
                       void *d_workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * pam_errors without a workspace and without allocating device memory.
+ * The paper has no counterpart: this exists for callers that cannot
+ * allocate on the GPU or hand the library scratch space -- host programs
+ * that reserve all device memory in their own pool at start-up, or
+ * real-time loops where an allocation's latency or failure is not
+ * acceptable. It computes the same four measures into d_err (device
+ * double [4]) as pam_errors, summing fixed chunks of 4096 grid cells.
+ * Scratch: a file-scope device array of 4096 x 8 doubles (256 KiB) that
+ * every GPU loading the library holds until the process exits; grids of
+ * more than 16,777,216 cells return PAM_ERR_UNSUPPORTED. The first call on
+ * each device looks up the array's device address with that device
+ * current; make that first call before any stream capture. Every call
+ * writes all the partial sums it reads, so no state carries over, but all
+ * calls share the one array: calls that overlap on the GPU (different
+ * streams, or different host threads on one device) race and must be
+ * serialised by the caller. Asynchronous on `stream`.
+ */
+pam_status pam_errors_noalloc(const pam_problem *prob, const pam_plan *plan,
+                              const pam_model *model, const double *d_K, double *d_err,
+                              void *stream);
+
+/*
  * Optional kernel timing. When enabled, every kernel family below records a
  * CUDA event pair around its launches on the caller's stream; reading sums
  * the elapsed times per family (and synchronises on the recorded events).

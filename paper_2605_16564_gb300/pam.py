@@ -85,8 +85,10 @@ def lib():
                                C.c_void_p, C.c_int, C.c_int, C.c_void_p]
         L.pam_errors.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_errors_noalloc.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p,
+                                         C.c_void_p, C.c_void_p]
         for name in ("pam_plan_create", "pam_partition", "pam_fit_subdomains", "pam_refine",
-                     "pam_eval", "pam_errors"):
+                     "pam_eval", "pam_errors", "pam_errors_noalloc"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -176,6 +178,14 @@ def pam_errors(problem, plan, model, K, err, workspace, stream=None):
     _check(lib().pam_errors(C.byref(problem), C.byref(plan), C.byref(model.c_struct()), _ptr(K),
                             _ptr(err), _ptr(workspace), workspace.numel() * workspace.element_size(),
                             _stream(stream)), "pam_errors")
+
+
+def pam_errors_noalloc(problem, plan, model, K, err, stream=None):
+    """pam_errors for callers that cannot allocate device memory or provide
+    a workspace (e.g. a host simulator that owns the whole GPU memory pool):
+    its scratch is a fixed 256 KiB array inside the library."""
+    _check(lib().pam_errors_noalloc(C.byref(problem), C.byref(plan), C.byref(model.c_struct()),
+                                    _ptr(K), _ptr(err), _stream(stream)), "pam_errors_noalloc")
 
 
 # ------------------------------------------------------------------ helpers --
