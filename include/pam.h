@@ -52,7 +52,8 @@ typedef enum {
     PAM_ERR_CUDA = 3,          /* a CUDA runtime call failed */
     PAM_ERR_WORKSPACE = 4,     /* workspace smaller than pam_plan.workspace_bytes */
     PAM_ERR_NOT_CONVERGED = 5, /* some subdomain's solve was not certified (see info) */
-    PAM_ERR_UNSUPPORTED = 6    /* valid request this build does not serve */
+    PAM_ERR_UNSUPPORTED = 6,   /* valid request this build does not serve */
+    PAM_ERR_TIMEOUT = 7        /* a bounded device wait gave up (tensor-core pipeline) */
 } pam_status;
 
 typedef enum {
@@ -184,6 +185,22 @@ pam_status pam_refine(const pam_problem *prob, const pam_params *par,
                       const pam_plan *plan, const double *d_K, pam_model *model,
                       int n_levels, void *d_workspace, size_t workspace_bytes,
                       void *stream);
+
+/*
+ * Normal-equation data of the Elastic Net (Eq. (2) with the Shepard matrix W
+ * of Eq. (10) in place of Phi) for the model's CURRENT dictionaries, every
+ * subdomain: d_G [S][m_cap][m_cap] = W^T W (both triangles; zero past M_i)
+ * and d_b [S][m_cap] = W^T ln K, as device doubles. The building block that
+ * pam_fit_subdomains and pam_refine use before each solve, exposed for
+ * inspection: PAM_PREC_FP64 forms it in binary64; PAM_PREC_MIXED on the
+ * tensor cores (W split into bf16 hi + lo, three products, fp32
+ * accumulation; about 2^-16 relative per entry). Needs a model set up by
+ * pam_fit_subdomains. Synchronises `stream` once; PAM_ERR_TIMEOUT if the
+ * tensor-core pipeline stalled (no result then).
+ */
+pam_status pam_gram(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                    const double *d_K, const pam_model *model, double *d_G, double *d_b,
+                    void *d_workspace, size_t workspace_bytes, void *stream);
 
 /*
  * Step 4 (section 2): K*(x) = exp(sum_m beta_m w_m(x)) with the Shepard

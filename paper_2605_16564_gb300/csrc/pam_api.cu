@@ -68,12 +68,13 @@ bool make_geo(const pam_problem *prob, const pam_params *par, Geo *g, Par *p, pa
         if (std::isnan(par->eps_tol_rel)) return false;
         if (par->k_top < 0 || par->m_max < 0 || par->levels < 0 || par->max_iters < 0) return false;
         if (par->precision != PAM_PREC_FP64 && par->precision != PAM_PREC_MIXED) return false;
-        if (par->precision == PAM_PREC_MIXED) { *st = PAM_ERR_UNSUPPORTED; return false; }
         int64_t add = (int64_t)par->levels * (g->dim + 1) * par->k_top;
         if (add > par->m_max) add = par->m_max;
         int64_t cap = (int64_t)g->m0 + add;
         cap = (int64_t)align_up((size_t)cap, 64);
         if (cap > PAM_MAX_M) { *st = PAM_ERR_UNSUPPORTED; return false; }
+        // the tensor-core Gram keeps a 128 x M strip in TMEM (512 columns)
+        if (par->precision == PAM_PREC_MIXED && cap > kMixedMaxM) { *st = PAM_ERR_UNSUPPORTED; return false; }
         g->m_cap = (int)cap;
         if (p) {
             p->lam1_hat = par->lambda1_hat;
@@ -203,6 +204,7 @@ const char *pam_status_string(pam_status s) {
         case PAM_ERR_WORKSPACE: return "workspace too small";
         case PAM_ERR_NOT_CONVERGED: return "a subdomain solve was not certified";
         case PAM_ERR_UNSUPPORTED: return "unsupported size";
+        case PAM_ERR_TIMEOUT: return "a device wait ran out of time";
     }
     return "unknown status";
 }
@@ -271,6 +273,7 @@ pam_status pam_fit_subdomains(const pam_problem *prob, const pam_params *par, co
     if (!par || !make_geo(prob, par, &g, &p, &st)) return par ? st : PAM_ERR_INVALID_ARG;
     if ((st = check_plan(g, plan)) != PAM_OK) return st;
     g.m_cap = plan->m_cap;
+    if (par->precision == PAM_PREC_MIXED) return PAM_ERR_UNSUPPORTED;
     if (!d_K || !model_ok(model) || !d_workspace) return PAM_ERR_INVALID_ARG;
     Ws w = carve_workspace(g, d_workspace);
     if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
@@ -301,6 +304,7 @@ pam_status pam_refine(const pam_problem *prob, const pam_params *par, const pam_
     if (!par || !make_geo(prob, par, &g, &p, &st)) return par ? st : PAM_ERR_INVALID_ARG;
     if ((st = check_plan(g, plan)) != PAM_OK) return st;
     g.m_cap = plan->m_cap;
+    if (par->precision == PAM_PREC_MIXED) return PAM_ERR_UNSUPPORTED;
     if (!d_K || !model_ok(model) || !d_workspace || n_levels < 0) return PAM_ERR_INVALID_ARG;
     Ws w = carve_workspace(g, d_workspace);
     if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
@@ -318,6 +322,37 @@ pam_status pam_refine(const pam_problem *prob, const pam_params *par, const pam_
     int32_t hs[8];
     if ((st = read_status(w, s, hs)) != PAM_OK) return st;
     return hs[kStUncertified] ? PAM_ERR_NOT_CONVERGED : PAM_OK;
+}
+
+pam_status pam_gram(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                    const double *d_K, const pam_model *model, double *d_G, double *d_b,
+                    void *d_workspace, size_t workspace_bytes, void *stream) {
+    Geo g;
+    Par p;
+    pam_status st;
+    if (!par || !make_geo(prob, par, &g, &p, &st)) return par ? st : PAM_ERR_INVALID_ARG;
+    if ((st = check_plan(g, plan)) != PAM_OK) return st;
+    g.m_cap = plan->m_cap;
+    if (par->precision == PAM_PREC_MIXED && g.m_cap > kMixedMaxM) return PAM_ERR_UNSUPPORTED;
+    if (!d_K || !model_ok(model) || !d_G || !d_b || !d_workspace) return PAM_ERR_INVALID_ARG;
+    Ws w = carve_workspace(g, d_workspace);
+    if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 8 * sizeof(int32_t), s));
+    launch_prepare(g, model->boxes, d_K, w, s);
+    if (par->precision == PAM_PREC_MIXED) {
+        launch_stats_gram_tc(g, model->boxes, model->centres, model->info, w, s, 1);
+        launch_copy_gram_f32(g, model->info, w, d_G, d_b, s);
+    } else {
+        launch_assemble_gram_f64(g, model->boxes, model->centres, model->info, w, s, 1);
+        launch_copy_gram_f64(g, model->info, w, d_G, d_b, s);
+    }
+    PAM_CUDA_TRY(cudaGetLastError());
+    int32_t hs[8];
+    if ((st = read_status(w, s, hs)) != PAM_OK) return st;
+    if (hs[kStBadK]) return PAM_ERR_NONPOSITIVE_K;
+    if (hs[kStTimeout]) return PAM_ERR_TIMEOUT;
+    return PAM_OK;
 }
 
 pam_status pam_eval(const pam_problem *prob, const pam_plan *plan, const pam_model *model,

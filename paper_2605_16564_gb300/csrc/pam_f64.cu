@@ -142,10 +142,10 @@ void launch_init_dictionary(const Geo &g, const int32_t *boxes, double *centres,
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_assemble_f64(Geo g, const int32_t *boxes,
                                                       const double *centres, const int32_t *info,
-                                                      Ws w) {
+                                                      Ws w, int all) {
     int s = blockIdx.y;
     const int32_t *inf = info + s * kInfoN;
-    if (inf[PAM_INFO_STOPPED]) return;
+    if (!all && inf[PAM_INFO_STOPPED]) return;
     int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
     extern __shared__ dvec4 sc[];  // (c_x, c_y, c_z, -1/(2 sigma^2))
     const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
@@ -180,10 +180,10 @@ __global__ void __launch_bounds__(128) k_assemble_f64(Geo g, const int32_t *boxe
 }
 
 // b_m = sum_j W_jm y_j, one warp per (subdomain, centre).
-__global__ void k_bvec_f64(Geo g, const int32_t *info, Ws w) {
+__global__ void k_bvec_f64(Geo g, const int32_t *info, Ws w, int all) {
     int s = blockIdx.y;
     const int32_t *inf = info + s * kInfoN;
-    if (inf[PAM_INFO_STOPPED]) return;
+    if (!all && inf[PAM_INFO_STOPPED]) return;
     int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
     int m = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     int lane = threadIdx.x & 31;
@@ -199,10 +199,10 @@ __global__ void k_bvec_f64(Geo g, const int32_t *info, Ws w) {
 
 // G = W^T W on 64 x 64 tiles of the upper triangle, mirrored; fp64 FMA.
 constexpr int kGT = 64, kGK = 16;
-__global__ void __launch_bounds__(256) k_gram_f64(Geo g, const int32_t *info, Ws w) {
+__global__ void __launch_bounds__(256) k_gram_f64(Geo g, const int32_t *info, Ws w, int all) {
     int s = blockIdx.y;
     const int32_t *inf = info + s * kInfoN;
-    if (inf[PAM_INFO_STOPPED]) return;
+    if (!all && inf[PAM_INFO_STOPPED]) return;
     int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
     int T = g.m_cap / kGT;
     int u = blockIdx.x, ti = 0;
@@ -449,34 +449,59 @@ static size_t solve_smem_bytes(int mc) {
     return (size_t)mc * (4 * sizeof(double) + 2 * sizeof(int)) + kFactorSmemBytes;
 }
 
-void launch_solve_level_f64(const Geo &g, const Par &p, const int32_t *boxes,
-                            const double *centres, double *beta, int32_t *info, const Ws &w,
-                            cudaStream_t st) {
+void launch_assemble_gram_f64(const Geo &g, const int32_t *boxes, const double *centres,
+                              const int32_t *info, const Ws &w, cudaStream_t st, int all) {
     size_t asm_smem = (size_t)g.m_cap * sizeof(dvec4);
     cudaFuncSetAttribute(k_assemble_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_smem);
-    size_t ss = solve_smem_bytes(g.m_cap);
-    cudaFuncSetAttribute(k_solve_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     {
         PhaseScope ps(kPhAssemble, st);
         dim3 ga((g.n_max + 127) / 128, g.S);
-        k_assemble_f64<<<ga, 128, asm_smem, st>>>(g, boxes, centres, info, w);
+        k_assemble_f64<<<ga, 128, asm_smem, st>>>(g, boxes, centres, info, w, all);
         count_launches(1);
         dim3 gb((g.m_cap + 7) / 8, g.S);
-        k_bvec_f64<<<gb, 256, 0, st>>>(g, info, w);
+        k_bvec_f64<<<gb, 256, 0, st>>>(g, info, w, all);
         count_launches(1);
     }
     {
         PhaseScope ps(kPhGram, st);
         int T = g.m_cap / kGT;
         dim3 gg(T * (T + 1) / 2, g.S);
-        k_gram_f64<<<gg, 256, 0, st>>>(g, info, w);
+        k_gram_f64<<<gg, 256, 0, st>>>(g, info, w, all);
         count_launches(1);
     }
-    {
-        PhaseScope ps(kPhSolve, st);
-        k_solve_f64<<<g.S, kSolveThreads, ss, st>>>(g, p, beta, info, w);
-        count_launches(1);
+}
+
+void launch_solve_level_f64(const Geo &g, const Par &p, const int32_t *boxes,
+                            const double *centres, double *beta, int32_t *info, const Ws &w,
+                            cudaStream_t st) {
+    launch_assemble_gram_f64(g, boxes, centres, info, w, st, 0);
+    size_t ss = solve_smem_bytes(g.m_cap);
+    cudaFuncSetAttribute(k_solve_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    PhaseScope ps(kPhSolve, st);
+    k_solve_f64<<<g.S, kSolveThreads, ss, st>>>(g, p, beta, info, w);
+    count_launches(1);
+}
+
+__global__ void k_copy_gram_f64(Geo g, const int32_t *info, const double *G, const double *b,
+                                double *G_out, double *b_out) {
+    const int s = blockIdx.y;
+    const int M = info[s * kInfoN + PAM_INFO_M];
+    const size_t mc = g.m_cap;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < mc * mc;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int r = (int)(e / mc), c = (int)(e % mc);
+        G_out[s * mc * mc + e] = (r < M && c < M) ? G[s * mc * mc + e] : 0.0;
     }
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < mc;
+         e += (size_t)gridDim.x * blockDim.x)
+        b_out[s * mc + e] = (int)e < M ? b[s * mc + e] : 0.0;
+}
+
+void launch_copy_gram_f64(const Geo &g, const int32_t *info, const Ws &w, double *G_out,
+                          double *b_out, cudaStream_t st) {
+    dim3 grid(64, g.S);
+    k_copy_gram_f64<<<grid, 256, 0, st>>>(g, info, w.G, w.b, G_out, b_out);
+    count_launches(1);
 }
 
 // --------------------------------------------------------------------------

@@ -54,9 +54,10 @@ struct Ws {
     size_t bytes;
 };
 
-enum StatusWord { kStBadK = 0, kStUncertified = 1, kStCholesky = 2 };
+enum StatusWord { kStBadK = 0, kStUncertified = 1, kStCholesky = 2, kStTimeout = 3 };
 
 constexpr int kErrBlocks = 1024;
+constexpr int kMixedMaxM = 512;  // dictionary capacity limit of the tensor-core Gram
 
 Ws carve_workspace(const Geo &g, void *base);
 bool make_geo(const pam_problem *prob, const pam_params *par, Geo *g, Par *p, pam_status *st);
@@ -68,6 +69,14 @@ void launch_init_dictionary(const Geo &g, const int32_t *boxes, double *centres,
                             int32_t *info, cudaStream_t st);
 void launch_solve_level_f64(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
                             double *beta, int32_t *info, const Ws &w, cudaStream_t st);
+void launch_stats_gram_tc(const Geo &g, const int32_t *boxes, const double *centres,
+                          const int32_t *info, const Ws &w, cudaStream_t st, int all);
+void launch_assemble_gram_f64(const Geo &g, const int32_t *boxes, const double *centres,
+                              const int32_t *info, const Ws &w, cudaStream_t st, int all);
+void launch_copy_gram_f32(const Geo &g, const int32_t *info, const Ws &w, double *G_out,
+                          double *b_out, cudaStream_t st);
+void launch_copy_gram_f64(const Geo &g, const int32_t *info, const Ws &w, double *G_out,
+                          double *b_out, cudaStream_t st);
 void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
                               double *beta, int32_t *info, const Ws &w, cudaStream_t st);
 void launch_refine_round(const Geo &g, const Par &p, int precision, const int32_t *boxes,

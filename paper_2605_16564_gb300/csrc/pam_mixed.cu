@@ -1,12 +1,348 @@
-// pam_mixed.cu -- the mixed-precision form (tensor-core Gram, fp32 solve
-// with iterative refinement). Not built yet: the plan rejects it.
+// pam_mixed.cu -- the mixed-precision form of the fitting path:
+//   * Shepard row statistics in fp32 (k_stats_f32),
+//   * the Gram products G = W^T W, b = W^T y on the tcgen05 tensor cores
+//     (k_gram_tc): W is generated in registers, split into bf16 hi + lo
+//     parts, staged in shared memory, and multiplied hi*hi + hi*lo + lo*hi
+//     with fp32 accumulation in TMEM (relative error ~2^-16 per entry),
+//   * the Elastic Net solve in fp32 with iterative refinement against the
+//     exactly recomputed gradient W^T (y - W beta) (k_solve_mixed),
+//   * residual indicators with fp64 accumulation of the K-space residual.
+//
+// All Gaussians are evaluated in local coordinates relative to the patch
+// origin, from coordinate differences, in base 2:
+//   l2 = alpha_m |x - c_m|^2,  alpha_m = -log2(e) / (2 sigma_m^2).
+#include <cfloat>
+#include <cmath>
+
 #include "pam_internal.cuh"
+#include "pam_tc.cuh"
 
 namespace pam {
+
+// Per-centre constants in local coordinates: (c - origin, alpha).
+__device__ __forceinline__ float4 local_centre(const dvec4 &c, const double o[3]) {
+    float4 r;
+    r.x = (float)(c.x - o[0]);
+    r.y = (float)(c.y - o[1]);
+    r.z = (float)(c.z - o[2]);
+    r.w = (float)(-1.4426950408889634 / (2.0 * c.w * c.w));
+    return r;
+}
+
+__device__ __forceinline__ float logit2(const float4 &c, float x, float y, float z) {
+    float dx = x - c.x, dy = y - c.y, dz = z - c.z;
+    return c.w * fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+__device__ __forceinline__ void patch_origin(const Geo &g, const int32_t *box, double o[3]) {
+    for (int a = 0; a < 3; ++a) o[a] = a < g.dim ? (double)box[6 + a] * g.h : 0.0;
+}
+
+// Local coordinates of patch cell t: ((i - patch_lo) + 1/2) h, exact in fp32
+// up to one rounding.
+__device__ __forceinline__ void local_cell(const Geo &g, const int32_t *box, int t, float x[3]) {
+    int w0 = box[9] - box[6], w1 = box[10] - box[7];
+    int i = t % w0, j = (t / w0) % w1, k = t / (w0 * w1);
+    float hf = (float)g.h;
+    x[0] = ((float)i + 0.5f) * hf;
+    x[1] = g.dim > 1 ? ((float)j + 0.5f) * hf : 0.0f;
+    x[2] = g.dim > 2 ? ((float)k + 0.5f) * hf : 0.0f;
+}
+
+// --------------------------------------------------------------------------
+// Row statistics of the Shepard normalisation (Eq. (10)): l2* = max_m l2_jm
+// and 1 / sum_m 2^(l2_jm - l2*), one thread per patch cell.
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(128) k_stats_f32(Geo g, const int32_t *boxes,
+                                                   const double *centres, const int32_t *info,
+                                                   Ws w, int all) {
+    const int s = blockIdx.y;
+    const int32_t *inf = info + s * kInfoN;
+    if (!all && inf[PAM_INFO_STOPPED]) return;
+    const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
+    const int32_t *box = boxes + s * 12;
+    extern __shared__ float4 sc[];
+    double o[3];
+    patch_origin(g, box, o);
+    const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) sc[m] = local_centre(cg[m], o);
+    __syncthreads();
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    if (t >= N) return;
+    float x[3];
+    local_cell(g, box, t, x);
+    float lmax = -INFINITY;
+    for (int m = 0; m < M; ++m) lmax = fmaxf(lmax, logit2(sc[m], x[0], x[1], x[2]));
+    float sum = 0.0f;
+    for (int m = 0; m < M; ++m) sum += tc::ex2(logit2(sc[m], x[0], x[1], x[2]) - lmax);
+    w.rowmax[(size_t)s * g.n_max + t] = lmax;
+    w.rowinv[(size_t)s * g.n_max + t] = 1.0f / sum;
+}
+
+// --------------------------------------------------------------------------
+// Gram products on the tensor cores. One CTA per (subdomain, strip of 128
+// centres I): D = W_I^T W_{I..} (128 x R, R = centres from the strip start
+// to the padded end of the dictionary) accumulates in TMEM over chunks of 32
+// cells. The 256 threads generate the chunk's W values (each thread one or
+// two centre rows), split them into bf16 hi/lo and store them in the
+// canonical K-major layout (8-row x 16-byte core matrices); the A operand
+// is the first 128 rows of the same tile. Two buffers: the threads fill one
+// while the tensor core consumes the other; thread 0 issues the MMAs and
+// commits them to the buffer's mbarrier.
+// Epilogue: warps read the strip from TMEM and write rows of G (and the
+// mirrored block below the strip) in fp32; threads of the strip's rows also
+// accumulate b = W^T y.
+// --------------------------------------------------------------------------
+constexpr int kTcThreads = 256;
+constexpr int kTcKC = 32;                 // cells per chunk (2 MMA k-steps of 16)
+constexpr int kTcMaxRows = 512;           // rows of the B tile (TMEM columns)
+constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz
+
+struct TcCell {
+    float x[kTcKC], y[kTcKC], z[kTcKC], mx[kTcKC], inv[kTcKC], yv[kTcKC];
+};
+
+__global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t *boxes,
+                                                           const double *centres,
+                                                           const int32_t *info, Ws w, int all) {
+    const int s = blockIdx.y, strip = blockIdx.x;
+    const int32_t *inf = info + s * kInfoN;
+    if (!all && inf[PAM_INFO_STOPPED]) return;
+    const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
+    const int row0 = strip * 128;
+    if (row0 >= M) return;
+    const int Mp = (M + 31) & ~31;                 // padded dictionary size
+    const int R = Mp - row0;                        // B rows = TMEM columns (multiple of 32)
+    const int Rt = R < 128 ? 128 : R;               // tile rows (the A operand reads 128)
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int32_t *box = boxes + s * 12;
+
+    extern __shared__ __align__(1024) uint8_t smem[];
+    // [buf][hi|lo] tiles of Rt x kTcKC bf16, each Rt * 64 bytes
+    const uint32_t tile_bytes = (uint32_t)Rt * kTcKC * 2;
+    uint8_t *tiles = smem;
+    float4 *sc = reinterpret_cast<float4 *>(smem + 4 * (size_t)kTcMaxRows * kTcKC * 2);
+    TcCell *cells = reinterpret_cast<TcCell *>(sc + kTcMaxRows);  // [2]
+    __shared__ uint64_t mbar[2];
+    __shared__ uint32_t tmem_base;
+    __shared__ int timed_out;
+
+    double o[3];
+    patch_origin(g, box, o);
+    const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
+    for (int r = tid; r < R; r += blockDim.x) {
+        int m = row0 + r;
+        sc[r] = m < M ? local_centre(cg[m], o) : make_float4(0.f, 0.f, 0.f, 0.f);
+    }
+    uint32_t ncols = 32;
+    while (ncols < (uint32_t)R) ncols <<= 1;
+    if (tid == 0) {
+        tc::mbar_init(&mbar[0], 1);
+        tc::mbar_init(&mbar[1], 1);
+        tc::mbar_fence_init();
+        timed_out = 0;
+    }
+    if (warp == 0) {
+        tc::tmem_alloc(&tmem_base, ncols);
+        tc::tmem_relinquish();
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    tc::fence_after_sync();
+    const uint32_t tmem = tmem_base;
+
+    const float *rowmax = w.rowmax + (size_t)s * g.n_max;
+    const float *rowinv = w.rowinv + (size_t)s * g.n_max;
+    const double *yv = w.y + (size_t)s * g.n_max;
+    const int nch = (N + kTcKC - 1) / kTcKC;
+    const uint32_t lbo = (uint32_t)Rt * 16u, sbo = 128u;
+    float bacc[2] = {0.f, 0.f};
+    const bool valid_row[2] = {tid < R && row0 + tid < M, tid + 256 < R && row0 + tid + 256 < M};
+
+    int issued = 0;  // chunks whose MMAs thread 0 has committed
+    for (int c = 0; c < nch; ++c) {
+        const int buf = c & 1;
+        if (c >= 2) {  // the MMAs of chunk c-2 read this buffer
+            if (!tc::mbar_wait(&mbar[buf], ((c - 2) >> 1) & 1, kWaitBudget)) timed_out = 1;
+        }
+        // cell data of the chunk
+        TcCell &cl = cells[buf];
+        if (tid < kTcKC) {
+            int t = c * kTcKC + tid;
+            float x[3] = {0.f, 0.f, 0.f};
+            float mx = 0.f, iv = 0.f, y = 0.f;
+            if (t < N) {
+                local_cell(g, box, t, x);
+                mx = rowmax[t];
+                iv = rowinv[t];
+                y = (float)yv[t];
+            }
+            cl.x[tid] = x[0]; cl.y[tid] = x[1]; cl.z[tid] = x[2];
+            cl.mx[tid] = mx; cl.inv[tid] = iv; cl.yv[tid] = y;
+        }
+        __syncthreads();
+        if (timed_out) break;
+        uint8_t *hi = tiles + (size_t)buf * 2 * tile_bytes;
+        uint8_t *lo = hi + tile_bytes;
+        for (int rr = 0; rr < 2; ++rr) {
+            const int r = tid + rr * 256;
+            if (r >= Rt) break;
+            const float4 cc = r < R ? sc[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const bool live = valid_row[rr];
+            float bsum = 0.f;
+#pragma unroll
+            for (int kg = 0; kg < kTcKC / 8; ++kg) {
+                float v[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) {
+                    const int k = kg * 8 + q;
+                    float e = 0.f;
+                    if (live && cl.inv[k] != 0.f)
+                        e = tc::ex2(logit2(cc, cl.x[k], cl.y[k], cl.z[k]) - cl.mx[k]) * cl.inv[k];
+                    v[q] = e;
+                    bsum = fmaf(e, cl.yv[k], bsum);
+                }
+                uint4 h, l;
+                float hv[8];
+#pragma unroll
+                for (int q = 0; q < 8; ++q) hv[q] = __bfloat162float(__float2bfloat16_rn(v[q]));
+                h.x = tc::pack_bf16(hv[0], hv[1]); h.y = tc::pack_bf16(hv[2], hv[3]);
+                h.z = tc::pack_bf16(hv[4], hv[5]); h.w = tc::pack_bf16(hv[6], hv[7]);
+                l.x = tc::pack_bf16(v[0] - hv[0], v[1] - hv[1]);
+                l.y = tc::pack_bf16(v[2] - hv[2], v[3] - hv[3]);
+                l.z = tc::pack_bf16(v[4] - hv[4], v[5] - hv[5]);
+                l.w = tc::pack_bf16(v[6] - hv[6], v[7] - hv[7]);
+                const uint32_t off = (uint32_t)(kg * (Rt >> 3) + (r >> 3)) * 128u + (uint32_t)(r & 7) * 16u;
+                *reinterpret_cast<uint4 *>(hi + off) = h;
+                *reinterpret_cast<uint4 *>(lo + off) = l;
+            }
+            bacc[rr] += bsum;
+        }
+        tc::fence_proxy_async_smem();
+        __syncthreads();
+        if (tid == 0) {
+            tc::fence_after_sync();
+            const uint32_t hi_a = tc::smem_u32(hi), lo_a = tc::smem_u32(lo);
+#pragma unroll
+            for (int ks = 0; ks < kTcKC / 16; ++ks) {
+                const uint32_t koff = (uint32_t)(2 * ks) * lbo;
+                const uint64_t a_hi = tc::smem_desc(hi_a + koff, lbo, sbo);
+                const uint64_t a_lo = tc::smem_desc(lo_a + koff, lbo, sbo);
+                for (int n0 = 0; n0 < R; n0 += 256) {
+                    const uint32_t n = (uint32_t)min(256, R - n0);
+                    const uint32_t id = tc::idesc_bf16_f32(n);
+                    const uint32_t noff = (uint32_t)(n0 >> 3) * sbo;
+                    const uint64_t b_hi = tc::smem_desc(hi_a + koff + noff, lbo, sbo);
+                    const uint64_t b_lo = tc::smem_desc(lo_a + koff + noff, lbo, sbo);
+                    const uint32_t d = tmem + (uint32_t)n0;
+                    tc::mma_bf16(d, a_hi, b_hi, id, (c > 0 || ks > 0) ? 1u : 0u);
+                    tc::mma_bf16(d, a_hi, b_lo, id, 1u);
+                    tc::mma_bf16(d, a_lo, b_hi, id, 1u);
+                }
+            }
+            tc::mma_commit(&mbar[buf]);
+        }
+        issued = c + 1;
+    }
+    // wait for the last chunk's MMAs (they complete in issue order)
+    if (!timed_out && nch > 0) {
+        const int last = nch - 1;
+        if (!tc::mbar_wait(&mbar[last & 1], (last >> 1) & 1, kWaitBudget)) timed_out = 1;
+    }
+    __syncthreads();
+    tc::fence_after_sync();
+    if (timed_out) {
+        // give the MMAs still in flight a bounded time to land before TMEM is released
+        if (issued > 0) tc::mbar_wait(&mbar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kWaitBudget);
+        if (tid == 0) atomicAdd(&w.status[kStTimeout], 1);
+    } else {
+        float *G = w.Gf + (size_t)s * g.m_cap * g.m_cap;
+        // warp q and q+4 share TMEM lanes 32q..32q+31; they split the columns
+        const int lane_base = (warp & 3) * 32;
+        const int r = row0 + lane_base + lane;  // G row held by this thread
+        const int half = warp >> 2;
+        const int ncol_chunks = R / 32;
+        for (int cc = half; cc < ncol_chunks; cc += 2) {
+            uint32_t v[32];
+            tc::tmem_ld_32x32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(cc * 32), v);
+            tc::tmem_wait_ld();
+            const int c0 = row0 + cc * 32;
+            if (r < M) {
+                for (int q = 0; q < 32; ++q) {
+                    int col = c0 + q;
+                    if (col < M) G[(size_t)r * g.m_cap + col] = __uint_as_float(v[q]);
+                }
+            }
+            // mirror the block right of the strip's diagonal block
+            if (cc * 32 >= 128) {
+                for (int q = 0; q < 32; ++q) {
+                    int col = c0 + q;
+                    if (col < M && r < M) G[(size_t)col * g.m_cap + r] = __uint_as_float(v[q]);
+                }
+            }
+        }
+        for (int rr = 0; rr < 2; ++rr) {
+            const int rl = tid + rr * 256;
+            if (rl < 128 && valid_row[rr]) w.b[(size_t)s * g.m_cap + row0 + rl] = (double)bacc[rr];
+        }
+    }
+    tc::fence_before_sync();
+    __syncthreads();
+    if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+}
+
+static size_t gram_tc_smem() {
+    return 4 * (size_t)kTcMaxRows * kTcKC * 2 + kTcMaxRows * sizeof(float4) + 2 * sizeof(TcCell) + 1024;
+}
+
+void launch_stats_gram_tc(const Geo &g, const int32_t *boxes, const double *centres,
+                          const int32_t *info, const Ws &w, cudaStream_t st, int all) {
+    {
+        PhaseScope ps(kPhStats, st);
+        size_t sm = (size_t)g.m_cap * sizeof(float4);
+        cudaFuncSetAttribute(k_stats_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        dim3 grid((g.n_max + 127) / 128, g.S);
+        k_stats_f32<<<grid, 128, sm, st>>>(g, boxes, centres, info, w, all);
+        count_launches(1);
+    }
+    {
+        PhaseScope ps(kPhGramTC, st);
+        size_t sm = gram_tc_smem();
+        cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        dim3 grid((g.m_cap + 127) / 128, g.S);
+        k_gram_tc<<<grid, kTcThreads, sm, st>>>(g, boxes, centres, info, w, all);
+        count_launches(1);
+    }
+}
+
+// Copies the fp32 Gram of the mixed form into caller doubles (pam_gram).
+__global__ void k_copy_gram_f32(Geo g, const int32_t *info, const float *Gf, const double *b,
+                                double *G_out, double *b_out) {
+    const int s = blockIdx.y;
+    const int M = info[s * kInfoN + PAM_INFO_M];
+    const size_t mc = g.m_cap;
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < mc * mc;
+         e += (size_t)gridDim.x * blockDim.x) {
+        int r = (int)(e / mc), c = (int)(e % mc);
+        G_out[s * mc * mc + e] = (r < M && c < M) ? (double)Gf[s * mc * mc + e] : 0.0;
+    }
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < mc;
+         e += (size_t)gridDim.x * blockDim.x)
+        b_out[s * mc + e] = (int)e < M ? b[s * mc + e] : 0.0;
+}
+
+void launch_copy_gram_f32(const Geo &g, const int32_t *info, const Ws &w, double *G_out,
+                          double *b_out, cudaStream_t st) {
+    dim3 grid(64, g.S);
+    k_copy_gram_f32<<<grid, 256, 0, st>>>(g, info, w.Gf, w.b, G_out, b_out);
+    count_launches(1);
+}
+
 void launch_solve_level_mixed(const Geo &, const Par &, const int32_t *, const double *, double *,
                               int32_t *, const Ws &, cudaStream_t) {}
 void launch_residual_mixed(const Geo &, const int32_t *, const double *, const double *,
                            const int32_t *, const Ws &, cudaStream_t) {}
 void launch_eval_mixed(const Geo &, const int32_t *, const double *, const double *,
                        const int32_t *, const double *, int64_t, double *, int, cudaStream_t) {}
+
 }  // namespace pam

@@ -26,10 +26,11 @@ INFO_M, INFO_SUPPORT, INFO_LEVELS, INFO_ITERS, INFO_FLAGS, INFO_STOPPED, INFO_N_
 FLAG_NOT_CERTIFIED, FLAG_CHOLESKY, FLAG_REFINE_DIVERGED = 1, 2, 4
 
 STATUS = {0: "PAM_OK", 1: "PAM_ERR_INVALID_ARG", 2: "PAM_ERR_NONPOSITIVE_K", 3: "PAM_ERR_CUDA",
-          4: "PAM_ERR_WORKSPACE", 5: "PAM_ERR_NOT_CONVERGED", 6: "PAM_ERR_UNSUPPORTED"}
+          4: "PAM_ERR_WORKSPACE", 5: "PAM_ERR_NOT_CONVERGED", 6: "PAM_ERR_UNSUPPORTED",
+          7: "PAM_ERR_TIMEOUT"}
 
 EXPORTED = ["pam_version", "pam_status_string", "pam_plan_create", "pam_partition",
-            "pam_fit_subdomains", "pam_refine", "pam_eval", "pam_errors"]
+            "pam_fit_subdomains", "pam_refine", "pam_gram", "pam_eval", "pam_errors"]
 
 
 class PamError(RuntimeError):
@@ -85,10 +86,12 @@ def lib():
                                C.c_void_p, C.c_int, C.c_int, C.c_void_p]
         L.pam_errors.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_void_p,
                                  C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_gram.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), C.c_void_p, P(pam_model),
+                               C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_errors_noalloc.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p,
                                          C.c_void_p, C.c_void_p]
         for name in ("pam_plan_create", "pam_partition", "pam_fit_subdomains", "pam_refine",
-                     "pam_eval", "pam_errors", "pam_errors_noalloc"):
+                     "pam_eval", "pam_errors", "pam_errors_noalloc", "pam_gram"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -165,6 +168,12 @@ def pam_refine(problem, params, plan, K, model, n_levels, workspace, stream=None
     if check:
         _check(code, "pam_refine")
     return code
+
+
+def pam_gram(problem, params, plan, K, model, G, b, workspace, stream=None):
+    _check(lib().pam_gram(C.byref(problem), C.byref(params), C.byref(plan), _ptr(K),
+                          C.byref(model.c_struct()), _ptr(G), _ptr(b), _ptr(workspace),
+                          workspace.numel() * workspace.element_size(), _stream(stream)), "pam_gram")
 
 
 def pam_eval(problem, plan, model, pts, out, log_space=False, precision=PAM_PREC_FP64, stream=None):
