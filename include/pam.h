@@ -203,17 +203,28 @@ pam_status pam_gram(const pam_problem *prob, const pam_params *par, const pam_pl
                     void *d_workspace, size_t workspace_bytes, void *stream);
 
 /*
+ * Device scratch pam_eval needs for n_pts points (owner keys, ranks and the
+ * bucketed point order: 12 bytes per point plus 8 per subdomain).
+ * PAM_ERR_UNSUPPORTED above 2^31 - 1 points.
+ */
+pam_status pam_eval_workspace_size(const pam_plan *plan, int64_t n_pts, size_t *bytes);
+
+/*
  * Step 4 (section 2): K*(x) = exp(sum_m beta_m w_m(x)) with the Shepard
  * weights w_m (Eq. (9)) over the whole dictionary of the subdomain whose
  * core contains x (half-open cores, outer face of the grid closed).
  * d_pts: device double [n_pts][dim]; d_out: device double [n_pts], K*(x),
  * or the log-space value when log_space != 0; NaN for points outside the
- * grid. precision PAM_PREC_MIXED evaluates the Gaussians in fp32.
+ * grid. The points are bucketed by owner in d_workspace (at least
+ * pam_eval_workspace_size bytes). PAM_PREC_FP64 evaluates in binary64;
+ * PAM_PREC_MIXED evaluates the Gaussians in fp32 (local coordinates, 2^x on
+ * the special-function unit) and the final exp in fp64.
  * Asynchronous (no synchronisation); n_pts == 0 is a no-op.
  */
 pam_status pam_eval(const pam_problem *prob, const pam_plan *plan,
                     const pam_model *model, const double *d_pts, int64_t n_pts,
-                    double *d_out, int log_space, int precision, void *stream);
+                    double *d_out, int log_space, int precision, void *d_workspace,
+                    size_t workspace_bytes, void *stream);
 
 /*
  * Relative errors of the reconstruction over the source cells, each cell
@@ -221,12 +232,13 @@ pam_status pam_eval(const pam_problem *prob, const pam_plan *plan,
  * d_err[0] = sum |K_T - K*| / sum |K_T|, d_err[1] = (Eq. (12))
  * (sum (K_T - K*)^2 / sum K_T^2)^(1/2), d_err[2] = sum |ln K_T - ln K*| /
  * sum |ln K_T|, d_err[3] = max_T |log10 K_T - log10 K*(x_T)|; fp64
- * accumulation. d_err: device double [4]. Uses the workspace.
- * Asynchronous.
+ * accumulation in a fixed order (deterministic). precision selects how the
+ * Gaussians are evaluated (as pam_eval). d_err: device double [4]. Uses the
+ * fit workspace. Asynchronous.
  */
 pam_status pam_errors(const pam_problem *prob, const pam_plan *plan,
                       const pam_model *model, const double *d_K, double *d_err,
-                      void *d_workspace, size_t workspace_bytes, void *stream);
+                      int precision, void *d_workspace, size_t workspace_bytes, void *stream);
 
 /*
  * pam_errors without a workspace and without allocating device memory.
@@ -235,7 +247,8 @@ pam_status pam_errors(const pam_problem *prob, const pam_plan *plan,
  * that reserve all device memory in their own pool at start-up, or
  * real-time loops where an allocation's latency or failure is not
  * acceptable. It computes the same four measures into d_err (device
- * double [4]) as pam_errors, summing fixed chunks of 4096 grid cells.
+ * double [4]) as pam_errors with PAM_PREC_FP64, summing fixed chunks of
+ * 4096 grid cells.
  * Scratch: a file-scope device array of 4096 x 8 doubles (256 KiB) that
  * every GPU loading the library holds until the process exits; grids of
  * more than 16,777,216 cells return PAM_ERR_UNSUPPORTED. The first call on

@@ -103,7 +103,7 @@ static size_t carve(const Geo &g, char *base, Ws *w) {
     const size_t S = (size_t)g.S, nm = (size_t)g.n_max, mc = (size_t)g.m_cap;
     w->status = (int32_t *)take(8 * sizeof(int32_t));
     w->kmax_bits = (unsigned long long *)take(S * sizeof(unsigned long long));
-    w->err_part = (double *)take((size_t)kErrBlocks * 4 * sizeof(double));
+    w->err_part = (double *)take((S > (size_t)kErrBlocks ? S : (size_t)kErrBlocks) * 8 * sizeof(double));
     w->y = (double *)take(S * nm * sizeof(double));
     w->kv = (double *)take(S * nm * sizeof(double));
     w->inv_s = (double *)take(S * nm * sizeof(double));
@@ -273,7 +273,8 @@ pam_status pam_fit_subdomains(const pam_problem *prob, const pam_params *par, co
     if (!par || !make_geo(prob, par, &g, &p, &st)) return par ? st : PAM_ERR_INVALID_ARG;
     if ((st = check_plan(g, plan)) != PAM_OK) return st;
     g.m_cap = plan->m_cap;
-    if (par->precision == PAM_PREC_MIXED) return PAM_ERR_UNSUPPORTED;
+    if (par->precision == PAM_PREC_MIXED && (g.m_cap > kMixedMaxM || !mixed_solve_fits(g)))
+        return PAM_ERR_UNSUPPORTED;
     if (!d_K || !model_ok(model) || !d_workspace) return PAM_ERR_INVALID_ARG;
     Ws w = carve_workspace(g, d_workspace);
     if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
@@ -292,6 +293,7 @@ pam_status pam_fit_subdomains(const pam_problem *prob, const pam_params *par, co
         launch_solve_level_f64(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
     PAM_CUDA_TRY(cudaGetLastError());
     if ((st = read_status(w, s, hs)) != PAM_OK) return st;
+    if (hs[kStTimeout]) return PAM_ERR_TIMEOUT;
     return hs[kStUncertified] ? PAM_ERR_NOT_CONVERGED : PAM_OK;
 }
 
@@ -304,7 +306,8 @@ pam_status pam_refine(const pam_problem *prob, const pam_params *par, const pam_
     if (!par || !make_geo(prob, par, &g, &p, &st)) return par ? st : PAM_ERR_INVALID_ARG;
     if ((st = check_plan(g, plan)) != PAM_OK) return st;
     g.m_cap = plan->m_cap;
-    if (par->precision == PAM_PREC_MIXED) return PAM_ERR_UNSUPPORTED;
+    if (par->precision == PAM_PREC_MIXED && (g.m_cap > kMixedMaxM || !mixed_solve_fits(g)))
+        return PAM_ERR_UNSUPPORTED;
     if (!d_K || !model_ok(model) || !d_workspace || n_levels < 0) return PAM_ERR_INVALID_ARG;
     Ws w = carve_workspace(g, d_workspace);
     if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
@@ -321,6 +324,7 @@ pam_status pam_refine(const pam_problem *prob, const pam_params *par, const pam_
     PAM_CUDA_TRY(cudaGetLastError());
     int32_t hs[8];
     if ((st = read_status(w, s, hs)) != PAM_OK) return st;
+    if (hs[kStTimeout]) return PAM_ERR_TIMEOUT;
     return hs[kStUncertified] ? PAM_ERR_NOT_CONVERGED : PAM_OK;
 }
 
@@ -355,9 +359,16 @@ pam_status pam_gram(const pam_problem *prob, const pam_params *par, const pam_pl
     return PAM_OK;
 }
 
+pam_status pam_eval_workspace_size(const pam_plan *plan, int64_t n_pts, size_t *bytes) {
+    if (!plan || !bytes || n_pts < 0 || plan->n_subdomains < 1) return PAM_ERR_INVALID_ARG;
+    if (n_pts > (int64_t)INT32_MAX) return PAM_ERR_UNSUPPORTED;
+    *bytes = eval_workspace_bytes(plan->n_subdomains, n_pts);
+    return PAM_OK;
+}
+
 pam_status pam_eval(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
                     const double *d_pts, int64_t n_pts, double *d_out, int log_space, int precision,
-                    void *stream) {
+                    void *d_workspace, size_t workspace_bytes, void *stream) {
     Geo g;
     pam_status st;
     if (!make_geo(prob, nullptr, &g, nullptr, &st)) return st;
@@ -367,18 +378,19 @@ pam_status pam_eval(const pam_problem *prob, const pam_plan *plan, const pam_mod
     g.n_max = plan->max_patch_cells;
     if (n_pts < 0 || !model_ok(model)) return PAM_ERR_INVALID_ARG;
     if (precision != PAM_PREC_FP64 && precision != PAM_PREC_MIXED) return PAM_ERR_INVALID_ARG;
-    if (precision == PAM_PREC_MIXED) return PAM_ERR_UNSUPPORTED;
+    if (n_pts > (int64_t)INT32_MAX) return PAM_ERR_UNSUPPORTED;
     if (n_pts == 0) return PAM_OK;
-    if (!d_pts || !d_out) return PAM_ERR_INVALID_ARG;
+    if (!d_pts || !d_out || !d_workspace) return PAM_ERR_INVALID_ARG;
+    if (workspace_bytes < eval_workspace_bytes(g.S, n_pts)) return PAM_ERR_WORKSPACE;
     launch_eval(g, model->boxes, model->centres, model->beta, model->info, d_pts, n_pts, d_out,
-                log_space, precision, (cudaStream_t)stream);
+                log_space, precision, d_workspace, (cudaStream_t)stream);
     PAM_CUDA_TRY(cudaGetLastError());
     return PAM_OK;
 }
 
 pam_status pam_errors(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
-                      const double *d_K, double *d_err, void *d_workspace, size_t workspace_bytes,
-                      void *stream) {
+                      const double *d_K, double *d_err, int precision, void *d_workspace,
+                      size_t workspace_bytes, void *stream) {
     Geo g;
     pam_status st;
     if (!make_geo(prob, nullptr, &g, nullptr, &st)) return st;
@@ -387,12 +399,11 @@ pam_status pam_errors(const pam_problem *prob, const pam_plan *plan, const pam_m
     g.m_cap = plan->m_cap;
     g.n_max = plan->max_patch_cells;
     if (!model_ok(model) || !d_K || !d_err || !d_workspace) return PAM_ERR_INVALID_ARG;
+    if (precision != PAM_PREC_FP64 && precision != PAM_PREC_MIXED) return PAM_ERR_INVALID_ARG;
     Ws w = carve_workspace(g, d_workspace);
-    if (workspace_bytes < (size_t)((char *)w.err_part - (char *)d_workspace) +
-                              (size_t)kErrBlocks * 4 * sizeof(double))
-        return PAM_ERR_WORKSPACE;
-    launch_errors(g, model->boxes, model->centres, model->beta, model->info, d_K, d_err, w,
-                  (cudaStream_t)stream);
+    if (workspace_bytes < (size_t)((char *)w.y - (char *)d_workspace)) return PAM_ERR_WORKSPACE;
+    launch_errors(g, model->boxes, model->centres, model->beta, model->info, d_K, d_err, precision,
+                  w, (cudaStream_t)stream);
     PAM_CUDA_TRY(cudaGetLastError());
     return PAM_OK;
 }

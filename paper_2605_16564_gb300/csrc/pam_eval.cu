@@ -1,0 +1,353 @@
+// pam_eval.cu -- Step 4 (global reconstruction): evaluation of the piecewise
+// surrogate K*(x) = exp(sum_m beta_m w_m(x)) at arbitrary points, and the
+// error measures over the source cells.
+//
+// Evaluation buckets the points by owner subdomain first (owner of each
+// point, warp-aggregated counts, an exclusive scan, a scatter of point
+// indices), then one block per owner stages that owner's dictionary in
+// shared memory and sweeps its points. Results are written by point index,
+// so the (non-deterministic) order inside a bucket does not matter.
+//
+// fp64 form: two passes per point (maximum logit, then the shifted sum).
+// fp32 form: one pass without a shift. Every point of a core lies within
+//   half a lattice spacing (per axis) of an initial lattice centre of width
+//   = the largest spacing, so the largest Gaussian is at least
+//   exp(-d/8) >= 0.68: the unshifted sum neither underflows nor overflows
+//   (a guard recomputes with the shift if it ever falls below 2^-100).
+#include <cfloat>
+#include <cmath>
+
+#include "pam_internal.cuh"
+#include "pam_tc.cuh"
+
+namespace pam {
+
+struct EvalWs {
+    int32_t *owner, *rank, *perm, *count, *start;
+    size_t bytes;
+};
+
+static size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+EvalWs carve_eval_workspace(int S, int64_t n, void *base) {
+    EvalWs e;
+    size_t off = 0;
+    auto take = [&](size_t bytes) -> int32_t * {
+        int32_t *p = base ? (int32_t *)((char *)base + off) : nullptr;
+        off = align256(off + bytes);
+        return p;
+    };
+    e.owner = take((size_t)n * 4);
+    e.rank = take((size_t)n * 4);
+    e.perm = take((size_t)n * 4);
+    e.count = take((size_t)S * 4);
+    e.start = take((size_t)(S + 1) * 4);
+    e.bytes = off;
+    return e;
+}
+
+size_t eval_workspace_bytes(int S, int64_t n_pts) { return carve_eval_workspace(S, n_pts, nullptr).bytes; }
+
+__global__ void k_eval_owner(Geo g, const double *pts, int64_t n, int32_t *owner, int32_t *rank,
+                             int32_t *count, double *out) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s = -2;  // lanes past the end take a key no real owner has
+    if (p < n) {
+        double x[3] = {0, 0, 0};
+        for (int a = 0; a < g.dim; ++a) x[a] = pts[p * g.dim + a];
+        s = owner_of_point(g, x);
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, s);
+    const int lane = threadIdx.x & 31;
+    const int leader = __ffs(peers) - 1;
+    int base = 0;
+    if (lane == leader && s >= 0) base = atomicAdd(&count[s], __popc(peers));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (p < n) {
+        owner[p] = s;
+        rank[p] = base + __popc(peers & ((1u << lane) - 1u));
+        if (s < 0) out[p] = nan("");
+    }
+}
+
+// Exclusive scan of count[0..S) into start[0..S] by one block of 1024.
+__global__ void __launch_bounds__(1024) k_eval_scan(const int32_t *count, int32_t *start, int S) {
+    __shared__ int wsum[32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int per = (S + 1023) / 1024;
+    const int b = tid * per, e = min(S, b + per);
+    int local = 0;
+    for (int i = b; i < e; ++i) local += count[i];
+    int v = local;
+    for (int o = 1; o < 32; o <<= 1) {
+        int u = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += u;
+    }
+    if (lane == 31) wsum[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        int t = wsum[lane];
+        for (int o = 1; o < 32; o <<= 1) {
+            int u = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += u;
+        }
+        wsum[lane] = t;
+    }
+    __syncthreads();
+    int run = v - local + (warp > 0 ? wsum[warp - 1] : 0);
+    for (int i = b; i < e; ++i) {
+        start[i] = run;
+        run += count[i];
+    }
+    if (tid == 1023) start[S] = run;
+}
+
+__global__ void k_eval_scatter(const int32_t *owner, const int32_t *rank, const int32_t *start,
+                               int32_t *perm, int64_t n) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const int s = owner[p];
+    if (s >= 0) perm[start[s] + rank[p]] = (int32_t)p;
+}
+
+// ---------------------------------------------------------------- fp64 ------
+__device__ __forceinline__ double shepard_f64_smem(const dvec4 *sc, const double *sb, int M,
+                                                   const double x[3]) {
+    double lmax = -INFINITY;
+    for (int m = 0; m < M; ++m) {
+        const dvec4 c = sc[m];
+        double d0 = x[0] - c.x, d1 = x[1] - c.y, d2 = x[2] - c.z;
+        lmax = fmax(lmax, (d0 * d0 + d1 * d1 + d2 * d2) * c.w);
+    }
+    double num = 0.0, den = 0.0;
+    for (int m = 0; m < M; ++m) {
+        const dvec4 c = sc[m];
+        double d0 = x[0] - c.x, d1 = x[1] - c.y, d2 = x[2] - c.z;
+        double e = exp((d0 * d0 + d1 * d1 + d2 * d2) * c.w - lmax);
+        num += sb[m] * e;
+        den += e;
+    }
+    return num / den;
+}
+
+// Dictionary of subdomain s in shared memory: (c, -1/(2 sigma^2)) and beta.
+__device__ void stage_f64(const Geo &g, const double *centres, const double *beta, int s, int M,
+                          dvec4 *sc, double *sb) {
+    const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        dvec4 c = cg[m];
+        c.w = -1.0 / (2.0 * c.w * c.w);
+        sc[m] = c;
+        sb[m] = beta[(size_t)s * g.m_cap + m];
+    }
+    __syncthreads();
+}
+
+__global__ void k_eval_bucket_f64(Geo g, const double *centres, const double *beta,
+                                  const int32_t *info, const double *pts, const int32_t *perm,
+                                  const int32_t *start, double *out, int log_space) {
+    const int s = blockIdx.x;
+    const int b = start[s], e = start[s + 1];
+    if (b == e) return;
+    const int M = info[s * kInfoN + PAM_INFO_M];
+    extern __shared__ uint8_t smb[];
+    dvec4 *sc = reinterpret_cast<dvec4 *>(smb);
+    double *sb = reinterpret_cast<double *>(sc + g.m_cap);
+    stage_f64(g, centres, beta, s, M, sc, sb);
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+        const int p = perm[i];
+        double x[3] = {0, 0, 0};
+        for (int a = 0; a < g.dim; ++a) x[a] = pts[(int64_t)p * g.dim + a];
+        const double v = shepard_f64_smem(sc, sb, M, x);
+        out[p] = log_space ? v : exp(v);
+    }
+}
+
+// ---------------------------------------------------------------- fp32 ------
+__device__ __forceinline__ float4 local_centre_e(const dvec4 &c, const double o[3]) {
+    float4 r;
+    r.x = (float)(c.x - o[0]);
+    r.y = (float)(c.y - o[1]);
+    r.z = (float)(c.z - o[2]);
+    r.w = (float)(-1.4426950408889634 / (2.0 * c.w * c.w));
+    return r;
+}
+
+__device__ __forceinline__ float logit2_e(const float4 &c, float x, float y, float z) {
+    float dx = x - c.x, dy = y - c.y, dz = z - c.z;
+    return c.w * fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+__device__ __forceinline__ float shepard_f32_smem(const float4 *sc, const float *sb, int M,
+                                                  float x, float y, float z) {
+    float num = 0.f, den = 0.f;
+    for (int m = 0; m < M; ++m) {
+        const float e = tc::ex2(logit2_e(sc[m], x, y, z));
+        num = fmaf(sb[m], e, num);
+        den += e;
+    }
+    if (!(den > 7.9e-31f)) {  // 2^-100: recompute with the maximum logit subtracted
+        float lmax = -INFINITY;
+        for (int m = 0; m < M; ++m) lmax = fmaxf(lmax, logit2_e(sc[m], x, y, z));
+        num = 0.f;
+        den = 0.f;
+        for (int m = 0; m < M; ++m) {
+            const float e = tc::ex2(logit2_e(sc[m], x, y, z) - lmax);
+            num = fmaf(sb[m], e, num);
+            den += e;
+        }
+    }
+    return num / den;
+}
+
+__device__ void stage_f32(const Geo &g, const int32_t *boxes, const double *centres,
+                          const double *beta, int s, int M, float4 *sc, float *sb, double o[3]) {
+    const int32_t *box = boxes + s * 12;
+    for (int a = 0; a < 3; ++a) o[a] = a < g.dim ? (double)box[6 + a] * g.h : 0.0;
+    const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        sc[m] = local_centre_e(cg[m], o);
+        sb[m] = (float)beta[(size_t)s * g.m_cap + m];
+    }
+    __syncthreads();
+}
+
+__global__ void k_eval_bucket_f32(Geo g, const int32_t *boxes, const double *centres,
+                                  const double *beta, const int32_t *info, const double *pts,
+                                  const int32_t *perm, const int32_t *start, double *out,
+                                  int log_space) {
+    const int s = blockIdx.x;
+    const int b = start[s], e = start[s + 1];
+    if (b == e) return;
+    const int M = info[s * kInfoN + PAM_INFO_M];
+    extern __shared__ uint8_t smb[];
+    float4 *sc = reinterpret_cast<float4 *>(smb);
+    float *sb = reinterpret_cast<float *>(sc + g.m_cap);
+    double o[3];
+    stage_f32(g, boxes, centres, beta, s, M, sc, sb, o);
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+        const int p = perm[i];
+        double x[3] = {0, 0, 0};
+        for (int a = 0; a < g.dim; ++a) x[a] = pts[(int64_t)p * g.dim + a];
+        const float v = shepard_f32_smem(sc, sb, M, (float)(x[0] - o[0]), (float)(x[1] - o[1]),
+                                         (float)(x[2] - o[2]));
+        out[p] = log_space ? (double)v : exp((double)v);
+    }
+}
+
+void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
+                 const int32_t *info, const double *pts, int64_t n_pts, double *out, int log_space,
+                 int precision, void *ws, cudaStream_t st) {
+    PhaseScope ps(kPhEval, st);
+    EvalWs e = carve_eval_workspace(g.S, n_pts, ws);
+    cudaMemsetAsync(e.count, 0, (size_t)g.S * sizeof(int32_t), st);
+    const unsigned nb = (unsigned)((n_pts + 255) / 256);
+    k_eval_owner<<<nb, 256, 0, st>>>(g, pts, n_pts, e.owner, e.rank, e.count, out);
+    k_eval_scan<<<1, 1024, 0, st>>>(e.count, e.start, g.S);
+    k_eval_scatter<<<nb, 256, 0, st>>>(e.owner, e.rank, e.start, e.perm, n_pts);
+    if (precision == PAM_PREC_MIXED) {
+        size_t sm = (size_t)g.m_cap * (sizeof(float4) + sizeof(float));
+        k_eval_bucket_f32<<<g.S, 256, sm, st>>>(g, boxes, centres, beta, info, pts, e.perm, e.start,
+                                                out, log_space);
+    } else {
+        size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));
+        cudaFuncSetAttribute(k_eval_bucket_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_eval_bucket_f64<<<g.S, 256, sm, st>>>(g, centres, beta, info, pts, e.perm, e.start, out,
+                                                log_space);
+    }
+    count_launches(4);
+}
+
+// --------------------------------------------------------------------------
+// Errors over the source cells: one block per owner sweeps its core cells
+// (each cell measured with its owner's surrogate at the centroid) and writes
+// seven fp64 partial sums; one thread combines the S rows in order.
+// --------------------------------------------------------------------------
+constexpr int kErrThreads = 256;
+
+template <bool F32>
+__global__ void __launch_bounds__(kErrThreads) k_errors_owner(Geo g, const int32_t *boxes,
+                                                              const double *centres,
+                                                              const double *beta,
+                                                              const int32_t *info, const double *K,
+                                                              double *part) {
+    const int s = blockIdx.x;
+    const int M = info[s * kInfoN + PAM_INFO_M];
+    const int32_t *box = boxes + s * 12;
+    extern __shared__ uint8_t smb[];
+    dvec4 *sc64 = reinterpret_cast<dvec4 *>(smb);
+    double *sb64 = reinterpret_cast<double *>(sc64 + g.m_cap);
+    float4 *sc32 = reinterpret_cast<float4 *>(smb);
+    float *sb32 = reinterpret_cast<float *>(sc32 + g.m_cap);
+    double o[3];
+    if (F32) stage_f32(g, boxes, centres, beta, s, M, sc32, sb32, o);
+    else stage_f64(g, centres, beta, s, M, sc64, sb64);
+    const int w0 = box[3] - box[0], w1 = box[4] - box[1], w2 = box[5] - box[2];
+    const int cnt = w0 * w1 * w2;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+        const int i = box[0] + t % w0, j = box[1] + (t / w0) % w1, k = box[2] + t / (w0 * w1);
+        const int idx[3] = {i, j, k};
+        double x[3] = {0, 0, 0};
+        for (int a = 0; a < g.dim; ++a) x[a] = __dmul_rn((double)idx[a] + 0.5, g.h);
+        double v;
+        if (F32)
+            v = (double)shepard_f32_smem(sc32, sb32, M, (float)(x[0] - o[0]), (float)(x[1] - o[1]),
+                                         (float)(x[2] - o[2]));
+        else
+            v = shepard_f64_smem(sc64, sb64, M, x);
+        const int64_t gi = (int64_t)i + (int64_t)g.n[0] * ((int64_t)j + (int64_t)g.n[1] * k);
+        const double kk = K[gi], ks = exp(v), lk = log(kk);
+        acc[0] += fabs(kk - ks);
+        acc[1] += fabs(kk);
+        acc[2] += (kk - ks) * (kk - ks);
+        acc[3] += kk * kk;
+        acc[4] += fabs(lk - v);
+        acc[5] += fabs(lk);
+        acc[6] = fmax(acc[6], fabs(lk - v));
+    }
+    __shared__ double red[kErrThreads / 32][7];
+    for (int q = 0; q < 7; ++q) {
+        const double v = (q == 6) ? warp_max(acc[q]) : warp_sum(acc[q]);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int q = threadIdx.x;
+        double v = 0.0;
+        if (q < 7)
+            for (int wdx = 0; wdx < kErrThreads / 32; ++wdx)
+                v = (q == 6) ? fmax(v, red[wdx][q]) : v + red[wdx][q];
+        part[(size_t)s * 8 + q] = v;
+    }
+}
+
+__global__ void k_errors_combine(const double *part, int rows, double *err) {
+    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+    double a[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int r = 0; r < rows; ++r)
+        for (int q = 0; q < 7; ++q)
+            a[q] = (q == 6) ? fmax(a[q], part[(size_t)r * 8 + q]) : a[q] + part[(size_t)r * 8 + q];
+    err[0] = a[0] / a[1];
+    err[1] = sqrt(a[2] / a[3]);
+    err[2] = a[5] > 0.0 ? a[4] / a[5] : a[4];
+    err[3] = a[6] / log(10.0);
+}
+
+void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
+                   const int32_t *info, const double *K, double *err, int precision, const Ws &w,
+                   cudaStream_t st) {
+    PhaseScope ps(kPhErrors, st);
+    if (precision == PAM_PREC_MIXED) {
+        size_t sm = (size_t)g.m_cap * (sizeof(float4) + sizeof(float));
+        k_errors_owner<true><<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, w.err_part);
+    } else {
+        size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));
+        cudaFuncSetAttribute(k_errors_owner<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_errors_owner<false><<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, w.err_part);
+    }
+    k_errors_combine<<<1, 32, 0, st>>>(w.err_part, g.S, err);
+    count_launches(2);
+}
+
+}  // namespace pam

@@ -689,136 +689,6 @@ void launch_residual_f64(const Geo &g, const double *beta, const int32_t *info, 
 }
 
 // --------------------------------------------------------------------------
-// Step 4: evaluation of the piecewise surrogate, and the error measures.
-// --------------------------------------------------------------------------
-// Shepard value sum_m beta_m w_m(x) of subdomain s at x (two passes: the
-// maximum logit, then the normalised sum), binary64.
-__device__ double shepard_value_f64(const Geo &g, const double *centres, const double *beta,
-                                    int s, int M, const double x[3]) {
-    const dvec4 *cs = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
-    const double *bs = beta + (size_t)s * g.m_cap;
-    double lmax = -INFINITY;
-    for (int m = 0; m < M; ++m) {
-        dvec4 c = cs[m];
-        double d0 = x[0] - c.x, d1 = x[1] - c.y, d2 = x[2] - c.z;
-        double l = -(d0 * d0 + d1 * d1 + d2 * d2) / (2.0 * c.w * c.w);
-        lmax = fmax(lmax, l);
-    }
-    double num = 0.0, den = 0.0;
-    for (int m = 0; m < M; ++m) {
-        dvec4 c = cs[m];
-        double d0 = x[0] - c.x, d1 = x[1] - c.y, d2 = x[2] - c.z;
-        double e = exp(-(d0 * d0 + d1 * d1 + d2 * d2) / (2.0 * c.w * c.w) - lmax);
-        num += bs[m] * e;
-        den += e;
-    }
-    return num / den;
-}
-
-__global__ void k_eval_f64(Geo g, const double *centres, const double *beta, const int32_t *info,
-                           const double *pts, int64_t n_pts, double *out, int log_space) {
-    int64_t q = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (q >= n_pts) return;
-    double x[3] = {0, 0, 0};
-    for (int a = 0; a < g.dim; ++a) x[a] = pts[q * g.dim + a];
-    int s = owner_of_point(g, x);
-    if (s < 0) { out[q] = nan(""); return; }
-    int M = info[s * kInfoN + PAM_INFO_M];
-    double v = shepard_value_f64(g, centres, beta, s, M, x);
-    out[q] = log_space ? v : exp(v);
-}
-
-void launch_eval_mixed(const Geo &g, const int32_t *boxes, const double *centres,
-                       const double *beta, const int32_t *info, const double *pts, int64_t n_pts,
-                       double *out, int log_space, cudaStream_t st);
-
-void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
-                 const int32_t *info, const double *pts, int64_t n_pts, double *out, int log_space,
-                 int precision, cudaStream_t st) {
-    if (precision == PAM_PREC_MIXED) {
-        launch_eval_mixed(g, boxes, centres, beta, info, pts, n_pts, out, log_space, st);
-        return;
-    }
-    int64_t blocks = (n_pts + 127) / 128;
-    PhaseScope ps(kPhEval, st);
-    k_eval_f64<<<(unsigned)blocks, 128, 0, st>>>(g, centres, beta, info, pts, n_pts, out, log_space);
-    count_launches(1);
-}
-
-// Per-block partial sums over the grid cells, in a fixed order:
-// [0] sum |K - K*|, [1] sum |K|, [2] sum (K - K*)^2, [3] sum K^2 -> err_part
-// [4] sum |ln K - ln K*|, [5] sum |ln K|, [6] max |ln K - ln K*|
-constexpr int kErrThreads = 256;
-__global__ void __launch_bounds__(kErrThreads) k_errors_partial(Geo g, const double *centres,
-                                                                const double *beta,
-                                                                const int32_t *info,
-                                                                const double *K, double *part) {
-    const int64_t total = (int64_t)g.n[0] * g.n[1] * g.n[2];
-    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < total;
-         c += (int64_t)gridDim.x * blockDim.x) {
-        int64_t i = c % g.n[0], j = (c / g.n[0]) % g.n[1], k = c / ((int64_t)g.n[0] * g.n[1]);
-        int idx[3] = {(int)i, (int)j, (int)k};
-        double x[3] = {0, 0, 0};
-        int js[3] = {0, 0, 0};
-        for (int a = 0; a < g.dim; ++a) {
-            x[a] = __dmul_rn((double)idx[a] + 0.5, g.h);
-            js[a] = core_of(idx[a], g.n[a], g.p[a]);
-        }
-        int s = js[0] + g.p[0] * (js[1] + g.p[1] * js[2]);
-        int M = info[s * kInfoN + PAM_INFO_M];
-        double v = shepard_value_f64(g, centres, beta, s, M, x);
-        double kk = K[c], ks = exp(v), lk = log(kk);
-        acc[0] += fabs(kk - ks);
-        acc[1] += fabs(kk);
-        acc[2] += (kk - ks) * (kk - ks);
-        acc[3] += kk * kk;
-        acc[4] += fabs(lk - v);
-        acc[5] += fabs(lk);
-        acc[6] = fmax(acc[6], fabs(lk - v));
-    }
-    __shared__ double red[kErrThreads / 32][7];
-    for (int q = 0; q < 7; ++q) {
-        double v = acc[q];
-        if (q == 6) v = warp_max(v);
-        else v = warp_sum(v);
-        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = v;
-    }
-    __syncthreads();
-    if (threadIdx.x < 7) {
-        int q = threadIdx.x;
-        double v = 0.0;
-        for (int wdx = 0; wdx < kErrThreads / 32; ++wdx)
-            v = (q == 6) ? fmax(v, red[wdx][q]) : v + red[wdx][q];
-        part[(size_t)blockIdx.x * 8 + q] = v;
-    }
-}
-
-__global__ void k_errors_final(const double *part, int nblocks, double *err) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
-    double a[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int b = 0; b < nblocks; ++b)
-        for (int q = 0; q < 7; ++q)
-            a[q] = (q == 6) ? fmax(a[q], part[(size_t)b * 8 + q]) : a[q] + part[(size_t)b * 8 + q];
-    err[0] = a[0] / a[1];
-    err[1] = sqrt(a[2] / a[3]);
-    err[2] = a[5] > 0.0 ? a[4] / a[5] : a[4];
-    err[3] = a[6] / log(10.0);
-}
-
-void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
-                   const int32_t *info, const double *K, double *err, const Ws &w,
-                   cudaStream_t st) {
-    (void)boxes;
-    int nb = kErrBlocks / 2;  // err_part holds kErrBlocks*4 doubles = nb rows of 8
-    PhaseScope ps(kPhErrors, st);
-    k_errors_partial<<<nb, kErrThreads, 0, st>>>(g, centres, beta, info, K, w.err_part);
-    count_launches(1);
-    k_errors_final<<<1, 32, 0, st>>>(w.err_part, nb, err);
-    count_launches(1);
-}
-
-// --------------------------------------------------------------------------
 // One refinement round: residuals of the current fit, then mark + enrich.
 // --------------------------------------------------------------------------
 void launch_residual_mixed(const Geo &g, const int32_t *boxes, const double *centres,

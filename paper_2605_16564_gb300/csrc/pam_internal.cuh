@@ -83,9 +83,12 @@ void launch_refine_round(const Geo &g, const Par &p, int precision, const int32_
                          double *centres, double *beta, int32_t *info, const Ws &w, cudaStream_t st);
 void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
                  const int32_t *info, const double *pts, int64_t n_pts, double *out, int log_space,
-                 int precision, cudaStream_t st);
+                 int precision, void *ws, cudaStream_t st);
+size_t eval_workspace_bytes(int S, int64_t n_pts);
 void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
-                   const int32_t *info, const double *K, double *err, const Ws &w, cudaStream_t st);
+                   const int32_t *info, const double *K, double *err, int precision, const Ws &w,
+                   cudaStream_t st);
+bool mixed_solve_fits(const Geo &g);
 
 // Kernel families timed by the optional event profiler (pam_timing_*).
 enum Phase {

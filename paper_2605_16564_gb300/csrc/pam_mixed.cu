@@ -338,11 +338,341 @@ void launch_copy_gram_f32(const Geo &g, const int32_t *info, const Ws &w, double
     count_launches(1);
 }
 
-void launch_solve_level_mixed(const Geo &, const Par &, const int32_t *, const double *, double *,
-                              int32_t *, const Ws &, cudaStream_t) {}
+// --------------------------------------------------------------------------
+// Elastic Net (Eq. (2)) in the mixed form, one block per subdomain.
+// Stage 1: primal-dual active-set iterations on the tensor-core Gram G~
+//   (fp32): for a support guess S with signs s, solve
+//   (G~_SS + lambda2 I) x_S = b_S - lambda1 s_S by fp32 Cholesky and correct
+//   the guess until sign(x_S) = s and |b_j - G~_jS x_S| <= lambda1 off S.
+// Stage 2: iterative refinement against the exact gradient. With W
+//   regenerated from the row statistics, e = y - W x and c = W^T e are
+//   recomputed (fp32 exps, fp32 sums), the stationarity residual
+//   r_S = c_S - lambda2 x_S - lambda1 s_S is corrected through the same
+//   factor, x_S += (G~_SS + lambda2 I)^{-1} r_S, and the support is updated
+//   from the exact optimality conditions (entries whose sign flips leave S,
+//   violators |c_j| > lambda1 join it). It contracts by about
+//   ||(G~ + lambda2 I)^{-1} (G - G~)|| per step (~1e-2 here).
+// Finally the residual indicators R_T = |T| (exp(W x)_T - K_T)^2 of the
+// final coefficients are written (fp64 for the K-space residual), so the
+// refinement round needs no separate residual pass.
+// --------------------------------------------------------------------------
+constexpr int kMxThreads = 256;
+constexpr int kMxFactorBytes = 64 * 1024;
+constexpr int kMxMaxRefine = 6;
+
+struct MxShared {
+    int cnt, bad, viol, flag, changed;
+    float inv_piv, dmax, xmax;
+};
+
+__device__ void mx_compact(const int *sg, int M, int *idx, int *cnt) {
+    if (threadIdx.x < 32) {
+        int lane = threadIdx.x, base = 0;
+        for (int j0 = 0; j0 < M; j0 += 32) {
+            int j = j0 + lane;
+            bool on = j < M && sg[j] != 0;
+            unsigned bal = __ballot_sync(0xffffffffu, on);
+            if (on) idx[base + __popc(bal & ((1u << lane) - 1u))] = j;
+            base += __popc(bal);
+        }
+        if (lane == 0) *cnt = base;
+    }
+    __syncthreads();
+}
+
+__device__ __forceinline__ int tri_i(int p, int q) { return p * (p + 1) / 2 + q; }
+
+__device__ void mx_cholesky(float *A, int s, int *flag, float *inv_piv) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    for (int k = 0; k < s; ++k) {
+        if (tid == 0) {
+            float d = A[tri_i(k, k)];
+            if (!(d > 0.f)) { *flag = 1; d = 1.f; }
+            float l = sqrtf(d);
+            A[tri_i(k, k)] = l;
+            *inv_piv = 1.f / l;
+        }
+        __syncthreads();
+        const float iv = *inv_piv;
+        for (int i = k + 1 + tid; i < s; i += blockDim.x) A[tri_i(i, k)] *= iv;
+        __syncthreads();
+        for (int i = k + 1 + warp; i < s; i += nw) {
+            const float lik = A[tri_i(i, k)];
+            float *row = A + tri_i(i, 0);
+            for (int j = k + 1 + lane; j <= i; j += 32) row[j] = fmaf(-lik, A[tri_i(j, k)], row[j]);
+        }
+        __syncthreads();
+    }
+}
+
+__device__ void mx_chol_solve(const float *A, int s, float *r) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x;
+        for (int q = 0; q < s; ++q) {
+            float v = r[q] / A[tri_i(q, q)];
+            __syncwarp();
+            if (lane == 0) r[q] = v;
+            for (int p = q + 1 + lane; p < s; p += 32) r[p] = fmaf(-A[tri_i(p, q)], v, r[p]);
+            __syncwarp();
+        }
+        for (int q = s - 1; q >= 0; --q) {
+            float v = r[q] / A[tri_i(q, q)];
+            __syncwarp();
+            if (lane == 0) r[q] = v;
+            const float *row = A + tri_i(q, 0);
+            for (int p = lane; p < q; p += 32) r[p] = fmaf(-row[p], v, r[p]);
+            __syncwarp();
+        }
+    }
+    __syncthreads();
+}
+
+__global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const int32_t *boxes,
+                                                            const double *centres, double *beta,
+                                                            int32_t *info, Ws w) {
+    const int s = blockIdx.x;
+    int32_t *inf = info + s * kInfoN;
+    if (inf[PAM_INFO_STOPPED]) return;
+    const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS], mc = g.m_cap;
+    const float lam1 = (float)((double)N * p.lam1_hat), lam2 = (float)((double)N * p.lam2_hat);
+    const float tol_pdas = lam1 * (1.0f + 1e-6f);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int32_t *box = boxes + s * 12;
+
+    extern __shared__ __align__(16) uint8_t sm[];
+    float *x = reinterpret_cast<float *>(sm);     // [mc]
+    float *gr = x + mc;                           // [mc] b - G~ x (stage 1), exact c (stage 2)
+    float *bv = gr + mc;                          // [mc]
+    float *rhs = bv + mc;                         // [mc]
+    int *sg = reinterpret_cast<int *>(rhs + mc);  // [mc]
+    int *idx = sg + mc;                           // [mc]
+    float4 *sc = reinterpret_cast<float4 *>(idx + mc);      // [mc] local centres
+    float4 *cell = sc + mc;                                 // [n_max] (x, y, z, rowmax)
+    float *cinv = reinterpret_cast<float *>(cell + g.n_max);// [n_max]
+    float *ce = cinv + g.n_max;                             // [n_max] y, then e = y - W x
+    float *Asm = ce + g.n_max;                              // packed factor
+    __shared__ MxShared sh;
+
+    const float *G = w.Gf + (size_t)s * mc * mc;
+    const float *rowmax = w.rowmax + (size_t)s * g.n_max;
+    const float *rowinv = w.rowinv + (size_t)s * g.n_max;
+    double o[3];
+    patch_origin(g, box, o);
+    const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * mc;
+    for (int j = tid; j < mc; j += blockDim.x) {
+        float b0 = j < M ? (float)beta[(size_t)s * mc + j] : 0.f;
+        x[j] = b0;
+        bv[j] = j < M ? (float)w.b[(size_t)s * mc + j] : 0.f;
+        sg[j] = (j < M) ? ((b0 > 0.f) - (b0 < 0.f)) : 0;
+        if (j < M) sc[j] = local_centre(cg[j], o);
+    }
+    for (int t = tid; t < N; t += blockDim.x) {
+        float xl[3];
+        local_cell(g, box, t, xl);
+        cell[t] = make_float4(xl[0], xl[1], xl[2], rowmax[t]);
+        cinv[t] = rowinv[t];
+    }
+    if (tid == 0) sh.flag = 0;
+    __syncthreads();
+
+    // ---------------- stage 1: active-set iterations on G~ ----------------
+    int it = 0, scnt = 0, ok1 = 0;
+    float *A = Asm;
+    for (; it < p.max_iters; ++it) {
+        mx_compact(sg, M, idx, &sh.cnt);
+        scnt = sh.cnt;
+        A = (tri_i(scnt, 0) * 4 <= kMxFactorBytes) ? Asm
+            : reinterpret_cast<float *>(w.L + (size_t)s * ((size_t)mc * (mc + 1) / 2));
+        for (int pp = warp; pp < scnt; pp += nw) {
+            const float *Gr = G + (size_t)idx[pp] * mc;
+            for (int q = lane; q <= pp; q += 32) A[tri_i(pp, q)] = Gr[idx[q]] + (q == pp ? lam2 : 0.f);
+            if (lane == 0) rhs[pp] = bv[idx[pp]] - lam1 * (float)sg[idx[pp]];
+        }
+        __syncthreads();
+        mx_cholesky(A, scnt, &sh.flag, &sh.inv_piv);
+        if (sh.flag) break;
+        mx_chol_solve(A, scnt, rhs);
+        for (int j = tid; j < M; j += blockDim.x) x[j] = 0.f;
+        __syncthreads();
+        for (int pp = tid; pp < scnt; pp += blockDim.x) x[idx[pp]] = rhs[pp];
+        __syncthreads();
+        for (int j = warp; j < M; j += nw) {
+            const float *Gr = G + (size_t)j * mc;
+            float acc = 0.f;
+            for (int pp = lane; pp < scnt; pp += 32) acc = fmaf(Gr[idx[pp]], rhs[pp], acc);
+            acc = warp_sumf(acc);
+            if (lane == 0) gr[j] = bv[j] - acc;
+        }
+        if (tid == 0) { sh.bad = 0; sh.viol = 0; }
+        __syncthreads();
+        int mb = 0, mv = 0;
+        for (int j = tid; j < M; j += blockDim.x) {
+            if (sg[j] != 0) mb += !(x[j] * (float)sg[j] > 0.f);
+            else mv += fabsf(gr[j]) > tol_pdas;
+        }
+        if (mb) atomicAdd(&sh.bad, mb);
+        if (mv) atomicAdd(&sh.viol, mv);
+        __syncthreads();
+        if (sh.bad == 0 && sh.viol == 0) { ok1 = 1; break; }
+        const bool single = it >= 16;
+        if (single && sh.bad == 0) {
+            if (tid == 0) {
+                float best = -1.f;
+                int bj = -1;
+                for (int j = 0; j < M; ++j)
+                    if (sg[j] == 0 && fabsf(gr[j]) > tol_pdas && fabsf(gr[j]) > best) { best = fabsf(gr[j]); bj = j; }
+                if (bj >= 0) sg[bj] = gr[bj] > 0.f ? 1 : -1;
+            }
+        } else {
+            for (int j = tid; j < M; j += blockDim.x) {
+                if (sg[j] != 0) {
+                    if (!(x[j] * (float)sg[j] > 0.f)) sg[j] = 0;
+                } else if (!single && fabsf(gr[j]) > tol_pdas) {
+                    sg[j] = gr[j] > 0.f ? 1 : -1;
+                }
+            }
+        }
+        __syncthreads();
+    }
+    (void)ok1;
+
+    // ---------------- stage 2: refinement with the exact gradient ---------
+    const float kkt_tol = lam1 * (1.0f + 1e-4f);
+    int certified = 0, refine_it = 0;
+    const double *yv = w.y + (size_t)s * g.n_max;
+    for (; refine_it < kMxMaxRefine && !sh.flag; ++refine_it) {
+        // e = y - W x over the patch (only the support contributes)
+        for (int t = tid; t < N; t += blockDim.x) {
+            const float4 cx = cell[t];
+            float acc = 0.f;
+            for (int pp = 0; pp < scnt; ++pp) {
+                const int m = idx[pp];
+                acc = fmaf(tc::ex2(logit2(sc[m], cx.x, cx.y, cx.z) - cx.w), x[m], acc);
+            }
+            ce[t] = (float)yv[t] - acc * cinv[t];
+        }
+        __syncthreads();
+        // c_j = sum_t W_tj e_t for every centre (exact gradient of the data term)
+        for (int j = tid; j < M; j += blockDim.x) {
+            const float4 cj = sc[j];
+            float acc = 0.f;
+            for (int t = 0; t < N; ++t) {
+                const float4 cx = cell[t];
+                acc = fmaf(tc::ex2(logit2(cj, cx.x, cx.y, cx.z) - cx.w) * cinv[t], ce[t], acc);
+            }
+            gr[j] = acc;
+        }
+        if (tid == 0) { sh.viol = 0; sh.changed = 0; sh.dmax = 0.f; sh.xmax = 0.f; }
+        __syncthreads();
+        // optimality off the support; violators join it
+        int mv = 0;
+        for (int j = tid; j < M; j += blockDim.x)
+            if (sg[j] == 0 && fabsf(gr[j]) > kkt_tol) { sg[j] = gr[j] > 0.f ? 1 : -1; x[j] = 0.f; ++mv; }
+        if (mv) { atomicAdd(&sh.viol, mv); atomicOr(&sh.changed, 1); }
+        __syncthreads();
+        if (sh.changed) {
+            mx_compact(sg, M, idx, &sh.cnt);
+            scnt = sh.cnt;
+            A = (tri_i(scnt, 0) * 4 <= kMxFactorBytes) ? Asm
+                : reinterpret_cast<float *>(w.L + (size_t)s * ((size_t)mc * (mc + 1) / 2));
+            for (int pp = warp; pp < scnt; pp += nw) {
+                const float *Gr = G + (size_t)idx[pp] * mc;
+                for (int q = lane; q <= pp; q += 32) A[tri_i(pp, q)] = Gr[idx[q]] + (q == pp ? lam2 : 0.f);
+            }
+            __syncthreads();
+            mx_cholesky(A, scnt, &sh.flag, &sh.inv_piv);
+            if (sh.flag) break;
+        }
+        // Newton correction on the support
+        for (int pp = tid; pp < scnt; pp += blockDim.x) {
+            const int m = idx[pp];
+            rhs[pp] = gr[m] - lam2 * x[m] - lam1 * (float)sg[m];
+        }
+        __syncthreads();
+        mx_chol_solve(A, scnt, rhs);
+        float dmax = 0.f, xmax = 0.f;
+        int dropped = 0;
+        for (int pp = tid; pp < scnt; pp += blockDim.x) {
+            const int m = idx[pp];
+            const float nx = x[m] + rhs[pp];
+            dmax = fmaxf(dmax, fabsf(rhs[pp]));
+            if (!(nx * (float)sg[m] > 0.f)) { sg[m] = 0; x[m] = 0.f; ++dropped; }
+            else { x[m] = nx; xmax = fmaxf(xmax, fabsf(nx)); }
+        }
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o2));
+            xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o2));
+            dropped += __shfl_xor_sync(0xffffffffu, dropped, o2);
+        }
+        if (lane == 0) {
+            atomicMax(reinterpret_cast<int *>(&sh.dmax), __float_as_int(dmax));
+            atomicMax(reinterpret_cast<int *>(&sh.xmax), __float_as_int(xmax));
+            if (dropped) atomicOr(&sh.changed, 2);
+        }
+        __syncthreads();
+        if (sh.changed & 2) {  // support shrank: recompact, refactor next round
+            mx_compact(sg, M, idx, &sh.cnt);
+            scnt = sh.cnt;
+            A = (tri_i(scnt, 0) * 4 <= kMxFactorBytes) ? Asm
+                : reinterpret_cast<float *>(w.L + (size_t)s * ((size_t)mc * (mc + 1) / 2));
+            for (int pp = warp; pp < scnt; pp += nw) {
+                const float *Gr = G + (size_t)idx[pp] * mc;
+                for (int q = lane; q <= pp; q += 32) A[tri_i(pp, q)] = Gr[idx[q]] + (q == pp ? lam2 : 0.f);
+            }
+            __syncthreads();
+            mx_cholesky(A, scnt, &sh.flag, &sh.inv_piv);
+            continue;
+        }
+        if (sh.viol == 0 && sh.dmax <= 1e-6f * fmaxf(sh.xmax, 1.f)) { certified = 1; ++refine_it; break; }
+    }
+
+    // final residual e = y - W x, and the indicators R_T (Eq. (4), midpoint)
+    for (int t = tid; t < N; t += blockDim.x) {
+        const float4 cx = cell[t];
+        float acc = 0.f;
+        for (int pp = 0; pp < scnt; ++pp) {
+            const int m = idx[pp];
+            acc = fmaf(tc::ex2(logit2(sc[m], cx.x, cx.y, cx.z) - cx.w), x[m], acc);
+        }
+        const double yhat = (double)(acc * cinv[t]);
+        const double kv = w.kv[(size_t)s * g.n_max + t];
+        const double e = exp(yhat) - kv;
+        w.R[(size_t)s * g.n_max + t] = g.vol * (e * e);
+    }
+    for (int j = tid; j < M; j += blockDim.x) beta[(size_t)s * mc + j] = (double)x[j];
+    if (tid == 0) {
+        int flags = inf[PAM_INFO_FLAGS] & ~(PAM_FLAG_NOT_CERTIFIED | PAM_FLAG_CHOLESKY);
+        if (!certified) {
+            flags |= PAM_FLAG_NOT_CERTIFIED;
+            atomicAdd(&w.status[kStUncertified], 1);
+        }
+        if (sh.flag) flags |= PAM_FLAG_CHOLESKY;
+        inf[PAM_INFO_FLAGS] = flags;
+        inf[PAM_INFO_SUPPORT] = scnt;
+        inf[PAM_INFO_ITERS] = it + refine_it;
+    }
+}
+
+static size_t solve_mixed_smem(const Geo &g) {
+    return (size_t)g.m_cap * (4 * sizeof(float) + 2 * sizeof(int) + sizeof(float4)) +
+           (size_t)g.n_max * (sizeof(float4) + 2 * sizeof(float)) + kMxFactorBytes + 64;
+}
+
+bool mixed_solve_fits(const Geo &g) { return solve_mixed_smem(g) <= 227 * 1024; }
+
+void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes,
+                              const double *centres, double *beta, int32_t *info, const Ws &w,
+                              cudaStream_t st) {
+    launch_stats_gram_tc(g, boxes, centres, info, w, st, 0);
+    size_t sm = solve_mixed_smem(g);
+    cudaFuncSetAttribute(k_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    PhaseScope ps(kPhSolve, st);
+    k_solve_mixed<<<g.S, kMxThreads, sm, st>>>(g, p, boxes, centres, beta, info, w);
+    count_launches(1);
+}
+
+// The mixed solve already wrote the indicators of its final coefficients.
 void launch_residual_mixed(const Geo &, const int32_t *, const double *, const double *,
                            const int32_t *, const Ws &, cudaStream_t) {}
-void launch_eval_mixed(const Geo &, const int32_t *, const double *, const double *,
-                       const int32_t *, const double *, int64_t, double *, int, cudaStream_t) {}
 
 }  // namespace pam

@@ -30,7 +30,8 @@ STATUS = {0: "PAM_OK", 1: "PAM_ERR_INVALID_ARG", 2: "PAM_ERR_NONPOSITIVE_K", 3: 
           7: "PAM_ERR_TIMEOUT"}
 
 EXPORTED = ["pam_version", "pam_status_string", "pam_plan_create", "pam_partition",
-            "pam_fit_subdomains", "pam_refine", "pam_gram", "pam_eval", "pam_errors"]
+            "pam_fit_subdomains", "pam_refine", "pam_gram", "pam_eval_workspace_size", "pam_eval",
+            "pam_errors"]
 
 
 class PamError(RuntimeError):
@@ -82,16 +83,18 @@ def lib():
                                          P(pam_model), C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_refine.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), C.c_void_p,
                                  P(pam_model), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_eval_workspace_size.argtypes = [P(pam_plan), C.c_int64, P(C.c_size_t)]
         L.pam_eval.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_int64,
-                               C.c_void_p, C.c_int, C.c_int, C.c_void_p]
+                               C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_errors.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_void_p,
-                                 C.c_void_p, C.c_size_t, C.c_void_p]
+                                 C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_gram.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), C.c_void_p, P(pam_model),
                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_errors_noalloc.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p,
                                          C.c_void_p, C.c_void_p]
         for name in ("pam_plan_create", "pam_partition", "pam_fit_subdomains", "pam_refine",
-                     "pam_eval", "pam_errors", "pam_errors_noalloc", "pam_gram"):
+                     "pam_eval", "pam_errors", "pam_errors_noalloc", "pam_gram",
+                     "pam_eval_workspace_size"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -176,17 +179,25 @@ def pam_gram(problem, params, plan, K, model, G, b, workspace, stream=None):
                           workspace.numel() * workspace.element_size(), _stream(stream)), "pam_gram")
 
 
-def pam_eval(problem, plan, model, pts, out, log_space=False, precision=PAM_PREC_FP64, stream=None):
+def pam_eval_workspace_size(plan, n_pts):
+    n = C.c_size_t(0)
+    _check(lib().pam_eval_workspace_size(C.byref(plan), int(n_pts), C.byref(n)), "pam_eval_workspace_size")
+    return n.value
+
+
+def pam_eval(problem, plan, model, pts, out, log_space=False, precision=PAM_PREC_FP64, workspace=None,
+             stream=None):
     n = pts.shape[0] if pts is not None else 0
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
     _check(lib().pam_eval(C.byref(problem), C.byref(plan), C.byref(model.c_struct()), _ptr(pts),
-                          int(n), _ptr(out), int(bool(log_space)), int(precision), _stream(stream)),
-           "pam_eval")
+                          int(n), _ptr(out), int(bool(log_space)), int(precision), _ptr(workspace),
+                          nbytes, _stream(stream)), "pam_eval")
 
 
-def pam_errors(problem, plan, model, K, err, workspace, stream=None):
+def pam_errors(problem, plan, model, K, err, workspace, precision=PAM_PREC_FP64, stream=None):
     _check(lib().pam_errors(C.byref(problem), C.byref(plan), C.byref(model.c_struct()), _ptr(K),
-                            _ptr(err), _ptr(workspace), workspace.numel() * workspace.element_size(),
-                            _stream(stream)), "pam_errors")
+                            _ptr(err), int(precision), _ptr(workspace),
+                            workspace.numel() * workspace.element_size(), _stream(stream)), "pam_errors")
 
 
 def pam_errors_noalloc(problem, plan, model, K, err, stream=None):
@@ -256,18 +267,29 @@ class Fitter:
                         stream, check) if lv > 0 else 0
         return c1 or c2
 
+    def eval_workspace(self, n_pts):
+        import torch
+        need = pam_eval_workspace_size(self.plan, n_pts)
+        ws = getattr(self, "_eval_ws", None)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+            self._eval_ws = ws
+        return ws
+
     def eval(self, pts, out=None, log_space=False, precision=None, stream=None):
         import torch
         if out is None:
             out = torch.empty(pts.shape[0], dtype=torch.float64, device=pts.device)
         prec = self.params.precision if precision is None else precision
-        pam_eval(self.problem, self.plan, self.model, pts, out, log_space, prec, stream)
+        pam_eval(self.problem, self.plan, self.model, pts, out, log_space, prec,
+                 self.eval_workspace(pts.shape[0]), stream)
         return out
 
-    def errors(self, K, stream=None):
+    def errors(self, K, precision=None, stream=None):
         import torch
         err = torch.zeros(4, dtype=torch.float64, device=K.device)
-        pam_errors(self.problem, self.plan, self.model, K, err, self.workspace, stream)
+        prec = self.params.precision if precision is None else precision
+        pam_errors(self.problem, self.plan, self.model, K, err, self.workspace, prec, stream)
         e = err.cpu().numpy()
         return dict(l1=e[0], l2=e[1], l1_log=e[2], max_log10=e[3])
 

@@ -98,4 +98,4 @@ def test_null_arguments_are_rejected(pam):
     par = pam.make_params()
     plan = pam.pam_plan_create(pr, par)
     assert L.pam_fit_subdomains(C.byref(pr), C.byref(par), C.byref(plan), None, None, None, 0, None) == 1
-    assert L.pam_eval(C.byref(pr), C.byref(plan), None, None, 0, None, 0, 0, None) == 1
+    assert L.pam_eval(C.byref(pr), C.byref(plan), None, None, 0, None, 0, 0, None, 0, None) == 1

@@ -86,3 +86,119 @@ def test_tensor_core_gram_single_chunk_and_ragged(env):
     # patches smaller than one 32-cell chunk, and a dictionary of 3 x 5
     K = fields.voronoi_field(37, n_sites=6, seed=32)[:23, :]
     _gram_case(env, K, (37, 23), (8, 6), 0, (3, 5), 0, range(48), k_top=3, levels=1)
+
+
+# ------------------------------------------------------------------ the fit --
+LOG10_RTOL = 1e-3   # per cell: |dlog10 K*| <= 1e-3 max(1, |log10 K*_oracle|)
+L1_RTOL = 0.01      # final L1 within 1 % of the oracle's
+
+
+def _mixed_fit(env, K, n_cells, n_sub, overlap, g, levels, **params):
+    torch, pam, dev = env
+    fit = pam.Fitter(n_cells, n_sub, overlap, g, device=dev, precision=pam.PAM_PREC_MIXED, **params)
+    Kd = torch.from_numpy(np.ascontiguousarray(K)).to(dev)
+    pam.pam_fit_subdomains(fit.problem, fit.params, fit.plan, Kd, fit.model, fit.workspace)
+    if levels:
+        pam.pam_refine(fit.problem, fit.params, fit.plan, Kd, fit.model, levels, fit.workspace)
+    torch.cuda.synchronize()
+    return fit, Kd
+
+
+def _log10_close(a, b):
+    la, lb = np.log10(a), np.log10(b)
+    return np.abs(la - lb) <= LOG10_RTOL * np.maximum(1.0, np.abs(lb))
+
+
+def _cell_centroids(n_cells):
+    h = 1.0 / max(n_cells)
+    return fields.cell_centred_points(n_cells, [n * h for n in n_cells])
+
+
+def test_mixed_level0_matches_oracle_per_cell(env):
+    torch, pam, dev = env
+    K = fields.voronoi_field(256, n_sites=32, seed=2)
+    params = dict(k_top=37, levels=3)
+    fit, Kd = _mixed_fit(env, K, (256, 256), (8, 8), 2, (8, 8), 0, **params)
+    ref = oracle.fit_all(K, (256, 256), (8, 8), 2, (8, 8), oracle.default_params(k_top=37, levels=0))
+    got = fit.host_model()
+    np.testing.assert_array_equal(got["M"], ref["M"])
+    pts = _cell_centroids((256, 256))
+    km = fit.eval(torch.from_numpy(pts).to(dev)).cpu().numpy()
+    ko = oracle.evaluate(ref, pts)
+    ok = _log10_close(km, ko)
+    assert ok.all(), (np.count_nonzero(~ok), np.abs(np.log10(km) - np.log10(ko)).max())
+    # the fp64 evaluation of the same mixed model agrees with its fp32 evaluation
+    k64 = fit.eval(torch.from_numpy(pts).to(dev), precision=pam.PAM_PREC_FP64).cpu().numpy()
+    assert np.abs(np.log(km) - np.log(k64)).max() <= 1e-4
+
+
+def test_mixed_full_fit_voronoi(env):
+    torch, pam, dev = env
+    K = fields.voronoi_field(256, n_sites=32, seed=2)
+    params = dict(k_top=37, levels=3)
+    fit, Kd = _mixed_fit(env, K, (256, 256), (8, 8), 2, (8, 8), 3, **params)
+    ref = oracle.fit_all(K, (256, 256), (8, 8), 2, (8, 8), oracle.default_params(**params))
+    got = fit.host_model()
+    e_m = fit.errors(Kd)
+    e_o = oracle.errors(ref, K)
+    assert abs(e_m["l1"] - e_o["l1"]) <= L1_RTOL * e_o["l1"], (e_m["l1"], e_o["l1"])
+    # where the refinement made the same decisions the surrogates agree per cell
+    same = [s for s in range(64) if got["M"][s] == ref["M"][s]
+            and np.array_equal(got["c"][s, :ref["M"][s]], ref["c"][s, :ref["M"][s]])]
+    assert len(same) >= 48, len(same)
+    boxes = ref["boxes"]
+    h = 1.0 / 256
+    pts = []
+    for s in same:
+        b = boxes[s]
+        xs = (np.arange(b[0], b[3]) + 0.5) * h
+        ys = (np.arange(b[1], b[4]) + 0.5) * h
+        X, Y = np.meshgrid(xs, ys)
+        pts.append(np.stack([X.ravel(), Y.ravel()], 1))
+    pts = np.concatenate(pts)
+    km = fit.eval(torch.from_numpy(pts).to(dev)).cpu().numpy()
+    ko = oracle.evaluate(ref, pts)
+    ok = _log10_close(km, ko)
+    assert ok.all(), (np.count_nonzero(~ok), np.abs(np.log10(km) - np.log10(ko)).max())
+    flags = got["info"][:, pam.INFO_FLAGS]
+    assert np.count_nonzero(flags & pam.FLAG_NOT_CERTIFIED) == 0
+
+
+def test_mixed_3d_layered_sample(env):
+    torch, pam, dev = env
+    shape = (60, 220, 85)
+    K = fields.layered_field(shape, seed=5)
+    params = dict(k_top=30, levels=3)
+    fit, Kd = _mixed_fit(env, K, shape, (6, 22, 17), 1, (4, 4, 2), 3, **params)
+    which = list(range(0, 2244, 97))
+    ref = oracle.fit_all(K, shape, (6, 22, 17), 1, (4, 4, 2), oracle.default_params(**params), which=which)
+    got = fit.host_model()
+    h = 1.0 / 220
+    same, l1m, l1o, den = 0, 0.0, 0.0, 0.0
+    bad = 0
+    for s in which:
+        b = ref["boxes"][s]
+        ax = [(np.arange(b[a], b[3 + a]) + 0.5) * h for a in range(3)]
+        Z, Y, X = np.meshgrid(ax[2], ax[1], ax[0], indexing="ij")
+        pts = np.stack([X.ravel(), Y.ravel(), Z.ravel()], 1)
+        km = fit.eval(torch.from_numpy(pts).to(dev)).cpu().numpy()
+        ko = oracle.evaluate(ref, pts)
+        kt = K[b[2]:b[5], b[1]:b[4], b[0]:b[3]].ravel()
+        l1m += np.abs(kt - km).sum(); l1o += np.abs(kt - ko).sum(); den += np.abs(kt).sum()
+        m = ref["M"][s]
+        if got["M"][s] == m and np.array_equal(got["c"][s, :m], ref["c"][s, :m]):
+            same += 1
+            bad += np.count_nonzero(~_log10_close(km, ko))
+    assert same >= 0.75 * len(which), same
+    assert bad == 0
+    assert abs(l1m - l1o) <= L1_RTOL * l1o, (l1m / den, l1o / den)
+
+
+def test_mixed_eval_outside_and_empty(env):
+    torch, pam, dev = env
+    K = fields.voronoi_field(64, n_sites=6, seed=33)
+    fit, Kd = _mixed_fit(env, K, (64, 64), (4, 4), 1, (4, 4), 1, k_top=5, levels=1)
+    pts = np.array([[-0.1, 0.5], [0.5, 1.2], [0.5, 0.5], [1.0, 1.0], [0.0, 0.0]])
+    out = fit.eval(torch.from_numpy(pts).to(dev)).cpu().numpy()
+    assert np.isnan(out[:2]).all() and np.isfinite(out[2:]).all()
+    assert fit.eval(torch.zeros((0, 2), dtype=torch.float64, device=dev)).numel() == 0

@@ -47,7 +47,7 @@ def test_noalloc_errors_match_the_workspace_version_on_consecutive_calls(env):
     for K, n_cells, n_sub, overlap, g in cases:
         fit, Kd = _fitted(torch, pam, dev, K, n_cells, n_sub, overlap, g, k_top=8, levels=2)
         ref = torch.zeros(4, dtype=torch.float64, device=dev)
-        pam.pam_errors(fit.problem, fit.plan, fit.model, Kd, ref, fit.workspace)
+        pam.pam_errors(fit.problem, fit.plan, fit.model, Kd, ref, fit.workspace, pam.PAM_PREC_FP64)
         outs = []
         for _ in range(2):  # two calls in a row share the library's scratch array
             out = torch.full((4,), float("nan"), dtype=torch.float64, device=dev)
