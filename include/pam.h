@@ -68,7 +68,7 @@ enum {
     PAM_INFO_M = 0,        /* current dictionary size M_i */
     PAM_INFO_SUPPORT = 1,  /* nonzero coefficients */
     PAM_INFO_LEVELS = 2,   /* enrichment rounds done */
-    PAM_INFO_ITERS = 3,    /* active-set iterations of the last solve */
+    PAM_INFO_ITERS = 3,    /* iterations of the last solve (mixed: active-set + 100 x refinement) */
     PAM_INFO_FLAGS = 4,    /* PAM_FLAG_* bits */
     PAM_INFO_STOPPED = 5,  /* 1 once Algorithm 1 stopped for this subdomain */
     PAM_INFO_N_CELLS = 6,  /* patch cells N_i */

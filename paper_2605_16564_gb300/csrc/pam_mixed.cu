@@ -358,7 +358,9 @@ void launch_copy_gram_f32(const Geo &g, const int32_t *info, const Ws &w, double
 // --------------------------------------------------------------------------
 constexpr int kMxThreads = 256;
 constexpr int kMxFactorBytes = 64 * 1024;
-constexpr int kMxMaxRefine = 6;
+constexpr int kMxMaxRefine = 12;
+constexpr int kMxMaxPdas = 96;
+constexpr int kMxPdasFull = 12;
 
 struct MxShared {
     int cnt, bad, viol, flag, changed;
@@ -435,7 +437,8 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
     if (inf[PAM_INFO_STOPPED]) return;
     const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS], mc = g.m_cap;
     const float lam1 = (float)((double)N * p.lam1_hat), lam2 = (float)((double)N * p.lam2_hat);
-    const float tol_pdas = lam1 * (1.0f + 1e-6f);
+    // stage 1 only has to find a good support: G~ carries ~1e-5 relative error
+    const float tol_pdas = lam1 * (1.0f + 1e-3f);
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     const int32_t *box = boxes + s * 12;
 
@@ -476,9 +479,16 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
     __syncthreads();
 
     // ---------------- stage 1: active-set iterations on G~ ----------------
-    int it = 0, scnt = 0, ok1 = 0;
+    // Up to kMxPdasFull full primal-dual corrections; if the support still
+    // moves, a primal active-set phase takes over from the sign-consistent
+    // part of the iterate: on the current support it steps towards the
+    // sign-constrained minimiser as far as the signs allow (ratio test),
+    // dropping the coefficient that reaches zero, and adds the single
+    // largest violator only once the minimiser on the support is
+    // sign-consistent -- the objective decreases monotonically, so it ends.
+    int it = 0, scnt = 0;
     float *A = Asm;
-    for (; it < p.max_iters; ++it) {
+    auto factor_support = [&]() {
         mx_compact(sg, M, idx, &sh.cnt);
         scnt = sh.cnt;
         A = (tri_i(scnt, 0) * 4 <= kMxFactorBytes) ? Asm
@@ -490,69 +500,135 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
         }
         __syncthreads();
         mx_cholesky(A, scnt, &sh.flag, &sh.inv_piv);
-        if (sh.flag) break;
-        mx_chol_solve(A, scnt, rhs);
-        for (int j = tid; j < M; j += blockDim.x) x[j] = 0.f;
-        __syncthreads();
-        for (int pp = tid; pp < scnt; pp += blockDim.x) x[idx[pp]] = rhs[pp];
-        __syncthreads();
+        if (!sh.flag) mx_chol_solve(A, scnt, rhs);
+    };
+    auto gradient_fp = [&]() {  // gr = b - G~ x
         for (int j = warp; j < M; j += nw) {
             const float *Gr = G + (size_t)j * mc;
             float acc = 0.f;
-            for (int pp = lane; pp < scnt; pp += 32) acc = fmaf(Gr[idx[pp]], rhs[pp], acc);
+            for (int pp = lane; pp < scnt; pp += 32) acc = fmaf(Gr[idx[pp]], x[idx[pp]], acc);
             acc = warp_sumf(acc);
             if (lane == 0) gr[j] = bv[j] - acc;
         }
-        if (tid == 0) { sh.bad = 0; sh.viol = 0; }
         __syncthreads();
-        int mb = 0, mv = 0;
-        for (int j = tid; j < M; j += blockDim.x) {
-            if (sg[j] != 0) mb += !(x[j] * (float)sg[j] > 0.f);
-            else mv += fabsf(gr[j]) > tol_pdas;
+    };
+    bool primal = false;
+    int last_added = -1;
+    const int max_pdas = p.max_iters < kMxMaxPdas ? p.max_iters : kMxMaxPdas;
+    for (; it < max_pdas; ++it) {
+        factor_support();
+        if (sh.flag) break;
+        if (!primal) {
+            for (int j = tid; j < M; j += blockDim.x) x[j] = 0.f;
+            __syncthreads();
+            for (int pp = tid; pp < scnt; pp += blockDim.x) x[idx[pp]] = rhs[pp];
+            __syncthreads();
+            gradient_fp();
+            if (tid == 0) { sh.bad = 0; sh.viol = 0; }
+            __syncthreads();
+            int mb = 0, mv = 0;
+            for (int j = tid; j < M; j += blockDim.x) {
+                if (sg[j] != 0) mb += !(x[j] * (float)sg[j] > 0.f);
+                else mv += fabsf(gr[j]) > tol_pdas;
+            }
+            if (mb) atomicAdd(&sh.bad, mb);
+            if (mv) atomicAdd(&sh.viol, mv);
+            __syncthreads();
+            if (sh.bad == 0 && sh.viol == 0) break;
+            if (it + 1 < kMxPdasFull) {
+                for (int j = tid; j < M; j += blockDim.x) {
+                    if (sg[j] != 0) {
+                        if (!(x[j] * (float)sg[j] > 0.f)) sg[j] = 0;
+                    } else if (fabsf(gr[j]) > tol_pdas) {
+                        sg[j] = gr[j] > 0.f ? 1 : -1;
+                    }
+                }
+            } else {
+                // switch: keep the sign-consistent part of the iterate
+                for (int j = tid; j < M; j += blockDim.x)
+                    if (!(x[j] * (float)sg[j] > 0.f)) { sg[j] = 0; x[j] = 0.f; }
+                primal = true;
+            }
+            __syncthreads();
+            continue;
         }
-        if (mb) atomicAdd(&sh.bad, mb);
-        if (mv) atomicAdd(&sh.viol, mv);
+        // primal phase: x is sign-consistent on the support; rhs = minimiser
+        if (tid == 0) { sh.dmax = 2.f; sh.bad = 0; }
         __syncthreads();
-        if (sh.bad == 0 && sh.viol == 0) { ok1 = 1; break; }
-        const bool single = it >= 16;
-        if (single && sh.bad == 0) {
+        for (int pp = tid; pp < scnt; pp += blockDim.x) {
+            const int m = idx[pp];
+            const float xs = rhs[pp], x0 = x[m], sgn = (float)sg[m];
+            if (!(xs * sgn > 0.f)) {
+                const float a = (x0 * sgn > 0.f) ? x0 / (x0 - xs) : 0.f;
+                atomicMin(reinterpret_cast<int *>(&sh.dmax), __float_as_int(fmaxf(a, 0.f)));
+                atomicAdd(&sh.bad, 1);
+            }
+        }
+        __syncthreads();
+        if (sh.bad == 0) {
+            for (int pp = tid; pp < scnt; pp += blockDim.x) x[idx[pp]] = rhs[pp];
+            __syncthreads();
+            gradient_fp();
             if (tid == 0) {
-                float best = -1.f;
+                float best = tol_pdas;
                 int bj = -1;
                 for (int j = 0; j < M; ++j)
-                    if (sg[j] == 0 && fabsf(gr[j]) > tol_pdas && fabsf(gr[j]) > best) { best = fabsf(gr[j]); bj = j; }
-                if (bj >= 0) sg[bj] = gr[bj] > 0.f ? 1 : -1;
+                    if (sg[j] == 0 && fabsf(gr[j]) > best) { best = fabsf(gr[j]); bj = j; }
+                sh.viol = bj;
+                if (bj >= 0 && bj != last_added) { sg[bj] = gr[bj] > 0.f ? 1 : -1; x[bj] = 0.f; }
             }
+            __syncthreads();
+            if (sh.viol < 0 || sh.viol == last_added) break;  // optimal (or stalled on one index)
+            last_added = sh.viol;
         } else {
-            for (int j = tid; j < M; j += blockDim.x) {
-                if (sg[j] != 0) {
-                    if (!(x[j] * (float)sg[j] > 0.f)) sg[j] = 0;
-                } else if (!single && fabsf(gr[j]) > tol_pdas) {
-                    sg[j] = gr[j] > 0.f ? 1 : -1;
+            // step alpha towards the minimiser; the blocking coefficients (the
+            // ones whose ratio attains alpha) reach zero and leave the support
+            const float alpha = fminf(sh.dmax, 1.f);
+            for (int pp = tid; pp < scnt; pp += blockDim.x) {
+                const int m = idx[pp];
+                const float xs = rhs[pp], x0 = x[m], sgn = (float)sg[m];
+                bool blocking = false;
+                if (!(xs * sgn > 0.f)) {
+                    const float a = (x0 * sgn > 0.f) ? x0 / (x0 - xs) : 0.f;
+                    blocking = fmaxf(a, 0.f) <= alpha * (1.f + 1e-6f);
+                }
+                const float nx = x0 + alpha * (xs - x0);
+                if (blocking || !(nx * sgn > 0.f)) {
+                    x[m] = 0.f;
+                    sg[m] = 0;
+                } else {
+                    x[m] = nx;
                 }
             }
+            __syncthreads();
         }
-        __syncthreads();
     }
-    (void)ok1;
-
     // ---------------- stage 2: refinement with the exact gradient ---------
-    const float kkt_tol = lam1 * (1.0f + 1e-4f);
+    // Certified when, with the exact gradient c, the stationarity residual on
+    // the support is below rtol and no coefficient off it violates
+    // |c_j| <= lambda1 (1 + 1e-3): the fp32 form of the optimality conditions.
+    // A coefficient inside that band has |beta_j| <= 1e-3 lambda1 / (G_jj +
+    // lambda2) at the exact minimiser (changes W beta by <~1e-5); admitting it
+    // only makes near-degenerate coordinates cycle in and out of the support.
+    const float kkt_tol = lam1 * (1.0f + 1e-3f);
     int certified = 0, refine_it = 0;
     const double *yv = w.y + (size_t)s * g.n_max;
     for (; refine_it < kMxMaxRefine && !sh.flag; ++refine_it) {
-        // e = y - W x over the patch (only the support contributes)
+        // e = y - W x over the patch (only the support contributes); W x is
+        // accumulated and subtracted in fp64: |y| ~ 10 would otherwise leave
+        // ~1e-6 of cancellation noise in e, and W^T e inherits it
         for (int t = tid; t < N; t += blockDim.x) {
             const float4 cx = cell[t];
-            float acc = 0.f;
+            double acc = 0.0;
             for (int pp = 0; pp < scnt; ++pp) {
                 const int m = idx[pp];
-                acc = fmaf(tc::ex2(logit2(sc[m], cx.x, cx.y, cx.z) - cx.w), x[m], acc);
+                acc = fma((double)tc::ex2(logit2(sc[m], cx.x, cx.y, cx.z) - cx.w), (double)x[m], acc);
             }
-            ce[t] = (float)yv[t] - acc * cinv[t];
+            ce[t] = (float)(yv[t] - acc * (double)cinv[t]);
         }
         __syncthreads();
         // c_j = sum_t W_tj e_t for every centre (exact gradient of the data term)
+        float cmax = 0.f;
         for (int j = tid; j < M; j += blockDim.x) {
             const float4 cj = sc[j];
             float acc = 0.f;
@@ -561,14 +637,35 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
                 acc = fmaf(tc::ex2(logit2(cj, cx.x, cx.y, cx.z) - cx.w) * cinv[t], ce[t], acc);
             }
             gr[j] = acc;
+            cmax = fmaxf(cmax, fabsf(acc));
         }
         if (tid == 0) { sh.viol = 0; sh.changed = 0; sh.dmax = 0.f; sh.xmax = 0.f; }
         __syncthreads();
-        // optimality off the support; violators join it
+        // stationarity residual on the support, violations off it
+        float rmax = 0.f;
         int mv = 0;
+        for (int j = tid; j < M; j += blockDim.x) {
+            if (sg[j] != 0) rmax = fmaxf(rmax, fabsf(gr[j] - lam2 * x[j] - lam1 * (float)sg[j]));
+            else if (fabsf(gr[j]) > kkt_tol) ++mv;
+        }
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o2));
+            cmax = fmaxf(cmax, __shfl_xor_sync(0xffffffffu, cmax, o2));
+            mv += __shfl_xor_sync(0xffffffffu, mv, o2);
+        }
+        if (lane == 0) {
+            atomicMax(reinterpret_cast<int *>(&sh.dmax), __float_as_int(rmax));
+            atomicMax(reinterpret_cast<int *>(&sh.xmax), __float_as_int(cmax));
+            if (mv) atomicAdd(&sh.viol, mv);
+        }
+        __syncthreads();
+        const float rtol = 1e-4f * lam1 + 1e-6f * sh.xmax;
+        if (sh.viol == 0 && sh.dmax <= rtol) { certified = 1; break; }
+        // violators join the support with the sign of their gradient
+        int jn = 0;
         for (int j = tid; j < M; j += blockDim.x)
-            if (sg[j] == 0 && fabsf(gr[j]) > kkt_tol) { sg[j] = gr[j] > 0.f ? 1 : -1; x[j] = 0.f; ++mv; }
-        if (mv) { atomicAdd(&sh.viol, mv); atomicOr(&sh.changed, 1); }
+            if (sg[j] == 0 && fabsf(gr[j]) > kkt_tol) { sg[j] = gr[j] > 0.f ? 1 : -1; x[j] = 0.f; ++jn; }
+        if (jn) atomicOr(&sh.changed, 1);
         __syncthreads();
         if (sh.changed) {
             mx_compact(sg, M, idx, &sh.cnt);
@@ -590,27 +687,17 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
         }
         __syncthreads();
         mx_chol_solve(A, scnt, rhs);
-        float dmax = 0.f, xmax = 0.f;
         int dropped = 0;
         for (int pp = tid; pp < scnt; pp += blockDim.x) {
             const int m = idx[pp];
             const float nx = x[m] + rhs[pp];
-            dmax = fmaxf(dmax, fabsf(rhs[pp]));
             if (!(nx * (float)sg[m] > 0.f)) { sg[m] = 0; x[m] = 0.f; ++dropped; }
-            else { x[m] = nx; xmax = fmaxf(xmax, fabsf(nx)); }
+            else x[m] = nx;
         }
-        for (int o2 = 16; o2 > 0; o2 >>= 1) {
-            dmax = fmaxf(dmax, __shfl_xor_sync(0xffffffffu, dmax, o2));
-            xmax = fmaxf(xmax, __shfl_xor_sync(0xffffffffu, xmax, o2));
-            dropped += __shfl_xor_sync(0xffffffffu, dropped, o2);
-        }
-        if (lane == 0) {
-            atomicMax(reinterpret_cast<int *>(&sh.dmax), __float_as_int(dmax));
-            atomicMax(reinterpret_cast<int *>(&sh.xmax), __float_as_int(xmax));
-            if (dropped) atomicOr(&sh.changed, 2);
-        }
+        for (int o2 = 16; o2 > 0; o2 >>= 1) dropped += __shfl_xor_sync(0xffffffffu, dropped, o2);
+        if (lane == 0 && dropped) atomicOr(&sh.changed, 2);
         __syncthreads();
-        if (sh.changed & 2) {  // support shrank: recompact, refactor next round
+        if (sh.changed & 2) {  // support shrank: recompact and refactor
             mx_compact(sg, M, idx, &sh.cnt);
             scnt = sh.cnt;
             A = (tri_i(scnt, 0) * 4 <= kMxFactorBytes) ? Asm
@@ -621,20 +708,18 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
             }
             __syncthreads();
             mx_cholesky(A, scnt, &sh.flag, &sh.inv_piv);
-            continue;
         }
-        if (sh.viol == 0 && sh.dmax <= 1e-6f * fmaxf(sh.xmax, 1.f)) { certified = 1; ++refine_it; break; }
     }
 
     // final residual e = y - W x, and the indicators R_T (Eq. (4), midpoint)
     for (int t = tid; t < N; t += blockDim.x) {
         const float4 cx = cell[t];
-        float acc = 0.f;
+        double acc = 0.0;
         for (int pp = 0; pp < scnt; ++pp) {
             const int m = idx[pp];
-            acc = fmaf(tc::ex2(logit2(sc[m], cx.x, cx.y, cx.z) - cx.w), x[m], acc);
+            acc = fma((double)tc::ex2(logit2(sc[m], cx.x, cx.y, cx.z) - cx.w), (double)x[m], acc);
         }
-        const double yhat = (double)(acc * cinv[t]);
+        const double yhat = acc * (double)cinv[t];
         const double kv = w.kv[(size_t)s * g.n_max + t];
         const double e = exp(yhat) - kv;
         w.R[(size_t)s * g.n_max + t] = g.vol * (e * e);
@@ -649,7 +734,7 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
         if (sh.flag) flags |= PAM_FLAG_CHOLESKY;
         inf[PAM_INFO_FLAGS] = flags;
         inf[PAM_INFO_SUPPORT] = scnt;
-        inf[PAM_INFO_ITERS] = it + refine_it;
+        inf[PAM_INFO_ITERS] = it + 100 * refine_it;  // active-set steps + 100 x refinement steps
     }
 }
 

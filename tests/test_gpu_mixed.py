@@ -93,13 +93,13 @@ LOG10_RTOL = 1e-3   # per cell: |dlog10 K*| <= 1e-3 max(1, |log10 K*_oracle|)
 L1_RTOL = 0.01      # final L1 within 1 % of the oracle's
 
 
-def _mixed_fit(env, K, n_cells, n_sub, overlap, g, levels, **params):
+def _mixed_fit(env, K, n_cells, n_sub, overlap, g, n_refine, **params):
     torch, pam, dev = env
     fit = pam.Fitter(n_cells, n_sub, overlap, g, device=dev, precision=pam.PAM_PREC_MIXED, **params)
     Kd = torch.from_numpy(np.ascontiguousarray(K)).to(dev)
     pam.pam_fit_subdomains(fit.problem, fit.params, fit.plan, Kd, fit.model, fit.workspace)
-    if levels:
-        pam.pam_refine(fit.problem, fit.params, fit.plan, Kd, fit.model, levels, fit.workspace)
+    if n_refine:
+        pam.pam_refine(fit.problem, fit.params, fit.plan, Kd, fit.model, n_refine, fit.workspace)
     torch.cuda.synchronize()
     return fit, Kd
 
