@@ -41,6 +41,9 @@ WORKLOADS = {
     "layered3d": dict(shape=(60, 220, 85), n_sub=(6, 22, 17), overlap=1, g=(4, 4, 2),
                       params=dict(k_top=30, levels=3), eval_counts=(120, 440, 170),
                       field=lambda seed: fields.layered_field((60, 220, 85), seed=seed), seed=5),
+    "layered3d_quarter": dict(shape=(30, 110, 85), n_sub=(3, 11, 17), overlap=1, g=(4, 4, 2),
+                              params=dict(k_top=30, levels=3), eval_counts=(60, 220, 170),
+                              field=lambda seed: fields.layered_field((30, 110, 85), seed=seed), seed=5),
     "channel2d": dict(shape=(1024, 1024), n_sub=(32, 32), overlap=2, g=(8, 8),
                       params=dict(k_top=37, levels=3), eval_counts=(1536, 1536),
                       field=lambda seed: fields.channel_field(1024, seed=seed), seed=3),

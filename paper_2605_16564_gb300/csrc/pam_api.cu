@@ -76,6 +76,7 @@ bool make_geo(const pam_problem *prob, const pam_params *par, Geo *g, Par *p, pa
         // the tensor-core Gram keeps a 128 x M strip in TMEM (512 columns)
         if (par->precision == PAM_PREC_MIXED && cap > kMixedMaxM) { *st = PAM_ERR_UNSUPPORTED; return false; }
         g->m_cap = (int)cap;
+        g->prec = par->precision;
         if (p) {
             p->lam1_hat = par->lambda1_hat;
             p->lam2_hat = par->lambda2_hat;
@@ -111,10 +112,14 @@ static size_t carve(const Geo &g, char *base, Ws *w) {
     w->rowmax = (float *)take(S * nm * sizeof(float));
     w->rowinv = (float *)take(S * nm * sizeof(float));
     w->b = (double *)take(S * mc * sizeof(double));
-    w->L = (double *)take(S * (mc * (mc + 1) / 2) * sizeof(double));
-    w->G = (double *)take(S * mc * mc * sizeof(double));
-    w->Gf = (float *)w->G;  // the mixed form keeps its fp32 Gram in the same region
-    w->E = (double *)take(S * mc * nm * sizeof(double));
+    // large regions: the fp64 form needs E, G and fp64 factors; the mixed
+    // form only its fp32 Gram and fp32 factors
+    const bool f64 = g.prec == PAM_PREC_FP64;
+    w->L = (double *)take(S * (mc * (mc + 1) / 2) * (f64 ? sizeof(double) : sizeof(float)));
+    w->Lf = (float *)w->L;
+    w->G = (double *)take(S * mc * mc * (f64 ? sizeof(double) : sizeof(float)));
+    w->Gf = (float *)w->G;
+    w->E = f64 ? (double *)take(S * mc * nm * sizeof(double)) : nullptr;
     w->bytes = off;
     return off;
 }

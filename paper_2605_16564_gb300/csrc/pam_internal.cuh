@@ -28,6 +28,7 @@ struct Geo {
     int S;          // subdomains
     int n_max;      // max patch cells (padded stride of per-cell arrays)
     int m0, m_cap;
+    int prec;       // pam_precision of the fit calls (sizes the workspace)
 };
 
 struct Par {
@@ -44,7 +45,8 @@ struct Ws {
     double *G;        // [S][m_cap][m_cap] Gram W^T W (fp64 form)
     double *b;        // [S][m_cap]   W^T y
     double *R;        // [S][n_max]   residual indicators
-    double *L;        // [S][m_cap (m_cap+1)/2] packed Cholesky factor when it exceeds shared memory
+    double *L;        // [S][m_cap (m_cap+1)/2] packed fp64 Cholesky factor when it exceeds shared memory
+    float *Lf;        // the same region as fp32 factors (mixed form), same per-subdomain stride in elements
     float *Gf;        // [S][m_cap][m_cap] Gram in fp32 (mixed form)
     float *rowmax;    // [S][n_max]   row maximum of the logits (mixed form)
     float *rowinv;    // [S][n_max]   1 / Shepard sum (mixed form)

@@ -93,7 +93,7 @@ __global__ void __launch_bounds__(128) k_stats_f32(Geo g, const int32_t *boxes,
 // mirrored block below the strip) in fp32; threads of the strip's rows also
 // accumulate b = W^T y.
 // --------------------------------------------------------------------------
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 512;
 constexpr int kTcKC = 32;                 // cells per chunk (2 MMA k-steps of 16)
 constexpr int kTcMaxRows = 512;           // rows of the B tile (TMEM columns)
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz
@@ -101,6 +101,22 @@ constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz
 struct TcCell {
     float x[kTcKC], y[kTcKC], z[kTcKC], mx[kTcKC], inv[kTcKC], yv[kTcKC];
 };
+
+__device__ __forceinline__ void load_cells(const Geo &g, const int32_t *box, int c, int N,
+                                           const float *rowmax, const float *rowinv,
+                                           const double *yv, TcCell &cl, int lane) {
+    const int t = c * kTcKC + lane;
+    float x[3] = {0.f, 0.f, 0.f};
+    float mx = 0.f, iv = 0.f, y = 0.f;
+    if (t < N) {
+        local_cell(g, box, t, x);
+        mx = rowmax[t];
+        iv = rowinv[t];
+        y = (float)yv[t];
+    }
+    cl.x[lane] = x[0]; cl.y[lane] = x[1]; cl.z[lane] = x[2];
+    cl.mx[lane] = mx; cl.inv[lane] = iv; cl.yv[lane] = y;
+}
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t *boxes,
                                                            const double *centres,
@@ -130,10 +146,14 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
     double o[3];
     patch_origin(g, box, o);
     const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
-    for (int r = tid; r < R; r += blockDim.x) {
+    for (int r = tid; r < Rt; r += blockDim.x) {
         int m = row0 + r;
-        sc[r] = m < M ? local_centre(cg[m], o) : make_float4(0.f, 0.f, 0.f, 0.f);
+        sc[r] = (r < R && m < M) ? local_centre(cg[m], o) : make_float4(0.f, 0.f, 0.f, 0.f);
     }
+    const float *rowmax = w.rowmax + (size_t)s * g.n_max;
+    const float *rowinv = w.rowinv + (size_t)s * g.n_max;
+    const double *yv = w.y + (size_t)s * g.n_max;
+    if (warp == 1) load_cells(g, box, 0, N, rowmax, rowinv, yv, cells[0], lane);
     uint32_t ncols = 32;
     while (ncols < (uint32_t)R) ncols <<= 1;
     if (tid == 0) {
@@ -151,13 +171,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
 
-    const float *rowmax = w.rowmax + (size_t)s * g.n_max;
-    const float *rowinv = w.rowinv + (size_t)s * g.n_max;
-    const double *yv = w.y + (size_t)s * g.n_max;
     const int nch = (N + kTcKC - 1) / kTcKC;
     const uint32_t lbo = (uint32_t)Rt * 16u, sbo = 128u;
-    float bacc[2] = {0.f, 0.f};
-    const bool valid_row[2] = {tid < R && row0 + tid < M, tid + 256 < R && row0 + tid + 256 < M};
+    const int r = tid;                              // the tile row this thread produces
+    const bool live = r < R && row0 + r < M;
+    const float4 cc = r < Rt ? sc[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+    float bacc = 0.f;
 
     int issued = 0;  // chunks whose MMAs thread 0 has committed
     for (int c = 0; c < nch; ++c) {
@@ -165,30 +184,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
         if (c >= 2) {  // the MMAs of chunk c-2 read this buffer
             if (!tc::mbar_wait(&mbar[buf], ((c - 2) >> 1) & 1, kWaitBudget)) timed_out = 1;
         }
-        // cell data of the chunk
-        TcCell &cl = cells[buf];
-        if (tid < kTcKC) {
-            int t = c * kTcKC + tid;
-            float x[3] = {0.f, 0.f, 0.f};
-            float mx = 0.f, iv = 0.f, y = 0.f;
-            if (t < N) {
-                local_cell(g, box, t, x);
-                mx = rowmax[t];
-                iv = rowinv[t];
-                y = (float)yv[t];
-            }
-            cl.x[tid] = x[0]; cl.y[tid] = x[1]; cl.z[tid] = x[2];
-            cl.mx[tid] = mx; cl.inv[tid] = iv; cl.yv[tid] = y;
-        }
-        __syncthreads();
-        if (timed_out) break;
+        // next chunk's cell data goes to the other buffer (read after the barrier)
+        if (warp == 1 && c + 1 < nch) load_cells(g, box, c + 1, N, rowmax, rowinv, yv, cells[buf ^ 1], lane);
+        const TcCell &cl = cells[buf];
         uint8_t *hi = tiles + (size_t)buf * 2 * tile_bytes;
         uint8_t *lo = hi + tile_bytes;
-        for (int rr = 0; rr < 2; ++rr) {
-            const int r = tid + rr * 256;
-            if (r >= Rt) break;
-            const float4 cc = r < R ? sc[r] : make_float4(0.f, 0.f, 0.f, 0.f);
-            const bool live = valid_row[rr];
+        if (r < Rt) {
             float bsum = 0.f;
 #pragma unroll
             for (int kg = 0; kg < kTcKC / 8; ++kg) {
@@ -196,30 +197,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
 #pragma unroll
                 for (int q = 0; q < 8; ++q) {
                     const int k = kg * 8 + q;
-                    float e = 0.f;
-                    if (live && cl.inv[k] != 0.f)
-                        e = tc::ex2(logit2(cc, cl.x[k], cl.y[k], cl.z[k]) - cl.mx[k]) * cl.inv[k];
+                    const float e = live ? tc::ex2(logit2(cc, cl.x[k], cl.y[k], cl.z[k]) - cl.mx[k]) * cl.inv[k]
+                                         : 0.f;
                     v[q] = e;
                     bsum = fmaf(e, cl.yv[k], bsum);
                 }
-                uint4 h, l;
-                float hv[8];
+                uint32_t hp[4], lp[4];
 #pragma unroll
-                for (int q = 0; q < 8; ++q) hv[q] = __bfloat162float(__float2bfloat16_rn(v[q]));
-                h.x = tc::pack_bf16(hv[0], hv[1]); h.y = tc::pack_bf16(hv[2], hv[3]);
-                h.z = tc::pack_bf16(hv[4], hv[5]); h.w = tc::pack_bf16(hv[6], hv[7]);
-                l.x = tc::pack_bf16(v[0] - hv[0], v[1] - hv[1]);
-                l.y = tc::pack_bf16(v[2] - hv[2], v[3] - hv[3]);
-                l.z = tc::pack_bf16(v[4] - hv[4], v[5] - hv[5]);
-                l.w = tc::pack_bf16(v[6] - hv[6], v[7] - hv[7]);
+                for (int q = 0; q < 4; ++q) {
+                    hp[q] = tc::pack_bf16(v[2 * q], v[2 * q + 1]);
+                    const float h0 = __uint_as_float(hp[q] << 16), h1 = __uint_as_float(hp[q] & 0xffff0000u);
+                    lp[q] = tc::pack_bf16(v[2 * q] - h0, v[2 * q + 1] - h1);
+                }
                 const uint32_t off = (uint32_t)(kg * (Rt >> 3) + (r >> 3)) * 128u + (uint32_t)(r & 7) * 16u;
-                *reinterpret_cast<uint4 *>(hi + off) = h;
-                *reinterpret_cast<uint4 *>(lo + off) = l;
+                *reinterpret_cast<uint4 *>(hi + off) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+                *reinterpret_cast<uint4 *>(lo + off) = make_uint4(lp[0], lp[1], lp[2], lp[3]);
             }
-            bacc[rr] += bsum;
+            bacc += bsum;
         }
         tc::fence_proxy_async_smem();
         __syncthreads();
+        if (timed_out) break;
         if (tid == 0) {
             tc::fence_after_sync();
             const uint32_t hi_a = tc::smem_u32(hi), lo_a = tc::smem_u32(lo);
@@ -257,34 +255,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
         if (tid == 0) atomicAdd(&w.status[kStTimeout], 1);
     } else {
         float *G = w.Gf + (size_t)s * g.m_cap * g.m_cap;
-        // warp q and q+4 share TMEM lanes 32q..32q+31; they split the columns
+        // warp q reads TMEM lanes 32 (q % 4) ..; the four warps of a lane
+        // quarter split the 32-column chunks. Rows go out through a padded
+        // shared-memory transpose so that each store is one coalesced row
+        // segment; the mirrored block below the strip is already coalesced.
+        float *stage = reinterpret_cast<float *>(tiles) + (size_t)warp * 32 * 33;
         const int lane_base = (warp & 3) * 32;
-        const int r = row0 + lane_base + lane;  // G row held by this thread
-        const int half = warp >> 2;
+        const int rl = lane_base + lane;      // D row (TMEM lane) held by this thread
+        const int rg = row0 + rl;             // its G row
         const int ncol_chunks = R / 32;
-        for (int cc = half; cc < ncol_chunks; cc += 2) {
+        for (int ch = warp >> 2; ch < ncol_chunks; ch += 4) {
             uint32_t v[32];
-            tc::tmem_ld_32x32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(cc * 32), v);
+            tc::tmem_ld_32x32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(ch * 32), v);
             tc::tmem_wait_ld();
-            const int c0 = row0 + cc * 32;
-            if (r < M) {
+            const int c0 = row0 + ch * 32;
+            if (ch * 32 >= 128) {
                 for (int q = 0; q < 32; ++q) {
-                    int col = c0 + q;
-                    if (col < M) G[(size_t)r * g.m_cap + col] = __uint_as_float(v[q]);
+                    const int col = c0 + q;
+                    if (col < M && rg < M) G[(size_t)col * g.m_cap + rg] = __uint_as_float(v[q]);
                 }
             }
-            // mirror the block right of the strip's diagonal block
-            if (cc * 32 >= 128) {
-                for (int q = 0; q < 32; ++q) {
-                    int col = c0 + q;
-                    if (col < M && r < M) G[(size_t)col * g.m_cap + r] = __uint_as_float(v[q]);
-                }
+#pragma unroll
+            for (int q = 0; q < 32; ++q) stage[lane * 33 + q] = __uint_as_float(v[q]);
+            __syncwarp();
+            const int col = c0 + lane;
+            for (int q = 0; q < 32; ++q) {
+                const int row = row0 + lane_base + q;
+                if (row < M && col < M) G[(size_t)row * g.m_cap + col] = stage[q * 33 + lane];
             }
+            __syncwarp();
         }
-        for (int rr = 0; rr < 2; ++rr) {
-            const int rl = tid + rr * 256;
-            if (rl < 128 && valid_row[rr]) w.b[(size_t)s * g.m_cap + row0 + rl] = (double)bacc[rr];
-        }
+        if (r < 128 && live) w.b[(size_t)s * g.m_cap + row0 + r] = (double)bacc;
     }
     tc::fence_before_sync();
     __syncthreads();
@@ -356,6 +357,7 @@ void launch_copy_gram_f32(const Geo &g, const int32_t *info, const Ws &w, double
 // final coefficients are written (fp64 for the K-space residual), so the
 // refinement round needs no separate residual pass.
 // --------------------------------------------------------------------------
+
 constexpr int kMxThreads = 256;
 constexpr int kMxFactorBytes = 64 * 1024;
 constexpr int kMxMaxRefine = 12;
@@ -384,50 +386,176 @@ __device__ void mx_compact(const int *sg, int M, int *idx, int *cnt) {
 
 __device__ __forceinline__ int tri_i(int p, int q) { return p * (p + 1) / 2 + q; }
 
-__device__ void mx_cholesky(float *A, int s, int *flag, float *inv_piv) {
+#ifdef PAM_SOLVE_PROFILE
+// Profiling builds only: clock64 totals per phase of the mixed solve.
+__device__ unsigned long long g_solve_prof[16];
+#define PROF_T0() long long _pt = clock64()
+#define PROF_MARK(k)                                                          \
+    do {                                                                      \
+        if (threadIdx.x == 0) atomicAdd(&g_solve_prof[k], (unsigned long long)(clock64() - _pt)); \
+        _pt = clock64();                                                      \
+    } while (0)
+#else
+#define PROF_T0()
+#define PROF_MARK(k)
+#endif
+
+// Blocked right-looking Cholesky of the packed lower s x s matrix A, in
+// place, with blocks of 32 columns. The 32 x 32 diagonal block is factored
+// by warp 0 in registers (lane i holds row i; columns broadcast by
+// shuffles); every other thread solves one panel row against it from
+// registers (L_kk read as shared-memory broadcasts), then all threads update
+// the trailing triangle. Three block barriers per 32 columns.
+// dinv[k] receives 1 / L_kk for the triangular solves.
+__device__ void mx_cholesky(float *A, int s, int *flag, float *dinv) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    for (int k = 0; k < s; ++k) {
-        if (tid == 0) {
-            float d = A[tri_i(k, k)];
-            if (!(d > 0.f)) { *flag = 1; d = 1.f; }
-            float l = sqrtf(d);
-            A[tri_i(k, k)] = l;
-            *inv_piv = 1.f / l;
+    PROF_T0();
+    for (int k0 = 0; k0 < s; k0 += 32) {
+        const int kw = min(32, s - k0);
+        if (warp == 0) {
+            // column by column; lane i owns row k0 + i of the block
+            const int i = k0 + lane;
+            for (int k = 0; k < kw; ++k) {
+                float iv = 0.f;
+                if (lane == k) {
+                    float d = A[tri_i(i, i)];
+                    if (!(d > 0.f)) { *flag = 1; d = 1.f; }
+                    const float l = sqrtf(d);
+                    iv = 1.f / l;
+                    A[tri_i(i, i)] = l;
+                    dinv[i] = iv;
+                }
+                iv = __shfl_sync(0xffffffffu, iv, k);
+                float lik = 0.f;
+                if (lane > k && lane < kw) {
+                    lik = A[tri_i(i, k0 + k)] * iv;
+                    A[tri_i(i, k0 + k)] = lik;
+                }
+                // eight independent load-fma-store chains per step
+                float *ai = A + tri_i(i, 0) + k0;
+                for (int j0 = k + 1; j0 < kw; j0 += 8) {
+                    float lj[8], av[8];
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) lj[u] = __shfl_sync(0xffffffffu, lik, (j0 + u) & 31);
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int j = j0 + u;
+                        av[u] = (j < kw && lane >= j && lane < kw) ? ai[j] : 0.f;
+                    }
+#pragma unroll
+                    for (int u = 0; u < 8; ++u) {
+                        const int j = j0 + u;
+                        if (j < kw && lane >= j && lane < kw) ai[j] = fmaf(-lik, lj[u], av[u]);
+                    }
+                }
+                __syncwarp();
+            }
         }
         __syncthreads();
-        const float iv = *inv_piv;
-        for (int i = k + 1 + tid; i < s; i += blockDim.x) A[tri_i(i, k)] *= iv;
+        PROF_MARK(12);
+        // panel rows: L[i, k0:k0+kw] = A[i, k0:k0+kw] L_kk^{-T}, in place
+        for (int i = k0 + kw + tid; i < s; i += blockDim.x) {
+            float *ri = A + tri_i(i, 0) + k0;
+            for (int q = 0; q < kw; ++q) {
+                const float *lq = A + tri_i(k0 + q, 0) + k0;
+                float a0 = ri[q], a1 = 0.f, a2 = 0.f, a3 = 0.f;
+                int r = 0;
+                for (; r + 3 < q; r += 4) {
+                    a0 = fmaf(-ri[r], lq[r], a0);
+                    a1 = fmaf(-ri[r + 1], lq[r + 1], a1);
+                    a2 = fmaf(-ri[r + 2], lq[r + 2], a2);
+                    a3 = fmaf(-ri[r + 3], lq[r + 3], a3);
+                }
+                for (; r < q; ++r) a0 = fmaf(-ri[r], lq[r], a0);
+                ri[q] = ((a0 + a1) + (a2 + a3)) * dinv[k0 + q];
+            }
+        }
         __syncthreads();
-        for (int i = k + 1 + warp; i < s; i += nw) {
-            const float lik = A[tri_i(i, k)];
+        PROF_MARK(13);
+        // trailing update of rows/cols >= k0 + kw
+        for (int i = k0 + kw + warp; i < s; i += nw) {
+            const float *li = A + tri_i(i, 0) + k0;
             float *row = A + tri_i(i, 0);
-            for (int j = k + 1 + lane; j <= i; j += 32) row[j] = fmaf(-lik, A[tri_i(j, k)], row[j]);
+            for (int j = k0 + kw + lane; j <= i; j += 32) {
+                const float *lj = A + tri_i(j, 0) + k0;
+                float acc = 0.f;
+                for (int q = 0; q < kw; ++q) acc = fmaf(li[q], lj[q], acc);
+                row[j] -= acc;
+            }
+        }
+        __syncthreads();
+        PROF_MARK(14);
+    }
+}
+
+// Solves L L^T z = r in place (packed L from mx_cholesky, dinv = 1/diag):
+// per 32-row block, warp 0 solves the diagonal block with shuffles and all
+// threads apply the block's contribution to the remaining entries.
+__device__ void mx_chol_solve(const float *A, const float *dinv, int s, float *r) {
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    // forward: L z = r
+    for (int k0 = 0; k0 < s; k0 += 32) {
+        const int kw = min(32, s - k0);
+        if (warp == 0) {
+            const int i = k0 + lane;
+            float ri = lane < kw ? r[i] : 0.f;
+            for (int q = 0; q < kw; ++q) {
+                if (lane == q) ri *= dinv[k0 + q];
+                const float zq = __shfl_sync(0xffffffffu, ri, q);
+                if (lane > q && lane < kw) ri = fmaf(-A[tri_i(i, k0 + q)], zq, ri);
+            }
+            if (lane < kw) r[i] = ri;
+        }
+        __syncthreads();
+        for (int i = k0 + kw + tid; i < s; i += blockDim.x) {
+            const float *li = A + tri_i(i, 0) + k0;
+            float acc = 0.f;
+            for (int q = 0; q < kw; ++q) acc = fmaf(li[q], r[k0 + q], acc);
+            r[i] -= acc;
+        }
+        __syncthreads();
+    }
+    // backward: L^T x = z
+    for (int k0 = ((s - 1) / 32) * 32; k0 >= 0 && s > 0; k0 -= 32) {
+        const int kw = min(32, s - k0);
+        if (warp == 0) {
+            const int p = k0 + lane;
+            float rp = lane < kw ? r[p] : 0.f;
+            for (int q = kw - 1; q >= 0; --q) {
+                if (lane == q) rp *= dinv[k0 + q];
+                const float xq = __shfl_sync(0xffffffffu, rp, q);
+                if (lane < q) rp = fmaf(-A[tri_i(k0 + q, k0 + lane)], xq, rp);
+            }
+            if (lane < kw) r[p] = rp;
+        }
+        __syncthreads();
+        for (int p = tid; p < k0; p += blockDim.x) {
+            float acc = 0.f;
+            for (int q = 0; q < kw; ++q) acc = fmaf(A[tri_i(k0 + q, p)], r[k0 + q], acc);
+            r[p] -= acc;
         }
         __syncthreads();
     }
 }
 
-__device__ void mx_chol_solve(const float *A, int s, float *r) {
-    if (threadIdx.x < 32) {
-        const int lane = threadIdx.x;
-        for (int q = 0; q < s; ++q) {
-            float v = r[q] / A[tri_i(q, q)];
-            __syncwarp();
-            if (lane == 0) r[q] = v;
-            for (int p = q + 1 + lane; p < s; p += 32) r[p] = fmaf(-A[tri_i(p, q)], v, r[p]);
-            __syncwarp();
-        }
-        for (int q = s - 1; q >= 0; --q) {
-            float v = r[q] / A[tri_i(q, q)];
-            __syncwarp();
-            if (lane == 0) r[q] = v;
-            const float *row = A + tri_i(q, 0);
-            for (int p = lane; p < q; p += 32) r[p] = fmaf(-row[p], v, r[p]);
-            __syncwarp();
-        }
+// Compensated (double-float) accumulation: s + c carries the running sum of
+// exact fp32 products to about 2^-44 relative, using fp32 operations only
+// (TwoProduct by fma, TwoSum by Knuth).
+struct DFAcc {
+    float s = 0.f, c = 0.f;
+    __device__ __forceinline__ void add_prod(float a, float b) {
+        // explicitly rounded operations: contraction into fma would break the
+        // error-free transformations
+        const float p = __fmul_rn(a, b);
+        const float pe = fmaf(a, b, -p);
+        const float t = __fadd_rn(s, p);
+        const float bp = __fsub_rn(t, s);
+        const float err = __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+        s = t;
+        c = __fadd_rn(c, __fadd_rn(err, pe));
     }
-    __syncthreads();
-}
+    __device__ __forceinline__ double value() const { return (double)s + (double)c; }
+};
 
 __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const int32_t *boxes,
                                                             const double *centres, double *beta,
@@ -453,7 +581,8 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
     float4 *cell = sc + mc;                                 // [n_max] (x, y, z, rowmax)
     float *cinv = reinterpret_cast<float *>(cell + g.n_max);// [n_max]
     float *ce = cinv + g.n_max;                             // [n_max] y, then e = y - W x
-    float *Asm = ce + g.n_max;                              // packed factor
+    float *dinv = ce + g.n_max;                             // [mc] 1 / diag of the factor
+    float *Asm = dinv + mc;                                 // packed factor
     __shared__ MxShared sh;
 
     const float *G = w.Gf + (size_t)s * mc * mc;
@@ -477,6 +606,8 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
     }
     if (tid == 0) sh.flag = 0;
     __syncthreads();
+    PROF_T0();
+    PROF_MARK(0);
 
     // ---------------- stage 1: active-set iterations on G~ ----------------
     // Up to kMxPdasFull full primal-dual corrections; if the support still
@@ -492,23 +623,31 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
         mx_compact(sg, M, idx, &sh.cnt);
         scnt = sh.cnt;
         A = (tri_i(scnt, 0) * 4 <= kMxFactorBytes) ? Asm
-            : reinterpret_cast<float *>(w.L + (size_t)s * ((size_t)mc * (mc + 1) / 2));
+            : (w.Lf + (size_t)s * ((size_t)mc * (mc + 1) / 2));
+        PROF_MARK(8);
         for (int pp = warp; pp < scnt; pp += nw) {
             const float *Gr = G + (size_t)idx[pp] * mc;
             for (int q = lane; q <= pp; q += 32) A[tri_i(pp, q)] = Gr[idx[q]] + (q == pp ? lam2 : 0.f);
             if (lane == 0) rhs[pp] = bv[idx[pp]] - lam1 * (float)sg[idx[pp]];
         }
         __syncthreads();
-        mx_cholesky(A, scnt, &sh.flag, &sh.inv_piv);
-        if (!sh.flag) mx_chol_solve(A, scnt, rhs);
+        PROF_MARK(9);
+        mx_cholesky(A, scnt, &sh.flag, dinv);
+        PROF_MARK(10);
+        if (!sh.flag) mx_chol_solve(A, dinv, scnt, rhs);
+        PROF_MARK(11);
     };
-    auto gradient_fp = [&]() {  // gr = b - G~ x
-        for (int j = warp; j < M; j += nw) {
-            const float *Gr = G + (size_t)j * mc;
-            float acc = 0.f;
-            for (int pp = lane; pp < scnt; pp += 32) acc = fmaf(Gr[idx[pp]], x[idx[pp]], acc);
-            acc = warp_sumf(acc);
-            if (lane == 0) gr[j] = bv[j] - acc;
+    auto gradient_fp = [&]() {  // gr = b - G~ x; G~ symmetric: rows of the support, coalesced over j
+        for (int j = tid; j < M; j += blockDim.x) {
+            float acc0 = 0.f, acc1 = 0.f;
+            int pp = 0;
+            for (; pp + 1 < scnt; pp += 2) {
+                const int m0 = idx[pp], m1 = idx[pp + 1];
+                acc0 = fmaf(G[(size_t)m0 * mc + j], x[m0], acc0);
+                acc1 = fmaf(G[(size_t)m1 * mc + j], x[m1], acc1);
+            }
+            if (pp < scnt) acc0 = fmaf(G[(size_t)idx[pp] * mc + j], x[idx[pp]], acc0);
+            gr[j] = bv[j] - (acc0 + acc1);
         }
         __syncthreads();
     };
@@ -517,6 +656,7 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
     const int max_pdas = p.max_iters < kMxMaxPdas ? p.max_iters : kMxMaxPdas;
     for (; it < max_pdas; ++it) {
         factor_support();
+        PROF_MARK(1);
         if (sh.flag) break;
         if (!primal) {
             for (int j = tid; j < M; j += blockDim.x) x[j] = 0.f;
@@ -524,6 +664,7 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
             for (int pp = tid; pp < scnt; pp += blockDim.x) x[idx[pp]] = rhs[pp];
             __syncthreads();
             gradient_fp();
+            PROF_MARK(2);
             if (tid == 0) { sh.bad = 0; sh.viol = 0; }
             __syncthreads();
             int mb = 0, mv = 0;
@@ -550,6 +691,7 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
                 primal = true;
             }
             __syncthreads();
+            PROF_MARK(3);
             continue;
         }
         // primal phase: x is sign-consistent on the support; rhs = minimiser
@@ -615,18 +757,19 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
     const double *yv = w.y + (size_t)s * g.n_max;
     for (; refine_it < kMxMaxRefine && !sh.flag; ++refine_it) {
         // e = y - W x over the patch (only the support contributes); W x is
-        // accumulated and subtracted in fp64: |y| ~ 10 would otherwise leave
-        // ~1e-6 of cancellation noise in e, and W^T e inherits it
+        // accumulated in double-float and subtracted in fp64: |y| ~ 10 would
+        // otherwise leave ~1e-6 of cancellation noise in e, and W^T e inherits it
         for (int t = tid; t < N; t += blockDim.x) {
             const float4 cx = cell[t];
-            double acc = 0.0;
+            DFAcc acc;
             for (int pp = 0; pp < scnt; ++pp) {
                 const int m = idx[pp];
-                acc = fma((double)tc::ex2(logit2(sc[m], cx.x, cx.y, cx.z) - cx.w), (double)x[m], acc);
+                acc.add_prod(tc::ex2(logit2(sc[m], cx.x, cx.y, cx.z) - cx.w), x[m]);
             }
-            ce[t] = (float)(yv[t] - acc * (double)cinv[t]);
+            ce[t] = (float)(yv[t] - acc.value() * (double)cinv[t]);
         }
         __syncthreads();
+        PROF_MARK(4);
         // c_j = sum_t W_tj e_t for every centre (exact gradient of the data term)
         float cmax = 0.f;
         for (int j = tid; j < M; j += blockDim.x) {
@@ -641,6 +784,7 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
         }
         if (tid == 0) { sh.viol = 0; sh.changed = 0; sh.dmax = 0.f; sh.xmax = 0.f; }
         __syncthreads();
+        PROF_MARK(5);
         // stationarity residual on the support, violations off it
         float rmax = 0.f;
         int mv = 0;
@@ -671,13 +815,13 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
             mx_compact(sg, M, idx, &sh.cnt);
             scnt = sh.cnt;
             A = (tri_i(scnt, 0) * 4 <= kMxFactorBytes) ? Asm
-                : reinterpret_cast<float *>(w.L + (size_t)s * ((size_t)mc * (mc + 1) / 2));
+                : (w.Lf + (size_t)s * ((size_t)mc * (mc + 1) / 2));
             for (int pp = warp; pp < scnt; pp += nw) {
                 const float *Gr = G + (size_t)idx[pp] * mc;
                 for (int q = lane; q <= pp; q += 32) A[tri_i(pp, q)] = Gr[idx[q]] + (q == pp ? lam2 : 0.f);
             }
             __syncthreads();
-            mx_cholesky(A, scnt, &sh.flag, &sh.inv_piv);
+            mx_cholesky(A, scnt, &sh.flag, dinv);
             if (sh.flag) break;
         }
         // Newton correction on the support
@@ -686,7 +830,7 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
             rhs[pp] = gr[m] - lam2 * x[m] - lam1 * (float)sg[m];
         }
         __syncthreads();
-        mx_chol_solve(A, scnt, rhs);
+        mx_chol_solve(A, dinv, scnt, rhs);
         int dropped = 0;
         for (int pp = tid; pp < scnt; pp += blockDim.x) {
             const int m = idx[pp];
@@ -701,30 +845,33 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
             mx_compact(sg, M, idx, &sh.cnt);
             scnt = sh.cnt;
             A = (tri_i(scnt, 0) * 4 <= kMxFactorBytes) ? Asm
-                : reinterpret_cast<float *>(w.L + (size_t)s * ((size_t)mc * (mc + 1) / 2));
+                : (w.Lf + (size_t)s * ((size_t)mc * (mc + 1) / 2));
             for (int pp = warp; pp < scnt; pp += nw) {
                 const float *Gr = G + (size_t)idx[pp] * mc;
                 for (int q = lane; q <= pp; q += 32) A[tri_i(pp, q)] = Gr[idx[q]] + (q == pp ? lam2 : 0.f);
             }
             __syncthreads();
-            mx_cholesky(A, scnt, &sh.flag, &sh.inv_piv);
+            mx_cholesky(A, scnt, &sh.flag, dinv);
         }
     }
 
+    PROF_MARK(6);
     // final residual e = y - W x, and the indicators R_T (Eq. (4), midpoint)
     for (int t = tid; t < N; t += blockDim.x) {
         const float4 cx = cell[t];
-        double acc = 0.0;
+        DFAcc acc;
         for (int pp = 0; pp < scnt; ++pp) {
             const int m = idx[pp];
-            acc = fma((double)tc::ex2(logit2(sc[m], cx.x, cx.y, cx.z) - cx.w), (double)x[m], acc);
+            acc.add_prod(tc::ex2(logit2(sc[m], cx.x, cx.y, cx.z) - cx.w), x[m]);
         }
-        const double yhat = acc * (double)cinv[t];
+        const double yhat = acc.value() * (double)cinv[t];
         const double kv = w.kv[(size_t)s * g.n_max + t];
         const double e = exp(yhat) - kv;
         w.R[(size_t)s * g.n_max + t] = g.vol * (e * e);
     }
     for (int j = tid; j < M; j += blockDim.x) beta[(size_t)s * mc + j] = (double)x[j];
+    __syncthreads();
+    PROF_MARK(7);
     if (tid == 0) {
         int flags = inf[PAM_INFO_FLAGS] & ~(PAM_FLAG_NOT_CERTIFIED | PAM_FLAG_CHOLESKY);
         if (!certified) {
@@ -739,9 +886,19 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
 }
 
 static size_t solve_mixed_smem(const Geo &g) {
-    return (size_t)g.m_cap * (4 * sizeof(float) + 2 * sizeof(int) + sizeof(float4)) +
+    return (size_t)g.m_cap * (5 * sizeof(float) + 2 * sizeof(int) + sizeof(float4)) +
            (size_t)g.n_max * (sizeof(float4) + 2 * sizeof(float)) + kMxFactorBytes + 64;
 }
+
+#ifdef PAM_SOLVE_PROFILE
+extern "C" void pam_debug_solve_profile(unsigned long long *out, int reset) {
+    cudaMemcpyFromSymbol(out, g_solve_prof, sizeof(g_solve_prof));
+    if (reset) {
+        unsigned long long z[16] = {};
+        cudaMemcpyToSymbol(g_solve_prof, z, sizeof(z));
+    }
+}
+#endif
 
 bool mixed_solve_fits(const Geo &g) { return solve_mixed_smem(g) <= 227 * 1024; }
 
