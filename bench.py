@@ -154,14 +154,16 @@ FP64_NOMINAL_TFLOPS = 1.25
 
 
 def accounting(fit, Kd, levels, pam):
-    """Algorithmic work of one step, counted from the dictionary sizes each
-    solve actually had: Gram flops sum N_i M_i (M_i + 1) (the multiply-adds
-    of the upper triangle of the symmetric W^T W, two flops each) and
-    assembly exps sum N_i M_i over every (subdomain, solve). Runs the fit level by level
-    (outside the timed region) and reads the sizes after each level."""
-    gram, exps = 0.0, 0.0
+    """Algorithmic work of one step, counted from the sizes each solve actually
+    had (the fit is re-run level by level outside the timed region):
+      gram_flops  sum N_i M_i (M_i + 1): the multiply-adds of the upper
+                  triangle of the symmetric W^T W, two flops each;
+      pairs       sum N_i M_i: Gaussians evaluated once per (cell, centre);
+      chol_flops  sum iters * s^3 / 3 over the active-set steps (fp32 form);
+      eval_pairs  filled in by the caller (points x their owner's M)."""
+    out = dict(gram_flops=0.0, pairs=0.0, chol_flops=0.0, m_final=None)
     fit_levels = [0] + [1] * levels
-    for r, lv in enumerate(fit_levels):
+    for r, _ in enumerate(fit_levels):
         if r == 0:
             pam.pam_fit_subdomains(fit.problem, fit.params, fit.plan, Kd, fit.model, fit.workspace)
         else:
@@ -170,9 +172,58 @@ def accounting(fit, Kd, levels, pam):
         solved = info[:, pam.INFO_STOPPED] == 0 if r > 0 else np.ones(len(info), bool)
         n = info[solved, pam.INFO_N_CELLS].astype(float)
         m = info[solved, pam.INFO_M].astype(float)
-        gram += float(np.sum(n * m * (m + 1.0)))
-        exps += float(np.sum(n * m))
-    return gram, exps
+        sup = info[solved, pam.INFO_SUPPORT].astype(float)
+        iters = (info[solved, pam.INFO_ITERS] % 100).astype(float)
+        out["gram_flops"] += float(np.sum(n * m * (m + 1.0)))
+        out["pairs"] += float(np.sum(n * m))
+        out["chol_flops"] += float(np.sum(iters * sup ** 3 / 3.0))
+    out["m_final"] = fit.model.info.cpu().numpy()[:, pam.INFO_M].astype(float)
+    return out
+
+
+# Special-function-unit rate: 16 ex2 per SM per clock (4 per SM sub-partition)
+# x 152 SMs x 2.07 GHz, the roof of the exp-bound kernels.
+SFU_EX2_PER_S = 152 * 16 * 2.07e9
+# fp32 FMA rate: 128 lanes per SM x 2 flops x 152 SMs x 2.07 GHz.
+FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
+
+
+def roofline_entries(phase_ms, work, n_pts, mixed, peaks, peak_src):
+    """Roofline objects per kernel family: achieved = algorithmic work per
+    step / that family's CUDA-event time per step."""
+    r = {}
+    def t(k):
+        return phase_ms[k][0] / 1e3 if k in phase_ms else None
+    if t("gram_tc"):
+        ach = work["gram_flops"] / t("gram_tc") / 1e12
+        pk = peaks.get("bf16_tflops", 1900.0)
+        r["gram_tc"] = {"kernel": "k_gram_tc", "bound": "tensor", "achieved": ach, "peak": pk, "unit": "TFLOP/s",
+                        "frac": ach / pk, "traffic": None,
+                        "peak_source": f"bf16_tflops of {peak_src} (the kernel issues 3 bf16 products per flop pair)"}
+    if t("gram"):
+        ach = work["gram_flops"] / t("gram") / 1e12
+        r["gram"] = {"kernel": "k_gram_f64", "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS,
+                     "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None,
+                     "peak_source": "nominal GB300 fp64 dense rate"}
+    if t("stats"):
+        ach = 2.0 * work["pairs"] / t("stats")  # two passes: row maximum, then the sum
+        r["stats"] = {"kernel": "k_stats_f32", "bound": "alu", "achieved": ach / 1e12,
+                      "peak": SFU_EX2_PER_S / 1e12, "unit": "Texp/s", "frac": ach / SFU_EX2_PER_S,
+                      "traffic": None, "peak_source": "SFU ex2 16/clk/SM x 152 SMs x 2.07 GHz"}
+    if t("eval"):
+        pairs = work.get("eval_pairs")
+        if pairs:
+            ach = pairs / t("eval")
+            r["eval"] = {"kernel": "k_eval_bucket_f32" if mixed else "k_eval_bucket_f64", "bound": "alu",
+                         "achieved": ach / 1e12, "peak": SFU_EX2_PER_S / 1e12, "unit": "Texp/s",
+                         "frac": ach / SFU_EX2_PER_S, "traffic": None,
+                         "peak_source": "SFU ex2 16/clk/SM x 152 SMs x 2.07 GHz"}
+    if t("solve") and mixed:
+        ach = work["chol_flops"] / t("solve") / 1e12
+        r["solve"] = {"kernel": "k_solve_mixed", "bound": "alu", "achieved": ach, "peak": FP32_TFLOPS,
+                      "unit": "TFLOP/s", "frac": ach / FP32_TFLOPS, "traffic": None,
+                      "peak_source": "fp32 FMA 128/clk/SM x 152 SMs x 2.07 GHz; work = active-set Cholesky flops"}
+    return r
 
 
 def run_pam(args, rank, ws):
@@ -290,31 +341,38 @@ def run_pam(args, rank, ws):
                  "l1_ratio_chosen_over_plain": err["l1"] / perr["l1"]}
         del pf
 
-    # --- roofline of the dominant kernel family -----------------------------
+    # --- roofline of every kernel family, the dominant one first ------------
     peaks, peak_src = _peaks()
-    gram_flops, exps = accounting(fit, Kd, W["params"]["levels"], pam)
-    dom = max(phase_ms.items(), key=lambda kv: kv[1][0]) if phase_ms else ("none", (0.0, 0))
-    roof = None
-    if dom[0] in ("gram", "gram_tc"):
-        if prec == pam.PAM_PREC_MIXED:
-            peak = peaks.get("bf16_tflops", 1900.0)
-            ach = gram_flops / (dom[1][0] / 1e3) / 1e12
-            roof = {"kernel": "gram_tc", "bound": "tensor", "achieved": ach, "peak": peak,
-                    "unit": "TFLOP/s", "frac": ach / peak, "traffic": None,
-                    "peak_source": f"bf16_tflops of {peak_src}"}
-        else:
-            ach = gram_flops / (dom[1][0] / 1e3) / 1e12
-            roof = {"kernel": "gram_f64", "bound": "alu", "achieved": ach, "peak": FP64_NOMINAL_TFLOPS,
-                    "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None,
-                    "peak_source": "nominal GB300 FP64 dense rate"}
-    else:
-        roof = {"kernel": dom[0], "bound": "alu", "achieved": None, "peak": None, "unit": None,
-                "frac": None, "traffic": None}
+    work = accounting(fit, Kd, W["params"]["levels"], pam)
+    owners = owner_counts(W, pts)
+    work["eval_pairs"] = float(np.sum(owners * work["m_final"]))
+    roofs = roofline_entries(phase_ms, work, n_pts, prec == pam.PAM_PREC_MIXED, peaks, peak_src)
+    dom = max(phase_ms.items(), key=lambda kv: kv[1][0])[0] if phase_ms else None
+    roof = roofs.get(dom) or {"kernel": dom, "bound": None, "achieved": None, "peak": None,
+                              "unit": None, "frac": None, "traffic": None}
 
     return dict(value=value, step_ms=step_ms, times=times, err=err, phase_ms=phase_ms, launches=launches,
-                clocks=clk.summary(), e2e_s=e2e_s, h2d=h2d, d2h=d2h, plain=plain, roof=roof,
-                prec_name=prec_name, n_cells=n_cells, n_pts=n_pts, info=info, gram_flops=gram_flops,
-                exps=exps)
+                clocks=clk.summary(), e2e_s=e2e_s, h2d=h2d, d2h=d2h, plain=plain, roof=roof, roofs=roofs,
+                prec_name=prec_name, n_cells=n_cells, n_pts=n_pts, info=info)
+
+
+def owner_counts(W, pts):
+    """Target points per owner subdomain (half-open cores, outer face closed)."""
+    shape, n_sub = W["shape"], W["n_sub"]
+    nmax = max(shape)
+    idx = []
+    for a, (n, p) in enumerate(zip(shape, n_sub)):
+        i = np.minimum(np.floor(pts[:, a] * nmax).astype(np.int64), n - 1)
+        j = (i * p) // n
+        lo_next = ((j + 1) * n) // p
+        j = np.where((j + 1 < p) & (lo_next <= i), j + 1, j)
+        idx.append(j)
+    s = idx[0]
+    stride = n_sub[0]
+    for a in range(1, len(shape)):
+        s = s + stride * idx[a]
+        stride *= n_sub[a]
+    return np.bincount(s, minlength=int(np.prod(n_sub))).astype(float)
 
 
 def _mixed_available(pam):
@@ -434,6 +492,7 @@ def main():
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
         "phase_ms_per_step": {k: round(v[0], 4) for k, v in r["phase_ms"].items()},
+        "roofline_all": r["roofs"],
         "plain_fp64": r["plain"],
     }
     fit_ms = sum(v[0] for k, v in r["phase_ms"].items() if k not in ("eval", "errors"))

@@ -93,13 +93,15 @@ __global__ void __launch_bounds__(128) k_stats_f32(Geo g, const int32_t *boxes,
 // mirrored block below the strip) in fp32; threads of the strip's rows also
 // accumulate b = W^T y.
 // --------------------------------------------------------------------------
-constexpr int kTcThreads = 512;
+constexpr int kTcThreads = 1024;         // two producer threads per centre row
 constexpr int kTcKC = 32;                 // cells per chunk (2 MMA k-steps of 16)
 constexpr int kTcMaxRows = 512;           // rows of the B tile (TMEM columns)
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz
 
+// Cell data of a chunk; sh = l2* - log2(1/sum) folds the Shepard normaliser
+// into the exponent (W = 2^(alpha d^2 - sh)); sh = +inf for padding cells.
 struct TcCell {
-    float x[kTcKC], y[kTcKC], z[kTcKC], mx[kTcKC], inv[kTcKC], yv[kTcKC];
+    float x[kTcKC], y[kTcKC], z[kTcKC], sh[kTcKC], yv[kTcKC];
 };
 
 __device__ __forceinline__ void load_cells(const Geo &g, const int32_t *box, int c, int N,
@@ -107,15 +109,14 @@ __device__ __forceinline__ void load_cells(const Geo &g, const int32_t *box, int
                                            const double *yv, TcCell &cl, int lane) {
     const int t = c * kTcKC + lane;
     float x[3] = {0.f, 0.f, 0.f};
-    float mx = 0.f, iv = 0.f, y = 0.f;
+    float sh = INFINITY, y = 0.f;
     if (t < N) {
         local_cell(g, box, t, x);
-        mx = rowmax[t];
-        iv = rowinv[t];
+        sh = rowmax[t] - log2f(rowinv[t]);
         y = (float)yv[t];
     }
     cl.x[lane] = x[0]; cl.y[lane] = x[1]; cl.z[lane] = x[2];
-    cl.mx[lane] = mx; cl.inv[lane] = iv; cl.yv[lane] = y;
+    cl.sh[lane] = sh; cl.yv[lane] = y;
 }
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t *boxes,
@@ -173,7 +174,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
 
     const int nch = (N + kTcKC - 1) / kTcKC;
     const uint32_t lbo = (uint32_t)Rt * 16u, sbo = 128u;
-    const int r = tid;                              // the tile row this thread produces
+    const int r = tid & (kTcMaxRows - 1);           // the tile row this thread produces
+    const int half = tid >> 9;                      // ... for k-groups 2*half, 2*half+1
     const bool live = r < R && row0 + r < M;
     const float4 cc = r < Rt ? sc[r] : make_float4(0.f, 0.f, 0.f, 0.f);
     float bacc = 0.f;
@@ -192,15 +194,21 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
         if (r < Rt) {
             float bsum = 0.f;
 #pragma unroll
-            for (int kg = 0; kg < kTcKC / 8; ++kg) {
+            for (int kh = 0; kh < 2; ++kh) {
+                const int kg = 2 * half + kh;
                 float v[8];
+                if (live) {
 #pragma unroll
-                for (int q = 0; q < 8; ++q) {
-                    const int k = kg * 8 + q;
-                    const float e = live ? tc::ex2(logit2(cc, cl.x[k], cl.y[k], cl.z[k]) - cl.mx[k]) * cl.inv[k]
-                                         : 0.f;
-                    v[q] = e;
-                    bsum = fmaf(e, cl.yv[k], bsum);
+                    for (int q = 0; q < 8; ++q) {
+                        const int k = kg * 8 + q;
+                        const float dx = cl.x[k] - cc.x, dy = cl.y[k] - cc.y, dz = cl.z[k] - cc.z;
+                        const float e = tc::ex2(fmaf(cc.w, fmaf(dz, dz, fmaf(dy, dy, dx * dx)), -cl.sh[k]));
+                        v[q] = e;
+                        bsum = fmaf(e, cl.yv[k], bsum);
+                    }
+                } else {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) v[q] = 0.f;
                 }
                 uint32_t hp[4], lp[4];
 #pragma unroll
@@ -259,12 +267,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
         // quarter split the 32-column chunks. Rows go out through a padded
         // shared-memory transpose so that each store is one coalesced row
         // segment; the mirrored block below the strip is already coalesced.
-        float *stage = reinterpret_cast<float *>(tiles) + (size_t)warp * 32 * 33;
+        float *stage = reinterpret_cast<float *>(tiles) + (size_t)(warp & 15) * 32 * 33;
         const int lane_base = (warp & 3) * 32;
         const int rl = lane_base + lane;      // D row (TMEM lane) held by this thread
         const int rg = row0 + rl;             // its G row
         const int ncol_chunks = R / 32;
-        for (int ch = warp >> 2; ch < ncol_chunks; ch += 4) {
+        for (int ch = warp >> 2; warp < 16 && ch < ncol_chunks; ch += 4) {
             uint32_t v[32];
             tc::tmem_ld_32x32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(ch * 32), v);
             tc::tmem_wait_ld();
@@ -285,7 +293,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
             }
             __syncwarp();
         }
-        if (r < 128 && live) w.b[(size_t)s * g.m_cap + row0 + r] = (double)bacc;
+        // b = W^T y for the strip's rows: the two halves of a row add up
+        float *bh = reinterpret_cast<float *>(sc);  // the centre table is no longer needed
+        __syncthreads();
+        if (half == 1 && r < 128) bh[r] = bacc;
+        __syncthreads();
+        if (half == 0 && r < 128 && live) w.b[(size_t)s * g.m_cap + row0 + r] = (double)(bacc + bh[r]);
     }
     tc::fence_before_sync();
     __syncthreads();
