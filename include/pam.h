@@ -104,6 +104,9 @@ typedef struct {
     int levels;          /* enrichment rounds planned (sizes the capacity) */
     int max_iters;       /* active-set iteration cap per solve (0: default 64) */
     int precision;       /* pam_precision */
+    int warm_start;      /* pam_fit_subdomains: 1 = start the solve from the caller's
+                            model->beta[s][0..m0) (e.g. a learned prediction; its
+                            nonzero pattern and signs seed the active set), 0 = from 0 */
 } pam_params;
 
 /* Sizes derived from a problem and parameters by pam_plan_create. */
@@ -262,6 +265,33 @@ pam_status pam_errors(const pam_problem *prob, const pam_plan *plan,
 pam_status pam_errors_noalloc(const pam_problem *prob, const pam_plan *plan,
                               const pam_model *model, const double *d_K, double *d_err,
                               void *stream);
+
+/*
+ * Learned warm start (spec addition; the paper has no learned part).
+ * A convolutional network maps a 32 x 32 patch of log10(K)/3 to 256 support
+ * logits and 256 coefficients / 4 of the patch's 16 x 16 dictionary:
+ * conv3x3 stride 2 (1->32), (32->64), (64->128), conv3x3 stride 1 (128->128),
+ * each + ReLU, dense 2048->256 + ReLU, dense 256->512. Parameters are fp32
+ * (flat, layout from pam_nn_layer_offsets: per layer weight offset, bias
+ * offset, rows, cols, with W[row][col] and conv columns (ky*3+kx)*cin+c,
+ * zero-padded to a multiple of 32); the passes run in bf16 on the tensor
+ * cores with fp32 accumulation. batch: a multiple of 32.
+ */
+pam_status pam_nn_sizes(int batch, int64_t *n_params, size_t *workspace_bytes);
+pam_status pam_nn_layer_offsets(int64_t *h_offsets /* [6][4] */);
+/* d_x [batch][32][32] fp32; d_out [batch][512] fp32 (logits | beta/4). */
+pam_status pam_nn_forward(const float *d_params, const float *d_x, int batch, float *d_out,
+                          void *d_workspace, size_t workspace_bytes, void *stream);
+/* Forward + loss + backward: d_grads (same layout as the parameters) and
+ * d_loss [2] = (mean BCE of the support logits against d_support in {0,1},
+ * mean squared error of beta/4 against d_beta / 4), both [batch][256]. */
+pam_status pam_nn_gradients(const float *d_params, const float *d_x, const float *d_support,
+                            const float *d_beta, int batch, float *d_grads, float *d_loss,
+                            void *d_workspace, size_t workspace_bytes, void *stream);
+/* One AdamW step (decoupled weight decay) on n fp32 parameters; step >= 1. */
+pam_status pam_nn_adamw(float *d_params, const float *d_grads, float *d_m, float *d_v, int64_t n,
+                        float lr, float beta1, float beta2, float eps, float weight_decay, int step,
+                        void *stream);
 
 /*
  * Optional kernel timing. When enabled, every kernel family below records a

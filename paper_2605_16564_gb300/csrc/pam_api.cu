@@ -67,6 +67,7 @@ bool make_geo(const pam_problem *prob, const pam_params *par, Geo *g, Par *p, pa
         if (!(par->eta > 0.0 && par->eta < 1.0)) return false;
         if (std::isnan(par->eps_tol_rel)) return false;
         if (par->k_top < 0 || par->m_max < 0 || par->levels < 0 || par->max_iters < 0) return false;
+        if (par->warm_start != 0 && par->warm_start != 1) return false;
         if (par->precision != PAM_PREC_FP64 && par->precision != PAM_PREC_MIXED) return false;
         int64_t add = (int64_t)par->levels * (g->dim + 1) * par->k_top;
         if (add > par->m_max) add = par->m_max;
@@ -291,7 +292,8 @@ pam_status pam_fit_subdomains(const pam_problem *prob, const pam_params *par, co
     int32_t hs[8];
     if ((st = read_status(w, s, hs)) != PAM_OK) return st;
     if (hs[kStBadK]) return PAM_ERR_NONPOSITIVE_K;
-    launch_init_dictionary(g, model->boxes, model->centres, model->beta, model->info, s);
+    launch_init_dictionary(g, model->boxes, model->centres, model->beta, model->info, s,
+                           par->warm_start != 0);
     if (par->precision == PAM_PREC_MIXED)
         launch_solve_level_mixed(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
     else

@@ -90,7 +90,7 @@ void launch_prepare(const Geo &g, const int32_t *boxes, const double *K, const W
 // box, cell-centred, sigma = the lattice spacing (largest over the axes).
 // --------------------------------------------------------------------------
 __global__ void k_init_dictionary(Geo g, const int32_t *boxes, double *centres, double *beta,
-                                  int32_t *info) {
+                                  int32_t *info, int keep_beta) {
     int s = blockIdx.y;
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t *box = boxes + s * 12;
@@ -111,7 +111,8 @@ __global__ void k_init_dictionary(Geo g, const int32_t *boxes, double *centres, 
         } else {
             c[0] = c[1] = c[2] = c[3] = 0.0;
         }
-        beta[(size_t)s * g.m_cap + m] = 0.0;
+        // a warm start keeps the caller's coefficients of the initial lattice
+        if (!keep_beta || m >= g.m0) beta[(size_t)s * g.m_cap + m] = 0.0;
     }
     if (m == 0) {
         int ext[3];
@@ -129,9 +130,9 @@ __global__ void k_init_dictionary(Geo g, const int32_t *boxes, double *centres, 
 }
 
 void launch_init_dictionary(const Geo &g, const int32_t *boxes, double *centres, double *beta,
-                            int32_t *info, cudaStream_t st) {
+                            int32_t *info, cudaStream_t st, int keep_beta) {
     dim3 grid((g.m_cap + 127) / 128, g.S);
-    k_init_dictionary<<<grid, 128, 0, st>>>(g, boxes, centres, beta, info);
+    k_init_dictionary<<<grid, 128, 0, st>>>(g, boxes, centres, beta, info, keep_beta);
     count_launches(1);
 }
 

@@ -68,7 +68,7 @@ bool make_geo(const pam_problem *prob, const pam_params *par, Geo *g, Par *p, pa
 void launch_partition(const Geo &g, int32_t *boxes, cudaStream_t st);
 void launch_prepare(const Geo &g, const int32_t *boxes, const double *K, const Ws &w, cudaStream_t st);
 void launch_init_dictionary(const Geo &g, const int32_t *boxes, double *centres, double *beta,
-                            int32_t *info, cudaStream_t st);
+                            int32_t *info, cudaStream_t st, int keep_beta);
 void launch_solve_level_f64(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
                             double *beta, int32_t *info, const Ws &w, cudaStream_t st);
 void launch_stats_gram_tc(const Geo &g, const int32_t *boxes, const double *centres,

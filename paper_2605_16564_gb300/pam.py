@@ -49,7 +49,7 @@ class pam_params(C.Structure):
     _fields_ = [("lambda1_hat", C.c_double), ("lambda2_hat", C.c_double),
                 ("eps_tol_rel", C.c_double), ("eta", C.c_double), ("k_top", C.c_int),
                 ("m_max", C.c_int), ("levels", C.c_int), ("max_iters", C.c_int),
-                ("precision", C.c_int)]
+                ("precision", C.c_int), ("warm_start", C.c_int)]
 
 
 class pam_plan(C.Structure):
@@ -90,6 +90,17 @@ def lib():
                                  C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_gram.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), C.c_void_p, P(pam_model),
                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_nn_sizes.argtypes = [C.c_int, P(C.c_int64), P(C.c_size_t)]
+        L.pam_nn_layer_offsets.argtypes = [C.c_void_p]
+        L.pam_nn_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t,
+                                     C.c_void_p]
+        L.pam_nn_gradients.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
+                                       C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_nn_adamw.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float,
+                                   C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, C.c_void_p]
+        for name in ("pam_nn_sizes", "pam_nn_layer_offsets", "pam_nn_forward", "pam_nn_gradients",
+                     "pam_nn_adamw"):
+            getattr(L, name).restype = C.c_int
         L.pam_errors_noalloc.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p,
                                          C.c_void_p, C.c_void_p]
         for name in ("pam_plan_create", "pam_partition", "pam_fit_subdomains", "pam_refine",
@@ -128,8 +139,9 @@ def make_problem(n_cells, n_sub, overlap, g_init):
 
 
 def make_params(lambda1_hat=4.59e-4, lambda2_hat=4.64e-6, eps_tol_rel=1e-3, eta=0.5, k_top=37,
-                m_max=1 << 30, levels=3, max_iters=0, precision=PAM_PREC_FP64):
+                m_max=1 << 30, levels=3, max_iters=0, precision=PAM_PREC_FP64, warm_start=0):
     p = pam_params()
+    p.warm_start = warm_start
     p.lambda1_hat, p.lambda2_hat, p.eps_tol_rel, p.eta = lambda1_hat, lambda2_hat, eps_tol_rel, eta
     p.k_top, p.m_max, p.levels, p.max_iters, p.precision = k_top, min(m_max, (1 << 31) - 1), levels, \
         max_iters, precision
@@ -206,6 +218,35 @@ def pam_errors_noalloc(problem, plan, model, K, err, stream=None):
     its scratch is a fixed 256 KiB array inside the library."""
     _check(lib().pam_errors_noalloc(C.byref(problem), C.byref(plan), C.byref(model.c_struct()),
                                     _ptr(K), _ptr(err), _stream(stream)), "pam_errors_noalloc")
+
+
+def pam_nn_sizes(batch):
+    n, ws = C.c_int64(0), C.c_size_t(0)
+    _check(lib().pam_nn_sizes(int(batch), C.byref(n), C.byref(ws)), "pam_nn_sizes")
+    return n.value, ws.value
+
+
+def pam_nn_layer_offsets():
+    off = np.zeros(24, dtype=np.int64)
+    _check(lib().pam_nn_layer_offsets(off.ctypes.data), "pam_nn_layer_offsets")
+    return off.reshape(6, 4)
+
+
+def pam_nn_forward(params, x, out, workspace, stream=None):
+    _check(lib().pam_nn_forward(_ptr(params), _ptr(x), int(x.shape[0]), _ptr(out), _ptr(workspace),
+                                workspace.numel(), _stream(stream)), "pam_nn_forward")
+
+
+def pam_nn_gradients(params, x, support, beta, grads, loss, workspace, stream=None):
+    _check(lib().pam_nn_gradients(_ptr(params), _ptr(x), _ptr(support), _ptr(beta), int(x.shape[0]),
+                                  _ptr(grads), _ptr(loss), _ptr(workspace), workspace.numel(),
+                                  _stream(stream)), "pam_nn_gradients")
+
+
+def pam_nn_adamw(params, grads, m, v, lr, beta1, beta2, eps, weight_decay, step, stream=None):
+    _check(lib().pam_nn_adamw(_ptr(params), _ptr(grads), _ptr(m), _ptr(v), int(params.numel()),
+                              float(lr), float(beta1), float(beta2), float(eps), float(weight_decay),
+                              int(step), _stream(stream)), "pam_nn_adamw")
 
 
 # ------------------------------------------------------------------ helpers --
