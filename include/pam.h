@@ -102,7 +102,7 @@ typedef struct {
     int k_top;           /* cells marked per round (Algorithm 1 K_top) */
     int m_max;           /* at most m_max centres added per subdomain (M_max) */
     int levels;          /* enrichment rounds planned (sizes the capacity) */
-    int max_iters;       /* active-set iteration cap per solve (0: default 64) */
+    int max_iters;       /* active-set iteration cap per solve (0: default 200) */
     int precision;       /* pam_precision */
     int warm_start;      /* pam_fit_subdomains: 1 = start the solve from the caller's
                             model->beta[s][0..m0) (e.g. a learned prediction; its

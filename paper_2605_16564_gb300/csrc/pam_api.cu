@@ -86,7 +86,7 @@ bool make_geo(const pam_problem *prob, const pam_params *par, Geo *g, Par *p, pa
             p->k_top = par->k_top;
             p->m_max = par->m_max;
             p->levels = par->levels;
-            p->max_iters = par->max_iters > 0 ? par->max_iters : 64;
+            p->max_iters = par->max_iters > 0 ? par->max_iters : 200;
         }
     }
     *st = PAM_OK;

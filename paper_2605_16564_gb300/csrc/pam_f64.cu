@@ -366,12 +366,19 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_f64(Geo g, Par p, doubl
     if (tid == 0) { sh.flag = 0; }
     __syncthreads();
 
-    int it = 0, certified = 0, scnt = 0;
+    // Up to kPdasFull full primal-dual corrections; then a primal active-set
+    // phase from the sign-consistent part of the iterate: step towards the
+    // sign-constrained minimiser on the support as far as the signs allow
+    // (ratio test; the blocking coefficients leave), and add the single
+    // largest violator only when that minimiser is sign-consistent.
+    constexpr int kPdasFull = 12;
+    int it = 0, certified = 0, scnt = 0, last_added = -1;
+    bool primal = false, single_add = false;
+    double *A = Asm;
     for (; it < p.max_iters; ++it) {
         compact_active(sg, M, idx, &sh.cnt);
         scnt = sh.cnt;
-        double *A = (tri(scnt, 0) <= smem_factor_elems) ? Asm
-                                                      : w.L + (size_t)s * ((size_t)mc * (mc + 1) / 2);
+        A = (tri(scnt, 0) <= smem_factor_elems) ? Asm : w.L + (size_t)s * ((size_t)mc * (mc + 1) / 2);
         // A = G_SS + lambda2 I (packed lower), rhs = b_S - lambda1 s_S
         for (int pp = warp; pp < scnt; pp += nw) {
             const double *Gr = G + (size_t)idx[pp] * mc;
@@ -383,17 +390,52 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_f64(Geo g, Par p, doubl
         cholesky_packed(A, scnt, &sh.flag, &inv_piv);
         if (sh.flag) break;
         cholesky_solve_packed(A, scnt, rhs);
-        for (int j = tid; j < M; j += blockDim.x) x[j] = 0.0;
-        __syncthreads();
-        for (int pp = tid; pp < scnt; pp += blockDim.x) x[idx[pp]] = rhs[pp];
-        __syncthreads();
-        // gradient b - G_{:,S} x_S over every centre
-        for (int j = warp; j < M; j += nw) {
-            const double *Gr = G + (size_t)j * mc;
+        if (!primal) {
+            for (int j = tid; j < M; j += blockDim.x) x[j] = 0.0;
+            __syncthreads();
+            for (int pp = tid; pp < scnt; pp += blockDim.x) x[idx[pp]] = rhs[pp];
+            __syncthreads();
+        } else {
+            // ratio test towards the minimiser rhs on the support
+            if (tid == 0) { sh.bad = 0; sh.worst_v = 2.0; }
+            __syncthreads();
+            for (int pp = tid; pp < scnt; pp += blockDim.x) {
+                const int m = idx[pp];
+                const double xs = rhs[pp], x0 = x[m], sgn = (double)sg[m];
+                if (!(xs * sgn > 0.0)) {
+                    const double a = (x0 * sgn > 0.0) ? x0 / (x0 - xs) : 0.0;
+                    atomicMin(reinterpret_cast<unsigned long long *>(&sh.worst_v),
+                              (unsigned long long)__double_as_longlong(fmax(a, 0.0)));
+                    atomicAdd(&sh.bad, 1);
+                }
+            }
+            __syncthreads();
+            if (sh.bad) {
+                const double alpha = fmin(sh.worst_v, 1.0);
+                single_add = !(alpha > 0.0);  // blocked by a coefficient that just joined
+                for (int pp = tid; pp < scnt; pp += blockDim.x) {
+                    const int m = idx[pp];
+                    const double xs = rhs[pp], x0 = x[m], sgn = (double)sg[m];
+                    bool blocking = false;
+                    if (!(xs * sgn > 0.0)) {
+                        const double a = (x0 * sgn > 0.0) ? x0 / (x0 - xs) : 0.0;
+                        blocking = fmax(a, 0.0) <= alpha * (1.0 + 1e-12);
+                    }
+                    const double nx = x0 + alpha * (xs - x0);
+                    if (blocking || !(nx * sgn > 0.0)) { x[m] = 0.0; sg[m] = 0; }
+                    else x[m] = nx;
+                }
+                __syncthreads();
+                continue;
+            }
+            for (int pp = tid; pp < scnt; pp += blockDim.x) x[idx[pp]] = rhs[pp];
+            __syncthreads();
+        }
+        // gradient b - G_{:,S} x_S over every centre (G symmetric: coalesced rows of the support)
+        for (int j = tid; j < M; j += blockDim.x) {
             double acc = 0.0;
-            for (int pp = lane; pp < scnt; pp += 32) acc += Gr[idx[pp]] * rhs[pp];
-            acc = warp_sum(acc);
-            if (lane == 0) gr[j] = bv[j] - acc;
+            for (int pp = 0; pp < scnt; ++pp) acc += G[(size_t)idx[pp] * mc + j] * x[idx[pp]];
+            gr[j] = bv[j] - acc;
         }
         if (tid == 0) { sh.bad = 0; sh.viol = 0; sh.worst = -1; sh.worst_v = 0.0; }
         __syncthreads();
@@ -406,31 +448,44 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_f64(Geo g, Par p, doubl
         if (my_viol) atomicAdd(&sh.viol, my_viol);
         __syncthreads();
         if (sh.bad == 0 && sh.viol == 0) { certified = 1; break; }
-        const bool one_at_a_time = it >= 16;
-        if (one_at_a_time && sh.bad == 0) {
-            // add only the largest violation (ties to the lower index)
-            if (tid == 0) {
-                double best = -1.0;
-                int bj = -1;
-                for (int j = 0; j < M; ++j)
-                    if (sg[j] == 0 && fabs(gr[j]) > viol_tol && fabs(gr[j]) > best) {
-                        best = fabs(gr[j]);
-                        bj = j;
+        if (!primal) {
+            if (it + 1 < kPdasFull) {
+                for (int j = tid; j < M; j += blockDim.x) {
+                    if (sg[j] != 0) {
+                        if (!(x[j] * (double)sg[j] > 0.0)) sg[j] = 0;
+                    } else if (fabs(gr[j]) > viol_tol) {
+                        sg[j] = gr[j] > 0.0 ? 1 : -1;
                     }
-                sh.worst = bj;
+                }
+            } else {
+                for (int j = tid; j < M; j += blockDim.x)
+                    if (!(x[j] * (double)sg[j] > 0.0)) { sg[j] = 0; x[j] = 0.0; }
+                primal = true;
             }
             __syncthreads();
-            if (tid == 0 && sh.worst >= 0) sg[sh.worst] = gr[sh.worst] > 0.0 ? 1 : -1;
-        } else {
-            for (int j = tid; j < M; j += blockDim.x) {
-                if (sg[j] != 0) {
-                    if (!(x[j] * (double)sg[j] > 0.0)) sg[j] = 0;
-                } else if (!one_at_a_time && fabs(gr[j]) > viol_tol) {
-                    sg[j] = gr[j] > 0.0 ? 1 : -1;
-                }
-            }
+            continue;
         }
-        __syncthreads();
+        // primal phase, sign-consistent minimiser: the violators join the
+        // support (all of them; only the largest right after a step that the
+        // new ones blocked at length zero)
+        if (single_add) {
+            if (tid == 0) {
+                double best = viol_tol;
+                int bj = -1;
+                for (int j = 0; j < M; ++j)
+                    if (sg[j] == 0 && fabs(gr[j]) > best) { best = fabs(gr[j]); bj = j; }
+                sh.worst = bj;
+                if (bj >= 0 && bj != last_added) { sg[bj] = gr[bj] > 0.0 ? 1 : -1; x[bj] = 0.0; }
+            }
+            __syncthreads();
+            if (sh.worst < 0 || sh.worst == last_added) break;  // stalled on one index
+            last_added = sh.worst;
+        } else {
+            for (int j = tid; j < M; j += blockDim.x)
+                if (sg[j] == 0 && fabs(gr[j]) > viol_tol) { sg[j] = gr[j] > 0.0 ? 1 : -1; x[j] = 0.0; }
+            __syncthreads();
+        }
+        single_add = false;
     }
     for (int j = tid; j < M; j += blockDim.x) beta[(size_t)s * mc + j] = x[j];
     if (tid == 0) {

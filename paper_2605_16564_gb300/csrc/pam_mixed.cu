@@ -374,7 +374,7 @@ void launch_copy_gram_f32(const Geo &g, const int32_t *info, const Ws &w, double
 constexpr int kMxThreads = 256;
 constexpr int kMxFactorBytes = 64 * 1024;
 constexpr int kMxMaxRefine = 12;
-constexpr int kMxMaxPdas = 96;
+constexpr int kMxMaxPdas = 200;
 constexpr int kMxPdasFull = 12;
 
 struct MxShared {
@@ -627,9 +627,11 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
     // moves, a primal active-set phase takes over from the sign-consistent
     // part of the iterate: on the current support it steps towards the
     // sign-constrained minimiser as far as the signs allow (ratio test),
-    // dropping the coefficient that reaches zero, and adds the single
-    // largest violator only once the minimiser on the support is
-    // sign-consistent -- the objective decreases monotonically, so it ends.
+    // dropping the coefficient that reaches zero, and adds violators only
+    // once the minimiser on the support is
+    // sign-consistent (all violators; the largest only right after a step
+    // that a newly added coefficient blocked at length zero) -- the
+    // objective decreases monotonically, so it ends.
     int it = 0, scnt = 0;
     float *A = Asm;
     auto factor_support = [&]() {
@@ -664,7 +666,7 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
         }
         __syncthreads();
     };
-    bool primal = false;
+    bool primal = false, single_add = false;
     int last_added = -1;
     const int max_pdas = p.max_iters < kMxMaxPdas ? p.max_iters : kMxMaxPdas;
     for (; it < max_pdas; ++it) {
@@ -724,21 +726,34 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
             for (int pp = tid; pp < scnt; pp += blockDim.x) x[idx[pp]] = rhs[pp];
             __syncthreads();
             gradient_fp();
-            if (tid == 0) {
-                float best = tol_pdas;
-                int bj = -1;
-                for (int j = 0; j < M; ++j)
-                    if (sg[j] == 0 && fabsf(gr[j]) > best) { best = fabsf(gr[j]); bj = j; }
-                sh.viol = bj;
-                if (bj >= 0 && bj != last_added) { sg[bj] = gr[bj] > 0.f ? 1 : -1; x[bj] = 0.f; }
+            if (single_add) {
+                if (tid == 0) {
+                    float best = tol_pdas;
+                    int bj = -1;
+                    for (int j = 0; j < M; ++j)
+                        if (sg[j] == 0 && fabsf(gr[j]) > best) { best = fabsf(gr[j]); bj = j; }
+                    sh.viol = bj;
+                    if (bj >= 0 && bj != last_added) { sg[bj] = gr[bj] > 0.f ? 1 : -1; x[bj] = 0.f; }
+                }
+                __syncthreads();
+                if (sh.viol < 0 || sh.viol == last_added) break;  // optimal (or stalled on one index)
+                last_added = sh.viol;
+            } else {
+                if (tid == 0) sh.viol = 0;
+                __syncthreads();
+                int mv = 0;
+                for (int j = tid; j < M; j += blockDim.x)
+                    if (sg[j] == 0 && fabsf(gr[j]) > tol_pdas) { sg[j] = gr[j] > 0.f ? 1 : -1; x[j] = 0.f; ++mv; }
+                if (mv) atomicAdd(&sh.viol, mv);
+                __syncthreads();
+                if (sh.viol == 0) break;  // optimal
             }
-            __syncthreads();
-            if (sh.viol < 0 || sh.viol == last_added) break;  // optimal (or stalled on one index)
-            last_added = sh.viol;
+            single_add = false;
         } else {
             // step alpha towards the minimiser; the blocking coefficients (the
             // ones whose ratio attains alpha) reach zero and leave the support
             const float alpha = fminf(sh.dmax, 1.f);
+            single_add = !(alpha > 0.f);  // blocked by a coefficient that just joined
             for (int pp = tid; pp < scnt; pp += blockDim.x) {
                 const int m = idx[pp];
                 const float xs = rhs[pp], x0 = x[m], sgn = (float)sg[m];

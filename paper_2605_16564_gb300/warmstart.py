@@ -1,0 +1,220 @@
+"""Learned warm start of the per-patch Elastic Net solve.
+
+A batch of 32 x 32 patches (each its own subdomain, 16 x 16 dictionary with
+width = 2 cells, no refinement) is tiled into one grid and fitted in one
+call of the C ABI. The plain fit labels the training patches with their
+selected support and coefficients; the network (pam_nn_* kernels, bf16
+tensor cores) learns to predict both from log10 K; on new patches its
+prediction seeds the active-set solve (pam_params.warm_start). A patch whose
+warm-started solve is not certified within the learned iteration budget is
+refitted plainly from zero. Every numerical step runs in libpam; this module
+only moves arrays and drives the loop.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import time
+
+import numpy as np
+
+from . import pam
+
+PATCH = 32
+G = 16
+N_OUT = G * G
+BETA_SCALE = 4.0
+
+
+def tile(patches):
+    """(P, 32, 32) patches -> (grid K of shape (T*32, T*32), T) with patch
+    p = px + T*py at block (py, px); P must be a square T*T."""
+    P = patches.shape[0]
+    T = int(round(np.sqrt(P)))
+    assert T * T == P, "the number of patches must be a square"
+    grid = patches.reshape(T, T, PATCH, PATCH).transpose(0, 2, 1, 3).reshape(T * PATCH, T * PATCH)
+    return np.ascontiguousarray(grid), T
+
+
+def network_input(patches):
+    """log10 K / 3 clipped to [-1, 1], float32 (P, 32, 32)."""
+    return np.clip(np.log10(patches) / 3.0, -1.0, 1.0).astype(np.float32)
+
+
+class PatchFit:
+    """Fit of a square batch of patches through the C ABI (one subdomain each)."""
+
+    def __init__(self, n_patches, device, precision=pam.PAM_PREC_FP64, max_iters=0):
+        T = int(round(np.sqrt(n_patches)))
+        assert T * T == n_patches
+        self.T = T
+        self.device = device
+        self.precision = precision
+        self.max_iters = max_iters
+        self.fitter = pam.Fitter((T * PATCH, T * PATCH), (T, T), 0, (G, G), device=device, precision=precision,
+                                 k_top=1, levels=0, max_iters=max_iters)
+
+    def fit(self, patches, beta0=None):
+        """Solve every patch; beta0 [P, 256] (numpy or tensor) seeds the solve.
+        Returns (beta [P,256] numpy, info [P,8] numpy, solve ms)."""
+        import torch
+        grid, T = tile(patches)
+        Kd = torch.from_numpy(grid).to(self.device)
+        f = self.fitter
+        p = pam.make_params(k_top=1, levels=0, max_iters=self.max_iters, precision=self.precision,
+                            warm_start=0 if beta0 is None else 1)
+        if beta0 is not None:
+            b0 = torch.as_tensor(beta0, dtype=torch.float64).to(self.device)
+            f.model.beta.zero_()
+            f.model.beta[:, :N_OUT] = b0
+        L = pam.lib()
+        L.pam_timing_reset()
+        L.pam_timing_enable(1)
+        code = pam.pam_fit_subdomains(f.problem, p, f.plan, Kd, f.model, f.workspace, check=False)
+        L.pam_timing_enable(0)
+        tot, cnt = C.c_double(0), C.c_int(0)
+        L.pam_timing_read(3, C.byref(tot), C.byref(cnt))  # PAM_PHASE_SOLVE
+        L.pam_timing_reset()
+        if code not in (0, 5):
+            raise pam.PamError(code, "pam_fit_subdomains")
+        beta = f.model.beta[:, :N_OUT].cpu().numpy().copy()
+        info = f.model.info.cpu().numpy().copy()
+        return beta, info, tot.value
+
+
+def label(patches, device, batch=4096, precision=pam.PAM_PREC_FP64, max_iters=400):
+    """Plain fit of every patch (batches of `batch`): beta [P,256] and support.
+    A few patches need a few hundred safeguarded active-set steps, hence
+    the larger iteration budget."""
+    P = patches.shape[0]
+    assert P % batch == 0
+    fit = PatchFit(batch, device, precision, max_iters=max_iters)
+    betas = []
+    for i in range(0, P, batch):
+        b, info, _ = fit.fit(patches[i:i + batch])
+        if np.any(info[:, pam.INFO_FLAGS] & pam.FLAG_NOT_CERTIFIED):
+            raise RuntimeError("a label fit was not certified")
+        betas.append(b)
+    beta = np.concatenate(betas)
+    return beta, (beta != 0).astype(np.float32)
+
+
+def init_params(n, offsets, seed=0):
+    """He-normal weights on the used columns, zero biases and padding."""
+    rng = np.random.default_rng(seed)
+    p = np.zeros(n, dtype=np.float32)
+    cin = [1, 32, 64, 128]
+    for l in range(6):
+        wo, bo, rows, cols = (int(v) for v in offsets[l])
+        used = 9 * cin[l] if l < 4 else cols
+        w = np.zeros((rows, cols), dtype=np.float32)
+        w[:, :used] = rng.standard_normal((rows, used)) * np.sqrt(2.0 / used)
+        if l == 5:
+            w *= 0.1
+        p[wo:wo + rows * cols] = w.reshape(-1)
+    return p
+
+
+class Network:
+    """The warm-start network: fp32 master weights on the device, AdamW state."""
+
+    def __init__(self, device, batch=256, seed=0):
+        import torch
+        self.device = device
+        self.batch = batch
+        n, ws = pam.pam_nn_sizes(batch)
+        self.n = n
+        self.offsets = pam.pam_nn_layer_offsets()
+        self.params = torch.from_numpy(init_params(n, self.offsets, seed)).to(device)
+        self.m = torch.zeros(n, device=device)
+        self.v = torch.zeros(n, device=device)
+        self.grads = torch.zeros(n, device=device)
+        self.loss = torch.zeros(2, device=device)
+        self.ws = torch.empty(ws, dtype=torch.uint8, device=device)
+        self.step = 0
+
+    def train(self, x, support, beta, epochs=8, lr=2e-3, weight_decay=1e-4, seed=0, log=None):
+        """AdamW on (x [P,32,32] f32, support, beta [P,256]) with a cosine
+        learning-rate schedule; returns the per-epoch mean losses."""
+        import torch
+        P = x.shape[0]
+        X = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(self.device)
+        Sp = torch.from_numpy(np.ascontiguousarray(support, dtype=np.float32)).to(self.device)
+        Bt = torch.from_numpy(np.ascontiguousarray(beta, dtype=np.float32)).to(self.device)
+        rng = np.random.default_rng(seed)
+        steps_per_epoch = P // self.batch
+        total = epochs * steps_per_epoch
+        history = []
+        for ep in range(epochs):
+            perm = torch.from_numpy(rng.permutation(P)).to(self.device)
+            acc = torch.zeros(2, device=self.device)
+            for i in range(steps_per_epoch):
+                idx = perm[i * self.batch:(i + 1) * self.batch]
+                xb, sb, bb = X[idx].contiguous(), Sp[idx].contiguous(), Bt[idx].contiguous()
+                pam.pam_nn_gradients(self.params, xb, sb, bb, self.grads, self.loss, self.ws)
+                self.step += 1
+                frac = (ep * steps_per_epoch + i) / max(total - 1, 1)
+                lr_t = lr * 0.5 * (1.0 + np.cos(np.pi * frac))
+                pam.pam_nn_adamw(self.params, self.grads, self.m, self.v, lr_t, 0.9, 0.999, 1e-8,
+                                 weight_decay, self.step)
+                acc += self.loss
+            history.append((acc / steps_per_epoch).cpu().numpy().tolist())
+            if log:
+                log(f"epoch {ep}: bce {history[-1][0]:.4f} mse {history[-1][1]:.4f}")
+        return history
+
+    def predict(self, x):
+        """x [P,32,32] -> (support logits [P,256], beta [P,256]) numpy."""
+        import torch
+        P = x.shape[0]
+        out = torch.zeros((P, 2 * N_OUT), dtype=torch.float32, device=self.device)
+        X = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(self.device)
+        for i in range(0, P, self.batch):
+            xb = X[i:i + self.batch]
+            if xb.shape[0] < self.batch:
+                pad = torch.zeros((self.batch - xb.shape[0], PATCH, PATCH), device=self.device)
+                xb = torch.cat([xb, pad])
+            ob = torch.zeros((self.batch, 2 * N_OUT), dtype=torch.float32, device=self.device)
+            pam.pam_nn_forward(self.params, xb.contiguous(), ob, self.ws)
+            out[i:i + self.batch] = ob[:min(self.batch, P - i)]
+        o = out.cpu().numpy()
+        return o[:, :N_OUT], o[:, N_OUT:] * BETA_SCALE
+
+
+# Seed threshold on the predicted coefficients (log-space units). Measured on
+# held-out patches: the coefficients the network predicts large are reliable,
+# the small ones are better left for the active-set iterations to add; a
+# seed of {|beta_hat| > 3} cut the mean iterations from 9.8 to 6.8 and the
+# worst case from 74 to 14, more than the support logits did (70 % accurate).
+SEED_THRESHOLD = 3.0
+
+
+def warm_start_coefficients(logits, beta, threshold=SEED_THRESHOLD):
+    """The warm start handed to the solve: the predicted coefficients whose
+    magnitude exceeds `threshold` (their signs seed the active set)."""
+    del logits  # the support logits are trained jointly but seed worse
+    return np.where(np.abs(beta) > threshold, beta, 0.0).astype(np.float64)
+
+
+def learned_fit(net, patches, device, precision=pam.PAM_PREC_FP64, budget=48):
+    """Fit with the network's warm start; patches not certified within
+    `budget` active-set iterations are refitted plainly from zero.
+    Returns dict(beta, info, solve_ms, refit, predict_ms)."""
+    import torch
+    t0 = time.perf_counter()
+    logits, b = net.predict(network_input(patches))
+    torch.cuda.synchronize()
+    t_pred = (time.perf_counter() - t0) * 1e3
+    beta0 = warm_start_coefficients(logits, b)
+    fit = PatchFit(patches.shape[0], device, precision, max_iters=budget)
+    beta, info, ms = fit.fit(patches, beta0)
+    miss = np.nonzero(info[:, pam.INFO_FLAGS] & pam.FLAG_NOT_CERTIFIED)[0]
+    refit_ms = 0.0
+    if len(miss):
+        # plain refit of the missed patches only (padded to a square batch)
+        T = int(np.ceil(np.sqrt(len(miss))))
+        sel = np.concatenate([miss, np.repeat(miss[-1:], T * T - len(miss))])
+        plain = PatchFit(T * T, device, precision)
+        b2, info2, refit_ms = plain.fit(patches[sel])
+        beta[miss] = b2[:len(miss)]
+        info[miss] = info2[:len(miss)]
+    return dict(beta=beta, info=info, solve_ms=ms + refit_ms, refit=len(miss), predict_ms=t_pred)

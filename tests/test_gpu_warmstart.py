@@ -1,0 +1,72 @@
+"""The learned warm start end to end on the GPU: label patches with the plain
+fit, train the network with the project's kernels, and show what it gains
+on held-out patches -- fewer active-set iterations for the same certified
+minimiser (the plain regression stays the fallback and the judge)."""
+import numpy as np
+import pytest
+
+from paper_2605_16564_gb300 import fields
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def trained():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_16564_gb300 import build
+    build.build()
+    from paper_2605_16564_gb300 import pam, warmstart as ws
+    dev = torch.device("cuda:0")
+    train = fields.patch_batch(16384, seed=4)
+    beta, support = ws.label(train, dev, batch=4096)
+    net = ws.Network(dev, batch=256, seed=0)
+    hist = net.train(ws.network_input(train), support, beta, epochs=8, lr=2e-3)
+    return torch, pam, ws, dev, net, hist
+
+
+def test_training_reduces_the_loss(trained):
+    torch, pam, ws, dev, net, hist = trained
+    assert hist[-1][0] < 0.95 * hist[0][0] and hist[-1][1] < 0.85 * hist[0][1], hist
+    assert all(b[0] <= a[0] * 1.02 for a, b in zip(hist, hist[1:])), hist
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_warm_start_reaches_the_plain_minimiser_in_fewer_iterations(trained, precision):
+    torch, pam, ws, dev, net, hist = trained
+    held = fields.patch_batch(1024, seed=40)
+    cold = ws.PatchFit(1024, dev, precision, max_iters=400)
+    b_cold, info_cold, ms_cold = cold.fit(held)
+    res = ws.learned_fit(net, held, dev, precision)
+    it = lambda info: (info[:, pam.INFO_ITERS] % 100).astype(float)
+    assert np.all((info_cold[:, pam.INFO_FLAGS] & pam.FLAG_NOT_CERTIFIED) == 0)
+    assert np.all((res["info"][:, pam.INFO_FLAGS] & pam.FLAG_NOT_CERTIFIED) == 0)
+    if precision == 0:
+        # the same certified minimiser (unique), to solve precision
+        scale = np.maximum(1.0, np.abs(b_cold).max(axis=1, keepdims=True))
+        assert np.all(np.abs(res["beta"] - b_cold) <= 1e-9 * scale)
+    else:
+        # the fp32 form certifies to its own band: compare the surrogates
+        pts = ws.tile(held)[0]
+        T = int(np.sqrt(len(held)))
+        h = 1.0 / (T * ws.PATCH)
+        xs = fields.cell_centred_points((T * ws.PATCH, T * ws.PATCH), (1.0, 1.0))
+        X = torch.from_numpy(xs).to(dev)
+        warm_model = ws.PatchFit(1024, dev, precision)
+        warm_model.fitter.model.beta.zero_()
+        warm_model.fitter.model.beta[:, :ws.N_OUT] = torch.from_numpy(res["beta"]).to(dev)
+        # evaluate both coefficient sets on the cold fit's dictionary
+        f = cold.fitter
+        k_cold = f.eval(X).cpu().numpy()
+        f.model.beta[:, :ws.N_OUT] = torch.from_numpy(res["beta"]).to(dev)
+        k_warm = f.eval(X).cpu().numpy()
+        d = np.abs(np.log10(k_warm) - np.log10(k_cold)) / np.maximum(1.0, np.abs(np.log10(k_cold)))
+        assert d.max() <= 1e-3, d.max()
+        del pts, h
+    mean_cold, mean_warm = it(info_cold).mean(), it(res["info"]).mean()
+    print(f"precision {precision}: active-set iterations cold {mean_cold:.2f} -> warm {mean_warm:.2f} "
+          f"(max {it(info_cold).max():.0f} -> {it(res['info']).max():.0f}), "
+          f"solve {ms_cold:.2f} ms -> {res['solve_ms']:.2f} ms, plain refits {res['refit']}")
+    assert mean_warm <= 0.85 * mean_cold
+    assert it(res["info"]).max() < it(info_cold).max()
