@@ -169,9 +169,13 @@ __device__ __forceinline__ float4 local_centre_e(const dvec4 &c, const double o[
     r.x = (float)(c.x - o[0]);
     r.y = (float)(c.y - o[1]);
     r.z = (float)(c.z - o[2]);
-    r.w = (float)(-1.4426950408889634 / (2.0 * c.w * c.w));
+    const float sg = (float)c.w;  // fp32 alpha (no fp64 divide)
+    r.w = -1.44269504f / (2.f * sg * sg);
     return r;
 }
+
+// exp in fp32 on the special-function unit (relative error ~1e-7)
+__device__ __forceinline__ double exp_f32(float v) { return (double)tc::ex2(v * 1.44269504f); }
 
 __device__ __forceinline__ float logit2_e(const float4 &c, float x, float y, float z) {
     float dx = x - c.x, dy = y - c.y, dz = z - c.z;
@@ -231,7 +235,7 @@ __global__ void k_eval_bucket_f32(Geo g, const int32_t *boxes, const double *cen
         for (int a = 0; a < g.dim; ++a) x[a] = pts[(int64_t)p * g.dim + a];
         const float v = shepard_f32_smem(sc, sb, M, (float)(x[0] - o[0]), (float)(x[1] - o[1]),
                                          (float)(x[2] - o[2]));
-        out[p] = log_space ? (double)v : exp((double)v);
+        out[p] = log_space ? (double)v : exp_f32(v);
     }
 }
 
@@ -297,7 +301,7 @@ __global__ void __launch_bounds__(kErrThreads) k_errors_owner(Geo g, const int32
         else
             v = shepard_f64_smem(sc64, sb64, M, x);
         const int64_t gi = (int64_t)i + (int64_t)g.n[0] * ((int64_t)j + (int64_t)g.n[1] * k);
-        const double kk = K[gi], ks = exp(v), lk = log(kk);
+        const double kk = K[gi], ks = F32 ? exp_f32((float)v) : exp(v), lk = log(kk);
         acc[0] += fabs(kk - ks);
         acc[1] += fabs(kk);
         acc[2] += (kk - ks) * (kk - ks);

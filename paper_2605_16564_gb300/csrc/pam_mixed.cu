@@ -13,6 +13,7 @@
 //   l2 = alpha_m |x - c_m|^2,  alpha_m = -log2(e) / (2 sigma_m^2).
 #include <cfloat>
 #include <cmath>
+#include <cstdlib>
 
 #include "pam_internal.cuh"
 #include "pam_tc.cuh"
@@ -25,7 +26,8 @@ __device__ __forceinline__ float4 local_centre(const dvec4 &c, const double o[3]
     r.x = (float)(c.x - o[0]);
     r.y = (float)(c.y - o[1]);
     r.z = (float)(c.z - o[2]);
-    r.w = (float)(-1.4426950408889634 / (2.0 * c.w * c.w));
+    const float sg = (float)c.w;  // alpha in fp32: relative error ~1e-7, no fp64 divide
+    r.w = -1.44269504f / (2.f * sg * sg);
     return r;
 }
 
@@ -98,26 +100,12 @@ constexpr int kTcKC = 32;                 // cells per chunk (2 MMA k-steps of 1
 constexpr int kTcMaxRows = 512;           // rows of the B tile (TMEM columns)
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz
 
-// Cell data of a chunk; sh = l2* - log2(1/sum) folds the Shepard normaliser
-// into the exponent (W = 2^(alpha d^2 - sh)); sh = +inf for padding cells.
-struct TcCell {
-    float x[kTcKC], y[kTcKC], z[kTcKC], sh[kTcKC], yv[kTcKC];
+// Cell data of the patch, staged once: local coordinates, sh = l2* -
+// log2(1/sum) (the Shepard normaliser folded into the exponent, W =
+// 2^(alpha d^2 - sh); +inf for padding cells) and y = ln K.
+struct TcCellAll {
+    float4 p;  // (x, y, z, sh)
 };
-
-__device__ __forceinline__ void load_cells(const Geo &g, const int32_t *box, int c, int N,
-                                           const float *rowmax, const float *rowinv,
-                                           const double *yv, TcCell &cl, int lane) {
-    const int t = c * kTcKC + lane;
-    float x[3] = {0.f, 0.f, 0.f};
-    float sh = INFINITY, y = 0.f;
-    if (t < N) {
-        local_cell(g, box, t, x);
-        sh = rowmax[t] - log2f(rowinv[t]);
-        y = (float)yv[t];
-    }
-    cl.x[lane] = x[0]; cl.y[lane] = x[1]; cl.z[lane] = x[2];
-    cl.sh[lane] = sh; cl.yv[lane] = y;
-}
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t *boxes,
                                                            const double *centres,
@@ -139,7 +127,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
     const uint32_t tile_bytes = (uint32_t)Rt * kTcKC * 2;
     uint8_t *tiles = smem;
     float4 *sc = reinterpret_cast<float4 *>(smem + 4 * (size_t)kTcMaxRows * kTcKC * 2);
-    TcCell *cells = reinterpret_cast<TcCell *>(sc + kTcMaxRows);  // [2]
+    float4 *cellp = sc + kTcMaxRows;                       // [nch * 32] (x, y, z, sh)
+    const int nch = (N + kTcKC - 1) / kTcKC;
+    float *celly = reinterpret_cast<float *>(cellp + (size_t)nch * kTcKC);  // [nch * 32] ln K
     __shared__ uint64_t mbar[2];
     __shared__ uint32_t tmem_base;
     __shared__ int timed_out;
@@ -154,7 +144,17 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
     const float *rowmax = w.rowmax + (size_t)s * g.n_max;
     const float *rowinv = w.rowinv + (size_t)s * g.n_max;
     const double *yv = w.y + (size_t)s * g.n_max;
-    if (warp == 1) load_cells(g, box, 0, N, rowmax, rowinv, yv, cells[0], lane);
+    for (int t = tid; t < nch * kTcKC; t += blockDim.x) {
+        float x[3] = {0.f, 0.f, 0.f};
+        float sh = INFINITY, y = 0.f;
+        if (t < N) {
+            local_cell(g, box, t, x);
+            sh = rowmax[t] - log2f(rowinv[t]);
+            y = (float)yv[t];
+        }
+        cellp[t] = make_float4(x[0], x[1], x[2], sh);
+        celly[t] = y;
+    }
     uint32_t ncols = 32;
     while (ncols < (uint32_t)R) ncols <<= 1;
     if (tid == 0) {
@@ -172,7 +172,6 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
 
-    const int nch = (N + kTcKC - 1) / kTcKC;
     const uint32_t lbo = (uint32_t)Rt * 16u, sbo = 128u;
     const int r = tid & (kTcMaxRows - 1);           // the tile row this thread produces
     const int half = tid >> 9;                      // ... for k-groups 2*half, 2*half+1
@@ -186,9 +185,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
         if (c >= 2) {  // the MMAs of chunk c-2 read this buffer
             if (!tc::mbar_wait(&mbar[buf], ((c - 2) >> 1) & 1, kWaitBudget)) timed_out = 1;
         }
-        // next chunk's cell data goes to the other buffer (read after the barrier)
-        if (warp == 1 && c + 1 < nch) load_cells(g, box, c + 1, N, rowmax, rowinv, yv, cells[buf ^ 1], lane);
-        const TcCell &cl = cells[buf];
+        const float4 *cl = cellp + c * kTcKC;
+        const float *cy = celly + c * kTcKC;
         uint8_t *hi = tiles + (size_t)buf * 2 * tile_bytes;
         uint8_t *lo = hi + tile_bytes;
         if (r < Rt) {
@@ -201,10 +199,11 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int k = kg * 8 + q;
-                        const float dx = cl.x[k] - cc.x, dy = cl.y[k] - cc.y, dz = cl.z[k] - cc.z;
-                        const float e = tc::ex2(fmaf(cc.w, fmaf(dz, dz, fmaf(dy, dy, dx * dx)), -cl.sh[k]));
+                        const float4 cp = cl[k];
+                        const float dx = cp.x - cc.x, dy = cp.y - cc.y, dz = cp.z - cc.z;
+                        const float e = tc::ex2(fmaf(cc.w, fmaf(dz, dz, fmaf(dy, dy, dx * dx)), -cp.w));
                         v[q] = e;
-                        bsum = fmaf(e, cl.yv[k], bsum);
+                        bsum = fmaf(e, cy[k], bsum);
                     }
                 } else {
 #pragma unroll
@@ -305,8 +304,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
     if (warp == 0) tc::tmem_dealloc(tmem, ncols);
 }
 
-static size_t gram_tc_smem() {
-    return 4 * (size_t)kTcMaxRows * kTcKC * 2 + kTcMaxRows * sizeof(float4) + 2 * sizeof(TcCell) + 1024;
+static size_t gram_tc_smem(const Geo &g) {
+    const size_t cells = (size_t)((g.n_max + kTcKC - 1) / kTcKC) * kTcKC;
+    return 4 * (size_t)kTcMaxRows * kTcKC * 2 + kTcMaxRows * sizeof(float4) + cells * (sizeof(float4) + sizeof(float)) + 1024;
 }
 
 void launch_stats_gram_tc(const Geo &g, const int32_t *boxes, const double *centres,
@@ -321,7 +321,7 @@ void launch_stats_gram_tc(const Geo &g, const int32_t *boxes, const double *cent
     }
     {
         PhaseScope ps(kPhGramTC, st);
-        size_t sm = gram_tc_smem();
+        size_t sm = gram_tc_smem(g);
         cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         dim3 grid((g.m_cap + 127) / 128, g.S);
         k_gram_tc<<<grid, kTcThreads, sm, st>>>(g, boxes, centres, info, w, all);
@@ -372,7 +372,7 @@ void launch_copy_gram_f32(const Geo &g, const int32_t *info, const Ws &w, double
 // --------------------------------------------------------------------------
 
 constexpr int kMxThreads = 256;
-constexpr int kMxFactorBytes = 64 * 1024;
+constexpr int kMxFactorBytesDefault = 64 * 1024;
 constexpr int kMxMaxRefine = 12;
 constexpr int kMxMaxPdas = 200;
 constexpr int kMxPdasFull = 12;
@@ -572,7 +572,7 @@ struct DFAcc {
 
 __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const int32_t *boxes,
                                                             const double *centres, double *beta,
-                                                            int32_t *info, Ws w) {
+                                                            int32_t *info, Ws w, int kMxFactorBytes) {
     const int s = blockIdx.x;
     int32_t *inf = info + s * kInfoN;
     if (inf[PAM_INFO_STOPPED]) return;
@@ -913,9 +913,23 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
     }
 }
 
+// Shared-memory budget of the packed factor: supports with s (s+1)/2 fp32
+// beyond it keep their factor in global memory (L1/L2). A smaller budget
+// lets more subdomains share an SM. PAM_FACTOR_SMEM_KB overrides the
+// default for tuning.
+static int factor_smem_bytes() {
+    static int v = -1;
+    if (v < 0) {
+        const char *e = getenv("PAM_FACTOR_SMEM_KB");
+        v = e ? atoi(e) * 1024 : kMxFactorBytesDefault;
+        if (v < 4096) v = 4096;
+    }
+    return v;
+}
+
 static size_t solve_mixed_smem(const Geo &g) {
     return (size_t)g.m_cap * (5 * sizeof(float) + 2 * sizeof(int) + sizeof(float4)) +
-           (size_t)g.n_max * (sizeof(float4) + 2 * sizeof(float)) + kMxFactorBytes + 64;
+           (size_t)g.n_max * (sizeof(float4) + 2 * sizeof(float)) + factor_smem_bytes() + 64;
 }
 
 #ifdef PAM_SOLVE_PROFILE
@@ -928,7 +942,9 @@ extern "C" void pam_debug_solve_profile(unsigned long long *out, int reset) {
 }
 #endif
 
-bool mixed_solve_fits(const Geo &g) { return solve_mixed_smem(g) <= 227 * 1024; }
+bool mixed_solve_fits(const Geo &g) {
+    return solve_mixed_smem(g) <= 227 * 1024 && gram_tc_smem(g) <= 227 * 1024;
+}
 
 void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes,
                               const double *centres, double *beta, int32_t *info, const Ws &w,
@@ -937,7 +953,7 @@ void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes,
     size_t sm = solve_mixed_smem(g);
     cudaFuncSetAttribute(k_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     PhaseScope ps(kPhSolve, st);
-    k_solve_mixed<<<g.S, kMxThreads, sm, st>>>(g, p, boxes, centres, beta, info, w);
+    k_solve_mixed<<<g.S, kMxThreads, sm, st>>>(g, p, boxes, centres, beta, info, w, factor_smem_bytes());
     count_launches(1);
 }
 

@@ -188,3 +188,21 @@ def test_empty_evaluation_is_a_noop(torch_dev):
     fit, _ = _fit_gpu(torch, dev, K, (16, 16), (2, 2), 1, (2, 2), k_top=2, levels=1)
     out = fit.eval(torch.zeros((0, 2), dtype=torch.float64, device=dev))
     assert out.numel() == 0
+
+
+def test_channel_field_1024_sampled_subdomains(torch_dev):
+    # 1024 x 1024 channelised field, 32 x 32 subdomains, overlap 2, 8 x 8
+    # initial centres, 3 levels: the GPU fits all 1024 subdomains, the oracle
+    # a sample of them.
+    torch, dev = torch_dev
+    K = fields.channel_field(1024, seed=3)
+    params = dict(k_top=37, levels=3)
+    fit, Kd = _fit_gpu(torch, dev, K, (1024, 1024), (32, 32), 2, (8, 8), **params)
+    which = list(range(0, 1024, 53)) + [1023]
+    ref = oracle.fit_all(K, (1024, 1024), (32, 32), 2, (8, 8), oracle.default_params(**params), which=which)
+    _compare_models(fit.host_model(), ref, which)
+    h = 1.0 / 1024
+    rng = np.random.default_rng(14)
+    pts = np.concatenate([ref["boxes"][s, 0:2] * h + rng.uniform(0, 1, size=(100, 2)) * 32 * h for s in which])
+    out = fit.eval(torch.from_numpy(pts).to(dev)).cpu().numpy()
+    assert np.abs(out - oracle.evaluate(ref, pts)).max() <= KSTAR_RTOL * (K.max() - K.min())

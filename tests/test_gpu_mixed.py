@@ -202,3 +202,32 @@ def test_mixed_eval_outside_and_empty(env):
     out = fit.eval(torch.from_numpy(pts).to(dev)).cpu().numpy()
     assert np.isnan(out[:2]).all() and np.isfinite(out[2:]).all()
     assert fit.eval(torch.zeros((0, 2), dtype=torch.float64, device=dev)).numel() == 0
+
+
+def test_mixed_channel_field_1024_sample(env):
+    torch, pam, dev = env
+    K = fields.channel_field(1024, seed=3)
+    params = dict(k_top=37, levels=3)
+    fit, Kd = _mixed_fit(env, K, (1024, 1024), (32, 32), 2, (8, 8), 3, **params)
+    which = list(range(0, 1024, 37))
+    ref = oracle.fit_all(K, (1024, 1024), (32, 32), 2, (8, 8), oracle.default_params(**params), which=which)
+    got = fit.host_model()
+    h = 1.0 / 1024
+    same, bad, l1m, l1o = 0, 0, 0.0, 0.0
+    for s in which:
+        b = ref["boxes"][s]
+        xs = (np.arange(b[0], b[3]) + 0.5) * h
+        ys = (np.arange(b[1], b[4]) + 0.5) * h
+        X, Y = np.meshgrid(xs, ys)
+        pts = np.stack([X.ravel(), Y.ravel()], 1)
+        km = fit.eval(torch.from_numpy(pts).to(dev)).cpu().numpy()
+        ko = oracle.evaluate(ref, pts)
+        kt = K[b[1]:b[4], b[0]:b[3]].ravel()
+        l1m += np.abs(kt - km).sum(); l1o += np.abs(kt - ko).sum()
+        m = ref["M"][s]
+        if got["M"][s] == m and np.array_equal(got["c"][s, :m], ref["c"][s, :m]):
+            same += 1
+            bad += np.count_nonzero(~_log10_close(km, ko))
+    assert same >= 0.75 * len(which), same
+    assert bad == 0
+    assert abs(l1m - l1o) <= L1_RTOL * l1o
