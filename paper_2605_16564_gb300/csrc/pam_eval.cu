@@ -326,16 +326,30 @@ __global__ void __launch_bounds__(kErrThreads) k_errors_owner(Geo g, const int32
     }
 }
 
-__global__ void k_errors_combine(const double *part, int rows, double *err) {
-    if (threadIdx.x != 0 || blockIdx.x != 0) return;
+// Sums the per-owner rows in a fixed order: thread t adds the contiguous
+// rows [t*per, (t+1)*per) in order, then a fixed tree over the threads.
+__global__ void __launch_bounds__(256) k_errors_combine(const double *part, int rows, double *err) {
+    __shared__ double red[7][256];
+    const int t = threadIdx.x;
+    const int per = (rows + 255) / 256;
     double a[7] = {0, 0, 0, 0, 0, 0, 0};
-    for (int r = 0; r < rows; ++r)
+    for (int r = t * per; r < min(rows, (t + 1) * per); ++r)
         for (int q = 0; q < 7; ++q)
             a[q] = (q == 6) ? fmax(a[q], part[(size_t)r * 8 + q]) : a[q] + part[(size_t)r * 8 + q];
-    err[0] = a[0] / a[1];
-    err[1] = sqrt(a[2] / a[3]);
-    err[2] = a[5] > 0.0 ? a[4] / a[5] : a[4];
-    err[3] = a[6] / log(10.0);
+    for (int q = 0; q < 7; ++q) red[q][t] = a[q];
+    __syncthreads();
+    for (int o = 128; o > 0; o >>= 1) {
+        if (t < o)
+            for (int q = 0; q < 7; ++q)
+                red[q][t] = (q == 6) ? fmax(red[q][t], red[q][t + o]) : red[q][t] + red[q][t + o];
+        __syncthreads();
+    }
+    if (t == 0) {
+        err[0] = red[0][0] / red[1][0];
+        err[1] = sqrt(red[2][0] / red[3][0]);
+        err[2] = red[5][0] > 0.0 ? red[4][0] / red[5][0] : red[4][0];
+        err[3] = red[6][0] / log(10.0);
+    }
 }
 
 void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
@@ -350,7 +364,7 @@ void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, co
         cudaFuncSetAttribute(k_errors_owner<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_errors_owner<false><<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, w.err_part);
     }
-    k_errors_combine<<<1, 32, 0, st>>>(w.err_part, g.S, err);
+    k_errors_combine<<<1, 256, 0, st>>>(w.err_part, g.S, err);
     count_launches(2);
 }
 

@@ -683,14 +683,41 @@ __global__ void __launch_bounds__(kMarkThreads) k_mark_enrich(Geo g, Par p, cons
         lo[a] = __dmul_rn((double)box[6 + a], g.h);
         hi[a] = __dmul_rn((double)box[9 + a], g.h);
     }
+    float ext = 0.f;
+    for (int a = 0; a < g.dim; ++a) ext = fmaxf(ext, (float)(hi[a] - lo[a]));
+    const float e_loc = 2e-7f * ext;
+    float4 *scl = reinterpret_cast<float4 *>(keys);  // the keys are no longer needed
+    for (int m = tid; m < M; m += blockDim.x)
+        scl[m] = make_float4((float)(cs[(size_t)m * 4 + 0] - lo[0]), (float)(cs[(size_t)m * 4 + 1] - lo[1]),
+                             (float)(cs[(size_t)m * 4 + 2] - lo[2]), 0.f);
+    __syncthreads();
     for (int r = tid; r < nm; r += blockDim.x) {
         if (r * per >= add) continue;
         double xt[3];
         int64_t gi;
         patch_cell(g, box, marked[r], xt, &gi);
+        // nearest current centre: an fp32 pass in patch-local coordinates
+        // bounds the minimum; the exact unfused binary64 distances then decide
+        // among the centres the fp32 pass cannot rule out, ties to the lower
+        // index. Every local coordinate lies in [0, ext], so each fp32
+        // difference is off by at most e = 3 * 2^-24 * ext and a squared
+        // distance D by at most 3.47 e sqrt(D) + 3 e^2 + 1.8e-7 D; the cut
+        // below exceeds the minimum by more than twice that.
+        float xl[3];
+        for (int a = 0; a < 3; ++a) xl[a] = (float)(xt[a] - lo[a]);
+        float bf = INFINITY;
+        for (int m = 0; m < M; ++m) {
+            const float4 c = scl[m];
+            const float d0 = c.x - xl[0], d1 = c.y - xl[1], d2 = c.z - xl[2];
+            bf = fminf(bf, fmaf(d2, d2, fmaf(d1, d1, d0 * d0)));
+        }
+        const float cut = bf * 1.001f + 8.f * e_loc * sqrtf(bf) + 24.f * e_loc * e_loc + 1e-30f;
         int bestm = 0;
         double bd = INFINITY;
         for (int m = 0; m < M; ++m) {
+            const float4 c = scl[m];
+            const float d0 = c.x - xl[0], d1 = c.y - xl[1], dd2 = c.z - xl[2];
+            if (fmaf(dd2, dd2, fmaf(d1, d1, d0 * d0)) > cut) continue;
             double d2 = 0.0;
             for (int a = 0; a < g.dim; ++a) {
                 double d = __dsub_rn(xt[a], cs[(size_t)m * 4 + a]);
@@ -729,6 +756,7 @@ __global__ void __launch_bounds__(kMarkThreads) k_mark_enrich(Geo g, Par p, cons
 void launch_mark_enrich(const Geo &g, const Par &p, const int32_t *boxes, double *centres,
                         double *beta, int32_t *info, const Ws &w, cudaStream_t st) {
     size_t sm = (size_t)g.n_max * sizeof(unsigned long long);
+    if (sm < (size_t)g.m_cap * sizeof(float4)) sm = (size_t)g.m_cap * sizeof(float4);
     cudaFuncSetAttribute(k_mark_enrich, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     PhaseScope ps(kPhMark, st);
     k_mark_enrich<<<g.S, kMarkThreads, sm, st>>>(g, p, boxes, centres, beta, info, w);
