@@ -402,6 +402,7 @@ __device__ __forceinline__ int tri_i(int p, int q) { return p * (p + 1) / 2 + q;
 #ifdef PAM_SOLVE_PROFILE
 // Profiling builds only: clock64 totals per phase of the mixed solve.
 __device__ unsigned long long g_solve_prof[16];
+__device__ unsigned long long g_solve_blk[8192];
 #define PROF_T0() long long _pt = clock64()
 #define PROF_MARK(k)                                                          \
     do {                                                                      \
@@ -414,75 +415,78 @@ __device__ unsigned long long g_solve_prof[16];
 #endif
 
 // Blocked right-looking Cholesky of the packed lower s x s matrix A, in
-// place, with blocks of 32 columns. The 32 x 32 diagonal block is factored
-// by warp 0 in registers (lane i holds row i; columns broadcast by
-// shuffles); every other thread solves one panel row against it from
-// registers (L_kk read as shared-memory broadcasts), then all threads update
-// the trailing triangle. Three block barriers per 32 columns.
+// place, with blocks of 32 columns. Warp 0 factors the 32 x 32 diagonal
+// block in registers (lane i holds row i, fully unrolled so every index is
+// static; rows past the end of a partial block are padded with the
+// identity); every other thread solves one panel row against it, again
+// from registers, reading L_kk as shared-memory broadcasts; then all
+// threads update the trailing triangle. Three block barriers per 32 columns.
 // dinv[k] receives 1 / L_kk for the triangular solves.
+__device__ __forceinline__ void mx_diag_block(float *A, int k0, int kw, int *flag, float *dinv) {
+    const unsigned full = 0xffffffffu;
+    const int lane = threadIdx.x & 31, i = k0 + lane;
+    const bool live = lane < kw;
+    float a[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j)
+        a[j] = (live && j <= lane) ? A[tri_i(i, k0 + j)] : (j == lane ? 1.f : 0.f);
+    float my_iv = 1.f;
+    bool bad = false;
+#pragma unroll
+    for (int k = 0; k < 32; ++k) {
+        float d = __shfl_sync(full, a[k], k);
+        if (!(d > 0.f)) { bad = true; d = 1.f; }
+        const float iv = rsqrtf(d);
+        if (lane == k) { a[k] = d * iv; my_iv = iv; }
+        else a[k] *= iv;  // above the diagonal (lane < k) the value is never used
+#pragma unroll
+        for (int j = k + 1; j < 32; ++j) a[j] = fmaf(-a[k], __shfl_sync(full, a[k], j), a[j]);
+    }
+    if (live) {
+#pragma unroll
+        for (int j = 0; j < 32; ++j)
+            if (j <= lane) A[tri_i(i, k0 + j)] = a[j];
+        dinv[i] = my_iv;
+    }
+    if (__any_sync(full, bad && live)) {
+        if (lane == 0) *flag = 1;
+    }
+}
+
+// Panel row i: L[i, k0:k0+32] = A[i, k0:k0+32] L_kk^{-T} (kw == 32 only:
+// a partial block is the last one and has no rows below it).
+__device__ __forceinline__ void mx_panel_row(float *A, int k0, int i, const float *dinv) {
+    float *ri = A + tri_i(i, 0) + k0;
+    float r[32];
+#pragma unroll
+    for (int j = 0; j < 32; ++j) r[j] = ri[j];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+        const float *lq = A + tri_i(k0 + q, 0) + k0;
+        float a0 = r[q], a1 = 0.f, a2 = 0.f, a3 = 0.f;
+#pragma unroll
+        for (int rr = 0; rr < q; ++rr) {
+            if ((rr & 3) == 0) a0 = fmaf(-r[rr], lq[rr], a0);
+            else if ((rr & 3) == 1) a1 = fmaf(-r[rr], lq[rr], a1);
+            else if ((rr & 3) == 2) a2 = fmaf(-r[rr], lq[rr], a2);
+            else a3 = fmaf(-r[rr], lq[rr], a3);
+        }
+        r[q] = ((a0 + a1) + (a2 + a3)) * dinv[k0 + q];
+    }
+#pragma unroll
+    for (int j = 0; j < 32; ++j) ri[j] = r[j];
+}
+
 __device__ void mx_cholesky(float *A, int s, int *flag, float *dinv) {
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
     PROF_T0();
     for (int k0 = 0; k0 < s; k0 += 32) {
         const int kw = min(32, s - k0);
-        if (warp == 0) {
-            // column by column; lane i owns row k0 + i of the block
-            const int i = k0 + lane;
-            for (int k = 0; k < kw; ++k) {
-                float iv = 0.f;
-                if (lane == k) {
-                    float d = A[tri_i(i, i)];
-                    if (!(d > 0.f)) { *flag = 1; d = 1.f; }
-                    const float l = sqrtf(d);
-                    iv = 1.f / l;
-                    A[tri_i(i, i)] = l;
-                    dinv[i] = iv;
-                }
-                iv = __shfl_sync(0xffffffffu, iv, k);
-                float lik = 0.f;
-                if (lane > k && lane < kw) {
-                    lik = A[tri_i(i, k0 + k)] * iv;
-                    A[tri_i(i, k0 + k)] = lik;
-                }
-                // eight independent load-fma-store chains per step
-                float *ai = A + tri_i(i, 0) + k0;
-                for (int j0 = k + 1; j0 < kw; j0 += 8) {
-                    float lj[8], av[8];
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) lj[u] = __shfl_sync(0xffffffffu, lik, (j0 + u) & 31);
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int j = j0 + u;
-                        av[u] = (j < kw && lane >= j && lane < kw) ? ai[j] : 0.f;
-                    }
-#pragma unroll
-                    for (int u = 0; u < 8; ++u) {
-                        const int j = j0 + u;
-                        if (j < kw && lane >= j && lane < kw) ai[j] = fmaf(-lik, lj[u], av[u]);
-                    }
-                }
-                __syncwarp();
-            }
-        }
+        if (warp == 0) mx_diag_block(A, k0, kw, flag, dinv);
         __syncthreads();
         PROF_MARK(12);
-        // panel rows: L[i, k0:k0+kw] = A[i, k0:k0+kw] L_kk^{-T}, in place
-        for (int i = k0 + kw + tid; i < s; i += blockDim.x) {
-            float *ri = A + tri_i(i, 0) + k0;
-            for (int q = 0; q < kw; ++q) {
-                const float *lq = A + tri_i(k0 + q, 0) + k0;
-                float a0 = ri[q], a1 = 0.f, a2 = 0.f, a3 = 0.f;
-                int r = 0;
-                for (; r + 3 < q; r += 4) {
-                    a0 = fmaf(-ri[r], lq[r], a0);
-                    a1 = fmaf(-ri[r + 1], lq[r + 1], a1);
-                    a2 = fmaf(-ri[r + 2], lq[r + 2], a2);
-                    a3 = fmaf(-ri[r + 3], lq[r + 3], a3);
-                }
-                for (; r < q; ++r) a0 = fmaf(-ri[r], lq[r], a0);
-                ri[q] = ((a0 + a1) + (a2 + a3)) * dinv[k0 + q];
-            }
-        }
+        if (k0 + kw >= s) break;  // last block: nothing below it
+        for (int i = k0 + kw + tid; i < s; i += blockDim.x) mx_panel_row(A, k0, i, dinv);
         __syncthreads();
         PROF_MARK(13);
         // trailing update of rows/cols >= k0 + kw
@@ -491,9 +495,13 @@ __device__ void mx_cholesky(float *A, int s, int *flag, float *dinv) {
             float *row = A + tri_i(i, 0);
             for (int j = k0 + kw + lane; j <= i; j += 32) {
                 const float *lj = A + tri_i(j, 0) + k0;
-                float acc = 0.f;
-                for (int q = 0; q < kw; ++q) acc = fmaf(li[q], lj[q], acc);
-                row[j] -= acc;
+                float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+                for (int q = 0; q < 32; q += 2) {
+                    acc0 = fmaf(li[q], lj[q], acc0);
+                    acc1 = fmaf(li[q + 1], lj[q + 1], acc1);
+                }
+                row[j] -= acc0 + acc1;
             }
         }
         __syncthreads();
@@ -502,52 +510,75 @@ __device__ void mx_cholesky(float *A, int s, int *flag, float *dinv) {
 }
 
 // Solves L L^T z = r in place (packed L from mx_cholesky, dinv = 1/diag):
-// per 32-row block, warp 0 solves the diagonal block with shuffles and all
+// per 32-row block, warp 0 solves the diagonal block with shuffles (fully
+// unrolled; the matrix loads do not depend on the recurrence) and all
 // threads apply the block's contribution to the remaining entries.
 __device__ void mx_chol_solve(const float *A, const float *dinv, int s, float *r) {
+    const unsigned full = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     // forward: L z = r
     for (int k0 = 0; k0 < s; k0 += 32) {
         const int kw = min(32, s - k0);
         if (warp == 0) {
             const int i = k0 + lane;
-            float ri = lane < kw ? r[i] : 0.f;
-            for (int q = 0; q < kw; ++q) {
-                if (lane == q) ri *= dinv[k0 + q];
-                const float zq = __shfl_sync(0xffffffffu, ri, q);
-                if (lane > q && lane < kw) ri = fmaf(-A[tri_i(i, k0 + q)], zq, ri);
+            const bool live = lane < kw;
+            float ri = live ? r[i] : 0.f;
+            const float di = live ? dinv[i] : 1.f;
+#pragma unroll
+            for (int q = 0; q < 32; ++q) {
+                const float lik = (live && lane > q) ? A[tri_i(i, k0 + q)] : 0.f;
+                if (lane == q) ri *= di;
+                const float zq = __shfl_sync(full, ri, q);
+                ri = fmaf(-lik, zq, ri);
             }
-            if (lane < kw) r[i] = ri;
+            if (live) r[i] = ri;
         }
         __syncthreads();
-        for (int i = k0 + kw + tid; i < s; i += blockDim.x) {
-            const float *li = A + tri_i(i, 0) + k0;
-            float acc = 0.f;
-            for (int q = 0; q < kw; ++q) acc = fmaf(li[q], r[k0 + q], acc);
-            r[i] -= acc;
+        if (k0 + kw < s) {
+            for (int i = k0 + kw + tid; i < s; i += blockDim.x) {
+                const float *li = A + tri_i(i, 0) + k0;
+                float acc0 = 0.f, acc1 = 0.f;
+#pragma unroll
+                for (int q = 0; q < 32; q += 2) {
+                    acc0 = fmaf(li[q], r[k0 + q], acc0);
+                    acc1 = fmaf(li[q + 1], r[k0 + q + 1], acc1);
+                }
+                r[i] -= acc0 + acc1;
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
     // backward: L^T x = z
     for (int k0 = ((s - 1) / 32) * 32; k0 >= 0 && s > 0; k0 -= 32) {
         const int kw = min(32, s - k0);
         if (warp == 0) {
-            const int p = k0 + lane;
-            float rp = lane < kw ? r[p] : 0.f;
-            for (int q = kw - 1; q >= 0; --q) {
-                if (lane == q) rp *= dinv[k0 + q];
-                const float xq = __shfl_sync(0xffffffffu, rp, q);
-                if (lane < q) rp = fmaf(-A[tri_i(k0 + q, k0 + lane)], xq, rp);
+            const int pr = k0 + lane;
+            const bool live = lane < kw;
+            float rp = live ? r[pr] : 0.f;
+            const float dp = live ? dinv[pr] : 1.f;
+#pragma unroll
+            for (int q = 31; q >= 0; --q) {
+                const float lqp = (q < kw && lane < q) ? A[tri_i(k0 + q, k0 + lane)] : 0.f;
+                if (lane == q) rp *= dp;
+                const float xq = __shfl_sync(full, rp, q);
+                rp = fmaf(-lqp, xq, rp);
             }
-            if (lane < kw) r[p] = rp;
+            if (live) r[pr] = rp;
         }
         __syncthreads();
-        for (int p = tid; p < k0; p += blockDim.x) {
-            float acc = 0.f;
-            for (int q = 0; q < kw; ++q) acc = fmaf(A[tri_i(k0 + q, p)], r[k0 + q], acc);
-            r[p] -= acc;
+        if (k0 > 0) {
+            for (int pr = tid; pr < k0; pr += blockDim.x) {
+                float acc0 = 0.f, acc1 = 0.f;
+                int q = 0;
+                for (; q + 1 < kw; q += 2) {
+                    acc0 = fmaf(A[tri_i(k0 + q, pr)], r[k0 + q], acc0);
+                    acc1 = fmaf(A[tri_i(k0 + q + 1, pr)], r[k0 + q + 1], acc1);
+                }
+                if (q < kw) acc0 = fmaf(A[tri_i(k0 + q, pr)], r[k0 + q], acc0);
+                r[pr] -= acc0 + acc1;
+            }
+            __syncthreads();
         }
-        __syncthreads();
     }
 }
 
@@ -570,7 +601,7 @@ struct DFAcc {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
-__global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const int32_t *boxes,
+__global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, const int32_t *boxes,
                                                             const double *centres, double *beta,
                                                             int32_t *info, Ws w, int kMxFactorBytes) {
     const int s = blockIdx.x;
@@ -621,6 +652,9 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
     __syncthreads();
     PROF_T0();
     PROF_MARK(0);
+#ifdef PAM_SOLVE_PROFILE
+    const long long t_blk0 = clock64();
+#endif
 
     // ---------------- stage 1: active-set iterations on G~ ----------------
     // Up to kMxPdasFull full primal-dual corrections; if the support still
@@ -900,6 +934,9 @@ __global__ void __launch_bounds__(kMxThreads) k_solve_mixed(Geo g, Par p, const 
     for (int j = tid; j < M; j += blockDim.x) beta[(size_t)s * mc + j] = (double)x[j];
     __syncthreads();
     PROF_MARK(7);
+#ifdef PAM_SOLVE_PROFILE
+    if (tid == 0 && s < 8192) g_solve_blk[s] = (unsigned long long)(clock64() - t_blk0);
+#endif
     if (tid == 0) {
         int flags = inf[PAM_INFO_FLAGS] & ~(PAM_FLAG_NOT_CERTIFIED | PAM_FLAG_CHOLESKY);
         if (!certified) {
@@ -933,6 +970,9 @@ static size_t solve_mixed_smem(const Geo &g) {
 }
 
 #ifdef PAM_SOLVE_PROFILE
+extern "C" void pam_debug_solve_blocks(unsigned long long *out, int n) {
+    cudaMemcpyFromSymbol(out, g_solve_blk, sizeof(unsigned long long) * (n < 8192 ? n : 8192));
+}
 extern "C" void pam_debug_solve_profile(unsigned long long *out, int reset) {
     cudaMemcpyFromSymbol(out, g_solve_prof, sizeof(g_solve_prof));
     if (reset) {
