@@ -82,65 +82,138 @@ __global__ void __launch_bounds__(128) k_stats_f32(Geo g, const int32_t *boxes,
 }
 
 // --------------------------------------------------------------------------
-// Gram products on the tensor cores. One CTA per (subdomain, strip of 128
-// centres I): D = W_I^T W_{I..} (128 x R, R = centres from the strip start
-// to the padded end of the dictionary) accumulates in TMEM over chunks of 32
-// cells. The 256 threads generate the chunk's W values (each thread one or
-// two centre rows), split them into bf16 hi/lo and store them in the
-// canonical K-major layout (8-row x 16-byte core matrices); the A operand
-// is the first 128 rows of the same tile. Two buffers: the threads fill one
-// while the tensor core consumes the other; thread 0 issues the MMAs and
-// commits them to the buffer's mbarrier.
-// Epilogue: warps read the strip from TMEM and write rows of G (and the
-// mirrored block below the strip) in fp32; threads of the strip's rows also
-// accumulate b = W^T y.
+// Gram products on the tensor cores. The dictionary (padded to Mp, a
+// multiple of 32) is cut into strips of 128 centres; strip i needs
+// D_i = W_{I_i}^T W_{[128 i, Mp)} (128 x R_i, R_i = Mp - 128 i: the upper
+// block row, by symmetry). Consecutive strips are grouped, from the last one
+// backwards, while their D blocks fit the 512 TMEM columns together; one CTA
+// per (subdomain, group) generates W once for the rows from the group's
+// first strip to Mp and accumulates every D block of the group over chunks
+// of 32 cells. Warp-specialised pipeline over nst (3, or 2 where shared
+// memory is short) stages:
+//   * warps 1..31 produce: each thread generates the chunk's W values of one
+//     centre row for one, two or four groups of 8 cells, splits them into
+//     bf16 hi/lo parts and stores them in the canonical K-major layout
+//     (8-row x 16-byte core matrices), then its warp arrives on the stage's
+//     `full` barrier;
+//   * one thread of warp 0 waits for `full`, issues hi*hi + hi*lo + lo*hi for
+//     every strip of the group (A = the strip's 128 rows of the tile, B = the
+//     tile from the same row on) and commits to the stage's `empty` barrier,
+//     which the producers wait for before they overwrite the stage.
+// No block-wide barrier inside the loop. Epilogue: all warps read the D
+// blocks from TMEM and write rows of G (and the mirrored blocks below the
+// strips) in fp32; the producers' partial sums give b = W^T y.
 // --------------------------------------------------------------------------
-constexpr int kTcThreads = 1024;         // two producer threads per centre row
+constexpr int kTcThreads = 1024;
+constexpr int kTcIssuers = 4;            // warps 0..3: one MMA-issuing thread each
+constexpr int kTcProdWarps = kTcThreads / 32 - kTcIssuers;
 constexpr int kTcKC = 32;                 // cells per chunk (2 MMA k-steps of 16)
-constexpr int kTcMaxRows = 512;           // rows of the B tile (TMEM columns)
+constexpr int kTcMaxStages = 3;            // 3 where shared memory allows, else 2
+constexpr int kTcMaxRows = kMixedMaxM;    // rows of the B tile
+constexpr int kTcCols = 512;              // TMEM columns
 constexpr long long kWaitBudget = 4000000000LL;  // ~2 s at 2 GHz
+constexpr int kTcStageFloats = 32 * 33;   // epilogue transpose buffer per warp
+constexpr size_t kSmemLimit = 227 * 1024;  // dynamic shared memory per CTA
 
-// Cell data of the patch, staged once: local coordinates, sh = l2* -
-// log2(1/sum) (the Shepard normaliser folded into the exponent, W =
-// 2^(alpha d^2 - sh); +inf for padding cells) and y = ln K.
-struct TcCellAll {
-    float4 p;  // (x, y, z, sh)
-};
+__device__ __forceinline__ void mbar_arrive(uint64_t *m) {
+    asm volatile("{\n\t.reg .b64 st;\n\tmbarrier.arrive.shared::cta.b64 st, [%0];\n\t}\n"
+                 ::"r"(tc::smem_u32(m)) : "memory");
+}
+
+// Strip group q of a padded dictionary of Mp centres: strips [*i0, *i1).
+// Groups are formed from the last strip backwards while sum R_i <= 512 and
+// numbered from the front. Returns the number of groups (at most 4).
+__host__ __device__ __forceinline__ int tc_strip_group(int Mp, int q, int *i0, int *i1) {
+    const int nS = (Mp + 127) / 128;
+    int start[4], n = 0;
+    for (int i = nS - 1; i >= 0 && n < 4;) {
+        int sum = 0, j = i;
+        while (j >= 0 && sum + (Mp - 128 * j) <= kTcCols) { sum += Mp - 128 * j; --j; }
+        start[n++] = j + 1;
+        i = j;
+    }
+    const int b = n - 1 - q;  // groups were listed back to front
+    if (b >= 0 && b < n) {
+        *i0 = start[b];
+        *i1 = b == 0 ? nS : start[b - 1];
+    }
+    return n;
+}
+
+// Tile rows of a group: the generated rows, padded so that every strip's
+// 128 A rows lie inside the tile.
+__host__ __device__ __forceinline__ int tc_tile_rows(int Mp, int i0, int i1) {
+    const int R = Mp - 128 * i0;
+    return R > 128 * (i1 - i0) ? R : 128 * (i1 - i0);
+}
+
+// The largest tile of any dictionary size up to m_cap: the shared-memory
+// layout of every CTA of a launch.
+static int tc_rows_cap(int m_cap) {
+    int cap = 128;
+    for (int Mp = 32; Mp <= ((m_cap + 31) & ~31); Mp += 32) {
+        int i0 = 0, i1 = 0;
+        const int n = tc_strip_group(Mp, 0, &i0, &i1);
+        for (int q = 0; q < n; ++q) {
+            tc_strip_group(Mp, q, &i0, &i1);
+            const int rt = tc_tile_rows(Mp, i0, i1);
+            cap = rt > cap ? rt : cap;
+        }
+    }
+    return cap;
+}
+
+#ifdef PAM_SOLVE_PROFILE
+// Profiling builds only: clock64 totals of the Gram pipeline (per CTA, seen
+// from the MMA thread and from the first producer thread).
+__device__ unsigned long long g_gram_prof[16];
+#define GP_ADD(k, v) atomicAdd(&g_gram_prof[k], (unsigned long long)(v))
+#else
+#define GP_ADD(k, v)
+#endif
 
 __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t *boxes,
                                                            const double *centres,
-                                                           const int32_t *info, Ws w, int all) {
-    const int s = blockIdx.y, strip = blockIdx.x;
+                                                           const int32_t *info, Ws w, int all,
+                                                           int nst, int Rcap) {
+    const int s = blockIdx.y;
     const int32_t *inf = info + s * kInfoN;
     if (!all && inf[PAM_INFO_STOPPED]) return;
     const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
-    const int row0 = strip * 128;
-    if (row0 >= M) return;
     const int Mp = (M + 31) & ~31;                 // padded dictionary size
-    const int R = Mp - row0;                        // B rows = TMEM columns (multiple of 32)
-    const int Rt = R < 128 ? 128 : R;               // tile rows (the A operand reads 128)
+    int i0 = 0, i1 = 0;
+    if ((int)blockIdx.x >= tc_strip_group(Mp, blockIdx.x, &i0, &i1)) return;
+#ifdef PAM_SOLVE_PROFILE
+    const long long gp_t0 = clock64();
+#endif
+    const int row0 = 128 * i0;                      // first generated row
+    const int Rl = M - row0;                        // live rows (the rest are zero)
+    const int Rt = tc_tile_rows(Mp, i0, i1);        // tile rows (<= Rcap)
+    int tcols = 0;
+    for (int i = i0; i < i1; ++i) tcols += Mp - 128 * i;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int32_t *box = boxes + s * 12;
 
     extern __shared__ __align__(1024) uint8_t smem[];
-    // [buf][hi|lo] tiles of Rt x kTcKC bf16, each Rt * 64 bytes
+    // stage st: hi tile then lo tile, each Rt x kTcKC bf16 (Rt * 64 bytes)
     const uint32_t tile_bytes = (uint32_t)Rt * kTcKC * 2;
     uint8_t *tiles = smem;
-    float4 *sc = reinterpret_cast<float4 *>(smem + 4 * (size_t)kTcMaxRows * kTcKC * 2);
-    float4 *cellp = sc + kTcMaxRows;                       // [nch * 32] (x, y, z, sh)
+    const size_t tiles_region = (size_t)nst * 2 * Rcap * kTcKC * 2 > (size_t)32 * kTcStageFloats * 4
+                                    ? (size_t)nst * 2 * Rcap * kTcKC * 2
+                                    : (size_t)32 * kTcStageFloats * 4;
+    float4 *sc = reinterpret_cast<float4 *>(smem + tiles_region);   // [Rcap]
+    float *bpart = reinterpret_cast<float *>(sc + Rcap);             // [4][Rcap]
+    float4 *cellp = reinterpret_cast<float4 *>(bpart + 4 * Rcap);    // [nch * 32] (x, y, z, sh)
     const int nch = (N + kTcKC - 1) / kTcKC;
     float *celly = reinterpret_cast<float *>(cellp + (size_t)nch * kTcKC);  // [nch * 32] ln K
-    __shared__ uint64_t mbar[2];
+    __shared__ uint64_t full[kTcMaxStages], empty[kTcMaxStages], drain;
     __shared__ uint32_t tmem_base;
     __shared__ int timed_out;
 
     double o[3];
     patch_origin(g, box, o);
     const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
-    for (int r = tid; r < Rt; r += blockDim.x) {
-        int m = row0 + r;
-        sc[r] = (r < R && m < M) ? local_centre(cg[m], o) : make_float4(0.f, 0.f, 0.f, 0.f);
-    }
+    for (int r = tid; r < Rl; r += blockDim.x) sc[r] = local_centre(cg[row0 + r], o);
     const float *rowmax = w.rowmax + (size_t)s * g.n_max;
     const float *rowinv = w.rowinv + (size_t)s * g.n_max;
     const double *yv = w.y + (size_t)s * g.n_max;
@@ -155,11 +228,27 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
         cellp[t] = make_float4(x[0], x[1], x[2], sh);
         celly[t] = y;
     }
+    // rows past the live ones stay zero in every stage
+    {
+        const int nz = Rt - Rl, per = 4 * nz;  // (row, k-group) pairs per tile
+        for (int e = tid; e < nst * 2 * per; e += blockDim.x) {
+            const int t2 = e / per, rem = e % per, kg = rem / nz, r = Rl + rem % nz;
+            const uint32_t off = (uint32_t)(kg * (Rt >> 3) + (r >> 3)) * 128u + (uint32_t)(r & 7) * 16u;
+            *reinterpret_cast<uint4 *>(tiles + (size_t)t2 * tile_bytes + off) = make_uint4(0u, 0u, 0u, 0u);
+        }
+    }
     uint32_t ncols = 32;
-    while (ncols < (uint32_t)R) ncols <<= 1;
+    while (ncols < (uint32_t)tcols) ncols <<= 1;
+    // D regions (strip, 256-column piece); region k goes to issuer k % kTcIssuers
+    int nreg = 0;
+    for (int i = i0; i < i1; ++i) nreg += (Mp - 128 * i + 255) / 256;
+    const int nact = nreg < kTcIssuers ? nreg : kTcIssuers;  // active issuers
     if (tid == 0) {
-        tc::mbar_init(&mbar[0], 1);
-        tc::mbar_init(&mbar[1], 1);
+        for (int st = 0; st < nst; ++st) {
+            tc::mbar_init(&full[st], kTcProdWarps);
+            tc::mbar_init(&empty[st], nact);
+        }
+        tc::mbar_init(&drain, nact);
         tc::mbar_fence_init();
         timed_out = 0;
     }
@@ -167,35 +256,99 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
         tc::tmem_alloc(&tmem_base, ncols);
         tc::tmem_relinquish();
     }
+    tc::fence_proxy_async_smem();  // the zero rows, for the tensor core
     tc::fence_before_sync();
     __syncthreads();
     tc::fence_after_sync();
     const uint32_t tmem = tmem_base;
+    volatile int *vto = &timed_out;
+#ifdef PAM_SOLVE_PROFILE
+    const long long gp_t1 = clock64();
+    if (tid == 32 * kTcIssuers) { GP_ADD(0, gp_t1 - gp_t0); GP_ADD(15, 1); }
+#endif
 
-    const uint32_t lbo = (uint32_t)Rt * 16u, sbo = 128u;
-    const int r = tid & (kTcMaxRows - 1);           // the tile row this thread produces
-    const int half = tid >> 9;                      // ... for k-groups 2*half, 2*half+1
-    const bool live = r < R && row0 + r < M;
-    const float4 cc = r < Rt ? sc[r] : make_float4(0.f, 0.f, 0.f, 0.f);
-    float bacc = 0.f;
-
-    int issued = 0;  // chunks whose MMAs thread 0 has committed
-    for (int c = 0; c < nch; ++c) {
-        const int buf = c & 1;
-        if (c >= 2) {  // the MMAs of chunk c-2 read this buffer
-            if (!tc::mbar_wait(&mbar[buf], ((c - 2) >> 1) & 1, kWaitBudget)) timed_out = 1;
-        }
-        const float4 *cl = cellp + c * kTcKC;
-        const float *cy = celly + c * kTcKC;
-        uint8_t *hi = tiles + (size_t)buf * 2 * tile_bytes;
-        uint8_t *lo = hi + tile_bytes;
-        if (r < Rt) {
-            float bsum = 0.f;
+    if (warp < kTcIssuers) {
+        // ---- MMA issuers: lane 0 of warp j issues the regions k = j mod 4 ----
+        if (lane == 0 && warp < nact) {
+            const uint32_t lbo = (uint32_t)Rt * 16u, sbo = 128u;
+            // descriptors of the stage-0 hi tile; every other operand start is
+            // a multiple of 16 bytes away (address field = byte address / 16)
+            const uint64_t desc0 = tc::smem_desc(tc::smem_u32(tiles), lbo, sbo);
+            for (int c = 0; c < nch; ++c) {
+                const int st = c % nst;
+#ifdef PAM_SOLVE_PROFILE
+                const long long gw = clock64();
+#endif
+                if (!tc::mbar_wait(&full[st], (uint32_t)(c / nst) & 1u, kWaitBudget) || *vto) {
+                    *vto = 1;
+                    break;
+                }
+#ifdef PAM_SOLVE_PROFILE
+                const long long gi = clock64();
+                if (warp == 0) GP_ADD(1, gi - gw);
+#endif
+                tc::fence_after_sync();
+                const uint64_t hi_d = desc0 + (((uint64_t)st * 2 * tile_bytes) >> 4);
+                const uint64_t lo_d = hi_d + (tile_bytes >> 4);
 #pragma unroll
-            for (int kh = 0; kh < 2; ++kh) {
-                const int kg = 2 * half + kh;
-                float v[8];
-                if (live) {
+                for (int ks = 0; ks < kTcKC / 16; ++ks) {
+                    const uint64_t koff = (uint64_t)(2 * ks) * (lbo >> 4);
+                    uint32_t dcol = 0;
+                    int k = 0;
+                    for (int i = i0; i < i1; ++i) {
+                        const uint64_t roff = (uint64_t)((128 * (i - i0)) >> 3) * (sbo >> 4);
+                        const uint64_t a_hi = hi_d + koff + roff, a_lo = lo_d + koff + roff;
+                        const int Ri = Mp - 128 * i;
+                        for (int n0 = 0; n0 < Ri; n0 += 256, ++k) {
+                            if (k % kTcIssuers != warp) continue;
+                            const uint32_t n = (uint32_t)min(256, Ri - n0);
+                            const uint32_t id = tc::idesc_bf16_f32(n);
+                            const uint64_t noff = (uint64_t)(n0 >> 3) * (sbo >> 4);
+                            const uint32_t d = tmem + dcol + (uint32_t)n0;
+                            tc::mma_bf16(d, a_hi, hi_d + koff + roff + noff, id, (c > 0 || ks > 0) ? 1u : 0u);
+                            tc::mma_bf16(d, a_hi, lo_d + koff + roff + noff, id, 1u);
+                            tc::mma_bf16(d, a_lo, hi_d + koff + roff + noff, id, 1u);
+                        }
+                        dcol += (uint32_t)Ri;
+                    }
+                }
+                tc::mma_commit(&empty[st]);
+                if (warp == 0) GP_ADD(2, clock64() - gi);
+            }
+            tc::mma_commit(&drain);  // every MMA this thread issued, done or not
+        }
+    } else {
+        // ---- producers ----
+        const int pth = tid - 32 * kTcIssuers;  // 0 .. 32 * kTcProdWarps - 1
+        const int tpr = (4 * Rl <= 32 * kTcProdWarps) ? 4 : (2 * Rl <= 32 * kTcProdWarps ? 2 : 1);
+        const int nkg = 4 / tpr;
+        const int r = pth / tpr, part = pth % tpr;
+        const bool live = r < Rl;
+        const float4 cc = live ? sc[r] : make_float4(0.f, 0.f, 0.f, 0.f);
+        float bacc = 0.f;
+        for (int c = 0; c < nch; ++c) {
+            const int st = c % nst;
+            bool bad = false;
+#ifdef PAM_SOLVE_PROFILE
+            const long long pw = clock64();
+#endif
+            if (c >= nst)  // the MMAs of chunk c - nst read this stage
+                bad = !tc::mbar_wait(&empty[st], (uint32_t)(c / nst - 1) & 1u, kWaitBudget);
+#ifdef PAM_SOLVE_PROFILE
+            const long long pp0 = clock64();
+            if (pth == 0) GP_ADD(3, pp0 - pw);
+#endif
+            if (bad) *vto = 1;
+            if (__any_sync(0xffffffffu, bad || *vto)) break;  // warp-uniform exit
+            if (live) {
+                const float4 *cl = cellp + c * kTcKC;
+                const float *cy = celly + c * kTcKC;
+                uint8_t *hi = tiles + (size_t)st * 2 * tile_bytes;
+                uint8_t *lo = hi + tile_bytes;
+                float bsum = 0.f;
+                for (int kk = 0; kk < nkg; ++kk) {
+                    const int kg = part * nkg + kk;
+                    float v[8];
 #pragma unroll
                     for (int q = 0; q < 8; ++q) {
                         const int k = kg * 8 + q;
@@ -205,77 +358,58 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
                         v[q] = e;
                         bsum = fmaf(e, cy[k], bsum);
                     }
-                } else {
+                    uint32_t hp[4], lp[4];
 #pragma unroll
-                    for (int q = 0; q < 8; ++q) v[q] = 0.f;
+                    for (int q = 0; q < 4; ++q) {
+                        hp[q] = tc::pack_bf16(v[2 * q], v[2 * q + 1]);
+                        const float h0 = __uint_as_float(hp[q] << 16), h1 = __uint_as_float(hp[q] & 0xffff0000u);
+                        lp[q] = tc::pack_bf16(v[2 * q] - h0, v[2 * q + 1] - h1);
+                    }
+                    const uint32_t off = (uint32_t)(kg * (Rt >> 3) + (r >> 3)) * 128u + (uint32_t)(r & 7) * 16u;
+                    *reinterpret_cast<uint4 *>(hi + off) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
+                    *reinterpret_cast<uint4 *>(lo + off) = make_uint4(lp[0], lp[1], lp[2], lp[3]);
                 }
-                uint32_t hp[4], lp[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    hp[q] = tc::pack_bf16(v[2 * q], v[2 * q + 1]);
-                    const float h0 = __uint_as_float(hp[q] << 16), h1 = __uint_as_float(hp[q] & 0xffff0000u);
-                    lp[q] = tc::pack_bf16(v[2 * q] - h0, v[2 * q + 1] - h1);
-                }
-                const uint32_t off = (uint32_t)(kg * (Rt >> 3) + (r >> 3)) * 128u + (uint32_t)(r & 7) * 16u;
-                *reinterpret_cast<uint4 *>(hi + off) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
-                *reinterpret_cast<uint4 *>(lo + off) = make_uint4(lp[0], lp[1], lp[2], lp[3]);
+                bacc += bsum;
             }
-            bacc += bsum;
+            tc::fence_proxy_async_smem();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&full[st]);
+#ifdef PAM_SOLVE_PROFILE
+            if (pth == 0) GP_ADD(4, clock64() - pp0);
+#endif
         }
-        tc::fence_proxy_async_smem();
-        __syncthreads();
-        if (timed_out) break;
-        if (tid == 0) {
-            tc::fence_after_sync();
-            const uint32_t hi_a = tc::smem_u32(hi), lo_a = tc::smem_u32(lo);
-#pragma unroll
-            for (int ks = 0; ks < kTcKC / 16; ++ks) {
-                const uint32_t koff = (uint32_t)(2 * ks) * lbo;
-                const uint64_t a_hi = tc::smem_desc(hi_a + koff, lbo, sbo);
-                const uint64_t a_lo = tc::smem_desc(lo_a + koff, lbo, sbo);
-                for (int n0 = 0; n0 < R; n0 += 256) {
-                    const uint32_t n = (uint32_t)min(256, R - n0);
-                    const uint32_t id = tc::idesc_bf16_f32(n);
-                    const uint32_t noff = (uint32_t)(n0 >> 3) * sbo;
-                    const uint64_t b_hi = tc::smem_desc(hi_a + koff + noff, lbo, sbo);
-                    const uint64_t b_lo = tc::smem_desc(lo_a + koff + noff, lbo, sbo);
-                    const uint32_t d = tmem + (uint32_t)n0;
-                    tc::mma_bf16(d, a_hi, b_hi, id, (c > 0 || ks > 0) ? 1u : 0u);
-                    tc::mma_bf16(d, a_hi, b_lo, id, 1u);
-                    tc::mma_bf16(d, a_lo, b_hi, id, 1u);
-                }
-            }
-            tc::mma_commit(&mbar[buf]);
-        }
-        issued = c + 1;
+        if (live) bpart[part * Rcap + r] = bacc;
     }
     // wait for the last chunk's MMAs (they complete in issue order)
-    if (!timed_out && nch > 0) {
-        const int last = nch - 1;
-        if (!tc::mbar_wait(&mbar[last & 1], (last >> 1) & 1, kWaitBudget)) timed_out = 1;
-    }
+#ifdef PAM_SOLVE_PROFILE
+    if (tid == 32 * kTcIssuers) GP_ADD(5, clock64() - gp_t1);
+#endif
+    // every issuer committed its MMAs to `drain` (they complete in issue order)
+    __syncthreads();
+    __syncwarp();
+    if (!tc::mbar_wait(&drain, 0u, kWaitBudget)) *vto = 1;
     __syncthreads();
     tc::fence_after_sync();
-    if (timed_out) {
-        // give the MMAs still in flight a bounded time to land before TMEM is released
-        if (issued > 0) tc::mbar_wait(&mbar[(issued - 1) & 1], ((issued - 1) >> 1) & 1, kWaitBudget);
+    if (*vto) {
         if (tid == 0) atomicAdd(&w.status[kStTimeout], 1);
     } else {
         float *G = w.Gf + (size_t)s * g.m_cap * g.m_cap;
-        // warp q reads TMEM lanes 32 (q % 4) ..; the four warps of a lane
-        // quarter split the 32-column chunks. Rows go out through a padded
-        // shared-memory transpose so that each store is one coalesced row
-        // segment; the mirrored block below the strip is already coalesced.
-        float *stage = reinterpret_cast<float *>(tiles) + (size_t)(warp & 15) * 32 * 33;
+        // warp q reads TMEM lanes 32 (q % 4) ..; the eight warps of a lane
+        // quarter split the 32-column chunks of the group's D blocks. Rows go
+        // out through a padded shared-memory transpose so that each store is
+        // one coalesced row segment; the mirrored blocks below the strips are
+        // already coalesced.
+        float *stage = reinterpret_cast<float *>(tiles) + (size_t)warp * kTcStageFloats;
         const int lane_base = (warp & 3) * 32;
-        const int rl = lane_base + lane;      // D row (TMEM lane) held by this thread
-        const int rg = row0 + rl;             // its G row
-        const int ncol_chunks = R / 32;
-        for (int ch = warp >> 2; warp < 16 && ch < ncol_chunks; ch += 4) {
+        for (int f = warp >> 2; f < tcols / 32; f += 8) {
+            int i = i0, ch = f, dcol = 0;
+            while (ch >= (Mp - 128 * i) / 32) { ch -= (Mp - 128 * i) / 32; dcol += Mp - 128 * i; ++i; }
+            const int srow = 128 * i;                 // the strip's first centre
+            const int rg = srow + lane_base + lane;   // G row held by this thread
             uint32_t v[32];
-            tc::tmem_ld_32x32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(ch * 32), v);
+            tc::tmem_ld_32x32(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(dcol + ch * 32), v);
             tc::tmem_wait_ld();
-            const int c0 = row0 + ch * 32;
+            const int c0 = srow + ch * 32;
             if (ch * 32 >= 128) {
                 for (int q = 0; q < 32; ++q) {
                     const int col = c0 + q;
@@ -287,26 +421,37 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
             __syncwarp();
             const int col = c0 + lane;
             for (int q = 0; q < 32; ++q) {
-                const int row = row0 + lane_base + q;
+                const int row = srow + lane_base + q;
                 if (row < M && col < M) G[(size_t)row * g.m_cap + col] = stage[q * 33 + lane];
             }
             __syncwarp();
         }
-        // b = W^T y for the strip's rows: the two halves of a row add up
-        float *bh = reinterpret_cast<float *>(sc);  // the centre table is no longer needed
-        __syncthreads();
-        if (half == 1 && r < 128) bh[r] = bacc;
-        __syncthreads();
-        if (half == 0 && r < 128 && live) w.b[(size_t)s * g.m_cap + row0 + r] = (double)(bacc + bh[r]);
+        // b = W^T y for the group's rows: the parts of a row in a fixed order
+        const int tpr = (4 * Rl <= 32 * kTcProdWarps) ? 4 : (2 * Rl <= 32 * kTcProdWarps ? 2 : 1);
+        const int rend = min(Rl, 128 * (i1 - i0));
+        for (int r = tid; r < rend; r += blockDim.x) {
+            float acc = 0.f;
+            for (int q = 0; q < tpr; ++q) acc += bpart[q * Rcap + r];
+            w.b[(size_t)s * g.m_cap + row0 + r] = (double)acc;
+        }
     }
     tc::fence_before_sync();
     __syncthreads();
+    __syncwarp();
     if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+#ifdef PAM_SOLVE_PROFILE
+    if (tid == 32 * kTcIssuers) GP_ADD(6, clock64() - gp_t0);
+#endif
 }
 
-static size_t gram_tc_smem(const Geo &g) {
+static_assert(kTcMaxRows <= 32 * kTcProdWarps, "one producer thread per row at least");
+
+static size_t gram_tc_smem(const Geo &g, int stages) {
+    const size_t Rcap = (size_t)tc_rows_cap(g.m_cap);
     const size_t cells = (size_t)((g.n_max + kTcKC - 1) / kTcKC) * kTcKC;
-    return 4 * (size_t)kTcMaxRows * kTcKC * 2 + kTcMaxRows * sizeof(float4) + cells * (sizeof(float4) + sizeof(float)) + 1024;
+    size_t tiles = (size_t)stages * 2 * Rcap * kTcKC * 2;
+    if (tiles < (size_t)32 * kTcStageFloats * 4) tiles = (size_t)32 * kTcStageFloats * 4;
+    return tiles + Rcap * sizeof(float4) + 4 * Rcap * sizeof(float) + cells * (sizeof(float4) + sizeof(float));
 }
 
 void launch_stats_gram_tc(const Geo &g, const int32_t *boxes, const double *centres,
@@ -321,10 +466,11 @@ void launch_stats_gram_tc(const Geo &g, const int32_t *boxes, const double *cent
     }
     {
         PhaseScope ps(kPhGramTC, st);
-        size_t sm = gram_tc_smem(g);
+        const int stages = gram_tc_smem(g, kTcMaxStages) <= kSmemLimit ? kTcMaxStages : 2;
+        size_t sm = gram_tc_smem(g, stages);
         cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         dim3 grid((g.m_cap + 127) / 128, g.S);
-        k_gram_tc<<<grid, kTcThreads, sm, st>>>(g, boxes, centres, info, w, all);
+        k_gram_tc<<<grid, kTcThreads, sm, st>>>(g, boxes, centres, info, w, all, stages, tc_rows_cap(g.m_cap));
         count_launches(1);
     }
 }
@@ -413,6 +559,33 @@ __device__ unsigned long long g_solve_blk[8192];
 #define PROF_T0()
 #define PROF_MARK(k)
 #endif
+
+// Packed support matrix: A[tri(p, q)] = G~[idx[p]][idx[q]] (+ lambda2 on
+// the diagonal) for q <= p < s, flat over the packed entries so that every
+// thread keeps eight independent gathers from G~ in flight.
+__device__ void mx_build(float *A, const float *G, const int *idx, int s, int mc, float lam2) {
+    const int n = s * (s + 1) / 2, nt = blockDim.x;
+    for (int e0 = threadIdx.x; e0 < n; e0 += 8 * nt) {
+        float v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * nt;
+            v[u] = 0.f;
+            if (e < n) {
+                int pr = (int)((sqrtf(8.f * (float)e + 1.f) - 1.f) * 0.5f);
+                if (tri_i(pr + 1, 0) <= e) ++pr;
+                if (tri_i(pr, 0) > e) --pr;
+                const int q = e - tri_i(pr, 0);
+                v[u] = G[(size_t)idx[pr] * mc + idx[q]] + (q == pr ? lam2 : 0.f);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int e = e0 + u * nt;
+            if (e < n) A[e] = v[u];
+        }
+    }
+}
 
 // Blocked right-looking Cholesky of the packed lower s x s matrix A, in
 // place, with blocks of 32 columns. Warp 0 factors the 32 x 32 diagonal
@@ -611,7 +784,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
     const float lam1 = (float)((double)N * p.lam1_hat), lam2 = (float)((double)N * p.lam2_hat);
     // stage 1 only has to find a good support: G~ carries ~1e-5 relative error
     const float tol_pdas = lam1 * (1.0f + 1e-3f);
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+    const int tid = threadIdx.x, lane = tid & 31;
     const int32_t *box = boxes + s * 12;
 
     extern __shared__ __align__(16) uint8_t sm[];
@@ -674,11 +847,8 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
         A = (tri_i(scnt, 0) * 4 <= kMxFactorBytes) ? Asm
             : (w.Lf + (size_t)s * ((size_t)mc * (mc + 1) / 2));
         PROF_MARK(8);
-        for (int pp = warp; pp < scnt; pp += nw) {
-            const float *Gr = G + (size_t)idx[pp] * mc;
-            for (int q = lane; q <= pp; q += 32) A[tri_i(pp, q)] = Gr[idx[q]] + (q == pp ? lam2 : 0.f);
-            if (lane == 0) rhs[pp] = bv[idx[pp]] - lam1 * (float)sg[idx[pp]];
-        }
+        mx_build(A, G, idx, scnt, mc, lam2);
+        for (int pp = tid; pp < scnt; pp += blockDim.x) rhs[pp] = bv[idx[pp]] - lam1 * (float)sg[idx[pp]];
         __syncthreads();
         PROF_MARK(9);
         mx_cholesky(A, scnt, &sh.flag, dinv);
@@ -878,10 +1048,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
             scnt = sh.cnt;
             A = (tri_i(scnt, 0) * 4 <= kMxFactorBytes) ? Asm
                 : (w.Lf + (size_t)s * ((size_t)mc * (mc + 1) / 2));
-            for (int pp = warp; pp < scnt; pp += nw) {
-                const float *Gr = G + (size_t)idx[pp] * mc;
-                for (int q = lane; q <= pp; q += 32) A[tri_i(pp, q)] = Gr[idx[q]] + (q == pp ? lam2 : 0.f);
-            }
+            mx_build(A, G, idx, scnt, mc, lam2);
             __syncthreads();
             mx_cholesky(A, scnt, &sh.flag, dinv);
             if (sh.flag) break;
@@ -908,10 +1075,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
             scnt = sh.cnt;
             A = (tri_i(scnt, 0) * 4 <= kMxFactorBytes) ? Asm
                 : (w.Lf + (size_t)s * ((size_t)mc * (mc + 1) / 2));
-            for (int pp = warp; pp < scnt; pp += nw) {
-                const float *Gr = G + (size_t)idx[pp] * mc;
-                for (int q = lane; q <= pp; q += 32) A[tri_i(pp, q)] = Gr[idx[q]] + (q == pp ? lam2 : 0.f);
-            }
+            mx_build(A, G, idx, scnt, mc, lam2);
             __syncthreads();
             mx_cholesky(A, scnt, &sh.flag, dinv);
         }
@@ -970,6 +1134,13 @@ static size_t solve_mixed_smem(const Geo &g) {
 }
 
 #ifdef PAM_SOLVE_PROFILE
+extern "C" void pam_debug_gram_profile(unsigned long long *out, int reset) {
+    cudaMemcpyFromSymbol(out, g_gram_prof, sizeof(g_gram_prof));
+    if (reset) {
+        unsigned long long z[16] = {};
+        cudaMemcpyToSymbol(g_gram_prof, z, sizeof(z));
+    }
+}
 extern "C" void pam_debug_solve_blocks(unsigned long long *out, int n) {
     cudaMemcpyFromSymbol(out, g_solve_blk, sizeof(unsigned long long) * (n < 8192 ? n : 8192));
 }
@@ -983,7 +1154,7 @@ extern "C" void pam_debug_solve_profile(unsigned long long *out, int reset) {
 #endif
 
 bool mixed_solve_fits(const Geo &g) {
-    return solve_mixed_smem(g) <= 227 * 1024 && gram_tc_smem(g) <= 227 * 1024;
+    return solve_mixed_smem(g) <= kSmemLimit && gram_tc_smem(g, 2) <= kSmemLimit;
 }
 
 void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes,
