@@ -76,6 +76,12 @@ bool make_geo(const pam_problem *prob, const pam_params *par, Geo *g, Par *p, pa
         if (cap > PAM_MAX_M) { *st = PAM_ERR_UNSUPPORTED; return false; }
         // the tensor-core Gram keeps a 128 x M strip in TMEM (512 columns)
         if (par->precision == PAM_PREC_MIXED && cap > kMixedMaxM) { *st = PAM_ERR_UNSUPPORTED; return false; }
+        // marking sorts a patch's keys in shared memory: 2^ceil(log2 N) x 8 bytes
+        if (par->levels > 0) {
+            int64_t P = 1;
+            while (P < g->n_max) P <<= 1;
+            if (P * 8 > 227 * 1024) { *st = PAM_ERR_UNSUPPORTED; return false; }
+        }
         g->m_cap = (int)cap;
         g->prec = par->precision;
         if (p) {

@@ -601,14 +601,40 @@ __device__ __forceinline__ void simplex_dir(int dim, int q, double u[3]) {
         else if (q == 1) { u[0] = c30; u[1] = -0.5; }
         else { u[1] = 1.0; }
     } else {
-        const double r3 = 0.57735026918962576451;  // 1/sqrt(3)
-        const int sgn[4][3] = {{1, 1, 1}, {1, -1, -1}, {-1, 1, -1}, {-1, -1, 1}};
-        for (int a = 0; a < 3; ++a) u[a] = (double)sgn[q][a] * r3;
+        // (1,1,1), (1,-1,-1), (-1,1,-1), (-1,-1,1), each / sqrt(3)
+        const double r3 = 0.57735026918962576451;
+        u[0] = (q == 0 || q == 1) ? r3 : -r3;
+        u[1] = (q == 0 || q == 2) ? r3 : -r3;
+        u[2] = (q == 0 || q == 3) ? r3 : -r3;
     }
 }
 
 constexpr int kMarkThreads = 256;
+
+#ifdef PAM_SOLVE_PROFILE
+// Profiling builds only: clock64 totals of the marking kernel's phases.
+__device__ unsigned long long g_mark_prof[8];
+#define MK_T(v) const long long v = clock64()
+#define MK_ADD(k, a, b) do { if (threadIdx.x == 0) atomicAdd(&g_mark_prof[k], (unsigned long long)((b) - (a))); } while (0)
+extern "C" void pam_debug_mark_profile(unsigned long long *out, int reset) {
+    cudaMemcpyFromSymbol(out, g_mark_prof, sizeof(g_mark_prof));
+    if (reset) {
+        unsigned long long z[8] = {};
+        cudaMemcpyToSymbol(g_mark_prof, z, sizeof(z));
+    }
+}
+#else
+#define MK_T(v)
+#define MK_ADD(k, a, b)
+#endif
 constexpr int kMaxKTop = 1024;
+
+// Power of two >= n (the bitonic sort's padded length).
+__host__ __device__ __forceinline__ int mark_sort_len(int n) {
+    int P = 1;
+    while (P < n) P <<= 1;
+    return P;
+}
 
 __global__ void __launch_bounds__(kMarkThreads) k_mark_enrich(Geo g, Par p, const int32_t *boxes,
                                                               double *centres, double *beta,
@@ -619,11 +645,10 @@ __global__ void __launch_bounds__(kMarkThreads) k_mark_enrich(Geo g, Par p, cons
     const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS], L = inf[PAM_INFO_LEVELS];
     int64_t lim = (int64_t)g.m0 + p.m_max;
     const int m_limit = (int)(lim < g.m_cap ? lim : g.m_cap);
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     __shared__ int marked[kMaxKTop];
-    __shared__ unsigned long long wbest[kMarkThreads / 32];
     __shared__ int n_marked;
-    extern __shared__ unsigned long long keys[];  // [n_max]
+    extern __shared__ __align__(16) unsigned long long keys[];  // [P], later the enrichment tables
     if (L >= p.levels || M >= m_limit) {
         if (tid == 0) inf[PAM_INFO_STOPPED] = 1;
         return;
@@ -638,37 +663,49 @@ __global__ void __launch_bounds__(kMarkThreads) k_mark_enrich(Geo g, Par p, cons
     }
     const float ek = (float)eps;
     const double *R = w.R + (size_t)s * g.n_max;
-    for (int t = tid; t < N; t += blockDim.x) {
-        float key = (float)R[t];
-        keys[t] = (key >= ek) ? (((unsigned long long)(__float_as_uint(key) + 1u) << 32) |
-                                 (unsigned long long)(0xffffffffu - (unsigned)t))
-                              : 0ull;
+    MK_T(mk0);
+    // key = (fp32 R_T + 1 ulp step, ~index): strictly ordered, ties to the
+    // lower index; 0 for cells below the tolerance and for the padding
+    const int P = mark_sort_len(N);
+    for (int t = tid; t < P; t += blockDim.x) {
+        unsigned long long k = 0ull;
+        if (t < N) {
+            const float key = (float)R[t];
+            if (key >= ek)
+                k = ((unsigned long long)(__float_as_uint(key) + 1u) << 32) |
+                    (unsigned long long)(0xffffffffu - (unsigned)t);
+        }
+        keys[t] = k;
     }
     if (tid == 0) n_marked = 0;
     __syncthreads();
     const int k_top = p.k_top < kMaxKTop ? p.k_top : kMaxKTop;
-    for (int r = 0; r < k_top; ++r) {
-        unsigned long long best = 0;
-        for (int t = tid; t < N; t += blockDim.x) best = keys[t] > best ? keys[t] : best;
-        for (int o = 16; o > 0; o >>= 1) {
-            unsigned long long v = __shfl_xor_sync(0xffffffffu, best, o);
-            best = v > best ? v : best;
-        }
-        if ((tid & 31) == 0) wbest[tid >> 5] = best;
-        __syncthreads();
-        if (tid == 0) {
-            unsigned long long b = 0;
-            for (int q = 0; q < kMarkThreads / 32; ++q) b = wbest[q] > b ? wbest[q] : b;
-            if (b != 0) {
-                int t = (int)(0xffffffffu - (unsigned)(b & 0xffffffffull));
-                marked[n_marked++] = t;
-                keys[t] = 0ull;
+    MK_T(mk1);
+    MK_ADD(0, mk0, mk1);
+    // bitonic sort, descending (the keys are distinct, so the order is unique)
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = tid; i < (P >> 1); i += blockDim.x) {
+                const int l = 2 * i - (i & (j - 1)), r = l + j;
+                const unsigned long long a = keys[l], b = keys[r];
+                const bool desc = (l & k) == 0;
+                if (desc ? (a < b) : (a > b)) { keys[l] = b; keys[r] = a; }
             }
+            __syncthreads();
         }
-        __syncthreads();
-        if (n_marked <= r) break;
     }
+    // the nonzero keys form a prefix: mark the first k_top of them
+    for (int r = tid; r < k_top && r < P; r += blockDim.x) {
+        const unsigned long long kr = keys[r];
+        if (kr != 0ull) {
+            marked[r] = (int)(0xffffffffu - (unsigned)(kr & 0xffffffffull));
+            if (r + 1 == k_top || r + 1 == P || keys[r + 1] == 0ull) n_marked = r + 1;
+        }
+    }
+    __syncthreads();
     const int nm = n_marked;
+    MK_T(mk2);
+    MK_ADD(1, mk1, mk2);
     if (nm == 0) {
         if (tid == 0) { inf[PAM_INFO_STOPPED] = 1; inf[PAM_INFO_MARKED] = 0; }
         return;
@@ -676,6 +713,7 @@ __global__ void __launch_bounds__(kMarkThreads) k_mark_enrich(Geo g, Par p, cons
     const int per = g.dim + 1;
     int add = nm * per;
     if (add > m_limit - M) add = m_limit - M;
+    const int nmu = (add + per - 1) / per;  // marked cells that receive centres
     double *cs = centres + (size_t)s * g.m_cap * 4;
     const int32_t *box = boxes + s * 12;
     double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
@@ -686,65 +724,104 @@ __global__ void __launch_bounds__(kMarkThreads) k_mark_enrich(Geo g, Par p, cons
     float ext = 0.f;
     for (int a = 0; a < g.dim; ++a) ext = fmaxf(ext, (float)(hi[a] - lo[a]));
     const float e_loc = 2e-7f * ext;
-    float4 *scl = reinterpret_cast<float4 *>(keys);  // the keys are no longer needed
+    // tables in the (now free) key space: local fp32 centres, marked-cell
+    // centroids (binary64), chosen parents
+    float4 *scl = reinterpret_cast<float4 *>(keys);          // [M]
+    double *cxt = reinterpret_cast<double *>(scl + M);        // [nmu][4]
+    int *cbest = reinterpret_cast<int *>(cxt + 4 * nmu);      // [nmu]
+    __syncthreads();  // every thread has read its keys
     for (int m = tid; m < M; m += blockDim.x)
         scl[m] = make_float4((float)(cs[(size_t)m * 4 + 0] - lo[0]), (float)(cs[(size_t)m * 4 + 1] - lo[1]),
                              (float)(cs[(size_t)m * 4 + 2] - lo[2]), 0.f);
-    __syncthreads();
-    for (int r = tid; r < nm; r += blockDim.x) {
-        if (r * per >= add) continue;
+    for (int r = tid; r < nmu; r += blockDim.x) {
         double xt[3];
         int64_t gi;
         patch_cell(g, box, marked[r], xt, &gi);
-        // nearest current centre: an fp32 pass in patch-local coordinates
-        // bounds the minimum; the exact unfused binary64 distances then decide
-        // among the centres the fp32 pass cannot rule out, ties to the lower
-        // index. Every local coordinate lies in [0, ext], so each fp32
-        // difference is off by at most e = 3 * 2^-24 * ext and a squared
-        // distance D by at most 3.47 e sqrt(D) + 3 e^2 + 1.8e-7 D; the cut
-        // below exceeds the minimum by more than twice that.
+        for (int a = 0; a < 3; ++a) cxt[4 * r + a] = xt[a];
+    }
+    __syncthreads();
+    MK_T(mk3);
+    MK_ADD(2, mk2, mk3);
+    // nearest current centre, one warp per marked cell: an fp32 pass in
+    // patch-local coordinates bounds the minimum. Every local coordinate lies
+    // in [0, ext], so each fp32 difference is off by at most e = 3 * 2^-24 ext
+    // and a squared distance D by at most 3.47 e sqrt(D) + 3 e^2 + 1.8e-7 D;
+    // the cut exceeds the minimum by more than twice that, so the nearest
+    // centre is among the candidates below it. A single candidate is the
+    // answer; several are decided by exact unfused binary64 distances, ties
+    // to the lower index.
+    for (int r = warp; r < nmu; r += nwarp) {
+        const double xt[3] = {cxt[4 * r], cxt[4 * r + 1], cxt[4 * r + 2]};
         float xl[3];
         for (int a = 0; a < 3; ++a) xl[a] = (float)(xt[a] - lo[a]);
         float bf = INFINITY;
-        for (int m = 0; m < M; ++m) {
+        for (int m = lane; m < M; m += 32) {
             const float4 c = scl[m];
             const float d0 = c.x - xl[0], d1 = c.y - xl[1], d2 = c.z - xl[2];
             bf = fminf(bf, fmaf(d2, d2, fmaf(d1, d1, d0 * d0)));
         }
+        for (int o = 16; o > 0; o >>= 1) bf = fminf(bf, __shfl_xor_sync(0xffffffffu, bf, o));
         const float cut = bf * 1.001f + 8.f * e_loc * sqrtf(bf) + 24.f * e_loc * e_loc + 1e-30f;
-        int bestm = 0;
-        double bd = INFINITY;
-        for (int m = 0; m < M; ++m) {
+        int ncand = 0, first = 0x7fffffff;
+        for (int m = lane; m < M; m += 32) {
             const float4 c = scl[m];
-            const float d0 = c.x - xl[0], d1 = c.y - xl[1], dd2 = c.z - xl[2];
-            if (fmaf(dd2, dd2, fmaf(d1, d1, d0 * d0)) > cut) continue;
-            double d2 = 0.0;
-            for (int a = 0; a < g.dim; ++a) {
-                double d = __dsub_rn(xt[a], cs[(size_t)m * 4 + a]);
-                d2 = __dadd_rn(d2, __dmul_rn(d, d));
+            const float d0 = c.x - xl[0], d1 = c.y - xl[1], d2 = c.z - xl[2];
+            if (fmaf(d2, d2, fmaf(d1, d1, d0 * d0)) <= cut) {
+                ++ncand;
+                first = min(first, m);
             }
-            if (d2 < bd) { bd = d2; bestm = m; }
         }
-        double sn = __dmul_rn(p.eta, cs[(size_t)bestm * 4 + 3]);
-        for (int q = 0; q < per; ++q) {
-            int slot = r * per + q;
-            if (slot >= add) break;
-            double u[3];
-            simplex_dir(g.dim, q, u);
-            double *c = cs + (size_t)(M + slot) * 4;
-            for (int a = 0; a < 3; ++a) {
-                double v = 0.0;
-                if (a < g.dim) {
-                    v = __dadd_rn(xt[a], __dmul_rn(sn, u[a]));
-                    if (v < lo[a]) v = lo[a];
-                    if (v > hi[a]) v = hi[a];
+        for (int o = 16; o > 0; o >>= 1) {
+            ncand += __shfl_xor_sync(0xffffffffu, ncand, o);
+            first = min(first, __shfl_xor_sync(0xffffffffu, first, o));
+        }
+        int bestm = first;
+        if (ncand > 1) {
+            double bd = INFINITY;
+            bestm = 0x7fffffff;
+            for (int m = lane; m < M; m += 32) {
+                const float4 c = scl[m];
+                const float d0 = c.x - xl[0], d1 = c.y - xl[1], dd2 = c.z - xl[2];
+                if (fmaf(dd2, dd2, fmaf(d1, d1, d0 * d0)) > cut) continue;
+                double d2 = 0.0;
+                for (int a = 0; a < g.dim; ++a) {
+                    double d = __dsub_rn(xt[a], cs[(size_t)m * 4 + a]);
+                    d2 = __dadd_rn(d2, __dmul_rn(d, d));
                 }
-                c[a] = v;
+                if (d2 < bd) { bd = d2; bestm = m; }  // m ascends per lane: ties keep the lower
             }
-            c[3] = sn;
-            beta[(size_t)s * g.m_cap + M + slot] = 0.0;
+            for (int o = 16; o > 0; o >>= 1) {
+                const double od = __shfl_xor_sync(0xffffffffu, bd, o);
+                const int om = __shfl_xor_sync(0xffffffffu, bestm, o);
+                if (od < bd || (od == bd && om < bestm)) { bd = od; bestm = om; }
+            }
         }
+        if (lane == 0) cbest[r] = bestm;
     }
+    __syncthreads();
+    // the new centres, one thread each: x_T + eta sigma_p u_q, clipped
+    for (int f = tid; f < add; f += blockDim.x) {
+        const int r = f / per, q = f % per;
+        const double xt[3] = {cxt[4 * r], cxt[4 * r + 1], cxt[4 * r + 2]};
+        const double sn = __dmul_rn(p.eta, cs[(size_t)cbest[r] * 4 + 3]);
+        double u[3];
+        simplex_dir(g.dim, q, u);
+        double *c = cs + (size_t)(M + f) * 4;
+        for (int a = 0; a < 3; ++a) {
+            double v = 0.0;
+            if (a < g.dim) {
+                v = __dadd_rn(xt[a], __dmul_rn(sn, u[a]));
+                if (v < lo[a]) v = lo[a];
+                if (v > hi[a]) v = hi[a];
+            }
+            c[a] = v;
+        }
+        c[3] = sn;
+        beta[(size_t)s * g.m_cap + M + f] = 0.0;
+    }
+    MK_T(mk4);
+    MK_ADD(3, mk3, mk4);
+    if (tid == 0) MK_ADD(4, 0, 1);
     if (tid == 0) {
         inf[PAM_INFO_M] = M + add;
         inf[PAM_INFO_LEVELS] = L + 1;
@@ -755,8 +832,11 @@ __global__ void __launch_bounds__(kMarkThreads) k_mark_enrich(Geo g, Par p, cons
 
 void launch_mark_enrich(const Geo &g, const Par &p, const int32_t *boxes, double *centres,
                         double *beta, int32_t *info, const Ws &w, cudaStream_t st) {
-    size_t sm = (size_t)g.n_max * sizeof(unsigned long long);
-    if (sm < (size_t)g.m_cap * sizeof(float4)) sm = (size_t)g.m_cap * sizeof(float4);
+    // the sort's keys, later the centre table, marked centroids and parents
+    size_t sm = (size_t)mark_sort_len(g.n_max) * sizeof(unsigned long long);
+    const int kt = p.k_top < kMaxKTop ? p.k_top : kMaxKTop;
+    const size_t tables = (size_t)g.m_cap * sizeof(float4) + (size_t)kt * (4 * sizeof(double) + sizeof(int));
+    if (sm < tables) sm = tables;
     cudaFuncSetAttribute(k_mark_enrich, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     PhaseScope ps(kPhMark, st);
     k_mark_enrich<<<g.S, kMarkThreads, sm, st>>>(g, p, boxes, centres, beta, info, w);

@@ -53,7 +53,8 @@ __device__ __forceinline__ void local_cell(const Geo &g, const int32_t *box, int
 
 // --------------------------------------------------------------------------
 // Row statistics of the Shepard normalisation (Eq. (10)): l2* = max_m l2_jm
-// and 1 / sum_m 2^(l2_jm - l2*), one thread per patch cell.
+// and 1 / sum_m 2^(l2_jm - l2*), one thread per patch cell, one pass over
+// the centres.
 // --------------------------------------------------------------------------
 __global__ void __launch_bounds__(128) k_stats_f32(Geo g, const int32_t *boxes,
                                                    const double *centres, const int32_t *info,
@@ -73,10 +74,18 @@ __global__ void __launch_bounds__(128) k_stats_f32(Geo g, const int32_t *boxes,
     if (t >= N) return;
     float x[3];
     local_cell(g, box, t, x);
-    float lmax = -INFINITY;
-    for (int m = 0; m < M; ++m) lmax = fmaxf(lmax, logit2(sc[m], x[0], x[1], x[2]));
-    float sum = 0.0f;
-    for (int m = 0; m < M; ++m) sum += tc::ex2(logit2(sc[m], x[0], x[1], x[2]) - lmax);
+    // one pass with a running maximum: the sum is rescaled whenever the
+    // maximum grows (sum = sum 2^(old - new) + 1), else gains 2^(l - max)
+    float lmax = -INFINITY, sum = 0.0f;
+    for (int m = 0; m < M; ++m) {
+        const float l = logit2(sc[m], x[0], x[1], x[2]);
+        if (l > lmax) {
+            sum = fmaf(sum, tc::ex2(lmax - l), 1.0f);
+            lmax = l;
+        } else {
+            sum += tc::ex2(l - lmax);
+        }
+    }
     w.rowmax[(size_t)s * g.n_max + t] = lmax;
     w.rowinv[(size_t)s * g.n_max + t] = 1.0f / sum;
 }
@@ -803,6 +812,17 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
     __shared__ MxShared sh;
 
     const float *G = w.Gf + (size_t)s * mc * mc;
+    {
+        // the active-set steps gather rows of G~ again and again: stream the
+        // M used rows into L2 once, up front (bulk prefetch, 32 KiB pieces)
+        const size_t bytes = (size_t)M * mc * sizeof(float);
+        for (size_t off = (size_t)tid * 32768; off < bytes; off += (size_t)blockDim.x * 32768) {
+            const size_t n = bytes - off < 32768 ? bytes - off : 32768;
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                         ::"l"(reinterpret_cast<const char *>(G) + off), "r"((uint32_t)((n + 15) & ~(size_t)15))
+                         : "memory");
+        }
+    }
     const float *rowmax = w.rowmax + (size_t)s * g.n_max;
     const float *rowinv = w.rowinv + (size_t)s * g.n_max;
     double o[3];
@@ -1082,8 +1102,18 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
     }
 
     PROF_MARK(6);
-    // final residual e = y - W x, and the indicators R_T (Eq. (4), midpoint)
-    for (int t = tid; t < N; t += blockDim.x) {
+    // indicators R_T (Eq. (4), midpoint) of the final x. A certified x is the
+    // one the last gradient pass saw, with e = y - W x (fp32) in ce:
+    // exp(y^) - K = K (exp(-e) - 1) = K expm1(-e), free of cancellation and
+    // of binary64 work (the fp64 pipe is narrow on this part).
+    if (certified) {
+        for (int t = tid; t < N; t += blockDim.x) {
+            const double ev = w.kv[(size_t)s * g.n_max + t] * (double)expm1f(-ce[t]);
+            w.R[(size_t)s * g.n_max + t] = g.vol * (ev * ev);
+        }
+    }
+    // otherwise x changed after the last pass: e = y - W x once more
+    for (int t = tid; t < N && !certified; t += blockDim.x) {
         const float4 cx = cell[t];
         DFAcc acc;
         for (int pp = 0; pp < scnt; ++pp) {
