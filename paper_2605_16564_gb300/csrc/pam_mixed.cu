@@ -854,11 +854,12 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
     // moves, a primal active-set phase takes over from the sign-consistent
     // part of the iterate: on the current support it steps towards the
     // sign-constrained minimiser as far as the signs allow (ratio test),
-    // dropping the coefficient that reaches zero, and adds violators only
-    // once the minimiser on the support is
-    // sign-consistent (all violators; the largest only right after a step
-    // that a newly added coefficient blocked at length zero) -- the
-    // objective decreases monotonically, so it ends.
+    // dropping the coefficients that reach zero, and adds all violators only
+    // once the minimiser on the support is sign-consistent. A coefficient
+    // that joined at zero stays (at zero) unless its own sign blocks the
+    // step, so a step of length zero sheds only the wrong-signed newcomers
+    // and the next step keeps the rest -- the objective never increases and
+    // every zero-length step shrinks the support, so it ends.
     int it = 0, scnt = 0;
     float *A = Asm;
     auto factor_support = [&]() {
@@ -890,8 +891,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
         }
         __syncthreads();
     };
-    bool primal = false, single_add = false;
-    int last_added = -1;
+    bool primal = false;
     const int max_pdas = p.max_iters < kMxMaxPdas ? p.max_iters : kMxMaxPdas;
     for (; it < max_pdas; ++it) {
         factor_support();
@@ -950,34 +950,19 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
             for (int pp = tid; pp < scnt; pp += blockDim.x) x[idx[pp]] = rhs[pp];
             __syncthreads();
             gradient_fp();
-            if (single_add) {
-                if (tid == 0) {
-                    float best = tol_pdas;
-                    int bj = -1;
-                    for (int j = 0; j < M; ++j)
-                        if (sg[j] == 0 && fabsf(gr[j]) > best) { best = fabsf(gr[j]); bj = j; }
-                    sh.viol = bj;
-                    if (bj >= 0 && bj != last_added) { sg[bj] = gr[bj] > 0.f ? 1 : -1; x[bj] = 0.f; }
-                }
-                __syncthreads();
-                if (sh.viol < 0 || sh.viol == last_added) break;  // optimal (or stalled on one index)
-                last_added = sh.viol;
-            } else {
-                if (tid == 0) sh.viol = 0;
-                __syncthreads();
-                int mv = 0;
-                for (int j = tid; j < M; j += blockDim.x)
-                    if (sg[j] == 0 && fabsf(gr[j]) > tol_pdas) { sg[j] = gr[j] > 0.f ? 1 : -1; x[j] = 0.f; ++mv; }
-                if (mv) atomicAdd(&sh.viol, mv);
-                __syncthreads();
-                if (sh.viol == 0) break;  // optimal
-            }
-            single_add = false;
+            if (tid == 0) sh.viol = 0;
+            __syncthreads();
+            int mv = 0;
+            for (int j = tid; j < M; j += blockDim.x)
+                if (sg[j] == 0 && fabsf(gr[j]) > tol_pdas) { sg[j] = gr[j] > 0.f ? 1 : -1; x[j] = 0.f; ++mv; }
+            if (mv) atomicAdd(&sh.viol, mv);
+            __syncthreads();
+            if (sh.viol == 0) break;  // optimal
         } else {
             // step alpha towards the minimiser; the blocking coefficients (the
-            // ones whose ratio attains alpha) reach zero and leave the support
+            // ones whose ratio attains alpha) reach zero and leave the support;
+            // a newcomer still at zero after a zero-length step stays
             const float alpha = fminf(sh.dmax, 1.f);
-            single_add = !(alpha > 0.f);  // blocked by a coefficient that just joined
             for (int pp = tid; pp < scnt; pp += blockDim.x) {
                 const int m = idx[pp];
                 const float xs = rhs[pp], x0 = x[m], sgn = (float)sg[m];
@@ -987,11 +972,11 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
                     blocking = fmaxf(a, 0.f) <= alpha * (1.f + 1e-6f);
                 }
                 const float nx = x0 + alpha * (xs - x0);
-                if (blocking || !(nx * sgn > 0.f)) {
+                if (blocking || (x0 != 0.f && !(nx * sgn > 0.f))) {
                     x[m] = 0.f;
                     sg[m] = 0;
                 } else {
-                    x[m] = nx;
+                    x[m] = nx * sgn > 0.f ? nx : 0.f;
                 }
             }
             __syncthreads();
