@@ -369,11 +369,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_f64(Geo g, Par p, doubl
     // Up to kPdasFull full primal-dual corrections; then a primal active-set
     // phase from the sign-consistent part of the iterate: step towards the
     // sign-constrained minimiser on the support as far as the signs allow
-    // (ratio test; the blocking coefficients leave), and add the single
-    // largest violator only when that minimiser is sign-consistent.
+    // (ratio test; the blocking coefficients leave, a coefficient that joined
+    // at zero stays unless its own sign blocks the step), and add all
+    // violators once that minimiser is sign-consistent. The objective never
+    // increases and every zero-length step shrinks the support, so it ends.
     constexpr int kPdasFull = 12;
-    int it = 0, certified = 0, scnt = 0, last_added = -1;
-    bool primal = false, single_add = false;
+    int it = 0, certified = 0, scnt = 0;
+    bool primal = false;
     double *A = Asm;
     for (; it < p.max_iters; ++it) {
         compact_active(sg, M, idx, &sh.cnt);
@@ -412,7 +414,6 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_f64(Geo g, Par p, doubl
             __syncthreads();
             if (sh.bad) {
                 const double alpha = fmin(sh.worst_v, 1.0);
-                single_add = !(alpha > 0.0);  // blocked by a coefficient that just joined
                 for (int pp = tid; pp < scnt; pp += blockDim.x) {
                     const int m = idx[pp];
                     const double xs = rhs[pp], x0 = x[m], sgn = (double)sg[m];
@@ -422,8 +423,8 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_f64(Geo g, Par p, doubl
                         blocking = fmax(a, 0.0) <= alpha * (1.0 + 1e-12);
                     }
                     const double nx = x0 + alpha * (xs - x0);
-                    if (blocking || !(nx * sgn > 0.0)) { x[m] = 0.0; sg[m] = 0; }
-                    else x[m] = nx;
+                    if (blocking || (x0 != 0.0 && !(nx * sgn > 0.0))) { x[m] = 0.0; sg[m] = 0; }
+                    else x[m] = nx * sgn > 0.0 ? nx : 0.0;
                 }
                 __syncthreads();
                 continue;
@@ -465,27 +466,10 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_f64(Geo g, Par p, doubl
             __syncthreads();
             continue;
         }
-        // primal phase, sign-consistent minimiser: the violators join the
-        // support (all of them; only the largest right after a step that the
-        // new ones blocked at length zero)
-        if (single_add) {
-            if (tid == 0) {
-                double best = viol_tol;
-                int bj = -1;
-                for (int j = 0; j < M; ++j)
-                    if (sg[j] == 0 && fabs(gr[j]) > best) { best = fabs(gr[j]); bj = j; }
-                sh.worst = bj;
-                if (bj >= 0 && bj != last_added) { sg[bj] = gr[bj] > 0.0 ? 1 : -1; x[bj] = 0.0; }
-            }
-            __syncthreads();
-            if (sh.worst < 0 || sh.worst == last_added) break;  // stalled on one index
-            last_added = sh.worst;
-        } else {
-            for (int j = tid; j < M; j += blockDim.x)
-                if (sg[j] == 0 && fabs(gr[j]) > viol_tol) { sg[j] = gr[j] > 0.0 ? 1 : -1; x[j] = 0.0; }
-            __syncthreads();
-        }
-        single_add = false;
+        // primal phase, sign-consistent minimiser: the violators join the support
+        for (int j = tid; j < M; j += blockDim.x)
+            if (sg[j] == 0 && fabs(gr[j]) > viol_tol) { sg[j] = gr[j] > 0.0 ? 1 : -1; x[j] = 0.0; }
+        __syncthreads();
     }
     for (int j = tid; j < M; j += blockDim.x) beta[(size_t)s * mc + j] = x[j];
     if (tid == 0) {
