@@ -614,13 +614,19 @@ __device__ __forceinline__ void mx_diag_block(float *A, int k0, int kw, int *fla
         a[j] = (live && j <= lane) ? A[tri_i(i, k0 + j)] : (j == lane ? 1.f : 0.f);
     float my_iv = 1.f;
     bool bad = false;
+    // dn: lane k's pivot a_kk after the updates of columns < k, computed by
+    // lane k itself one step early (the same fma as its share of the bulk
+    // update), so that the column chain is shfl -> rsqrt -> fmul -> fma and
+    // the bulk shuffles stay off it
+    float dn = a[0];
 #pragma unroll
     for (int k = 0; k < 32; ++k) {
-        float d = __shfl_sync(full, a[k], k);
+        float d = __shfl_sync(full, dn, k);
         if (!(d > 0.f)) { bad = true; d = 1.f; }
         const float iv = rsqrtf(d);
         if (lane == k) { a[k] = d * iv; my_iv = iv; }
         else a[k] *= iv;  // above the diagonal (lane < k) the value is never used
+        if (k + 1 < 32) dn = fmaf(-a[k], a[k], a[k + 1]);  // meaningful in lane k + 1
 #pragma unroll
         for (int j = k + 1; j < 32; ++j) a[j] = fmaf(-a[k], __shfl_sync(full, a[k], j), a[j]);
     }
@@ -695,6 +701,8 @@ __device__ void mx_cholesky(float *A, int s, int *flag, float *dinv) {
 // per 32-row block, warp 0 solves the diagonal block with shuffles (fully
 // unrolled; the matrix loads do not depend on the recurrence) and all
 // threads apply the block's contribution to the remaining entries.
+__device__ void mx_chol_backward(const float *A, const float *dinv, int s, float *r);
+
 __device__ void mx_chol_solve(const float *A, const float *dinv, int s, float *r) {
     const unsigned full = 0xffffffffu;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -730,7 +738,13 @@ __device__ void mx_chol_solve(const float *A, const float *dinv, int s, float *r
             __syncthreads();
         }
     }
-    // backward: L^T x = z
+    mx_chol_backward(A, dinv, s, r);
+}
+
+// Backward half: L^T x = z in place.
+__device__ void mx_chol_backward(const float *A, const float *dinv, int s, float *r) {
+    const unsigned full = 0xffffffffu;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int k0 = ((s - 1) / 32) * 32; k0 >= 0 && s > 0; k0 -= 32) {
         const int kw = min(32, s - k0);
         if (warp == 0) {
@@ -862,19 +876,39 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
     // every zero-length step shrinks the support, so it ends.
     int it = 0, scnt = 0;
     float *A = Asm;
+    // The right-hand side b_S - lambda1 s_S rides along as row scnt of the
+    // packed matrix (diagonal 1e30, never a pivot problem): the factorisation
+    // leaves L^-1 rhs there, and only the backward solve remains. (Not when
+    // the support is the whole capacity: no room for the extra row.)
     auto factor_support = [&]() {
         mx_compact(sg, M, idx, &sh.cnt);
         scnt = sh.cnt;
-        A = (tri_i(scnt, 0) * 4 <= kMxFactorBytes) ? Asm
+        const bool aug = scnt < mc;
+        const int nrow = scnt + (aug ? 1 : 0);
+        A = (tri_i(nrow, 0) * 4 <= kMxFactorBytes) ? Asm
             : (w.Lf + (size_t)s * ((size_t)mc * (mc + 1) / 2));
         PROF_MARK(8);
         mx_build(A, G, idx, scnt, mc, lam2);
-        for (int pp = tid; pp < scnt; pp += blockDim.x) rhs[pp] = bv[idx[pp]] - lam1 * (float)sg[idx[pp]];
+        float *arow = A + tri_i(scnt, 0);
+        for (int pp = tid; pp < scnt; pp += blockDim.x) {
+            const float r = bv[idx[pp]] - lam1 * (float)sg[idx[pp]];
+            if (aug) arow[pp] = r;
+            else rhs[pp] = r;
+        }
+        if (aug && tid == 0) arow[scnt] = 1e30f;
         __syncthreads();
         PROF_MARK(9);
-        mx_cholesky(A, scnt, &sh.flag, dinv);
+        mx_cholesky(A, nrow, &sh.flag, dinv);
         PROF_MARK(10);
-        if (!sh.flag) mx_chol_solve(A, dinv, scnt, rhs);
+        if (!sh.flag) {
+            if (aug) {
+                for (int pp = tid; pp < scnt; pp += blockDim.x) rhs[pp] = arow[pp];
+                __syncthreads();
+                mx_chol_backward(A, dinv, scnt, rhs);
+            } else {
+                mx_chol_solve(A, dinv, scnt, rhs);
+            }
+        }
         PROF_MARK(11);
     };
     auto gradient_fp = [&]() {  // gr = b - G~ x; G~ symmetric: rows of the support, coalesced over j
