@@ -204,6 +204,26 @@ __device__ __forceinline__ float shepard_f32_smem(const float4 *sc, const float 
     return num / den;
 }
 
+// Two points at once: every centre read from shared memory serves both
+// (halves the shared-memory traffic per Gaussian). Falls back to the single
+// point form when a sum underflows.
+__device__ __forceinline__ void shepard_f32_smem2(const float4 *sc, const float *sb, int M, const float p0[3],
+                                                  const float p1[3], float *v0, float *v1) {
+    float n0 = 0.f, d0 = 0.f, n1 = 0.f, d1 = 0.f;
+    for (int m = 0; m < M; ++m) {
+        const float4 c = sc[m];
+        const float bm = sb[m];
+        const float e0 = tc::ex2(logit2_e(c, p0[0], p0[1], p0[2]));
+        const float e1 = tc::ex2(logit2_e(c, p1[0], p1[1], p1[2]));
+        n0 = fmaf(bm, e0, n0);
+        d0 += e0;
+        n1 = fmaf(bm, e1, n1);
+        d1 += e1;
+    }
+    *v0 = (d0 > 7.9e-31f) ? n0 / d0 : shepard_f32_smem(sc, sb, M, p0[0], p0[1], p0[2]);
+    *v1 = (d1 > 7.9e-31f) ? n1 / d1 : shepard_f32_smem(sc, sb, M, p1[0], p1[1], p1[2]);
+}
+
 __device__ void stage_f32(const Geo &g, const int32_t *boxes, const double *centres,
                           const double *beta, int s, int M, float4 *sc, float *sb, double o[3]) {
     const int32_t *box = boxes + s * 12;
@@ -229,13 +249,20 @@ __global__ void k_eval_bucket_f32(Geo g, const int32_t *boxes, const double *cen
     float *sb = reinterpret_cast<float *>(sc + g.m_cap);
     double o[3];
     stage_f32(g, boxes, centres, beta, s, M, sc, sb, o);
-    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
-        const int p = perm[i];
-        double x[3] = {0, 0, 0};
-        for (int a = 0; a < g.dim; ++a) x[a] = pts[(int64_t)p * g.dim + a];
-        const float v = shepard_f32_smem(sc, sb, M, (float)(x[0] - o[0]), (float)(x[1] - o[1]),
-                                         (float)(x[2] - o[2]));
-        out[p] = log_space ? (double)v : exp_f32(v);
+    // two points per thread and pass: i and i + blockDim.x
+    for (int i = b + threadIdx.x; i < e; i += 2 * blockDim.x) {
+        const int i1 = i + blockDim.x;
+        const bool two = i1 < e;
+        const int p0 = perm[i], p1 = two ? perm[i1] : p0;
+        float x0[3] = {0.f, 0.f, 0.f}, x1[3] = {0.f, 0.f, 0.f};
+        for (int a = 0; a < g.dim; ++a) {
+            x0[a] = (float)(pts[(int64_t)p0 * g.dim + a] - o[a]);
+            x1[a] = (float)(pts[(int64_t)p1 * g.dim + a] - o[a]);
+        }
+        float v0, v1;
+        shepard_f32_smem2(sc, sb, M, x0, x1, &v0, &v1);
+        out[p0] = log_space ? (double)v0 : exp_f32(v0);
+        if (two) out[p1] = log_space ? (double)v1 : exp_f32(v1);
     }
 }
 
