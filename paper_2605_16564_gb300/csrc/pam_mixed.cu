@@ -331,7 +331,9 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
         const int pth = tid - 32 * kTcIssuers;  // 0 .. 32 * kTcProdWarps - 1
         const int tpr = (4 * Rl <= 32 * kTcProdWarps) ? 4 : (2 * Rl <= 32 * kTcProdWarps ? 2 : 1);
         const int nkg = 4 / tpr;
-        const int r = pth / tpr, part = pth % tpr;
+        // a warp covers 32 consecutive rows with one set of k-groups: its cell
+        // reads are broadcasts and its stores one contiguous 512-byte run
+        const int pw = pth >> 5, part = pw % tpr, r = (pw / tpr) * 32 + lane;
         const bool live = r < Rl;
         const float4 cc = live ? sc[r] : make_float4(0.f, 0.f, 0.f, 0.f);
         float bacc = 0.f;
