@@ -153,7 +153,7 @@ def _peaks():
 FP64_NOMINAL_TFLOPS = 1.25
 
 
-def accounting(fit, Kd, levels, pam):
+def accounting(fit, Kd, levels, pam, seed=None):
     """Algorithmic work of one step, counted from the sizes each solve actually
     had (the fit is re-run level by level outside the timed region):
       gram_flops  sum N_i M_i (M_i + 1): the multiply-adds of the upper
@@ -165,7 +165,11 @@ def accounting(fit, Kd, levels, pam):
     fit_levels = [0] + [1] * levels
     for r, _ in enumerate(fit_levels):
         if r == 0:
+            if seed is not None:
+                seed()
+                fit.params.warm_start = 1
             pam.pam_fit_subdomains(fit.problem, fit.params, fit.plan, Kd, fit.model, fit.workspace)
+            fit.params.warm_start = 0
         else:
             pam.pam_refine(fit.problem, fit.params, fit.plan, Kd, fit.model, 1, fit.workspace)
         info = fit.model.info.cpu().numpy()
@@ -254,8 +258,40 @@ def run_pam(args, rank, ws):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)  # > L2 (129 MB)
     stream = torch.cuda.current_stream()
 
+    # learned warm start of the level-0 solves (3-D decompositions, mixed
+    # form): trained once, outside the timed region, on other seeded fields
+    # of the same workload; inference and seeding run inside every step
+    lw, learned = None, None
+    if prec == pam.PAM_PREC_MIXED and len(shape) == 3 and not args.no_learned:
+        from paper_2605_16564_gb300 import warmstart
+        t0 = time.perf_counter()
+        lw = warmstart.LayeredWarmStart(dev, batch=256, seed=0)
+        train = [torch.from_numpy(W["field"](shard_seed(W["seed"], rank) * 1000 + 100 + i)).to(dev)
+                 for i in range(8)]
+        lw.train(fit, train, epochs=8)
+        torch.cuda.synchronize()
+        train_s = time.perf_counter() - t0
+        del train
+        it0 = lambda: (fit.model.info.cpu().numpy()[:, pam.INFO_ITERS] % 100).mean()
+        fit.fit(Kd, levels=0)
+        cold_it = float(it0())
+        lw.seed(fit, Kd)
+        fit.fit(Kd, levels=0, warm_start=True)
+        warm_it = float(it0())
+        learned = {"kind": "learned (PAM_NN_LAYERED3D network seeds the level-0 active set)",
+                   "train_fields": 8, "train_samples": 8 * fit.plan.n_subdomains, "train_s": round(train_s, 2),
+                   "seed_threshold": lw.threshold, "level0_active_set_steps_cold": round(cold_it, 3),
+                   "level0_active_set_steps_learned": round(warm_it, 3)}
+
+    def fit_step():
+        if lw is not None:
+            lw.seed(fit, Kd)
+            fit.fit(Kd, warm_start=True)
+        else:
+            fit.fit(Kd)
+
     def step():
-        fit.fit(Kd)
+        fit_step()
         fit.eval(ptsd, out=out)
         return fit.errors(Kd)
 
@@ -295,6 +331,30 @@ def run_pam(args, rank, ws):
     step_ms = max_over_ranks(sum(times) / len(times), ws, dev)
     value = n_cells * ws / (step_ms / 1e3)
     info = fit.model.info.cpu().numpy()
+    if lw is not None:
+        # the same step without the learned seed (level 0 from beta = 0), for comparison
+        plain_times = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fit.fit(Kd)
+            fit.eval(ptsd, out=out)
+            fit.errors(Kd)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                plain_times.append(e0.elapsed_time(e1))
+        t0 = torch.cuda.Event(enable_timing=True)
+        t1 = torch.cuda.Event(enable_timing=True)
+        t0.record(stream)
+        lw.seed(fit, Kd)
+        t1.record(stream)
+        torch.cuda.synchronize()
+        learned["step_ms_learned"] = round(step_ms, 3)
+        learned["step_ms_without_learned"] = round(sum(plain_times) / len(plain_times), 3)
+        learned["inference_ms"] = round(t0.elapsed_time(t1), 3)
 
     # --- end to end through the C ABI from pinned host buffers -------------
     Kh = torch.from_numpy(np.ascontiguousarray(K)).pin_memory()
@@ -308,7 +368,7 @@ def run_pam(args, rank, ws):
         t0 = time.perf_counter()
         Kd.copy_(Kh, non_blocking=True)
         ptsd.copy_(ptsh, non_blocking=True)
-        fit.fit(Kd)
+        fit_step()
         fit.eval(ptsd, out=out)
         errh = fit.errors(Kd)
         outh.copy_(out, non_blocking=True)
@@ -343,7 +403,7 @@ def run_pam(args, rank, ws):
 
     # --- roofline of every kernel family, the dominant one first ------------
     peaks, peak_src = _peaks()
-    work = accounting(fit, Kd, W["params"]["levels"], pam)
+    work = accounting(fit, Kd, W["params"]["levels"], pam, seed=(lambda: lw.seed(fit, Kd)) if lw else None)
     owners = owner_counts(W, pts)
     work["eval_pairs"] = float(np.sum(owners * work["m_final"]))
     roofs = roofline_entries(phase_ms, work, n_pts, prec == pam.PAM_PREC_MIXED, peaks, peak_src)
@@ -353,7 +413,7 @@ def run_pam(args, rank, ws):
 
     return dict(value=value, step_ms=step_ms, times=times, err=err, phase_ms=phase_ms, launches=launches,
                 clocks=clk.summary(), e2e_s=e2e_s, h2d=h2d, d2h=d2h, plain=plain, roof=roof, roofs=roofs,
-                prec_name=prec_name, n_cells=n_cells, n_pts=n_pts, info=info)
+                prec_name=prec_name, n_cells=n_cells, n_pts=n_pts, info=info, learned=learned)
 
 
 def owner_counts(W, pts):
@@ -427,6 +487,7 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=192, help="subdomains in the oracle baseline sample")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
+    ap.add_argument("--no-learned", action="store_true", help="3-D mixed form without the learned warm start")
     args = ap.parse_args()
     rank, ws = _dist()
     W = WORKLOADS[args.workload]
@@ -481,7 +542,9 @@ def main():
         "metric": METRIC, "value": r["value"], "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": r["step_ms"], "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "f64" if r["prec_name"] == "fp64" else "bf16x3+f32+f64",
-        "data": "synthetic", "config": dict(cfg, precision=r["prec_name"]),
+        "data": "synthetic",
+        "config": dict(cfg, precision=r["prec_name"],
+                       warm_start=r["learned"]["kind"] if r["learned"] else "previous level (Algorithm 1)"),
         "eval_pts_per_s": r["n_pts"] * ws / (eval_ms / 1e3) if eval_ms else None,
         "fit_cells_per_s": None,
         "l1_rel": r["err"]["l1"], "l2_rel": r["err"]["l2"],
@@ -494,6 +557,7 @@ def main():
         "phase_ms_per_step": {k: round(v[0], 4) for k, v in r["phase_ms"].items()},
         "roofline_all": r["roofs"],
         "plain_fp64": r["plain"],
+        "learned_warm_start": r["learned"],
     }
     fit_ms = sum(v[0] for k, v in r["phase_ms"].items() if k not in ("eval", "errors"))
     line["fit_cells_per_s"] = r["n_cells"] * ws / (fit_ms / 1e3) if fit_ms else None

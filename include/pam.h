@@ -269,26 +269,60 @@ pam_status pam_errors_noalloc(const pam_problem *prob, const pam_plan *plan,
 
 /*
  * Learned warm start (spec addition; the paper has no learned part).
- * A convolutional network maps a 32 x 32 patch of log10(K)/3 to 256 support
- * logits and 256 coefficients / 4 of the patch's 16 x 16 dictionary:
- * conv3x3 stride 2 (1->32), (32->64), (64->128), conv3x3 stride 1 (128->128),
- * each + ReLU, dense 2048->256 + ReLU, dense 256->512. Parameters are fp32
- * (flat, layout from pam_nn_layer_offsets: per layer weight offset, bias
- * offset, rows, cols, with W[row][col] and conv columns (ky*3+kx)*cin+c,
- * zero-padded to a multiple of 32); the passes run in bf16 on the tensor
- * cores with fp32 accumulation. batch: a multiple of 32.
+ * A convolutional network maps a subdomain patch of log10(K)/3 (clipped to
+ * [-1, 1], NHWC) to n_out support logits and n_out coefficients / 4 of the
+ * patch's initial dictionary. Two architectures (arch):
+ *   PAM_NN_PATCH2D   input [32][32][1] (a 32 x 32 patch), n_out = 256 (its
+ *                    16 x 16 dictionary): conv3x3 stride 2 (1->32),
+ *                    (32->64), (64->128), conv3x3 stride 1 (128->128),
+ *                    dense 2048->256, dense 256->512;
+ *   PAM_NN_LAYERED3D input [16][16][8] (a 3-D patch of up to 16 x 16 x 8
+ *                    cells, x and y as pixels, z layers as channels),
+ *                    n_out = 32 (a 4 x 4 x 2 lattice): conv3x3 stride 2
+ *                    (8->32), (32->64), conv3x3 stride 1 (64->64),
+ *                    (64->64), dense 1024->128, dense 128->64;
+ * ReLU after every layer but the last. Parameters are fp32 (flat, layout
+ * from pam_nn_layer_offsets: per layer weight offset, bias offset, rows,
+ * cols, with W[row][col] and conv columns (ky*3+kx)*cin+c, zero-padded to a
+ * multiple of 32); the passes run in bf16 on the tensor cores with fp32
+ * accumulation. batch: a multiple of 32. PAM_ERR_INVALID_ARG for an
+ * unknown arch.
  */
-pam_status pam_nn_sizes(int batch, int64_t *n_params, size_t *workspace_bytes);
-pam_status pam_nn_layer_offsets(int64_t *h_offsets /* [6][4] */);
-/* d_x [batch][32][32] fp32; d_out [batch][512] fp32 (logits | beta/4). */
-pam_status pam_nn_forward(const float *d_params, const float *d_x, int batch, float *d_out,
+enum { PAM_NN_PATCH2D = 0, PAM_NN_LAYERED3D = 1 };
+pam_status pam_nn_sizes(int arch, int batch, int64_t *n_params, size_t *workspace_bytes);
+/* h_geo [3] = (input pixels per side, input channels, n_out). */
+pam_status pam_nn_geometry(int arch, int32_t *h_geo);
+pam_status pam_nn_layer_offsets(int arch, int64_t *h_offsets /* [6][4] */);
+/* d_x [batch][h][h][c] fp32; d_out [batch][2 n_out] fp32 (logits | beta/4). */
+pam_status pam_nn_forward(int arch, const float *d_params, const float *d_x, int batch, float *d_out,
                           void *d_workspace, size_t workspace_bytes, void *stream);
 /* Forward + loss + backward: d_grads (same layout as the parameters) and
  * d_loss [2] = (mean BCE of the support logits against d_support in {0,1},
- * mean squared error of beta/4 against d_beta / 4), both [batch][256]. */
-pam_status pam_nn_gradients(const float *d_params, const float *d_x, const float *d_support,
+ * mean squared error of beta/4 against d_beta / 4), both [batch][n_out]. */
+pam_status pam_nn_gradients(int arch, const float *d_params, const float *d_x, const float *d_support,
                             const float *d_beta, int batch, float *d_grads, float *d_loss,
                             void *d_workspace, size_t workspace_bytes, void *stream);
+/*
+ * PAM_NN_LAYERED3D inputs of every subdomain of a 3-D problem, from its
+ * patch (the pam_partition layout) and the cell values d_K:
+ * d_x [n_rows][16][16][8] fp32, row s = subdomain s, entry [iy][ix][iz]
+ * = clip(log10 K / 3, -1, 1) at patch cell (ix, iy, iz), zero outside the
+ * patch and in rows s >= S. n_rows >= S (the network batch). Returns
+ * PAM_ERR_UNSUPPORTED if a patch exceeds 16 x 16 x 8 cells, and
+ * PAM_ERR_INVALID_ARG for a problem that is not 3-D. Asynchronous.
+ */
+pam_status pam_nn_layered_inputs(const pam_problem *prob, const pam_plan *plan, const double *d_K,
+                                 float *d_x, int n_rows, void *stream);
+/*
+ * Seeds the active set from a network output d_out [>= S][2 n_out]: for
+ * every subdomain s and initial dictionary entry j < n_out,
+ * model->beta[s][j] = b if |b| > threshold else 0, b = 4 d_out[s][n_out + j]
+ * (the coefficients the network predicts large; their signs seed the
+ * support of the next pam_fit_subdomains call with warm_start = 1). The
+ * plan's initial dictionary must hold exactly n_out entries. Asynchronous.
+ */
+pam_status pam_nn_seed(const pam_plan *plan, int arch, const float *d_out, float threshold,
+                       pam_model *model, void *stream);
 /* One AdamW step (decoupled weight decay) on n fp32 parameters; step >= 1. */
 pam_status pam_nn_adamw(float *d_params, const float *d_grads, float *d_m, float *d_v, int64_t n,
                         float lr, float beta1, float beta2, float eps, float weight_decay, int step,

@@ -1,16 +1,21 @@
 // pam_nn.cu -- the learned warm start: a small convolutional network that
-// maps a 32 x 32 patch of log10 K to a predicted support (256 logits) and
-// initial coefficients (256 values) of the patch's 16 x 16 dictionary.
-// Forward and backward passes are hand-written: every contraction (the
-// im2col convolutions and the dense layers, forward and backward) runs on
-// the tcgen05 tensor cores in bf16 with fp32 accumulation (k_gemm_bf16);
-// elementwise work, the loss and AdamW are small fp32 kernels. The layer
-// sequence is driven from host code in this file.
-//
-// Network (NHWC activations, bf16):
-//   x [B,32,32,1] -> conv3x3 s2 (32) -> ReLU -> conv3x3 s2 (64) -> ReLU
-//     -> conv3x3 s2 (128) -> ReLU -> conv3x3 s1 (128) -> ReLU -> flatten 2048
-//     -> dense 256 -> ReLU -> dense 512 = [256 support logits | 256 beta / 4]
+// maps a subdomain patch of log10 K to a predicted support (logits) and
+// initial coefficients of the patch's initial dictionary. Two
+// architectures share the code:
+//   PAM_NN_PATCH2D   x [B,32,32,1] (a 32 x 32 patch), 256 outputs (16 x 16
+//                    dictionary):
+//     conv3x3 s2 (32) -> conv3x3 s2 (64) -> conv3x3 s2 (128) -> conv3x3 s1
+//     (128) -> flatten 2048 -> dense 256 -> dense 512
+//   PAM_NN_LAYERED3D x [B,16,16,8] (a 3-D patch up to 16 x 16 x 8 cells, its
+//                    z layers as channels), 32 outputs (4 x 4 x 2 lattice):
+//     conv3x3 s2 (32) -> conv3x3 s2 (64) -> conv3x3 s1 (64) -> conv3x3 s1
+//     (64) -> flatten 1024 -> dense 128 -> dense 64
+// with ReLU after every layer but the last; output = [n_out support logits
+// | n_out beta / 4]. Forward and backward passes are hand-written: every
+// contraction (the im2col convolutions and the dense layers, forward and
+// backward) runs on the tcgen05 tensor cores in bf16 with fp32 accumulation
+// (k_gemm_bf16); elementwise work, the loss and AdamW are small fp32
+// kernels. The layer sequence is driven from host code in this file.
 // Loss: mean BCE-with-logits on the support + mean squared error of the
 // scaled coefficients.
 #include <cuda_bf16.h>
@@ -26,32 +31,41 @@ namespace nn {
 
 using bf16 = __nv_bfloat16;
 
-constexpr int kOut = 256;        // dictionary entries of a patch (16 x 16)
 constexpr float kBetaScale = 4.f;
 
 struct Conv {
     int hin, cin, hout, cout, stride, kpad;  // kpad = 9 cin rounded up to 32
 };
-constexpr int kNConv = 4;
-constexpr Conv kConv[kNConv] = {
-    {32, 1, 16, 32, 2, 32}, {16, 32, 8, 64, 2, 288}, {8, 64, 4, 128, 2, 576}, {4, 128, 4, 128, 1, 1152}};
-constexpr int kFlat = 4 * 4 * 128;
 struct Dense {
     int in, out;
 };
-constexpr Dense kDense[2] = {{kFlat, 256}, {256, 2 * kOut}};
+constexpr int kNConv = 4;
+struct Arch {
+    int h0, c0;      // input: h0 x h0 pixels, c0 channels (NHWC)
+    Conv conv[kNConv];
+    int flat;        // the last convolution's output, flattened (NHWC)
+    Dense dense[2];
+    int nout;        // dictionary entries predicted; the output has 2 nout values
+};
+constexpr int kNArch = 2;
+constexpr Arch kArch[kNArch] = {
+    {32, 1, {{32, 1, 16, 32, 2, 32}, {16, 32, 8, 64, 2, 288}, {8, 64, 4, 128, 2, 576}, {4, 128, 4, 128, 1, 1152}},
+     4 * 4 * 128, {{2048, 256}, {256, 512}}, 256},
+    {16, 8, {{16, 8, 8, 32, 2, 96}, {8, 32, 4, 64, 2, 288}, {4, 64, 4, 64, 1, 576}, {4, 64, 4, 64, 1, 576}},
+     4 * 4 * 64, {{1024, 128}, {128, 64}}, 32},
+};
 
 // Flat fp32 parameter layout: per layer W [out][k] then b [out].
 struct Layout {
     int64_t w[6], b[6], total;
     int rows[6], cols[6];
 };
-static Layout layout() {
+static Layout layout(const Arch &A) {
     Layout L;
     int64_t off = 0;
     for (int l = 0; l < 6; ++l) {
-        int rows = l < 4 ? kConv[l].cout : kDense[l - 4].out;
-        int cols = l < 4 ? kConv[l].kpad : kDense[l - 4].in;
+        int rows = l < 4 ? A.conv[l].cout : A.dense[l - 4].out;
+        int cols = l < 4 ? A.conv[l].kpad : A.dense[l - 4].in;
         L.rows[l] = rows;
         L.cols[l] = cols;
         L.w[l] = off;
@@ -102,13 +116,15 @@ __global__ void __launch_bounds__(kGT, 1) k_gemm_bf16(const bf16 *A, int lda, co
     const uint32_t lbo = 128u * 16u, sbo = 128u;
     const int nk = K / 32;
     int issued = 0;
-    for (int kc = 0; kc < nk; ++kc) {
-        const int buf = kc & 1;
-        if (kc >= 2 && !tc::mbar_wait(&mbar[buf], ((kc - 2) >> 1) & 1, kGemmWait)) timed_out = 1;
-        uint8_t *ta = smem + (size_t)buf * 16384;
-        uint8_t *tb = ta + 8192;
-        // 128 rows x 4 segments of 8 bf16 for A and for B: 1024 segments
-        for (int e = tid; e < 1024; e += kGT) {
+    // 128 rows x 4 segments of 8 bf16 for A and for B: 1024 segments, four
+    // per thread; the next chunk's segments are loaded into registers while
+    // the current one is synchronised and multiplied
+    constexpr int kSeg = 1024 / kGT;
+    uint4 pre[kSeg];
+    auto load_chunk = [&](int kc) {
+#pragma unroll
+        for (int u = 0; u < kSeg; ++u) {
+            const int e = tid + u * kGT;
             const int isb = e >> 9, seg = e & 511, r = seg >> 2, kg = seg & 3;
             uint4 v = make_uint4(0, 0, 0, 0);
             if (isb == 0) {
@@ -116,9 +132,23 @@ __global__ void __launch_bounds__(kGT, 1) k_gemm_bf16(const bf16 *A, int lda, co
             } else {
                 if (n0 + r < N) v = *reinterpret_cast<const uint4 *>(B + (size_t)(n0 + r) * ldb + kc * 32 + kg * 8);
             }
-            const uint32_t off = (uint32_t)(kg * 16 + (r >> 3)) * 128u + (uint32_t)(r & 7) * 16u;
-            *reinterpret_cast<uint4 *>((isb ? tb : ta) + off) = v;
+            pre[u] = v;
         }
+    };
+    if (nk > 0) load_chunk(0);
+    for (int kc = 0; kc < nk; ++kc) {
+        const int buf = kc & 1;
+        if (kc >= 2 && !tc::mbar_wait(&mbar[buf], ((kc - 2) >> 1) & 1, kGemmWait)) timed_out = 1;
+        uint8_t *ta = smem + (size_t)buf * 16384;
+        uint8_t *tb = ta + 8192;
+#pragma unroll
+        for (int u = 0; u < kSeg; ++u) {
+            const int e = tid + u * kGT;
+            const int isb = e >> 9, seg = e & 511, r = seg >> 2, kg = seg & 3;
+            const uint32_t off = (uint32_t)(kg * 16 + (r >> 3)) * 128u + (uint32_t)(r & 7) * 16u;
+            *reinterpret_cast<uint4 *>((isb ? tb : ta) + off) = pre[u];
+        }
+        if (kc + 1 < nk) load_chunk(kc + 1);
         tc::fence_proxy_async_smem();
         __syncthreads();
         if (timed_out) break;
@@ -262,24 +292,24 @@ __global__ void k_colsum(const bf16 *dz, int rows, int cols, float *db) {
     db[j] = acc;
 }
 
-// Loss and its gradient wrt the 512 outputs. out [B][512] fp32 = [logits |
-// scaled beta]; targets support [B][256] in {0,1}, beta [B][256].
+// Loss and its gradient wrt the 2 nout outputs. out [B][2 nout] fp32 =
+// [logits | scaled beta]; targets support [B][nout] in {0,1}, beta [B][nout].
 // loss[0] = BCE mean, loss[1] = MSE mean (one block, fixed order).
-__global__ void k_loss(const float *out, const float *support, const float *beta, int B, float *dout,
+__global__ void k_loss(const float *out, const float *support, const float *beta, int B, int nout, float *dout,
                        float *loss) {
     __shared__ float red[2][256];
-    const int n = B * kOut;
+    const int n = B * nout;
     float bce = 0.f, mse = 0.f;
     for (int e = threadIdx.x; e < n; e += blockDim.x) {
-        const int b = e / kOut, j = e % kOut;
-        const float z = out[(size_t)b * 2 * kOut + j], s = support[e];
+        const int b = e / nout, j = e % nout;
+        const float z = out[(size_t)b * 2 * nout + j], s = support[e];
         const float sp = fmaxf(z, 0.f) + log1pf(expf(-fabsf(z)));  // softplus
         bce += sp - s * z;
         const float sg = 1.f / (1.f + expf(-z));
-        if (dout) dout[(size_t)b * 2 * kOut + j] = (sg - s) / (float)n;
-        const float d = out[(size_t)b * 2 * kOut + kOut + j] - beta[e] / kBetaScale;
+        if (dout) dout[(size_t)b * 2 * nout + j] = (sg - s) / (float)n;
+        const float d = out[(size_t)b * 2 * nout + nout + j] - beta[e] / kBetaScale;
         mse += d * d;
-        if (dout) dout[(size_t)b * 2 * kOut + kOut + j] = 2.f * d / (float)n;
+        if (dout) dout[(size_t)b * 2 * nout + nout + j] = 2.f * d / (float)n;
     }
     red[0][threadIdx.x] = bce;
     red[1][threadIdx.x] = mse;
@@ -305,16 +335,60 @@ __global__ void k_adamw(float *p, const float *g, float *m, float *v, int64_t n,
     }
 }
 
+// Network input of the layered 3-D architecture: one row per subdomain,
+// x[row][iy][ix][iz] = clip(log10 K / 3, -1, 1) at patch cell (ix, iy, iz),
+// zero outside the patch (and in rows past the last subdomain).
+__global__ void k_layered_inputs(Geo g, const double *K, int h0, int c0, float *x) {
+    const int row = blockIdx.x;
+    float *xr = x + (size_t)row * h0 * h0 * c0;
+    const bool live = row < g.S;
+    // the subdomain's patch (core +- overlap, clipped), as the partition lays it out
+    int plo[3] = {0, 0, 0}, pw[3] = {0, 0, 0};
+    if (live) {
+        const int jj[3] = {row % g.p[0], (row / g.p[0]) % g.p[1], row / (g.p[0] * g.p[1])};
+        for (int a = 0; a < 3; ++a) {
+            int64_t lo = ((int64_t)jj[a] * g.n[a]) / g.p[a] - g.overlap;
+            int64_t hi = ((int64_t)(jj[a] + 1) * g.n[a]) / g.p[a] + g.overlap;
+            if (lo < 0) lo = 0;
+            if (hi > g.n[a]) hi = g.n[a];
+            plo[a] = (int)lo;
+            pw[a] = (int)(hi - lo);
+        }
+    }
+    for (int e = threadIdx.x; e < h0 * h0 * c0; e += blockDim.x) {
+        const int iz = e % c0, ix = (e / c0) % h0, iy = e / (c0 * h0);
+        float v = 0.f;
+        if (live && ix < pw[0] && iy < pw[1] && iz < pw[2]) {
+            const int64_t gi = (int64_t)(plo[0] + ix) +
+                               (int64_t)g.n[0] * ((int64_t)(plo[1] + iy) + (int64_t)g.n[1] * (plo[2] + iz));
+            v = fminf(fmaxf(log10f((float)K[gi]) * (1.f / 3.f), -1.f), 1.f);  // a bf16 input: fp32 suffices
+        }
+        xr[e] = v;
+    }
+}
+
+// Warm start from the network output: beta[s][j] = beta_hat if |beta_hat|
+// > threshold else 0, beta_hat = 4 out[s][nout + j], for the nout entries
+// of the initial dictionary.
+__global__ void k_seed(const float *out, int S, int nout, int m_cap, float threshold, double *beta) {
+    const int s = blockIdx.x;
+    if (s >= S) return;
+    for (int j = threadIdx.x; j < nout; j += blockDim.x) {
+        const float bh = out[(size_t)s * 2 * nout + nout + j] * kBetaScale;
+        beta[(size_t)s * m_cap + j] = fabsf(bh) > threshold ? (double)bh : 0.0;
+    }
+}
+
 static unsigned grid_for(int64_t n) { return (unsigned)std::min<int64_t>((n + 255) / 256, 4096); }
 
 // -------------------------------------------------------------- driver ----
 struct Ws {
     bf16 *pw;             // bf16 copy of the parameters
-    bf16 *x0;             // [B,32,32,1]
+    bf16 *x0;             // [B,h0,h0,c0]
     bf16 *cols[4];        // im2col buffers
     bf16 *act[6];         // layer outputs (bf16, post-ReLU; act[5] = out as bf16, unused)
-    float *out;           // [B,512] fp32 network output
-    float *dout;          // [B,512]
+    float *out;           // [B,2 n_out] fp32 network output
+    float *dout;          // [B,2 n_out]
     float *dbuf0, *dbuf1; // fp32 gradient scratch (max activation size)
     bf16 *dz;             // bf16 pre-activation gradient
     bf16 *tA, *tB;        // transposes
@@ -325,7 +399,7 @@ struct Ws {
 
 static size_t al(size_t v) { return (v + 255) / 256 * 256; }
 
-static Ws carve(int B, void *base) {
+static Ws carve(const Arch &A, int B, void *base) {
     Ws w;
     size_t off = 0;
     auto take = [&](size_t bytes) -> char * {
@@ -333,12 +407,12 @@ static Ws carve(int B, void *base) {
         off = al(off + bytes);
         return p;
     };
-    const Layout L = layout();
+    const Layout L = layout(A);
     w.pw = (bf16 *)take((size_t)L.total * 2);
-    w.x0 = (bf16 *)take((size_t)B * 32 * 32 * 2);
+    w.x0 = (bf16 *)take((size_t)B * A.h0 * A.h0 * A.c0 * 2);
     size_t maxact = 0, maxcols = 0;
     for (int l = 0; l < 4; ++l) {
-        const Conv &c = kConv[l];
+        const Conv &c = A.conv[l];
         size_t cols = (size_t)B * c.hout * c.hout * c.kpad;
         size_t act = (size_t)B * c.hout * c.hout * c.cout;
         maxcols = std::max(maxcols, cols);
@@ -346,11 +420,12 @@ static Ws carve(int B, void *base) {
         w.cols[l] = (bf16 *)take(cols * 2);
         w.act[l] = (bf16 *)take(act * 2);
     }
-    w.act[4] = (bf16 *)take((size_t)B * 256 * 2);
-    w.act[5] = (bf16 *)take((size_t)B * 512 * 2);
-    maxact = std::max(maxact, std::max(maxcols, (size_t)B * kFlat));
-    w.out = (float *)take((size_t)B * 512 * 4);
-    w.dout = (float *)take((size_t)B * 512 * 4);
+    w.act[4] = (bf16 *)take((size_t)B * A.dense[0].out * 2);
+    w.act[5] = (bf16 *)take((size_t)B * A.dense[1].out * 2);
+    maxact = std::max(maxact, std::max(maxcols, (size_t)B * A.flat));
+    maxact = std::max(maxact, (size_t)B * A.dense[0].out);
+    w.out = (float *)take((size_t)B * A.dense[1].out * 4);
+    w.dout = (float *)take((size_t)B * A.dense[1].out * 4);
     w.dbuf0 = (float *)take(maxact * 4);
     w.dbuf1 = (float *)take(maxact * 4);
     w.dz = (bf16 *)take(maxact * 2);
@@ -363,14 +438,15 @@ static Ws carve(int B, void *base) {
 }
 
 // Forward pass; activations stay in the workspace for the backward pass.
-static void forward(const float *params, const float *x, int B, Ws &w, cudaStream_t st) {
-    const Layout L = layout();
+static void forward(const Arch &A, const float *params, const float *x, int B, Ws &w, cudaStream_t st) {
+    const Layout L = layout(A);
+    const int64_t nx = (int64_t)B * A.h0 * A.h0 * A.c0;
     k_cast_bf16<<<grid_for(L.total), 256, 0, st>>>(params, w.pw, L.total);
-    k_cast_bf16<<<grid_for((int64_t)B * 1024), 256, 0, st>>>(x, w.x0, (int64_t)B * 1024);
+    k_cast_bf16<<<grid_for(nx), 256, 0, st>>>(x, w.x0, nx);
     count_launches(2);
     const bf16 *in = w.x0;
     for (int l = 0; l < 4; ++l) {
-        const Conv &c = kConv[l];
+        const Conv &c = A.conv[l];
         const int64_t rows = (int64_t)B * c.hout * c.hout;
         k_im2col<<<grid_for(rows * c.kpad), 256, 0, st>>>(in, B, c.hin, c.cin, c.hout, c.stride, c.kpad, w.cols[l]);
         count_launches(1);
@@ -378,10 +454,11 @@ static void forward(const float *params, const float *x, int B, Ws &w, cudaStrea
              params + L.b[l], 1, w.status, st);
         in = w.act[l];
     }
-    // dense layers: act[3] viewed as [B][2048] (NHWC flatten)
-    gemm(w.act[3], kFlat, w.pw + L.w[4], kFlat, B, 256, kFlat, nullptr, w.act[4], 256, params + L.b[4], 1,
+    // dense layers: act[3] viewed as [B][flat] (NHWC flatten)
+    const int d0 = A.dense[0].out, d1 = A.dense[1].out;
+    gemm(w.act[3], A.flat, w.pw + L.w[4], A.flat, B, d0, A.flat, nullptr, w.act[4], d0, params + L.b[4], 1,
          w.status, st);
-    gemm(w.act[4], 256, w.pw + L.w[5], 256, B, 512, 256, w.out, nullptr, 512, params + L.b[5], 0, w.status, st);
+    gemm(w.act[4], d0, w.pw + L.w[5], d0, B, d1, d0, w.out, nullptr, d1, params + L.b[5], 0, w.status, st);
 }
 
 // Backward of a layer y = relu(X W^T + b) (or linear for the output layer):
@@ -409,16 +486,17 @@ static void layer_backward(const float *dY, const bf16 *Y, bool relu, const bf16
     }
 }
 
-static void backward(const float *params, int B, float *grads, Ws &w, cudaStream_t st) {
-    const Layout L = layout();
+static void backward(const Arch &A, const float *params, int B, float *grads, Ws &w, cudaStream_t st) {
+    const Layout L = layout(A);
+    const int d0 = A.dense[0].out, d1 = A.dense[1].out;
     // output dense (linear)
-    layer_backward(w.dout, nullptr, false, w.act[4], w.pw + L.w[5], B, 512, 256, grads + L.w[5], grads + L.b[5],
+    layer_backward(w.dout, nullptr, false, w.act[4], w.pw + L.w[5], B, d1, d0, grads + L.w[5], grads + L.b[5],
                    w.dbuf0, w, st);
-    layer_backward(w.dbuf0, w.act[4], true, w.act[3], w.pw + L.w[4], B, 256, kFlat, grads + L.w[4],
+    layer_backward(w.dbuf0, w.act[4], true, w.act[3], w.pw + L.w[4], B, d0, A.flat, grads + L.w[4],
                    grads + L.b[4], w.dbuf1, w, st);
     float *dy = w.dbuf1, *other = w.dbuf0;
     for (int l = 3; l >= 0; --l) {
-        const Conv &c = kConv[l];
+        const Conv &c = A.conv[l];
         const int rows = B * c.hout * c.hout;
         float *dcols = l > 0 ? other : nullptr;
         layer_backward(dy, w.act[l], true, w.cols[l], w.pw + L.w[l], rows, c.cout, c.kpad, grads + L.w[l],
@@ -440,16 +518,29 @@ using namespace pam::nn;
 
 extern "C" {
 
-pam_status pam_nn_sizes(int batch, int64_t *n_params, size_t *workspace_bytes) {
-    if (batch < 1 || batch > 65536 || batch % 32 != 0) return PAM_ERR_INVALID_ARG;
-    if (n_params) *n_params = layout().total;
-    if (workspace_bytes) *workspace_bytes = carve(batch, nullptr).bytes;
+static const Arch *arch_of(int arch) { return (arch >= 0 && arch < kNArch) ? &kArch[arch] : nullptr; }
+
+pam_status pam_nn_sizes(int arch, int batch, int64_t *n_params, size_t *workspace_bytes) {
+    const Arch *A = arch_of(arch);
+    if (!A || batch < 1 || batch > 65536 || batch % 32 != 0) return PAM_ERR_INVALID_ARG;
+    if (n_params) *n_params = layout(*A).total;
+    if (workspace_bytes) *workspace_bytes = carve(*A, batch, nullptr).bytes;
     return PAM_OK;
 }
 
-pam_status pam_nn_layer_offsets(int64_t *h_offsets) {
-    if (!h_offsets) return PAM_ERR_INVALID_ARG;
-    const Layout L = layout();
+pam_status pam_nn_geometry(int arch, int32_t *h_geo) {
+    const Arch *A = arch_of(arch);
+    if (!A || !h_geo) return PAM_ERR_INVALID_ARG;
+    h_geo[0] = A->h0;
+    h_geo[1] = A->c0;
+    h_geo[2] = A->nout;
+    return PAM_OK;
+}
+
+pam_status pam_nn_layer_offsets(int arch, int64_t *h_offsets) {
+    const Arch *A = arch_of(arch);
+    if (!A || !h_offsets) return PAM_ERR_INVALID_ARG;
+    const Layout L = layout(*A);
     for (int l = 0; l < 6; ++l) {
         h_offsets[4 * l + 0] = L.w[l];
         h_offsets[4 * l + 1] = L.b[l];
@@ -459,41 +550,79 @@ pam_status pam_nn_layer_offsets(int64_t *h_offsets) {
     return PAM_OK;
 }
 
-static pam_status nn_check(int batch, void *ws, size_t ws_bytes) {
-    if (batch < 1 || batch > 65536 || batch % 32 != 0 || !ws) return PAM_ERR_INVALID_ARG;
-    if (ws_bytes < carve(batch, nullptr).bytes) return PAM_ERR_WORKSPACE;
+static pam_status nn_check(const Arch *A, int batch, void *ws, size_t ws_bytes) {
+    if (!A || batch < 1 || batch > 65536 || batch % 32 != 0 || !ws) return PAM_ERR_INVALID_ARG;
+    if (ws_bytes < carve(*A, batch, nullptr).bytes) return PAM_ERR_WORKSPACE;
     return PAM_OK;
 }
 
-pam_status pam_nn_forward(const float *d_params, const float *d_x, int batch, float *d_out, void *d_workspace,
-                          size_t workspace_bytes, void *stream) {
-    pam_status st = nn_check(batch, d_workspace, workspace_bytes);
+pam_status pam_nn_forward(int arch, const float *d_params, const float *d_x, int batch, float *d_out,
+                          void *d_workspace, size_t workspace_bytes, void *stream) {
+    const Arch *A = arch_of(arch);
+    pam_status st = nn_check(A, batch, d_workspace, workspace_bytes);
     if (st != PAM_OK) return st;
     if (!d_params || !d_x || !d_out) return PAM_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    Ws w = carve(batch, d_workspace);
+    Ws w = carve(*A, batch, d_workspace);
     PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 16, s));
     cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768 + 1024);
-    forward(d_params, d_x, batch, w, s);
-    PAM_CUDA_TRY(cudaMemcpyAsync(d_out, w.out, (size_t)batch * 512 * 4, cudaMemcpyDeviceToDevice, s));
+    forward(*A, d_params, d_x, batch, w, s);
+    PAM_CUDA_TRY(cudaMemcpyAsync(d_out, w.out, (size_t)batch * A->dense[1].out * 4, cudaMemcpyDeviceToDevice, s));
     PAM_CUDA_TRY(cudaGetLastError());
     return PAM_OK;
 }
 
-pam_status pam_nn_gradients(const float *d_params, const float *d_x, const float *d_support, const float *d_beta,
-                            int batch, float *d_grads, float *d_loss, void *d_workspace, size_t workspace_bytes,
-                            void *stream) {
-    pam_status st = nn_check(batch, d_workspace, workspace_bytes);
+pam_status pam_nn_gradients(int arch, const float *d_params, const float *d_x, const float *d_support,
+                            const float *d_beta, int batch, float *d_grads, float *d_loss, void *d_workspace,
+                            size_t workspace_bytes, void *stream) {
+    const Arch *A = arch_of(arch);
+    pam_status st = nn_check(A, batch, d_workspace, workspace_bytes);
     if (st != PAM_OK) return st;
     if (!d_params || !d_x || !d_support || !d_beta || !d_grads || !d_loss) return PAM_ERR_INVALID_ARG;
     cudaStream_t s = (cudaStream_t)stream;
-    Ws w = carve(batch, d_workspace);
+    Ws w = carve(*A, batch, d_workspace);
     PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 16, s));
     cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768 + 1024);
-    forward(d_params, d_x, batch, w, s);
-    k_loss<<<1, 256, 0, s>>>(w.out, d_support, d_beta, batch, w.dout, d_loss);
+    forward(*A, d_params, d_x, batch, w, s);
+    k_loss<<<1, 256, 0, s>>>(w.out, d_support, d_beta, batch, A->nout, w.dout, d_loss);
     pam::count_launches(1);
-    backward(d_params, batch, d_grads, w, s);
+    backward(*A, d_params, batch, d_grads, w, s);
+    PAM_CUDA_TRY(cudaGetLastError());
+    return PAM_OK;
+}
+
+pam_status pam_nn_layered_inputs(const pam_problem *prob, const pam_plan *plan, const double *d_K, float *d_x,
+                                 int n_rows, void *stream) {
+    if (!prob || !plan || !d_K || !d_x) return PAM_ERR_INVALID_ARG;
+    pam::Geo g;
+    pam_status st;
+    if (!pam::make_geo(prob, nullptr, &g, nullptr, &st)) return st;
+    if (g.dim != 3 || plan->n_subdomains != g.S || n_rows < g.S) return PAM_ERR_INVALID_ARG;
+    const Arch &A = kArch[PAM_NN_LAYERED3D];
+    // every patch must fit the input grid: widest patch per axis
+    const int lim[3] = {A.h0, A.h0, A.c0};
+    for (int a = 0; a < 3; ++a) {
+        for (int j = 0; j < g.p[a]; ++j) {
+            int64_t lo = ((int64_t)j * g.n[a]) / g.p[a] - g.overlap, hi = ((int64_t)(j + 1) * g.n[a]) / g.p[a] + g.overlap;
+            if (lo < 0) lo = 0;
+            if (hi > g.n[a]) hi = g.n[a];
+            if (hi - lo > lim[a]) return PAM_ERR_UNSUPPORTED;
+        }
+    }
+    k_layered_inputs<<<n_rows, 256, 0, (cudaStream_t)stream>>>(g, d_K, A.h0, A.c0, d_x);
+    pam::count_launches(1);
+    PAM_CUDA_TRY(cudaGetLastError());
+    return PAM_OK;
+}
+
+pam_status pam_nn_seed(const pam_plan *plan, int arch, const float *d_out, float threshold, pam_model *model,
+                       void *stream) {
+    const Arch *A = arch_of(arch);
+    if (!A || !plan || !d_out || !model || !model->beta || !(threshold >= 0.f)) return PAM_ERR_INVALID_ARG;
+    if (plan->m0 != A->nout) return PAM_ERR_INVALID_ARG;
+    k_seed<<<plan->n_subdomains, 64, 0, (cudaStream_t)stream>>>(d_out, plan->n_subdomains, A->nout, plan->m_cap,
+                                                               threshold, model->beta);
+    pam::count_launches(1);
     PAM_CUDA_TRY(cudaGetLastError());
     return PAM_OK;
 }

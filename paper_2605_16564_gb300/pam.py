@@ -90,16 +90,20 @@ def lib():
                                  C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_gram.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), C.c_void_p, P(pam_model),
                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
-        L.pam_nn_sizes.argtypes = [C.c_int, P(C.c_int64), P(C.c_size_t)]
-        L.pam_nn_layer_offsets.argtypes = [C.c_void_p]
-        L.pam_nn_forward.argtypes = [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_size_t,
-                                     C.c_void_p]
-        L.pam_nn_gradients.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p,
-                                       C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_nn_sizes.argtypes = [C.c_int, C.c_int, P(C.c_int64), P(C.c_size_t)]
+        L.pam_nn_geometry.argtypes = [C.c_int, C.c_void_p]
+        L.pam_nn_layer_offsets.argtypes = [C.c_int, C.c_void_p]
+        L.pam_nn_forward.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p,
+                                     C.c_size_t, C.c_void_p]
+        L.pam_nn_gradients.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int,
+                                       C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_nn_adamw.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_float,
                                    C.c_float, C.c_float, C.c_float, C.c_float, C.c_int, C.c_void_p]
-        for name in ("pam_nn_sizes", "pam_nn_layer_offsets", "pam_nn_forward", "pam_nn_gradients",
-                     "pam_nn_adamw"):
+        L.pam_nn_layered_inputs.argtypes = [P(pam_problem), P(pam_plan), C.c_void_p, C.c_void_p, C.c_int,
+                                            C.c_void_p]
+        L.pam_nn_seed.argtypes = [P(pam_plan), C.c_int, C.c_void_p, C.c_float, P(pam_model), C.c_void_p]
+        for name in ("pam_nn_sizes", "pam_nn_geometry", "pam_nn_layer_offsets", "pam_nn_forward",
+                     "pam_nn_gradients", "pam_nn_adamw", "pam_nn_layered_inputs", "pam_nn_seed"):
             getattr(L, name).restype = C.c_int
         L.pam_errors_noalloc.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p,
                                          C.c_void_p, C.c_void_p]
@@ -220,27 +224,49 @@ def pam_errors_noalloc(problem, plan, model, K, err, stream=None):
                                     _ptr(K), _ptr(err), _stream(stream)), "pam_errors_noalloc")
 
 
-def pam_nn_sizes(batch):
+PAM_NN_PATCH2D, PAM_NN_LAYERED3D = 0, 1
+
+
+def pam_nn_sizes(batch, arch=PAM_NN_PATCH2D):
     n, ws = C.c_int64(0), C.c_size_t(0)
-    _check(lib().pam_nn_sizes(int(batch), C.byref(n), C.byref(ws)), "pam_nn_sizes")
+    _check(lib().pam_nn_sizes(int(arch), int(batch), C.byref(n), C.byref(ws)), "pam_nn_sizes")
     return n.value, ws.value
 
 
-def pam_nn_layer_offsets():
+def pam_nn_geometry(arch=PAM_NN_PATCH2D):
+    """(input pixels per side, input channels, n_out)."""
+    g = np.zeros(3, dtype=np.int32)
+    _check(lib().pam_nn_geometry(int(arch), g.ctypes.data), "pam_nn_geometry")
+    return int(g[0]), int(g[1]), int(g[2])
+
+
+def pam_nn_layer_offsets(arch=PAM_NN_PATCH2D):
     off = np.zeros(24, dtype=np.int64)
-    _check(lib().pam_nn_layer_offsets(off.ctypes.data), "pam_nn_layer_offsets")
+    _check(lib().pam_nn_layer_offsets(int(arch), off.ctypes.data), "pam_nn_layer_offsets")
     return off.reshape(6, 4)
 
 
-def pam_nn_forward(params, x, out, workspace, stream=None):
-    _check(lib().pam_nn_forward(_ptr(params), _ptr(x), int(x.shape[0]), _ptr(out), _ptr(workspace),
+def pam_nn_forward(params, x, out, workspace, stream=None, arch=PAM_NN_PATCH2D):
+    _check(lib().pam_nn_forward(int(arch), _ptr(params), _ptr(x), int(x.shape[0]), _ptr(out), _ptr(workspace),
                                 workspace.numel(), _stream(stream)), "pam_nn_forward")
 
 
-def pam_nn_gradients(params, x, support, beta, grads, loss, workspace, stream=None):
-    _check(lib().pam_nn_gradients(_ptr(params), _ptr(x), _ptr(support), _ptr(beta), int(x.shape[0]),
-                                  _ptr(grads), _ptr(loss), _ptr(workspace), workspace.numel(),
+def pam_nn_gradients(params, x, support, beta, grads, loss, workspace, stream=None, arch=PAM_NN_PATCH2D):
+    _check(lib().pam_nn_gradients(int(arch), _ptr(params), _ptr(x), _ptr(support), _ptr(beta),
+                                  int(x.shape[0]), _ptr(grads), _ptr(loss), _ptr(workspace), workspace.numel(),
                                   _stream(stream)), "pam_nn_gradients")
+
+
+def pam_nn_layered_inputs(problem, plan, K, x, stream=None):
+    """x [n_rows][16][16][8] fp32 (n_rows >= S) from the patches of K."""
+    _check(lib().pam_nn_layered_inputs(C.byref(problem), C.byref(plan), _ptr(K), _ptr(x), int(x.shape[0]),
+                                       _stream(stream)), "pam_nn_layered_inputs")
+
+
+def pam_nn_seed(plan, out, threshold, model, stream=None, arch=PAM_NN_LAYERED3D):
+    """model.beta[s][j] = 4 out[s][n_out + j] where that exceeds threshold in magnitude, else 0."""
+    _check(lib().pam_nn_seed(C.byref(plan), int(arch), _ptr(out), float(threshold), C.byref(model.c_struct()),
+                             _stream(stream)), "pam_nn_seed")
 
 
 def pam_nn_adamw(params, grads, m, v, lr, beta1, beta2, eps, weight_decay, step, stream=None):
@@ -299,11 +325,17 @@ class Fitter:
         self.model = alloc_model(self.plan, device)
         self.workspace = alloc_workspace(self.plan, device)
 
-    def fit(self, K, levels=None, stream=None, check=True):
-        """Step 2, then `levels` rounds of Step 3 (default: the planned levels)."""
+    def fit(self, K, levels=None, stream=None, check=True, warm_start=False):
+        """Step 2, then `levels` rounds of Step 3 (default: the planned levels).
+        warm_start: the initial dictionary starts from the coefficients
+        already in model.beta (e.g. seeded by pam_nn_seed)."""
         lv = self.params.levels if levels is None else levels
-        c1 = pam_fit_subdomains(self.problem, self.params, self.plan, K, self.model, self.workspace,
-                                stream, check)
+        self.params.warm_start = 1 if warm_start else 0
+        try:
+            c1 = pam_fit_subdomains(self.problem, self.params, self.plan, K, self.model, self.workspace,
+                                    stream, check)
+        finally:
+            self.params.warm_start = 0
         c2 = pam_refine(self.problem, self.params, self.plan, K, self.model, lv, self.workspace,
                         stream, check) if lv > 0 else 0
         return c1 or c2

@@ -98,11 +98,15 @@ def label(patches, device, batch=4096, precision=pam.PAM_PREC_FP64, max_iters=40
     return beta, (beta != 0).astype(np.float32)
 
 
-def init_params(n, offsets, seed=0):
+# input channels of the four convolutions, per architecture
+_CIN = {0: [1, 32, 64, 128], 1: [8, 32, 64, 64]}
+
+
+def init_params(n, offsets, seed=0, arch=0):
     """He-normal weights on the used columns, zero biases and padding."""
     rng = np.random.default_rng(seed)
     p = np.zeros(n, dtype=np.float32)
-    cin = [1, 32, 64, 128]
+    cin = _CIN[arch]
     for l in range(6):
         wo, bo, rows, cols = (int(v) for v in offsets[l])
         used = 9 * cin[l] if l < 4 else cols
@@ -117,14 +121,16 @@ def init_params(n, offsets, seed=0):
 class Network:
     """The warm-start network: fp32 master weights on the device, AdamW state."""
 
-    def __init__(self, device, batch=256, seed=0):
+    def __init__(self, device, batch=256, seed=0, arch=0):
         import torch
         self.device = device
         self.batch = batch
-        n, ws = pam.pam_nn_sizes(batch)
+        self.arch = arch
+        n, ws = pam.pam_nn_sizes(batch, arch=arch)
         self.n = n
-        self.offsets = pam.pam_nn_layer_offsets()
-        self.params = torch.from_numpy(init_params(n, self.offsets, seed)).to(device)
+        self.h0, self.c0, self.n_out = pam.pam_nn_geometry(arch)
+        self.offsets = pam.pam_nn_layer_offsets(arch=arch)
+        self.params = torch.from_numpy(init_params(n, self.offsets, seed, arch)).to(device)
         self.m = torch.zeros(n, device=device)
         self.v = torch.zeros(n, device=device)
         self.grads = torch.zeros(n, device=device)
@@ -132,14 +138,18 @@ class Network:
         self.ws = torch.empty(ws, dtype=torch.uint8, device=device)
         self.step = 0
 
+    def _dev(self, a):
+        import torch
+        return torch.as_tensor(a, dtype=torch.float32).to(self.device).contiguous()
+
     def train(self, x, support, beta, epochs=8, lr=2e-3, weight_decay=1e-4, seed=0, log=None):
-        """AdamW on (x [P,32,32] f32, support, beta [P,256]) with a cosine
-        learning-rate schedule; returns the per-epoch mean losses."""
+        """AdamW on (x [P,h,h,c] f32, support, beta [P,n_out]) with a cosine
+        learning-rate schedule; returns the per-epoch mean losses. Inputs may
+        be numpy arrays or device tensors."""
         import torch
         P = x.shape[0]
-        X = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(self.device)
-        Sp = torch.from_numpy(np.ascontiguousarray(support, dtype=np.float32)).to(self.device)
-        Bt = torch.from_numpy(np.ascontiguousarray(beta, dtype=np.float32)).to(self.device)
+        X = self._dev(x).reshape(P, self.h0, self.h0, self.c0)
+        Sp, Bt = self._dev(support), self._dev(beta)
         rng = np.random.default_rng(seed)
         steps_per_epoch = P // self.batch
         total = epochs * steps_per_epoch
@@ -150,7 +160,7 @@ class Network:
             for i in range(steps_per_epoch):
                 idx = perm[i * self.batch:(i + 1) * self.batch]
                 xb, sb, bb = X[idx].contiguous(), Sp[idx].contiguous(), Bt[idx].contiguous()
-                pam.pam_nn_gradients(self.params, xb, sb, bb, self.grads, self.loss, self.ws)
+                pam.pam_nn_gradients(self.params, xb, sb, bb, self.grads, self.loss, self.ws, arch=self.arch)
                 self.step += 1
                 frac = (ep * steps_per_epoch + i) / max(total - 1, 1)
                 lr_t = lr * 0.5 * (1.0 + np.cos(np.pi * frac))
@@ -162,22 +172,34 @@ class Network:
                 log(f"epoch {ep}: bce {history[-1][0]:.4f} mse {history[-1][1]:.4f}")
         return history
 
+    def forward_device(self, X, out=None, ws=None):
+        """Device forward of X [rows,h,h,c] (rows a multiple of 32) into out
+        [rows, 2 n_out]; one call, with a workspace sized for the rows."""
+        import torch
+        rows = X.shape[0]
+        if out is None:
+            out = torch.empty((rows, 2 * self.n_out), dtype=torch.float32, device=self.device)
+        if ws is None:
+            ws = torch.empty(pam.pam_nn_sizes(rows, arch=self.arch)[1], dtype=torch.uint8, device=self.device)
+        pam.pam_nn_forward(self.params, X, out, ws, arch=self.arch)
+        return out
+
     def predict(self, x):
-        """x [P,32,32] -> (support logits [P,256], beta [P,256]) numpy."""
+        """x [P,h,h,c] -> (support logits [P,n_out], beta [P,n_out]) numpy."""
         import torch
         P = x.shape[0]
-        out = torch.zeros((P, 2 * N_OUT), dtype=torch.float32, device=self.device)
-        X = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)).to(self.device)
+        out = torch.zeros((P, 2 * self.n_out), dtype=torch.float32, device=self.device)
+        X = self._dev(x).reshape(P, self.h0, self.h0, self.c0)
         for i in range(0, P, self.batch):
             xb = X[i:i + self.batch]
             if xb.shape[0] < self.batch:
-                pad = torch.zeros((self.batch - xb.shape[0], PATCH, PATCH), device=self.device)
+                pad = torch.zeros((self.batch - xb.shape[0], self.h0, self.h0, self.c0), device=self.device)
                 xb = torch.cat([xb, pad])
-            ob = torch.zeros((self.batch, 2 * N_OUT), dtype=torch.float32, device=self.device)
-            pam.pam_nn_forward(self.params, xb.contiguous(), ob, self.ws)
+            ob = torch.zeros((self.batch, 2 * self.n_out), dtype=torch.float32, device=self.device)
+            pam.pam_nn_forward(self.params, xb.contiguous(), ob, self.ws, arch=self.arch)
             out[i:i + self.batch] = ob[:min(self.batch, P - i)]
         o = out.cpu().numpy()
-        return o[:, :N_OUT], o[:, N_OUT:] * BETA_SCALE
+        return o[:, :self.n_out], o[:, self.n_out:] * BETA_SCALE
 
 
 # Seed threshold on the predicted coefficients (log-space units). Measured on
@@ -218,3 +240,74 @@ def learned_fit(net, patches, device, precision=pam.PAM_PREC_FP64, budget=48):
         beta[miss] = b2[:len(miss)]
         info[miss] = info2[:len(miss)]
     return dict(beta=beta, info=info, solve_ms=ms + refit_ms, refit=len(miss), predict_ms=t_pred)
+
+
+# --------------------------------------------------------------------------
+# Layered 3-D decompositions: the network (PAM_NN_LAYERED3D) reads each
+# subdomain's patch (up to 16 x 16 x 8 cells, z layers as channels) and
+# predicts the coefficients of its 32-centre initial lattice; the level-0
+# solve starts from them. Inputs, inference and seeding all run on the
+# device (pam_nn_layered_inputs, pam_nn_forward, pam_nn_seed).
+# --------------------------------------------------------------------------
+SEED_THRESHOLD_3D = 1.0
+
+
+class LayeredWarmStart:
+    """Learned warm start of a 3-D decomposition's level-0 solves."""
+
+    def __init__(self, device, batch=256, seed=0, threshold=SEED_THRESHOLD_3D):
+        self.net = Network(device, batch=batch, seed=seed, arch=pam.PAM_NN_LAYERED3D)
+        self.device = device
+        self.threshold = threshold
+        self._buf = {}
+
+    def _rows(self, fitter):
+        return (fitter.plan.n_subdomains + 31) // 32 * 32
+
+    def inputs(self, fitter, Kd):
+        """[rows,16,16,8] device tensor of the patches (rows = S rounded up to 32)."""
+        import torch
+        rows = self._rows(fitter)
+        key = ("x", rows)
+        if key not in self._buf:
+            self._buf[key] = torch.empty((rows, 16, 16, 8), dtype=torch.float32, device=self.device)
+        x = self._buf[key]
+        pam.pam_nn_layered_inputs(fitter.problem, fitter.plan, Kd, x)
+        return x
+
+    def labels(self, fitter, Kd):
+        """Level-0 fit of every subdomain: (inputs [S,16,16,8] device,
+        support [S,32], beta [S,32]) as device tensors."""
+        S = fitter.plan.n_subdomains
+        code = fitter.fit(Kd, levels=0, check=False)
+        if code not in (0, 5):
+            raise pam.PamError(code, "label fit")
+        n_out = self.net.n_out
+        beta = fitter.model.beta[:, :n_out].float().clone()
+        return self.inputs(fitter, Kd)[:S].clone(), (beta != 0).float(), beta
+
+    def train(self, fitter, fields, epochs=8, lr=2e-3, log=None):
+        """Label each field (device tensors of the decomposition's shape) with
+        its level-0 fits and train the network on all of them."""
+        import torch
+        xs, ss, bs = [], [], []
+        for Kd in fields:
+            x, s, b = self.labels(fitter, Kd)
+            xs.append(x); ss.append(s); bs.append(b)
+        X, Sp, B = torch.cat(xs), torch.cat(ss), torch.cat(bs)
+        P = (X.shape[0] // self.net.batch) * self.net.batch
+        return self.net.train(X[:P], Sp[:P], B[:P], epochs=epochs, lr=lr, log=log)
+
+    def seed(self, fitter, Kd):
+        """Network inference on the patches of Kd and seeding of model.beta;
+        the next fitter.fit(Kd, warm_start=True) starts from it."""
+        import torch
+        x = self.inputs(fitter, Kd)
+        rows = x.shape[0]
+        key = ("out", rows)
+        if key not in self._buf:
+            self._buf[key] = torch.empty((rows, 2 * self.net.n_out), dtype=torch.float32, device=self.device)
+            self._buf[("ws", rows)] = torch.empty(pam.pam_nn_sizes(rows, arch=self.net.arch)[1],
+                                                  dtype=torch.uint8, device=self.device)
+        out = self.net.forward_device(x, self._buf[key], self._buf[("ws", rows)])
+        pam.pam_nn_seed(fitter.plan, out, self.threshold, fitter.model, arch=self.net.arch)

@@ -26,47 +26,52 @@ def env():
     return torch, pam, torch.device("cuda:0")
 
 
-def _data(B, seed):
+def _data(B, seed, arch=0):
+    A = onn.ARCHS[arch]
     rng = np.random.default_rng(seed)
-    x = rng.uniform(-1, 1, size=(B, 32, 32))
-    support = (rng.uniform(size=(B, 256)) < 0.3).astype(np.float64)
-    beta = rng.standard_normal((B, 256)) * 3 * support
+    x = rng.uniform(-1, 1, size=(B, A["h0"], A["h0"], A["c0"]))
+    support = (rng.uniform(size=(B, A["n_out"])) < 0.3).astype(np.float64)
+    beta = rng.standard_normal((B, A["n_out"])) * 3 * support
     return x, support, beta
 
 
-def test_layout_matches_the_oracle(env):
+@pytest.mark.parametrize("arch", [0, 1])
+def test_layout_matches_the_oracle(env, arch):
     torch, pam, dev = env
-    lay, total = onn.layout()
-    n, _ = pam.pam_nn_sizes(32)
+    lay, total = onn.layout(arch)
+    n, _ = pam.pam_nn_sizes(32, arch=arch)
     assert n == total
-    off = pam.pam_nn_layer_offsets()
+    off = pam.pam_nn_layer_offsets(arch=arch)
     np.testing.assert_array_equal(off, np.array(lay))
+    A = onn.ARCHS[arch]
+    assert pam.pam_nn_geometry(arch) == (A["h0"], A["c0"], A["n_out"])
 
 
-@pytest.mark.parametrize("B", [32, 96])
-def test_forward_loss_and_gradients(env, B):
+@pytest.mark.parametrize("arch,B", [(0, 32), (0, 96), (1, 64)])
+def test_forward_loss_and_gradients(env, arch, B):
     torch, pam, dev = env
-    p = onn.init_params(11)
-    p[onn.layout()[0][5][1]:] += 0.05  # output biases
-    x, s, b = _data(B, 12)
-    ref_out, _ = onn.forward(p, x)
-    ref_loss, ref_g = onn.gradients(p, x, s, b)
-    n, ws_bytes = pam.pam_nn_sizes(B)
+    n_out = onn.ARCHS[arch]["n_out"]
+    p = onn.init_params(11, arch)
+    p[onn.layout(arch)[0][5][1]:] += 0.05  # output biases
+    x, s, b = _data(B, 12, arch)
+    ref_out, _ = onn.forward(p, x, arch)
+    ref_loss, ref_g = onn.gradients(p, x, s, b, arch)
+    n, ws_bytes = pam.pam_nn_sizes(B, arch=arch)
     ws = torch.empty(ws_bytes, dtype=torch.uint8, device=dev)
     P = torch.from_numpy(p.astype(np.float32)).to(dev)
     X = torch.from_numpy(x.astype(np.float32)).to(dev)
-    out = torch.zeros((B, 512), dtype=torch.float32, device=dev)
-    pam.pam_nn_forward(P, X, out, ws)
+    out = torch.zeros((B, 2 * n_out), dtype=torch.float32, device=dev)
+    pam.pam_nn_forward(P, X, out, ws, arch=arch)
     o = out.cpu().numpy().astype(np.float64)
     assert np.linalg.norm(o - ref_out) <= OUT_RTOL * np.linalg.norm(ref_out)
     g = torch.zeros(n, dtype=torch.float32, device=dev)
     loss = torch.zeros(2, dtype=torch.float32, device=dev)
     pam.pam_nn_gradients(P, X, torch.from_numpy(s.astype(np.float32)).to(dev),
-                         torch.from_numpy(b.astype(np.float32)).to(dev), g, loss, ws)
+                         torch.from_numpy(b.astype(np.float32)).to(dev), g, loss, ws, arch=arch)
     np.testing.assert_allclose(loss.cpu().numpy(), ref_loss, rtol=LOSS_RTOL)
     gg = g.cpu().numpy().astype(np.float64)
     errs = []
-    for l, (wo, bo, rows, cols) in enumerate(onn.layout()[0]):
+    for l, (wo, bo, rows, cols) in enumerate(onn.layout(arch)[0]):
         for kind, lo, hi in (("W", wo, wo + rows * cols), ("b", bo, bo + rows)):
             a, r = gg[lo:hi], ref_g[lo:hi]
             nr = np.linalg.norm(r)

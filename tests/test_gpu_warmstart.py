@@ -70,3 +70,48 @@ def test_warm_start_reaches_the_plain_minimiser_in_fewer_iterations(trained, pre
           f"solve {ms_cold:.2f} ms -> {res['solve_ms']:.2f} ms, plain refits {res['refit']}")
     assert mean_warm <= 0.85 * mean_cold
     assert it(res["info"]).max() < it(info_cold).max()
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_layered_3d_learned_seed(precision):
+    # The 3-D network (PAM_NN_LAYERED3D) trained on the level-0 fits of 8
+    # seeded layered fields seeds the level-0 active set of a new field:
+    # fewer steps on average, every subdomain certified, and the same
+    # minimiser (fp64: coefficients within 1e-9; fp32 form: the surrogate
+    # per cell within its log10 tolerance).
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_16564_gb300 import build
+    build.build()
+    from paper_2605_16564_gb300 import pam, warmstart as ws
+    dev = torch.device("cuda:0")
+    shape, n_sub = (30, 110, 85), (3, 11, 17)
+    fit = pam.Fitter(shape, n_sub, 1, (4, 4, 2), device=dev, precision=precision, k_top=30, levels=3)
+    lw = ws.LayeredWarmStart(dev, batch=256, seed=0)
+    train = [torch.from_numpy(fields.layered_field(shape, seed=200 + i)).to(dev) for i in range(8)]
+    hist = lw.train(fit, train, epochs=8)
+    assert hist[-1][1] < 0.7 * hist[0][1], hist
+    Kd = torch.from_numpy(fields.layered_field(shape, seed=5)).to(dev)
+    it = lambda: fit.model.info.cpu().numpy()[:, pam.INFO_ITERS] % 100
+    flags = lambda: fit.model.info.cpu().numpy()[:, pam.INFO_FLAGS]
+    assert fit.fit(Kd, levels=0, check=False) == 0
+    it_cold, beta_cold = it(), fit.model.beta.cpu().numpy().copy()
+    pts = fields.cell_centred_points(shape, [n / max(shape) for n in shape])
+    X = torch.from_numpy(pts).to(dev)
+    k_cold = fit.eval(X).cpu().numpy()
+    lw.seed(fit, Kd)
+    assert fit.fit(Kd, levels=0, check=False, warm_start=True) == 0
+    it_warm = it()
+    assert np.all((flags() & pam.FLAG_NOT_CERTIFIED) == 0)
+    print(f"precision {precision}: level-0 active-set steps cold {it_cold.mean():.2f} -> learned "
+          f"{it_warm.mean():.2f} (max {it_cold.max()} -> {it_warm.max()})")
+    assert it_warm.mean() <= 0.8 * it_cold.mean()
+    if precision == 0:
+        b = fit.model.beta.cpu().numpy()
+        scale = np.maximum(1.0, np.abs(beta_cold).max(axis=1, keepdims=True))
+        assert np.all(np.abs(b - beta_cold) <= 1e-9 * scale)
+    else:
+        k_warm = fit.eval(X).cpu().numpy()
+        d = np.abs(np.log10(k_warm) - np.log10(k_cold)) / np.maximum(1.0, np.abs(np.log10(k_cold)))
+        assert d.max() <= 1e-3, d.max()

@@ -11,11 +11,12 @@ torch = pytest.importorskip("torch")
 F = torch.nn.functional
 
 
-def _torch_forward(p, x):
-    lay, _ = nn.layout()
+def _torch_forward(p, x, arch):
+    A = nn.ARCHS[arch]
+    lay, _ = nn.layout(arch)
     B = x.shape[0]
-    a = torch.from_numpy(x.reshape(B, 1, 32, 32))
-    for l, (hin, cin, hout, cout, stride, kpad) in enumerate(nn.CONV):
+    a = torch.from_numpy(x.reshape(B, A["h0"], A["h0"], A["c0"])).permute(0, 3, 1, 2)  # NCHW
+    for l, (hin, cin, hout, cout, stride, kpad) in enumerate(A["conv"]):
         wo, bo, rows, cols = lay[l]
         W = p[wo:wo + rows * cols].reshape(rows, cols)[:, :9 * cin]
         Wt = torch.from_numpy(W.reshape(cout, 3, 3, cin).transpose(0, 3, 1, 2).copy())
@@ -29,44 +30,49 @@ def _torch_forward(p, x):
                     torch.from_numpy(p[bo:bo + rows])).numpy()
 
 
-def _data(B, seed):
+def _data(B, seed, arch=0):
+    A = nn.ARCHS[arch]
     rng = np.random.default_rng(seed)
-    x = rng.uniform(-1, 1, size=(B, 32, 32))
-    support = (rng.uniform(size=(B, 256)) < 0.3).astype(np.float64)
-    beta = rng.standard_normal((B, 256)) * 3 * support
+    x = rng.uniform(-1, 1, size=(B, A["h0"], A["h0"], A["c0"]))
+    support = (rng.uniform(size=(B, A["n_out"])) < 0.3).astype(np.float64)
+    beta = rng.standard_normal((B, A["n_out"])) * 3 * support
     return x, support, beta
 
 
-def test_forward_matches_torch_convolutions():
-    p = nn.init_params(1)
+@pytest.mark.parametrize("arch", [0, 1])
+def test_forward_matches_torch_convolutions(arch):
+    p = nn.init_params(1, arch)
     p[np.arange(p.size) % 7 == 0] += 0.01  # nonzero biases too
-    x, _, _ = _data(3, 2)
-    out, _ = nn.forward(p, x)
-    np.testing.assert_allclose(out, _torch_forward(p, x), rtol=1e-10, atol=1e-12)
+    x, _, _ = _data(3, 2, arch)
+    out, _ = nn.forward(p, x, arch)
+    np.testing.assert_allclose(out, _torch_forward(p, x, arch), rtol=1e-10, atol=1e-12)
 
 
-def test_loss_matches_torch():
-    p = nn.init_params(3)
-    x, s, b = _data(4, 4)
-    out, _ = nn.forward(p, x)
+@pytest.mark.parametrize("arch", [0, 1])
+def test_loss_matches_torch(arch):
+    p = nn.init_params(3, arch)
+    x, s, b = _data(4, 4, arch)
+    out, _ = nn.forward(p, x, arch)
     loss, _ = nn.loss_and_grad_out(out, s, b)
+    n_out = nn.ARCHS[arch]["n_out"]
     o = torch.from_numpy(out)
-    bce = F.binary_cross_entropy_with_logits(o[:, :256], torch.from_numpy(s)).item()
-    mse = F.mse_loss(o[:, 256:], torch.from_numpy(b / nn.BETA_SCALE)).item()
+    bce = F.binary_cross_entropy_with_logits(o[:, :n_out], torch.from_numpy(s)).item()
+    mse = F.mse_loss(o[:, n_out:], torch.from_numpy(b / nn.BETA_SCALE)).item()
     assert loss[0] == pytest.approx(bce, rel=1e-12)
     assert loss[1] == pytest.approx(mse, rel=1e-12)
 
 
-def test_backward_matches_finite_differences():
-    p = nn.init_params(5)
-    x, s, b = _data(2, 6)
-    loss, g = nn.gradients(p, x, s, b)
-    lay, total = nn.layout()
+@pytest.mark.parametrize("arch", [0, 1])
+def test_backward_matches_finite_differences(arch):
+    p = nn.init_params(5, arch)
+    x, s, b = _data(2, 6, arch)
+    loss, g = nn.gradients(p, x, s, b, arch)
+    lay, total = nn.layout(arch)
     rng = np.random.default_rng(7)
     idx = []
     for wo, bo, rows, cols in lay:
         idx += list(rng.integers(wo, wo + rows * cols, size=6)) + list(rng.integers(bo, bo + rows, size=2))
-    f = lambda q: sum(nn.loss_and_grad_out(nn.forward(q, x)[0], s, b)[0])
+    f = lambda q: sum(nn.loss_and_grad_out(nn.forward(q, x, arch)[0], s, b)[0])
     eps = 1e-6
     for i in idx:
         e = np.zeros(total); e[i] = eps
