@@ -239,20 +239,24 @@ static void transpose(const bf16 *in, int rows, int cols, int ldi, bf16 *out, in
 }
 
 // im2col of a 3x3 pad-1 convolution, NHWC input [B,h,h,c] -> [B*ho*ho][kpad],
-// column (ky*3 + kx)*c + ch, zero padding and zero columns past 9c.
+// column (ky*3 + kx)*c + ch, zero padding and zero columns past 9c. A block
+// per output pixel (grid-stride), its threads over the columns: the pixel's
+// coordinates are decomposed once, the columns with 32-bit arithmetic.
 __global__ void k_im2col(const bf16 *x, int B, int h, int c, int ho, int stride, int kpad, bf16 *cols) {
-    const int64_t total = (int64_t)B * ho * ho * kpad;
-    for (int64_t e = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-        const int k = (int)(e % kpad);
-        const int64_t p = e / kpad;
+    const int64_t nrows = (int64_t)B * ho * ho;
+    for (int64_t p = blockIdx.x; p < nrows; p += gridDim.x) {
         const int ox = (int)(p % ho), oy = (int)((p / ho) % ho), b = (int)(p / ((int64_t)ho * ho));
-        bf16 v = __float2bfloat16_rn(0.f);
-        if (k < 9 * c) {
-            const int tap = k / c, ch = k % c, ky = tap / 3, kx = tap % 3;
-            const int iy = oy * stride - 1 + ky, ix = ox * stride - 1 + kx;
-            if (iy >= 0 && iy < h && ix >= 0 && ix < h) v = x[(((int64_t)b * h + iy) * h + ix) * c + ch];
+        bf16 *dst = cols + p * kpad;
+        const bf16 *xb = x + (int64_t)b * h * h * c;
+        for (int k = threadIdx.x; k < kpad; k += blockDim.x) {
+            bf16 v = __float2bfloat16_rn(0.f);
+            if (k < 9 * c) {
+                const int tap = k / c, ch = k - tap * c, ky = tap / 3, kx = tap - 3 * ky;
+                const int iy = oy * stride - 1 + ky, ix = ox * stride - 1 + kx;
+                if (iy >= 0 && iy < h && ix >= 0 && ix < h) v = xb[(iy * h + ix) * c + ch];
+            }
+            dst[k] = v;
         }
-        cols[e] = v;
     }
 }
 
@@ -448,7 +452,9 @@ static void forward(const Arch &A, const float *params, const float *x, int B, W
     for (int l = 0; l < 4; ++l) {
         const Conv &c = A.conv[l];
         const int64_t rows = (int64_t)B * c.hout * c.hout;
-        k_im2col<<<grid_for(rows * c.kpad), 256, 0, st>>>(in, B, c.hin, c.cin, c.hout, c.stride, c.kpad, w.cols[l]);
+        const int thr = c.kpad < 256 ? (c.kpad + 31) / 32 * 32 : 256;
+        k_im2col<<<(unsigned)std::min<int64_t>(rows, 16384), thr, 0, st>>>(in, B, c.hin, c.cin, c.hout, c.stride,
+                                                                            c.kpad, w.cols[l]);
         count_launches(1);
         gemm(w.cols[l], c.kpad, w.pw + L.w[l], c.kpad, (int)rows, c.cout, c.kpad, nullptr, w.act[l], c.cout,
              params + L.b[l], 1, w.status, st);
