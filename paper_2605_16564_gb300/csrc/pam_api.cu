@@ -119,6 +119,8 @@ static size_t carve(const Geo &g, char *base, Ws *w) {
     w->rowmax = (float *)take(S * nm * sizeof(float));
     w->rowinv = (float *)take(S * nm * sizeof(float));
     w->b = (double *)take(S * mc * sizeof(double));
+    w->cost = (uint32_t *)take(S * sizeof(uint32_t));
+    w->order = (int32_t *)take(S * sizeof(int32_t));
     // large regions: the fp64 form needs E, G and fp64 factors; the mixed
     // form only its fp32 Gram and fp32 factors
     const bool f64 = g.prec == PAM_PREC_FP64;

@@ -53,6 +53,8 @@ struct Ws {
     double *err_part; // [err_blocks][4] per-block partial sums of the error measures
     unsigned long long *kmax_bits; // [S] max K of each patch as ordered bits
     int32_t *status;  // [8] device status words
+    uint32_t *cost;   // [S] clock cycles of each subdomain's last mixed solve (a scheduling hint)
+    int32_t *order;   // [S] subdomains in decreasing cost, the mixed solve's block order
     size_t bytes;
 };
 

@@ -801,8 +801,12 @@ struct DFAcc {
 
 __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, const int32_t *boxes,
                                                             const double *centres, double *beta,
-                                                            int32_t *info, Ws w, int kMxFactorBytes) {
-    const int s = blockIdx.x;
+                                                            int32_t *info, Ws w, int kMxFactorBytes,
+                                                            int ordered) {
+    // blocks take the subdomains in decreasing cost of their previous solve,
+    // so the longest start first and the level does not wait on a late one
+    const int s = ordered ? w.order[blockIdx.x] : blockIdx.x;
+    const long long t_start = clock64();
     int32_t *inf = info + s * kInfoN;
     if (inf[PAM_INFO_STOPPED]) return;
     const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS], mc = g.m_cap;
@@ -1162,7 +1166,33 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
         inf[PAM_INFO_FLAGS] = flags;
         inf[PAM_INFO_SUPPORT] = scnt;
         inf[PAM_INFO_ITERS] = it + 100 * refine_it;  // active-set steps + 100 x refinement steps
+        const long long dt = clock64() - t_start;
+        w.cost[s] = dt > 0xffffffffLL ? 0xffffffffu : (uint32_t)dt;
     }
+}
+
+// Block order of the next mixed solve: the subdomains sorted by the cost of
+// their previous solve, descending, ties to the lower index (one block,
+// bitonic sort of (cost, ~index) keys in shared memory). Any order gives the
+// same results; this one only shortens the tail of the launch.
+__global__ void __launch_bounds__(1024) k_solve_order(const uint32_t *cost, int S, int P, int32_t *order) {
+    extern __shared__ unsigned long long okeys[];
+    for (int i = threadIdx.x; i < P; i += blockDim.x)
+        okeys[i] = i < S ? (((unsigned long long)cost[i] << 32) | (unsigned long long)(0xffffffffu - (unsigned)i))
+                         : 0ull;
+    __syncthreads();
+    for (int k = 2; k <= P; k <<= 1) {
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            for (int i = threadIdx.x; i < (P >> 1); i += blockDim.x) {
+                const int l = 2 * i - (i & (j - 1)), r = l + j;
+                const unsigned long long a = okeys[l], b = okeys[r];
+                if (((l & k) == 0) ? (a < b) : (a > b)) { okeys[l] = b; okeys[r] = a; }
+            }
+            __syncthreads();
+        }
+    }
+    for (int i = threadIdx.x; i < S; i += blockDim.x)
+        order[i] = (int32_t)(0xffffffffu - (unsigned)(okeys[i] & 0xffffffffull));
 }
 
 // Shared-memory budget of the packed factor: supports with s (s+1)/2 fp32
@@ -1215,7 +1245,16 @@ void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes,
     size_t sm = solve_mixed_smem(g);
     cudaFuncSetAttribute(k_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     PhaseScope ps(kPhSolve, st);
-    k_solve_mixed<<<g.S, kMxThreads, sm, st>>>(g, p, boxes, centres, beta, info, w, factor_smem_bytes());
+    int P = 1;
+    while (P < g.S) P <<= 1;
+    const int ordered = P <= 16384 ? 1 : 0;  // the sort keeps P keys in shared memory
+    if (ordered) {
+        cudaFuncSetAttribute(k_solve_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(P * 8));
+        k_solve_order<<<1, 1024, (size_t)P * 8, st>>>(w.cost, g.S, P, w.order);
+        count_launches(1);
+    }
+    k_solve_mixed<<<g.S, kMxThreads, sm, st>>>(g, p, boxes, centres, beta, info, w, factor_smem_bytes(),
+                                               ordered);
     count_launches(1);
 }
 
