@@ -221,8 +221,8 @@ pam_status pam_eval_workspace_size(const pam_plan *plan, int64_t n_pts, size_t *
  * or the log-space value when log_space != 0; NaN for points outside the
  * grid. The points are bucketed by owner in d_workspace (at least
  * pam_eval_workspace_size bytes). PAM_PREC_FP64 evaluates in binary64;
- * PAM_PREC_MIXED evaluates the Gaussians in fp32 (local coordinates, 2^x on
- * the special-function unit) and the final exp in fp64.
+ * PAM_PREC_MIXED evaluates the Gaussians, their weighted sums and the final
+ * exp in fp32 (local coordinates, 2^x on the special-function unit).
  * Asynchronous (no synchronisation); n_pts == 0 is a no-op.
  */
 pam_status pam_eval(const pam_problem *prob, const pam_plan *plan,
