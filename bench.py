@@ -312,7 +312,9 @@ def run_pam(args, rank, ws):
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
+            torch.cuda.nvtx.range_push("pam_step")  # lets a profiler select the timed steps
             err = step()
+            torch.cuda.nvtx.range_pop()
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))

@@ -260,6 +260,27 @@ __global__ void k_im2col(const bf16 *x, int B, int h, int c, int ho, int stride,
     }
 }
 
+// The same with 16-byte moves (8 channels at a time) when c is a multiple of
+// 8: a tap's channels are contiguous both in the input pixel and in the row.
+__global__ void k_im2col_v8(const bf16 *x, int B, int h, int c, int ho, int stride, int kpad, bf16 *cols) {
+    const int64_t nrows = (int64_t)B * ho * ho;
+    const int cv = c >> 3, kv = kpad >> 3;  // 16-byte units
+    for (int64_t p = blockIdx.x; p < nrows; p += gridDim.x) {
+        const int ox = (int)(p % ho), oy = (int)((p / ho) % ho), b = (int)(p / ((int64_t)ho * ho));
+        uint4 *dst = reinterpret_cast<uint4 *>(cols + p * kpad);
+        const uint4 *xb = reinterpret_cast<const uint4 *>(x + (int64_t)b * h * h * c);
+        for (int k = threadIdx.x; k < kv; k += blockDim.x) {
+            uint4 v = make_uint4(0u, 0u, 0u, 0u);
+            if (k < 9 * cv) {
+                const int tap = k / cv, cq = k - tap * cv, ky = tap / 3, kx = tap - 3 * ky;
+                const int iy = oy * stride - 1 + ky, ix = ox * stride - 1 + kx;
+                if (iy >= 0 && iy < h && ix >= 0 && ix < h) v = xb[(iy * h + ix) * cv + cq];
+            }
+            dst[k] = v;
+        }
+    }
+}
+
 // dx [B,h,h,c] = col2im(dcols): each input element gathers the column
 // entries that read it (deterministic, no atomics).
 __global__ void k_col2im(const float *dcols, int B, int h, int c, int ho, int stride, int kpad, float *dx) {
@@ -287,12 +308,30 @@ __global__ void k_relu_back(const float *dy, const bf16 *y, int64_t n, bf16 *dz)
         dz[i] = __float2bfloat16_rn(__bfloat162float(y[i]) > 0.f ? dy[i] : 0.f);
 }
 
-// db[j] = sum_i dz[i][j] (fixed order per column).
-__global__ void k_colsum(const bf16 *dz, int rows, int cols, float *db) {
+// db[j] = sum_i dz[i][j], in two fixed-order stages: block (cb, ch) sums the
+// rows of chunk ch for 32 columns (8 row phases x 32 columns, then the 8
+// phases in order) into part[ch][j]; k_colsum_final adds the chunks in order.
+constexpr int kColChunks = 64;
+__global__ void k_colsum_part(const bf16 *dz, int rows, int cols, int chunk_rows, float *part) {
+    __shared__ float red[8][33];
+    const int c = blockIdx.x * 32 + (threadIdx.x & 31), ph = threadIdx.x >> 5;
+    const int r0 = blockIdx.y * chunk_rows, r1 = min(rows, r0 + chunk_rows);
+    float acc = 0.f;
+    if (c < cols)
+        for (int i = r0 + ph; i < r1; i += 8) acc += __bfloat162float(dz[(size_t)i * cols + c]);
+    red[ph][threadIdx.x & 31] = acc;
+    __syncthreads();
+    if (ph == 0 && c < cols) {
+        float v = 0.f;
+        for (int q = 0; q < 8; ++q) v += red[q][threadIdx.x];
+        part[(size_t)blockIdx.y * cols + c] = v;
+    }
+}
+__global__ void k_colsum_final(const float *part, int nchunks, int cols, float *db) {
     const int j = blockIdx.x * blockDim.x + threadIdx.x;
     if (j >= cols) return;
     float acc = 0.f;
-    for (int i = 0; i < rows; ++i) acc += __bfloat162float(dz[(size_t)i * cols + j]);
+    for (int q = 0; q < nchunks; ++q) acc += part[(size_t)q * cols + j];
     db[j] = acc;
 }
 
@@ -397,6 +436,7 @@ struct Ws {
     bf16 *dz;             // bf16 pre-activation gradient
     bf16 *tA, *tB;        // transposes
     float *loss;          // [4]
+    float *colpart;       // [kColChunks][512] bias-gradient partial sums
     int32_t *status;
     size_t bytes;
 };
@@ -436,6 +476,7 @@ static Ws carve(const Arch &A, int B, void *base) {
     w.tA = (bf16 *)take(std::max(maxact, (size_t)L.total) * 2);
     w.tB = (bf16 *)take(std::max(maxact, (size_t)L.total) * 2);
     w.loss = (float *)take(16);
+    w.colpart = (float *)take((size_t)kColChunks * 512 * 4);
     w.status = (int32_t *)take(16);
     w.bytes = off;
     return w;
@@ -452,9 +493,14 @@ static void forward(const Arch &A, const float *params, const float *x, int B, W
     for (int l = 0; l < 4; ++l) {
         const Conv &c = A.conv[l];
         const int64_t rows = (int64_t)B * c.hout * c.hout;
-        const int thr = c.kpad < 256 ? (c.kpad + 31) / 32 * 32 : 256;
-        k_im2col<<<(unsigned)std::min<int64_t>(rows, 16384), thr, 0, st>>>(in, B, c.hin, c.cin, c.hout, c.stride,
-                                                                            c.kpad, w.cols[l]);
+        const unsigned blocks = (unsigned)std::min<int64_t>(rows, 16384);
+        if (c.cin % 8 == 0) {
+            const int kv = c.kpad / 8, thr = kv < 256 ? (kv + 31) / 32 * 32 : 256;
+            k_im2col_v8<<<blocks, thr, 0, st>>>(in, B, c.hin, c.cin, c.hout, c.stride, c.kpad, w.cols[l]);
+        } else {
+            const int thr = c.kpad < 256 ? (c.kpad + 31) / 32 * 32 : 256;
+            k_im2col<<<blocks, thr, 0, st>>>(in, B, c.hin, c.cin, c.hout, c.stride, c.kpad, w.cols[l]);
+        }
         count_launches(1);
         gemm(w.cols[l], c.kpad, w.pw + L.w[l], c.kpad, (int)rows, c.cout, c.kpad, nullptr, w.act[l], c.cout,
              params + L.b[l], 1, w.status, st);
@@ -479,8 +525,13 @@ static void layer_backward(const float *dY, const bf16 *Y, bool relu, const bf16
         k_cast_bf16<<<grid_for(ny), 256, 0, st>>>(dY, w.dz, ny);
     }
     count_launches(1);
-    k_colsum<<<(n + 127) / 128, 128, 0, st>>>(w.dz, rows, n, gb);
-    count_launches(1);
+    {
+        const int chunks = std::max(1, std::min(kColChunks, (rows + 255) / 256));
+        const int chunk_rows = (rows + chunks - 1) / chunks;
+        k_colsum_part<<<dim3((n + 31) / 32, chunks), 256, 0, st>>>(w.dz, rows, n, chunk_rows, w.colpart);
+        k_colsum_final<<<(n + 127) / 128, 128, 0, st>>>(w.colpart, chunks, n, gb);
+        count_launches(2);
+    }
     // dW [n][k] = dZ^T [n][rows] . X^T [k][rows]^T  (contraction over rows)
     transpose(w.dz, rows, n, n, w.tA, rows, st);
     transpose(X, rows, k, k, w.tB, rows, st);
