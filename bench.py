@@ -192,6 +192,17 @@ SFU_EX2_PER_S = 152 * 16 * 2.07e9
 FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
+# DRAM bytes (read + write) of one launch of each mixed-form kernel on the
+# layered 3-D workload: ncu --set full of the last level's launches on the
+# quarter-size workload (561 of the 2,244 subdomains, same subdomain shape),
+# scaled by 4 (profiles/kernels_layered3d_quarter_mixed.md). Only valid for
+# that workload and for the kernels as captured.
+TRAFFIC_LAYERED3D = {"k_solve_mixed": 1.404e9, "k_gram_tc": 1.221e9, "k_stats_f32": 2.8e7,
+                     "k_eval_bucket_f32": 3.06e8}
+TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the level-3 launch (eval: its one launch), "
+                "captured on layered3d_quarter and scaled x4 by subdomains")
+
+
 def roofline_entries(phase_ms, work, n_pts, mixed, peaks, peak_src):
     """Roofline objects per kernel family: achieved = algorithmic work per
     step / that family's CUDA-event time per step."""
@@ -228,6 +239,18 @@ def roofline_entries(phase_ms, work, n_pts, mixed, peaks, peak_src):
                       "unit": "TFLOP/s", "frac": ach / FP32_TFLOPS, "traffic": None,
                       "peak_source": "fp32 FMA 128/clk/SM x 152 SMs x 2.07 GHz; work = active-set Cholesky flops"}
     return r
+
+
+def attach_traffic(roofs, workload):
+    """Fill `traffic` from the recorded ncu capture where it applies."""
+    if workload != "layered3d":
+        return roofs
+    for v in roofs.values():
+        t = TRAFFIC_LAYERED3D.get(v.get("kernel"))
+        if t is not None:
+            v["traffic"] = t
+            v["traffic_note"] = TRAFFIC_NOTE
+    return roofs
 
 
 def run_pam(args, rank, ws):
@@ -408,7 +431,8 @@ def run_pam(args, rank, ws):
     work = accounting(fit, Kd, W["params"]["levels"], pam, seed=(lambda: lw.seed(fit, Kd)) if lw else None)
     owners = owner_counts(W, pts)
     work["eval_pairs"] = float(np.sum(owners * work["m_final"]))
-    roofs = roofline_entries(phase_ms, work, n_pts, prec == pam.PAM_PREC_MIXED, peaks, peak_src)
+    roofs = attach_traffic(roofline_entries(phase_ms, work, n_pts, prec == pam.PAM_PREC_MIXED, peaks, peak_src),
+                           args.workload)
     dom = max(phase_ms.items(), key=lambda kv: kv[1][0])[0] if phase_ms else None
     roof = roofs.get(dom) or {"kernel": dom, "bound": None, "achieved": None, "peak": None,
                               "unit": None, "frac": None, "traffic": None}
