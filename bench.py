@@ -274,7 +274,8 @@ def run_pam(args, rank, ws):
         prec_name = "mixed" if _mixed_available(pam) else "fp64"
     prec = pam.PAM_PREC_MIXED if prec_name == "mixed" else pam.PAM_PREC_FP64
 
-    fit = pam.Fitter(shape, W["n_sub"], W["overlap"], W["g"], device=dev, precision=prec, **W["params"])
+    fit = pam.Fitter(shape, W["n_sub"], W["overlap"], W["g"], device=dev, precision=prec, quad=args.quad,
+                     **W["params"])
     Kd = torch.from_numpy(np.ascontiguousarray(K)).to(dev)
     ptsd = torch.from_numpy(pts).to(dev)
     out = torch.empty(n_pts, dtype=torch.float64, device=dev)
@@ -417,7 +418,7 @@ def run_pam(args, rank, ws):
     plain = None
     if prec == pam.PAM_PREC_MIXED and not args.skip_plain:
         pf = pam.Fitter(shape, W["n_sub"], W["overlap"], W["g"], device=dev,
-                        precision=pam.PAM_PREC_FP64, **W["params"])
+                        precision=pam.PAM_PREC_FP64, quad=args.quad, **W["params"])
         pf.fit(Kd)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -523,6 +524,8 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="3-D mixed form without the learned warm start")
+    ap.add_argument("--quad", type=int, default=0, choices=[0, 1],
+                    help="indicator and error quadrature: 0 midpoint, 1 two-point Gauss-Legendre per axis")
     args = ap.parse_args()
     rank, ws = _dist()
     W = WORKLOADS[args.workload]
@@ -579,6 +582,7 @@ def main():
         "vs_baseline": None, "dtype": "f64" if r["prec_name"] == "fp64" else "bf16x3+f32+f64",
         "data": "synthetic",
         "config": dict(cfg, precision=r["prec_name"],
+                       quadrature="midpoint" if args.quad == 0 else "Gauss-Legendre 2^dim points",
                        warm_start=r["learned"]["kind"] if r["learned"] else "previous level (Algorithm 1)"),
         "eval_pts_per_s": r["n_pts"] * ws / (eval_ms / 1e3) if eval_ms else None,
         "fit_cells_per_s": None,

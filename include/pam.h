@@ -107,6 +107,10 @@ typedef struct {
     int warm_start;      /* pam_fit_subdomains: 1 = start the solve from the caller's
                             model->beta[s][0..m0) (e.g. a learned prediction; its
                             nonzero pattern and signs seed the active set), 0 = from 0 */
+    int quad;            /* quadrature of the indicators R_T (Eq. (4)): 0 = midpoint
+                            (one node, the centroid), 1 = tensor two-point
+                            Gauss-Legendre (2^dim nodes x_T +- h / (2 sqrt 3) per
+                            axis, weight |T| / 2^dim each) */
 } pam_params;
 
 /* Sizes derived from a problem and parameters by pam_plan_create. */
@@ -232,17 +236,21 @@ pam_status pam_eval(const pam_problem *prob, const pam_plan *plan,
 
 /*
  * Relative errors of the reconstruction over the source cells, each cell
- * measured with its owner's surrogate at its centroid:
+ * measured with its owner's surrogate at its centroid (quad = 0) or at the
+ * 2^dim Gauss-Legendre nodes of pam_params.quad = 1 (weight 1/2^dim of the
+ * cell each):
  * d_err[0] = sum |K_T - K*| / sum |K_T|, d_err[1] = (Eq. (12))
  * (sum (K_T - K*)^2 / sum K_T^2)^(1/2), d_err[2] = sum |ln K_T - ln K*| /
- * sum |ln K_T|, d_err[3] = max_T |log10 K_T - log10 K*(x_T)|; fp64
- * accumulation in a fixed order (deterministic). precision selects how the
- * Gaussians are evaluated (as pam_eval). d_err: device double [4]. Uses the
- * fit workspace. Asynchronous.
+ * sum |ln K_T|, d_err[3] = max over the nodes of |log10 K_T - log10 K*(x)|;
+ * fp64 accumulation in a fixed order (deterministic). precision selects how
+ * the Gaussians are evaluated (as pam_eval). d_err: device double [4]. Uses
+ * the fit workspace. PAM_ERR_INVALID_ARG for quad outside {0, 1}.
+ * Asynchronous.
  */
 pam_status pam_errors(const pam_problem *prob, const pam_plan *plan,
                       const pam_model *model, const double *d_K, double *d_err,
-                      int precision, void *d_workspace, size_t workspace_bytes, void *stream);
+                      int precision, int quad, void *d_workspace, size_t workspace_bytes,
+                      void *stream);
 
 /*
  * pam_errors without a workspace and without allocating device memory.

@@ -80,8 +80,13 @@ def lib():
                                    C.c_int64, f64p, C.c_int, f64p, C.c_void_p]
             L.orc_eval.restype = None
             L.orc_errors.argtypes = [C.c_int, i32p, i32p, C.c_int, i32p, f64p, f64p,
-                                     f64p, f64p]
+                                     f64p, C.c_int, f64p]
             L.orc_errors.restype = None
+            L.orc_gl_points.argtypes = [C.c_int, f64p, C.c_double, f64p]
+            L.orc_gl_points.restype = None
+            L.orc_residual_gl.argtypes = [C.c_int, C.c_int64, f64p, C.c_int, f64p, f64p, f64p, C.c_double,
+                                          C.c_double, f64p]
+            L.orc_residual_gl.restype = None
             _lib = L
     return _lib
 
@@ -90,7 +95,7 @@ class _Params(C.Structure):
     _fields_ = [("lambda1_hat", C.c_double), ("lambda2_hat", C.c_double),
                 ("eps_tol_rel", C.c_double), ("eta", C.c_double),
                 ("k_top", C.c_int), ("m_max", C.c_int), ("levels", C.c_int),
-                ("max_sweeps", C.c_int)]
+                ("max_sweeps", C.c_int), ("quad", C.c_int)]
 
 
 def _i32(a):
@@ -223,7 +228,7 @@ def enrich(dim, c, marked, x, ext_lo, ext_hi, eta, m_limit):
 
 def default_params(**kw):
     p = dict(lambda1_hat=4.59e-4, lambda2_hat=4.64e-6, eps_tol_rel=1e-3, eta=0.5,
-             k_top=37, m_max=1 << 30, levels=3, max_sweeps=200000)
+             k_top=37, m_max=1 << 30, levels=3, max_sweeps=200000, quad=0)
     p.update(kw)
     return p
 
@@ -269,11 +274,30 @@ def evaluate(model, pts, log_space=False, return_owner=False):
     return (out, own) if return_owner else out
 
 
-def errors(model, K):
-    """dict(l1, l2, l1_log, max_log10) of the reconstruction over the source cells."""
+def errors(model, K, quad=0):
+    """dict(l1, l2, l1_log, max_log10) of the reconstruction over the source cells
+    (quad 0: midpoint rule, 1: 2^dim-point Gauss-Legendre rule per cell)."""
     n_cells, n_sub = model["n_cells"], model["n_sub"]
     dim = len(n_cells)
     err = np.zeros(4)
     lib().orc_errors(dim, _pad3(n_cells, 1), _pad3(n_sub, 1), int(model["m_cap"]), _i32(model["M"]),
-                     _f64(model["c"]), _f64(model["beta"]), _f64(K).reshape(-1), err)
+                     _f64(model["c"]), _f64(model["beta"]), _f64(K).reshape(-1), int(quad), err)
     return dict(l1=err[0], l2=err[1], l1_log=err[2], max_log10=err[3])
+
+
+def gl_points(x, h):
+    """The 2^dim Gauss-Legendre nodes of the cell of side h centred at x [dim]."""
+    x = _f64(x).reshape(-1)
+    dim = x.shape[0]
+    pts = np.zeros(((1 << dim), dim))
+    lib().orc_gl_points(dim, x, float(h), pts)
+    return pts
+
+
+def residual_gl(x, c, beta, kv, vol, h, dim):
+    """Eq. (4) with the Gauss-Legendre rule for cells x [n, 3] (padded), dictionary c [m, 4]."""
+    x = _f64(x).reshape(-1, 3)
+    n, m = x.shape[0], int(c.shape[0])
+    R = np.zeros(n)
+    lib().orc_residual_gl(dim, n, x, m, _f64(c), _f64(beta), _f64(kv), float(vol), float(h), R)
+    return R

@@ -439,6 +439,49 @@ void orc_residual(int64_t n, int m, const double *W, const double *beta,
 }
 
 /*
+ * Two-point Gauss-Legendre rule per axis on a cell of side h centred at x
+ * (the tensor rule has 2^dim nodes, each of weight |T| / 2^dim): node q has
+ * x_a + s h / (2 sqrt(3)) on axis a, s = -1 if bit a of q is clear else +1.
+ * It integrates every polynomial of degree <= 3 in each variable exactly.
+ */
+void orc_gl_points(int dim, const double *x, double h, double *pts)
+{
+    const double off = 0.5 * h / sqrt(3.0);
+    for (int q = 0; q < (1 << dim); ++q)
+        for (int a = 0; a < dim; ++a)
+            pts[q * dim + a] = x[a] + (((q >> a) & 1) ? off : -off);
+}
+
+/*
+ * Eq. (4) with the 2^dim-point Gauss-Legendre rule instead of the midpoint:
+ * R_T = sum_q (|T| / 2^dim) (K*(x_T^q) - K_T)^2, K* = exp(W(x) beta) with the
+ * Shepard row W(x) of the subdomain's whole dictionary at each node.
+ */
+void orc_residual_gl(int dim, int64_t n, const double *x, int m, const double *c,
+                     const double *beta, const double *kv, double vol, double h, double *R)
+{
+    const int nq = 1 << dim;
+    double pts[8 * ORC_MAXD];
+    double *Wq = (double *)malloc(sizeof(double) * (size_t)nq * (size_t)(m > 0 ? m : 1));
+    for (int64_t j = 0; j < n; ++j) {
+        orc_gl_points(dim, x + j * 3, h, pts);
+        double pq[8 * 3];
+        for (int q = 0; q < nq; ++q)
+            for (int a = 0; a < 3; ++a) pq[q * 3 + a] = a < dim ? pts[q * dim + a] : 0.0;
+        orc_assemble(dim, nq, pq, m, c, Wq);
+        double r = 0.0;
+        for (int q = 0; q < nq; ++q) {
+            double t = 0.0;
+            for (int k = 0; k < m; ++k) t += Wq[q * m + k] * beta[k];
+            double e = exp(t) - kv[j];
+            r += (vol / (double)nq) * (e * e);
+        }
+        R[j] = r;
+    }
+    free(Wq);
+}
+
+/*
  * Algorithm 1 (3): E_worst = the k_top cells with the largest R_T.
  * Reading: only cells with R_T >= eps_tol are candidates (so "E_worst empty"
  * is reachable and equals the tolerance stop max R_T < eps_tol); cells are
@@ -550,6 +593,7 @@ typedef struct {
     double eps_tol_rel;              /* eps_tol = |T| (eps_tol_rel max K)^2; <0: no filter */
     double eta;
     int k_top, m_max, levels, max_sweeps;
+    int quad; /* R_T quadrature: 0 midpoint, 1 2^dim-point Gauss-Legendre */
 } orc_params;
 
 /* Per-subdomain diagnostics written by orc_fit_subdomain. */
@@ -610,7 +654,8 @@ int orc_fit_subdomain(int dim, const int *n_cells, const double *K,
         if (orc_enet(m, G, b, lam1, lam2, beta, P->max_sweeps, inf) != 0) certified = 0;
         sweeps += (int)inf[0];
         if (inf[2] < min_margin) min_margin = inf[2];
-        orc_residual(N, m, W, beta, kv, vol, R);
+        if (P->quad) orc_residual_gl(dim, N, x, m, c, beta, kv, vol, h, R);
+        else orc_residual(N, m, W, beta, kv, vol, R);
         maxR = 0.0;
         for (int64_t j = 0; j < N; ++j) if (R[j] > maxR) maxR = R[j];
         if (level >= P->levels || m >= m_limit) break;
@@ -729,36 +774,46 @@ void orc_eval(int dim, const int *n_cells, const int *n_sub, int m_cap,
 
 /*
  * Relative errors of the reconstruction over the source cells, each cell
- * measured with its owner's surrogate at its centroid (midpoint rule):
- *   err[0] = L1 in K:   sum |T| |K_T - K*(x_T)| / sum |T| |K_T|
- *   err[1] = L2 in K:   Eq. (12), (sum |T| (K_T - K*)^2 / sum |T| K_T^2)^(1/2)
- *   err[2] = L1 in log: sum |T| |ln K_T - ln K*(x_T)| / sum |T| |ln K_T|
- *   err[3] = max_T |log10 K_T - log10 K*(x_T)|
+ * measured with its owner's surrogate, by the midpoint rule (quad = 0: the
+ * centroid) or the 2^dim-point Gauss-Legendre rule (quad = 1: the nodes of
+ * orc_gl_points, weight 1/2^dim of the cell each, all inside the cell and
+ * so owned by the cell's subdomain):
+ *   err[0] = L1 in K:   sum_T sum_q w_q |K_T - K*(x_q)| / sum |T| |K_T|
+ *   err[1] = L2 in K:   Eq. (12), (sum w_q (K_T - K*)^2 / sum |T| K_T^2)^(1/2)
+ *   err[2] = L1 in log: sum w_q |ln K_T - ln K*(x_q)| / sum |T| |ln K_T|
+ *   err[3] = max over the points of |log10 K_T - log10 K*(x_q)|
  */
 void orc_errors(int dim, const int *n_cells, const int *n_sub, int m_cap,
                 const int32_t *M, const double *c, const double *beta,
-                const double *K, double *err)
+                const double *K, int quad, double *err)
 {
     int n[ORC_MAXD] = {1, 1, 1}, nmax = 1;
     for (int a = 0; a < dim; ++a) { n[a] = n_cells[a]; if (n[a] > nmax) nmax = n[a]; }
     double h = 1.0 / (double)nmax;
+    const int nq = quad ? (1 << dim) : 1;
     int64_t total = (int64_t)n[0] * n[1] * n[2];
-    double *x = (double *)malloc(sizeof(double) * (size_t)total * (size_t)dim);
-    double *v = (double *)malloc(sizeof(double) * (size_t)total);
+    double *x = (double *)malloc(sizeof(double) * (size_t)total * (size_t)nq * (size_t)dim);
+    double *v = (double *)malloc(sizeof(double) * (size_t)total * (size_t)nq);
     for (int64_t g = 0; g < total; ++g) {
         int64_t idx[3] = {g % n[0], (g / n[0]) % n[1], g / ((int64_t)n[0] * n[1])};
-        for (int a = 0; a < dim; ++a) x[g * dim + a] = ((double)idx[a] + 0.5) * h;
+        double xc[ORC_MAXD];
+        for (int a = 0; a < dim; ++a) xc[a] = ((double)idx[a] + 0.5) * h;
+        if (quad) orc_gl_points(dim, xc, h, x + g * nq * dim);
+        else for (int a = 0; a < dim; ++a) x[g * dim + a] = xc[a];
     }
-    orc_eval(dim, n_cells, n_sub, m_cap, M, c, beta, total, x, 1, v, NULL);
+    orc_eval(dim, n_cells, n_sub, m_cap, M, c, beta, total * nq, x, 1, v, NULL);
     double a1 = 0, b1 = 0, a2 = 0, b2 = 0, al = 0, bl = 0, mx = 0;
     for (int64_t g = 0; g < total; ++g) {
-        double ks = exp(v[g]);
         double lk = log(K[g]);
-        a1 += fabs(K[g] - ks); b1 += fabs(K[g]);
-        a2 += (K[g] - ks) * (K[g] - ks); b2 += K[g] * K[g];
-        al += fabs(lk - v[g]); bl += fabs(lk);
-        double d = fabs(lk - v[g]) / log(10.0);
-        if (d > mx) mx = d;
+        b1 += fabs(K[g]); b2 += K[g] * K[g]; bl += fabs(lk);
+        for (int q = 0; q < nq; ++q) {
+            double vq = v[g * nq + q], ks = exp(vq), w = 1.0 / (double)nq;
+            a1 += w * fabs(K[g] - ks);
+            a2 += w * (K[g] - ks) * (K[g] - ks);
+            al += w * fabs(lk - vq);
+            double d = fabs(lk - vq) / log(10.0);
+            if (d > mx) mx = d;
+        }
     }
     err[0] = a1 / b1;
     err[1] = sqrt(a2 / b2);

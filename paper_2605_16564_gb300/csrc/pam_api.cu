@@ -68,6 +68,7 @@ bool make_geo(const pam_problem *prob, const pam_params *par, Geo *g, Par *p, pa
         if (std::isnan(par->eps_tol_rel)) return false;
         if (par->k_top < 0 || par->m_max < 0 || par->levels < 0 || par->max_iters < 0) return false;
         if (par->warm_start != 0 && par->warm_start != 1) return false;
+        if (par->quad != 0 && par->quad != 1) return false;
         if (par->precision != PAM_PREC_FP64 && par->precision != PAM_PREC_MIXED) return false;
         int64_t add = (int64_t)par->levels * (g->dim + 1) * par->k_top;
         if (add > par->m_max) add = par->m_max;
@@ -93,6 +94,7 @@ bool make_geo(const pam_problem *prob, const pam_params *par, Geo *g, Par *p, pa
             p->m_max = par->m_max;
             p->levels = par->levels;
             p->max_iters = par->max_iters > 0 ? par->max_iters : 200;
+            p->quad = par->quad;
         }
     }
     *st = PAM_OK;
@@ -404,7 +406,7 @@ pam_status pam_eval(const pam_problem *prob, const pam_plan *plan, const pam_mod
 }
 
 pam_status pam_errors(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
-                      const double *d_K, double *d_err, int precision, void *d_workspace,
+                      const double *d_K, double *d_err, int precision, int quad, void *d_workspace,
                       size_t workspace_bytes, void *stream) {
     Geo g;
     pam_status st;
@@ -415,10 +417,11 @@ pam_status pam_errors(const pam_problem *prob, const pam_plan *plan, const pam_m
     g.n_max = plan->max_patch_cells;
     if (!model_ok(model) || !d_K || !d_err || !d_workspace) return PAM_ERR_INVALID_ARG;
     if (precision != PAM_PREC_FP64 && precision != PAM_PREC_MIXED) return PAM_ERR_INVALID_ARG;
+    if (quad != 0 && quad != 1) return PAM_ERR_INVALID_ARG;
     Ws w = carve_workspace(g, d_workspace);
     if (workspace_bytes < (size_t)((char *)w.y - (char *)d_workspace)) return PAM_ERR_WORKSPACE;
     launch_errors(g, model->boxes, model->centres, model->beta, model->info, d_K, d_err, precision,
-                  w, (cudaStream_t)stream);
+                  quad, w, (cudaStream_t)stream);
     PAM_CUDA_TRY(cudaGetLastError());
     return PAM_OK;
 }

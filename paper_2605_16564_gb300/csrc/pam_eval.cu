@@ -301,7 +301,7 @@ __global__ void __launch_bounds__(kErrThreads) k_errors_owner(Geo g, const int32
                                                               const double *centres,
                                                               const double *beta,
                                                               const int32_t *info, const double *K,
-                                                              double *part) {
+                                                              int quad, double *part) {
     const int s = blockIdx.x;
     const int M = info[s * kInfoN + PAM_INFO_M];
     const int32_t *box = boxes + s * 12;
@@ -316,26 +316,36 @@ __global__ void __launch_bounds__(kErrThreads) k_errors_owner(Geo g, const int32
     const int w0 = box[3] - box[0], w1 = box[4] - box[1], w2 = box[5] - box[2];
     const int cnt = w0 * w1 * w2;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    // the cell's nodes: its centroid, or the 2^dim Gauss-Legendre nodes
+    // (weight 1/nq of the cell each); all of them lie inside the cell
+    const int nq = quad ? (1 << g.dim) : 1;
+    const double off = __dmul_rn(0.5, g.h) / sqrt(3.0), wq = 1.0 / (double)nq;
     for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
         const int i = box[0] + t % w0, j = box[1] + (t / w0) % w1, k = box[2] + t / (w0 * w1);
         const int idx[3] = {i, j, k};
-        double x[3] = {0, 0, 0};
-        for (int a = 0; a < g.dim; ++a) x[a] = __dmul_rn((double)idx[a] + 0.5, g.h);
-        double v;
-        if (F32)
-            v = (double)shepard_f32_smem(sc32, sb32, M, (float)(x[0] - o[0]), (float)(x[1] - o[1]),
-                                         (float)(x[2] - o[2]));
-        else
-            v = shepard_f64_smem(sc64, sb64, M, x);
+        double xc[3] = {0, 0, 0};
+        for (int a = 0; a < g.dim; ++a) xc[a] = __dmul_rn((double)idx[a] + 0.5, g.h);
         const int64_t gi = (int64_t)i + (int64_t)g.n[0] * ((int64_t)j + (int64_t)g.n[1] * k);
-        const double kk = K[gi], ks = F32 ? exp_f32((float)v) : exp(v), lk = log(kk);
-        acc[0] += fabs(kk - ks);
+        const double kk = K[gi], lk = log(kk);
         acc[1] += fabs(kk);
-        acc[2] += (kk - ks) * (kk - ks);
         acc[3] += kk * kk;
-        acc[4] += fabs(lk - v);
         acc[5] += fabs(lk);
-        acc[6] = fmax(acc[6], fabs(lk - v));
+        for (int q = 0; q < nq; ++q) {
+            double x[3] = {xc[0], xc[1], xc[2]};
+            if (quad)
+                for (int a = 0; a < g.dim; ++a) x[a] = __dadd_rn(xc[a], ((q >> a) & 1) ? off : -off);
+            double v;
+            if (F32)
+                v = (double)shepard_f32_smem(sc32, sb32, M, (float)(x[0] - o[0]), (float)(x[1] - o[1]),
+                                             (float)(x[2] - o[2]));
+            else
+                v = shepard_f64_smem(sc64, sb64, M, x);
+            const double ks = F32 ? exp_f32((float)v) : exp(v);
+            acc[0] += wq * fabs(kk - ks);
+            acc[2] += wq * ((kk - ks) * (kk - ks));
+            acc[4] += wq * fabs(lk - v);
+            acc[6] = fmax(acc[6], fabs(lk - v));
+        }
     }
     __shared__ double red[kErrThreads / 32][7];
     for (int q = 0; q < 7; ++q) {
@@ -380,19 +390,93 @@ __global__ void __launch_bounds__(256) k_errors_combine(const double *part, int 
 }
 
 void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
-                   const int32_t *info, const double *K, double *err, int precision, const Ws &w,
-                   cudaStream_t st) {
+                   const int32_t *info, const double *K, double *err, int precision, int quad,
+                   const Ws &w, cudaStream_t st) {
     PhaseScope ps(kPhErrors, st);
     if (precision == PAM_PREC_MIXED) {
         size_t sm = (size_t)g.m_cap * (sizeof(float4) + sizeof(float));
-        k_errors_owner<true><<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, w.err_part);
+        k_errors_owner<true><<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, quad, w.err_part);
     } else {
         size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));
         cudaFuncSetAttribute(k_errors_owner<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_errors_owner<false><<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, w.err_part);
+        k_errors_owner<false><<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, quad, w.err_part);
     }
     k_errors_combine<<<1, 256, 0, st>>>(w.err_part, g.S, err);
     count_launches(2);
+}
+
+// --------------------------------------------------------------------------
+// Indicators R_T (Eq. (4)) with the tensor two-point Gauss-Legendre rule:
+// R_T = sum_q (|T| / 2^dim) (K*(x_q) - K_T)^2 over the nodes x_T +- h/(2
+// sqrt 3) per axis, K* from the subdomain's whole dictionary at each node
+// (Shepard weights, max-shifted). One block per running subdomain, a thread
+// per patch cell (patch order, x fastest).
+// --------------------------------------------------------------------------
+template <bool F32>
+__global__ void __launch_bounds__(256) k_residual_quad(Geo g, const int32_t *boxes, const double *centres,
+                                                       const double *beta, const int32_t *info, Ws w) {
+    const int s = blockIdx.x;
+    const int32_t *inf = info + s * kInfoN;
+    if (inf[PAM_INFO_STOPPED]) return;
+    const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
+    const int32_t *box = boxes + s * 12;
+    extern __shared__ uint8_t smb[];
+    dvec4 *sc64 = reinterpret_cast<dvec4 *>(smb);
+    double *sb64 = reinterpret_cast<double *>(sc64 + g.m_cap);
+    float4 *sc32 = reinterpret_cast<float4 *>(smb);
+    float *sb32 = reinterpret_cast<float *>(sc32 + g.m_cap);
+    double o[3];
+    if (F32) stage_f32(g, boxes, centres, beta, s, M, sc32, sb32, o);
+    else stage_f64(g, centres, beta, s, M, sc64, sb64);
+    const int w0 = box[9] - box[6], w1 = box[10] - box[7];
+    const int nq = 1 << g.dim;
+    const double off = __dmul_rn(0.5, g.h) / sqrt(3.0), wq = g.vol / (double)nq;
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        const int idx[3] = {box[6] + t % w0, box[7] + (t / w0) % w1, box[8] + t / (w0 * w1)};
+        double xc[3] = {0, 0, 0};
+        for (int a = 0; a < g.dim; ++a) xc[a] = __dmul_rn((double)idx[a] + 0.5, g.h);
+        const double kv = w.kv[(size_t)s * g.n_max + t];
+        double r = 0.0;
+        // nodes in pairs (q, q + 1): in the fp32 form one pass over the
+        // centres serves both; the sum keeps the node order
+        for (int q = 0; q < nq; q += 2) {
+            double x0[3] = {0, 0, 0}, x1[3] = {0, 0, 0};
+            for (int a = 0; a < g.dim; ++a) {
+                x0[a] = __dadd_rn(xc[a], ((q >> a) & 1) ? off : -off);
+                x1[a] = __dadd_rn(xc[a], (((q + 1) >> a) & 1) ? off : -off);
+            }
+            double v0, v1;
+            if (F32) {
+                const float p0[3] = {(float)(x0[0] - o[0]), (float)(x0[1] - o[1]), (float)(x0[2] - o[2])};
+                const float p1[3] = {(float)(x1[0] - o[0]), (float)(x1[1] - o[1]), (float)(x1[2] - o[2])};
+                float f0, f1;
+                shepard_f32_smem2(sc32, sb32, M, p0, p1, &f0, &f1);
+                v0 = f0;
+                v1 = f1;
+            } else {
+                v0 = shepard_f64_smem(sc64, sb64, M, x0);
+                v1 = shepard_f64_smem(sc64, sb64, M, x1);
+            }
+            const double e0 = __dsub_rn(exp(v0), kv), e1 = __dsub_rn(exp(v1), kv);
+            r = __dadd_rn(r, __dmul_rn(wq, __dmul_rn(e0, e0)));
+            r = __dadd_rn(r, __dmul_rn(wq, __dmul_rn(e1, e1)));
+        }
+        w.R[(size_t)s * g.n_max + t] = r;
+    }
+}
+
+void launch_residual_quad(const Geo &g, int precision, const int32_t *boxes, const double *centres,
+                          const double *beta, const int32_t *info, const Ws &w, cudaStream_t st) {
+    PhaseScope ps(kPhResidual, st);
+    if (precision == PAM_PREC_MIXED) {
+        size_t sm = (size_t)g.m_cap * (sizeof(float4) + sizeof(float));
+        k_residual_quad<true><<<g.S, 256, sm, st>>>(g, boxes, centres, beta, info, w);
+    } else {
+        size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));
+        cudaFuncSetAttribute(k_residual_quad<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_residual_quad<false><<<g.S, 256, sm, st>>>(g, boxes, centres, beta, info, w);
+    }
+    count_launches(1);
 }
 
 }  // namespace pam

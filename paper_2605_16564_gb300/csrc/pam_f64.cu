@@ -845,7 +845,9 @@ void launch_residual_mixed(const Geo &g, const int32_t *boxes, const double *cen
 void launch_refine_round(const Geo &g, const Par &p, int precision, const int32_t *boxes,
                          double *centres, double *beta, int32_t *info, const Ws &w,
                          cudaStream_t st) {
-    if (precision == PAM_PREC_MIXED)
+    if (p.quad)
+        launch_residual_quad(g, precision, boxes, centres, beta, info, w, st);
+    else if (precision == PAM_PREC_MIXED)
         launch_residual_mixed(g, boxes, centres, beta, info, w, st);
     else
         launch_residual_f64(g, beta, info, w, st);

@@ -34,6 +34,7 @@ struct Geo {
 struct Par {
     double lam1_hat, lam2_hat, eps_tol_rel, eta;
     int k_top, m_max, levels, max_iters;
+    int quad;  // 0 midpoint, 1 Gauss-Legendre indicators
 };
 
 // Workspace carve-up. Every region is 256-byte aligned.
@@ -90,8 +91,10 @@ void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, cons
                  int precision, void *ws, cudaStream_t st);
 size_t eval_workspace_bytes(int S, int64_t n_pts);
 void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
-                   const int32_t *info, const double *K, double *err, int precision, const Ws &w,
-                   cudaStream_t st);
+                   const int32_t *info, const double *K, double *err, int precision, int quad,
+                   const Ws &w, cudaStream_t st);
+void launch_residual_quad(const Geo &g, int precision, const int32_t *boxes, const double *centres,
+                          const double *beta, const int32_t *info, const Ws &w, cudaStream_t st);
 bool mixed_solve_fits(const Geo &g);
 
 // Kernel families timed by the optional event profiler (pam_timing_*).

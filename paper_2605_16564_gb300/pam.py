@@ -49,7 +49,7 @@ class pam_params(C.Structure):
     _fields_ = [("lambda1_hat", C.c_double), ("lambda2_hat", C.c_double),
                 ("eps_tol_rel", C.c_double), ("eta", C.c_double), ("k_top", C.c_int),
                 ("m_max", C.c_int), ("levels", C.c_int), ("max_iters", C.c_int),
-                ("precision", C.c_int), ("warm_start", C.c_int)]
+                ("precision", C.c_int), ("warm_start", C.c_int), ("quad", C.c_int)]
 
 
 class pam_plan(C.Structure):
@@ -87,7 +87,7 @@ def lib():
         L.pam_eval.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_int64,
                                C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_errors.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_void_p,
-                                 C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
+                                 C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_gram.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), C.c_void_p, P(pam_model),
                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_nn_sizes.argtypes = [C.c_int, C.c_int, P(C.c_int64), P(C.c_size_t)]
@@ -143,9 +143,11 @@ def make_problem(n_cells, n_sub, overlap, g_init):
 
 
 def make_params(lambda1_hat=4.59e-4, lambda2_hat=4.64e-6, eps_tol_rel=1e-3, eta=0.5, k_top=37,
-                m_max=1 << 30, levels=3, max_iters=0, precision=PAM_PREC_FP64, warm_start=0):
+                m_max=1 << 30, levels=3, max_iters=0, precision=PAM_PREC_FP64, warm_start=0, quad=0):
+    """quad: quadrature of the indicators R_T, 0 midpoint, 1 two-point Gauss-Legendre per axis."""
     p = pam_params()
     p.warm_start = warm_start
+    p.quad = quad
     p.lambda1_hat, p.lambda2_hat, p.eps_tol_rel, p.eta = lambda1_hat, lambda2_hat, eps_tol_rel, eta
     p.k_top, p.m_max, p.levels, p.max_iters, p.precision = k_top, min(m_max, (1 << 31) - 1), levels, \
         max_iters, precision
@@ -210,9 +212,9 @@ def pam_eval(problem, plan, model, pts, out, log_space=False, precision=PAM_PREC
                           nbytes, _stream(stream)), "pam_eval")
 
 
-def pam_errors(problem, plan, model, K, err, workspace, precision=PAM_PREC_FP64, stream=None):
+def pam_errors(problem, plan, model, K, err, workspace, precision=PAM_PREC_FP64, stream=None, quad=0):
     _check(lib().pam_errors(C.byref(problem), C.byref(plan), C.byref(model.c_struct()), _ptr(K),
-                            _ptr(err), int(precision), _ptr(workspace),
+                            _ptr(err), int(precision), int(quad), _ptr(workspace),
                             workspace.numel() * workspace.element_size(), _stream(stream)), "pam_errors")
 
 
@@ -358,11 +360,13 @@ class Fitter:
                  self.eval_workspace(pts.shape[0]), stream)
         return out
 
-    def errors(self, K, precision=None, stream=None):
+    def errors(self, K, precision=None, stream=None, quad=None):
+        """quad: the errors' quadrature (default: the fit's indicator quadrature)."""
         import torch
         err = torch.zeros(4, dtype=torch.float64, device=K.device)
         prec = self.params.precision if precision is None else precision
-        pam_errors(self.problem, self.plan, self.model, K, err, self.workspace, prec, stream)
+        q = self.params.quad if quad is None else quad
+        pam_errors(self.problem, self.plan, self.model, K, err, self.workspace, prec, stream, quad=q)
         e = err.cpu().numpy()
         return dict(l1=e[0], l2=e[1], l1_log=e[2], max_log10=e[3])
 

@@ -206,3 +206,26 @@ def test_channel_field_1024_sampled_subdomains(torch_dev):
     pts = np.concatenate([ref["boxes"][s, 0:2] * h + rng.uniform(0, 1, size=(100, 2)) * 32 * h for s in which])
     out = fit.eval(torch.from_numpy(pts).to(dev)).cpu().numpy()
     assert np.abs(out - oracle.evaluate(ref, pts)).max() <= KSTAR_RTOL * (K.max() - K.min())
+
+
+@pytest.mark.parametrize("case", ["voronoi2d", "layered3d"])
+def test_gauss_legendre_indicators_match_the_oracle(torch_dev, case):
+    # pam_params.quad = 1: the indicators R_T (and the errors) on the
+    # 2^dim-point Gauss-Legendre rule; same decisions as the oracle's.
+    torch, dev = torch_dev
+    if case == "voronoi2d":
+        K = fields.voronoi_field(64, n_sites=8, seed=34)
+        geo = ((64, 64), (2, 2), 1, (4, 4))
+    else:
+        K = fields.layered_field((24, 44, 17), seed=7)
+        geo = ((24, 44, 17), (2, 4, 1), 1, (4, 4, 2))
+    params = dict(k_top=5, levels=2, quad=1)
+    fit, Kd = _fit_gpu(torch, dev, K, *geo, **params)
+    ref = oracle.fit_all(K, *geo, oracle.default_params(**params))
+    assert ref["failed"] == 0
+    _compare_models(fit.host_model(), ref)
+    e_gpu, e_ref = fit.errors(Kd), oracle.errors(ref, K, quad=1)
+    for k in ("l1", "l2", "l1_log", "max_log10"):
+        assert e_gpu[k] == pytest.approx(e_ref[k], rel=1e-9), k
+    # the midpoint errors of the same model differ (the rule is really applied)
+    assert fit.errors(Kd, quad=0)["l1"] != pytest.approx(e_gpu["l1"], rel=1e-6)

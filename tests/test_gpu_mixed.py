@@ -231,3 +231,18 @@ def test_mixed_channel_field_1024_sample(env):
     assert same >= 0.75 * len(which), same
     assert bad == 0
     assert abs(l1m - l1o) <= L1_RTOL * l1o
+
+
+def test_mixed_gauss_legendre_indicators(env):
+    # the mixed form with pam_params.quad = 1 against the oracle on the same
+    # rule: final L1 (Gauss-Legendre errors) within 1 %
+    torch, pam, dev = env
+    K = fields.voronoi_field(256, n_sites=32, seed=2)
+    params = dict(k_top=37, levels=3, quad=1)
+    fit, Kd = _mixed_fit(env, K, (256, 256), (8, 8), 2, (8, 8), 3, **params)
+    ref = oracle.fit_all(K, (256, 256), (8, 8), 2, (8, 8), oracle.default_params(**params))
+    e_m = fit.errors(Kd)
+    e_o = oracle.errors(ref, K, quad=1)
+    assert abs(e_m["l1"] - e_o["l1"]) <= L1_RTOL * e_o["l1"], (e_m["l1"], e_o["l1"])
+    flags = fit.host_model()["info"][:, pam.INFO_FLAGS]
+    assert np.count_nonzero(flags & pam.FLAG_NOT_CERTIFIED) == 0

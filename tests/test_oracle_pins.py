@@ -366,6 +366,96 @@ def test_residual_indicators_sum_to_the_squared_l2_error():
     assert np.all(R >= 0)
 
 
+# Gauss-Legendre indicators (quad = 1), the first "next" row: pinned by the
+# rule's exactness on cubics, a constant surrogate, a brute-force fine
+# subdivision and the L2 identity above under the same rule.
+
+@pytest.mark.parametrize("dim", [1, 2, 3])
+def test_gauss_legendre_nodes_integrate_cubics_exactly(dim):
+    rng = np.random.default_rng(31)
+    h = 0.37
+    x0 = rng.uniform(-1, 1, size=dim)
+    pts = oracle.gl_points(x0, h)
+    assert pts.shape == (2 ** dim, dim)
+    # the cell average of prod_a x_a^p_a, exactly, for every degree <= 3
+    def exact(p):
+        v = 1.0
+        for a in range(dim):
+            lo, hi = x0[a] - h / 2, x0[a] + h / 2
+            v *= (hi ** (p[a] + 1) - lo ** (p[a] + 1)) / ((p[a] + 1) * h)
+        return v
+    for p in np.ndindex(*([4] * dim)):
+        q = np.prod(pts ** np.array(p), axis=1).mean()
+        assert q == pytest.approx(exact(p), rel=1e-12, abs=1e-14), p
+    # ... and not for degree 4 (it is not the midpoint rule in disguise)
+    p4 = [4] + [0] * (dim - 1)
+    assert abs(np.prod(pts ** np.array(p4), axis=1).mean() - exact(p4)) > 1e-6
+
+
+def test_gauss_legendre_residual_of_a_constant_surrogate():
+    # W rows sum to one, so beta = b for every centre gives K* = e^b at every
+    # node: R_T = |T| (e^b - K_T)^2 for each rule.
+    rng = np.random.default_rng(32)
+    x, c = _random_problem(rng, n=40, m=9, dim=2, spread=0.5)
+    kv = rng.uniform(0.5, 2.0, size=40)
+    beta = np.full(9, 0.3)
+    vol, h = 0.01, 0.1
+    R = oracle.residual_gl(x, c, beta, kv, vol, h, 2)
+    np.testing.assert_allclose(R, vol * (np.exp(0.3) - kv) ** 2, rtol=1e-12)
+
+
+def test_gauss_legendre_residual_against_fine_subdivision():
+    # a smooth surrogate (wide Gaussians): the two-point rule matches a 64 x 64
+    # midpoint subdivision of each cell far better than the one-point rule
+    n_cells = (12, 12)
+    h = 1 / 12
+    c = oracle.initial_dictionary(n_cells, (0, 0, 0), (12, 12, 1), (3, 3))
+    rng = np.random.default_rng(33)
+    beta = rng.normal(size=c.shape[0])
+    x, _, _ = oracle.box_cells(n_cells, (0, 0, 0), (12, 12, 1), np.ones((12, 12)))
+    kv = np.full(x.shape[0], 1.7)
+    vol = h * h
+    R_gl = oracle.residual_gl(x, c, beta, kv, vol, h, 2)
+    R_mid = oracle.residual(oracle.assemble(2, x, c), beta, kv, vol)
+    f = (np.arange(64) + 0.5) / 64 - 0.5
+    R_ref = np.zeros(x.shape[0])
+    for j in range(x.shape[0]):
+        sub = np.zeros((64 * 64, 3))
+        sub[:, 0] = x[j, 0] + np.repeat(f, 64) * h
+        sub[:, 1] = x[j, 1] + np.tile(f, 64) * h
+        t = oracle.assemble(2, sub, c) @ beta
+        R_ref[j] = vol * np.mean((np.exp(t) - kv[j]) ** 2)
+    e_gl = np.abs(R_gl - R_ref) / R_ref
+    e_mid = np.abs(R_mid - R_ref) / R_ref
+    assert e_gl.max() <= 1e-3
+    assert np.median(e_gl) < 0.05 * np.median(e_mid)
+
+
+def test_gauss_legendre_indicators_sum_to_the_squared_l2_error():
+    # the L2 identity of the midpoint test, with both sides on the same
+    # two-point rule (the errors through the independent evaluation path)
+    K = fields.voronoi_field(24, n_sites=6, seed=12)
+    n_cells = (24, 24)
+    x, y, kv = oracle.box_cells(n_cells, (0, 0, 0), (24, 24, 1), K)
+    c = oracle.initial_dictionary(n_cells, (0, 0, 0), (24, 24, 1), (6, 6))
+    W = oracle.assemble(2, x, c)
+    G, b = oracle.gram(W, y)
+    beta, _ = oracle.enet(G, b, 24 * 24 * 4.59e-4, 24 * 24 * 4.64e-6)
+    vol = (1 / 24) ** 2
+    R = oracle.residual_gl(x, c, beta, kv, vol, 1 / 24, 2)
+    model = _single_model(c, beta, n_cells)
+    err = oracle.errors(model, K, quad=1)
+    assert R.sum() / (vol * (kv ** 2).sum()) == pytest.approx(err["l2"] ** 2, rel=1e-11)
+
+
+def test_algorithm1_with_gauss_legendre_indicators_certifies():
+    K = fields.voronoi_field(64, n_sites=8, seed=34)
+    params = oracle.default_params(k_top=5, levels=2, quad=1)
+    ref = oracle.fit_all(K, (64, 64), (2, 2), 1, (4, 4), params)
+    assert ref["failed"] == 0
+    assert np.all(ref["M"] == 16 + 2 * 3 * 5)
+
+
 def test_mark_matches_sorting():
     rng = np.random.default_rng(13)
     for trial in range(20):
