@@ -71,6 +71,8 @@ def test_plan_sizes(pam):
     dict(params=dict(eta=1.0)),
     dict(params=dict(k_top=-1)),
     dict(params=dict(precision=7)),
+    dict(params=dict(quad=2)),
+    dict(params=dict(warm_start=3)),
 ])
 def test_invalid_arguments_are_rejected(pam, bad):
     base = dict(n_cells=(8, 8), n_sub=(2, 2), overlap=1, g_init=(2, 2))
@@ -99,3 +101,31 @@ def test_null_arguments_are_rejected(pam):
     plan = pam.pam_plan_create(pr, par)
     assert L.pam_fit_subdomains(C.byref(pr), C.byref(par), C.byref(plan), None, None, None, 0, None) == 1
     assert L.pam_eval(C.byref(pr), C.byref(plan), None, None, 0, None, 0, 0, None, 0, None) == 1
+
+
+def test_network_sizes_and_geometry(pam):
+    # both architectures: parameter counts from the layer tables, geometry,
+    # and rejection of unknown architectures and bad batches (host only)
+    import oracle.nn as onn
+    for arch in (0, 1):
+        n, ws = pam.pam_nn_sizes(64, arch=arch)
+        assert n == onn.layout(arch)[1] and ws > 0
+        A = onn.ARCHS[arch]
+        assert pam.pam_nn_geometry(arch) == (A["h0"], A["c0"], A["n_out"])
+    L = pam.lib()
+    import ctypes as C
+    n, ws = C.c_int64(0), C.c_size_t(0)
+    assert L.pam_nn_sizes(2, 64, C.byref(n), C.byref(ws)) == 1
+    assert L.pam_nn_sizes(0, 33, C.byref(n), C.byref(ws)) == 1
+
+
+def test_layered_inputs_reject_unsupported_problems(pam):
+    import ctypes as C
+    L = pam.lib()
+    # a 2-D problem, and a 3-D one whose patches exceed 16 x 16 x 8 cells
+    pr2 = pam.make_problem((8, 8), (2, 2), 1, (2, 2))
+    plan2 = pam.pam_plan_create(pr2, pam.make_params())
+    assert L.pam_nn_layered_inputs(C.byref(pr2), C.byref(plan2), C.c_void_p(8), C.c_void_p(8), 32, None) == 1
+    pr3 = pam.make_problem((40, 20, 10), (1, 1, 1), 0, (4, 4, 2))
+    plan3 = pam.pam_plan_create(pr3, pam.make_params())
+    assert L.pam_nn_layered_inputs(C.byref(pr3), C.byref(plan3), C.c_void_p(8), C.c_void_p(8), 32, None) == 6
