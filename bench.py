@@ -307,27 +307,92 @@ def run_pam(args, rank, ws):
                    "seed_threshold": lw.threshold, "level0_active_set_steps_cold": round(cold_it, 3),
                    "level0_active_set_steps_learned": round(warm_it, 3)}
 
-    def fit_step():
+    def fit_step(deferred=False):
         if lw is not None:
             lw.seed(fit, Kd)
-            fit.fit(Kd, warm_start=True)
+            fit.fit(Kd, warm_start=True, deferred=deferred)
         else:
-            fit.fit(Kd)
+            fit.fit(Kd, deferred=deferred)
+
+    errd = torch.zeros(4, dtype=torch.float64, device=dev)
 
     def step():
         fit_step()
         fit.eval(ptsd, out=out)
         return fit.errors(Kd)
 
+    def step_body(seeded=True):
+        # the same step without host synchronisation (deferred status), so
+        # that it can be captured in a CUDA graph and replayed
+        if seeded:
+            fit_step(deferred=True)
+        else:
+            fit.fit(Kd, deferred=True)
+        fit.eval(ptsd, out=out)
+        fit.errors_device(Kd, errd)
+
+    def check_status():
+        code = fit.status()
+        if code != 0:
+            raise pam.PamError(code, "deferred fit")
+
+    def capture(body, timed=False):
+        cap = torch.cuda.Stream(device=dev)
+        cap.wait_stream(torch.cuda.current_stream())
+        with torch.cuda.stream(cap):
+            body()  # one eager pass on a side stream before capture
+        torch.cuda.current_stream().wait_stream(cap)
+        torch.cuda.synchronize()
+        check_status()
+        g = torch.cuda.CUDAGraph()
+        L.pam_timing_enable(1 if timed else 0)  # phase event pairs of the captured launches only
+        try:
+            with torch.cuda.graph(g):
+                body()
+        finally:
+            L.pam_timing_enable(0)
+        return g
+
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
 
     L = pam.lib()
+    import ctypes as C
+
+    def read_phases():
+        got = {}
+        for i, name in enumerate(PHASES):
+            tot, cnt = C.c_double(0), C.c_int(0)
+            L.pam_timing_read(i, C.byref(tot), C.byref(cnt))
+            if cnt.value:
+                got[name] = (tot.value, cnt.value)
+        return got
+
+    # the timed step is a CUDA graph of the whole step (captured once, with
+    # the phase event pairs as graph nodes), else eager launches
+    graph, mode = None, "eager"
     L.pam_timing_reset()
-    L.pam_timing_enable(1)
-    launches0 = L.pam_kernel_launches()
+    if not args.no_graph:
+        try:
+            l0 = L.pam_kernel_launches()
+            graph = capture(step_body, timed=True)
+            launches_per_step = (L.pam_kernel_launches() - l0) // 2  # the eager pre-pass + the capture
+            for _ in range(args.warmup):
+                graph.replay()
+            torch.cuda.synchronize()
+            check_status()
+            mode = "graph"
+        except Exception as e:  # reported in the JSON line; the eager step is timed instead
+            graph = None
+            torch.cuda.synchronize()
+            L.pam_timing_reset()
+            mode = f"eager (graph capture failed: {type(e).__name__}: {str(e)[:160]})"
+    if graph is None:
+        L.pam_timing_enable(1)
+        launches0 = L.pam_kernel_launches()
     times = []
+    phase_tot = {}
     barrier(ws)
     torch.cuda.synchronize()
     with ClockSampler(dev.index) as clk:
@@ -337,41 +402,60 @@ def run_pam(args, rank, ws):
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
             torch.cuda.nvtx.range_push("pam_step")  # lets a profiler select the timed steps
-            err = step()
+            if graph is not None:
+                graph.replay()
+            else:
+                err = step()
             torch.cuda.nvtx.range_pop()
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
+            if graph is not None:  # this replay's phase times (host work between timed steps)
+                for k, (t, c) in read_phases().items():
+                    a = phase_tot.setdefault(k, [0.0, c])
+                    a[0] += t
     barrier(ws)
-    launches = L.pam_kernel_launches() - launches0
-    L.pam_timing_enable(0)
     phase_ms = {}
-    for i, name in enumerate(PHASES):
-        import ctypes as C
-        tot, cnt = C.c_double(0), C.c_int(0)
-        L.pam_timing_read(i, C.byref(tot), C.byref(cnt))
-        if cnt.value:
-            phase_ms[name] = (tot.value / args.steps, cnt.value // args.steps)
+    if graph is not None:
+        check_status()
+        err = pam.error_dict(errd)
+        launches = launches_per_step * args.steps
+        phase_ms = {k: (v[0] / args.steps, v[1]) for k, v in phase_tot.items()}
+    else:
+        launches = L.pam_kernel_launches() - launches0
+        L.pam_timing_enable(0)
+        for k, (t, c) in read_phases().items():
+            phase_ms[k] = (t / args.steps, c // args.steps)
+    del graph
+    torch.cuda.synchronize()
     L.pam_timing_reset()
 
     step_ms = max_over_ranks(sum(times) / len(times), ws, dev)
     value = n_cells * ws / (step_ms / 1e3)
     info = fit.model.info.cpu().numpy()
     if lw is not None:
-        # the same step without the learned seed (level 0 from beta = 0), for comparison
+        # the same step without the learned seed (level 0 from beta = 0), for
+        # comparison, in the same launch mode
+        g2 = capture(lambda: step_body(seeded=False)) if mode == "graph" else None
         plain_times = []
         for i in range(args.warmup + args.steps):
             flush.fill_(1)
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
             e0.record(stream)
-            fit.fit(Kd)
-            fit.eval(ptsd, out=out)
-            fit.errors(Kd)
+            if g2 is not None:
+                g2.replay()
+            else:
+                fit.fit(Kd)
+                fit.eval(ptsd, out=out)
+                fit.errors(Kd)
             e1.record(stream)
             torch.cuda.synchronize()
             if i >= args.warmup:
                 plain_times.append(e0.elapsed_time(e1))
+        if g2 is not None:
+            check_status()
+            del g2
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
@@ -386,33 +470,53 @@ def run_pam(args, rank, ws):
     Kh = torch.from_numpy(np.ascontiguousarray(K)).pin_memory()
     ptsh = torch.from_numpy(pts).pin_memory()
     outh = torch.empty(n_pts, dtype=torch.float64).pin_memory()
-    e2e_times = []
+    errh = torch.empty(4, dtype=torch.float64).pin_memory()
     side = torch.cuda.Stream(device=dev)  # the evaluation points and the result travel beside the fit
+    pts_ready, out_ready = torch.cuda.Event(), torch.cuda.Event()
+
+    def e2e_body():
+        cur = torch.cuda.current_stream()
+        side.wait_stream(cur)
+        with torch.cuda.stream(side):
+            ptsd.copy_(ptsh, non_blocking=True)
+            pts_ready.record(side)
+        Kd.copy_(Kh, non_blocking=True)
+        fit_step(deferred=True)
+        cur.wait_event(pts_ready)
+        fit.eval(ptsd, out=out)
+        out_ready.record(cur)
+        with torch.cuda.stream(side):
+            side.wait_event(out_ready)
+            outh.copy_(out, non_blocking=True)
+        fit.errors_device(Kd, errd)
+        errh.copy_(errd, non_blocking=True)
+        cur.wait_stream(side)
+
+    ge = None
+    if mode == "graph":
+        try:
+            ge = capture(e2e_body)
+        except Exception:
+            ge = None
+    e2e_times = []
     for it in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         flush.fill_(1)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        with torch.cuda.stream(side):
-            ptsd.copy_(ptsh, non_blocking=True)
-            pts_ready = torch.cuda.Event()
-            pts_ready.record(side)
-        Kd.copy_(Kh, non_blocking=True)
-        fit_step()
-        stream.wait_event(pts_ready)
-        fit.eval(ptsd, out=out)
-        out_ready = torch.cuda.Event()
-        out_ready.record(stream)
-        with torch.cuda.stream(side):
-            side.wait_event(out_ready)
-            outh.copy_(out, non_blocking=True)
-        errh = fit.errors(Kd)
+        if ge is not None:
+            ge.replay()
+        else:
+            e2e_body()
         torch.cuda.synchronize()
         if it >= args.warmup:
             e2e_times.append(time.perf_counter() - t0)
+    check_status()
+    e2e_mode = "graph" if ge is not None else "eager"
+    del ge
     e2e_s = max_over_ranks(sum(e2e_times) / len(e2e_times), ws, dev)
     h2d = Kh.numel() * 8 + ptsh.numel() * 8
-    d2h = outh.numel() * 8 + 4 * 8
+    d2h = outh.numel() * 8 + errh.numel() * 8
 
     # --- the plain binary64 form, for the chosen-vs-plain ratio -------------
     plain = None
@@ -449,7 +553,8 @@ def run_pam(args, rank, ws):
 
     return dict(value=value, step_ms=step_ms, times=times, err=err, phase_ms=phase_ms, launches=launches,
                 clocks=clk.summary(), e2e_s=e2e_s, h2d=h2d, d2h=d2h, plain=plain, roof=roof, roofs=roofs,
-                prec_name=prec_name, n_cells=n_cells, n_pts=n_pts, info=info, learned=learned)
+                prec_name=prec_name, n_cells=n_cells, n_pts=n_pts, info=info, learned=learned, mode=mode,
+                e2e_mode=e2e_mode)
 
 
 def owner_counts(W, pts):
@@ -524,6 +629,7 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="3-D mixed form without the learned warm start")
+    ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of a CUDA graph replay")
     ap.add_argument("--quad", type=int, default=0, choices=[0, 1],
                     help="indicator and error quadrature: 0 midpoint, 1 two-point Gauss-Legendre per axis")
     args = ap.parse_args()
@@ -583,14 +689,15 @@ def main():
         "data": "synthetic",
         "config": dict(cfg, precision=r["prec_name"],
                        quadrature="midpoint" if args.quad == 0 else "Gauss-Legendre 2^dim points",
-                       warm_start=r["learned"]["kind"] if r["learned"] else "previous level (Algorithm 1)"),
+                       warm_start=r["learned"]["kind"] if r["learned"] else "previous level (Algorithm 1)",
+                       launch=r["mode"]),
         "eval_pts_per_s": r["n_pts"] * ws / (eval_ms / 1e3) if eval_ms else None,
         "fit_cells_per_s": None,
         "l1_rel": r["err"]["l1"], "l2_rel": r["err"]["l2"],
         "roofline": r["roof"],
         "cpu_baseline": cpu,
         "e2e": {"value": r["n_cells"] * ws / r["e2e_s"], "unit": "cells/s",
-                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"]},
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"], "launch": r["e2e_mode"]},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
         "phase_ms_per_step": {k: round(v[0], 4) for k, v in r["phase_ms"].items()},

@@ -111,6 +111,12 @@ typedef struct {
                             (one node, the centroid), 1 = tensor two-point
                             Gauss-Legendre (2^dim nodes x_T +- h / (2 sqrt 3) per
                             axis, weight |T| / 2^dim each) */
+    int deferred_status; /* pam_fit_subdomains / pam_refine: 0 = synchronise once and
+                            return the device status; 1 = no host synchronisation
+                            (the calls can be captured in a CUDA graph): they return
+                            PAM_OK after the launches, fit even when some K_T is
+                            invalid, and the status accumulates in the workspace
+                            until pam_status_read */
 } pam_params;
 
 /* Sizes derived from a problem and parameters by pam_plan_create. */
@@ -178,6 +184,15 @@ pam_status pam_fit_subdomains(const pam_problem *prob, const pam_params *par,
                               const pam_plan *plan, const double *d_K,
                               pam_model *model, void *d_workspace,
                               size_t workspace_bytes, void *stream);
+
+/*
+ * Status of the pam_fit_subdomains / pam_refine calls made with
+ * deferred_status = 1 on this workspace since the last pam_fit_subdomains:
+ * synchronises `stream` and returns PAM_ERR_NONPOSITIVE_K (some K_T <= 0,
+ * NaN or Inf: the results are meaningless), PAM_ERR_TIMEOUT,
+ * PAM_ERR_NOT_CONVERGED (some solve not certified) or PAM_OK.
+ */
+pam_status pam_status_read(const pam_plan *plan, void *d_workspace, size_t workspace_bytes, void *stream);
 
 /*
  * Step 3 (section 2; Algorithm 1 (2)-(5)) n_levels times on every
@@ -343,6 +358,11 @@ pam_status pam_nn_adamw(float *d_params, const float *d_grads, float *d_m, float
  * Families: PAM_PHASE_* (prepare, assemble, gram, solve, residual, mark,
  * eval, errors, stats, gram_tc, refine). Not thread-safe against concurrent
  * enable/reset; intended for benchmarks. No counterpart in the paper.
+ * Calls made while `stream` is being captured into a CUDA graph record the
+ * pairs as event-record nodes of the graph: each replay re-records them, so
+ * pam_timing_read after a replay returns that replay's times, and
+ * pam_timing_reset (which destroys the events) must wait until the graph is
+ * destroyed. pam_kernel_launches counts a captured launch once, at capture.
  */
 enum {
     PAM_PHASE_PREPARE = 0, PAM_PHASE_ASSEMBLE, PAM_PHASE_GRAM, PAM_PHASE_SOLVE,

@@ -69,6 +69,7 @@ bool make_geo(const pam_problem *prob, const pam_params *par, Geo *g, Par *p, pa
         if (par->k_top < 0 || par->m_max < 0 || par->levels < 0 || par->max_iters < 0) return false;
         if (par->warm_start != 0 && par->warm_start != 1) return false;
         if (par->quad != 0 && par->quad != 1) return false;
+        if (par->deferred_status != 0 && par->deferred_status != 1) return false;
         if (par->precision != PAM_PREC_FP64 && par->precision != PAM_PREC_MIXED) return false;
         int64_t add = (int64_t)par->levels * (g->dim + 1) * par->k_top;
         if (add > par->m_max) add = par->m_max;
@@ -151,19 +152,28 @@ std::mutex g_mu;
 
 void count_launches(int n) { g_launches += n; }
 
-PhaseScope::PhaseScope(int phase, cudaStream_t st) : phase_(phase), st_(st), stop_(nullptr), on_(g_timing) {
+PhaseScope::PhaseScope(int phase, cudaStream_t st)
+    : phase_(phase), st_(st), stop_(nullptr), on_(g_timing), capturing_(false) {
     if (!on_) return;
     cudaEvent_t a, b;
     cudaEventCreate(&a);
     cudaEventCreate(&b);
-    cudaEventRecord(a, st);
+    // inside a stream capture the pair becomes event-record nodes of the
+    // graph, re-recorded by every replay (read them after each replay)
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    cudaStreamIsCapturing(st, &cs);
+    capturing_ = cs == cudaStreamCaptureStatusActive;
+    if (capturing_) cudaEventRecordWithFlags(a, st, cudaEventRecordExternal);
+    else cudaEventRecord(a, st);
     stop_ = b;
     std::lock_guard<std::mutex> lk(g_mu);
     g_pairs.push_back({phase, a, b});
 }
 
 PhaseScope::~PhaseScope() {
-    if (on_) cudaEventRecord(stop_, st_);
+    if (!on_) return;
+    if (capturing_) cudaEventRecordWithFlags(stop_, st_, cudaEventRecordExternal);
+    else cudaEventRecord(stop_, st_);
 }
 
 Ws carve_workspace(const Geo &g, void *base) {
@@ -295,13 +305,16 @@ pam_status pam_fit_subdomains(const pam_problem *prob, const pam_params *par, co
     Ws w = carve_workspace(g, d_workspace);
     if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
+    const bool deferred = par->deferred_status != 0;
     PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 8 * sizeof(int32_t), s));
     launch_partition(g, model->boxes, s);
     launch_prepare(g, model->boxes, d_K, w, s);
     PAM_CUDA_TRY(cudaGetLastError());
     int32_t hs[8];
-    if ((st = read_status(w, s, hs)) != PAM_OK) return st;
-    if (hs[kStBadK]) return PAM_ERR_NONPOSITIVE_K;
+    if (!deferred) {
+        if ((st = read_status(w, s, hs)) != PAM_OK) return st;
+        if (hs[kStBadK]) return PAM_ERR_NONPOSITIVE_K;
+    }
     launch_init_dictionary(g, model->boxes, model->centres, model->beta, model->info, s,
                            par->warm_start != 0);
     if (par->precision == PAM_PREC_MIXED)
@@ -309,7 +322,20 @@ pam_status pam_fit_subdomains(const pam_problem *prob, const pam_params *par, co
     else
         launch_solve_level_f64(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
     PAM_CUDA_TRY(cudaGetLastError());
+    if (deferred) return PAM_OK;
     if ((st = read_status(w, s, hs)) != PAM_OK) return st;
+    if (hs[kStTimeout]) return PAM_ERR_TIMEOUT;
+    return hs[kStUncertified] ? PAM_ERR_NOT_CONVERGED : PAM_OK;
+}
+
+pam_status pam_status_read(const pam_plan *plan, void *d_workspace, size_t workspace_bytes, void *stream) {
+    // the status words are the workspace's first region, whatever the problem
+    if (!plan || !d_workspace || workspace_bytes < 8 * sizeof(int32_t)) return PAM_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    int32_t hs[8];
+    PAM_CUDA_TRY(cudaMemcpyAsync(hs, d_workspace, 8 * sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+    PAM_CUDA_TRY(cudaStreamSynchronize(s));
+    if (hs[kStBadK]) return PAM_ERR_NONPOSITIVE_K;
     if (hs[kStTimeout]) return PAM_ERR_TIMEOUT;
     return hs[kStUncertified] ? PAM_ERR_NOT_CONVERGED : PAM_OK;
 }
@@ -329,7 +355,9 @@ pam_status pam_refine(const pam_problem *prob, const pam_params *par, const pam_
     Ws w = carve_workspace(g, d_workspace);
     if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
     cudaStream_t s = (cudaStream_t)stream;
-    PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 8 * sizeof(int32_t), s));
+    const bool deferred = par->deferred_status != 0;
+    // deferred: the status keeps accumulating from pam_fit_subdomains
+    if (!deferred) PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 8 * sizeof(int32_t), s));
     for (int lv = 0; lv < n_levels; ++lv) {
         launch_refine_round(g, p, par->precision, model->boxes, model->centres, model->beta,
                             model->info, w, s);
@@ -339,6 +367,7 @@ pam_status pam_refine(const pam_problem *prob, const pam_params *par, const pam_
             launch_solve_level_f64(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
     }
     PAM_CUDA_TRY(cudaGetLastError());
+    if (deferred) return PAM_OK;
     int32_t hs[8];
     if ((st = read_status(w, s, hs)) != PAM_OK) return st;
     if (hs[kStTimeout]) return PAM_ERR_TIMEOUT;

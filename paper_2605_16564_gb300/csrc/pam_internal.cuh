@@ -115,6 +115,7 @@ struct PhaseScope {
     cudaStream_t st_;
     cudaEvent_t stop_;
     bool on_;
+    bool capturing_;
 };
 
 // ---------------------------------------------------------------- device ---

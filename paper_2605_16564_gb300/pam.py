@@ -28,10 +28,12 @@ FLAG_NOT_CERTIFIED, FLAG_CHOLESKY, FLAG_REFINE_DIVERGED = 1, 2, 4
 STATUS = {0: "PAM_OK", 1: "PAM_ERR_INVALID_ARG", 2: "PAM_ERR_NONPOSITIVE_K", 3: "PAM_ERR_CUDA",
           4: "PAM_ERR_WORKSPACE", 5: "PAM_ERR_NOT_CONVERGED", 6: "PAM_ERR_UNSUPPORTED",
           7: "PAM_ERR_TIMEOUT"}
+(PAM_OK, PAM_ERR_INVALID_ARG, PAM_ERR_NONPOSITIVE_K, PAM_ERR_CUDA, PAM_ERR_WORKSPACE, PAM_ERR_NOT_CONVERGED,
+ PAM_ERR_UNSUPPORTED, PAM_ERR_TIMEOUT) = range(8)
 
 EXPORTED = ["pam_version", "pam_status_string", "pam_plan_create", "pam_partition",
             "pam_fit_subdomains", "pam_refine", "pam_gram", "pam_eval_workspace_size", "pam_eval",
-            "pam_errors"]
+            "pam_errors", "pam_status_read"]
 
 
 class PamError(RuntimeError):
@@ -49,7 +51,8 @@ class pam_params(C.Structure):
     _fields_ = [("lambda1_hat", C.c_double), ("lambda2_hat", C.c_double),
                 ("eps_tol_rel", C.c_double), ("eta", C.c_double), ("k_top", C.c_int),
                 ("m_max", C.c_int), ("levels", C.c_int), ("max_iters", C.c_int),
-                ("precision", C.c_int), ("warm_start", C.c_int), ("quad", C.c_int)]
+                ("precision", C.c_int), ("warm_start", C.c_int), ("quad", C.c_int),
+                ("deferred_status", C.c_int)]
 
 
 class pam_plan(C.Structure):
@@ -83,6 +86,7 @@ def lib():
                                          P(pam_model), C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_refine.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), C.c_void_p,
                                  P(pam_model), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_status_read.argtypes = [P(pam_plan), C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_eval_workspace_size.argtypes = [P(pam_plan), C.c_int64, P(C.c_size_t)]
         L.pam_eval.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_int64,
                                C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
@@ -143,11 +147,15 @@ def make_problem(n_cells, n_sub, overlap, g_init):
 
 
 def make_params(lambda1_hat=4.59e-4, lambda2_hat=4.64e-6, eps_tol_rel=1e-3, eta=0.5, k_top=37,
-                m_max=1 << 30, levels=3, max_iters=0, precision=PAM_PREC_FP64, warm_start=0, quad=0):
-    """quad: quadrature of the indicators R_T, 0 midpoint, 1 two-point Gauss-Legendre per axis."""
+                m_max=1 << 30, levels=3, max_iters=0, precision=PAM_PREC_FP64, warm_start=0, quad=0,
+                deferred_status=0):
+    """quad: quadrature of the indicators R_T, 0 midpoint, 1 two-point Gauss-Legendre per axis.
+    deferred_status: 1 = the fit calls never synchronise the host (read the
+    status with pam_status_read), so they can be captured in a CUDA graph."""
     p = pam_params()
     p.warm_start = warm_start
     p.quad = quad
+    p.deferred_status = deferred_status
     p.lambda1_hat, p.lambda2_hat, p.eps_tol_rel, p.eta = lambda1_hat, lambda2_hat, eps_tol_rel, eta
     p.k_top, p.m_max, p.levels, p.max_iters, p.precision = k_top, min(m_max, (1 << 31) - 1), levels, \
         max_iters, precision
@@ -189,6 +197,11 @@ def pam_refine(problem, params, plan, K, model, n_levels, workspace, stream=None
     if check:
         _check(code, "pam_refine")
     return code
+
+
+def pam_status_read(plan, workspace, stream=None):
+    """Status code (0 = ok) accumulated by deferred-status fit calls."""
+    return lib().pam_status_read(C.byref(plan), _ptr(workspace), int(workspace.numel()), _stream(stream))
 
 
 def pam_gram(problem, params, plan, K, model, G, b, workspace, stream=None):
@@ -315,6 +328,12 @@ def alloc_workspace(plan, device="cuda"):
     return torch.empty(int(plan.workspace_bytes), dtype=torch.uint8, device=device)
 
 
+def error_dict(err):
+    """Host dict of the error measures in a [4] tensor written by pam_errors."""
+    e = err.cpu().numpy()
+    return dict(l1=e[0], l2=e[1], l1_log=e[2], max_log10=e[3])
+
+
 class Fitter:
     """A problem, its parameters and plan, with the device buffers they need."""
 
@@ -327,20 +346,28 @@ class Fitter:
         self.model = alloc_model(self.plan, device)
         self.workspace = alloc_workspace(self.plan, device)
 
-    def fit(self, K, levels=None, stream=None, check=True, warm_start=False):
+    def fit(self, K, levels=None, stream=None, check=True, warm_start=False, deferred=False):
         """Step 2, then `levels` rounds of Step 3 (default: the planned levels).
         warm_start: the initial dictionary starts from the coefficients
-        already in model.beta (e.g. seeded by pam_nn_seed)."""
+        already in model.beta (e.g. seeded by pam_nn_seed).
+        deferred: launch only, no host synchronisation (capturable in a CUDA
+        graph); the status is read later with status()."""
         lv = self.params.levels if levels is None else levels
         self.params.warm_start = 1 if warm_start else 0
+        self.params.deferred_status = 1 if deferred else 0
         try:
             c1 = pam_fit_subdomains(self.problem, self.params, self.plan, K, self.model, self.workspace,
                                     stream, check)
+            c2 = pam_refine(self.problem, self.params, self.plan, K, self.model, lv, self.workspace,
+                            stream, check) if lv > 0 else 0
         finally:
             self.params.warm_start = 0
-        c2 = pam_refine(self.problem, self.params, self.plan, K, self.model, lv, self.workspace,
-                        stream, check) if lv > 0 else 0
+            self.params.deferred_status = 0
         return c1 or c2
+
+    def status(self, stream=None):
+        """Status of the deferred fit calls since the last fit (synchronises)."""
+        return pam_status_read(self.plan, self.workspace, stream)
 
     def eval_workspace(self, n_pts):
         import torch
@@ -364,11 +391,16 @@ class Fitter:
         """quad: the errors' quadrature (default: the fit's indicator quadrature)."""
         import torch
         err = torch.zeros(4, dtype=torch.float64, device=K.device)
+        self.errors_device(K, err, precision, stream, quad)
+        return error_dict(err)
+
+    def errors_device(self, K, err, precision=None, stream=None, quad=None):
+        """The four error measures into the device tensor err [4] (no host
+        synchronisation; read them with error_dict)."""
         prec = self.params.precision if precision is None else precision
         q = self.params.quad if quad is None else quad
         pam_errors(self.problem, self.plan, self.model, K, err, self.workspace, prec, stream, quad=q)
-        e = err.cpu().numpy()
-        return dict(l1=e[0], l2=e[1], l1_log=e[2], max_log10=e[3])
+        return err
 
     def host_model(self):
         return self.model.to_host(self.n_cells, self.n_sub, self.plan.m_cap)

@@ -48,6 +48,17 @@ def test_partition_matches_the_oracle(pam, n_cells, n_sub, overlap):
     np.testing.assert_array_equal(pam.pam_partition(pr), oracle.partition(n_cells, n_sub, overlap))
 
 
+def test_status_read_rejects_bad_arguments(pam):
+    import ctypes as C
+    pr = pam.make_problem((8, 8), (2, 2), 1, (2, 2))
+    plan = pam.pam_plan_create(pr, pam.make_params())
+    L = pam.lib()
+    assert L.pam_status_read(None, None, 0, None) == 1
+    assert L.pam_status_read(C.byref(plan), None, 1024, None) == 1
+    buf = (C.c_int32 * 4)()
+    assert L.pam_status_read(C.byref(plan), C.cast(buf, C.c_void_p), 16, None) == 1  # < 8 words
+
+
 def test_plan_sizes(pam):
     pr = pam.make_problem((60, 220, 85), (6, 22, 17), 1, (4, 4, 2))
     plan = pam.pam_plan_create(pr, pam.make_params(k_top=30, levels=3))
@@ -73,6 +84,7 @@ def test_plan_sizes(pam):
     dict(params=dict(precision=7)),
     dict(params=dict(quad=2)),
     dict(params=dict(warm_start=3)),
+    dict(params=dict(deferred_status=2)),
 ])
 def test_invalid_arguments_are_rejected(pam, bad):
     base = dict(n_cells=(8, 8), n_sub=(2, 2), overlap=1, g_init=(2, 2))
