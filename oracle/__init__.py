@@ -8,7 +8,8 @@ share no code.
 The arithmetic lives in ``pam_oracle.c`` (plain C, binary64, no fused
 multiply-add); this module compiles it with gcc on first use and wraps each
 function with numpy marshalling. Which paper passage each function follows is
-stated beside it in the C source.
+stated beside it in the C source. ``cv_lambda`` composes those primitives in
+a plain Python loop (its residual dot products in numpy).
 """
 from __future__ import annotations
 
@@ -301,3 +302,55 @@ def residual_gl(x, c, beta, kv, vol, h, dim):
     R = np.zeros(n)
     lib().orc_residual_gl(dim, n, x, m, _f64(c), _f64(beta), _f64(kv), float(vol), float(h), R)
     return R
+
+
+# --------------------------------------------------------------------------
+# Per-subdomain choice of the Elastic Net weights (section 5, Experiment 1.2:
+# lambda is chosen independently on each subdomain; the rule is not stated).
+# Reading: k-fold cross-validation over a caller-given grid of
+# (lambda1_hat, lambda2_hat) pairs on the subdomain's final dictionary.
+# --------------------------------------------------------------------------
+
+def cv_lambda(model, K, grid, n_folds, which=None):
+    """For each subdomain: cell t of the patch (local row-major index) is in
+    fold t mod n_folds; for every grid pair and fold the Elastic Net (Eq. (2),
+    lambda_k = N_train lambda_k_hat) is solved on the other folds' cells and
+    its squared log-residuals y_t - (W beta)_t on the held-out cells summed;
+    cv = that sum over all folds / N. choice = first grid index of least cv;
+    the coefficients are then refit on all N cells with the chosen pair.
+
+    Returns dict(cv [S, n_grid], choice [S], beta [S, m_cap], certified [S]).
+    Subdomains not in ``which`` are skipped (cv NaN, choice -1).
+    """
+    n_cells = tuple(model["n_cells"])
+    dim = len(n_cells)
+    boxes = model["boxes"]
+    S, mc = boxes.shape[0], int(model["m_cap"])
+    grid = np.asarray(grid, dtype=np.float64).reshape(-1, 2)
+    cv = np.full((S, grid.shape[0]), np.nan)
+    choice = np.full(S, -1, dtype=np.int32)
+    beta = np.zeros((S, mc))
+    certified = np.zeros(S, dtype=bool)
+    for s in (range(S) if which is None else which):
+        x, y, _ = box_cells(n_cells, boxes[s, 6:9], boxes[s, 9:12], K)
+        M = int(model["M"][s])
+        W = assemble(dim, x, model["c"][s, :M])
+        N = y.shape[0]
+        fold = np.arange(N) % n_folds
+        for gi, (l1h, l2h) in enumerate(grid):
+            total = 0.0
+            for f in range(n_folds):
+                train = fold != f
+                n_tr = int(train.sum())
+                G, b = gram(W[train], y[train])
+                bf, _ = enet(G, b, n_tr * l1h, n_tr * l2h)
+                r = y[~train] - W[~train] @ bf
+                total += float(r @ r)
+            cv[s, gi] = total / N
+        choice[s] = int(np.argmin(cv[s]))
+        l1h, l2h = grid[choice[s]]
+        G, b = gram(W, y)
+        bs, inf = enet(G, b, N * l1h, N * l2h)
+        beta[s, :M] = bs
+        certified[s] = inf["certified"]
+    return dict(cv=cv, choice=choice, beta=beta, certified=certified)
