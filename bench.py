@@ -540,6 +540,45 @@ def run_pam(args, rank, ws):
                  "l1_ratio_chosen_over_plain": err["l1"] / perr["l1"]}
         del pf
 
+    # --- per-subdomain lambda choice by k-fold cross-validation (binary64) ---
+    lcv = None
+    if args.lambda_cv:
+        grid = [(W["params"].get("lambda1_hat", 4.59e-4) * f, W["params"].get("lambda2_hat", 4.64e-6) * f)
+                for f in (0.25, 1.0, 4.0)]
+        folds = 3
+        cf = pam.Fitter(shape, W["n_sub"], W["overlap"], W["g"], device=dev, precision=pam.PAM_PREC_FP64,
+                        **W["params"])
+        cf.fit(Kd, check=False)
+        beta0 = cf.model.beta.clone()
+        info0 = cf.model.info.clone()
+        L.pam_timing_reset()
+        cv_times = []
+        for i in range(1 + args.steps):
+            cf.model.beta.copy_(beta0)
+            cf.model.info.copy_(info0)
+            flush.fill_(1)
+            if i == 1:
+                L.pam_timing_enable(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            cv, choice, code = cf.lambda_cv(Kd, grid, folds)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= 1:
+                cv_times.append(e0.elapsed_time(e1))
+        L.pam_timing_enable(0)
+        ph = {k: round(v[0] / args.steps, 3) for k, v in read_phases().items()}
+        L.pam_timing_reset()
+        ms = sum(cv_times) / len(cv_times)
+        S = cf.plan.n_subdomains
+        hist = np.bincount(choice.cpu().numpy(), minlength=len(grid)).tolist()
+        lcv = {"ms": round(ms, 3), "grid": [list(map(float, g)) for g in grid], "folds": folds,
+               "solves": S * (len(grid) * folds + 1), "solves_per_s": S * (len(grid) * folds + 1) / (ms / 1e3),
+               "cells_per_s": n_cells / (ms / 1e3), "status": int(code), "choice_histogram": hist,
+               "phase_ms": ph}
+        del cf, beta0, info0
+
     # --- roofline of every kernel family, the dominant one first ------------
     peaks, peak_src = _peaks()
     work = accounting(fit, Kd, W["params"]["levels"], pam, seed=(lambda: lw.seed(fit, Kd)) if lw else None)
@@ -554,7 +593,7 @@ def run_pam(args, rank, ws):
     return dict(value=value, step_ms=step_ms, times=times, err=err, phase_ms=phase_ms, launches=launches,
                 clocks=clk.summary(), e2e_s=e2e_s, h2d=h2d, d2h=d2h, plain=plain, roof=roof, roofs=roofs,
                 prec_name=prec_name, n_cells=n_cells, n_pts=n_pts, info=info, learned=learned, mode=mode,
-                e2e_mode=e2e_mode)
+                e2e_mode=e2e_mode, lambda_cv=lcv)
 
 
 def owner_counts(W, pts):
@@ -629,6 +668,8 @@ def main():
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="3-D mixed form without the learned warm start")
+    ap.add_argument("--lambda-cv", action="store_true",
+                    help="also time the per-subdomain 3-fold cross-validation of 3 lambda pairs (binary64)")
     ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of a CUDA graph replay")
     ap.add_argument("--quad", type=int, default=0, choices=[0, 1],
                     help="indicator and error quadrature: 0 midpoint, 1 two-point Gauss-Legendre per axis")
@@ -705,6 +746,8 @@ def main():
         "plain_fp64": r["plain"],
         "learned_warm_start": r["learned"],
     }
+    if r["lambda_cv"] is not None:
+        line["lambda_cv"] = r["lambda_cv"]
     fit_ms = sum(v[0] for k, v in r["phase_ms"].items() if k not in ("eval", "errors"))
     line["fit_cells_per_s"] = r["n_cells"] * ws / (fit_ms / 1e3) if fit_ms else None
     print(json.dumps(line))

@@ -186,6 +186,36 @@ pam_status pam_fit_subdomains(const pam_problem *prob, const pam_params *par,
                               size_t workspace_bytes, void *stream);
 
 /*
+ * Per-subdomain choice of the Elastic Net weights by k-fold cross-validation
+ * (section 5, Experiment 1.2 chooses (lambda1, lambda2) on each subdomain
+ * independently without stating the rule; this is the rule here). On the
+ * model's current dictionary (after pam_fit_subdomains / pam_refine), cell t
+ * of each patch (local row-major index, x fastest) is in fold t mod n_folds.
+ * For every grid pair q and fold f the Elastic Net of Eq. (2) is solved on the
+ * other folds' cells with lambda_k = N_train h_grid[q][k] and the squared
+ * log-residuals (ln K_t - ln K*(x_t))^2 of the held-out cells summed;
+ * d_cv[s][q] = that sum over the folds / N_i. d_choice[s] = the first q of
+ * least d_cv[s][q]; model->beta and the support, iteration and flag entries
+ * of model->info are then refit on all N_i cells with that pair (the
+ * dictionary is kept).
+ *   h_grid        host [n_grid][2] (lambda1_hat >= 0, lambda2_hat > 0), 1 <= n_grid <= 32
+ *   n_folds       2 ... 1024 (a fold with no cell contributes nothing)
+ *   d_cv          device [S][n_grid] binary64, written; d_choice device [S] int32, written
+ *   d_workspace   the fit workspace of `plan`; d_cv_workspace: pam_lambda_cv_workspace_size bytes
+ * The binary64 form only: par->precision must be PAM_PREC_FP64 (else
+ * PAM_ERR_UNSUPPORTED), with the plan made from the same problem and
+ * parameters. Synchronises once (unless par->deferred_status) and returns
+ * PAM_ERR_NONPOSITIVE_K, PAM_ERR_NOT_CONVERGED (some solve not certified) or
+ * PAM_OK.
+ */
+pam_status pam_lambda_cv_workspace_size(const pam_plan *plan, size_t *bytes);
+pam_status pam_lambda_cv(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                         const double *d_K, pam_model *model, const double *h_grid, int n_grid,
+                         int n_folds, double *d_cv, int32_t *d_choice, void *d_workspace,
+                         size_t workspace_bytes, void *d_cv_workspace, size_t cv_workspace_bytes,
+                         void *stream);
+
+/*
  * Status of the pam_fit_subdomains / pam_refine calls made with
  * deferred_status = 1 on this workspace since the last pam_fit_subdomains:
  * synchronises `stream` and returns PAM_ERR_NONPOSITIVE_K (some K_T <= 0,

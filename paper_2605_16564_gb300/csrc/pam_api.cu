@@ -6,6 +6,8 @@
 #include <mutex>
 #include <vector>
 
+#include <cfloat>
+
 #include "pam_internal.cuh"
 
 namespace pam {
@@ -96,6 +98,8 @@ bool make_geo(const pam_problem *prob, const pam_params *par, Geo *g, Par *p, pa
             p->levels = par->levels;
             p->max_iters = par->max_iters > 0 ? par->max_iters : 200;
             p->quad = par->quad;
+            p->cv_folds = 0;
+            p->cv_fold = 0;
         }
     }
     *st = PAM_OK;
@@ -324,6 +328,54 @@ pam_status pam_fit_subdomains(const pam_problem *prob, const pam_params *par, co
     PAM_CUDA_TRY(cudaGetLastError());
     if (deferred) return PAM_OK;
     if ((st = read_status(w, s, hs)) != PAM_OK) return st;
+    if (hs[kStTimeout]) return PAM_ERR_TIMEOUT;
+    return hs[kStUncertified] ? PAM_ERR_NOT_CONVERGED : PAM_OK;
+}
+
+pam_status pam_lambda_cv_workspace_size(const pam_plan *plan, size_t *bytes) {
+    if (!plan || !bytes || plan->n_subdomains <= 0 || plan->m_cap <= 0) return PAM_ERR_INVALID_ARG;
+    Geo g{};
+    g.S = plan->n_subdomains;
+    g.m_cap = plan->m_cap;
+    *bytes = cv_workspace_bytes(g);
+    return PAM_OK;
+}
+
+pam_status pam_lambda_cv(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                         const double *d_K, pam_model *model, const double *h_grid, int n_grid,
+                         int n_folds, double *d_cv, int32_t *d_choice, void *d_workspace,
+                         size_t workspace_bytes, void *d_cv_workspace, size_t cv_workspace_bytes_,
+                         void *stream) {
+    Geo g;
+    Par p;
+    pam_status st;
+    if (!par || !make_geo(prob, par, &g, &p, &st)) return par ? st : PAM_ERR_INVALID_ARG;
+    if ((st = check_plan(g, plan)) != PAM_OK) return st;
+    g.m_cap = plan->m_cap;
+    if (par->precision != PAM_PREC_FP64) return PAM_ERR_UNSUPPORTED;
+    if (!d_K || !model_ok(model) || !d_workspace || !h_grid || !d_cv || !d_choice || !d_cv_workspace)
+        return PAM_ERR_INVALID_ARG;
+    if (n_grid < 1 || n_grid > kCvMaxGrid || n_folds < 2 || n_folds > 1024) return PAM_ERR_INVALID_ARG;
+    CvGrid grid{};
+    grid.n = n_grid;
+    for (int q = 0; q < n_grid; ++q) {
+        const double l1 = h_grid[2 * q], l2 = h_grid[2 * q + 1];
+        if (!(l1 >= 0.0 && l1 <= DBL_MAX) || !(l2 > 0.0 && l2 <= DBL_MAX)) return PAM_ERR_INVALID_ARG;
+        grid.lam[q][0] = l1;
+        grid.lam[q][1] = l2;
+    }
+    Ws w = carve_workspace(g, d_workspace);
+    if (workspace_bytes < w.bytes || cv_workspace_bytes_ < cv_workspace_bytes(g)) return PAM_ERR_WORKSPACE;
+    cudaStream_t s = (cudaStream_t)stream;
+    PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 8 * sizeof(int32_t), s));
+    launch_prepare(g, model->boxes, d_K, w, s);
+    launch_lambda_cv(g, p, model->boxes, model->centres, model->beta, model->info, w, grid, n_folds, d_cv,
+                     d_choice, d_cv_workspace, s);
+    PAM_CUDA_TRY(cudaGetLastError());
+    if (par->deferred_status) return PAM_OK;
+    int32_t hs[8];
+    if ((st = read_status(w, s, hs)) != PAM_OK) return st;
+    if (hs[kStBadK]) return PAM_ERR_NONPOSITIVE_K;
     if (hs[kStTimeout]) return PAM_ERR_TIMEOUT;
     return hs[kStUncertified] ? PAM_ERR_NOT_CONVERGED : PAM_OK;
 }

@@ -180,8 +180,14 @@ __global__ void __launch_bounds__(128) k_assemble_f64(Geo g, const int32_t *boxe
     w.inv_s[(size_t)s * g.n_max + t] = 1.0 / sum;
 }
 
+// Row mask of the cross-validation folds: with folds > 0 only the cells t
+// with t mod folds != fold enter G and b (the training rows of that fold).
+__device__ __forceinline__ bool cv_keep(int t, int folds, int fold) {
+    return folds == 0 || t % folds != fold;
+}
+
 // b_m = sum_j W_jm y_j, one warp per (subdomain, centre).
-__global__ void k_bvec_f64(Geo g, const int32_t *info, Ws w, int all) {
+__global__ void k_bvec_f64(Geo g, const int32_t *info, Ws w, int all, int folds, int fold) {
     int s = blockIdx.y;
     const int32_t *inf = info + s * kInfoN;
     if (!all && inf[PAM_INFO_STOPPED]) return;
@@ -193,14 +199,16 @@ __global__ void k_bvec_f64(Geo g, const int32_t *info, Ws w, int all) {
     const double *iv = w.inv_s + (size_t)s * g.n_max;
     const double *y = w.y + (size_t)s * g.n_max;
     double acc = 0.0;
-    for (int t = lane; t < N; t += 32) acc += E[t] * iv[t] * y[t];
+    for (int t = lane; t < N; t += 32)
+        if (cv_keep(t, folds, fold)) acc += E[t] * iv[t] * y[t];
     acc = warp_sum(acc);
     if (lane == 0) w.b[(size_t)s * g.m_cap + m] = acc;
 }
 
 // G = W^T W on 64 x 64 tiles of the upper triangle, mirrored; fp64 FMA.
 constexpr int kGT = 64, kGK = 16;
-__global__ void __launch_bounds__(256) k_gram_f64(Geo g, const int32_t *info, Ws w, int all) {
+__global__ void __launch_bounds__(256) k_gram_f64(Geo g, const int32_t *info, Ws w, int all, int folds,
+                                                  int fold) {
     int s = blockIdx.y;
     const int32_t *inf = info + s * kInfoN;
     if (!all && inf[PAM_INFO_STOPPED]) return;
@@ -219,7 +227,7 @@ __global__ void __launch_bounds__(256) k_gram_f64(Geo g, const int32_t *info, Ws
     for (int t0 = 0; t0 < N; t0 += kGK) {
         for (int e = tid; e < kGT * kGK; e += 256) {
             int row = e / kGK, kk = e % kGK, t = t0 + kk;
-            double sc = t < N ? iv[t] : 0.0;
+            double sc = (t < N && cv_keep(t, folds, fold)) ? iv[t] : 0.0;
             double a = (t < N && I0 + row < M) ? E[(size_t)(I0 + row) * g.n_max + t] * sc : 0.0;
             double b = (t < N && J0 + row < M) ? E[(size_t)(J0 + row) * g.n_max + t] * sc : 0.0;
             As[kk][row] = a;
@@ -335,13 +343,21 @@ __device__ void cholesky_solve_packed(const double *A, int s, double *r) {
     __syncthreads();
 }
 
+// lam_tab (optional): per-subdomain (lambda1_hat, lambda2_hat) pairs in place
+// of p's; all: solve also the subdomains whose refinement has stopped. With
+// p.cv_folds > 0 the system is that of the training rows of fold p.cv_fold
+// and lambda_k = N_train lambda_k_hat.
 __global__ void __launch_bounds__(kSolveThreads) k_solve_f64(Geo g, Par p, double *beta,
-                                                             int32_t *info, Ws w) {
+                                                             int32_t *info, Ws w, const double *lam_tab,
+                                                             int all) {
     const int s = blockIdx.x;
     int32_t *inf = info + s * kInfoN;
-    if (inf[PAM_INFO_STOPPED]) return;
+    if (!all && inf[PAM_INFO_STOPPED]) return;
     const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS], mc = g.m_cap;
-    const double lam1 = (double)N * p.lam1_hat, lam2 = (double)N * p.lam2_hat;
+    const int n_out = (p.cv_folds > 0 && N > p.cv_fold) ? (N - 1 - p.cv_fold) / p.cv_folds + 1 : 0;
+    const double n_fit = (double)(N - n_out);
+    const double l1h = lam_tab ? lam_tab[2 * s] : p.lam1_hat, l2h = lam_tab ? lam_tab[2 * s + 1] : p.lam2_hat;
+    const double lam1 = n_fit * l1h, lam2 = n_fit * l2h;
     const double viol_tol = lam1 * (1.0 + 1e-9);
     extern __shared__ double sm[];
     double *x = sm;          // [mc] full coefficient vector of the current iterate
@@ -489,6 +505,21 @@ static size_t solve_smem_bytes(int mc) {
     return (size_t)mc * (4 * sizeof(double) + 2 * sizeof(int)) + kFactorSmemBytes;
 }
 
+void launch_bgram_f64(const Geo &g, const int32_t *info, const Ws &w, cudaStream_t st, int all, int folds,
+                      int fold) {
+    {
+        PhaseScope ps(kPhAssemble, st);
+        dim3 gb((g.m_cap + 7) / 8, g.S);
+        k_bvec_f64<<<gb, 256, 0, st>>>(g, info, w, all, folds, fold);
+        count_launches(1);
+    }
+    PhaseScope ps(kPhGram, st);
+    int T = g.m_cap / kGT;
+    dim3 gg(T * (T + 1) / 2, g.S);
+    k_gram_f64<<<gg, 256, 0, st>>>(g, info, w, all, folds, fold);
+    count_launches(1);
+}
+
 void launch_assemble_gram_f64(const Geo &g, const int32_t *boxes, const double *centres,
                               const int32_t *info, const Ws &w, cudaStream_t st, int all) {
     size_t asm_smem = (size_t)g.m_cap * sizeof(dvec4);
@@ -498,28 +529,24 @@ void launch_assemble_gram_f64(const Geo &g, const int32_t *boxes, const double *
         dim3 ga((g.n_max + 127) / 128, g.S);
         k_assemble_f64<<<ga, 128, asm_smem, st>>>(g, boxes, centres, info, w, all);
         count_launches(1);
-        dim3 gb((g.m_cap + 7) / 8, g.S);
-        k_bvec_f64<<<gb, 256, 0, st>>>(g, info, w, all);
-        count_launches(1);
     }
-    {
-        PhaseScope ps(kPhGram, st);
-        int T = g.m_cap / kGT;
-        dim3 gg(T * (T + 1) / 2, g.S);
-        k_gram_f64<<<gg, 256, 0, st>>>(g, info, w, all);
-        count_launches(1);
-    }
+    launch_bgram_f64(g, info, w, st, all, 0, 0);
+}
+
+void launch_solve_f64(const Geo &g, const Par &p, double *beta, int32_t *info, const Ws &w,
+                      const double *lam_tab, int all, cudaStream_t st) {
+    size_t ss = solve_smem_bytes(g.m_cap);
+    cudaFuncSetAttribute(k_solve_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    PhaseScope ps(kPhSolve, st);
+    k_solve_f64<<<g.S, kSolveThreads, ss, st>>>(g, p, beta, info, w, lam_tab, all);
+    count_launches(1);
 }
 
 void launch_solve_level_f64(const Geo &g, const Par &p, const int32_t *boxes,
                             const double *centres, double *beta, int32_t *info, const Ws &w,
                             cudaStream_t st) {
     launch_assemble_gram_f64(g, boxes, centres, info, w, st, 0);
-    size_t ss = solve_smem_bytes(g.m_cap);
-    cudaFuncSetAttribute(k_solve_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
-    PhaseScope ps(kPhSolve, st);
-    k_solve_f64<<<g.S, kSolveThreads, ss, st>>>(g, p, beta, info, w);
-    count_launches(1);
+    launch_solve_f64(g, p, beta, info, w, nullptr, 0, st);
 }
 
 __global__ void k_copy_gram_f64(Geo g, const int32_t *info, const double *G, const double *b,

@@ -35,6 +35,7 @@ struct Par {
     double lam1_hat, lam2_hat, eps_tol_rel, eta;
     int k_top, m_max, levels, max_iters;
     int quad;  // 0 midpoint, 1 Gauss-Legendre indicators
+    int cv_folds, cv_fold;  // cross-validation fold of a solve (0: all rows)
 };
 
 // Workspace carve-up. Every region is 256-byte aligned.
@@ -78,6 +79,10 @@ void launch_stats_gram_tc(const Geo &g, const int32_t *boxes, const double *cent
                           const int32_t *info, const Ws &w, cudaStream_t st, int all);
 void launch_assemble_gram_f64(const Geo &g, const int32_t *boxes, const double *centres,
                               const int32_t *info, const Ws &w, cudaStream_t st, int all);
+void launch_bgram_f64(const Geo &g, const int32_t *info, const Ws &w, cudaStream_t st, int all, int folds,
+                      int fold);
+void launch_solve_f64(const Geo &g, const Par &p, double *beta, int32_t *info, const Ws &w,
+                      const double *lam_tab, int all, cudaStream_t st);
 void launch_copy_gram_f32(const Geo &g, const int32_t *info, const Ws &w, double *G_out,
                           double *b_out, cudaStream_t st);
 void launch_copy_gram_f64(const Geo &g, const int32_t *info, const Ws &w, double *G_out,
@@ -96,6 +101,17 @@ void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, co
 void launch_residual_quad(const Geo &g, int precision, const int32_t *boxes, const double *centres,
                           const double *beta, const int32_t *info, const Ws &w, cudaStream_t st);
 bool mixed_solve_fits(const Geo &g);
+
+// Grid of (lambda1_hat, lambda2_hat) pairs of the cross-validation (by value).
+constexpr int kCvMaxGrid = 32;
+struct CvGrid {
+    int n;
+    double lam[kCvMaxGrid][2];
+};
+size_t cv_workspace_bytes(const Geo &g);
+void launch_lambda_cv(const Geo &g, const Par &p, const int32_t *boxes, const double *centres, double *beta,
+                      int32_t *info, const Ws &w, const CvGrid &grid, int folds, double *cv, int32_t *choice,
+                      void *cv_ws, cudaStream_t st);
 
 // Kernel families timed by the optional event profiler (pam_timing_*).
 enum Phase {

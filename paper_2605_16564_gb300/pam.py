@@ -33,7 +33,7 @@ STATUS = {0: "PAM_OK", 1: "PAM_ERR_INVALID_ARG", 2: "PAM_ERR_NONPOSITIVE_K", 3: 
 
 EXPORTED = ["pam_version", "pam_status_string", "pam_plan_create", "pam_partition",
             "pam_fit_subdomains", "pam_refine", "pam_gram", "pam_eval_workspace_size", "pam_eval",
-            "pam_errors", "pam_status_read"]
+            "pam_errors", "pam_status_read", "pam_lambda_cv_workspace_size", "pam_lambda_cv"]
 
 
 class PamError(RuntimeError):
@@ -87,6 +87,10 @@ def lib():
         L.pam_refine.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), C.c_void_p,
                                  P(pam_model), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_status_read.argtypes = [P(pam_plan), C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_lambda_cv_workspace_size.argtypes = [P(pam_plan), P(C.c_size_t)]
+        L.pam_lambda_cv.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), C.c_void_p, P(pam_model),
+                                    C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p,
+                                    C.c_size_t, C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_eval_workspace_size.argtypes = [P(pam_plan), C.c_int64, P(C.c_size_t)]
         L.pam_eval.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_int64,
                                C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
@@ -202,6 +206,26 @@ def pam_refine(problem, params, plan, K, model, n_levels, workspace, stream=None
 def pam_status_read(plan, workspace, stream=None):
     """Status code (0 = ok) accumulated by deferred-status fit calls."""
     return lib().pam_status_read(C.byref(plan), _ptr(workspace), int(workspace.numel()), _stream(stream))
+
+
+def pam_lambda_cv_workspace_size(plan):
+    n = C.c_size_t(0)
+    _check(lib().pam_lambda_cv_workspace_size(C.byref(plan), C.byref(n)), "pam_lambda_cv_workspace_size")
+    return int(n.value)
+
+
+def pam_lambda_cv(problem, params, plan, K, model, grid, n_folds, cv, choice, workspace, cv_workspace,
+                  stream=None, check=True):
+    """k-fold cross-validation of the grid of (lambda1_hat, lambda2_hat)
+    pairs on every subdomain, then the refit with the chosen pair."""
+    g = np.ascontiguousarray(np.asarray(grid, dtype=np.float64).reshape(-1, 2))
+    code = lib().pam_lambda_cv(C.byref(problem), C.byref(params), C.byref(plan), _ptr(K),
+                               C.byref(model.c_struct()), g.ctypes.data, int(g.shape[0]), int(n_folds),
+                               _ptr(cv), _ptr(choice), _ptr(workspace), int(workspace.numel()),
+                               _ptr(cv_workspace), int(cv_workspace.numel()), _stream(stream))
+    if check and code not in (0, 5):
+        _check(code, "pam_lambda_cv")
+    return code
 
 
 def pam_gram(problem, params, plan, K, model, G, b, workspace, stream=None):
@@ -364,6 +388,24 @@ class Fitter:
             self.params.warm_start = 0
             self.params.deferred_status = 0
         return c1 or c2
+
+    def lambda_cv(self, K, grid, n_folds, stream=None, check=True):
+        """Per-subdomain k-fold cross-validation of the grid pairs on the
+        current dictionary and refit with the chosen pair (binary64 form).
+        Returns (cv [S, n_grid] device, choice [S] device, status code)."""
+        import torch
+        S = self.plan.n_subdomains
+        n_grid = int(np.asarray(grid).reshape(-1, 2).shape[0])
+        cv = torch.empty((S, n_grid), dtype=torch.float64, device=self.device)
+        choice = torch.empty(S, dtype=torch.int32, device=self.device)
+        need = pam_lambda_cv_workspace_size(self.plan)
+        ws = getattr(self, "_cv_ws", None)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=self.device)
+            self._cv_ws = ws
+        code = pam_lambda_cv(self.problem, self.params, self.plan, K, self.model, grid, n_folds, cv, choice,
+                             self.workspace, ws, stream, check)
+        return cv, choice, code
 
     def status(self, stream=None):
         """Status of the deferred fit calls since the last fit (synchronises)."""

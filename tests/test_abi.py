@@ -59,6 +59,27 @@ def test_status_read_rejects_bad_arguments(pam):
     assert L.pam_status_read(C.byref(plan), C.cast(buf, C.c_void_p), 16, None) == 1  # < 8 words
 
 
+def test_lambda_cv_rejects_bad_arguments(pam):
+    import ctypes as C
+    pr = pam.make_problem((16, 16), (2, 2), 1, (2, 2))
+    fake = C.c_void_p(256)  # never dereferenced: validation fails first
+    for prec, grid, folds, want in [(pam.PAM_PREC_MIXED, [(1e-4, 1e-6)], 3, 6),   # binary64 form only
+                                    (pam.PAM_PREC_FP64, [(1e-4, 0.0)], 3, 1),    # lambda2_hat > 0
+                                    (pam.PAM_PREC_FP64, [(-1e-4, 1e-6)], 3, 1),  # lambda1_hat >= 0
+                                    (pam.PAM_PREC_FP64, [(1e-4, 1e-6)], 1, 1),   # at least two folds
+                                    (pam.PAM_PREC_FP64, [(1e-4, 1e-6)] * 33, 3, 1)]:  # at most 32 pairs
+        par = pam.make_params(precision=prec)
+        plan = pam.pam_plan_create(pr, par)
+        m = pam.pam_model(fake, fake, fake, fake)
+        g = np.ascontiguousarray(np.asarray(grid, dtype=np.float64))
+        code = pam.lib().pam_lambda_cv(C.byref(pr), C.byref(par), C.byref(plan), fake, C.byref(m),
+                                       g.ctypes.data, len(grid), folds, fake, fake, fake, 1 << 40, fake,
+                                       1 << 40, None)
+        assert code == want, (prec, grid[:1], folds, code)
+    n = C.c_size_t(0)
+    assert pam.lib().pam_lambda_cv_workspace_size(C.byref(plan), C.byref(n)) == 0 and n.value > 0
+
+
 def test_plan_sizes(pam):
     pr = pam.make_problem((60, 220, 85), (6, 22, 17), 1, (4, 4, 2))
     plan = pam.pam_plan_create(pr, pam.make_params(k_top=30, levels=3))
