@@ -540,44 +540,62 @@ def run_pam(args, rank, ws):
                  "l1_ratio_chosen_over_plain": err["l1"] / perr["l1"]}
         del pf
 
-    # --- per-subdomain lambda choice by k-fold cross-validation (binary64) ---
+    # --- per-subdomain lambda choice by k-fold cross-validation -------------
     lcv = None
     if args.lambda_cv:
         grid = [(W["params"].get("lambda1_hat", 4.59e-4) * f, W["params"].get("lambda2_hat", 4.64e-6) * f)
                 for f in (0.25, 1.0, 4.0)]
         folds = 3
-        cf = pam.Fitter(shape, W["n_sub"], W["overlap"], W["g"], device=dev, precision=pam.PAM_PREC_FP64,
-                        **W["params"])
-        cf.fit(Kd, check=False)
-        beta0 = cf.model.beta.clone()
-        info0 = cf.model.info.clone()
-        L.pam_timing_reset()
-        cv_times = []
-        for i in range(1 + args.steps):
-            cf.model.beta.copy_(beta0)
-            cf.model.info.copy_(info0)
-            flush.fill_(1)
-            if i == 1:
-                L.pam_timing_enable(1)
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            cv, choice, code = cf.lambda_cv(Kd, grid, folds)
-            e1.record(stream)
-            torch.cuda.synchronize()
-            if i >= 1:
-                cv_times.append(e0.elapsed_time(e1))
-        L.pam_timing_enable(0)
-        ph = {k: round(v[0] / args.steps, 3) for k, v in read_phases().items()}
-        L.pam_timing_reset()
-        ms = sum(cv_times) / len(cv_times)
-        S = cf.plan.n_subdomains
-        hist = np.bincount(choice.cpu().numpy(), minlength=len(grid)).tolist()
-        lcv = {"ms": round(ms, 3), "grid": [list(map(float, g)) for g in grid], "folds": folds,
-               "solves": S * (len(grid) * folds + 1), "solves_per_s": S * (len(grid) * folds + 1) / (ms / 1e3),
-               "cells_per_s": n_cells / (ms / 1e3), "status": int(code), "choice_histogram": hist,
-               "phase_ms": ph}
-        del cf, beta0, info0
+        lcv = {"grid": [list(map(float, g)) for g in grid], "folds": folds}
+        forms = [("mixed", pam.PAM_PREC_MIXED)] if prec == pam.PAM_PREC_MIXED else []
+        forms.append(("fp64", pam.PAM_PREC_FP64))
+        first = None
+        for name, pr in forms:
+            cf = pam.Fitter(shape, W["n_sub"], W["overlap"], W["g"], device=dev, precision=pr, **W["params"])
+            if first is None:
+                cf.fit(Kd, check=False)
+                first = [t.clone() for t in (cf.model.boxes, cf.model.centres, cf.model.beta, cf.model.info)]
+            else:  # the same dictionary as the first form's fit
+                for dst, src in zip((cf.model.boxes, cf.model.centres, cf.model.beta, cf.model.info), first):
+                    dst.copy_(src)
+            beta0 = cf.model.beta.clone()
+            info0 = cf.model.info.clone()
+            L.pam_timing_reset()
+            cv_times = []
+            for i in range(1 + args.steps):
+                cf.model.beta.copy_(beta0)
+                cf.model.info.copy_(info0)
+                flush.fill_(1)
+                if i == 1:
+                    L.pam_timing_enable(1)
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                cv, choice, code = cf.lambda_cv(Kd, grid, folds)
+                e1.record(stream)
+                torch.cuda.synchronize()
+                if i >= 1:
+                    cv_times.append(e0.elapsed_time(e1))
+            L.pam_timing_enable(0)
+            ph = {k: round(v[0] / args.steps, 3) for k, v in read_phases().items()}
+            L.pam_timing_reset()
+            ms = sum(cv_times) / len(cv_times)
+            S = cf.plan.n_subdomains
+            n_unc = int(((cf.model.info.cpu().numpy()[:, pam.INFO_FLAGS] & pam.FLAG_NOT_CERTIFIED) != 0).sum())
+            lcv[name] = {"ms": round(ms, 3), "solves": S * (len(grid) * folds + 1),
+                         "solves_per_s": S * (len(grid) * folds + 1) / (ms / 1e3),
+                         "cells_per_s": n_cells / (ms / 1e3), "status": int(code),
+                         "refit_not_certified": n_unc,
+                         "choice_histogram": np.bincount(choice.cpu().numpy(), minlength=len(grid)).tolist(),
+                         "phase_ms": ph}
+            if name == "mixed":
+                cv_m = cv.cpu().numpy()
+            else:
+                cv_d = cv.cpu().numpy()
+                if "mixed" in lcv:
+                    lcv["mixed_vs_fp64_cv_max_rel"] = float(np.max(np.abs(cv_m - cv_d) / cv_d))
+            del cf, beta0, info0
+        del first
 
     # --- roofline of every kernel family, the dominant one first ------------
     peaks, peak_src = _peaks()

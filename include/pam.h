@@ -202,9 +202,11 @@ pam_status pam_fit_subdomains(const pam_problem *prob, const pam_params *par,
  *   n_folds       2 ... 1024 (a fold with no cell contributes nothing)
  *   d_cv          device [S][n_grid] binary64, written; d_choice device [S] int32, written
  *   d_workspace   the fit workspace of `plan`; d_cv_workspace: pam_lambda_cv_workspace_size bytes
- * The binary64 form only: par->precision must be PAM_PREC_FP64 (else
- * PAM_ERR_UNSUPPORTED), with the plan made from the same problem and
- * parameters. Synchronises once (unless par->deferred_status) and returns
+ * par->precision selects the form (the plan made from the same problem and
+ * parameters): PAM_PREC_FP64, binary64 Gram and solves; PAM_PREC_MIXED, the
+ * tensor-core Gram of the training rows and the mixed solve, whose exact
+ * pass also gives the held-out residuals (PAM_ERR_UNSUPPORTED where the mixed
+ * fit is). Synchronises once (unless par->deferred_status) and returns
  * PAM_ERR_NONPOSITIVE_K, PAM_ERR_NOT_CONVERGED (some solve not certified) or
  * PAM_OK.
  */

@@ -352,7 +352,8 @@ pam_status pam_lambda_cv(const pam_problem *prob, const pam_params *par, const p
     if (!par || !make_geo(prob, par, &g, &p, &st)) return par ? st : PAM_ERR_INVALID_ARG;
     if ((st = check_plan(g, plan)) != PAM_OK) return st;
     g.m_cap = plan->m_cap;
-    if (par->precision != PAM_PREC_FP64) return PAM_ERR_UNSUPPORTED;
+    if (par->precision == PAM_PREC_MIXED && (g.m_cap > kMixedMaxM || !mixed_solve_fits(g)))
+        return PAM_ERR_UNSUPPORTED;
     if (!d_K || !model_ok(model) || !d_workspace || !h_grid || !d_cv || !d_choice || !d_cv_workspace)
         return PAM_ERR_INVALID_ARG;
     if (n_grid < 1 || n_grid > kCvMaxGrid || n_folds < 2 || n_folds > 1024) return PAM_ERR_INVALID_ARG;
@@ -369,8 +370,8 @@ pam_status pam_lambda_cv(const pam_problem *prob, const pam_params *par, const p
     cudaStream_t s = (cudaStream_t)stream;
     PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 8 * sizeof(int32_t), s));
     launch_prepare(g, model->boxes, d_K, w, s);
-    launch_lambda_cv(g, p, model->boxes, model->centres, model->beta, model->info, w, grid, n_folds, d_cv,
-                     d_choice, d_cv_workspace, s);
+    launch_lambda_cv(g, p, par->precision, model->boxes, model->centres, model->beta, model->info, w, grid,
+                     n_folds, d_cv, d_choice, d_cv_workspace, s);
     PAM_CUDA_TRY(cudaGetLastError());
     if (par->deferred_status) return PAM_OK;
     int32_t hs[8];

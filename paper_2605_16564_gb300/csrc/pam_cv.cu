@@ -11,11 +11,14 @@
 // folds / N. The least cv (first grid index on ties) is chosen and the
 // coefficients are refit on all N cells with it.
 //
-// Device layout: E (exp(l - l*), [S][m_cap][n_max]) and 1 / Shepard sum are
+// Binary64 form: E (exp(l - l*), [S][m_cap][n_max]) and 1 / Shepard sum are
 // assembled once for all folds; per fold the masked b and G are formed, and
 // per grid pair a scratch copy of the model's coefficients is solved in
 // place, then its held-out residuals are summed by one block per subdomain in
-// a fixed order (cv is bitwise reproducible).
+// a fixed order (cv is bitwise reproducible). Mixed form: the row statistics
+// once, per fold the tensor-core Gram of the training rows, and per grid pair
+// the mixed solve in its cross-validation form, which sums the held-out
+// residuals of its final coefficients itself (fixed order too).
 #include <cfloat>
 
 #include "pam_internal.cuh"
@@ -85,20 +88,24 @@ size_t cv_workspace_bytes(const Geo &g) {
            S * 2 * sizeof(double);
 }
 
-void launch_lambda_cv(const Geo &g, const Par &p, const int32_t *boxes, const double *centres, double *beta,
-                      int32_t *info, const Ws &w, const CvGrid &grid, int folds, double *cv, int32_t *choice,
-                      void *cv_ws, cudaStream_t st) {
+void launch_lambda_cv(const Geo &g, const Par &p, int precision, const int32_t *boxes, const double *centres,
+                      double *beta, int32_t *info, const Ws &w, const CvGrid &grid, int folds, double *cv,
+                      int32_t *choice, void *cv_ws, cudaStream_t st) {
     const size_t S = (size_t)g.S;
+    const bool mixed = precision == PAM_PREC_MIXED;
     char *base = (char *)cv_ws;
     double *beta_s = (double *)base;
     int32_t *info_s = (int32_t *)(base + ((S * g.m_cap * sizeof(double) + 255) / 256) * 256);
     double *lam_tab = (double *)((char *)info_s + ((S * kInfoN * 4 + 255) / 256) * 256);
-    // E and 1 / Shepard sum of every subdomain, once for all folds
-    launch_assemble_gram_f64(g, boxes, centres, info, w, st, 1);
+    // once for all folds: E and 1 / Shepard sum (binary64 form), or the row
+    // statistics of the Shepard rows (mixed form)
+    if (mixed) launch_stats_f32(g, boxes, centres, info, w, st, 1);
+    else launch_assemble_gram_f64(g, boxes, centres, info, w, st, 1);
     cudaMemsetAsync(cv, 0, S * grid.n * sizeof(double), st);
     const int nb = (int)S * g.m_cap, ni = (int)S * kInfoN;
     for (int f = 0; f < folds; ++f) {
-        launch_bgram_f64(g, info, w, st, 1, folds, f);
+        if (mixed) launch_gram_tc(g, boxes, centres, info, w, st, 1, folds, f);
+        else launch_bgram_f64(g, info, w, st, 1, folds, f);
         Par pf = p;
         pf.cv_folds = folds;
         pf.cv_fold = f;
@@ -107,16 +114,25 @@ void launch_lambda_cv(const Geo &g, const Par &p, const int32_t *boxes, const do
             pf.lam2_hat = grid.lam[q][1];
             k_cv_scratch<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(nb, beta, beta_s, ni, info, info_s);
             count_launches(1);
-            launch_solve_f64(g, pf, beta_s, info_s, w, nullptr, 1, st);
-            k_cv_heldout<<<(unsigned)S, 256, 0, st>>>(g, folds, f, beta_s, info_s, w, cv, grid.n, q);
-            count_launches(1);
+            if (mixed) {
+                launch_solve_mixed(g, pf, boxes, centres, beta_s, info_s, w, nullptr, 1, cv + q, grid.n, st);
+            } else {
+                launch_solve_f64(g, pf, beta_s, info_s, w, nullptr, 1, st);
+                k_cv_heldout<<<(unsigned)S, 256, 0, st>>>(g, folds, f, beta_s, info_s, w, cv, grid.n, q);
+                count_launches(1);
+            }
         }
     }
     k_cv_choose<<<(unsigned)((S + 127) / 128), 128, 0, st>>>((int)S, grid, info, cv, choice, lam_tab);
     count_launches(1);
     // refit on all cells with each subdomain's chosen pair
-    launch_bgram_f64(g, info, w, st, 1, 0, 0);
-    launch_solve_f64(g, p, beta, info, w, lam_tab, 1, st);
+    if (mixed) {
+        launch_gram_tc(g, boxes, centres, info, w, st, 1, 0, 0);
+        launch_solve_mixed(g, p, boxes, centres, beta, info, w, lam_tab, 1, nullptr, 0, st);
+    } else {
+        launch_bgram_f64(g, info, w, st, 1, 0, 0);
+        launch_solve_f64(g, p, beta, info, w, lam_tab, 1, st);
+    }
 }
 
 }  // namespace pam

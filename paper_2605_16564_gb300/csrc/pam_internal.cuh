@@ -83,6 +83,13 @@ void launch_bgram_f64(const Geo &g, const int32_t *info, const Ws &w, cudaStream
                       int fold);
 void launch_solve_f64(const Geo &g, const Par &p, double *beta, int32_t *info, const Ws &w,
                       const double *lam_tab, int all, cudaStream_t st);
+void launch_stats_f32(const Geo &g, const int32_t *boxes, const double *centres, const int32_t *info,
+                      const Ws &w, cudaStream_t st, int all);
+void launch_gram_tc(const Geo &g, const int32_t *boxes, const double *centres, const int32_t *info,
+                    const Ws &w, cudaStream_t st, int all, int folds, int fold);
+void launch_solve_mixed(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
+                        double *beta, int32_t *info, const Ws &w, const double *lam_tab, int all, double *cv,
+                        int cv_stride, cudaStream_t st);
 void launch_copy_gram_f32(const Geo &g, const int32_t *info, const Ws &w, double *G_out,
                           double *b_out, cudaStream_t st);
 void launch_copy_gram_f64(const Geo &g, const int32_t *info, const Ws &w, double *G_out,
@@ -109,9 +116,9 @@ struct CvGrid {
     double lam[kCvMaxGrid][2];
 };
 size_t cv_workspace_bytes(const Geo &g);
-void launch_lambda_cv(const Geo &g, const Par &p, const int32_t *boxes, const double *centres, double *beta,
-                      int32_t *info, const Ws &w, const CvGrid &grid, int folds, double *cv, int32_t *choice,
-                      void *cv_ws, cudaStream_t st);
+void launch_lambda_cv(const Geo &g, const Par &p, int precision, const int32_t *boxes, const double *centres,
+                      double *beta, int32_t *info, const Ws &w, const CvGrid &grid, int folds, double *cv,
+                      int32_t *choice, void *cv_ws, cudaStream_t st);
 
 // Kernel families timed by the optional event profiler (pam_timing_*).
 enum Phase {

@@ -181,10 +181,12 @@ __device__ unsigned long long g_gram_prof[16];
 #define GP_ADD(k, v)
 #endif
 
+// folds > 0: only the cells t with t mod folds != fold enter G and b (the
+// training rows of a cross-validation fold); the others stage as padding.
 __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t *boxes,
                                                            const double *centres,
                                                            const int32_t *info, Ws w, int all,
-                                                           int nst, int Rcap) {
+                                                           int nst, int Rcap, int folds, int fold) {
     const int s = blockIdx.y;
     const int32_t *inf = info + s * kInfoN;
     if (!all && inf[PAM_INFO_STOPPED]) return;
@@ -229,7 +231,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
     for (int t = tid; t < nch * kTcKC; t += blockDim.x) {
         float x[3] = {0.f, 0.f, 0.f};
         float sh = INFINITY, y = 0.f;
-        if (t < N) {
+        if (t < N && (folds == 0 || t % folds != fold)) {
             local_cell(g, box, t, x);
             sh = rowmax[t] - log2f(rowinv[t]);
             y = (float)yv[t];
@@ -465,25 +467,32 @@ static size_t gram_tc_smem(const Geo &g, int stages) {
     return tiles + Rcap * sizeof(float4) + 4 * Rcap * sizeof(float) + cells * (sizeof(float4) + sizeof(float));
 }
 
+void launch_gram_tc(const Geo &g, const int32_t *boxes, const double *centres, const int32_t *info,
+                    const Ws &w, cudaStream_t st, int all, int folds, int fold) {
+    PhaseScope ps(kPhGramTC, st);
+    const int stages = gram_tc_smem(g, kTcMaxStages) <= kSmemLimit ? kTcMaxStages : 2;
+    size_t sm = gram_tc_smem(g, stages);
+    cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dim3 grid((g.m_cap + 127) / 128, g.S);
+    k_gram_tc<<<grid, kTcThreads, sm, st>>>(g, boxes, centres, info, w, all, stages, tc_rows_cap(g.m_cap),
+                                            folds, fold);
+    count_launches(1);
+}
+
+void launch_stats_f32(const Geo &g, const int32_t *boxes, const double *centres, const int32_t *info,
+                      const Ws &w, cudaStream_t st, int all) {
+    PhaseScope ps(kPhStats, st);
+    size_t sm = (size_t)g.m_cap * sizeof(float4);
+    cudaFuncSetAttribute(k_stats_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    dim3 grid((g.n_max + 127) / 128, g.S);
+    k_stats_f32<<<grid, 128, sm, st>>>(g, boxes, centres, info, w, all);
+    count_launches(1);
+}
+
 void launch_stats_gram_tc(const Geo &g, const int32_t *boxes, const double *centres,
                           const int32_t *info, const Ws &w, cudaStream_t st, int all) {
-    {
-        PhaseScope ps(kPhStats, st);
-        size_t sm = (size_t)g.m_cap * sizeof(float4);
-        cudaFuncSetAttribute(k_stats_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        dim3 grid((g.n_max + 127) / 128, g.S);
-        k_stats_f32<<<grid, 128, sm, st>>>(g, boxes, centres, info, w, all);
-        count_launches(1);
-    }
-    {
-        PhaseScope ps(kPhGramTC, st);
-        const int stages = gram_tc_smem(g, kTcMaxStages) <= kSmemLimit ? kTcMaxStages : 2;
-        size_t sm = gram_tc_smem(g, stages);
-        cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        dim3 grid((g.m_cap + 127) / 128, g.S);
-        k_gram_tc<<<grid, kTcThreads, sm, st>>>(g, boxes, centres, info, w, all, stages, tc_rows_cap(g.m_cap));
-        count_launches(1);
-    }
+    launch_stats_f32(g, boxes, centres, info, w, st, all);
+    launch_gram_tc(g, boxes, centres, info, w, st, all, 0, 0);
 }
 
 // Copies the fp32 Gram of the mixed form into caller doubles (pam_gram).
@@ -799,18 +808,32 @@ struct DFAcc {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// Cross-validation form (cv != nullptr, p.cv_folds > 0): the system is that
+// of the training rows of fold p.cv_fold (G~ and b masked by the Gram, the
+// exact gradient over the training cells only), lambda_k = N_train
+// lambda_k_hat, no indicators are written, and the held-out cells' squared
+// residuals (y_t - (W x)_t)^2 of the final x are added to cv[s * cv_stride]
+// in a fixed order. lam_tab (optional): per-subdomain (lambda1_hat,
+// lambda2_hat) pairs in place of p's; all: solve also the subdomains whose
+// refinement has stopped.
 __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, const int32_t *boxes,
                                                             const double *centres, double *beta,
                                                             int32_t *info, Ws w, int kMxFactorBytes,
-                                                            int ordered) {
+                                                            int ordered, const double *lam_tab, int all,
+                                                            double *cv, int cv_stride) {
     // blocks take the subdomains in decreasing cost of their previous solve,
     // so the longest start first and the level does not wait on a late one
     const int s = ordered ? w.order[blockIdx.x] : blockIdx.x;
     const long long t_start = clock64();
     int32_t *inf = info + s * kInfoN;
-    if (inf[PAM_INFO_STOPPED]) return;
+    if (!all && inf[PAM_INFO_STOPPED]) return;
     const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS], mc = g.m_cap;
-    const float lam1 = (float)((double)N * p.lam1_hat), lam2 = (float)((double)N * p.lam2_hat);
+    const int folds = cv ? p.cv_folds : 0, fold = p.cv_fold;
+    const int n_out = (folds > 0 && N > fold) ? (N - 1 - fold) / folds + 1 : 0;
+    const double n_fit = (double)(N - n_out);
+    const double l1h = lam_tab ? lam_tab[2 * s] : p.lam1_hat, l2h = lam_tab ? lam_tab[2 * s + 1] : p.lam2_hat;
+    const float lam1 = (float)(n_fit * l1h), lam2 = (float)(n_fit * l2h);
+    double held = 0.0;  // this thread's held-out squared residuals of the last exact pass
     // stage 1 only has to find a good support: G~ carries ~1e-5 relative error
     const float tol_pdas = lam1 * (1.0f + 1e-3f);
     const int tid = threadIdx.x, lane = tid & 31;
@@ -1036,6 +1059,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
         // e = y - W x over the patch (only the support contributes); W x is
         // accumulated in double-float and subtracted in fp64: |y| ~ 10 would
         // otherwise leave ~1e-6 of cancellation noise in e, and W^T e inherits it
+        held = 0.0;
         for (int t = tid; t < N; t += blockDim.x) {
             const float4 cx = cell[t];
             DFAcc acc;
@@ -1043,7 +1067,13 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
                 const int m = idx[pp];
                 acc.add_prod(tc::ex2(logit2(sc[m], cx.x, cx.y, cx.z) - cx.w), x[m]);
             }
-            ce[t] = (float)(yv[t] - acc.value() * (double)cinv[t]);
+            const float e = (float)(yv[t] - acc.value() * (double)cinv[t]);
+            if (folds > 0 && t % folds == fold) {  // held out: not in the gradient
+                held += (double)e * (double)e;
+                ce[t] = 0.f;
+            } else {
+                ce[t] = e;
+            }
         }
         __syncthreads();
         PROF_MARK(4);
@@ -1131,14 +1161,38 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
     // one the last gradient pass saw, with e = y - W x (fp32) in ce:
     // exp(y^) - K = K (exp(-e) - 1) = K expm1(-e), free of cancellation and
     // of binary64 work (the fp64 pipe is narrow on this part).
-    if (certified) {
+    if (cv) {
+        // held-out residuals of the final x (the last exact pass saw it when certified)
+        if (!certified) {
+            held = 0.0;
+            for (int t = fold + folds * tid; t < N; t += folds * (int)blockDim.x) {
+                const float4 cx = cell[t];
+                DFAcc acc;
+                for (int pp = 0; pp < scnt; ++pp) {
+                    const int m = idx[pp];
+                    acc.add_prod(tc::ex2(logit2(sc[m], cx.x, cx.y, cx.z) - cx.w), x[m]);
+                }
+                const double e = yv[t] - acc.value() * (double)cinv[t];
+                held += e * e;
+            }
+        }
+        __shared__ double hpart[kMxThreads / 32];
+        for (int o2 = 16; o2 > 0; o2 >>= 1) held += __shfl_xor_sync(0xffffffffu, held, o2);
+        if (lane == 0) hpart[tid >> 5] = held;
+        __syncthreads();
+        if (tid == 0) {
+            double tot = 0.0;
+            for (int q = 0; q < kMxThreads / 32; ++q) tot += hpart[q];
+            cv[(size_t)s * cv_stride] += tot;
+        }
+    } else if (certified) {
         for (int t = tid; t < N; t += blockDim.x) {
             const double ev = w.kv[(size_t)s * g.n_max + t] * (double)expm1f(-ce[t]);
             w.R[(size_t)s * g.n_max + t] = g.vol * (ev * ev);
         }
     }
     // otherwise x changed after the last pass: e = y - W x once more
-    for (int t = tid; t < N && !certified; t += blockDim.x) {
+    for (int t = tid; t < N && !certified && !cv; t += blockDim.x) {
         const float4 cx = cell[t];
         DFAcc acc;
         for (int pp = 0; pp < scnt; ++pp) {
@@ -1238,10 +1292,9 @@ bool mixed_solve_fits(const Geo &g) {
     return solve_mixed_smem(g) <= kSmemLimit && gram_tc_smem(g, 2) <= kSmemLimit;
 }
 
-void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes,
-                              const double *centres, double *beta, int32_t *info, const Ws &w,
-                              cudaStream_t st) {
-    launch_stats_gram_tc(g, boxes, centres, info, w, st, 0);
+void launch_solve_mixed(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
+                        double *beta, int32_t *info, const Ws &w, const double *lam_tab, int all, double *cv,
+                        int cv_stride, cudaStream_t st) {
     size_t sm = solve_mixed_smem(g);
     cudaFuncSetAttribute(k_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     PhaseScope ps(kPhSolve, st);
@@ -1254,8 +1307,15 @@ void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes,
         count_launches(1);
     }
     k_solve_mixed<<<g.S, kMxThreads, sm, st>>>(g, p, boxes, centres, beta, info, w, factor_smem_bytes(),
-                                               ordered);
+                                               ordered, lam_tab, all, cv, cv_stride);
     count_launches(1);
+}
+
+void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes,
+                              const double *centres, double *beta, int32_t *info, const Ws &w,
+                              cudaStream_t st) {
+    launch_stats_gram_tc(g, boxes, centres, info, w, st, 0);
+    launch_solve_mixed(g, p, boxes, centres, beta, info, w, nullptr, 0, nullptr, 0, st);
 }
 
 // The mixed solve already wrote the indicators of its final coefficients.

@@ -63,8 +63,8 @@ def test_lambda_cv_rejects_bad_arguments(pam):
     import ctypes as C
     pr = pam.make_problem((16, 16), (2, 2), 1, (2, 2))
     fake = C.c_void_p(256)  # never dereferenced: validation fails first
-    for prec, grid, folds, want in [(pam.PAM_PREC_MIXED, [(1e-4, 1e-6)], 3, 6),   # binary64 form only
-                                    (pam.PAM_PREC_FP64, [(1e-4, 0.0)], 3, 1),    # lambda2_hat > 0
+    for prec, grid, folds, want in [(pam.PAM_PREC_FP64, [(1e-4, 0.0)], 3, 1),    # lambda2_hat > 0
+                                    (pam.PAM_PREC_MIXED, [(1e-4, 0.0)], 3, 1),
                                     (pam.PAM_PREC_FP64, [(-1e-4, 1e-6)], 3, 1),  # lambda1_hat >= 0
                                     (pam.PAM_PREC_FP64, [(1e-4, 1e-6)], 1, 1),   # at least two folds
                                     (pam.PAM_PREC_FP64, [(1e-4, 1e-6)] * 33, 3, 1)]:  # at most 32 pairs
