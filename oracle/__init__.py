@@ -354,3 +354,65 @@ def cv_lambda(model, K, grid, n_folds, which=None):
         beta[s, :M] = bs
         certified[s] = inf["certified"]
     return dict(cv=cv, choice=choice, beta=beta, certified=certified)
+
+
+# --------------------------------------------------------------------------
+# Interface gluing (Step 4 remark: the piecewise K* is discontinuous across
+# subdomain interfaces; a gluing or averaging across neighbours makes it
+# continuous; the paper leaves the procedure open). Reading: the local
+# log-surrogates u_i = sum_m beta_m w_m are blended with a tensor-product
+# partition of unity that ramps across each interior core face over a band
+# of half-width delta = band * h:
+#   psi_i(x) = prod_a phi_lo(x_a) phi_hi(x_a),
+#   phi_lo = r((x_a - lo_a + delta) / (2 delta)) (1 on the outer face),
+#   phi_hi = r((hi_a + delta - x_a) / (2 delta)) (1 on the outer face),
+#   r(t) = t^2 (3 - 2 t) on [0, 1] (clamped), so r(t) + r(1 - t) = 1,
+#   ln K*(x) = sum_i psi_i u_i / sum_i psi_i.
+# --------------------------------------------------------------------------
+
+def _smoothstep(t):
+    t = np.clip(t, 0.0, 1.0)
+    return t * t * (3.0 - 2.0 * t)
+
+
+def glue_weights(n_cells, n_sub, pts, band):
+    """psi_i(x) of every subdomain at points [n, dim]: [n, S] (brute force
+    over all subdomains; points outside the domain get 0)."""
+    n_cells = tuple(n_cells)
+    dim = len(n_cells)
+    pts = _f64(pts).reshape(-1, dim)
+    h = 1.0 / max(n_cells)
+    delta = band * h
+    boxes = partition(n_cells, n_sub, 0)
+    psi = np.ones((pts.shape[0], boxes.shape[0]))
+    for s in range(boxes.shape[0]):
+        for a in range(dim):
+            lo, hi = boxes[s, a], boxes[s, 3 + a]
+            xa = pts[:, a]
+            if lo > 0:
+                psi[:, s] *= _smoothstep((xa - lo * h + delta) / (2.0 * delta))
+            if hi < n_cells[a]:
+                psi[:, s] *= _smoothstep((hi * h + delta - xa) / (2.0 * delta))
+    inside = np.all((pts >= 0.0) & (pts <= np.asarray(n_cells) * h), axis=1)
+    psi[~inside] = 0.0
+    return psi
+
+
+def evaluate_glued(model, pts, band, log_space=False):
+    """Glued K*(x) (or its log) at points [n, dim]; NaN outside the domain."""
+    n_cells, n_sub = tuple(model["n_cells"]), tuple(model["n_sub"])
+    dim = len(n_cells)
+    pts = _f64(pts).reshape(-1, dim)
+    psi = glue_weights(n_cells, n_sub, pts, band)
+    num = np.zeros(pts.shape[0])
+    for s in range(psi.shape[1]):
+        sel = np.flatnonzero(psi[:, s] > 0.0)
+        if sel.size == 0:
+            continue
+        M = int(model["M"][s])
+        u = assemble(dim, pts[sel], model["c"][s, :M]) @ model["beta"][s, :M]
+        num[sel] += psi[sel, s] * u
+    den = psi.sum(axis=1)
+    with np.errstate(invalid="ignore", divide="ignore"):
+        v = np.where(den > 0.0, num / den, np.nan)
+    return v if log_space else np.exp(v)
