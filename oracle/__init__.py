@@ -88,6 +88,14 @@ def lib():
             L.orc_residual_gl.argtypes = [C.c_int, C.c_int64, f64p, C.c_int, f64p, f64p, f64p, C.c_double,
                                           C.c_double, f64p]
             L.orc_residual_gl.restype = None
+            L.orc_residual_cells.argtypes = [C.c_int64, C.c_int, f64p, f64p, f64p, f64p, f64p]
+            L.orc_residual_cells.restype = None
+            L.orc_mark_cells.argtypes = [C.c_int64, f64p, f64p, C.c_int, i32p]
+            L.orc_mark_cells.restype = C.c_int
+            i64p = np.ctypeslib.ndpointer(np.int64, flags="C_CONTIGUOUS")
+            L.orc_fit_cells_all.argtypes = [C.c_int, i32p, f64p, f64p, f64p, C.c_int, i32p, i64p, i32p, i32p,
+                                            C.c_void_p, C.c_int, C.c_void_p, C.c_int, f64p, f64p, f64p]
+            L.orc_fit_cells_all.restype = C.c_int
             _lib = L
     return _lib
 
@@ -203,6 +211,22 @@ def mark(R, eps_tol, k_top):
     R = _f64(R)
     out = np.zeros(max(int(k_top), 1), dtype=np.int32)
     n = lib().orc_mark(R.shape[0], R, float(eps_tol), int(k_top), out)
+    return out[:n].copy()
+
+
+def residual_cells(W, beta, kv, vol):
+    """R_T = |T| (exp(W beta)_T - K_T)^2 with a measure per cell."""
+    W = _f64(W)
+    R = np.zeros(W.shape[0])
+    lib().orc_residual_cells(W.shape[0], W.shape[1], W, _f64(beta), _f64(kv), _f64(vol), R)
+    return R
+
+
+def mark_cells(R, eps_cell, k_top):
+    """Marking with a threshold per cell."""
+    R = _f64(R)
+    out = np.zeros(max(int(k_top), 1), dtype=np.int32)
+    n = lib().orc_mark_cells(R.shape[0], R, _f64(eps_cell), int(k_top), out)
     return out[:n].copy()
 
 
@@ -416,3 +440,85 @@ def evaluate_glued(model, pts, band, log_space=False):
     with np.errstate(invalid="ignore", divide="ignore"):
         v = np.where(den > 0.0, num / den, np.nan)
     return v if log_space else np.exp(v)
+
+
+# --------------------------------------------------------------------------
+# General (unstructured) meshes given as cells (section 2: elements T of a
+# shape-regular partition, e.g. intervals, triangles or quadrilaterals, each
+# with a sampling point x_T in T, its value K_T and its measure |T|).
+# Reading: the subdomains are the boxes of the lattice decomposition of the
+# problem (cores [floor(j n / p) h, floor((j+1) n / p) h) per axis, h =
+# 1 / max n); an element belongs to the core holding its sampling point (the
+# owner rule of Step 4, so every element is in exactly one core and each
+# subdomain is a union of elements), and to the patch of every subdomain
+# whose core grown by `overlap` h holds its point (closed at the outer face
+# of the domain). A patch's local order is ascending element index.
+# --------------------------------------------------------------------------
+
+def partition_cells(n_cells, n_sub, overlap, x):
+    """(boxes [S, 12], patch_start int64 [S+1], patch_cells int32 [...]) for
+    elements with sampling points x [n, dim] (brute force over subdomains)."""
+    n_cells = tuple(n_cells)
+    dim = len(n_cells)
+    x = _f64(x).reshape(-1, dim)
+    nmax = max(n_cells)
+    u = x * float(nmax)
+    boxes = partition(n_cells, n_sub, overlap)
+    lists = []
+    for s in range(boxes.shape[0]):
+        ok = np.ones(x.shape[0], dtype=bool)
+        for a in range(dim):
+            lo, hi = boxes[s, 6 + a], boxes[s, 9 + a]
+            upper = (u[:, a] <= hi) if hi == n_cells[a] else (u[:, a] < hi)
+            ok &= (u[:, a] >= lo) & upper
+        lists.append(np.flatnonzero(ok).astype(np.int32))
+    start = np.zeros(len(lists) + 1, dtype=np.int64)
+    start[1:] = np.cumsum([len(v) for v in lists])
+    cells = np.concatenate(lists) if lists else np.zeros(0, dtype=np.int32)
+    return boxes, start, _i32(cells)
+
+
+def fit_cells(x, vol, K, n_cells, n_sub, overlap, g, params, which=None, m_cap=None):
+    """Algorithm 1 on every subdomain of a mesh given as cells (the subset
+    ``which`` if given). Returns the model dict of fit_all plus the patch
+    lists (patch_start, patch_cells)."""
+    n_cells = tuple(n_cells)
+    dim = len(n_cells)
+    x = _f64(x).reshape(-1, dim)
+    boxes, start, cells = partition_cells(n_cells, n_sub, overlap, x)
+    S = boxes.shape[0]
+    P = _Params(**{k: params[k] for k, _ in _Params._fields_})
+    P.quad = 0
+    if m_cap is None:
+        m_cap = m_capacity(g, dim, params["k_top"], params["levels"], params["m_max"])
+    c = np.zeros((S, m_cap, 4)); beta = np.zeros((S, m_cap)); info = np.zeros((S, NINFO))
+    wh = None if which is None else _i32(which)
+    failed = lib().orc_fit_cells_all(dim, _pad3(n_cells, 1), x, _f64(K).reshape(-1), _f64(vol).reshape(-1), S,
+                                     boxes, start, cells if cells.size else np.zeros(1, dtype=np.int32),
+                                     _pad3(g, 1), C.byref(P), int(m_cap),
+                                     None if wh is None else wh.ctypes.data, 0 if wh is None else wh.shape[0],
+                                     c, beta, info)
+    M = info[:, 0].astype(np.int32)
+    return dict(boxes=boxes, M=M, c=c, beta=beta, info=info, m_cap=int(m_cap), failed=int(failed),
+                n_cells=n_cells, n_sub=tuple(n_sub), patch_start=start, patch_cells=cells)
+
+
+def errors_cells(model, x, vol, K):
+    """Relative errors over the elements, each measured with its owner's
+    surrogate at its sampling point (midpoint rule, weight |T|):
+    l1 = sum |T| |K_T - K*| / sum |T| |K_T|, l2 = (sum |T| (K_T - K*)^2 /
+    sum |T| K_T^2)^(1/2) (Eq. (12)), l1_log = sum |T| |ln K_T - ln K*| /
+    sum |T| |ln K_T|, max_log10 = max |log10 K_T - log10 K*|."""
+    dim = len(model["n_cells"])
+    x = _f64(x).reshape(-1, dim)
+    v = evaluate(model, x, log_space=True)
+    K = _f64(K).reshape(-1)
+    vol = _f64(vol).reshape(-1)
+    lk = np.log(K)
+    ks = np.exp(v)
+    l1 = np.sum(vol * np.abs(K - ks)) / np.sum(vol * np.abs(K))
+    l2 = np.sqrt(np.sum(vol * (K - ks) ** 2) / np.sum(vol * K * K))
+    bl = np.sum(vol * np.abs(lk))
+    l1l = np.sum(vol * np.abs(lk - v)) / bl if bl > 0 else np.sum(vol * np.abs(lk - v))
+    return dict(l1=float(l1), l2=float(l2), l1_log=float(l1l),
+                max_log10=float(np.max(np.abs(lk - v)) / np.log(10.0)))

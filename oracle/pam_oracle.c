@@ -439,6 +439,21 @@ void orc_residual(int64_t n, int m, const double *W, const double *beta,
 }
 
 /*
+ * The same indicator for cells of unequal measure: R_T = |T| (K*(x_T) - K_T)^2
+ * with |T| = vol[j] (the midpoint rule on each cell, Eq. (4)).
+ */
+void orc_residual_cells(int64_t n, int m, const double *W, const double *beta,
+                        const double *kv, const double *vol, double *R)
+{
+    for (int64_t j = 0; j < n; ++j) {
+        double t = 0.0;
+        for (int k = 0; k < m; ++k) t += W[j * m + k] * beta[k];
+        double e = exp(t) - kv[j];
+        R[j] = vol[j] * (e * e);
+    }
+}
+
+/*
  * Two-point Gauss-Legendre rule per axis on a cell of side h centred at x
  * (the tensor rule has 2^dim nodes, each of weight |T| / 2^dim): node q has
  * x_a + s h / (2 sqrt(3)) on axis a, s = -1 if bit a of q is clear else +1.
@@ -490,15 +505,16 @@ void orc_residual_gl(int dim, int64_t n, const double *x, int m, const double *c
  * reorder cells whose indicators agree. marked[] receives the local indices
  * in rank order; returns how many (<= k_top).
  */
-int orc_mark(int64_t n, const double *R, double eps_tol, int k_top, int32_t *marked)
+static int mark_impl(int64_t n, const double *R, double eps_tol, const double *eps_cell, int k_top,
+                     int32_t *marked)
 {
-    float ek = (float)eps_tol;
     int cnt = 0;
     for (int t = 0; t < k_top; ++t) {
         int64_t best = -1;
         float bk = 0.0f;
         for (int64_t j = 0; j < n; ++j) {
             float kj = (float)R[j];
+            float ek = (float)(eps_cell ? eps_cell[j] : eps_tol);
             if (!(kj >= ek)) continue;
             int taken = 0;
             for (int u = 0; u < cnt; ++u) if (marked[u] == j) { taken = 1; break; }
@@ -509,6 +525,21 @@ int orc_mark(int64_t n, const double *R, double eps_tol, int k_top, int32_t *mar
         marked[cnt++] = (int32_t)best;
     }
     return cnt;
+}
+
+int orc_mark(int64_t n, const double *R, double eps_tol, int k_top, int32_t *marked)
+{
+    return mark_impl(n, R, eps_tol, NULL, k_top, marked);
+}
+
+/*
+ * The same marking with a threshold per cell, eps_cell[j] (cells of unequal
+ * measure: eps_T = |T| (eps_tol_rel max K)^2, so that R_T >= eps_T says
+ * |K*(x_T) - K_T| >= eps_tol_rel max K whatever the cell's size).
+ */
+int orc_mark_cells(int64_t n, const double *R, const double *eps_cell, int k_top, int32_t *marked)
+{
+    return mark_impl(n, R, 0.0, eps_cell, k_top, marked);
 }
 
 /* Unit directions of the new centres, the d+1 vertices of a regular simplex
@@ -611,6 +642,65 @@ typedef struct {
  * Reading on lambda: the printed values (Example 2) are per-sample weights,
  * lambda_k = N_i * lambda_k_hat for a patch of N_i cells.
  */
+/*
+ * Algorithm 1 on one patch given as cells: sampling points x [N][3]
+ * (unused axes 0), y = ln K, kv = K, measures vol [N] (|T|), the patch
+ * extent [ext_lo, ext_hi] that new centres are clipped to, the initial
+ * dictionary (c0, m0). quad = 1 (grid cells of side h only) takes the
+ * Gauss-Legendre indicators. eps_T = |T| (eps_tol_rel max K)^2 per cell.
+ */
+static int fit_patch(int dim, int64_t N, const double *x, const double *y, const double *kv,
+                     const double *vol, const double *ext_lo, const double *ext_hi, int quad, double h,
+                     const double *c0, int m0, const orc_params *P, int m_cap, double *c, double *beta,
+                     double *info)
+{
+    double kmax = 0.0;
+    for (int64_t j = 0; j < N; ++j) if (kv[j] > kmax) kmax = kv[j];
+    double *eps = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    for (int64_t j = 0; j < N; ++j)
+        eps[j] = P->eps_tol_rel < 0 ? -INFINITY
+                                    : vol[j] * (P->eps_tol_rel * kmax) * (P->eps_tol_rel * kmax);
+    double lam1 = (double)N * P->lambda1_hat, lam2 = (double)N * P->lambda2_hat;
+    int m_limit = m0 + P->m_max;
+    if (m_limit > m_cap) m_limit = m_cap;
+
+    memset(c, 0, sizeof(double) * (size_t)m_cap * 4);
+    memset(beta, 0, sizeof(double) * (size_t)m_cap);
+    memcpy(c, c0, sizeof(double) * (size_t)m0 * 4);
+    int m = m0, level = 0, certified = 1, sweeps = 0;
+    double min_margin = 1.0, maxR = 0.0;
+    double *W = (double *)malloc(sizeof(double) * (size_t)N * (size_t)m_cap);
+    double *G = (double *)malloc(sizeof(double) * (size_t)m_cap * (size_t)m_cap);
+    double *b = (double *)malloc(sizeof(double) * (size_t)m_cap);
+    double *R = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    int32_t *mk = (int32_t *)malloc(sizeof(int32_t) * (size_t)(P->k_top > 0 ? P->k_top : 1));
+    for (;;) {
+        double inf[5];
+        orc_assemble(dim, N, x, m, c, W);
+        orc_gram(N, m, W, y, G, b);
+        if (orc_enet(m, G, b, lam1, lam2, beta, P->max_sweeps, inf) != 0) certified = 0;
+        sweeps += (int)inf[0];
+        if (inf[2] < min_margin) min_margin = inf[2];
+        if (quad) orc_residual_gl(dim, N, x, m, c, beta, kv, vol[0], h, R);
+        else orc_residual_cells(N, m, W, beta, kv, vol, R);
+        maxR = 0.0;
+        for (int64_t j = 0; j < N; ++j) if (R[j] > maxR) maxR = R[j];
+        if (level >= P->levels || m >= m_limit) break;
+        int nm = orc_mark_cells(N, R, eps, P->k_top, mk);
+        if (nm == 0) break;
+        int m_new = orc_enrich(dim, m, c, nm, mk, x, ext_lo, ext_hi, P->eta, m_limit);
+        if (m_new == m) break;
+        m = m_new; /* beta[m_old..m_new) stays zero: the zero extension */
+        ++level;
+    }
+    int sup = 0;
+    for (int k = 0; k < m; ++k) if (beta[k] != 0.0) ++sup;
+    info[0] = m; info[1] = sup; info[2] = level; info[3] = certified;
+    info[4] = min_margin; info[5] = sweeps; info[6] = (double)N; info[7] = maxR;
+    free(eps); free(W); free(G); free(b); free(R); free(mk);
+    return certified ? 0 : 1;
+}
+
 int orc_fit_subdomain(int dim, const int *n_cells, const double *K,
                       const int32_t *box, const double *c0, int m0,
                       const orc_params *P, int m_cap, double *c, double *beta,
@@ -628,50 +718,49 @@ int orc_fit_subdomain(int dim, const int *n_cells, const double *K,
     double *x = (double *)malloc(sizeof(double) * (size_t)N * 3);
     double *y = (double *)malloc(sizeof(double) * (size_t)N);
     double *kv = (double *)malloc(sizeof(double) * (size_t)N);
+    double *vc = (double *)malloc(sizeof(double) * (size_t)N);
     orc_box_cells(dim, n_cells, plo, phi, K, x, y, kv);
-    double kmax = 0.0;
-    for (int64_t j = 0; j < N; ++j) if (kv[j] > kmax) kmax = kv[j];
-    double eps_tol = P->eps_tol_rel < 0 ? -INFINITY
-                                        : vol * (P->eps_tol_rel * kmax) * (P->eps_tol_rel * kmax);
-    double lam1 = (double)N * P->lambda1_hat, lam2 = (double)N * P->lambda2_hat;
-    int m_limit = m0 + P->m_max;
-    if (m_limit > m_cap) m_limit = m_cap;
+    for (int64_t j = 0; j < N; ++j) vc[j] = vol;
+    int r = fit_patch(dim, N, x, y, kv, vc, ext_lo, ext_hi, P->quad, h, c0, m0, P, m_cap, c, beta, info);
+    free(x); free(y); free(kv); free(vc);
+    return r;
+}
 
-    memset(c, 0, sizeof(double) * (size_t)m_cap * 4);
-    memset(beta, 0, sizeof(double) * (size_t)m_cap);
-    memcpy(c, c0, sizeof(double) * (size_t)m0 * 4);
-    int m = m0, level = 0, certified = 1, sweeps = 0;
-    double min_margin = 1.0, maxR = 0.0;
-    double *W = (double *)malloc(sizeof(double) * (size_t)N * (size_t)m_cap);
-    double *G = (double *)malloc(sizeof(double) * (size_t)m_cap * (size_t)m_cap);
-    double *b = (double *)malloc(sizeof(double) * (size_t)m_cap);
-    double *R = (double *)malloc(sizeof(double) * (size_t)N);
-    int32_t *mk = (int32_t *)malloc(sizeof(int32_t) * (size_t)(P->k_top > 0 ? P->k_top : 1));
-    for (;;) {
-        double inf[5];
-        orc_assemble(dim, N, x, m, c, W);
-        orc_gram(N, m, W, y, G, b);
-        if (orc_enet(m, G, b, lam1, lam2, beta, P->max_sweeps, inf) != 0) certified = 0;
-        sweeps += (int)inf[0];
-        if (inf[2] < min_margin) min_margin = inf[2];
-        if (P->quad) orc_residual_gl(dim, N, x, m, c, beta, kv, vol, h, R);
-        else orc_residual(N, m, W, beta, kv, vol, R);
-        maxR = 0.0;
-        for (int64_t j = 0; j < N; ++j) if (R[j] > maxR) maxR = R[j];
-        if (level >= P->levels || m >= m_limit) break;
-        int nm = orc_mark(N, R, eps_tol, P->k_top, mk);
-        if (nm == 0) break;
-        int m_new = orc_enrich(dim, m, c, nm, mk, x, ext_lo, ext_hi, P->eta, m_limit);
-        if (m_new == m) break;
-        m = m_new; /* beta[m_old..m_new) stays zero: the zero extension */
-        ++level;
+/*
+ * Algorithm 1 on a subdomain whose patch is a list of cells of a general
+ * (unstructured) mesh, section 2: each element T contributes its sampling
+ * point x_T (e.g. its centroid), its value K_T and its measure |T|.
+ * Inputs: all cells' points xs [n][dim], values Ks [n], measures vols [n];
+ * the patch's cell indices cells[0..N) (ascending: the local order); the
+ * subdomain's box row (core box for the initial dictionary, patch box for
+ * the extent of new centres, in units of h = 1/max n_cells).
+ */
+int orc_fit_cells_subdomain(int dim, const int *n_cells, const double *xs, const double *Ks,
+                            const double *vols, const int32_t *cells, int64_t N, const int32_t *box,
+                            const double *c0, int m0, const orc_params *P, int m_cap, double *c,
+                            double *beta, double *info)
+{
+    int nmax = 1;
+    for (int a = 0; a < dim; ++a) if (n_cells[a] > nmax) nmax = n_cells[a];
+    double h = 1.0 / (double)nmax;
+    double ext_lo[3] = {0, 0, 0}, ext_hi[3] = {0, 0, 0};
+    for (int a = 0; a < dim; ++a) { ext_lo[a] = box[6 + a] * h; ext_hi[a] = box[9 + a] * h; }
+    double *x = (double *)calloc((size_t)(N > 0 ? N : 1) * 3, sizeof(double));
+    double *y = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    double *kv = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    double *vc = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));
+    for (int64_t j = 0; j < N; ++j) {
+        int64_t t = cells[j];
+        for (int a = 0; a < dim; ++a) x[j * 3 + a] = xs[t * dim + a];
+        kv[j] = Ks[t];
+        y[j] = log(Ks[t]);
+        vc[j] = vols[t];
     }
-    int sup = 0;
-    for (int k = 0; k < m; ++k) if (beta[k] != 0.0) ++sup;
-    info[0] = m; info[1] = sup; info[2] = level; info[3] = certified;
-    info[4] = min_margin; info[5] = sweeps; info[6] = (double)N; info[7] = maxR;
-    free(x); free(y); free(kv); free(W); free(G); free(b); free(R); free(mk);
-    return certified ? 0 : 1;
+    orc_params Q = *P;
+    Q.quad = 0; /* element shapes are not given: the midpoint rule */
+    int r = fit_patch(dim, N, x, y, kv, vc, ext_lo, ext_hi, 0, h, c0, m0, &Q, m_cap, c, beta, info);
+    free(x); free(y); free(kv); free(vc);
+    return r;
 }
 
 /*
@@ -697,6 +786,31 @@ int orc_fit_all(int dim, const int *n_cells, const double *K, int S,
         failed += orc_fit_subdomain(dim, n_cells, K, boxes + s * 12, c0, m0, P, m_cap,
                                     c + (int64_t)s * m_cap * 4, beta + (int64_t)s * m_cap,
                                     info + (int64_t)s * ORC_NINFO);
+        free(c0);
+    }
+    return failed;
+}
+
+/*
+ * orc_fit_all for a mesh given as cells: patch s holds the cells
+ * patch_cells[patch_start[s] .. patch_start[s+1]).
+ */
+int orc_fit_cells_all(int dim, const int *n_cells, const double *xs, const double *Ks, const double *vols,
+                      int S, const int32_t *boxes, const int64_t *patch_start, const int32_t *patch_cells,
+                      const int *g, const orc_params *P, int m_cap, const int32_t *which, int n_which,
+                      double *c, double *beta, double *info)
+{
+    int failed = 0;
+    int count = which ? n_which : S;
+#pragma omp parallel for schedule(dynamic, 1) reduction(+ : failed)
+    for (int t = 0; t < count; ++t) {
+        int s = which ? which[t] : t;
+        double *c0 = (double *)malloc(sizeof(double) * (size_t)m_cap * 4);
+        int m0 = orc_initial_dictionary(dim, n_cells, boxes + s * 12, boxes + s * 12 + 3, g, c0);
+        failed += orc_fit_cells_subdomain(dim, n_cells, xs, Ks, vols, patch_cells + patch_start[s],
+                                          patch_start[s + 1] - patch_start[s], boxes + s * 12, c0, m0, P,
+                                          m_cap, c + (int64_t)s * m_cap * 4, beta + (int64_t)s * m_cap,
+                                          info + (int64_t)s * ORC_NINFO);
         free(c0);
     }
     return failed;

@@ -27,6 +27,7 @@ import numpy as np
 __all__ = [
     "cell_size", "numpy_shape", "disc_field", "voronoi_field", "channel_field",
     "layered_field", "patch_batch", "cell_centred_points", "step_field_1d",
+    "grid_as_cells", "triangle_mesh", "graded_mesh", "voronoi_at",
 ]
 
 
@@ -198,3 +199,77 @@ def cell_centred_points(counts, extent) -> np.ndarray:
     grids = np.meshgrid(*reversed(axes), indexing="ij")
     cols = [g.reshape(-1) for g in reversed(grids)]
     return np.stack(cols, axis=1).astype(np.float64)
+
+
+# --------------------------------------------------------------------------
+# General meshes given as cells: per element its sampling point x_T (the
+# centroid), its measure |T| and its value K_T, in a flat element order.
+# --------------------------------------------------------------------------
+
+def grid_as_cells(K: np.ndarray, shape):
+    """The cells of a structured grid field as a cell list in global order
+    (x fastest): (x [n, dim] centroids, vol [n] = h^dim, K [n])."""
+    dim = len(shape)
+    h = cell_size(shape)
+    axes = [(np.arange(n) + 0.5) * h for n in shape]  # (i + 1/2) h, as the grid path forms them
+    grids = np.meshgrid(*reversed(axes), indexing="ij")
+    x = np.stack([g.reshape(-1) for g in reversed(grids)], axis=1)
+    vol = np.full(x.shape[0], h ** dim)
+    return x, vol, np.ascontiguousarray(np.asarray(K, dtype=np.float64).reshape(-1))
+
+
+def voronoi_at(points: np.ndarray, n_sites: int = 32, seed: int = 2, log10_range=(-3.0, 3.0)) -> np.ndarray:
+    """The Voronoi field of voronoi_field (same sites and values for the same
+    seed) evaluated at arbitrary 2-D points [n, 2]."""
+    rng = np.random.default_rng(seed)
+    sites = rng.uniform(0.0, 1.0, size=(n_sites, 2))
+    logk = rng.uniform(log10_range[0], log10_range[1], size=n_sites)
+    p = np.asarray(points, dtype=np.float64)
+    d2 = (p[:, 0:1] - sites[:, 0]) ** 2 + (p[:, 1:2] - sites[:, 1]) ** 2
+    return (10.0 ** logk[np.argmin(d2, axis=1)]).astype(np.float64)
+
+
+def triangle_mesh(n: int, seed: int = 11, ny: int | None = None):
+    """Unstructured 2-D triangle mesh of the rectangle [0, n h] x [0, ny h]
+    (h = 1 / max(n, ny)): every grid square is cut along one of its two
+    diagonals, chosen at random per square, into two triangles of area h^2/2.
+    Returns (x [2 n ny, 2] triangle centroids, vol [2 n ny]) in square order
+    (x fastest), the two triangles of a square consecutive."""
+    ny = n if ny is None else ny
+    h = 1.0 / max(n, ny)
+    rng = np.random.default_rng(seed)
+    diag = rng.integers(0, 2, size=(ny, n))
+    i = np.arange(n)[None, :].repeat(ny, 0)
+    j = np.arange(ny)[:, None].repeat(n, 1)
+    # diagonal 0 joins (i, j)-(i+1, j+1): centroids (i+2/3, j+1/3), (i+1/3, j+2/3)
+    # diagonal 1 joins (i+1, j)-(i, j+1): centroids (i+1/3, j+1/3), (i+2/3, j+2/3)
+    a = np.where(diag == 0, 2.0, 1.0) / 3.0
+    b = np.where(diag == 0, 1.0, 2.0) / 3.0
+    t0 = np.stack([(i + a) * h, (j + 1.0 / 3.0) * h], -1)
+    t1 = np.stack([(i + b) * h, (j + 2.0 / 3.0) * h], -1)
+    x = np.stack([t0, t1], axis=2).reshape(-1, 2)
+    vol = np.full(x.shape[0], 0.5 * h * h)
+    return x, vol
+
+
+def graded_mesh(shape, seed: int = 12, ratio: float = 3.0):
+    """Non-uniform tensor mesh of the box [0, n_a h]: along each axis the n_a
+    cell widths are drawn from a seeded log-uniform law spanning ``ratio``
+    and rescaled to the axis length. Returns (x [n, dim] cell centroids,
+    vol [n] cell volumes) in x-fastest order."""
+    rng = np.random.default_rng(seed)
+    h = cell_size(shape)
+    edges = []
+    for n in shape:
+        w = np.exp(rng.uniform(0.0, np.log(ratio), size=n))
+        w *= n * h / w.sum()
+        e = np.concatenate([[0.0], np.cumsum(w)])
+        e[-1] = n * h
+        edges.append(e)
+    mids = [0.5 * (e[1:] + e[:-1]) for e in edges]
+    widths = [e[1:] - e[:-1] for e in edges]
+    grids = np.meshgrid(*reversed(mids), indexing="ij")
+    wgrid = np.meshgrid(*reversed(widths), indexing="ij")
+    x = np.stack([g.reshape(-1) for g in reversed(grids)], axis=1)
+    vol = np.prod(np.stack([g.reshape(-1) for g in wgrid], axis=1), axis=1)
+    return x, vol
