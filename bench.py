@@ -597,6 +597,32 @@ def run_pam(args, rank, ws):
             del cf, beta0, info0
         del first
 
+    # --- glued evaluation across subdomain interfaces (optional) ------------
+    glue = None
+    if args.glue > 0:
+        gout = torch.empty_like(out)
+        fit.eval_glued(ptsd, args.glue, out=gout)
+        gtimes = []
+        for i in range(args.warmup + args.steps):
+            flush.fill_(1)
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fit.eval_glued(ptsd, args.glue, out=gout)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            if i >= args.warmup:
+                gtimes.append(e0.elapsed_time(e1))
+        fit.eval(ptsd, out=out)
+        pw = out.cpu().numpy()
+        gl = gout.cpu().numpy()
+        gms = sum(gtimes) / len(gtimes)
+        pairs = glue_pairs_per_point(W, pts, args.glue)
+        glue = {"band_cells": args.glue, "ms": round(gms, 3), "pts_per_s": n_pts / (gms / 1e3),
+                "pairs_per_point": round(float(pairs.mean()), 4),
+                "points_blended": int((pairs > 1).sum()),
+                "max_abs_log_change": float(np.nanmax(np.abs(np.log(gl) - np.log(pw))))}
+
     # --- roofline of every kernel family, the dominant one first ------------
     peaks, peak_src = _peaks()
     work = accounting(fit, Kd, W["params"]["levels"], pam, seed=(lambda: lw.seed(fit, Kd)) if lw else None)
@@ -611,7 +637,26 @@ def run_pam(args, rank, ws):
     return dict(value=value, step_ms=step_ms, times=times, err=err, phase_ms=phase_ms, launches=launches,
                 clocks=clk.summary(), e2e_s=e2e_s, h2d=h2d, d2h=d2h, plain=plain, roof=roof, roofs=roofs,
                 prec_name=prec_name, n_cells=n_cells, n_pts=n_pts, info=info, learned=learned, mode=mode,
-                e2e_mode=e2e_mode, lambda_cv=lcv)
+                e2e_mode=e2e_mode, lambda_cv=lcv, glue=glue)
+
+
+def glue_pairs_per_point(W, pts, band):
+    """(point, subdomain) pairs of the glued evaluation per point: along each
+    axis two cores carry weight within band cells of an interior core face,
+    one elsewhere (host geometry, for the report)."""
+    shape, n_sub = W["shape"], W["n_sub"]
+    nmax = max(shape)
+    pairs = np.ones(pts.shape[0])
+    for a, (n, p) in enumerate(zip(shape, n_sub)):
+        faces = np.array([(j * n) // p for j in range(1, p)], dtype=np.float64)
+        if faces.size == 0:
+            continue
+        u = pts[:, a] * nmax
+        k = np.searchsorted(faces, u)
+        d = np.minimum(np.abs(u - faces[np.clip(k - 1, 0, faces.size - 1)]),
+                       np.abs(u - faces[np.clip(k, 0, faces.size - 1)]))
+        pairs *= np.where(d < band, 2.0, 1.0)
+    return pairs
 
 
 def owner_counts(W, pts):
@@ -689,6 +734,8 @@ def main():
     ap.add_argument("--lambda-cv", action="store_true",
                     help="also time the per-subdomain 3-fold cross-validation of 3 lambda pairs (binary64)")
     ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of a CUDA graph replay")
+    ap.add_argument("--glue", type=float, default=0.0,
+                    help="also time the glued evaluation (pam_eval_glued) with this band in cells")
     ap.add_argument("--quad", type=int, default=0, choices=[0, 1],
                     help="indicator and error quadrature: 0 midpoint, 1 two-point Gauss-Legendre per axis")
     args = ap.parse_args()
@@ -766,6 +813,8 @@ def main():
     }
     if r["lambda_cv"] is not None:
         line["lambda_cv"] = r["lambda_cv"]
+    if r["glue"] is not None:
+        line["glued_eval"] = r["glue"]
     fit_ms = sum(v[0] for k, v in r["phase_ms"].items() if k not in ("eval", "errors"))
     line["fit_cells_per_s"] = r["n_cells"] * ws / (fit_ms / 1e3) if fit_ms else None
     print(json.dumps(line))

@@ -10,6 +10,7 @@
  *   pam_refine           Step 3   indicators, marking, enrichment, re-solve
  *                                 (Algorithm 1, repeated n_levels times)
  *   pam_eval             Step 4   evaluate the piecewise surrogate anywhere
+ *   pam_eval_glued       Step 4   the same, blended across subdomain interfaces
  *   pam_errors                    relative L1/L2 errors over the source cells
  *
  * Conventions shared by every call:
@@ -280,6 +281,42 @@ pam_status pam_eval(const pam_problem *prob, const pam_plan *plan,
                     const pam_model *model, const double *d_pts, int64_t n_pts,
                     double *d_out, int log_space, int precision, void *d_workspace,
                     size_t workspace_bytes, void *stream);
+
+/*
+ * Glued evaluation (section 2, Step 4 remark: the piecewise surrogate of
+ * pam_eval is discontinuous across subdomain interfaces, and a gluing or
+ * averaging of neighbouring local surrogates makes it continuous; the paper
+ * leaves the procedure open, this is the one here). The local log-surrogates
+ * u_i(x) = sum_m beta_m w_m(x) of Eq. (9) are blended by a tensor-product
+ * partition of unity that ramps across every interior core face over a band
+ * of half-width delta = band * h:
+ *   psi_i(x) = prod_a r((x_a - lo_a + delta) / (2 delta)) r((hi_a + delta - x_a) / (2 delta))
+ * with r(t) = t^2 (3 - 2 t) on [0, 1] (clamped outside; r(t) + r(1 - t) = 1)
+ * and a factor of 1 at the outer faces of the grid; then
+ *   ln K*(x) = sum_i psi_i(x) u_i(x) / sum_i psi_i(x).
+ * Farther than delta from every interior face this equals pam_eval; the
+ * result is continuous (C^1 in the weights) across the interfaces.
+ *   band        half-width of the ramp in cells, 0 < band <= half the
+ *               narrowest core of any axis with more than one subdomain
+ *               (then at most 2^dim subdomains carry weight at a point);
+ *               PAM_ERR_INVALID_ARG otherwise
+ *   d_pts       device double [n_pts][dim]; d_out device double [n_pts]:
+ *               K*(x), or ln K*(x) when log_space != 0; NaN outside the grid
+ *   precision   PAM_PREC_FP64 (binary64 throughout) or PAM_PREC_MIXED (the
+ *               local surrogates in fp32 as in pam_eval, the blend in
+ *               binary64, the final exp in fp32)
+ *   d_workspace at least pam_eval_glued_workspace_size bytes (2^dim
+ *               (point, subdomain) slots per point: 16 bytes each, plus 8
+ *               per subdomain)
+ * The per-point sum runs over the subdomains in ascending index order
+ * (deterministic). PAM_ERR_UNSUPPORTED above (2^31 - 1) / 2^dim points.
+ * Asynchronous (no synchronisation); n_pts == 0 is a no-op.
+ */
+pam_status pam_eval_glued_workspace_size(const pam_problem *prob, const pam_plan *plan, int64_t n_pts,
+                                         size_t *bytes);
+pam_status pam_eval_glued(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
+                          const double *d_pts, int64_t n_pts, double band, double *d_out, int log_space,
+                          int precision, void *d_workspace, size_t workspace_bytes, void *stream);
 
 /*
  * Relative errors of the reconstruction over the source cells, each cell

@@ -487,6 +487,54 @@ pam_status pam_eval(const pam_problem *prob, const pam_plan *plan, const pam_mod
     return PAM_OK;
 }
 
+// Largest band (in cells) the glued evaluation accepts: half the narrowest
+// core along every axis that has an interior face.
+static double glue_band_limit(const Geo &g) {
+    double lim = INFINITY;
+    for (int a = 0; a < g.dim; ++a) {
+        if (g.p[a] < 2) continue;
+        for (int j = 0; j < g.p[a]; ++j) {
+            int64_t lo = ((int64_t)j * g.n[a]) / g.p[a], hi = ((int64_t)(j + 1) * g.n[a]) / g.p[a];
+            lim = fmin(lim, 0.5 * (double)(hi - lo));
+        }
+    }
+    return lim;
+}
+
+pam_status pam_eval_glued_workspace_size(const pam_problem *prob, const pam_plan *plan, int64_t n_pts,
+                                         size_t *bytes) {
+    Geo g;
+    pam_status st;
+    if (!make_geo(prob, nullptr, &g, nullptr, &st)) return st;
+    if (!plan || !bytes || n_pts < 0 || plan->n_subdomains != g.S) return PAM_ERR_INVALID_ARG;
+    if (n_pts > ((int64_t)INT32_MAX >> g.dim)) return PAM_ERR_UNSUPPORTED;
+    *bytes = glue_workspace_bytes(g.S, g.dim, n_pts);
+    return PAM_OK;
+}
+
+pam_status pam_eval_glued(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
+                          const double *d_pts, int64_t n_pts, double band, double *d_out, int log_space,
+                          int precision, void *d_workspace, size_t workspace_bytes, void *stream) {
+    Geo g;
+    pam_status st;
+    if (!make_geo(prob, nullptr, &g, nullptr, &st)) return st;
+    if (!plan || plan->n_subdomains != g.S || plan->m_cap > PAM_MAX_M || plan->m_cap < 1)
+        return PAM_ERR_INVALID_ARG;
+    g.m_cap = plan->m_cap;
+    g.n_max = plan->max_patch_cells;
+    if (n_pts < 0 || !model_ok(model)) return PAM_ERR_INVALID_ARG;
+    if (precision != PAM_PREC_FP64 && precision != PAM_PREC_MIXED) return PAM_ERR_INVALID_ARG;
+    if (!(band > 0.0) || !std::isfinite(band) || band > glue_band_limit(g)) return PAM_ERR_INVALID_ARG;
+    if (n_pts > ((int64_t)INT32_MAX >> g.dim)) return PAM_ERR_UNSUPPORTED;
+    if (n_pts == 0) return PAM_OK;
+    if (!d_pts || !d_out || !d_workspace) return PAM_ERR_INVALID_ARG;
+    if (workspace_bytes < glue_workspace_bytes(g.S, g.dim, n_pts)) return PAM_ERR_WORKSPACE;
+    launch_eval_glued(g, model->boxes, model->centres, model->beta, model->info, d_pts, n_pts, band, d_out,
+                      log_space, precision, d_workspace, (cudaStream_t)stream);
+    PAM_CUDA_TRY(cudaGetLastError());
+    return PAM_OK;
+}
+
 pam_status pam_errors(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
                       const double *d_K, double *d_err, int precision, int quad, void *d_workspace,
                       size_t workspace_bytes, void *stream) {

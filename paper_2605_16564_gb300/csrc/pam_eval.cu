@@ -290,6 +290,300 @@ void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, cons
 }
 
 // --------------------------------------------------------------------------
+// Glued evaluation across subdomain interfaces (section 2, Step 4 remark:
+// the piecewise surrogate jumps at the interfaces; a gluing of neighbouring
+// local surrogates makes it continuous, the procedure left open). The local
+// log-surrogates u_i = sum_m beta_m w_m are blended by a tensor-product
+// partition of unity that ramps across every interior core face over a band
+// of half-width delta = band * h:
+//   psi_i(x) = prod_a r((x_a - lo_a + delta) / (2 delta)) r((hi_a + delta - x_a) / (2 delta)),
+//   r(t) = t^2 (3 - 2 t) on [0, 1], clamped (r(t) + r(1 - t) = 1), a factor
+//   of 1 at the outer faces of the grid, and
+//   ln K*(x) = sum_i psi_i u_i / sum_i psi_i.
+// With band <= half the narrowest core, at most two cores per axis carry
+// weight at a point, so a point has at most 2^dim (point, subdomain) pairs,
+// slot p * 2^dim + c with bit a of c choosing the lower (0) or upper (1)
+// candidate along axis a; ascending c is ascending subdomain index.
+// Pairs are bucketed by subdomain like the points of pam_eval (counts,
+// scan, scatter); one block per subdomain evaluates u_i at its pairs into
+// val[slot]; a last pass sums psi_i u_i over each point's pairs in slot
+// order (deterministic) and divides by sum psi_i.
+// --------------------------------------------------------------------------
+struct GlueWs {
+    int32_t *rank, *perm, *count, *start, *sub;
+    double *val, *psi;
+    uint8_t *mask;
+    size_t bytes;
+};
+
+GlueWs carve_glue_workspace(int S, int dim, int64_t n, void *base) {
+    GlueWs e;
+    size_t off = 0;
+    const size_t slots = (size_t)n << dim;
+    auto take = [&](size_t bytes) -> void * {
+        void *p = base ? (void *)((char *)base + off) : nullptr;
+        off = align256(off + bytes);
+        return p;
+    };
+    e.val = (double *)take(slots * 8);
+    e.psi = (double *)take(slots * 8);
+    e.rank = (int32_t *)take(slots * 4);
+    e.perm = (int32_t *)take(slots * 4);
+    e.sub = (int32_t *)take(slots * 4);
+    e.mask = (uint8_t *)take((size_t)n);
+    e.count = (int32_t *)take((size_t)S * 4);
+    e.start = (int32_t *)take((size_t)(S + 1) * 4);
+    e.bytes = off;
+    return e;
+}
+
+size_t glue_workspace_bytes(int S, int dim, int64_t n_pts) {
+    return carve_glue_workspace(S, dim, n_pts, nullptr).bytes;
+}
+
+__device__ __forceinline__ double glue_ramp(double t) {
+    t = fmin(fmax(t, 0.0), 1.0);
+    return __dmul_rn(__dmul_rn(t, t), __dsub_rn(3.0, __dmul_rn(2.0, t)));
+}
+
+// Face factors of core c along an axis at coordinate xa: the lower face's
+// ramp (1 at the outer face) and the upper face's.
+__device__ __forceinline__ void glue_factors(int c, int n, int p, double h, double delta, double two_d,
+                                             double xa, double *l, double *r) {
+    const int64_t lo = ((int64_t)c * n) / p, hi = ((int64_t)(c + 1) * n) / p;
+    *l = c > 0 ? glue_ramp(__ddiv_rn(__dadd_rn(__dsub_rn(xa, __dmul_rn((double)lo, h)), delta), two_d)) : 1.0;
+    *r = c < p - 1 ? glue_ramp(__ddiv_rn(__dsub_rn(__dadd_rn(__dmul_rn((double)hi, h), delta), xa), two_d)) : 1.0;
+}
+
+// The pairs of point x: subdomain s[c] and weight psi[c] for the valid slots
+// c (bit c of the returned mask). Mask 0: x lies outside the grid. Along
+// each axis the owner core j carries weight, and so does at most one of its
+// neighbours (j - 1 below it or j + 1 above it; when band <= half the
+// narrowest core both can carry weight only by rounding at a ramp's end,
+// weight below 2^-100, and the larger is kept). Candidate 0 is the lower
+// core, so ascending c is ascending subdomain index. The weight multiplies
+// the face factors axis by axis, lower face first, in unfused binary64.
+template <int D>
+__device__ __forceinline__ unsigned glue_pairs(const Geo &g, double delta, const double x[3], int s[8],
+                                               double psi[8]) {
+    const double two_d = 2.0 * delta;
+    int c0[3] = {0, 0, 0}, c1[3] = {0, 0, 0}, cnt[3] = {1, 1, 1};
+    double l0[3] = {1.0, 1.0, 1.0}, r0[3] = {1.0, 1.0, 1.0}, l1[3] = {1.0, 1.0, 1.0}, r1[3] = {1.0, 1.0, 1.0};
+    bool inside = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const double u = x[a] * (double)g.nmax;
+        const bool in_a = (u >= 0.0) && (u <= (double)g.n[a]);
+        inside = inside && in_a;
+        int i = in_a ? (int)floor(u) : 0;
+        if (i >= g.n[a]) i = g.n[a] - 1;
+        const int j = core_of(i, g.n[a], g.p[a]);
+        // at least delta from both faces of the owner core (or at an outer
+        // face): the owner's factors are exactly 1 and the neighbours' 0 up
+        // to rounding (below 2^-100), so the ramps are not evaluated
+        const int64_t lo = ((int64_t)j * g.n[a]) / g.p[a], hi = ((int64_t)(j + 1) * g.n[a]) / g.p[a];
+        const bool far_lo = j == 0 || __dsub_rn(x[a], __dmul_rn((double)lo, g.h)) >= delta;
+        const bool far_hi = j == g.p[a] - 1 || __dsub_rn(__dmul_rn((double)hi, g.h), x[a]) >= delta;
+        if (far_lo && far_hi) {
+            c0[a] = j;
+        } else {
+            double lj, rj, lm = 0.0, rm = 0.0, lp = 0.0, rp = 0.0;
+            glue_factors(j, g.n[a], g.p[a], g.h, delta, two_d, x[a], &lj, &rj);
+            if (!far_lo) glue_factors(j - 1, g.n[a], g.p[a], g.h, delta, two_d, x[a], &lm, &rm);
+            if (!far_hi) glue_factors(j + 1, g.n[a], g.p[a], g.h, delta, two_d, x[a], &lp, &rp);
+            const double wm = __dmul_rn(lm, rm), wp = __dmul_rn(lp, rp);
+            bool use_m = wm > 0.0, use_p = wp > 0.0;
+            if (use_m && use_p) {
+                use_m = wm >= wp;
+                use_p = !use_m;
+            }
+            c0[a] = use_m ? j - 1 : j;
+            l0[a] = use_m ? lm : lj;
+            r0[a] = use_m ? rm : rj;
+            c1[a] = use_m ? j : j + 1;
+            l1[a] = use_m ? lj : lp;
+            r1[a] = use_m ? rj : rp;
+            cnt[a] = (use_m || use_p) ? 2 : 1;
+        }
+    }
+    unsigned mask = 0u;
+#pragma unroll
+    for (int c = 0; c < (1 << D); ++c) {
+        int idx = 0, mul = 1;
+        double w = 1.0;
+        bool ok = inside;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const bool up = (c >> a) & 1;
+            ok = ok && (!up || cnt[a] == 2);
+            w = __dmul_rn(w, up ? l1[a] : l0[a]);
+            w = __dmul_rn(w, up ? r1[a] : r0[a]);
+            idx += (up ? c1[a] : c0[a]) * mul;
+            mul *= g.p[a];
+        }
+        ok = ok && w > 0.0;
+        s[c] = ok ? idx : 0;
+        psi[c] = ok ? w : 0.0;
+        mask |= ok ? (1u << c) : 0u;
+    }
+    return mask;
+}
+
+__device__ __forceinline__ void load_point(const Geo &g, const double *pts, int64_t p, double x[3]) {
+    x[0] = x[1] = x[2] = 0.0;
+    for (int a = 0; a < g.dim; ++a) x[a] = pts[p * g.dim + a];
+}
+
+template <int D>
+__global__ void k_glue_count(Geo g, double delta, const double *pts, int64_t n, int32_t *rank,
+                             int32_t *count, double *out, GlueWs e) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    int s[8];
+    double psi[8];
+    unsigned mask = 0u;
+    if (p < n) {
+        double x[3];
+        load_point(g, pts, p, x);
+        mask = glue_pairs<D>(g, delta, x, s, psi);
+        if (mask == 0u) out[p] = nan("");
+        e.mask[p] = (uint8_t)mask;
+    }
+    constexpr int nslot = 1 << D;
+    const int lane = threadIdx.x & 31;
+#pragma unroll
+    for (int c = 0; c < nslot; ++c) {  // uniform across the warp
+        const bool have = (mask >> c) & 1u;
+        const int key = have ? s[c] : -2;
+        const unsigned peers = __match_any_sync(0xffffffffu, key);
+        const int leader = __ffs(peers) - 1;
+        int base = 0;
+        if (lane == leader && have) base = atomicAdd(&count[key], __popc(peers));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (have) {
+            rank[p * nslot + c] = base + __popc(peers & ((1u << lane) - 1u));
+            e.sub[p * nslot + c] = key;
+            e.psi[p * nslot + c] = psi[c];
+        }
+    }
+}
+
+template <int D>
+__global__ void k_glue_scatter(int64_t n, const int32_t *start, GlueWs e) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const unsigned mask = e.mask[p];
+    constexpr int nslot = 1 << D;
+#pragma unroll
+    for (int c = 0; c < nslot; ++c)
+        if ((mask >> c) & 1u) {
+            const int64_t slot = p * nslot + c;
+            e.perm[start[e.sub[slot]] + e.rank[slot]] = (int32_t)slot;
+        }
+}
+
+__global__ void k_glue_bucket_f64(Geo g, const double *centres, const double *beta, const int32_t *info,
+                                  const double *pts, const int32_t *perm, const int32_t *start, double *val) {
+    const int s = blockIdx.x;
+    const int b = start[s], e = start[s + 1];
+    if (b == e) return;
+    const int M = info[s * kInfoN + PAM_INFO_M];
+    extern __shared__ uint8_t smb[];
+    dvec4 *sc = reinterpret_cast<dvec4 *>(smb);
+    double *sb = reinterpret_cast<double *>(sc + g.m_cap);
+    stage_f64(g, centres, beta, s, M, sc, sb);
+    for (int i = b + threadIdx.x; i < e; i += blockDim.x) {
+        const int slot = perm[i];
+        double x[3];
+        load_point(g, pts, (int64_t)(slot >> g.dim), x);
+        val[slot] = shepard_f64_smem(sc, sb, M, x);
+    }
+}
+
+__global__ void k_glue_bucket_f32(Geo g, const int32_t *boxes, const double *centres, const double *beta,
+                                  const int32_t *info, const double *pts, const int32_t *perm,
+                                  const int32_t *start, double *val) {
+    const int s = blockIdx.x;
+    const int b = start[s], e = start[s + 1];
+    if (b == e) return;
+    const int M = info[s * kInfoN + PAM_INFO_M];
+    extern __shared__ uint8_t smb[];
+    float4 *sc = reinterpret_cast<float4 *>(smb);
+    float *sb = reinterpret_cast<float *>(sc + g.m_cap);
+    double o[3];
+    stage_f32(g, boxes, centres, beta, s, M, sc, sb, o);
+    for (int i = b + threadIdx.x; i < e; i += 2 * blockDim.x) {
+        const int i1 = i + blockDim.x;
+        const bool two = i1 < e;
+        const int q0 = perm[i], q1 = two ? perm[i1] : q0;
+        const int64_t p0 = q0 >> g.dim, p1 = q1 >> g.dim;
+        float x0[3] = {0.f, 0.f, 0.f}, x1[3] = {0.f, 0.f, 0.f};
+        for (int a = 0; a < g.dim; ++a) {
+            x0[a] = (float)(pts[p0 * g.dim + a] - o[a]);
+            x1[a] = (float)(pts[p1 * g.dim + a] - o[a]);
+        }
+        float v0, v1;
+        shepard_f32_smem2(sc, sb, M, x0, x1, &v0, &v1);
+        val[q0] = (double)v0;
+        if (two) val[q1] = (double)v1;
+    }
+}
+
+template <int D, bool F32>
+__global__ void k_glue_combine(int64_t n, GlueWs e, double *out, int log_space) {
+    const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (p >= n) return;
+    const unsigned mask = e.mask[p];
+    if (mask == 0u) return;  // NaN written by k_glue_count
+    constexpr int nslot = 1 << D;
+    double num = 0.0, den = 0.0;
+#pragma unroll
+    for (int c = 0; c < nslot; ++c)
+        if ((mask >> c) & 1u) {
+            const double w = e.psi[p * nslot + c];
+            num = __dadd_rn(num, __dmul_rn(w, e.val[p * nslot + c]));
+            den = __dadd_rn(den, w);
+        }
+    const double v = num / den;
+    out[p] = log_space ? v : (F32 ? exp_f32((float)v) : exp(v));
+}
+
+template <int D>
+static void glue_launches(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
+                          const int32_t *info, const double *pts, int64_t n_pts, double delta, double *out,
+                          int log_space, int precision, const GlueWs &e, cudaStream_t st) {
+    const unsigned nb = (unsigned)((n_pts + 255) / 256);
+    k_glue_count<D><<<nb, 256, 0, st>>>(g, delta, pts, n_pts, e.rank, e.count, out, e);
+    k_eval_scan<<<1, 1024, 0, st>>>(e.count, e.start, g.S);
+    k_glue_scatter<D><<<nb, 256, 0, st>>>(n_pts, e.start, e);
+    if (precision == PAM_PREC_MIXED) {
+        size_t sm = (size_t)g.m_cap * (sizeof(float4) + sizeof(float));
+        k_glue_bucket_f32<<<g.S, 256, sm, st>>>(g, boxes, centres, beta, info, pts, e.perm, e.start, e.val);
+        k_glue_combine<D, true><<<nb, 256, 0, st>>>(n_pts, e, out, log_space);
+    } else {
+        size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));
+        cudaFuncSetAttribute(k_glue_bucket_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_glue_bucket_f64<<<g.S, 256, sm, st>>>(g, centres, beta, info, pts, e.perm, e.start, e.val);
+        k_glue_combine<D, false><<<nb, 256, 0, st>>>(n_pts, e, out, log_space);
+    }
+}
+
+void launch_eval_glued(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
+                       const int32_t *info, const double *pts, int64_t n_pts, double band, double *out,
+                       int log_space, int precision, void *ws, cudaStream_t st) {
+    PhaseScope ps(kPhEval, st);
+    GlueWs e = carve_glue_workspace(g.S, g.dim, n_pts, ws);
+    const double delta = band * g.h;
+    cudaMemsetAsync(e.count, 0, (size_t)g.S * sizeof(int32_t), st);
+    if (g.dim == 1)
+        glue_launches<1>(g, boxes, centres, beta, info, pts, n_pts, delta, out, log_space, precision, e, st);
+    else if (g.dim == 2)
+        glue_launches<2>(g, boxes, centres, beta, info, pts, n_pts, delta, out, log_space, precision, e, st);
+    else
+        glue_launches<3>(g, boxes, centres, beta, info, pts, n_pts, delta, out, log_space, precision, e, st);
+    count_launches(5);
+}
+
+// --------------------------------------------------------------------------
 // Errors over the source cells: one block per owner sweeps its core cells
 // (each cell measured with its owner's surrogate at the centroid) and writes
 // seven fp64 partial sums; one thread combines the S rows in order.

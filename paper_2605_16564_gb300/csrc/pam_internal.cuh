@@ -102,6 +102,10 @@ void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, cons
                  const int32_t *info, const double *pts, int64_t n_pts, double *out, int log_space,
                  int precision, void *ws, cudaStream_t st);
 size_t eval_workspace_bytes(int S, int64_t n_pts);
+void launch_eval_glued(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
+                       const int32_t *info, const double *pts, int64_t n_pts, double band, double *out,
+                       int log_space, int precision, void *ws, cudaStream_t st);
+size_t glue_workspace_bytes(int S, int dim, int64_t n_pts);
 void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
                    const int32_t *info, const double *K, double *err, int precision, int quad,
                    const Ws &w, cudaStream_t st);

@@ -33,7 +33,8 @@ STATUS = {0: "PAM_OK", 1: "PAM_ERR_INVALID_ARG", 2: "PAM_ERR_NONPOSITIVE_K", 3: 
 
 EXPORTED = ["pam_version", "pam_status_string", "pam_plan_create", "pam_partition",
             "pam_fit_subdomains", "pam_refine", "pam_gram", "pam_eval_workspace_size", "pam_eval",
-            "pam_errors", "pam_status_read", "pam_lambda_cv_workspace_size", "pam_lambda_cv"]
+            "pam_errors", "pam_status_read", "pam_lambda_cv_workspace_size", "pam_lambda_cv",
+            "pam_eval_glued_workspace_size", "pam_eval_glued"]
 
 
 class PamError(RuntimeError):
@@ -94,6 +95,10 @@ def lib():
         L.pam_eval_workspace_size.argtypes = [P(pam_plan), C.c_int64, P(C.c_size_t)]
         L.pam_eval.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_int64,
                                C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_eval_glued_workspace_size.argtypes = [P(pam_problem), P(pam_plan), C.c_int64, P(C.c_size_t)]
+        L.pam_eval_glued.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_int64,
+                                     C.c_double, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t,
+                                     C.c_void_p]
         L.pam_errors.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_void_p,
                                  C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_gram.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), C.c_void_p, P(pam_model),
@@ -117,7 +122,7 @@ def lib():
                                          C.c_void_p, C.c_void_p]
         for name in ("pam_plan_create", "pam_partition", "pam_fit_subdomains", "pam_refine",
                      "pam_eval", "pam_errors", "pam_errors_noalloc", "pam_gram",
-                     "pam_eval_workspace_size"):
+                     "pam_eval_workspace_size", "pam_eval_glued", "pam_eval_glued_workspace_size"):
             getattr(L, name).restype = C.c_int
         _lib = L
     return _lib
@@ -247,6 +252,24 @@ def pam_eval(problem, plan, model, pts, out, log_space=False, precision=PAM_PREC
     _check(lib().pam_eval(C.byref(problem), C.byref(plan), C.byref(model.c_struct()), _ptr(pts),
                           int(n), _ptr(out), int(bool(log_space)), int(precision), _ptr(workspace),
                           nbytes, _stream(stream)), "pam_eval")
+
+
+def pam_eval_glued_workspace_size(problem, plan, n_pts):
+    n = C.c_size_t(0)
+    _check(lib().pam_eval_glued_workspace_size(C.byref(problem), C.byref(plan), int(n_pts), C.byref(n)),
+           "pam_eval_glued_workspace_size")
+    return n.value
+
+
+def pam_eval_glued(problem, plan, model, pts, out, band, log_space=False, precision=PAM_PREC_FP64,
+                   workspace=None, stream=None):
+    """K*(x) blended across subdomain interfaces over a ramp of half-width
+    band cells (0 < band <= half the narrowest core)."""
+    n = pts.shape[0] if pts is not None else 0
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().pam_eval_glued(C.byref(problem), C.byref(plan), C.byref(model.c_struct()), _ptr(pts),
+                                int(n), float(band), _ptr(out), int(bool(log_space)), int(precision),
+                                _ptr(workspace), nbytes, _stream(stream)), "pam_eval_glued")
 
 
 def pam_errors(problem, plan, model, K, err, workspace, precision=PAM_PREC_FP64, stream=None, quad=0):
@@ -427,6 +450,20 @@ class Fitter:
         prec = self.params.precision if precision is None else precision
         pam_eval(self.problem, self.plan, self.model, pts, out, log_space, prec,
                  self.eval_workspace(pts.shape[0]), stream)
+        return out
+
+    def eval_glued(self, pts, band, out=None, log_space=False, precision=None, stream=None):
+        """K*(x) blended across the subdomain interfaces (pam_eval_glued)."""
+        import torch
+        if out is None:
+            out = torch.empty(pts.shape[0], dtype=torch.float64, device=pts.device)
+        prec = self.params.precision if precision is None else precision
+        need = pam_eval_glued_workspace_size(self.problem, self.plan, pts.shape[0])
+        ws = getattr(self, "_glue_ws", None)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+            self._glue_ws = ws
+        pam_eval_glued(self.problem, self.plan, self.model, pts, out, band, log_space, prec, ws, stream)
         return out
 
     def errors(self, K, precision=None, stream=None, quad=None):

@@ -162,3 +162,34 @@ def test_layered_inputs_reject_unsupported_problems(pam):
     pr3 = pam.make_problem((40, 20, 10), (1, 1, 1), 0, (4, 4, 2))
     plan3 = pam.pam_plan_create(pr3, pam.make_params())
     assert L.pam_nn_layered_inputs(C.byref(pr3), C.byref(plan3), C.c_void_p(8), C.c_void_p(8), 32, None) == 6
+
+
+def test_eval_glued_checks_the_band_and_sizes(pam):
+    import ctypes as C
+    fake = C.c_void_p(256)  # never dereferenced: validation fails first
+    for n_cells, n_sub, good, bad in [((64, 64), (4, 4), 8.0, 8.01),      # cores of 16
+                                      ((37, 23), (4, 3), 3.5, 3.6),       # narrowest core 7
+                                      ((24, 44, 17), (3, 4, 2), 4.0, 4.5),
+                                      ((50,), (1,), 1e6, float("inf"))]:  # no interior face
+        pr = pam.make_problem(n_cells, n_sub, 1, (2,) * len(n_cells))
+        plan = pam.pam_plan_create(pr, pam.make_params())
+        m = pam.pam_model(fake, fake, fake, fake)
+        L = pam.lib()
+        for band, want in [(bad, 1), (0.0, 1), (-1.0, 1), (float("nan"), 1)]:
+            code = L.pam_eval_glued(C.byref(pr), C.byref(plan), C.byref(m), fake, 10, band, fake, 0, 0,
+                                    fake, 1 << 40, None)
+            assert code == want, (n_cells, band, code)
+        # a valid band with no points enqueues nothing and succeeds
+        assert L.pam_eval_glued(C.byref(pr), C.byref(plan), C.byref(m), None, 0, good, None, 0, 0,
+                                None, 0, None) == 0
+        # a valid band with a short workspace
+        assert L.pam_eval_glued(C.byref(pr), C.byref(plan), C.byref(m), fake, 10, good, fake, 0, 0,
+                                fake, 16, None) == 4
+        assert L.pam_eval_glued(C.byref(pr), C.byref(plan), C.byref(m), fake, 10, good, fake, 0, 7,
+                                fake, 1 << 40, None) == 1  # unknown precision
+        n = pam.pam_eval_glued_workspace_size(pr, plan, 1000)
+        assert n >= 1000 * (1 << len(n_cells)) * 16
+        dim = len(n_cells)
+        too_many = ((1 << 31) - 1) // (1 << dim) + 1
+        assert L.pam_eval_glued_workspace_size(C.byref(pr), C.byref(plan), too_many,
+                                               C.byref(C.c_size_t(0))) == 6
