@@ -50,6 +50,13 @@ WORKLOADS = {
     "voronoi2d": dict(shape=(256, 256), n_sub=(8, 8), overlap=2, g=(8, 8),
                       params=dict(k_top=37, levels=3), eval_counts=(384, 384),
                       field=lambda seed: fields.voronoi_field(256, seed=seed), seed=2),
+    # the channel workload on an unstructured mesh: every square of the
+    # 1024 x 1024 grid cut along a seeded random diagonal into two triangles
+    # (2,097,152 elements), each triangle carrying its square's value
+    "triangles2d": dict(shape=(1024, 1024), n_sub=(32, 32), overlap=2, g=(8, 8),
+                        params=dict(k_top=37, levels=3), eval_counts=(1536, 1536),
+                        field=lambda seed: fields.channel_field(1024, seed=seed), seed=3,
+                        mesh="triangles", mesh_seed=31, cpu_sample=32),
     "disc2d": dict(shape=(64, 64), n_sub=(1, 1), overlap=0, g=(16, 16),
                    params=dict(k_top=51, levels=2), eval_counts=(97, 97),
                    field=lambda seed: fields.disc_field(64), seed=0),
@@ -168,8 +175,13 @@ def accounting(fit, Kd, levels, pam, seed=None):
             if seed is not None:
                 seed()
                 fit.params.warm_start = 1
-            pam.pam_fit_subdomains(fit.problem, fit.params, fit.plan, Kd, fit.model, fit.workspace)
+            if getattr(fit, "cells", None) is not None:
+                pam.pam_fit_cells(fit.problem, fit.params, fit.plan, fit.cells, Kd, fit.model, fit.workspace)
+            else:
+                pam.pam_fit_subdomains(fit.problem, fit.params, fit.plan, Kd, fit.model, fit.workspace)
             fit.params.warm_start = 0
+        elif getattr(fit, "cells", None) is not None:
+            pam.pam_refine_cells(fit.problem, fit.params, fit.plan, fit.cells, Kd, fit.model, 1, fit.workspace)
         else:
             pam.pam_refine(fit.problem, fit.params, fit.plan, Kd, fit.model, 1, fit.workspace)
         info = fit.model.info.cpu().numpy()
@@ -253,6 +265,22 @@ def attach_traffic(roofs, workload):
     return roofs
 
 
+def workload_data(W, seed):
+    """(K, x, vol): the cell values of the workload and, for a mesh given as
+    cells, the element sampling points and measures (else None, None)."""
+    K = W["field"](seed)
+    if W.get("mesh") == "triangles":
+        x, vol = fields.triangle_mesh(W["shape"][0], seed=W["mesh_seed"], ny=W["shape"][1])
+        return np.repeat(np.ascontiguousarray(K).reshape(-1), 2), x, vol
+    return K, None, None
+
+
+def make_fitter(pam, W, x, vol, dev, **params):
+    if x is not None:
+        return pam.CellFitter(W["shape"], W["n_sub"], W["overlap"], W["g"], x, vol, device=dev, **params)
+    return pam.Fitter(W["shape"], W["n_sub"], W["overlap"], W["g"], device=dev, **params)
+
+
 def run_pam(args, rank, ws):
     import torch
     from paper_2605_16564_gb300 import build, pam
@@ -261,12 +289,12 @@ def run_pam(args, rank, ws):
     dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
     torch.cuda.set_device(dev)
     W = WORKLOADS[args.workload]
-    K = W["field"](shard_seed(W["seed"], rank))
+    K, x_el, vol_el = workload_data(W, shard_seed(W["seed"], rank))
     shape = W["shape"]
     h = fields.cell_size(shape)
     extent = [n * h for n in shape]
     pts = fields.cell_centred_points(W["eval_counts"], extent)
-    n_cells = int(np.prod(shape))
+    n_cells = int(np.asarray(K).size)  # grid cells, or the elements of a mesh given as cells
     n_pts = pts.shape[0]
 
     prec_name = args.precision
@@ -274,8 +302,7 @@ def run_pam(args, rank, ws):
         prec_name = "mixed" if _mixed_available(pam) else "fp64"
     prec = pam.PAM_PREC_MIXED if prec_name == "mixed" else pam.PAM_PREC_FP64
 
-    fit = pam.Fitter(shape, W["n_sub"], W["overlap"], W["g"], device=dev, precision=prec, quad=args.quad,
-                     **W["params"])
+    fit = make_fitter(pam, W, x_el, vol_el, dev, precision=prec, quad=args.quad, **W["params"])
     Kd = torch.from_numpy(np.ascontiguousarray(K)).to(dev)
     ptsd = torch.from_numpy(pts).to(dev)
     out = torch.empty(n_pts, dtype=torch.float64, device=dev)
@@ -521,8 +548,7 @@ def run_pam(args, rank, ws):
     # --- the plain binary64 form, for the chosen-vs-plain ratio -------------
     plain = None
     if prec == pam.PAM_PREC_MIXED and not args.skip_plain:
-        pf = pam.Fitter(shape, W["n_sub"], W["overlap"], W["g"], device=dev,
-                        precision=pam.PAM_PREC_FP64, quad=args.quad, **W["params"])
+        pf = make_fitter(pam, W, x_el, vol_el, dev, precision=pam.PAM_PREC_FP64, quad=args.quad, **W["params"])
         pf.fit(Kd)
         torch.cuda.synchronize()
         e0 = torch.cuda.Event(enable_timing=True)
@@ -661,6 +687,11 @@ def glue_pairs_per_point(W, pts, band):
 
 def owner_counts(W, pts):
     """Target points per owner subdomain (half-open cores, outer face closed)."""
+    return np.bincount(owner_index(W, pts), minlength=int(np.prod(W["n_sub"]))).astype(float)
+
+
+def owner_index(W, pts):
+    """Owner subdomain of each point (half-open cores, outer face closed)."""
     shape, n_sub = W["shape"], W["n_sub"]
     nmax = max(shape)
     idx = []
@@ -675,7 +706,7 @@ def owner_counts(W, pts):
     for a in range(1, len(shape)):
         s = s + stride * idx[a]
         stride *= n_sub[a]
-    return np.bincount(s, minlength=int(np.prod(n_sub))).astype(float)
+    return s
 
 
 def _mixed_available(pam):
@@ -692,7 +723,7 @@ def oracle_sample(workload: str, n_sub_sample: int, seed_offset=0):
     the workload (fit + evaluation of the target points inside their cores)."""
     import oracle
     W = WORKLOADS[workload]
-    K = W["field"](W["seed"] + seed_offset)
+    K, x_el, vol_el = workload_data(W, W["seed"] + seed_offset)
     shape = W["shape"]
     S = int(np.prod(W["n_sub"]))
     which = np.unique(np.linspace(0, S - 1, min(n_sub_sample, S)).astype(np.int32))
@@ -709,10 +740,16 @@ def oracle_sample(workload: str, n_sub_sample: int, seed_offset=0):
         g = np.meshgrid(*reversed(axes), indexing="ij")
         pts.append(np.stack([x.reshape(-1) for x in reversed(g)], axis=1))
     pts = np.concatenate(pts)
-    cells = int(np.prod(boxes[which, 3:6] - boxes[which, 0:3], axis=1).sum())
-    t0 = time.perf_counter()
-    model = oracle.fit_all(K, shape, W["n_sub"], W["overlap"], W["g"],
-                           oracle.default_params(**W["params"]), which=which)
+    if x_el is not None:
+        cells = int(np.isin(owner_index(W, x_el), which).sum())  # elements owned by the sample
+        t0 = time.perf_counter()
+        model = oracle.fit_cells(x_el, vol_el, K, shape, W["n_sub"], W["overlap"], W["g"],
+                                 oracle.default_params(**W["params"]), which=which)
+    else:
+        cells = int(np.prod(boxes[which, 3:6] - boxes[which, 0:3], axis=1).sum())
+        t0 = time.perf_counter()
+        model = oracle.fit_all(K, shape, W["n_sub"], W["overlap"], W["g"],
+                               oracle.default_params(**W["params"]), which=which)
     oracle.evaluate(model, pts)
     dt = time.perf_counter() - t0
     cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
@@ -727,7 +764,8 @@ def main():
     ap.add_argument("--impl", default="pam", choices=["pam", "reference"])
     ap.add_argument("--precision", default="auto", choices=["auto", "fp64", "mixed"])
     ap.add_argument("--workload", default="layered3d", choices=sorted(WORKLOADS))
-    ap.add_argument("--cpu-sample", type=int, default=192, help="subdomains in the oracle baseline sample")
+    ap.add_argument("--cpu-sample", type=int, default=None,
+                    help="subdomains in the oracle baseline sample (default: 192, 32 on the triangle mesh)")
     ap.add_argument("--skip-plain", action="store_true")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="3-D mixed form without the learned warm start")
@@ -741,11 +779,16 @@ def main():
     args = ap.parse_args()
     rank, ws = _dist()
     W = WORKLOADS[args.workload]
+    if args.cpu_sample is None:
+        args.cpu_sample = W.get("cpu_sample", 192)
     cfg = {"workload": f"{args.workload} {'x'.join(map(str, W['shape']))} cells, "
                        f"{'x'.join(map(str, W['n_sub']))} subdomains, overlap {W['overlap']}, "
                        f"{'x'.join(map(str, W['g']))} initial centres, {W['params']['levels']} levels, "
-                       f"eval {'x'.join(map(str, W['eval_counts']))}",
-           "cells_per_step": int(np.prod(W["shape"])), "eval_pts_per_step": int(np.prod(W["eval_counts"])),
+                       f"eval {'x'.join(map(str, W['eval_counts']))}"
+                       + (", triangle mesh (each square cut in two, 2 elements per cell)"
+                          if W.get("mesh") == "triangles" else ""),
+           "cells_per_step": int(np.prod(W["shape"])) * (2 if W.get("mesh") == "triangles" else 1),
+           "eval_pts_per_step": int(np.prod(W["eval_counts"])),
            "l2_flush": "256 MB buffer written between timed steps", "parallelism": f"replicas{ws}"}
 
     if ws > 1:

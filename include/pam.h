@@ -360,6 +360,67 @@ pam_status pam_errors_noalloc(const pam_problem *prob, const pam_plan *plan,
                               void *stream);
 
 /*
+ * General meshes given as cells (section 2: the data are piecewise constant
+ * on the elements T of a shape-regular partition -- intervals, triangles,
+ * quadrilaterals, ... -- each with a sampling point x_T in T, e.g. its
+ * centroid, a value K_T and a measure |T|). The problem's grid fields
+ * (n_cells, n_sub, overlap, g_init) keep their meaning for the domain and
+ * its decomposition only: the domain is the box [0, n_cells[a] h] (h =
+ * 1 / max n_cells), subdomain s owns the core box of pam_partition, and the
+ * initial dictionary is the same lattice over it. An element belongs to the
+ * core that holds its sampling point (the owner rule of pam_eval: half-open
+ * boxes, the outer face closed), and to the patch of every subdomain whose
+ * core grown by `overlap` h (clipped to the domain) holds it; a patch lists
+ * its elements in ascending index, the local order of the fit. Every step
+ * then runs as on a grid, with the element's own measure in R_T = |T| (K*(x_T)
+ * - K_T)^2 and in the marking tolerance eps_T = |T| (eps_tol_rel max K)^2.
+ * The midpoint rule only (pam_params.quad = 1 needs the element shapes:
+ * PAM_ERR_UNSUPPORTED). pam_eval and pam_eval_glued evaluate the model as
+ * for a grid.
+ */
+typedef struct {
+    int64_t n_cells;             /* elements n (< 2^31) */
+    const double *x;             /* device [n][dim] sampling points, inside the domain box */
+    const double *vol;           /* device [n] measures |T| > 0 */
+    const int32_t *patch_start;  /* device [S + 1]: patch s holds patch_cells[patch_start[s] ..
+                                    patch_start[s + 1]) */
+    const int32_t *patch_cells;  /* device: element indices, ascending within each patch */
+} pam_cells;
+
+/*
+ * Step 1 for a mesh given as cells, on the host: the patch lists of the
+ * elements with sampling points h_x [n_cells][dim] (host). Writes
+ * h_patch_start [S + 1] (offsets) and, when h_patch_cells is not NULL, the
+ * lists into h_patch_cells [h_patch_start[S]] (call once with NULL to size
+ * it). PAM_ERR_INVALID_ARG for a point outside the domain box (or NaN).
+ */
+pam_status pam_partition_cells(const pam_problem *prob, const double *h_x, int64_t n_cells,
+                               int32_t *h_patch_start, int32_t *h_patch_cells);
+/* pam_plan_create for a mesh given as cells: the patch size comes from the
+ * host patch offsets h_patch_start [S + 1]; workspace_bytes adds 32 bytes
+ * per patch-cell slot for the gathered points and measures. */
+pam_status pam_plan_create_cells(const pam_problem *prob, const pam_params *par, int64_t n_cells,
+                                 const int32_t *h_patch_start, pam_plan *out);
+/* pam_fit_subdomains / pam_refine on a mesh given as cells; d_K: device
+ * [n_cells] element values. A measure <= 0, NaN or Inf is reported like a bad
+ * K (PAM_ERR_NONPOSITIVE_K). Same synchronisation and status as the grid
+ * calls. */
+pam_status pam_fit_cells(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                         const pam_cells *cells, const double *d_K, pam_model *model, void *d_workspace,
+                         size_t workspace_bytes, void *stream);
+pam_status pam_refine_cells(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                            const pam_cells *cells, const double *d_K, pam_model *model, int n_levels,
+                            void *d_workspace, size_t workspace_bytes, void *stream);
+/* pam_errors over the elements, each measured with its owner's surrogate at
+ * its sampling point and weighted by |T|: d_err[0] = sum |T| |K_T - K*| /
+ * sum |T| |K_T|, d_err[1] = (sum |T| (K_T - K*)^2 / sum |T| K_T^2)^(1/2)
+ * (Eq. (12)), d_err[2] the first in log space, d_err[3] = max |log10 K_T -
+ * log10 K*|. Asynchronous. */
+pam_status pam_errors_cells(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
+                            const pam_cells *cells, const double *d_K, double *d_err, int precision,
+                            void *d_workspace, size_t workspace_bytes, void *stream);
+
+/*
  * Learned warm start (spec addition; the paper has no learned part).
  * A convolutional network maps a subdomain patch of log10(K)/3 (clipped to
  * [-1, 1], NHWC) to n_out support logits and n_out coefficients / 4 of the

@@ -136,6 +136,7 @@ static size_t carve(const Geo &g, char *base, Ws *w) {
     w->G = (double *)take(S * mc * mc * (f64 ? sizeof(double) : sizeof(float)));
     w->Gf = (float *)w->G;
     w->E = f64 ? (double *)take(S * mc * nm * sizeof(double)) : nullptr;
+    w->cxv = g.cells ? (double4_32a *)take(S * nm * sizeof(double4_32a)) : nullptr;
     w->bytes = off;
     return off;
 }
@@ -294,21 +295,10 @@ static pam_status read_status(const Ws &w, cudaStream_t st, int32_t host[8]) {
     return PAM_OK;
 }
 
-pam_status pam_fit_subdomains(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
-                              const double *d_K, pam_model *model, void *d_workspace,
-                              size_t workspace_bytes, void *stream) {
-    Geo g;
-    Par p;
+// Step 2 launches shared by the grid and the element-list entry points.
+static pam_status fit_launches(const Geo &g, const Par &p, const pam_params *par, const double *d_K,
+                               pam_model *model, const Ws &w, cudaStream_t s) {
     pam_status st;
-    if (!par || !make_geo(prob, par, &g, &p, &st)) return par ? st : PAM_ERR_INVALID_ARG;
-    if ((st = check_plan(g, plan)) != PAM_OK) return st;
-    g.m_cap = plan->m_cap;
-    if (par->precision == PAM_PREC_MIXED && (g.m_cap > kMixedMaxM || !mixed_solve_fits(g)))
-        return PAM_ERR_UNSUPPORTED;
-    if (!d_K || !model_ok(model) || !d_workspace) return PAM_ERR_INVALID_ARG;
-    Ws w = carve_workspace(g, d_workspace);
-    if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
-    cudaStream_t s = (cudaStream_t)stream;
     const bool deferred = par->deferred_status != 0;
     PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 8 * sizeof(int32_t), s));
     launch_partition(g, model->boxes, s);
@@ -330,6 +320,23 @@ pam_status pam_fit_subdomains(const pam_problem *prob, const pam_params *par, co
     if ((st = read_status(w, s, hs)) != PAM_OK) return st;
     if (hs[kStTimeout]) return PAM_ERR_TIMEOUT;
     return hs[kStUncertified] ? PAM_ERR_NOT_CONVERGED : PAM_OK;
+}
+
+pam_status pam_fit_subdomains(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                              const double *d_K, pam_model *model, void *d_workspace,
+                              size_t workspace_bytes, void *stream) {
+    Geo g;
+    Par p;
+    pam_status st;
+    if (!par || !make_geo(prob, par, &g, &p, &st)) return par ? st : PAM_ERR_INVALID_ARG;
+    if ((st = check_plan(g, plan)) != PAM_OK) return st;
+    g.m_cap = plan->m_cap;
+    if (par->precision == PAM_PREC_MIXED && (g.m_cap > kMixedMaxM || !mixed_solve_fits(g)))
+        return PAM_ERR_UNSUPPORTED;
+    if (!d_K || !model_ok(model) || !d_workspace) return PAM_ERR_INVALID_ARG;
+    Ws w = carve_workspace(g, d_workspace);
+    if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
+    return fit_launches(g, p, par, d_K, model, w, (cudaStream_t)stream);
 }
 
 pam_status pam_lambda_cv_workspace_size(const pam_plan *plan, size_t *bytes) {
@@ -393,21 +400,10 @@ pam_status pam_status_read(const pam_plan *plan, void *d_workspace, size_t works
     return hs[kStUncertified] ? PAM_ERR_NOT_CONVERGED : PAM_OK;
 }
 
-pam_status pam_refine(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
-                      const double *d_K, pam_model *model, int n_levels, void *d_workspace,
-                      size_t workspace_bytes, void *stream) {
-    Geo g;
-    Par p;
+// Step 3 launches shared by the grid and the element-list entry points.
+static pam_status refine_launches(const Geo &g, const Par &p, const pam_params *par, pam_model *model,
+                                  int n_levels, const Ws &w, cudaStream_t s) {
     pam_status st;
-    if (!par || !make_geo(prob, par, &g, &p, &st)) return par ? st : PAM_ERR_INVALID_ARG;
-    if ((st = check_plan(g, plan)) != PAM_OK) return st;
-    g.m_cap = plan->m_cap;
-    if (par->precision == PAM_PREC_MIXED && (g.m_cap > kMixedMaxM || !mixed_solve_fits(g)))
-        return PAM_ERR_UNSUPPORTED;
-    if (!d_K || !model_ok(model) || !d_workspace || n_levels < 0) return PAM_ERR_INVALID_ARG;
-    Ws w = carve_workspace(g, d_workspace);
-    if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
-    cudaStream_t s = (cudaStream_t)stream;
     const bool deferred = par->deferred_status != 0;
     // deferred: the status keeps accumulating from pam_fit_subdomains
     if (!deferred) PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 8 * sizeof(int32_t), s));
@@ -425,6 +421,23 @@ pam_status pam_refine(const pam_problem *prob, const pam_params *par, const pam_
     if ((st = read_status(w, s, hs)) != PAM_OK) return st;
     if (hs[kStTimeout]) return PAM_ERR_TIMEOUT;
     return hs[kStUncertified] ? PAM_ERR_NOT_CONVERGED : PAM_OK;
+}
+
+pam_status pam_refine(const pam_problem *prob, const pam_params *par,
+                      const pam_plan *plan, const double *d_K, pam_model *model, int n_levels,
+                      void *d_workspace, size_t workspace_bytes, void *stream) {
+    Geo g;
+    Par p;
+    pam_status st;
+    if (!par || !make_geo(prob, par, &g, &p, &st)) return par ? st : PAM_ERR_INVALID_ARG;
+    if ((st = check_plan(g, plan)) != PAM_OK) return st;
+    g.m_cap = plan->m_cap;
+    if (par->precision == PAM_PREC_MIXED && (g.m_cap > kMixedMaxM || !mixed_solve_fits(g)))
+        return PAM_ERR_UNSUPPORTED;
+    if (!d_K || !model_ok(model) || !d_workspace || n_levels < 0) return PAM_ERR_INVALID_ARG;
+    Ws w = carve_workspace(g, d_workspace);
+    if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
+    return refine_launches(g, p, par, model, n_levels, w, (cudaStream_t)stream);
 }
 
 pam_status pam_gram(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
@@ -552,6 +565,188 @@ pam_status pam_errors(const pam_problem *prob, const pam_plan *plan, const pam_m
     if (workspace_bytes < (size_t)((char *)w.y - (char *)d_workspace)) return PAM_ERR_WORKSPACE;
     launch_errors(g, model->boxes, model->centres, model->beta, model->info, d_K, d_err, precision,
                   quad, w, (cudaStream_t)stream);
+    PAM_CUDA_TRY(cudaGetLastError());
+    return PAM_OK;
+}
+
+// ------------------------------------------------------ element lists ---
+
+// Range of cores j along one axis whose patch [lo_j - ov, hi_j + ov)
+// (clipped to [0, n], closed at n) holds the cell coordinate u.
+static void patch_range(int n, int p, int ov, double u, int *j0, int *j1) {
+    *j0 = p;
+    *j1 = -1;
+    for (int j = 0; j < p; ++j) {
+        int64_t lo = ((int64_t)j * n) / p - ov, hi = ((int64_t)(j + 1) * n) / p + ov;
+        if (lo < 0) lo = 0;
+        if (hi > n) hi = n;
+        const bool in = u >= (double)lo && (hi == n ? u <= (double)hi : u < (double)hi);
+        if (in) {
+            if (j < *j0) *j0 = j;
+            *j1 = j;
+        }
+    }
+}
+
+pam_status pam_partition_cells(const pam_problem *prob, const double *h_x, int64_t n_cells,
+                               int32_t *h_patch_start, int32_t *h_patch_cells) {
+    Geo g;
+    pam_status st;
+    if (!make_geo(prob, nullptr, &g, nullptr, &st)) return st;
+    if (!h_patch_start || n_cells < 0 || (n_cells > 0 && !h_x)) return PAM_ERR_INVALID_ARG;
+    if (n_cells > (int64_t)INT32_MAX) return PAM_ERR_UNSUPPORTED;
+    std::vector<int64_t> cnt((size_t)g.S, 0);
+    std::vector<int> rng((size_t)n_cells * 6);
+    for (int64_t e = 0; e < n_cells; ++e) {
+        int *r = &rng[(size_t)e * 6];
+        for (int a = 0; a < 3; ++a) {
+            r[2 * a] = 0;
+            r[2 * a + 1] = 0;
+        }
+        for (int a = 0; a < g.dim; ++a) {
+            const double xa = h_x[e * g.dim + a];
+            const double u = xa * (double)g.nmax;
+            if (!(u >= 0.0) || u > (double)g.n[a]) return PAM_ERR_INVALID_ARG;  // outside the domain
+            patch_range(g.n[a], g.p[a], g.overlap, u, &r[2 * a], &r[2 * a + 1]);
+            if (r[2 * a] > r[2 * a + 1]) return PAM_ERR_INVALID_ARG;
+        }
+        for (int k = r[4]; k <= r[5]; ++k)
+            for (int j = r[2]; j <= r[3]; ++j)
+                for (int i = r[0]; i <= r[1]; ++i) ++cnt[(size_t)(i + g.p[0] * (j + g.p[1] * k))];
+    }
+    int64_t run = 0;
+    for (int s = 0; s < g.S; ++s) {
+        h_patch_start[s] = (int32_t)run;
+        run += cnt[(size_t)s];
+        if (run > (int64_t)INT32_MAX) return PAM_ERR_UNSUPPORTED;
+    }
+    h_patch_start[g.S] = (int32_t)run;
+    if (!h_patch_cells) return PAM_OK;
+    std::vector<int64_t> fill((size_t)g.S, 0);
+    for (int64_t e = 0; e < n_cells; ++e) {  // ascending element index within each patch
+        const int *r = &rng[(size_t)e * 6];
+        for (int k = r[4]; k <= r[5]; ++k)
+            for (int j = r[2]; j <= r[3]; ++j)
+                for (int i = r[0]; i <= r[1]; ++i) {
+                    const int s = i + g.p[0] * (j + g.p[1] * k);
+                    h_patch_cells[h_patch_start[s] + fill[(size_t)s]++] = (int32_t)e;
+                }
+    }
+    return PAM_OK;
+}
+
+// Geometry of an element-list problem: the grid view, then the patch size
+// from the patch lists (rounded to 32) in place of the grid patches'.
+static bool geo_cells(const pam_problem *prob, const pam_params *par, int max_patch, Geo *g, Par *p,
+                      pam_status *st) {
+    if (!make_geo(prob, par, g, p, st)) return false;
+    *st = PAM_ERR_INVALID_ARG;
+    if (max_patch < 1 || max_patch > (1 << 20)) {
+        *st = max_patch > (1 << 20) ? PAM_ERR_UNSUPPORTED : PAM_ERR_INVALID_ARG;
+        return false;
+    }
+    g->n_max = (int)align_up((size_t)max_patch, 32);
+    if (par && par->levels > 0) {
+        int64_t P = 1;
+        while (P < g->n_max) P <<= 1;
+        if (P * 8 > 227 * 1024) { *st = PAM_ERR_UNSUPPORTED; return false; }
+    }
+    if (par && par->quad != 0) { *st = PAM_ERR_UNSUPPORTED; return false; }  // element shapes not given
+    g->cells = 1;
+    *st = PAM_OK;
+    return true;
+}
+
+pam_status pam_plan_create_cells(const pam_problem *prob, const pam_params *par, int64_t n_cells,
+                                 const int32_t *h_patch_start, pam_plan *out) {
+    if (!prob || !par || !out || !h_patch_start || n_cells < 0) return PAM_ERR_INVALID_ARG;
+    Geo g0;
+    pam_status st;
+    if (!make_geo(prob, nullptr, &g0, nullptr, &st)) return st;
+    int max_patch = 0;
+    for (int s = 0; s < g0.S; ++s) {
+        const int32_t c = h_patch_start[s + 1] - h_patch_start[s];
+        if (c < 0 || h_patch_start[s] < 0) return PAM_ERR_INVALID_ARG;
+        if (c > max_patch) max_patch = c;
+    }
+    Geo g;
+    Par p;
+    if (!geo_cells(prob, par, max_patch < 1 ? 1 : max_patch, &g, &p, &st)) return st;
+    Ws w;
+    out->n_subdomains = g.S;
+    out->max_patch_cells = g.n_max;
+    out->m0 = g.m0;
+    out->m_cap = g.m_cap;
+    out->n_grid_cells = n_cells;
+    out->workspace_bytes = carve(g, nullptr, &w);
+    return PAM_OK;
+}
+
+static pam_status cells_setup(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                              const pam_cells *cells, Geo *g, Par *p) {
+    pam_status st;
+    if (!plan || !cells || !cells->x || !cells->vol || !cells->patch_start || !cells->patch_cells)
+        return PAM_ERR_INVALID_ARG;
+    if (cells->n_cells < 0 || cells->n_cells != plan->n_grid_cells) return PAM_ERR_INVALID_ARG;
+    if (!geo_cells(prob, par, plan->max_patch_cells, g, p, &st)) return st;
+    if (plan->n_subdomains != g->S || plan->max_patch_cells != g->n_max || plan->m_cap > PAM_MAX_M ||
+        plan->m_cap < 1 || plan->m_cap % 64 != 0 || (par && plan->m_cap < g->m_cap))
+        return PAM_ERR_INVALID_ARG;
+    g->m_cap = plan->m_cap;
+    g->cx = cells->x;
+    g->cvol = cells->vol;
+    g->pstart = cells->patch_start;
+    g->pcells = cells->patch_cells;
+    return PAM_OK;
+}
+
+pam_status pam_fit_cells(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                         const pam_cells *cells, const double *d_K, pam_model *model, void *d_workspace,
+                         size_t workspace_bytes, void *stream) {
+    Geo g;
+    Par p;
+    pam_status st;
+    if (!par) return PAM_ERR_INVALID_ARG;
+    if ((st = cells_setup(prob, par, plan, cells, &g, &p)) != PAM_OK) return st;
+    if (par->precision == PAM_PREC_MIXED && (g.m_cap > kMixedMaxM || !mixed_solve_fits(g)))
+        return PAM_ERR_UNSUPPORTED;
+    if (!d_K || !model_ok(model) || !d_workspace) return PAM_ERR_INVALID_ARG;
+    Ws w = carve_workspace(g, d_workspace);
+    if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
+    g.cxv = w.cxv;
+    return fit_launches(g, p, par, d_K, model, w, (cudaStream_t)stream);
+}
+
+pam_status pam_refine_cells(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                            const pam_cells *cells, const double *d_K, pam_model *model, int n_levels,
+                            void *d_workspace, size_t workspace_bytes, void *stream) {
+    Geo g;
+    Par p;
+    pam_status st;
+    if (!par) return PAM_ERR_INVALID_ARG;
+    if ((st = cells_setup(prob, par, plan, cells, &g, &p)) != PAM_OK) return st;
+    if (par->precision == PAM_PREC_MIXED && (g.m_cap > kMixedMaxM || !mixed_solve_fits(g)))
+        return PAM_ERR_UNSUPPORTED;
+    if (!d_K || !model_ok(model) || !d_workspace || n_levels < 0) return PAM_ERR_INVALID_ARG;
+    Ws w = carve_workspace(g, d_workspace);
+    if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
+    g.cxv = w.cxv;
+    return refine_launches(g, p, par, model, n_levels, w, (cudaStream_t)stream);
+}
+
+pam_status pam_errors_cells(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
+                            const pam_cells *cells, const double *d_K, double *d_err, int precision,
+                            void *d_workspace, size_t workspace_bytes, void *stream) {
+    Geo g;
+    Par p;
+    pam_status st;
+    if ((st = cells_setup(prob, nullptr, plan, cells, &g, &p)) != PAM_OK) return st;
+    if (!model_ok(model) || !d_K || !d_err || !d_workspace) return PAM_ERR_INVALID_ARG;
+    if (precision != PAM_PREC_FP64 && precision != PAM_PREC_MIXED) return PAM_ERR_INVALID_ARG;
+    Ws w = carve_workspace(g, d_workspace);
+    if (workspace_bytes < (size_t)((char *)w.y - (char *)d_workspace)) return PAM_ERR_WORKSPACE;
+    launch_errors_cells(g, model->boxes, model->centres, model->beta, model->info, d_K, d_err, precision, w,
+                        (cudaStream_t)stream);
     PAM_CUDA_TRY(cudaGetLastError());
     return PAM_OK;
 }

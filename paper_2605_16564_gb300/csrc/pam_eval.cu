@@ -700,6 +700,83 @@ void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, co
 }
 
 // --------------------------------------------------------------------------
+// Errors over the elements of a mesh given as cells: one block per
+// subdomain sweeps its patch list and measures the elements whose sampling
+// point it owns (Step 4 owner rule; every element has exactly one owner and
+// lies in its owner's patch), weighted by |T|; the same seven fp64 partial
+// sums and combine as the grid errors.
+// --------------------------------------------------------------------------
+template <bool F32>
+__global__ void __launch_bounds__(kErrThreads) k_errors_cells(Geo g, const int32_t *boxes,
+                                                              const double *centres, const double *beta,
+                                                              const int32_t *info, const double *K,
+                                                              double *part) {
+    const int s = blockIdx.x;
+    const int M = info[s * kInfoN + PAM_INFO_M];
+    extern __shared__ uint8_t smb[];
+    dvec4 *sc64 = reinterpret_cast<dvec4 *>(smb);
+    double *sb64 = reinterpret_cast<double *>(sc64 + g.m_cap);
+    float4 *sc32 = reinterpret_cast<float4 *>(smb);
+    float *sb32 = reinterpret_cast<float *>(sc32 + g.m_cap);
+    double o[3];
+    if (F32) stage_f32(g, boxes, centres, beta, s, M, sc32, sb32, o);
+    else stage_f64(g, centres, beta, s, M, sc64, sb64);
+    const int b = g.pstart[s], N = g.pstart[s + 1] - b;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int t = threadIdx.x; t < N; t += blockDim.x) {
+        const int64_t e = g.pcells[b + t];
+        double x[3] = {0, 0, 0};
+        for (int a = 0; a < g.dim; ++a) x[a] = g.cx[e * g.dim + a];
+        if (owner_of_point(g, x) != s) continue;
+        const double kk = K[e], vol = g.cvol[e], lk = log(kk);
+        acc[1] += vol * fabs(kk);
+        acc[3] += vol * (kk * kk);
+        acc[5] += vol * fabs(lk);
+        double v;
+        if (F32)
+            v = (double)shepard_f32_smem(sc32, sb32, M, (float)(x[0] - o[0]), (float)(x[1] - o[1]),
+                                         (float)(x[2] - o[2]));
+        else
+            v = shepard_f64_smem(sc64, sb64, M, x);
+        const double ks = F32 ? exp_f32((float)v) : exp(v);
+        acc[0] += vol * fabs(kk - ks);
+        acc[2] += vol * ((kk - ks) * (kk - ks));
+        acc[4] += vol * fabs(lk - v);
+        acc[6] = fmax(acc[6], fabs(lk - v));
+    }
+    __shared__ double red[kErrThreads / 32][7];
+    for (int q = 0; q < 7; ++q) {
+        const double v = (q == 6) ? warp_max(acc[q]) : warp_sum(acc[q]);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = v;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int q = threadIdx.x;
+        double v = 0.0;
+        if (q < 7)
+            for (int wdx = 0; wdx < kErrThreads / 32; ++wdx)
+                v = (q == 6) ? fmax(v, red[wdx][q]) : v + red[wdx][q];
+        part[(size_t)s * 8 + q] = v;
+    }
+}
+
+void launch_errors_cells(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
+                         const int32_t *info, const double *K, double *err, int precision, const Ws &w,
+                         cudaStream_t st) {
+    PhaseScope ps(kPhErrors, st);
+    if (precision == PAM_PREC_MIXED) {
+        size_t sm = (size_t)g.m_cap * (sizeof(float4) + sizeof(float));
+        k_errors_cells<true><<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, w.err_part);
+    } else {
+        size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));
+        cudaFuncSetAttribute(k_errors_cells<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_errors_cells<false><<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, w.err_part);
+    }
+    k_errors_combine<<<1, 256, 0, st>>>(w.err_part, g.S, err);
+    count_launches(2);
+}
+
+// --------------------------------------------------------------------------
 // Indicators R_T (Eq. (4)) with the tensor two-point Gauss-Legendre rule:
 // R_T = sum_q (|T| / 2^dim) (K*(x_q) - K_T)^2 over the nodes x_T +- h/(2
 // sqrt 3) per axis, K* from the subdomain's whole dictionary at each node

@@ -76,12 +76,55 @@ __global__ void k_prepare(Geo g, const int32_t *boxes, const double *K, Ws w) {
         atomicMax(&w.kmax_bits[s], (unsigned long long)__double_as_longlong(m));
 }
 
+// The same for a mesh given as cells: patch cell t of subdomain s is element
+// pcells[pstart[s] + t]; its sampling point and measure are gathered into
+// the workspace beside y and K (a measure <= 0, NaN or Inf is an input
+// fault like a bad K_T).
+__global__ void k_prepare_cells(Geo g, const double *K, Ws w) {
+    const int s = blockIdx.y;
+    const int b = g.pstart[s], N = g.pstart[s + 1] - b;
+    const int t = blockIdx.x * blockDim.x + threadIdx.x;
+    double kmax = 0.0;
+    if (t < g.n_max) {
+        const size_t o = (size_t)s * g.n_max + t;
+        double4_32a v;
+        v.x = v.y = v.z = v.w = 0.0;
+        if (t < N) {
+            const int64_t e = g.pcells[b + t];
+            double k = K[e];
+            double vol = g.cvol[e];
+            if (!(k > 0.0) || !(k <= DBL_MAX) || !(vol > 0.0) || !(vol <= DBL_MAX)) {
+                atomicAdd(&w.status[kStBadK], 1);
+                k = 1.0;
+                vol = g.vol;
+            }
+            v.x = g.cx[e * g.dim];
+            if (g.dim > 1) v.y = g.cx[e * g.dim + 1];
+            if (g.dim > 2) v.z = g.cx[e * g.dim + 2];
+            v.w = vol;
+            w.y[o] = log(k);
+            w.kv[o] = k;
+            kmax = k;
+        } else {
+            w.y[o] = 0.0;
+            w.kv[o] = 0.0;
+        }
+        w.cxv[o] = v;
+    }
+    double m = warp_max(kmax);
+    if ((threadIdx.x & 31) == 0 && m > 0.0)
+        atomicMax(&w.kmax_bits[s], (unsigned long long)__double_as_longlong(m));
+}
+
 void launch_prepare(const Geo &g, const int32_t *boxes, const double *K, const Ws &w,
                     cudaStream_t st) {
     PhaseScope ps(kPhPrepare, st);
     cudaMemsetAsync(w.kmax_bits, 0, sizeof(unsigned long long) * g.S, st);
     dim3 grid((g.n_max + 255) / 256, g.S);
-    k_prepare<<<grid, 256, 0, st>>>(g, boxes, K, w);
+    if (g.cells)
+        k_prepare_cells<<<grid, 256, 0, st>>>(g, K, w);
+    else
+        k_prepare<<<grid, 256, 0, st>>>(g, boxes, K, w);
     count_launches(1);
 }
 
@@ -124,7 +167,7 @@ __global__ void k_init_dictionary(Geo g, const int32_t *boxes, double *centres, 
         inf[PAM_INFO_ITERS] = 0;
         inf[PAM_INFO_FLAGS] = 0;
         inf[PAM_INFO_STOPPED] = 0;
-        inf[PAM_INFO_N_CELLS] = ext[0] * ext[1] * ext[2];
+        inf[PAM_INFO_N_CELLS] = g.cells ? g.pstart[s + 1] - g.pstart[s] : ext[0] * ext[1] * ext[2];
         inf[PAM_INFO_MARKED] = 0;
     }
 }
@@ -159,8 +202,7 @@ __global__ void __launch_bounds__(128) k_assemble_f64(Geo g, const int32_t *boxe
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N) return;
     double x[3];
-    int64_t gi;
-    patch_cell(g, boxes + s * 12, t, x, &gi);
+    cell_point(g, s, boxes + s * 12, t, x);
     double lmax = -INFINITY;
     for (int m = 0; m < M; ++m) {
         dvec4 c = sc[m];
@@ -591,7 +633,7 @@ __global__ void __launch_bounds__(128) k_residual_f64(Geo g, const double *beta,
     for (int m = 0; m < M; ++m) acc += E[(size_t)m * g.n_max] * sb[m];
     size_t o = (size_t)s * g.n_max + t;
     double e = exp(acc * w.inv_s[o]) - w.kv[o];
-    w.R[o] = g.vol * (e * e);
+    w.R[o] = cell_measure(g, s, t) * (e * e);
 }
 
 // --------------------------------------------------------------------------
@@ -666,11 +708,11 @@ __global__ void __launch_bounds__(kMarkThreads) k_mark_enrich(Geo g, Par p, cons
     }
     double kmax = __longlong_as_double((long long)w.kmax_bits[s]);
     double eps;
+    const double a_tol = p.eps_tol_rel * kmax;
     if (p.eps_tol_rel < 0.0) {
         eps = -INFINITY;
     } else {
-        double a = p.eps_tol_rel * kmax;
-        eps = g.vol * (a * a);
+        eps = g.vol * (a_tol * a_tol);
     }
     const float ek = (float)eps;
     const double *R = w.R + (size_t)s * g.n_max;
@@ -682,7 +724,11 @@ __global__ void __launch_bounds__(kMarkThreads) k_mark_enrich(Geo g, Par p, cons
         unsigned long long k = 0ull;
         if (t < N) {
             const float key = (float)R[t];
-            if (key >= ek)
+            // elements of unequal measure: eps_T = |T| (eps_tol_rel max K)^2
+            const float ekt = (g.cells && p.eps_tol_rel >= 0.0)
+                                  ? (float)__dmul_rn(__dmul_rn(cell_measure(g, s, t), a_tol), a_tol)
+                                  : ek;
+            if (key >= ekt)
                 k = ((unsigned long long)(__float_as_uint(key) + 1u) << 32) |
                     (unsigned long long)(0xffffffffu - (unsigned)t);
         }
@@ -746,8 +792,7 @@ __global__ void __launch_bounds__(kMarkThreads) k_mark_enrich(Geo g, Par p, cons
                              (float)(cs[(size_t)m * 4 + 2] - lo[2]), 0.f);
     for (int r = tid; r < nmu; r += blockDim.x) {
         double xt[3];
-        int64_t gi;
-        patch_cell(g, box, marked[r], xt, &gi);
+        cell_point(g, s, box, marked[r], xt);
         for (int a = 0; a < 3; ++a) cxt[4 * r + a] = xt[a];
     }
     __syncthreads();

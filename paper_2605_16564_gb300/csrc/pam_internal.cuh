@@ -29,6 +29,14 @@ struct Geo {
     int n_max;      // max patch cells (padded stride of per-cell arrays)
     int m0, m_cap;
     int prec;       // pam_precision of the fit calls (sizes the workspace)
+    // a general mesh given as cells (section 2: elements with a sampling
+    // point, a value and a measure); all NULL / 0 for a structured grid
+    int cells;               // 1: the patches are element lists
+    const double *cx;        // [n][dim] sampling points x_T
+    const double *cvol;      // [n] measures |T|
+    const int32_t *pstart;   // [S+1] offsets of the patch lists
+    const int32_t *pcells;   // element indices, ascending within a patch
+    const double4_32a *cxv;  // workspace [S][n_max]: (x, y, z, |T|) of each patch cell
 };
 
 struct Par {
@@ -57,6 +65,7 @@ struct Ws {
     int32_t *status;  // [8] device status words
     uint32_t *cost;   // [S] clock cycles of each subdomain's last mixed solve (a scheduling hint)
     int32_t *order;   // [S] subdomains in decreasing cost, the mixed solve's block order
+    double4_32a *cxv; // [S][n_max] gathered (x, y, z, |T|) of patch cells (element-list meshes only)
     size_t bytes;
 };
 
@@ -71,6 +80,9 @@ bool make_geo(const pam_problem *prob, const pam_params *par, Geo *g, Par *p, pa
 // Launchers implemented in the kernel translation units.
 void launch_partition(const Geo &g, int32_t *boxes, cudaStream_t st);
 void launch_prepare(const Geo &g, const int32_t *boxes, const double *K, const Ws &w, cudaStream_t st);
+void launch_errors_cells(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
+                         const int32_t *info, const double *K, double *err, int precision, const Ws &w,
+                         cudaStream_t st);
 void launch_init_dictionary(const Geo &g, const int32_t *boxes, double *centres, double *beta,
                             int32_t *info, cudaStream_t st, int keep_beta);
 void launch_solve_level_f64(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
@@ -167,6 +179,25 @@ __device__ __forceinline__ void patch_cell(const Geo &g, const int32_t *box, int
     x[1] = g.dim > 1 ? __dmul_rn((double)j + 0.5, g.h) : 0.0;
     x[2] = g.dim > 2 ? __dmul_rn((double)k + 0.5, g.h) : 0.0;
     *gidx = (int64_t)i + (int64_t)g.n[0] * ((int64_t)j + (int64_t)g.n[1] * (int64_t)k);
+}
+
+// Sampling point of local patch cell t of subdomain s: the gathered element
+// point for a mesh given as cells, else the grid centroid.
+__device__ __forceinline__ void cell_point(const Geo &g, int s, const int32_t *box, int t, double x[3]) {
+    if (g.cxv) {
+        const double4_32a v = g.cxv[(size_t)s * g.n_max + t];
+        x[0] = v.x;
+        x[1] = v.y;
+        x[2] = v.z;
+    } else {
+        int64_t gi;
+        patch_cell(g, box, t, x, &gi);
+    }
+}
+
+// Measure |T| of local patch cell t of subdomain s.
+__device__ __forceinline__ double cell_measure(const Geo &g, int s, int t) {
+    return g.cxv ? g.cxv[(size_t)s * g.n_max + t].w : g.vol;
 }
 
 // Index of the core interval [floor(j n / p), floor((j+1) n / p)) holding

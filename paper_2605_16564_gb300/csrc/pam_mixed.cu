@@ -41,8 +41,16 @@ __device__ __forceinline__ void patch_origin(const Geo &g, const int32_t *box, d
 }
 
 // Local coordinates of patch cell t: ((i - patch_lo) + 1/2) h, exact in fp32
-// up to one rounding.
-__device__ __forceinline__ void local_cell(const Geo &g, const int32_t *box, int t, float x[3]) {
+// up to one rounding; for a mesh given as cells, the gathered sampling point
+// minus the patch origin, rounded once to fp32.
+__device__ __forceinline__ void local_cell(const Geo &g, int s, const int32_t *box, int t, float x[3]) {
+    if (g.cxv) {
+        const double4_32a v = g.cxv[(size_t)s * g.n_max + t];
+        x[0] = (float)(v.x - (double)box[6] * g.h);
+        x[1] = g.dim > 1 ? (float)(v.y - (double)box[7] * g.h) : 0.0f;
+        x[2] = g.dim > 2 ? (float)(v.z - (double)box[8] * g.h) : 0.0f;
+        return;
+    }
     int w0 = box[9] - box[6], w1 = box[10] - box[7];
     int i = t % w0, j = (t / w0) % w1, k = t / (w0 * w1);
     float hf = (float)g.h;
@@ -73,7 +81,7 @@ __global__ void __launch_bounds__(128) k_stats_f32(Geo g, const int32_t *boxes,
     const int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N) return;
     float x[3];
-    local_cell(g, box, t, x);
+    local_cell(g, s, box, t, x);
     // one pass with a running maximum: the sum is rescaled whenever the
     // maximum grows (sum = sum 2^(old - new) + 1), else gains 2^(l - max)
     float lmax = -INFINITY, sum = 0.0f;
@@ -232,7 +240,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
         float x[3] = {0.f, 0.f, 0.f};
         float sh = INFINITY, y = 0.f;
         if (t < N && (folds == 0 || t % folds != fold)) {
-            local_cell(g, box, t, x);
+            local_cell(g, s, box, t, x);
             sh = rowmax[t] - log2f(rowinv[t]);
             y = (float)yv[t];
         }
@@ -880,7 +888,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
     }
     for (int t = tid; t < N; t += blockDim.x) {
         float xl[3];
-        local_cell(g, box, t, xl);
+        local_cell(g, s, box, t, xl);
         cell[t] = make_float4(xl[0], xl[1], xl[2], rowmax[t]);
         cinv[t] = rowinv[t];
     }
@@ -1188,7 +1196,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
     } else if (certified) {
         for (int t = tid; t < N; t += blockDim.x) {
             const double ev = w.kv[(size_t)s * g.n_max + t] * (double)expm1f(-ce[t]);
-            w.R[(size_t)s * g.n_max + t] = g.vol * (ev * ev);
+            w.R[(size_t)s * g.n_max + t] = cell_measure(g, s, t) * (ev * ev);
         }
     }
     // otherwise x changed after the last pass: e = y - W x once more
@@ -1202,7 +1210,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
         const double yhat = acc.value() * (double)cinv[t];
         const double kv = w.kv[(size_t)s * g.n_max + t];
         const double e = exp(yhat) - kv;
-        w.R[(size_t)s * g.n_max + t] = g.vol * (e * e);
+        w.R[(size_t)s * g.n_max + t] = cell_measure(g, s, t) * (e * e);
     }
     for (int j = tid; j < M; j += blockDim.x) beta[(size_t)s * mc + j] = (double)x[j];
     __syncthreads();

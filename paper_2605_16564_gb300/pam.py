@@ -34,7 +34,8 @@ STATUS = {0: "PAM_OK", 1: "PAM_ERR_INVALID_ARG", 2: "PAM_ERR_NONPOSITIVE_K", 3: 
 EXPORTED = ["pam_version", "pam_status_string", "pam_plan_create", "pam_partition",
             "pam_fit_subdomains", "pam_refine", "pam_gram", "pam_eval_workspace_size", "pam_eval",
             "pam_errors", "pam_status_read", "pam_lambda_cv_workspace_size", "pam_lambda_cv",
-            "pam_eval_glued_workspace_size", "pam_eval_glued"]
+            "pam_eval_glued_workspace_size", "pam_eval_glued", "pam_partition_cells", "pam_plan_create_cells",
+            "pam_fit_cells", "pam_refine_cells", "pam_errors_cells"]
 
 
 class PamError(RuntimeError):
@@ -59,6 +60,11 @@ class pam_params(C.Structure):
 class pam_plan(C.Structure):
     _fields_ = [("n_subdomains", C.c_int), ("max_patch_cells", C.c_int), ("m0", C.c_int),
                 ("m_cap", C.c_int), ("n_grid_cells", C.c_int64), ("workspace_bytes", C.c_size_t)]
+
+
+class pam_cells(C.Structure):
+    _fields_ = [("n_cells", C.c_int64), ("x", C.c_void_p), ("vol", C.c_void_p), ("patch_start", C.c_void_p),
+                ("patch_cells", C.c_void_p)]
 
 
 class pam_model(C.Structure):
@@ -95,6 +101,17 @@ def lib():
         L.pam_eval_workspace_size.argtypes = [P(pam_plan), C.c_int64, P(C.c_size_t)]
         L.pam_eval.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_int64,
                                C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_partition_cells.argtypes = [P(pam_problem), C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p]
+        L.pam_plan_create_cells.argtypes = [P(pam_problem), P(pam_params), C.c_int64, C.c_void_p, P(pam_plan)]
+        L.pam_fit_cells.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), P(pam_cells), C.c_void_p,
+                                    P(pam_model), C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_refine_cells.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), P(pam_cells), C.c_void_p,
+                                       P(pam_model), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_errors_cells.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), P(pam_cells), C.c_void_p,
+                                       C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
+        for name in ("pam_partition_cells", "pam_plan_create_cells", "pam_fit_cells", "pam_refine_cells",
+                     "pam_errors_cells"):
+            getattr(L, name).restype = C.c_int
         L.pam_eval_glued_workspace_size.argtypes = [P(pam_problem), P(pam_plan), C.c_int64, P(C.c_size_t)]
         L.pam_eval_glued.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_int64,
                                      C.c_double, C.c_void_p, C.c_int, C.c_int, C.c_void_p, C.c_size_t,
@@ -284,6 +301,54 @@ def pam_errors_noalloc(problem, plan, model, K, err, stream=None):
     its scratch is a fixed 256 KiB array inside the library."""
     _check(lib().pam_errors_noalloc(C.byref(problem), C.byref(plan), C.byref(model.c_struct()),
                                     _ptr(K), _ptr(err), _stream(stream)), "pam_errors_noalloc")
+
+
+def pam_partition_cells(problem, x):
+    """Patch lists of a mesh given as cells with sampling points x [n, dim]
+    (host numpy): (patch_start int32 [S+1], patch_cells int32)."""
+    x = np.ascontiguousarray(np.asarray(x, dtype=np.float64))
+    n = x.shape[0]
+    S = int(np.prod(list(problem.n_sub)[:problem.dim]))
+    start = np.zeros(S + 1, dtype=np.int32)
+    _check(lib().pam_partition_cells(C.byref(problem), x.ctypes.data, n, start.ctypes.data, None),
+           "pam_partition_cells")
+    cells = np.zeros(max(int(start[-1]), 1), dtype=np.int32)
+    _check(lib().pam_partition_cells(C.byref(problem), x.ctypes.data, n, start.ctypes.data, cells.ctypes.data),
+           "pam_partition_cells")
+    return start, cells[:int(start[-1])]
+
+
+def pam_plan_create_cells(problem, params, n_cells, patch_start):
+    plan = pam_plan()
+    ps = np.ascontiguousarray(np.asarray(patch_start, dtype=np.int32))
+    _check(lib().pam_plan_create_cells(C.byref(problem), C.byref(params), int(n_cells), ps.ctypes.data,
+                                       C.byref(plan)), "pam_plan_create_cells")
+    return plan
+
+
+def pam_fit_cells(problem, params, plan, cells, K, model, workspace, stream=None, check=True):
+    code = lib().pam_fit_cells(C.byref(problem), C.byref(params), C.byref(plan), C.byref(cells), _ptr(K),
+                               C.byref(model.c_struct()), _ptr(workspace),
+                               workspace.numel() * workspace.element_size(), _stream(stream))
+    if check:
+        _check(code, "pam_fit_cells")
+    return code
+
+
+def pam_refine_cells(problem, params, plan, cells, K, model, n_levels, workspace, stream=None, check=True):
+    code = lib().pam_refine_cells(C.byref(problem), C.byref(params), C.byref(plan), C.byref(cells), _ptr(K),
+                                  C.byref(model.c_struct()), int(n_levels), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _stream(stream))
+    if check:
+        _check(code, "pam_refine_cells")
+    return code
+
+
+def pam_errors_cells(problem, plan, model, cells, K, err, workspace, precision=PAM_PREC_FP64, stream=None):
+    _check(lib().pam_errors_cells(C.byref(problem), C.byref(plan), C.byref(model.c_struct()), C.byref(cells),
+                                  _ptr(K), _ptr(err), int(precision), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _stream(stream)),
+           "pam_errors_cells")
 
 
 PAM_NN_PATCH2D, PAM_NN_LAYERED3D = 0, 1
@@ -483,3 +548,51 @@ class Fitter:
 
     def host_model(self):
         return self.model.to_host(self.n_cells, self.n_sub, self.plan.m_cap)
+
+
+class CellFitter(Fitter):
+    """A problem on a general mesh given as cells (sampling points x [n, dim]
+    and measures vol [n], host arrays): the patch lists are built on the host
+    (pam_partition_cells) and kept on the device with the points and
+    measures; fit/errors take the element values K [n] on the device."""
+
+    def __init__(self, n_cells, n_sub, overlap, g_init, x, vol, device="cuda", **params):
+        import torch
+        self.n_cells, self.n_sub = tuple(n_cells), tuple(n_sub)
+        self.problem = make_problem(n_cells, n_sub, overlap, g_init)
+        self.params = make_params(**params)
+        x = np.ascontiguousarray(np.asarray(x, dtype=np.float64).reshape(-1, len(self.n_cells)))
+        start, lists = pam_partition_cells(self.problem, x)
+        self.plan = pam_plan_create_cells(self.problem, self.params, x.shape[0], start)
+        self.device = device
+        self.x = torch.from_numpy(x).to(device)
+        self.vol = torch.from_numpy(np.ascontiguousarray(np.asarray(vol, dtype=np.float64))).to(device)
+        self.patch_start = torch.from_numpy(start).to(device)
+        self.patch_cells = torch.from_numpy(np.ascontiguousarray(lists) if lists.size else
+                                            np.zeros(1, dtype=np.int32)).to(device)
+        self.cells = pam_cells(x.shape[0], self.x.data_ptr(), self.vol.data_ptr(), self.patch_start.data_ptr(),
+                               self.patch_cells.data_ptr())
+        self.model = alloc_model(self.plan, device)
+        self.workspace = alloc_workspace(self.plan, device)
+
+    def fit(self, K, levels=None, stream=None, check=True, warm_start=False, deferred=False):
+        lv = self.params.levels if levels is None else levels
+        self.params.warm_start = 1 if warm_start else 0
+        self.params.deferred_status = 1 if deferred else 0
+        try:
+            c1 = pam_fit_cells(self.problem, self.params, self.plan, self.cells, K, self.model, self.workspace,
+                               stream, check)
+            c2 = pam_refine_cells(self.problem, self.params, self.plan, self.cells, K, self.model, lv,
+                                  self.workspace, stream, check) if lv > 0 else 0
+        finally:
+            self.params.warm_start = 0
+            self.params.deferred_status = 0
+        return c1 or c2
+
+    def errors_device(self, K, err, precision=None, stream=None, quad=None):
+        prec = self.params.precision if precision is None else precision
+        pam_errors_cells(self.problem, self.plan, self.model, self.cells, K, err, self.workspace, prec, stream)
+        return err
+
+    def lambda_cv(self, *a, **k):
+        raise PamError(PAM_ERR_UNSUPPORTED, "lambda_cv on a mesh given as cells")

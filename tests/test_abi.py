@@ -193,3 +193,57 @@ def test_eval_glued_checks_the_band_and_sizes(pam):
         too_many = ((1 << 31) - 1) // (1 << dim) + 1
         assert L.pam_eval_glued_workspace_size(C.byref(pr), C.byref(plan), too_many,
                                                C.byref(C.c_size_t(0))) == 6
+
+
+@pytest.mark.parametrize("mesh", ["triangles", "graded3d", "grid1d"])
+def test_partition_cells_matches_the_oracle(pam, mesh):
+    from paper_2605_16564_gb300 import fields
+    if mesh == "triangles":
+        shape, n_sub, ov = (40, 33), (3, 4), 2
+        x, _ = fields.triangle_mesh(40, seed=5, ny=33)
+    elif mesh == "graded3d":
+        shape, n_sub, ov = (12, 14, 9), (2, 3, 2), 1
+        x, _ = fields.graded_mesh(shape, seed=6)
+    else:
+        shape, n_sub, ov = (50,), (7,), 3
+        x = fields.grid_as_cells(np.ones(50), shape)[0]
+    pr = pam.make_problem(shape, n_sub, ov, (2,) * len(shape))
+    start, cells = pam.pam_partition_cells(pr, x)
+    _, ostart, ocells = oracle.partition_cells(shape, n_sub, ov, x)
+    np.testing.assert_array_equal(start, ostart)
+    np.testing.assert_array_equal(cells, ocells)
+
+
+def test_cells_entry_points_check_their_arguments(pam):
+    import ctypes as C
+    from paper_2605_16564_gb300 import fields
+    pr = pam.make_problem((16, 16), (2, 2), 1, (2, 2))
+    x, vol = fields.triangle_mesh(16, seed=1)
+    start, cells = pam.pam_partition_cells(pr, x)
+    # a point outside the domain, or NaN
+    for bad in ((1.5, 0.5), (np.nan, 0.2), (-0.01, 0.3)):
+        xb = x.copy()
+        xb[3] = bad
+        with pytest.raises(pam.PamError):
+            pam.pam_partition_cells(pr, xb)
+    # the Gauss-Legendre rule needs element shapes
+    with pytest.raises(pam.PamError) as e:
+        pam.pam_plan_create_cells(pr, pam.make_params(quad=1), x.shape[0], start)
+    assert e.value.code == pam.PAM_ERR_UNSUPPORTED
+    plan = pam.pam_plan_create_cells(pr, pam.make_params(levels=1, k_top=3), x.shape[0], start)
+    assert plan.max_patch_cells % 32 == 0 and plan.max_patch_cells >= int(np.diff(start).max())
+    grid_plan = pam.pam_plan_create(pr, pam.make_params(levels=1, k_top=3))
+    assert plan.workspace_bytes > grid_plan.workspace_bytes or plan.max_patch_cells != grid_plan.max_patch_cells
+    fake = C.c_void_p(256)
+    m = pam.pam_model(fake, fake, fake, fake)
+    par = pam.make_params(levels=1, k_top=3)
+    L = pam.lib()
+    good = pam.pam_cells(x.shape[0], 256, 256, 256, 256)
+    for cells_s in (pam.pam_cells(x.shape[0] + 1, 256, 256, 256, 256),   # count differs from the plan
+                    pam.pam_cells(x.shape[0], 0, 256, 256, 256)):         # missing points
+        assert L.pam_fit_cells(C.byref(pr), C.byref(par), C.byref(plan), C.byref(cells_s), fake, C.byref(m),
+                               fake, 1 << 40, None) == 1
+    assert L.pam_fit_cells(C.byref(pr), C.byref(par), C.byref(plan), C.byref(good), fake, C.byref(m),
+                           fake, 16, None) == 4  # workspace too small
+    assert L.pam_errors_cells(C.byref(pr), C.byref(plan), C.byref(m), C.byref(good), fake, fake, 5, fake,
+                              1 << 40, None) == 1  # unknown precision
