@@ -355,6 +355,20 @@ __device__ __forceinline__ void glue_factors(int c, int n, int p, double h, doub
     *r = c < p - 1 ? glue_ramp(__ddiv_rn(__dsub_rn(__dadd_rn(__dmul_rn((double)hi, h), delta), xa), two_d)) : 1.0;
 }
 
+// fp32 form of the face factors (the mixed evaluation): the offset from the
+// face in binary64, the ramp in fp32 (relative error ~1e-7, like the fp32
+// local surrogates it blends).
+__device__ __forceinline__ float glue_ramp_f(float t) {
+    t = fminf(fmaxf(t, 0.f), 1.f);
+    return t * t * (3.f - 2.f * t);
+}
+__device__ __forceinline__ void glue_factors_f(int c, int n, int p, double h, float df, float inv, double xa,
+                                               double *l, double *r) {
+    const int64_t lo = ((int64_t)c * n) / p, hi = ((int64_t)(c + 1) * n) / p;
+    *l = c > 0 ? (double)glue_ramp_f(((float)(xa - (double)lo * h) + df) * inv) : 1.0;
+    *r = c < p - 1 ? (double)glue_ramp_f(((float)((double)hi * h - xa) + df) * inv) : 1.0;
+}
+
 // The pairs of point x: subdomain s[c] and weight psi[c] for the valid slots
 // c (bit c of the returned mask). Mask 0: x lies outside the grid. Along
 // each axis the owner core j carries weight, and so does at most one of its
@@ -363,10 +377,11 @@ __device__ __forceinline__ void glue_factors(int c, int n, int p, double h, doub
 // weight below 2^-100, and the larger is kept). Candidate 0 is the lower
 // core, so ascending c is ascending subdomain index. The weight multiplies
 // the face factors axis by axis, lower face first, in unfused binary64.
-template <int D>
+template <int D, bool F32W = false>
 __device__ __forceinline__ unsigned glue_pairs(const Geo &g, double delta, const double x[3], int s[8],
                                                double psi[8]) {
     const double two_d = 2.0 * delta;
+    const float df = (float)delta, inv = 1.0f / (2.0f * df);  // fp32 weights only
     int c0[3] = {0, 0, 0}, c1[3] = {0, 0, 0}, cnt[3] = {1, 1, 1};
     double l0[3] = {1.0, 1.0, 1.0}, r0[3] = {1.0, 1.0, 1.0}, l1[3] = {1.0, 1.0, 1.0}, r1[3] = {1.0, 1.0, 1.0};
     bool inside = true;
@@ -388,9 +403,15 @@ __device__ __forceinline__ unsigned glue_pairs(const Geo &g, double delta, const
             c0[a] = j;
         } else {
             double lj, rj, lm = 0.0, rm = 0.0, lp = 0.0, rp = 0.0;
-            glue_factors(j, g.n[a], g.p[a], g.h, delta, two_d, x[a], &lj, &rj);
-            if (!far_lo) glue_factors(j - 1, g.n[a], g.p[a], g.h, delta, two_d, x[a], &lm, &rm);
-            if (!far_hi) glue_factors(j + 1, g.n[a], g.p[a], g.h, delta, two_d, x[a], &lp, &rp);
+            if (F32W) {
+                glue_factors_f(j, g.n[a], g.p[a], g.h, df, inv, x[a], &lj, &rj);
+                if (!far_lo) glue_factors_f(j - 1, g.n[a], g.p[a], g.h, df, inv, x[a], &lm, &rm);
+                if (!far_hi) glue_factors_f(j + 1, g.n[a], g.p[a], g.h, df, inv, x[a], &lp, &rp);
+            } else {
+                glue_factors(j, g.n[a], g.p[a], g.h, delta, two_d, x[a], &lj, &rj);
+                if (!far_lo) glue_factors(j - 1, g.n[a], g.p[a], g.h, delta, two_d, x[a], &lm, &rm);
+                if (!far_hi) glue_factors(j + 1, g.n[a], g.p[a], g.h, delta, two_d, x[a], &lp, &rp);
+            }
             const double wm = __dmul_rn(lm, rm), wp = __dmul_rn(lp, rp);
             bool use_m = wm > 0.0, use_p = wp > 0.0;
             if (use_m && use_p) {
@@ -416,8 +437,12 @@ __device__ __forceinline__ unsigned glue_pairs(const Geo &g, double delta, const
         for (int a = 0; a < D; ++a) {
             const bool up = (c >> a) & 1;
             ok = ok && (!up || cnt[a] == 2);
-            w = __dmul_rn(w, up ? l1[a] : l0[a]);
-            w = __dmul_rn(w, up ? r1[a] : r0[a]);
+            if (F32W) {
+                w = (double)((float)w * (float)(up ? l1[a] : l0[a]) * (float)(up ? r1[a] : r0[a]));
+            } else {
+                w = __dmul_rn(w, up ? l1[a] : l0[a]);
+                w = __dmul_rn(w, up ? r1[a] : r0[a]);
+            }
             idx += (up ? c1[a] : c0[a]) * mul;
             mul *= g.p[a];
         }
@@ -434,7 +459,7 @@ __device__ __forceinline__ void load_point(const Geo &g, const double *pts, int6
     for (int a = 0; a < g.dim; ++a) x[a] = pts[p * g.dim + a];
 }
 
-template <int D>
+template <int D, bool F32W>
 __global__ void k_glue_count(Geo g, double delta, const double *pts, int64_t n, int32_t *rank,
                              int32_t *count, double *out, GlueWs e) {
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -444,7 +469,7 @@ __global__ void k_glue_count(Geo g, double delta, const double *pts, int64_t n, 
     if (p < n) {
         double x[3];
         load_point(g, pts, p, x);
-        mask = glue_pairs<D>(g, delta, x, s, psi);
+        mask = glue_pairs<D, F32W>(g, delta, x, s, psi);
         if (mask == 0u) out[p] = nan("");
         e.mask[p] = (uint8_t)mask;
     }
@@ -535,6 +560,19 @@ __global__ void k_glue_combine(int64_t n, GlueWs e, double *out, int log_space) 
     const unsigned mask = e.mask[p];
     if (mask == 0u) return;  // NaN written by k_glue_count
     constexpr int nslot = 1 << D;
+    if (F32) {  // the fp32 form blends in fp32 (its local surrogates are fp32)
+        float num = 0.f, den = 0.f;
+#pragma unroll
+        for (int c = 0; c < nslot; ++c)
+            if ((mask >> c) & 1u) {
+                const float w = (float)e.psi[p * nslot + c];
+                num = fmaf(w, (float)e.val[p * nslot + c], num);
+                den += w;
+            }
+        const float v = num / den;
+        out[p] = log_space ? (double)v : exp_f32(v);
+        return;
+    }
     double num = 0.0, den = 0.0;
 #pragma unroll
     for (int c = 0; c < nslot; ++c)
@@ -544,7 +582,7 @@ __global__ void k_glue_combine(int64_t n, GlueWs e, double *out, int log_space) 
             den = __dadd_rn(den, w);
         }
     const double v = num / den;
-    out[p] = log_space ? v : (F32 ? exp_f32((float)v) : exp(v));
+    out[p] = log_space ? v : exp(v);
 }
 
 template <int D>
@@ -552,7 +590,10 @@ static void glue_launches(const Geo &g, const int32_t *boxes, const double *cent
                           const int32_t *info, const double *pts, int64_t n_pts, double delta, double *out,
                           int log_space, int precision, const GlueWs &e, cudaStream_t st) {
     const unsigned nb = (unsigned)((n_pts + 255) / 256);
-    k_glue_count<D><<<nb, 256, 0, st>>>(g, delta, pts, n_pts, e.rank, e.count, out, e);
+    if (precision == PAM_PREC_MIXED)
+        k_glue_count<D, true><<<nb, 256, 0, st>>>(g, delta, pts, n_pts, e.rank, e.count, out, e);
+    else
+        k_glue_count<D, false><<<nb, 256, 0, st>>>(g, delta, pts, n_pts, e.rank, e.count, out, e);
     k_eval_scan<<<1, 1024, 0, st>>>(e.count, e.start, g.S);
     k_glue_scatter<D><<<nb, 256, 0, st>>>(n_pts, e.start, e);
     if (precision == PAM_PREC_MIXED) {
