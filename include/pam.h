@@ -360,6 +360,39 @@ pam_status pam_errors_noalloc(const pam_problem *prob, const pam_plan *plan,
                               void *stream);
 
 /*
+ * Checkpoint and resume (no counterpart in the paper, which fits in one
+ * run). A model serialises as one flat host blob: a header (magic
+ * "PAMMODEL", version 1, dim, n_cells, n_sub, overlap, g_init, S, m_cap)
+ * followed by boxes int32 [S][12], centres double [S][m_cap][4], beta
+ * double [S][m_cap] and info int32 [S][PAM_INFO_N], in host byte order.
+ *   pam_model_save  h_buf NULL: *size receives the blob size; otherwise
+ *                   *size must be at least that (else PAM_ERR_INVALID_ARG
+ *                   with *size set) and the blob is written; synchronises
+ *                   `stream` once.
+ *   pam_model_load  checks the header against the problem and plan, the
+ *                   boxes against pam_partition and every M_i against the
+ *                   capacity (PAM_ERR_INVALID_ARG on any mismatch, nothing
+ *                   copied), then copies the blob into the device model;
+ *                   synchronises once.
+ *   pam_resume      makes a workspace ready for pam_refine on a loaded
+ *                   model: prepares the cell data of d_K and solves every
+ *                   subdomain still running (info STOPPED = 0) from the
+ *                   model's coefficients (the same unique minimiser, so the
+ *                   coefficients are those of the saved fit up to the solve's
+ *                   rounding), which also recomputes the indicators. Returns
+ *                   as pam_fit_subdomains. pam_resume_cells: the same for a
+ *                   mesh given as cells.
+ * The network weights of the learned warm start are the caller's fp32
+ * arrays (pam_nn_*) and are saved by the caller.
+ */
+pam_status pam_model_save(const pam_problem *prob, const pam_plan *plan, const pam_model *model, void *h_buf,
+                          size_t *size, void *stream);
+pam_status pam_model_load(const pam_problem *prob, const pam_plan *plan, const void *h_buf, size_t size,
+                          pam_model *model, void *stream);
+pam_status pam_resume(const pam_problem *prob, const pam_params *par, const pam_plan *plan, const double *d_K,
+                      pam_model *model, void *d_workspace, size_t workspace_bytes, void *stream);
+
+/*
  * General meshes given as cells (section 2: the data are piecewise constant
  * on the elements T of a shape-regular partition -- intervals, triangles,
  * quadrilaterals, ... -- each with a sampling point x_T in T, e.g. its
@@ -419,6 +452,9 @@ pam_status pam_refine_cells(const pam_problem *prob, const pam_params *par, cons
 pam_status pam_errors_cells(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
                             const pam_cells *cells, const double *d_K, double *d_err, int precision,
                             void *d_workspace, size_t workspace_bytes, void *stream);
+pam_status pam_resume_cells(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                            const pam_cells *cells, const double *d_K, pam_model *model, void *d_workspace,
+                            size_t workspace_bytes, void *stream);
 
 /*
  * Learned warm start (spec addition; the paper has no learned part).

@@ -751,4 +751,181 @@ pam_status pam_errors_cells(const pam_problem *prob, const pam_plan *plan, const
     return PAM_OK;
 }
 
+// ------------------------------------------------ checkpoint / resume ---
+
+namespace {
+struct ModelBlobHeader {
+    char magic[8];      // "PAMMODEL"
+    int32_t version;    // 1
+    int32_t dim;
+    int32_t n_cells[3];
+    int32_t n_sub[3];
+    int32_t overlap;
+    int32_t g_init[3];
+    int32_t n_subdomains;
+    int32_t m_cap;
+    int32_t reserved[4];
+};
+const char kBlobMagic[8] = {'P', 'A', 'M', 'M', 'O', 'D', 'E', 'L'};
+
+size_t blob_bytes(int S, int m_cap) {
+    return sizeof(ModelBlobHeader) + (size_t)S * 12 * sizeof(int32_t) + (size_t)S * m_cap * 4 * sizeof(double) +
+           (size_t)S * m_cap * sizeof(double) + (size_t)S * PAM_INFO_N * sizeof(int32_t);
+}
+
+pam_status blob_geometry(const pam_problem *prob, const pam_plan *plan, Geo *g) {
+    pam_status st;
+    if (!make_geo(prob, nullptr, g, nullptr, &st)) return st;
+    if (!plan || plan->n_subdomains != g->S || plan->m_cap < 1 || plan->m_cap > PAM_MAX_M ||
+        plan->m_cap % 64 != 0)
+        return PAM_ERR_INVALID_ARG;
+    return PAM_OK;
+}
+}  // namespace
+
+pam_status pam_model_save(const pam_problem *prob, const pam_plan *plan, const pam_model *model, void *h_buf,
+                          size_t *size, void *stream) {
+    Geo g;
+    pam_status st;
+    if (!size) return PAM_ERR_INVALID_ARG;
+    if ((st = blob_geometry(prob, plan, &g)) != PAM_OK) return st;
+    const size_t need = blob_bytes(g.S, plan->m_cap);
+    if (!h_buf) {
+        *size = need;
+        return PAM_OK;
+    }
+    if (*size < need) {
+        *size = need;
+        return PAM_ERR_INVALID_ARG;
+    }
+    if (!model_ok(model)) return PAM_ERR_INVALID_ARG;
+    ModelBlobHeader h;
+    memset(&h, 0, sizeof(h));
+    memcpy(h.magic, kBlobMagic, 8);
+    h.version = 1;
+    h.dim = prob->dim;
+    for (int a = 0; a < 3; ++a) {
+        h.n_cells[a] = g.n[a];
+        h.n_sub[a] = g.p[a];
+        h.g_init[a] = g.g[a];
+    }
+    h.overlap = g.overlap;
+    h.n_subdomains = g.S;
+    h.m_cap = plan->m_cap;
+    char *b = (char *)h_buf;
+    memcpy(b, &h, sizeof(h));
+    size_t off = sizeof(h);
+    const size_t S = (size_t)g.S, mc = (size_t)plan->m_cap;
+    cudaStream_t st_ = (cudaStream_t)stream;
+    PAM_CUDA_TRY(cudaMemcpyAsync(b + off, model->boxes, S * 12 * 4, cudaMemcpyDeviceToHost, st_));
+    off += S * 12 * 4;
+    PAM_CUDA_TRY(cudaMemcpyAsync(b + off, model->centres, S * mc * 4 * 8, cudaMemcpyDeviceToHost, st_));
+    off += S * mc * 4 * 8;
+    PAM_CUDA_TRY(cudaMemcpyAsync(b + off, model->beta, S * mc * 8, cudaMemcpyDeviceToHost, st_));
+    off += S * mc * 8;
+    PAM_CUDA_TRY(cudaMemcpyAsync(b + off, model->info, S * PAM_INFO_N * 4, cudaMemcpyDeviceToHost, st_));
+    PAM_CUDA_TRY(cudaStreamSynchronize(st_));
+    *size = need;
+    return PAM_OK;
+}
+
+pam_status pam_model_load(const pam_problem *prob, const pam_plan *plan, const void *h_buf, size_t size,
+                          pam_model *model, void *stream) {
+    Geo g;
+    pam_status st;
+    if ((st = blob_geometry(prob, plan, &g)) != PAM_OK) return st;
+    if (!h_buf || !model_ok(model)) return PAM_ERR_INVALID_ARG;
+    const size_t need = blob_bytes(g.S, plan->m_cap);
+    if (size < need) return PAM_ERR_INVALID_ARG;
+    ModelBlobHeader h;
+    memcpy(&h, h_buf, sizeof(h));
+    if (memcmp(h.magic, kBlobMagic, 8) != 0 || h.version != 1 || h.dim != prob->dim || h.overlap != g.overlap ||
+        h.n_subdomains != g.S || h.m_cap != plan->m_cap)
+        return PAM_ERR_INVALID_ARG;
+    for (int a = 0; a < 3; ++a)
+        if (h.n_cells[a] != g.n[a] || h.n_sub[a] != g.p[a] || h.g_init[a] != g.g[a]) return PAM_ERR_INVALID_ARG;
+    const char *b = (const char *)h_buf;
+    const size_t S = (size_t)g.S, mc = (size_t)plan->m_cap;
+    // the boxes must be this problem's partition, and every size within the capacity
+    std::vector<int32_t> boxes(S * 12);
+    if ((st = pam_partition(prob, boxes.data())) != PAM_OK) return st;
+    if (memcmp(boxes.data(), b + sizeof(h), S * 12 * 4) != 0) return PAM_ERR_INVALID_ARG;
+    const char *info = b + sizeof(h) + S * 12 * 4 + S * mc * 40;
+    for (size_t s = 0; s < S; ++s) {
+        int32_t m;
+        memcpy(&m, info + (s * PAM_INFO_N + PAM_INFO_M) * sizeof(int32_t), sizeof(m));  // any alignment
+        if (m < 1 || m > (int32_t)mc) return PAM_ERR_INVALID_ARG;
+    }
+    cudaStream_t st_ = (cudaStream_t)stream;
+    size_t off = sizeof(h);
+    PAM_CUDA_TRY(cudaMemcpyAsync(model->boxes, b + off, S * 12 * 4, cudaMemcpyHostToDevice, st_));
+    off += S * 12 * 4;
+    PAM_CUDA_TRY(cudaMemcpyAsync(model->centres, b + off, S * mc * 4 * 8, cudaMemcpyHostToDevice, st_));
+    off += S * mc * 4 * 8;
+    PAM_CUDA_TRY(cudaMemcpyAsync(model->beta, b + off, S * mc * 8, cudaMemcpyHostToDevice, st_));
+    off += S * mc * 8;
+    PAM_CUDA_TRY(cudaMemcpyAsync(model->info, b + off, S * PAM_INFO_N * 4, cudaMemcpyHostToDevice, st_));
+    PAM_CUDA_TRY(cudaStreamSynchronize(st_));
+    return PAM_OK;
+}
+
+// Data preparation and one solve of every running subdomain from the
+// model's coefficients: afterwards the workspace holds what pam_refine
+// reads (cell data, indicators of the current coefficients).
+static pam_status resume_launches(const Geo &g, const Par &p, const pam_params *par, const double *d_K,
+                                  pam_model *model, const Ws &w, cudaStream_t s) {
+    pam_status st;
+    const bool deferred = par->deferred_status != 0;
+    PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 8 * sizeof(int32_t), s));
+    launch_prepare(g, model->boxes, d_K, w, s);
+    PAM_CUDA_TRY(cudaGetLastError());
+    int32_t hs[8];
+    if (!deferred) {
+        if ((st = read_status(w, s, hs)) != PAM_OK) return st;
+        if (hs[kStBadK]) return PAM_ERR_NONPOSITIVE_K;
+    }
+    if (par->precision == PAM_PREC_MIXED)
+        launch_solve_level_mixed(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
+    else
+        launch_solve_level_f64(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
+    PAM_CUDA_TRY(cudaGetLastError());
+    if (deferred) return PAM_OK;
+    if ((st = read_status(w, s, hs)) != PAM_OK) return st;
+    if (hs[kStTimeout]) return PAM_ERR_TIMEOUT;
+    return hs[kStUncertified] ? PAM_ERR_NOT_CONVERGED : PAM_OK;
+}
+
+pam_status pam_resume(const pam_problem *prob, const pam_params *par, const pam_plan *plan, const double *d_K,
+                      pam_model *model, void *d_workspace, size_t workspace_bytes, void *stream) {
+    Geo g;
+    Par p;
+    pam_status st;
+    if (!par || !make_geo(prob, par, &g, &p, &st)) return par ? st : PAM_ERR_INVALID_ARG;
+    if ((st = check_plan(g, plan)) != PAM_OK) return st;
+    g.m_cap = plan->m_cap;
+    if (par->precision == PAM_PREC_MIXED && (g.m_cap > kMixedMaxM || !mixed_solve_fits(g)))
+        return PAM_ERR_UNSUPPORTED;
+    if (!d_K || !model_ok(model) || !d_workspace) return PAM_ERR_INVALID_ARG;
+    Ws w = carve_workspace(g, d_workspace);
+    if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
+    return resume_launches(g, p, par, d_K, model, w, (cudaStream_t)stream);
+}
+
+pam_status pam_resume_cells(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                            const pam_cells *cells, const double *d_K, pam_model *model, void *d_workspace,
+                            size_t workspace_bytes, void *stream) {
+    Geo g;
+    Par p;
+    pam_status st;
+    if (!par) return PAM_ERR_INVALID_ARG;
+    if ((st = cells_setup(prob, par, plan, cells, &g, &p)) != PAM_OK) return st;
+    if (par->precision == PAM_PREC_MIXED && (g.m_cap > kMixedMaxM || !mixed_solve_fits(g)))
+        return PAM_ERR_UNSUPPORTED;
+    if (!d_K || !model_ok(model) || !d_workspace) return PAM_ERR_INVALID_ARG;
+    Ws w = carve_workspace(g, d_workspace);
+    if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
+    g.cxv = w.cxv;
+    return resume_launches(g, p, par, d_K, model, w, (cudaStream_t)stream);
+}
+
 }  // extern "C"

@@ -35,7 +35,8 @@ EXPORTED = ["pam_version", "pam_status_string", "pam_plan_create", "pam_partitio
             "pam_fit_subdomains", "pam_refine", "pam_gram", "pam_eval_workspace_size", "pam_eval",
             "pam_errors", "pam_status_read", "pam_lambda_cv_workspace_size", "pam_lambda_cv",
             "pam_eval_glued_workspace_size", "pam_eval_glued", "pam_partition_cells", "pam_plan_create_cells",
-            "pam_fit_cells", "pam_refine_cells", "pam_errors_cells"]
+            "pam_fit_cells", "pam_refine_cells", "pam_errors_cells", "pam_model_save", "pam_model_load",
+            "pam_resume", "pam_resume_cells"]
 
 
 class PamError(RuntimeError):
@@ -109,8 +110,15 @@ def lib():
                                        P(pam_model), C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_errors_cells.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), P(pam_cells), C.c_void_p,
                                        C.c_void_p, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_model_save.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, P(C.c_size_t),
+                                     C.c_void_p]
+        L.pam_model_load.argtypes = [P(pam_problem), P(pam_plan), C.c_void_p, C.c_size_t, P(pam_model), C.c_void_p]
+        L.pam_resume.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), C.c_void_p, P(pam_model), C.c_void_p,
+                                 C.c_size_t, C.c_void_p]
+        L.pam_resume_cells.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), P(pam_cells), C.c_void_p,
+                                       P(pam_model), C.c_void_p, C.c_size_t, C.c_void_p]
         for name in ("pam_partition_cells", "pam_plan_create_cells", "pam_fit_cells", "pam_refine_cells",
-                     "pam_errors_cells"):
+                     "pam_errors_cells", "pam_model_save", "pam_model_load", "pam_resume", "pam_resume_cells"):
             getattr(L, name).restype = C.c_int
         L.pam_eval_glued_workspace_size.argtypes = [P(pam_problem), P(pam_plan), C.c_int64, P(C.c_size_t)]
         L.pam_eval_glued.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_int64,
@@ -351,6 +359,41 @@ def pam_errors_cells(problem, plan, model, cells, K, err, workspace, precision=P
            "pam_errors_cells")
 
 
+def pam_model_save(problem, plan, model, stream=None):
+    """The model as a flat checkpoint blob (bytes)."""
+    n = C.c_size_t(0)
+    _check(lib().pam_model_save(C.byref(problem), C.byref(plan), C.byref(model.c_struct()), None, C.byref(n),
+                                _stream(stream)), "pam_model_save")
+    buf = np.zeros(int(n.value), dtype=np.uint8)
+    _check(lib().pam_model_save(C.byref(problem), C.byref(plan), C.byref(model.c_struct()), buf.ctypes.data,
+                                C.byref(n), _stream(stream)), "pam_model_save")
+    return buf.tobytes()
+
+
+def pam_model_load(problem, plan, blob, model, stream=None):
+    """Copies a checkpoint blob (from pam_model_save) into a device model."""
+    buf = np.frombuffer(blob, dtype=np.uint8)
+    _check(lib().pam_model_load(C.byref(problem), C.byref(plan), buf.ctypes.data, buf.size,
+                                C.byref(model.c_struct()), _stream(stream)), "pam_model_load")
+
+
+def pam_resume(problem, params, plan, K, model, workspace, stream=None, check=True):
+    code = lib().pam_resume(C.byref(problem), C.byref(params), C.byref(plan), _ptr(K), C.byref(model.c_struct()),
+                            _ptr(workspace), workspace.numel() * workspace.element_size(), _stream(stream))
+    if check:
+        _check(code, "pam_resume")
+    return code
+
+
+def pam_resume_cells(problem, params, plan, cells, K, model, workspace, stream=None, check=True):
+    code = lib().pam_resume_cells(C.byref(problem), C.byref(params), C.byref(plan), C.byref(cells), _ptr(K),
+                                  C.byref(model.c_struct()), _ptr(workspace),
+                                  workspace.numel() * workspace.element_size(), _stream(stream))
+    if check:
+        _check(code, "pam_resume_cells")
+    return code
+
+
 PAM_NN_PATCH2D, PAM_NN_LAYERED3D = 0, 1
 
 
@@ -549,6 +592,22 @@ class Fitter:
     def host_model(self):
         return self.model.to_host(self.n_cells, self.n_sub, self.plan.m_cap)
 
+    def save(self, stream=None):
+        """Checkpoint of the model (bytes, pam_model_save)."""
+        return pam_model_save(self.problem, self.plan, self.model, stream)
+
+    def load(self, blob, stream=None):
+        """Loads a checkpoint into this fitter's model (pam_model_load)."""
+        pam_model_load(self.problem, self.plan, blob, self.model, stream)
+
+    def resume(self, K, levels=0, stream=None, check=True):
+        """Readies the workspace for the loaded model and K (pam_resume), then
+        runs `levels` more refinement rounds."""
+        c1 = pam_resume(self.problem, self.params, self.plan, K, self.model, self.workspace, stream, check)
+        c2 = pam_refine(self.problem, self.params, self.plan, K, self.model, levels, self.workspace, stream,
+                        check) if levels > 0 else 0
+        return c1 or c2
+
 
 class CellFitter(Fitter):
     """A problem on a general mesh given as cells (sampling points x [n, dim]
@@ -593,6 +652,13 @@ class CellFitter(Fitter):
         prec = self.params.precision if precision is None else precision
         pam_errors_cells(self.problem, self.plan, self.model, self.cells, K, err, self.workspace, prec, stream)
         return err
+
+    def resume(self, K, levels=0, stream=None, check=True):
+        c1 = pam_resume_cells(self.problem, self.params, self.plan, self.cells, K, self.model, self.workspace,
+                              stream, check)
+        c2 = pam_refine_cells(self.problem, self.params, self.plan, self.cells, K, self.model, levels,
+                              self.workspace, stream, check) if levels > 0 else 0
+        return c1 or c2
 
     def lambda_cv(self, *a, **k):
         raise PamError(PAM_ERR_UNSUPPORTED, "lambda_cv on a mesh given as cells")

@@ -247,3 +247,38 @@ def test_cells_entry_points_check_their_arguments(pam):
                            fake, 16, None) == 4  # workspace too small
     assert L.pam_errors_cells(C.byref(pr), C.byref(plan), C.byref(m), C.byref(good), fake, fake, 5, fake,
                               1 << 40, None) == 1  # unknown precision
+
+
+def test_model_blob_checks_without_a_gpu(pam):
+    import ctypes as C
+    pr = pam.make_problem((32, 32), (2, 2), 1, (3, 3))
+    plan = pam.pam_plan_create(pr, pam.make_params(levels=1, k_top=4))
+    fake = C.c_void_p(256)
+    m = pam.pam_model(fake, fake, fake, fake)
+    L = pam.lib()
+    n = C.c_size_t(0)
+    assert L.pam_model_save(C.byref(pr), C.byref(plan), C.byref(m), None, C.byref(n), None) == 0
+    S, mc = plan.n_subdomains, plan.m_cap
+    assert n.value == 80 + S * 12 * 4 + S * mc * 40 + S * 8 * 4
+    small = C.c_size_t(16)
+    buf = (C.c_uint8 * 16)()
+    assert L.pam_model_save(C.byref(pr), C.byref(plan), C.byref(m), buf, C.byref(small), None) == 1
+    assert small.value == n.value
+    # a blob with the right header but boxes of another decomposition is rejected
+    # before anything is copied
+    blob = np.zeros(n.value, dtype=np.uint8)
+    hdr = np.zeros(18, dtype=np.int32)
+    hdr[0], hdr[1] = 1, 2                    # version, dim
+    hdr[2:5] = (32, 32, 1); hdr[5:8] = (2, 2, 1); hdr[8] = 1; hdr[9:12] = (3, 3, 1)
+    hdr[12], hdr[13] = S, mc
+    blob[:8] = np.frombuffer(b"PAMMODEL", dtype=np.uint8)
+    blob[8:80] = hdr.view(np.uint8)
+    assert L.pam_model_load(C.byref(pr), C.byref(plan), blob.ctypes.data, blob.size, C.byref(m), None) == 1
+    boxes = pam.pam_partition(pr)
+    blob[80:80 + boxes.nbytes] = boxes.reshape(-1).view(np.uint8)
+    # boxes right, but every M_i is 0
+    assert L.pam_model_load(C.byref(pr), C.byref(plan), blob.ctypes.data, blob.size, C.byref(m), None) == 1
+    blob2 = blob.copy()
+    blob2[0] = ord("X")
+    assert L.pam_model_load(C.byref(pr), C.byref(plan), blob2.ctypes.data, blob2.size, C.byref(m), None) == 1
+    assert L.pam_model_load(C.byref(pr), C.byref(plan), blob.ctypes.data, blob.size - 1, C.byref(m), None) == 1
