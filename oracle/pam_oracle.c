@@ -654,6 +654,18 @@ static int fit_patch(int dim, int64_t N, const double *x, const double *y, const
                      const double *c0, int m0, const orc_params *P, int m_cap, double *c, double *beta,
                      double *info)
 {
+    /* Reading: a patch without elements (a mesh with a hole) has no data and,
+     * with lambda_k = N lambda_k_hat, no penalty; its coefficients are the
+     * limit of the unique minimisers as lambda -> 0+ with G = 0, b = 0, i.e.
+     * beta = 0, and Algorithm 1 stops at once. */
+    if (N == 0) {
+        memset(c, 0, sizeof(double) * (size_t)m_cap * 4);
+        memset(beta, 0, sizeof(double) * (size_t)m_cap);
+        memcpy(c, c0, sizeof(double) * (size_t)m0 * 4);
+        info[0] = m0; info[1] = 0; info[2] = 0; info[3] = 1;
+        info[4] = 1.0; info[5] = 0; info[6] = 0; info[7] = 0;
+        return 0;
+    }
     double kmax = 0.0;
     for (int64_t j = 0; j < N; ++j) if (kv[j] > kmax) kmax = kv[j];
     double *eps = (double *)malloc(sizeof(double) * (size_t)(N > 0 ? N : 1));

@@ -27,7 +27,7 @@ import numpy as np
 __all__ = [
     "cell_size", "numpy_shape", "disc_field", "voronoi_field", "channel_field",
     "layered_field", "patch_batch", "cell_centred_points", "step_field_1d",
-    "grid_as_cells", "triangle_mesh", "graded_mesh", "voronoi_at",
+    "grid_as_cells", "triangle_mesh", "graded_mesh", "voronoi_at", "cut_box",
 ]
 
 
@@ -273,3 +273,11 @@ def graded_mesh(shape, seed: int = 12, ratio: float = 3.0):
     x = np.stack([g.reshape(-1) for g in reversed(grids)], axis=1)
     vol = np.prod(np.stack([g.reshape(-1) for g in wgrid], axis=1), axis=1)
     return x, vol
+
+
+def cut_box(x: np.ndarray, vol: np.ndarray, lo, hi):
+    """The mesh (x, vol) without the elements whose sampling point lies in the
+    open box (lo, hi): a domain with a rectangular hole."""
+    x = np.asarray(x)
+    inside = np.all((x > np.asarray(lo)) & (x < np.asarray(hi)), axis=1)
+    return np.ascontiguousarray(x[~inside]), np.ascontiguousarray(np.asarray(vol)[~inside])

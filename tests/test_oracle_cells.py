@@ -174,3 +174,29 @@ def test_step_error_does_not_increase_with_levels_on_a_graded_1d_mesh():
         prev = e
     assert prev < 0.5 * oracle.errors_cells(
         oracle.fit_cells(x, vol, K, (120,), (1,), 0, (4,), oracle.default_params(levels=0, k_top=2)), x, vol, K)["l1"]
+
+
+def test_a_hole_that_empties_a_patch():
+    # reading: no elements -> beta = 0 (the limit of the minimisers as
+    # lambda -> 0+ with G = 0, b = 0), stopped at once, K* = 1 in its core;
+    # the other subdomains are fitted exactly as without it
+    h = 1 / 64
+    x, vol = fields.triangle_mesh(64, seed=61)
+    x, vol = fields.cut_box(x, vol, (14.5 * h, 30.5 * h), (33.5 * h, 49.5 * h))
+    K = fields.voronoi_at(x, 10, 61)
+    geo = ((64, 64), (4, 4), 1, (4, 4))
+    p = oracle.default_params(levels=2, k_top=6)
+    m = oracle.fit_cells(x, vol, K, *geo, p)
+    sizes = np.diff(m["patch_start"])
+    assert sizes[9] == 0 and (np.delete(sizes, 9) > 0).all()
+    assert m["failed"] == 0
+    assert m["M"][9] == 16 and not m["beta"][9].any() and m["info"][9, 2] == 0
+    np.testing.assert_array_equal(m["c"][9, :16], oracle.initial_dictionary((64, 64), m["boxes"][9, 0:3],
+                                                                            m["boxes"][9, 3:6], (4, 4)))
+    assert oracle.evaluate(m, np.array([[24.0 * h, 40.0 * h]]))[0] == 1.0
+    others = [s for s in range(16) if s != 9]
+    m2 = oracle.fit_cells(x, vol, K, *geo, p, which=others)
+    for key in ("M", "c", "beta"):
+        np.testing.assert_array_equal(m[key][others], m2[key][others])
+    e = oracle.errors_cells(m, x, vol, K)
+    assert np.isfinite(e["l1"]) and e["l1"] < 1
