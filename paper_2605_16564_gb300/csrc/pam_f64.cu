@@ -154,8 +154,11 @@ __global__ void k_init_dictionary(Geo g, const int32_t *boxes, double *centres, 
         } else {
             c[0] = c[1] = c[2] = c[3] = 0.0;
         }
-        // a warm start keeps the caller's coefficients of the initial lattice
-        if (!keep_beta || m >= g.m0) beta[(size_t)s * g.m_cap + m] = 0.0;
+        // a warm start keeps the caller's coefficients of the initial lattice;
+        // a patch without elements (a mesh given as cells, e.g. with a hole)
+        // has no data: beta = 0
+        const bool empty = g.cells && g.pstart[s + 1] == g.pstart[s];
+        if (!keep_beta || m >= g.m0 || empty) beta[(size_t)s * g.m_cap + m] = 0.0;
     }
     if (m == 0) {
         int ext[3];
@@ -166,8 +169,9 @@ __global__ void k_init_dictionary(Geo g, const int32_t *boxes, double *centres, 
         inf[PAM_INFO_LEVELS] = 0;
         inf[PAM_INFO_ITERS] = 0;
         inf[PAM_INFO_FLAGS] = 0;
-        inf[PAM_INFO_STOPPED] = 0;
-        inf[PAM_INFO_N_CELLS] = g.cells ? g.pstart[s + 1] - g.pstart[s] : ext[0] * ext[1] * ext[2];
+        const int n_cells = g.cells ? g.pstart[s + 1] - g.pstart[s] : ext[0] * ext[1] * ext[2];
+        inf[PAM_INFO_STOPPED] = n_cells == 0 ? 1 : 0;  // nothing to fit: no solve, no refinement
+        inf[PAM_INFO_N_CELLS] = n_cells;
         inf[PAM_INFO_MARKED] = 0;
     }
 }

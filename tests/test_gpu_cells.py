@@ -152,3 +152,33 @@ def test_cells_bad_values_and_measures_are_reported(env):
         (K if which == "K" else v)[37] = bad
         fit = pam.CellFitter((16, 16), (2, 2), 1, (2, 2), x, v, device=dev)
         assert fit.fit(torch.from_numpy(K).to(dev), check=False) == pam.PAM_ERR_NONPOSITIVE_K, (which, bad)
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cells_mesh_with_a_hole_that_empties_a_patch(env, precision):
+    # a subdomain without elements: beta = 0, stopped at level 0, K* = 1 in
+    # its core, nothing flagged; the others as the oracle
+    torch, pam, dev = env
+    h = 1 / 64
+    x, vol = fields.triangle_mesh(64, seed=61)
+    x, vol = fields.cut_box(x, vol, (14.5 * h, 30.5 * h), (33.5 * h, 49.5 * h))
+    K = fields.voronoi_at(x, 10, 61)
+    geo = ((64, 64), (4, 4), 1, (4, 4))
+    params = dict(k_top=6, levels=2)
+    fit, Kd = _fit(env, x, vol, K, geo, precision=precision, **params)
+    ref = oracle.fit_cells(x, vol, K, *geo, oracle.default_params(**params))
+    got = fit.host_model()
+    assert got["info"][9, pam.INFO_N_CELLS] == 0 and got["info"][9, pam.INFO_STOPPED] == 1
+    assert not got["beta"][9].any() and got["M"][9] == 16
+    assert np.count_nonzero(got["info"][:, pam.INFO_FLAGS] & pam.FLAG_NOT_CERTIFIED) == 0
+    pts = np.array([[24.0 * h, 40.0 * h], [0.5, 0.1], [0.9, 0.9]])
+    out = fit.eval(torch.from_numpy(pts).to(dev)).cpu().numpy()
+    assert out[0] == pytest.approx(1.0, rel=1e-6)
+    if precision == 0:
+        _compare(got, ref)
+        np.testing.assert_allclose(out, oracle.evaluate(ref, pts), rtol=1e-10)
+        e_gpu, e_ref = fit.errors(Kd), oracle.errors_cells(ref, x, vol, K)
+        assert e_gpu["l1"] == pytest.approx(e_ref["l1"], rel=1e-9)
+    else:
+        e_m, e_o = fit.errors(Kd), oracle.errors_cells(ref, x, vol, K)
+        assert abs(e_m["l1"] - e_o["l1"]) <= L1_RTOL * e_o["l1"]
