@@ -1261,20 +1261,32 @@ __global__ void __launch_bounds__(1024) k_solve_order(const uint32_t *cost, int 
 // beyond it keep their factor in global memory (L1/L2). A smaller budget
 // lets more subdomains share an SM. PAM_FACTOR_SMEM_KB overrides the
 // default for tuning.
-static int factor_smem_bytes() {
-    static int v = -1;
-    if (v < 0) {
-        const char *e = getenv("PAM_FACTOR_SMEM_KB");
-        v = e ? atoi(e) * 1024 : kMxFactorBytesDefault;
-        if (v < 4096) v = 4096;
-    }
-    return v;
+// Shared memory of the mixed solve besides the packed factor.
+static size_t solve_mixed_smem_rest(const Geo &g) {
+    return (size_t)g.m_cap * (5 * sizeof(float) + 2 * sizeof(int) + sizeof(float4)) +
+           (size_t)g.n_max * (sizeof(float4) + 2 * sizeof(float)) + 64;
 }
 
-static size_t solve_mixed_smem(const Geo &g) {
-    return (size_t)g.m_cap * (5 * sizeof(float) + 2 * sizeof(int) + sizeof(float4)) +
-           (size_t)g.n_max * (sizeof(float4) + 2 * sizeof(float)) + factor_smem_bytes() + 64;
+// Shared-memory budget of the packed support factor (larger supports keep
+// their factor in global memory, L2-resident): the largest multiple of 1 KiB
+// up to 64 KiB with which two CTAs still fit on an SM (228 KiB per SM, 1 KiB
+// reserved per CTA, 1 KiB of static shared memory), so that the patch size
+// never halves the CTAs per SM; 64 KiB when even that cannot fit two.
+// PAM_FACTOR_SMEM_KB overrides it (tuning).
+static int factor_smem_bytes(const Geo &g) {
+    static int env = -2;
+    if (env == -2) {
+        const char *e = getenv("PAM_FACTOR_SMEM_KB");
+        env = e ? (atoi(e) * 1024 < 4096 ? 4096 : atoi(e) * 1024) : -1;
+    }
+    if (env > 0) return env;
+    const long long per_cta = 228 * 1024 / 2 - 1024 - 1024;
+    const long long room = (per_cta - (long long)solve_mixed_smem_rest(g)) / 1024 * 1024;
+    if (room < 16 * 1024) return kMxFactorBytesDefault;
+    return room < kMxFactorBytesDefault ? (int)room : kMxFactorBytesDefault;
 }
+
+static size_t solve_mixed_smem(const Geo &g) { return solve_mixed_smem_rest(g) + factor_smem_bytes(g); }
 
 #ifdef PAM_SOLVE_PROFILE
 extern "C" void pam_debug_gram_profile(unsigned long long *out, int reset) {
@@ -1314,7 +1326,7 @@ void launch_solve_mixed(const Geo &g, const Par &p, const int32_t *boxes, const 
         k_solve_order<<<1, 1024, (size_t)P * 8, st>>>(w.cost, g.S, P, w.order);
         count_launches(1);
     }
-    k_solve_mixed<<<g.S, kMxThreads, sm, st>>>(g, p, boxes, centres, beta, info, w, factor_smem_bytes(),
+    k_solve_mixed<<<g.S, kMxThreads, sm, st>>>(g, p, boxes, centres, beta, info, w, factor_smem_bytes(g),
                                                ordered, lam_tab, all, cv, cv_stride);
     count_launches(1);
 }
