@@ -306,8 +306,9 @@ pam_status pam_eval(const pam_problem *prob, const pam_plan *plan,
  *               local surrogates in fp32 as in pam_eval, the blend in
  *               binary64, the final exp in fp32)
  *   d_workspace at least pam_eval_glued_workspace_size bytes (2^dim
- *               (point, subdomain) slots per point: 16 bytes each, plus 8
- *               per subdomain)
+ *               (point, subdomain) slots per point, 28 bytes each: local
+ *               value, weight, subdomain, rank, bucket entry; one byte per
+ *               point and 8 per subdomain)
  * The per-point sum runs over the subdomains in ascending index order
  * (deterministic). PAM_ERR_UNSUPPORTED above (2^31 - 1) / 2^dim points.
  * Asynchronous (no synchronisation); n_pts == 0 is a no-op.
