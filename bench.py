@@ -384,6 +384,18 @@ def run_pam(args, rank, ws):
         step()
     torch.cuda.synchronize()
 
+    # launch tuning measured on this fitted problem (outside the timed region)
+    tune = None
+    if not args.no_autotune:
+        choice, ms = fit.autotune(Kd, ptsd)
+        names = ["gram_stages=3", "gram_stages=2", "factor_kb=builtin", "factor_kb=64", "factor_kb=48",
+                 "factor_kb=32", "factor_kb=24", "factor_kb=16", "eval_block=128", "eval_block=256",
+                 "eval_block=512", "eval_block=1024"]
+        tune = {"chosen": choice, "median_ms": {n: round(float(v), 4) for n, v in zip(names, ms) if v >= 0}}
+        for _ in range(2):
+            step()
+        torch.cuda.synchronize()
+
     L = pam.lib()
     import ctypes as C
 
@@ -663,7 +675,7 @@ def run_pam(args, rank, ws):
     return dict(value=value, step_ms=step_ms, times=times, err=err, phase_ms=phase_ms, launches=launches,
                 clocks=clk.summary(), e2e_s=e2e_s, h2d=h2d, d2h=d2h, plain=plain, roof=roof, roofs=roofs,
                 prec_name=prec_name, n_cells=n_cells, n_pts=n_pts, info=info, learned=learned, mode=mode,
-                e2e_mode=e2e_mode, lambda_cv=lcv, glue=glue)
+                e2e_mode=e2e_mode, lambda_cv=lcv, glue=glue, tune=tune)
 
 
 def glue_pairs_per_point(W, pts, band):
@@ -772,6 +784,7 @@ def main():
     ap.add_argument("--lambda-cv", action="store_true",
                     help="also time the per-subdomain 3-fold cross-validation of 3 lambda pairs (binary64)")
     ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of a CUDA graph replay")
+    ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch tuning")
     ap.add_argument("--glue", type=float, default=0.0,
                     help="also time the glued evaluation (pam_eval_glued) with this band in cells")
     ap.add_argument("--quad", type=int, default=0, choices=[0, 1],
@@ -858,6 +871,8 @@ def main():
         line["lambda_cv"] = r["lambda_cv"]
     if r["glue"] is not None:
         line["glued_eval"] = r["glue"]
+    if r["tune"] is not None:
+        line["tuning"] = r["tune"]
     fit_ms = sum(v[0] for k, v in r["phase_ms"].items() if k not in ("eval", "errors"))
     line["fit_cells_per_s"] = r["n_cells"] * ws / (fit_ms / 1e3) if fit_ms else None
     print(json.dumps(line))

@@ -519,6 +519,53 @@ pam_status pam_nn_adamw(float *d_params, const float *d_grads, float *d_m, float
                         void *stream);
 
 /*
+ * Launch tuning and the autotuner (tile and launch shapes; no counterpart in
+ * the paper). Three process-wide choices change the speed of the kernels
+ * but not their results:
+ *   factor_kb    shared-memory budget (KiB) of the mixed solve's packed
+ *                support factor; larger supports keep their factor in global
+ *                memory, and the budget sets how many CTAs fit per SM
+ *                (0: the largest budget up to 64 KiB with two CTAs per SM)
+ *   gram_stages  pipeline depth of the tensor-core Gram, 2 or 3 (0: 3 where
+ *                shared memory allows)
+ *   eval_block   threads per block of the evaluation kernels, 128, 256, 512
+ *                or 1024 (0: 256)
+ * pam_tuning_set (NULL: all built-in) applies to every later launch of the
+ * process; it is not synchronised with launches in flight on other threads.
+ * pam_autotune measures, on a fitted model (after pam_fit_subdomains /
+ * pam_refine on the same workspace), each candidate with CUDA events on
+ * `stream` (median of three runs after one warm-up): the stages on the
+ * tensor-core Gram of every subdomain, then the factor budgets {built-in, 64,
+ * 48, 32, 24, 16} on the mixed solve of every subdomain from its current
+ * coefficients (the same minimiser: the coefficients are re-solved, as by
+ * pam_resume, and the indicators rewritten), then the block sizes on
+ * pam_eval of d_pts [n_pts][dim] into d_out [n_pts] (skipped when n_pts ==
+ * 0; d_eval_workspace as for pam_eval). The binary64 form tunes the
+ * evaluation only. The fastest candidates become the process tuning and
+ * *out; h_ms (optional, [12]) receives the medians in ms in that order
+ * (stages 3, 2; budgets; blocks), -1 where a candidate was not run.
+ * Synchronises `stream`; not to be captured in a CUDA graph.
+ */
+typedef struct {
+    int factor_kb;
+    int gram_stages;
+    int eval_block;
+    int reserved[5];
+} pam_tuning;
+pam_status pam_tuning_set(const pam_tuning *t);
+pam_status pam_tuning_get(pam_tuning *t);
+pam_status pam_autotune(const pam_problem *prob, const pam_params *par, const pam_plan *plan, const double *d_K,
+                        pam_model *model, void *d_workspace, size_t workspace_bytes, const double *d_pts,
+                        int64_t n_pts, double *d_out, void *d_eval_workspace, size_t eval_workspace_bytes,
+                        void *stream, pam_tuning *out, double *h_ms);
+/* The same on a model fitted on a mesh given as cells (pam_fit_cells). */
+pam_status pam_autotune_cells(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                              const pam_cells *cells, const double *d_K, pam_model *model, void *d_workspace,
+                              size_t workspace_bytes, const double *d_pts, int64_t n_pts, double *d_out,
+                              void *d_eval_workspace, size_t eval_workspace_bytes, void *stream, pam_tuning *out,
+                              double *h_ms);
+
+/*
  * Optional kernel timing. When enabled, every kernel family below records a
  * CUDA event pair around its launches on the caller's stream; reading sums
  * the elapsed times per family (and synchronises on the recorded events).

@@ -189,6 +189,39 @@ Ws carve_workspace(const Geo &g, void *base) {
 
 }  // namespace pam
 
+namespace pam {
+static pam_tuning g_tuning = {0, 0, 0, {0, 0, 0, 0, 0}};  // factor_kb, gram_stages, eval_block
+const pam_tuning &tuning() { return g_tuning; }
+
+// Median of three timed runs of `body` (after one untimed run) on `st`, ms.
+template <class F>
+static pam_status time_median(cudaStream_t st, F body, double *ms) {
+    cudaEvent_t a, b;
+    PAM_CUDA_TRY(cudaEventCreate(&a));
+    PAM_CUDA_TRY(cudaEventCreate(&b));
+    body();
+    float t[3];
+    for (int r = 0; r < 3; ++r) {
+        cudaEventRecord(a, st);
+        body();
+        cudaEventRecord(b, st);
+        if (cudaEventSynchronize(b) != cudaSuccess) {
+            cudaEventDestroy(a);
+            cudaEventDestroy(b);
+            return PAM_ERR_CUDA;
+        }
+        cudaEventElapsedTime(&t[r], a, b);
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    const float lo = fminf(t[0], fminf(t[1], t[2])), hi = fmaxf(t[0], fmaxf(t[1], t[2]));
+    *ms = (double)(t[0] + t[1] + t[2] - lo - hi);
+    PAM_CUDA_TRY(cudaGetLastError());
+    return PAM_OK;
+}
+
+}  // namespace pam
+
 using namespace pam;
 
 extern "C" {
@@ -926,6 +959,132 @@ pam_status pam_resume_cells(const pam_problem *prob, const pam_params *par, cons
     if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
     g.cxv = w.cxv;
     return resume_launches(g, p, par, d_K, model, w, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------- autotuning ---
+
+
+pam_status pam_tuning_set(const pam_tuning *t) {
+    if (!t) {
+        memset(&g_tuning, 0, sizeof(g_tuning));
+        return PAM_OK;
+    }
+    if (t->factor_kb < 0 || (t->factor_kb > 0 && (t->factor_kb < 4 || t->factor_kb > 200))) return PAM_ERR_INVALID_ARG;
+    if (t->eval_block != 0 && t->eval_block != 128 && t->eval_block != 256 && t->eval_block != 512 &&
+        t->eval_block != 1024)
+        return PAM_ERR_INVALID_ARG;
+    if (t->gram_stages != 0 && t->gram_stages != 2 && t->gram_stages != 3) return PAM_ERR_INVALID_ARG;
+    g_tuning = *t;
+    return PAM_OK;
+}
+
+pam_status pam_tuning_get(pam_tuning *t) {
+    if (!t) return PAM_ERR_INVALID_ARG;
+    *t = g_tuning;
+    return PAM_OK;
+}
+
+static pam_status autotune_run(Geo g, const Par &p, const pam_params *par, pam_model *model, const Ws &w,
+                               const double *d_pts, int64_t n_pts, double *d_out, void *d_eval_workspace,
+                               cudaStream_t s, pam_tuning *out, double *h_ms) {
+    pam_status st;
+    const bool mixed = par->precision == PAM_PREC_MIXED;
+    if (mixed && (g.m_cap > kMixedMaxM || !mixed_solve_fits(g))) return PAM_ERR_UNSUPPORTED;
+    if (h_ms)
+        for (int i = 0; i < 12; ++i) h_ms[i] = -1.0;
+    const pam_tuning keep = g_tuning;
+    pam_tuning best = g_tuning;
+    double t;
+    PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 8 * sizeof(int32_t), s));
+    if (mixed) {
+        // the tensor-core Gram's pipeline depth (3 stages only where they fit)
+        const int gst[2] = {3, 2};
+        double bt = INFINITY;
+        for (int i = 0; i < 2; ++i) {
+            g_tuning.gram_stages = gst[i];
+            if ((st = time_median(s, [&] { launch_stats_gram_tc(g, model->boxes, model->centres, model->info, w, s, 1); },
+                                  &t)) != PAM_OK) { g_tuning = keep; return st; }
+            if (h_ms) h_ms[i] = t;
+            if (t < bt) { bt = t; best.gram_stages = gst[i]; }
+        }
+        g_tuning.gram_stages = best.gram_stages;
+        // the solve's shared-memory factor budget (0: the built-in choice);
+        // every subdomain is re-solved from its coefficients (same minimiser)
+        const int fkb[6] = {0, 64, 48, 32, 24, 16};
+        bt = INFINITY;
+        for (int i = 0; i < 6; ++i) {
+            g_tuning.factor_kb = fkb[i];
+            if (!mixed_solve_fits(g)) continue;
+            if ((st = time_median(s, [&] {
+                     launch_solve_mixed(g, p, model->boxes, model->centres, model->beta, model->info, w, nullptr, 1,
+                                        nullptr, 0, s);
+                 }, &t)) != PAM_OK) { g_tuning = keep; return st; }
+            if (h_ms) h_ms[2 + i] = t;
+            if (t < bt) { bt = t; best.factor_kb = fkb[i]; }
+        }
+        g_tuning.factor_kb = best.factor_kb;
+    }
+    if (n_pts > 0) {
+        // the evaluation's threads per block (model and points as given)
+        const int eb[4] = {128, 256, 512, 1024};
+        double bt = INFINITY;
+        for (int i = 0; i < 4; ++i) {
+            g_tuning.eval_block = eb[i];
+            if ((st = time_median(s, [&] {
+                     launch_eval(g, model->boxes, model->centres, model->beta, model->info, d_pts, n_pts, d_out, 0,
+                                 par->precision, d_eval_workspace, s);
+                 }, &t)) != PAM_OK) { g_tuning = keep; return st; }
+            if (h_ms) h_ms[8 + i] = t;
+            if (t < bt) { bt = t; best.eval_block = eb[i]; }
+        }
+    }
+    g_tuning = best;
+    *out = best;
+    int32_t hs[8];
+    if ((st = read_status(w, s, hs)) != PAM_OK) return st;
+    if (hs[kStTimeout]) return PAM_ERR_TIMEOUT;
+    return PAM_OK;
+}
+
+pam_status pam_autotune(const pam_problem *prob, const pam_params *par, const pam_plan *plan, const double *d_K,
+                        pam_model *model, void *d_workspace, size_t workspace_bytes, const double *d_pts,
+                        int64_t n_pts, double *d_out, void *d_eval_workspace, size_t eval_ws_bytes,
+                        void *stream, pam_tuning *out, double *h_ms) {
+    Geo g;
+    Par p;
+    pam_status st;
+    if (!par || !make_geo(prob, par, &g, &p, &st)) return par ? st : PAM_ERR_INVALID_ARG;
+    if ((st = check_plan(g, plan)) != PAM_OK) return st;
+    g.m_cap = plan->m_cap;
+    if (!d_K || !model_ok(model) || !d_workspace || !out || n_pts < 0) return PAM_ERR_INVALID_ARG;
+    if (n_pts > 0 && (!d_pts || !d_out || !d_eval_workspace)) return PAM_ERR_INVALID_ARG;
+    if (n_pts > (int64_t)INT32_MAX) return PAM_ERR_UNSUPPORTED;
+    if (n_pts > 0 && eval_ws_bytes < eval_workspace_bytes(g.S, n_pts)) return PAM_ERR_WORKSPACE;
+    Ws w = carve_workspace(g, d_workspace);
+    if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
+    return autotune_run(g, p, par, model, w, d_pts, n_pts, d_out, d_eval_workspace, (cudaStream_t)stream, out,
+                        h_ms);
+}
+
+pam_status pam_autotune_cells(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
+                              const pam_cells *cells, const double *d_K, pam_model *model, void *d_workspace,
+                              size_t workspace_bytes, const double *d_pts, int64_t n_pts, double *d_out,
+                              void *d_eval_workspace, size_t eval_ws_bytes, void *stream, pam_tuning *out,
+                              double *h_ms) {
+    Geo g;
+    Par p;
+    pam_status st;
+    if (!par) return PAM_ERR_INVALID_ARG;
+    if ((st = cells_setup(prob, par, plan, cells, &g, &p)) != PAM_OK) return st;
+    if (!d_K || !model_ok(model) || !d_workspace || !out || n_pts < 0) return PAM_ERR_INVALID_ARG;
+    if (n_pts > 0 && (!d_pts || !d_out || !d_eval_workspace)) return PAM_ERR_INVALID_ARG;
+    if (n_pts > (int64_t)INT32_MAX) return PAM_ERR_UNSUPPORTED;
+    if (n_pts > 0 && eval_ws_bytes < eval_workspace_bytes(g.S, n_pts)) return PAM_ERR_WORKSPACE;
+    Ws w = carve_workspace(g, d_workspace);
+    if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
+    g.cxv = w.cxv;
+    return autotune_run(g, p, par, model, w, d_pts, n_pts, d_out, d_eval_workspace, (cudaStream_t)stream, out,
+                        h_ms);
 }
 
 }  // extern "C"

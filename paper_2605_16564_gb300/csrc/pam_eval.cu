@@ -266,6 +266,12 @@ __global__ void k_eval_bucket_f32(Geo g, const int32_t *boxes, const double *cen
     }
 }
 
+// Threads per block of the bucket kernels (the tuned value, else 256).
+static int eval_block() {
+    const int b = tuning().eval_block;
+    return (b == 128 || b == 256 || b == 512 || b == 1024) ? b : 256;
+}
+
 void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
                  const int32_t *info, const double *pts, int64_t n_pts, double *out, int log_space,
                  int precision, void *ws, cudaStream_t st) {
@@ -278,12 +284,12 @@ void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, cons
     k_eval_scatter<<<nb, 256, 0, st>>>(e.owner, e.rank, e.start, e.perm, n_pts);
     if (precision == PAM_PREC_MIXED) {
         size_t sm = (size_t)g.m_cap * (sizeof(float4) + sizeof(float));
-        k_eval_bucket_f32<<<g.S, 256, sm, st>>>(g, boxes, centres, beta, info, pts, e.perm, e.start,
+        k_eval_bucket_f32<<<g.S, eval_block(), sm, st>>>(g, boxes, centres, beta, info, pts, e.perm, e.start,
                                                 out, log_space);
     } else {
         size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));
         cudaFuncSetAttribute(k_eval_bucket_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_eval_bucket_f64<<<g.S, 256, sm, st>>>(g, centres, beta, info, pts, e.perm, e.start, out,
+        k_eval_bucket_f64<<<g.S, eval_block(), sm, st>>>(g, centres, beta, info, pts, e.perm, e.start, out,
                                                 log_space);
     }
     count_launches(4);
@@ -598,12 +604,12 @@ static void glue_launches(const Geo &g, const int32_t *boxes, const double *cent
     k_glue_scatter<D><<<nb, 256, 0, st>>>(n_pts, e.start, e);
     if (precision == PAM_PREC_MIXED) {
         size_t sm = (size_t)g.m_cap * (sizeof(float4) + sizeof(float));
-        k_glue_bucket_f32<<<g.S, 256, sm, st>>>(g, boxes, centres, beta, info, pts, e.perm, e.start, e.val);
+        k_glue_bucket_f32<<<g.S, eval_block(), sm, st>>>(g, boxes, centres, beta, info, pts, e.perm, e.start, e.val);
         k_glue_combine<D, true><<<nb, 256, 0, st>>>(n_pts, e, out, log_space);
     } else {
         size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));
         cudaFuncSetAttribute(k_glue_bucket_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_glue_bucket_f64<<<g.S, 256, sm, st>>>(g, centres, beta, info, pts, e.perm, e.start, e.val);
+        k_glue_bucket_f64<<<g.S, eval_block(), sm, st>>>(g, centres, beta, info, pts, e.perm, e.start, e.val);
         k_glue_combine<D, false><<<nb, 256, 0, st>>>(n_pts, e, out, log_space);
     }
 }

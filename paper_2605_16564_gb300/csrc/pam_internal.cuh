@@ -136,6 +136,10 @@ void launch_lambda_cv(const Geo &g, const Par &p, int precision, const int32_t *
                       double *beta, int32_t *info, const Ws &w, const CvGrid &grid, int folds, double *cv,
                       int32_t *choice, void *cv_ws, cudaStream_t st);
 
+// Process-wide launch tuning (pam_tuning_set / pam_autotune); zero fields
+// take the built-in choices.
+const pam_tuning &tuning();
+
 // Kernel families timed by the optional event profiler (pam_timing_*).
 enum Phase {
     kPhPrepare = 0, kPhAssemble, kPhGram, kPhSolve, kPhResidual, kPhMark, kPhEval, kPhErrors,

@@ -478,7 +478,8 @@ static size_t gram_tc_smem(const Geo &g, int stages) {
 void launch_gram_tc(const Geo &g, const int32_t *boxes, const double *centres, const int32_t *info,
                     const Ws &w, cudaStream_t st, int all, int folds, int fold) {
     PhaseScope ps(kPhGramTC, st);
-    const int stages = gram_tc_smem(g, kTcMaxStages) <= kSmemLimit ? kTcMaxStages : 2;
+    int stages = gram_tc_smem(g, kTcMaxStages) <= kSmemLimit ? kTcMaxStages : 2;
+    if (tuning().gram_stages == 2) stages = 2;  // a tuned shallower pipeline (3 only where it fits)
     size_t sm = gram_tc_smem(g, stages);
     cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     dim3 grid((g.m_cap + 127) / 128, g.S);
@@ -1280,6 +1281,7 @@ static int factor_smem_bytes(const Geo &g) {
         env = e ? (atoi(e) * 1024 < 4096 ? 4096 : atoi(e) * 1024) : -1;
     }
     if (env > 0) return env;
+    if (tuning().factor_kb > 0) return tuning().factor_kb * 1024;
     const long long per_cta = 228 * 1024 / 2 - 1024 - 1024;
     const long long room = (per_cta - (long long)solve_mixed_smem_rest(g)) / 1024 * 1024;
     if (room < 16 * 1024) return kMxFactorBytesDefault;

@@ -36,7 +36,8 @@ EXPORTED = ["pam_version", "pam_status_string", "pam_plan_create", "pam_partitio
             "pam_errors", "pam_status_read", "pam_lambda_cv_workspace_size", "pam_lambda_cv",
             "pam_eval_glued_workspace_size", "pam_eval_glued", "pam_partition_cells", "pam_plan_create_cells",
             "pam_fit_cells", "pam_refine_cells", "pam_errors_cells", "pam_model_save", "pam_model_load",
-            "pam_resume", "pam_resume_cells"]
+            "pam_resume", "pam_resume_cells", "pam_tuning_set", "pam_tuning_get", "pam_autotune",
+            "pam_autotune_cells"]
 
 
 class PamError(RuntimeError):
@@ -66,6 +67,11 @@ class pam_plan(C.Structure):
 class pam_cells(C.Structure):
     _fields_ = [("n_cells", C.c_int64), ("x", C.c_void_p), ("vol", C.c_void_p), ("patch_start", C.c_void_p),
                 ("patch_cells", C.c_void_p)]
+
+
+class pam_tuning(C.Structure):
+    _fields_ = [("factor_kb", C.c_int), ("gram_stages", C.c_int), ("eval_block", C.c_int),
+                ("reserved", C.c_int * 5)]
 
 
 class pam_model(C.Structure):
@@ -117,8 +123,17 @@ def lib():
                                  C.c_size_t, C.c_void_p]
         L.pam_resume_cells.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), P(pam_cells), C.c_void_p,
                                        P(pam_model), C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_tuning_set.argtypes = [P(pam_tuning)]
+        L.pam_tuning_get.argtypes = [P(pam_tuning)]
+        L.pam_autotune.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), C.c_void_p, P(pam_model), C.c_void_p,
+                                   C.c_size_t, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p,
+                                   P(pam_tuning), C.c_void_p]
+        L.pam_autotune_cells.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), P(pam_cells), C.c_void_p,
+                                         P(pam_model), C.c_void_p, C.c_size_t, C.c_void_p, C.c_int64, C.c_void_p,
+                                         C.c_void_p, C.c_size_t, C.c_void_p, P(pam_tuning), C.c_void_p]
         for name in ("pam_partition_cells", "pam_plan_create_cells", "pam_fit_cells", "pam_refine_cells",
-                     "pam_errors_cells", "pam_model_save", "pam_model_load", "pam_resume", "pam_resume_cells"):
+                     "pam_errors_cells", "pam_model_save", "pam_model_load", "pam_resume", "pam_resume_cells",
+                     "pam_tuning_set", "pam_tuning_get", "pam_autotune", "pam_autotune_cells"):
             getattr(L, name).restype = C.c_int
         L.pam_eval_glued_workspace_size.argtypes = [P(pam_problem), P(pam_plan), C.c_int64, P(C.c_size_t)]
         L.pam_eval_glued.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_int64,
@@ -394,6 +409,44 @@ def pam_resume_cells(problem, params, plan, cells, K, model, workspace, stream=N
     return code
 
 
+def pam_tuning_set(factor_kb=0, gram_stages=0, eval_block=0, reset=False):
+    """Process-wide launch tuning (0 = built-in choice); reset=True restores all built-ins."""
+    if reset:
+        _check(lib().pam_tuning_set(None), "pam_tuning_set")
+        return
+    t = pam_tuning(int(factor_kb), int(gram_stages), int(eval_block))
+    _check(lib().pam_tuning_set(C.byref(t)), "pam_tuning_set")
+
+
+def pam_tuning_get():
+    t = pam_tuning()
+    _check(lib().pam_tuning_get(C.byref(t)), "pam_tuning_get")
+    return dict(factor_kb=t.factor_kb, gram_stages=t.gram_stages, eval_block=t.eval_block)
+
+
+def pam_autotune(problem, params, plan, K, model, workspace, pts=None, out=None, eval_workspace=None, stream=None,
+                 cells=None):
+    """Measures the tuning candidates on a fitted model (and pts, if given),
+    keeps the fastest process-wide; returns (choice dict, medians in ms [12]).
+    cells: the pam_cells of a mesh given as cells (pam_autotune_cells)."""
+    t = pam_tuning()
+    ms = np.zeros(12, dtype=np.float64)
+    n = pts.shape[0] if pts is not None else 0
+    ebytes = eval_workspace.numel() * eval_workspace.element_size() if eval_workspace is not None else 0
+    wbytes = workspace.numel() * workspace.element_size()
+    if cells is None:
+        code = lib().pam_autotune(C.byref(problem), C.byref(params), C.byref(plan), _ptr(K), C.byref(model.c_struct()),
+                                  _ptr(workspace), wbytes, _ptr(pts), int(n), _ptr(out), _ptr(eval_workspace), ebytes,
+                                  _stream(stream), C.byref(t), ms.ctypes.data)
+    else:
+        code = lib().pam_autotune_cells(C.byref(problem), C.byref(params), C.byref(plan), C.byref(cells), _ptr(K),
+                                        C.byref(model.c_struct()), _ptr(workspace), wbytes, _ptr(pts), int(n),
+                                        _ptr(out), _ptr(eval_workspace), ebytes, _stream(stream), C.byref(t),
+                                        ms.ctypes.data)
+    _check(code, "pam_autotune")
+    return dict(factor_kb=t.factor_kb, gram_stages=t.gram_stages, eval_block=t.eval_block), ms
+
+
 PAM_NN_PATCH2D, PAM_NN_LAYERED3D = 0, 1
 
 
@@ -591,6 +644,16 @@ class Fitter:
 
     def host_model(self):
         return self.model.to_host(self.n_cells, self.n_sub, self.plan.m_cap)
+
+    def autotune(self, K, pts=None, stream=None):
+        """pam_autotune on this fitter's fitted model (and evaluation points)."""
+        import torch
+        out = ws = None
+        if pts is not None and pts.shape[0] > 0:
+            out = torch.empty(pts.shape[0], dtype=torch.float64, device=pts.device)
+            ws = self.eval_workspace(pts.shape[0])
+        return pam_autotune(self.problem, self.params, self.plan, K, self.model, self.workspace, pts, out, ws, stream,
+                            cells=getattr(self, "cells", None))
 
     def save(self, stream=None):
         """Checkpoint of the model (bytes, pam_model_save)."""

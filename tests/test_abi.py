@@ -282,3 +282,16 @@ def test_model_blob_checks_without_a_gpu(pam):
     blob2[0] = ord("X")
     assert L.pam_model_load(C.byref(pr), C.byref(plan), blob2.ctypes.data, blob2.size, C.byref(m), None) == 1
     assert L.pam_model_load(C.byref(pr), C.byref(plan), blob.ctypes.data, blob.size - 1, C.byref(m), None) == 1
+
+
+def test_tuning_set_get_and_checks(pam):
+    pam.pam_tuning_set(reset=True)
+    assert pam.pam_tuning_get() == dict(factor_kb=0, gram_stages=0, eval_block=0)
+    pam.pam_tuning_set(factor_kb=48, gram_stages=2, eval_block=512)
+    assert pam.pam_tuning_get() == dict(factor_kb=48, gram_stages=2, eval_block=512)
+    for bad in (dict(factor_kb=-1), dict(factor_kb=2), dict(gram_stages=4), dict(gram_stages=1), dict(eval_block=300)):
+        with pytest.raises(pam.PamError):
+            pam.pam_tuning_set(**bad)
+    assert pam.pam_tuning_get() == dict(factor_kb=48, gram_stages=2, eval_block=512)  # unchanged
+    pam.pam_tuning_set(reset=True)
+    assert pam.pam_tuning_get()["factor_kb"] == 0
