@@ -130,9 +130,53 @@ __device__ __forceinline__ double shepard_f64_smem(const dvec4 *sc, const double
     return num / den;
 }
 
+// Copies subdomain s's centres (M x 32 bytes) and coefficients (M x 8
+// bytes, padded to 16 with the next entry: the capacity is a multiple of 64)
+// into shared memory with the bulk-copy engine, thread 0 issuing, everyone
+// waiting on one mbarrier (bounded). Returns false -- and nothing may be
+// read from dst_c / dst_b -- if an address is not 16-byte aligned or the
+// wait gave up; the caller then loads from global memory instead.
+__device__ bool stage_bulk(const Geo &g, const double *centres, const double *beta, int s, int M, dvec4 *dst_c,
+                           double *dst_b) {
+    __shared__ uint64_t bar;
+    __shared__ int use_bulk;
+    const dvec4 *src_c = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
+    const double *src_b = beta + (size_t)s * g.m_cap;
+    const uint32_t bytes_c = (uint32_t)M * 32u, bytes_b = ((uint32_t)M * 8u + 15u) & ~15u;
+    if (threadIdx.x == 0) {
+        const bool aligned = ((reinterpret_cast<uintptr_t>(src_c) | reinterpret_cast<uintptr_t>(src_b) |
+                               (uintptr_t)tc::smem_u32(dst_c) | (uintptr_t)tc::smem_u32(dst_b)) & 15u) == 0;
+        use_bulk = aligned && M > 0;
+        if (use_bulk) {
+            tc::mbar_init(&bar, 1);
+            tc::mbar_fence_init();
+        }
+    }
+    __syncthreads();
+    if (!use_bulk) return false;
+    if (threadIdx.x == 0) {
+        tc::mbar_arrive_expect_tx(&bar, bytes_c + bytes_b);
+        tc::bulk_g2s(dst_c, src_c, bytes_c, &bar);
+        tc::bulk_g2s(dst_b, src_b, bytes_b, &bar);
+    }
+    // ~1 s at 2 GHz (a bulk copy of a few KB takes microseconds); if it gives
+    // up, wait once more for the copy in flight before anyone falls back
+    bool ok = tc::mbar_wait(&bar, 0, 2000000000LL);
+    if (!ok) ok = tc::mbar_wait(&bar, 0, 2000000000LL);
+    return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
 // Dictionary of subdomain s in shared memory: (c, -1/(2 sigma^2)) and beta.
 __device__ void stage_f64(const Geo &g, const double *centres, const double *beta, int s, int M,
                           dvec4 *sc, double *sb) {
+    if (stage_bulk(g, centres, beta, s, M, sc, sb)) {  // copied as is; the width becomes the logit factor
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            const double sg = sc[m].w;
+            sc[m].w = -1.0 / (2.0 * sg * sg);
+        }
+        __syncthreads();
+        return;
+    }
     const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
         dvec4 c = cg[m];
@@ -224,10 +268,27 @@ __device__ __forceinline__ void shepard_f32_smem2(const float4 *sc, const float 
     *v1 = (d1 > 7.9e-31f) ? n1 / d1 : shepard_f32_smem(sc, sb, M, p1[0], p1[1], p1[2]);
 }
 
+// Dynamic shared memory of the fp32 staging: the converted centres and
+// coefficients, then (32-byte aligned) the raw copies the bulk copy lands in.
+static size_t stage_f32_smem(int m_cap) {
+    return ((size_t)m_cap * (sizeof(float4) + sizeof(float)) + 31) / 32 * 32 + 32 +  // + alignment slack
+           (size_t)m_cap * (sizeof(dvec4) + sizeof(double));
+}
+
 __device__ void stage_f32(const Geo &g, const int32_t *boxes, const double *centres,
                           const double *beta, int s, int M, float4 *sc, float *sb, double o[3]) {
     const int32_t *box = boxes + s * 12;
     for (int a = 0; a < 3; ++a) o[a] = a < g.dim ? (double)box[6 + a] * g.h : 0.0;
+    dvec4 *raw_c = reinterpret_cast<dvec4 *>((reinterpret_cast<uintptr_t>(sb + g.m_cap) + 31) & ~(uintptr_t)31);
+    double *raw_b = reinterpret_cast<double *>(raw_c + g.m_cap);
+    if (stage_bulk(g, centres, beta, s, M, raw_c, raw_b)) {
+        for (int m = threadIdx.x; m < M; m += blockDim.x) {
+            sc[m] = local_centre_e(raw_c[m], o);
+            sb[m] = (float)raw_b[m];
+        }
+        __syncthreads();
+        return;
+    }
     const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
         sc[m] = local_centre_e(cg[m], o);
@@ -283,7 +344,8 @@ void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, cons
     k_eval_scan<<<1, 1024, 0, st>>>(e.count, e.start, g.S);
     k_eval_scatter<<<nb, 256, 0, st>>>(e.owner, e.rank, e.start, e.perm, n_pts);
     if (precision == PAM_PREC_MIXED) {
-        size_t sm = (size_t)g.m_cap * (sizeof(float4) + sizeof(float));
+        size_t sm = stage_f32_smem(g.m_cap);
+        cudaFuncSetAttribute(k_eval_bucket_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_eval_bucket_f32<<<g.S, eval_block(), sm, st>>>(g, boxes, centres, beta, info, pts, e.perm, e.start,
                                                 out, log_space);
     } else {
@@ -603,7 +665,8 @@ static void glue_launches(const Geo &g, const int32_t *boxes, const double *cent
     k_eval_scan<<<1, 1024, 0, st>>>(e.count, e.start, g.S);
     k_glue_scatter<D><<<nb, 256, 0, st>>>(n_pts, e.start, e);
     if (precision == PAM_PREC_MIXED) {
-        size_t sm = (size_t)g.m_cap * (sizeof(float4) + sizeof(float));
+        size_t sm = stage_f32_smem(g.m_cap);
+        cudaFuncSetAttribute(k_glue_bucket_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_glue_bucket_f32<<<g.S, eval_block(), sm, st>>>(g, boxes, centres, beta, info, pts, e.perm, e.start, e.val);
         k_glue_combine<D, true><<<nb, 256, 0, st>>>(n_pts, e, out, log_space);
     } else {
@@ -735,7 +798,8 @@ void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, co
                    const Ws &w, cudaStream_t st) {
     PhaseScope ps(kPhErrors, st);
     if (precision == PAM_PREC_MIXED) {
-        size_t sm = (size_t)g.m_cap * (sizeof(float4) + sizeof(float));
+        size_t sm = stage_f32_smem(g.m_cap);
+        cudaFuncSetAttribute(k_errors_owner<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_errors_owner<true><<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, quad, w.err_part);
     } else {
         size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));
@@ -812,7 +876,8 @@ void launch_errors_cells(const Geo &g, const int32_t *boxes, const double *centr
                          cudaStream_t st) {
     PhaseScope ps(kPhErrors, st);
     if (precision == PAM_PREC_MIXED) {
-        size_t sm = (size_t)g.m_cap * (sizeof(float4) + sizeof(float));
+        size_t sm = stage_f32_smem(g.m_cap);
+        cudaFuncSetAttribute(k_errors_cells<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_errors_cells<true><<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, w.err_part);
     } else {
         size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));
@@ -887,7 +952,8 @@ void launch_residual_quad(const Geo &g, int precision, const int32_t *boxes, con
                           const double *beta, const int32_t *info, const Ws &w, cudaStream_t st) {
     PhaseScope ps(kPhResidual, st);
     if (precision == PAM_PREC_MIXED) {
-        size_t sm = (size_t)g.m_cap * (sizeof(float4) + sizeof(float));
+        size_t sm = stage_f32_smem(g.m_cap);
+        cudaFuncSetAttribute(k_residual_quad<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_residual_quad<true><<<g.S, 256, sm, st>>>(g, boxes, centres, beta, info, w);
     } else {
         size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));

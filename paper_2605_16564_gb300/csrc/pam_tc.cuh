@@ -123,6 +123,22 @@ __device__ __forceinline__ bool mbar_wait(uint64_t *m, uint32_t parity, long lon
     return true;
 }
 
+// One arrival that also expects `bytes` of asynchronous transactions (the
+// bulk copies below complete them).
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t *m, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(m)), "r"(bytes)
+                 : "memory");
+}
+
+// ---- bulk copy (TMA copy engine, untiled) -----------------------------------
+// Global -> shared copy of `bytes` bytes that completes its transactions on
+// mbarrier m. Both addresses 16-byte aligned, bytes a multiple of 16.
+__device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src, uint32_t bytes, uint64_t *m) {
+    asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];"
+                 ::"r"(smem_u32(dst_smem)), "l"(src), "r"(bytes), "r"(smem_u32(m))
+                 : "memory");
+}
+
 // ---- fp32 helpers -------------------------------------------------------------
 // 2^x on the special-function unit (max relative error about 2^-22).
 __device__ __forceinline__ float ex2(float x) {
