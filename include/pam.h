@@ -566,6 +566,17 @@ pam_status pam_autotune_cells(const pam_problem *prob, const pam_params *par, co
                               double *h_ms);
 
 /*
+ * Failure-detection self-test (no counterpart in the paper). One block waits
+ * on an mbarrier with the same bounded wait (a clock64 budget) that the
+ * tensor-core pipeline's waits use. arrive = 0: nothing ever arrives, so the
+ * wait gives up after about budget_cycles clocks (1,000 ... 4e9), the kernel
+ * writes 1 into d_flag (device int32) and returns -- no trap, no hang, the
+ * context stays usable -- and the call returns PAM_ERR_TIMEOUT; arrive = 1:
+ * the barrier completes at once, d_flag = 0, PAM_OK. Synchronises `stream`.
+ */
+pam_status pam_selftest_wait(int arrive, long long budget_cycles, int32_t *d_flag, void *stream);
+
+/*
  * Optional kernel timing. When enabled, every kernel family below records a
  * CUDA event pair around its launches on the caller's stream; reading sums
  * the elapsed times per family (and synchronises on the recorded events).

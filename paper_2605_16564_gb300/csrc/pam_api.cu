@@ -1087,4 +1087,16 @@ pam_status pam_autotune_cells(const pam_problem *prob, const pam_params *par, co
                         h_ms);
 }
 
+pam_status pam_selftest_wait(int arrive, long long budget_cycles, int32_t *d_flag, void *stream) {
+    if ((arrive != 0 && arrive != 1) || budget_cycles < 1000 || budget_cycles > 4000000000LL || !d_flag)
+        return PAM_ERR_INVALID_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    launch_wait_selftest(arrive, budget_cycles, d_flag, s);
+    PAM_CUDA_TRY(cudaGetLastError());
+    int32_t h = -1;
+    PAM_CUDA_TRY(cudaMemcpyAsync(&h, d_flag, sizeof(h), cudaMemcpyDeviceToHost, s));
+    PAM_CUDA_TRY(cudaStreamSynchronize(s));
+    return h == 1 ? PAM_ERR_TIMEOUT : (h == 0 ? PAM_OK : PAM_ERR_CUDA);
+}
+
 }  // extern "C"

@@ -124,6 +124,7 @@ void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, co
 void launch_residual_quad(const Geo &g, int precision, const int32_t *boxes, const double *centres,
                           const double *beta, const int32_t *info, const Ws &w, cudaStream_t st);
 bool mixed_solve_fits(const Geo &g);
+void launch_wait_selftest(int arrive, long long budget, int32_t *flag, cudaStream_t st);
 
 // Grid of (lambda1_hat, lambda2_hat) pairs of the cross-validation (by value).
 constexpr int kCvMaxGrid = 32;

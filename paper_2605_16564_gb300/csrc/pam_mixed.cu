@@ -1344,4 +1344,27 @@ void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes,
 void launch_residual_mixed(const Geo &, const int32_t *, const double *, const double *,
                            const int32_t *, const Ws &, cudaStream_t) {}
 
+// Failure-detection self-test: one thread waits on an mbarrier with the
+// bounded wait of the tensor-core pipeline. arrive = 0: nothing arrives, the
+// wait gives up after about `budget` clocks and flag = 1; arrive = 1: the
+// barrier completes at once and flag = 0. Never traps, never hangs.
+__global__ void k_wait_selftest(int arrive, long long budget, int32_t *flag) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        tc::mbar_init(&bar, 1);
+        tc::mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        if (arrive) mbar_arrive(&bar);
+        const bool ok = tc::mbar_wait(&bar, 0u, budget);
+        *flag = ok ? 0 : 1;
+    }
+}
+
+void launch_wait_selftest(int arrive, long long budget, int32_t *flag, cudaStream_t st) {
+    k_wait_selftest<<<1, 32, 0, st>>>(arrive, budget, flag);
+    count_launches(1);
+}
+
 }  // namespace pam

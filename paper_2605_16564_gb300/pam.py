@@ -37,7 +37,7 @@ EXPORTED = ["pam_version", "pam_status_string", "pam_plan_create", "pam_partitio
             "pam_eval_glued_workspace_size", "pam_eval_glued", "pam_partition_cells", "pam_plan_create_cells",
             "pam_fit_cells", "pam_refine_cells", "pam_errors_cells", "pam_model_save", "pam_model_load",
             "pam_resume", "pam_resume_cells", "pam_tuning_set", "pam_tuning_get", "pam_autotune",
-            "pam_autotune_cells"]
+            "pam_autotune_cells", "pam_selftest_wait"]
 
 
 class PamError(RuntimeError):
@@ -131,6 +131,8 @@ def lib():
         L.pam_autotune_cells.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), P(pam_cells), C.c_void_p,
                                          P(pam_model), C.c_void_p, C.c_size_t, C.c_void_p, C.c_int64, C.c_void_p,
                                          C.c_void_p, C.c_size_t, C.c_void_p, P(pam_tuning), C.c_void_p]
+        L.pam_selftest_wait.argtypes = [C.c_int, C.c_longlong, C.c_void_p, C.c_void_p]
+        L.pam_selftest_wait.restype = C.c_int
         for name in ("pam_partition_cells", "pam_plan_create_cells", "pam_fit_cells", "pam_refine_cells",
                      "pam_errors_cells", "pam_model_save", "pam_model_load", "pam_resume", "pam_resume_cells",
                      "pam_tuning_set", "pam_tuning_get", "pam_autotune", "pam_autotune_cells"):
@@ -445,6 +447,12 @@ def pam_autotune(problem, params, plan, K, model, workspace, pts=None, out=None,
                                         ms.ctypes.data)
     _check(code, "pam_autotune")
     return dict(factor_kb=t.factor_kb, gram_stages=t.gram_stages, eval_block=t.eval_block), ms
+
+
+def pam_selftest_wait(arrive, budget_cycles, flag, stream=None):
+    """Bounded-wait self-test: returns the status code (PAM_ERR_TIMEOUT when
+    nothing arrived and the wait gave up); flag: device int32 [1]."""
+    return lib().pam_selftest_wait(int(arrive), int(budget_cycles), _ptr(flag), _stream(stream))
 
 
 PAM_NN_PATCH2D, PAM_NN_LAYERED3D = 0, 1

@@ -295,3 +295,12 @@ def test_tuning_set_get_and_checks(pam):
     assert pam.pam_tuning_get() == dict(factor_kb=48, gram_stages=2, eval_block=512)  # unchanged
     pam.pam_tuning_set(reset=True)
     assert pam.pam_tuning_get()["factor_kb"] == 0
+
+
+def test_selftest_wait_checks_its_arguments(pam):
+    import ctypes as C
+    L = pam.lib()
+    fake = C.c_void_p(256)
+    assert L.pam_selftest_wait(2, 100000, fake, None) == 1
+    assert L.pam_selftest_wait(0, 10, fake, None) == 1
+    assert L.pam_selftest_wait(0, 100000, None, None) == 1
