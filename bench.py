@@ -168,7 +168,7 @@ def accounting(fit, Kd, levels, pam, seed=None):
       pairs       sum N_i M_i: Gaussians evaluated once per (cell, centre);
       chol_flops  sum iters * s^3 / 3 over the active-set steps (fp32 form);
       eval_pairs  filled in by the caller (points x their owner's M)."""
-    out = dict(gram_flops=0.0, pairs=0.0, chol_flops=0.0, m_final=None)
+    out = dict(gram_flops=0.0, pairs=0.0, chol_flops=0.0, solve_bytes=0.0, m_final=None)
     fit_levels = [0] + [1] * levels
     for r, _ in enumerate(fit_levels):
         if r == 0:
@@ -190,9 +190,14 @@ def accounting(fit, Kd, levels, pam, seed=None):
         m = info[solved, pam.INFO_M].astype(float)
         sup = info[solved, pam.INFO_SUPPORT].astype(float)
         iters = (info[solved, pam.INFO_ITERS] % 100).astype(float)
+        passes = (info[solved, pam.INFO_ITERS] // 100).astype(float)
         out["gram_flops"] += float(np.sum(n * m * (m + 1.0)))
         out["pairs"] += float(np.sum(n * m))
         out["chol_flops"] += float(np.sum(iters * sup ** 3 / 3.0))
+        # Gram streaming of the solve: every active-set step and refinement
+        # pass reads the support block (s^2) and the support's rows (s M) of
+        # the fp32 Gram (s = the final support, the step count of the solve)
+        out["solve_bytes"] += float(np.sum((iters + passes) * (sup * sup + sup * m) * 4.0))
     out["m_final"] = fit.model.info.cpu().numpy()[:, pam.INFO_M].astype(float)
     return out
 
@@ -246,10 +251,15 @@ def roofline_entries(phase_ms, work, n_pts, mixed, peaks, peak_src):
                          "frac": ach / SFU_EX2_PER_S, "traffic": None,
                          "peak_source": "SFU ex2 16/clk/SM x 152 SMs x 2.07 GHz"}
     if t("solve") and mixed:
-        ach = work["chol_flops"] / t("solve") / 1e12
-        r["solve"] = {"kernel": "k_solve_mixed", "bound": "alu", "achieved": ach, "peak": FP32_TFLOPS,
-                      "unit": "TFLOP/s", "frac": ach / FP32_TFLOPS, "traffic": None,
-                      "peak_source": "fp32 FMA 128/clk/SM x 152 SMs x 2.07 GHz; work = active-set Cholesky flops"}
+        ach = work["solve_bytes"] / t("solve") / 1e9
+        pk = peaks.get("hbm_gbs", 6800.0)
+        chol = work["chol_flops"] / t("solve") / 1e12
+        r["solve"] = {"kernel": "k_solve_mixed", "bound": "hbm", "achieved": ach, "peak": pk, "unit": "GB/s",
+                      "frac": ach / pk, "traffic": None,
+                      "peak_source": f"hbm_gbs of {peak_src}; work = Gram streaming, (steps + refinement passes) "
+                                     "x (s^2 + s M) x 4 bytes per subdomain and level (latency-bound: one CTA "
+                                     "per subdomain, see the clock-counter split)",
+                      "cholesky_tflops": chol, "cholesky_frac_of_fp32": chol / FP32_TFLOPS}
     return r
 
 
