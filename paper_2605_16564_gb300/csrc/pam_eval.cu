@@ -379,7 +379,8 @@ void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, cons
 // --------------------------------------------------------------------------
 struct GlueWs {
     int32_t *rank, *perm, *count, *start, *sub;
-    double *val, *psi;
+    double *val, *psi;   // binary64 form
+    float *valf, *psif;  // fp32 form (the same memory)
     uint8_t *mask;
     size_t bytes;
 };
@@ -399,6 +400,8 @@ GlueWs carve_glue_workspace(int S, int dim, int64_t n, void *base) {
     e.perm = (int32_t *)take(slots * 4);
     e.sub = (int32_t *)take(slots * 4);
     e.mask = (uint8_t *)take((size_t)n);
+    e.valf = reinterpret_cast<float *>(e.val);
+    e.psif = reinterpret_cast<float *>(e.psi);
     e.count = (int32_t *)take((size_t)S * 4);
     e.start = (int32_t *)take((size_t)(S + 1) * 4);
     e.bytes = off;
@@ -423,18 +426,9 @@ __device__ __forceinline__ void glue_factors(int c, int n, int p, double h, doub
     *r = c < p - 1 ? glue_ramp(__ddiv_rn(__dsub_rn(__dadd_rn(__dmul_rn((double)hi, h), delta), xa), two_d)) : 1.0;
 }
 
-// fp32 form of the face factors (the mixed evaluation): the offset from the
-// face in binary64, the ramp in fp32 (relative error ~1e-7, like the fp32
-// local surrogates it blends).
 __device__ __forceinline__ float glue_ramp_f(float t) {
     t = fminf(fmaxf(t, 0.f), 1.f);
     return t * t * (3.f - 2.f * t);
-}
-__device__ __forceinline__ void glue_factors_f(int c, int n, int p, double h, float df, float inv, double xa,
-                                               double *l, double *r) {
-    const int64_t lo = ((int64_t)c * n) / p, hi = ((int64_t)(c + 1) * n) / p;
-    *l = c > 0 ? (double)glue_ramp_f(((float)(xa - (double)lo * h) + df) * inv) : 1.0;
-    *r = c < p - 1 ? (double)glue_ramp_f(((float)((double)hi * h - xa) + df) * inv) : 1.0;
 }
 
 // The pairs of point x: subdomain s[c] and weight psi[c] for the valid slots
@@ -445,11 +439,10 @@ __device__ __forceinline__ void glue_factors_f(int c, int n, int p, double h, fl
 // weight below 2^-100, and the larger is kept). Candidate 0 is the lower
 // core, so ascending c is ascending subdomain index. The weight multiplies
 // the face factors axis by axis, lower face first, in unfused binary64.
-template <int D, bool F32W = false>
+template <int D>
 __device__ __forceinline__ unsigned glue_pairs(const Geo &g, double delta, const double x[3], int s[8],
                                                double psi[8]) {
     const double two_d = 2.0 * delta;
-    const float df = (float)delta, inv = 1.0f / (2.0f * df);  // fp32 weights only
     int c0[3] = {0, 0, 0}, c1[3] = {0, 0, 0}, cnt[3] = {1, 1, 1};
     double l0[3] = {1.0, 1.0, 1.0}, r0[3] = {1.0, 1.0, 1.0}, l1[3] = {1.0, 1.0, 1.0}, r1[3] = {1.0, 1.0, 1.0};
     bool inside = true;
@@ -471,15 +464,9 @@ __device__ __forceinline__ unsigned glue_pairs(const Geo &g, double delta, const
             c0[a] = j;
         } else {
             double lj, rj, lm = 0.0, rm = 0.0, lp = 0.0, rp = 0.0;
-            if (F32W) {
-                glue_factors_f(j, g.n[a], g.p[a], g.h, df, inv, x[a], &lj, &rj);
-                if (!far_lo) glue_factors_f(j - 1, g.n[a], g.p[a], g.h, df, inv, x[a], &lm, &rm);
-                if (!far_hi) glue_factors_f(j + 1, g.n[a], g.p[a], g.h, df, inv, x[a], &lp, &rp);
-            } else {
-                glue_factors(j, g.n[a], g.p[a], g.h, delta, two_d, x[a], &lj, &rj);
-                if (!far_lo) glue_factors(j - 1, g.n[a], g.p[a], g.h, delta, two_d, x[a], &lm, &rm);
-                if (!far_hi) glue_factors(j + 1, g.n[a], g.p[a], g.h, delta, two_d, x[a], &lp, &rp);
-            }
+            glue_factors(j, g.n[a], g.p[a], g.h, delta, two_d, x[a], &lj, &rj);
+            if (!far_lo) glue_factors(j - 1, g.n[a], g.p[a], g.h, delta, two_d, x[a], &lm, &rm);
+            if (!far_hi) glue_factors(j + 1, g.n[a], g.p[a], g.h, delta, two_d, x[a], &lp, &rp);
             const double wm = __dmul_rn(lm, rm), wp = __dmul_rn(lp, rp);
             bool use_m = wm > 0.0, use_p = wp > 0.0;
             if (use_m && use_p) {
@@ -505,18 +492,96 @@ __device__ __forceinline__ unsigned glue_pairs(const Geo &g, double delta, const
         for (int a = 0; a < D; ++a) {
             const bool up = (c >> a) & 1;
             ok = ok && (!up || cnt[a] == 2);
-            if (F32W) {
-                w = (double)((float)w * (float)(up ? l1[a] : l0[a]) * (float)(up ? r1[a] : r0[a]));
-            } else {
-                w = __dmul_rn(w, up ? l1[a] : l0[a]);
-                w = __dmul_rn(w, up ? r1[a] : r0[a]);
-            }
+            w = __dmul_rn(w, up ? l1[a] : l0[a]);
+            w = __dmul_rn(w, up ? r1[a] : r0[a]);
             idx += (up ? c1[a] : c0[a]) * mul;
             mul *= g.p[a];
         }
         ok = ok && w > 0.0;
         s[c] = ok ? idx : 0;
         psi[c] = ok ? w : 0.0;
+        mask |= ok ? (1u << c) : 0u;
+    }
+    return mask;
+}
+
+// The fp32 form of glue_pairs (the mixed evaluation): everything in fp32
+// cell units u = x / h, the ramps ((u - lo) + band) / (2 band) and
+// ((hi + band) - u) / (2 band); one conversion of each coordinate is the only
+// binary64 operation (GB300's FP64 pipe is narrow). Same candidates, order
+// and masks as glue_pairs, weights to fp32 rounding.
+template <int D>
+__device__ __forceinline__ unsigned glue_pairs_f(const Geo &g, float band, const double x[3], int s[8],
+                                                 float psi[8]) {
+    const float inv = 1.0f / (2.0f * band), nmax = (float)g.nmax;
+    int c0[3] = {0, 0, 0}, c1[3] = {0, 0, 0}, cnt[3] = {1, 1, 1};
+    float l0[3] = {1.f, 1.f, 1.f}, r0[3] = {1.f, 1.f, 1.f}, l1[3] = {1.f, 1.f, 1.f}, r1[3] = {1.f, 1.f, 1.f};
+    bool inside = true;
+#pragma unroll
+    for (int a = 0; a < D; ++a) {
+        const float u = (float)x[a] * nmax;
+        const bool in_a = (u >= 0.f) && (u <= (float)g.n[a]);
+        inside = inside && in_a;
+        int i = in_a ? (int)floorf(u) : 0;
+        if (i >= g.n[a]) i = g.n[a] - 1;
+        const int j = core_of(i, g.n[a], g.p[a]);
+        const int p = g.p[a], n = g.n[a];
+        const int64_t lo_i = ((int64_t)j * n) / p, hi_i = ((int64_t)(j + 1) * n) / p;
+        // far from both faces (with half a cell to spare for the fp32 u)
+        const bool far_lo = j == 0 || u - (float)lo_i >= band + 0.5f;
+        const bool far_hi = j == p - 1 || (float)hi_i - u >= band + 0.5f;
+        if (far_lo && far_hi) {
+            c0[a] = j;
+        } else {
+            // the offset from the lower face in binary64 (u ~ 1e3 cells would
+            // leave ~1e-4 cells of fp32 rounding), the ramps in fp32
+            const float d = (float)(x[a] * (double)g.nmax - (double)lo_i);  // u - lo
+            const float w = (float)(hi_i - lo_i);                           // core width
+            const float lj = j > 0 ? glue_ramp_f((d + band) * inv) : 1.f;
+            const float rj = j < p - 1 ? glue_ramp_f(((w + band) - d) * inv) : 1.f;
+            float lm = 0.f, rm = 0.f, lp = 0.f, rp = 0.f;
+            if (j > 0) {  // core j-1: its upper face is lo
+                const float wm_ = (float)(lo_i - ((int64_t)(j - 1) * n) / p);
+                lm = j - 1 > 0 ? glue_ramp_f(((d + wm_) + band) * inv) : 1.f;
+                rm = glue_ramp_f((band - d) * inv);
+            }
+            if (j < p - 1) {  // core j+1: its lower face is hi
+                const float wp_ = (float)(((int64_t)(j + 2) * n) / p - hi_i);
+                lp = glue_ramp_f(((d - w) + band) * inv);
+                rp = j + 1 < p - 1 ? glue_ramp_f(((wp_ + band) - (d - w)) * inv) : 1.f;
+            }
+            const float wm = lm * rm, wp = lp * rp;
+            bool use_m = wm > 0.f, use_p = wp > 0.f;
+            if (use_m && use_p) {
+                use_m = wm >= wp;
+                use_p = !use_m;
+            }
+            c0[a] = use_m ? j - 1 : j;
+            l0[a] = use_m ? lm : lj;
+            r0[a] = use_m ? rm : rj;
+            c1[a] = use_m ? j : j + 1;
+            l1[a] = use_m ? lj : lp;
+            r1[a] = use_m ? rj : rp;
+            cnt[a] = (use_m || use_p) ? 2 : 1;
+        }
+    }
+    unsigned mask = 0u;
+#pragma unroll
+    for (int c = 0; c < (1 << D); ++c) {
+        int idx = 0, mul = 1;
+        float w = 1.f;
+        bool ok = inside;
+#pragma unroll
+        for (int a = 0; a < D; ++a) {
+            const bool up = (c >> a) & 1;
+            ok = ok && (!up || cnt[a] == 2);
+            w = w * (up ? l1[a] : l0[a]) * (up ? r1[a] : r0[a]);
+            idx += (up ? c1[a] : c0[a]) * mul;
+            mul *= g.p[a];
+        }
+        ok = ok && w > 0.f;
+        s[c] = ok ? idx : 0;
+        psi[c] = ok ? w : 0.f;
         mask |= ok ? (1u << c) : 0u;
     }
     return mask;
@@ -533,11 +598,15 @@ __global__ void k_glue_count(Geo g, double delta, const double *pts, int64_t n, 
     const int64_t p = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     int s[8];
     double psi[8];
+    float psf[8];
     unsigned mask = 0u;
     if (p < n) {
         double x[3];
         load_point(g, pts, p, x);
-        mask = glue_pairs<D, F32W>(g, delta, x, s, psi);
+        if (F32W)
+            mask = glue_pairs_f<D>(g, (float)(delta * (double)g.nmax), x, s, psf);
+        else
+            mask = glue_pairs<D>(g, delta, x, s, psi);
         if (mask == 0u) out[p] = nan("");
         e.mask[p] = (uint8_t)mask;
     }
@@ -555,7 +624,8 @@ __global__ void k_glue_count(Geo g, double delta, const double *pts, int64_t n, 
         if (have) {
             rank[p * nslot + c] = base + __popc(peers & ((1u << lane) - 1u));
             e.sub[p * nslot + c] = key;
-            e.psi[p * nslot + c] = psi[c];
+            if (F32W) e.psif[p * nslot + c] = psf[c];
+            else e.psi[p * nslot + c] = psi[c];
         }
     }
 }
@@ -594,7 +664,7 @@ __global__ void k_glue_bucket_f64(Geo g, const double *centres, const double *be
 
 __global__ void k_glue_bucket_f32(Geo g, const int32_t *boxes, const double *centres, const double *beta,
                                   const int32_t *info, const double *pts, const int32_t *perm,
-                                  const int32_t *start, double *val) {
+                                  const int32_t *start, float *val) {
     const int s = blockIdx.x;
     const int b = start[s], e = start[s + 1];
     if (b == e) return;
@@ -616,8 +686,8 @@ __global__ void k_glue_bucket_f32(Geo g, const int32_t *boxes, const double *cen
         }
         float v0, v1;
         shepard_f32_smem2(sc, sb, M, x0, x1, &v0, &v1);
-        val[q0] = (double)v0;
-        if (two) val[q1] = (double)v1;
+        val[q0] = v0;
+        if (two) val[q1] = v1;
     }
 }
 
@@ -633,8 +703,8 @@ __global__ void k_glue_combine(int64_t n, GlueWs e, double *out, int log_space) 
 #pragma unroll
         for (int c = 0; c < nslot; ++c)
             if ((mask >> c) & 1u) {
-                const float w = (float)e.psi[p * nslot + c];
-                num = fmaf(w, (float)e.val[p * nslot + c], num);
+                const float w = e.psif[p * nslot + c];
+                num = fmaf(w, e.valf[p * nslot + c], num);
                 den += w;
             }
         const float v = num / den;
@@ -667,7 +737,7 @@ static void glue_launches(const Geo &g, const int32_t *boxes, const double *cent
     if (precision == PAM_PREC_MIXED) {
         size_t sm = stage_f32_smem(g.m_cap);
         cudaFuncSetAttribute(k_glue_bucket_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_glue_bucket_f32<<<g.S, eval_block(), sm, st>>>(g, boxes, centres, beta, info, pts, e.perm, e.start, e.val);
+        k_glue_bucket_f32<<<g.S, eval_block(), sm, st>>>(g, boxes, centres, beta, info, pts, e.perm, e.start, e.valf);
         k_glue_combine<D, true><<<nb, 256, 0, st>>>(n_pts, e, out, log_space);
     } else {
         size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));
