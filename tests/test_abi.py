@@ -304,3 +304,19 @@ def test_selftest_wait_checks_its_arguments(pam):
     assert L.pam_selftest_wait(2, 100000, fake, None) == 1
     assert L.pam_selftest_wait(0, 10, fake, None) == 1
     assert L.pam_selftest_wait(0, 100000, None, None) == 1
+
+
+def test_partition_cells_on_faces_matches_the_oracle(pam):
+    # sampling points exactly on cell faces, core faces, patch faces and the
+    # outer faces of the domain: the half-open rule, closed at the outer face
+    shape, n_sub, ov = (20, 12), (4, 3), 2
+    h = 1.0 / 20
+    xs = np.arange(0, 21) * h
+    ys = np.arange(0, 13) * h
+    X, Y = np.meshgrid(xs, ys, indexing="xy")
+    x = np.stack([X.reshape(-1), Y.reshape(-1)], axis=1)
+    pr = pam.make_problem(shape, n_sub, ov, (2, 2))
+    start, cells = pam.pam_partition_cells(pr, x)
+    _, ostart, ocells = oracle.partition_cells(shape, n_sub, ov, x)
+    np.testing.assert_array_equal(start, ostart)
+    np.testing.assert_array_equal(cells, ocells)
