@@ -308,10 +308,11 @@ def test_selftest_wait_checks_its_arguments(pam):
 
 def test_partition_cells_on_faces_matches_the_oracle(pam):
     # sampling points exactly on cell faces, core faces, patch faces and the
-    # outer faces of the domain: the half-open rule, closed at the outer face
-    shape, n_sub, ov = (20, 12), (4, 3), 2
-    h = 1.0 / 20
-    xs = np.arange(0, 21) * h
+    # outer faces of the domain (h = 1/16, so k h is exact): the half-open
+    # rule, closed at the outer face
+    shape, n_sub, ov = (16, 12), (4, 3), 2
+    h = 1.0 / 16
+    xs = np.arange(0, 17) * h
     ys = np.arange(0, 13) * h
     X, Y = np.meshgrid(xs, ys, indexing="xy")
     x = np.stack([X.reshape(-1), Y.reshape(-1)], axis=1)
@@ -320,3 +321,8 @@ def test_partition_cells_on_faces_matches_the_oracle(pam):
     _, ostart, ocells = oracle.partition_cells(shape, n_sub, ov, x)
     np.testing.assert_array_equal(start, ostart)
     np.testing.assert_array_equal(cells, ocells)
+    # every point lies in some patch, and a point one ulp outside the outer
+    # face is an input error (the library does not drop it silently)
+    assert np.bincount(cells, minlength=x.shape[0]).min() >= 1
+    with pytest.raises(pam.PamError):
+        pam.pam_partition_cells(pr, np.array([[0.5, np.nextafter(0.75, 1.0)]]))
