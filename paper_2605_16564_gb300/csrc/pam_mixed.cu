@@ -1238,30 +1238,35 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
 // their previous solve, descending, ties to the lower index (one block,
 // bitonic sort of (cost, ~index) keys in shared memory). Any order gives the
 // same results; this one only shortens the tail of the launch.
-__global__ void __launch_bounds__(1024) k_solve_order(const uint32_t *cost, int S, int P, int32_t *order) {
-    extern __shared__ unsigned long long okeys[];
-    for (int i = threadIdx.x; i < P; i += blockDim.x)
-        okeys[i] = i < S ? (((unsigned long long)cost[i] << 32) | (unsigned long long)(0xffffffffu - (unsigned)i))
-                         : 0ull;
-    __syncthreads();
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = threadIdx.x; i < (P >> 1); i += blockDim.x) {
-                const int l = 2 * i - (i & (j - 1)), r = l + j;
-                const unsigned long long a = okeys[l], b = okeys[r];
-                if (((l & k) == 0) ? (a < b) : (a > b)) { okeys[l] = b; okeys[r] = a; }
-            }
-            __syncthreads();
-        }
-    }
-    for (int i = threadIdx.x; i < S; i += blockDim.x)
-        order[i] = (int32_t)(0xffffffffu - (unsigned)(okeys[i] & 0xffffffffull));
+// Longest-first order of the subdomains by the clock cost of their previous
+// solve, by buckets of 1/8 octave (the leading bit and the next three of the
+// cost): one pass of shared-memory counts, a scan from the costliest bucket
+// down, one scatter. Within a bucket (costs within 12.5 %) the order is the
+// atomics'; the results of the solve do not depend on the order.
+__device__ __forceinline__ int cost_bucket(uint32_t c) {
+    if (c < 16u) return (int)c;  // 0..15
+    const int e = 31 - __clz((int)c);  // >= 4
+    return 8 * e + (int)((c >> (e - 3)) & 7u) - 16;  // 16..239, increasing with c
 }
 
-// Shared-memory budget of the packed factor: supports with s (s+1)/2 fp32
-// beyond it keep their factor in global memory (L1/L2). A smaller budget
-// lets more subdomains share an SM. PAM_FACTOR_SMEM_KB overrides the
-// default for tuning.
+__global__ void __launch_bounds__(1024) k_solve_order(const uint32_t *cost, int S, int32_t *order) {
+    constexpr int kB = 256;
+    __shared__ int cnt[kB], base[kB];
+    for (int i = threadIdx.x; i < kB; i += blockDim.x) cnt[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < S; i += blockDim.x) atomicAdd(&cnt[cost_bucket(cost[i])], 1);
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int run = 0;
+        for (int q = kB - 1; q >= 0; --q) {
+            base[q] = run;
+            run += cnt[q];
+        }
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < S; i += blockDim.x) order[atomicAdd(&base[cost_bucket(cost[i])], 1)] = i;
+}
+
 // Shared memory of the mixed solve besides the packed factor.
 static size_t solve_mixed_smem_rest(const Geo &g) {
     return (size_t)g.m_cap * (5 * sizeof(float) + 2 * sizeof(int) + sizeof(float4)) +
@@ -1320,14 +1325,9 @@ void launch_solve_mixed(const Geo &g, const Par &p, const int32_t *boxes, const 
     size_t sm = solve_mixed_smem(g);
     cudaFuncSetAttribute(k_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     PhaseScope ps(kPhSolve, st);
-    int P = 1;
-    while (P < g.S) P <<= 1;
-    const int ordered = P <= 16384 ? 1 : 0;  // the sort keeps P keys in shared memory
-    if (ordered) {
-        cudaFuncSetAttribute(k_solve_order, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(P * 8));
-        k_solve_order<<<1, 1024, (size_t)P * 8, st>>>(w.cost, g.S, P, w.order);
-        count_launches(1);
-    }
+    const int ordered = 1;
+    k_solve_order<<<1, 1024, 0, st>>>(w.cost, g.S, w.order);
+    count_launches(1);
     k_solve_mixed<<<g.S, kMxThreads, sm, st>>>(g, p, boxes, centres, beta, info, w, factor_smem_bytes(g),
                                                ordered, lam_tab, all, cv, cv_stride);
     count_launches(1);
