@@ -91,7 +91,7 @@ __global__ void __launch_bounds__(kGT, 1) k_gemm_bf16(const bf16 *A, int lda, co
                                                       int M, int N, int K, float *C32, bf16 *C16,
                                                       int ldc, const float *bias, int relu,
                                                       int32_t *status) {
-    const int n0 = blockIdx.x * 128, m0 = blockIdx.y * 128;
+    const int m0 = blockIdx.x * 128, n0 = blockIdx.y * 128;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nt = min(128, ((N - n0) + 15) & ~15);  // MMA N of this tile
     extern __shared__ __align__(1024) uint8_t smem[];
@@ -206,7 +206,9 @@ __global__ void __launch_bounds__(kGT, 1) k_gemm_bf16(const bf16 *A, int lda, co
 
 static void gemm(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K, float *C32,
                  bf16 *C16, int ldc, const float *bias, int relu, int32_t *status, cudaStream_t st) {
-    dim3 grid((N + 127) / 128, (M + 127) / 128);
+    // M tiles on x (up to 2^31 - 1 blocks): a 65,536-row forward pass has
+    // 2^17 row tiles in its first convolution
+    dim3 grid((M + 127) / 128, (N + 127) / 128);
     k_gemm_bf16<<<grid, kGT, 32768 + 1024, st>>>(A, lda, B, ldb, M, N, K, C32, C16, ldc, bias, relu, status);
     count_launches(1);
 }
@@ -220,7 +222,7 @@ __global__ void k_cast_bf16(const float *x, bf16 *y, int64_t n) {
 // out [cols][rows] = in [rows][cols]^T (bf16), 32 x 32 tiles.
 __global__ void k_transpose_bf16(const bf16 *in, int rows, int cols, int ldi, bf16 *out, int ldo) {
     __shared__ bf16 t[32][33];
-    const int r0 = blockIdx.y * 32, c0 = blockIdx.x * 32;
+    const int r0 = blockIdx.x * 32, c0 = blockIdx.y * 32;
     for (int k = threadIdx.y; k < 32; k += blockDim.y) {
         const int r = r0 + k, c = c0 + threadIdx.x;
         t[k][threadIdx.x] = (r < rows && c < cols) ? in[(size_t)r * ldi + c] : __float2bfloat16_rn(0.f);
@@ -233,7 +235,7 @@ __global__ void k_transpose_bf16(const bf16 *in, int rows, int cols, int ldi, bf
 }
 
 static void transpose(const bf16 *in, int rows, int cols, int ldi, bf16 *out, int ldo, cudaStream_t st) {
-    dim3 grid((cols + 31) / 32, (rows + 31) / 32), block(32, 8);
+    dim3 grid((rows + 31) / 32, (cols + 31) / 32), block(32, 8);  // rows on x: no 65,535 limit
     k_transpose_bf16<<<grid, block, 0, st>>>(in, rows, cols, ldi, out, ldo);
     count_launches(1);
 }

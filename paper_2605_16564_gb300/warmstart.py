@@ -172,6 +172,23 @@ class Network:
                 log(f"epoch {ep}: bce {history[-1][0]:.4f} mse {history[-1][1]:.4f}")
         return history
 
+    def mean_loss(self, x, support, beta):
+        """Mean (BCE, MSE) of the current weights over (x, support, beta),
+        in passes of the training batch size (a ragged tail is dropped);
+        the weights are not changed."""
+        import torch
+        P = x.shape[0] // self.batch * self.batch
+        X = self._dev(x[:P]).reshape(P, self.h0, self.h0, self.c0)
+        Sp, Bt = self._dev(support[:P]), self._dev(beta[:P])
+        grads = torch.zeros(self.n, device=self.device)
+        acc = torch.zeros(2, device=self.device)
+        for i in range(0, P, self.batch):
+            sl = slice(i, i + self.batch)
+            pam.pam_nn_gradients(self.params, X[sl].contiguous(), Sp[sl].contiguous(), Bt[sl].contiguous(),
+                                 grads, self.loss, self.ws, arch=self.arch)
+            acc += self.loss
+        return (acc / (P // self.batch)).cpu().numpy().tolist()
+
     def forward_device(self, X, out=None, ws=None):
         """Device forward of X [rows,h,h,c] (rows a multiple of 32) into out
         [rows, 2 n_out]; one call, with a workspace sized for the rows."""
@@ -184,12 +201,20 @@ class Network:
         pam.pam_nn_forward(self.params, X, out, ws, arch=self.arch)
         return out
 
-    def predict(self, x):
-        """x [P,h,h,c] -> (support logits [P,n_out], beta [P,n_out]) numpy."""
+    def predict(self, x, batched=False):
+        """x [P,h,h,c] -> (support logits [P,n_out], beta [P,n_out]) numpy.
+        batched: one forward pass over all P rows (padded to a multiple of
+        32) instead of passes of the training batch size."""
         import torch
         P = x.shape[0]
-        out = torch.zeros((P, 2 * self.n_out), dtype=torch.float32, device=self.device)
         X = self._dev(x).reshape(P, self.h0, self.h0, self.c0)
+        if batched:
+            rows = -(-P // 32) * 32
+            if rows > P:
+                X = torch.cat([X, torch.zeros((rows - P, self.h0, self.h0, self.c0), device=self.device)])
+            o = self.forward_device(X.contiguous())[:P].cpu().numpy()
+            return o[:, :self.n_out], o[:, self.n_out:] * BETA_SCALE
+        out = torch.zeros((P, 2 * self.n_out), dtype=torch.float32, device=self.device)
         for i in range(0, P, self.batch):
             xb = X[i:i + self.batch]
             if xb.shape[0] < self.batch:
@@ -220,10 +245,11 @@ def warm_start_coefficients(logits, beta, threshold=SEED_THRESHOLD):
 def learned_fit(net, patches, device, precision=pam.PAM_PREC_FP64, budget=48):
     """Fit with the network's warm start; patches not certified within
     `budget` active-set iterations are refitted plainly from zero.
+    The inference is one batched forward pass over all the patches.
     Returns dict(beta, info, solve_ms, refit, predict_ms)."""
     import torch
     t0 = time.perf_counter()
-    logits, b = net.predict(network_input(patches))
+    logits, b = net.predict(network_input(patches), batched=True)
     torch.cuda.synchronize()
     t_pred = (time.perf_counter() - t0) * 1e3
     beta0 = warm_start_coefficients(logits, b)
