@@ -778,6 +778,54 @@ def oracle_sample(workload: str, n_sub_sample: int, seed_offset=0):
     return dict(cells=cells, seconds=dt, cores=cores, n_sub=len(which), n_pts=len(pts))
 
 
+def oracle_patches(n_patches, seed=40):
+    """Time the FP64 oracle's plain fit (16 x 16 dictionary, no refinement)
+    of `n_patches` evenly spaced patches of a batch of 4,096 seeded 32 x 32
+    patches tiled 64 x 64: the labelling fit of the learned warm start."""
+    import oracle
+    held = fields.patch_batch(4096, seed=seed)
+    T, P = 64, 32
+    grid = np.ascontiguousarray(held.reshape(T, T, P, P).transpose(0, 2, 1, 3).reshape(T * P, T * P))
+    which = np.unique(np.linspace(0, 4095, n_patches).astype(np.int32))
+    t0 = time.perf_counter()
+    oracle.fit_all(grid, (T * P, T * P), (T, T), 0, (16, 16), oracle.default_params(k_top=1, levels=0),
+                   which=which)
+    return dict(cells=len(which) * P * P, seconds=time.perf_counter() - t0, n_sub=len(which))
+
+
+def oracle_table():
+    """The FP64 oracle on the host cores, per workload: the 64^2 disc, the
+    256^2 Voronoi field and the 60 x 220 x 85 layered field in full, the
+    1024^2 channel field and the 32 x 32 patches on evenly spaced samples
+    (their full time extrapolated linearly by subdomains); each on all
+    cores and on one thread (the layered field's one-thread figure on a
+    sample). Every time is fit + evaluation of the target points in the
+    timed subdomains' cores (the patches: the plain fit alone)."""
+    import oracle
+    n_all = oracle.threads()
+    rows = []
+    plan = [("disc2d", 1, 1), ("voronoi2d", 64, 64), ("channel2d", 64, 16), ("layered3d", 2244, 64),
+            ("patches32", 64, 16)]
+    for name, n_many, n_one in plan:
+        for nt, n in ((n_all, n_many), (1, n_one)):
+            oracle.threads(nt)
+            if name == "patches32":
+                r = oracle_patches(n)
+                total = 50176 + 4096
+            else:
+                r = oracle_sample(name, n)
+                total = int(np.prod(WORKLOADS[name]["n_sub"]))
+            full = r["n_sub"] == total
+            rows.append({"workload": name, "threads": nt, "subdomains": r["n_sub"], "of": total,
+                         "cells": r["cells"], "seconds": round(r["seconds"], 3),
+                         "cells_per_s": round(r["cells"] / r["seconds"], 1),
+                         "full_seconds": round(r["seconds"] * total / r["n_sub"], 1),
+                         "full_seconds_kind": "measured" if full else "extrapolated by subdomains"})
+            print(json.dumps(rows[-1]), flush=True)
+    oracle.threads(n_all)
+    return rows
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -799,7 +847,13 @@ def main():
                     help="also time the glued evaluation (pam_eval_glued) with this band in cells")
     ap.add_argument("--quad", type=int, default=0, choices=[0, 1],
                     help="indicator and error quadrature: 0 midpoint, 1 two-point Gauss-Legendre per axis")
+    ap.add_argument("--oracle-table", action="store_true",
+                    help="only time the FP64 oracle on every workload (all host cores and one thread)")
     args = ap.parse_args()
+    if args.oracle_table:
+        rows = oracle_table()
+        print(json.dumps({"oracle_table": rows, "host_cores": os.cpu_count()}))
+        return
     rank, ws = _dist()
     W = WORKLOADS[args.workload]
     if args.cpu_sample is None:

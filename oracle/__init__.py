@@ -96,8 +96,16 @@ def lib():
             L.orc_fit_cells_all.argtypes = [C.c_int, i32p, f64p, f64p, f64p, C.c_int, i32p, i64p, i32p, i32p,
                                             C.c_void_p, C.c_int, C.c_void_p, C.c_int, f64p, f64p, f64p]
             L.orc_fit_cells_all.restype = C.c_int
+            L.orc_threads.argtypes = [C.c_int]
+            L.orc_threads.restype = C.c_int
             _lib = L
     return _lib
+
+
+def threads(n=0):
+    """OpenMP threads of the oracle's loops (n > 0 sets them); returns the
+    count in effect. Timing only: the results do not depend on it."""
+    return int(lib().orc_threads(int(n)))
 
 
 class _Params(C.Structure):

@@ -26,6 +26,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define ORC_MAXD 3
 
@@ -946,4 +949,18 @@ void orc_errors(int dim, const int *n_cells, const int *n_sub, int m_cap,
     err[2] = bl > 0 ? al / bl : al;
     err[3] = mx;
     free(x); free(v);
+}
+
+/* Threads of the OpenMP loops over subdomains and points, for timing the
+ * oracle on a given number of host cores: n > 0 sets the count for the
+ * calling thread's later loops; returns the count in effect. */
+int orc_threads(int n)
+{
+#ifdef _OPENMP
+    if (n > 0) omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
 }

@@ -575,3 +575,22 @@ def test_algorithm1_certifies_every_subdomain_of_a_batched_case():
     assert np.all(mdl["M"] >= 16) and np.all(mdl["M"] <= 16 + 2 * 3 * 10)
     lam = [float(v) for _, v in _golden_rows("example2_lambdas.txt")]
     assert lam == [p["lambda1_hat"], p["lambda2_hat"]]
+
+
+def test_results_do_not_depend_on_the_thread_count():
+    # the OpenMP loops run subdomains and points independently: one thread
+    # and all threads give the same bits (the host timing table uses both)
+    K = fields.voronoi_field(64, n_sites=10, seed=18)
+    p = oracle.default_params(k_top=10, levels=2)
+    pts = np.random.default_rng(18).uniform(0, 1, size=(2000, 2))
+    n_all = oracle.threads()
+    try:
+        oracle.threads(1)
+        a = oracle.fit_all(K, (64, 64), (4, 4), 2, (4, 4), p)
+        ea = oracle.evaluate(a, pts)
+    finally:
+        oracle.threads(n_all)
+    b = oracle.fit_all(K, (64, 64), (4, 4), 2, (4, 4), p)
+    for key in ("M", "c", "beta", "info"):
+        np.testing.assert_array_equal(a[key], b[key])
+    np.testing.assert_array_equal(ea, oracle.evaluate(b, pts))
