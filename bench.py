@@ -341,13 +341,24 @@ def run_pam(args, rank, ws):
         warm_it = float(it0())
         learned = {"kind": "learned (PAM_NN_LAYERED3D network seeds the level-0 active set)",
                    "train_fields": 8, "train_samples": 8 * fit.plan.n_subdomains, "train_s": round(train_s, 2),
-                   "seed_threshold": lw.threshold, "level0_active_set_steps_cold": round(cold_it, 3),
+                   "seed_threshold": lw.threshold,
+                   "inference_stream": "a side stream beside the level-0 partition, cell data and Gram "
+                                       "products; the level-0 solve waits on its event",
+                   "level0_active_set_steps_cold": round(cold_it, 3),
                    "level0_active_set_steps_learned": round(warm_it, 3)}
+
+    # the inference runs on a side stream beside the level-0 partition, cell
+    # data and Gram products; the level-0 solve waits for its event
+    seed_stream = torch.cuda.Stream(device=dev) if lw is not None else None
+    seeded = torch.cuda.Event() if lw is not None else None
 
     def fit_step(deferred=False):
         if lw is not None:
-            lw.seed(fit, Kd)
-            fit.fit(Kd, warm_start=True, deferred=deferred)
+            seed_stream.wait_stream(torch.cuda.current_stream())
+            with torch.cuda.stream(seed_stream):
+                lw.seed(fit, Kd)
+                seeded.record(seed_stream)
+            fit.fit(Kd, warm_start=True, deferred=deferred, warm_start_event=seeded)
         else:
             fit.fit(Kd, deferred=deferred)
 

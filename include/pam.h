@@ -118,6 +118,18 @@ typedef struct {
                             PAM_OK after the launches, fit even when some K_T is
                             invalid, and the status accumulates in the workspace
                             until pam_status_read */
+    void *warm_start_event; /* pam_fit_subdomains / pam_fit_cells with warm_start = 1: a
+                            cudaEvent_t or NULL. When set, the stream waits on the event
+                            (cudaStreamWaitEvent) just before the level-0 solve, the first
+                            kernel that reads model->beta; the partition, the dictionary
+                            set-up (which leaves beta[s][0..m0) alone in warm-start mode),
+                            the cell data and the Gram products are enqueued before the
+                            wait. So a warm start written on another stream (pam_nn_seed)
+                            and followed by a record of this event overlaps them.
+                            pam_fit_cells waits before the dictionary set-up instead (it
+                            zeroes the coefficients of a patch without elements). Ignored
+                            otherwise and by the other calls. An invalid event gives
+                            PAM_ERR_CUDA. */
 } pam_params;
 
 /* Sizes derived from a problem and parameters by pam_plan_create. */

@@ -342,12 +342,20 @@ static pam_status fit_launches(const Geo &g, const Par &p, const pam_params *par
         if ((st = read_status(w, s, hs)) != PAM_OK) return st;
         if (hs[kStBadK]) return PAM_ERR_NONPOSITIVE_K;
     }
+    // a warm start still being written on another stream: the solve waits for
+    // it (element lists: the dictionary set-up already, which zeroes the
+    // coefficients of a patch without elements)
+    cudaEvent_t seeded = par->warm_start ? (cudaEvent_t)par->warm_start_event : nullptr;
+    if (seeded && g.cells) {
+        PAM_CUDA_TRY(cudaStreamWaitEvent(s, seeded, 0));
+        seeded = nullptr;
+    }
     launch_init_dictionary(g, model->boxes, model->centres, model->beta, model->info, s,
                            par->warm_start != 0);
     if (par->precision == PAM_PREC_MIXED)
-        launch_solve_level_mixed(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
+        launch_solve_level_mixed(g, p, model->boxes, model->centres, model->beta, model->info, w, s, seeded);
     else
-        launch_solve_level_f64(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
+        launch_solve_level_f64(g, p, model->boxes, model->centres, model->beta, model->info, w, s, seeded);
     PAM_CUDA_TRY(cudaGetLastError());
     if (deferred) return PAM_OK;
     if ((st = read_status(w, s, hs)) != PAM_OK) return st;

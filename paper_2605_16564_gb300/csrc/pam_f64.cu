@@ -590,8 +590,9 @@ void launch_solve_f64(const Geo &g, const Par &p, double *beta, int32_t *info, c
 
 void launch_solve_level_f64(const Geo &g, const Par &p, const int32_t *boxes,
                             const double *centres, double *beta, int32_t *info, const Ws &w,
-                            cudaStream_t st) {
+                            cudaStream_t st, cudaEvent_t before_solve) {
     launch_assemble_gram_f64(g, boxes, centres, info, w, st, 0);
+    if (before_solve) cudaStreamWaitEvent(st, before_solve, 0);  // an error surfaces in cudaGetLastError
     launch_solve_f64(g, p, beta, info, w, nullptr, 0, st);
 }
 

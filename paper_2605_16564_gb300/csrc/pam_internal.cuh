@@ -85,8 +85,11 @@ void launch_errors_cells(const Geo &g, const int32_t *boxes, const double *centr
                          cudaStream_t st);
 void launch_init_dictionary(const Geo &g, const int32_t *boxes, double *centres, double *beta,
                             int32_t *info, cudaStream_t st, int keep_beta);
+// before_solve: an event the stream waits on between the Gram products and
+// the solve (the first kernel of a level that reads beta), or null.
 void launch_solve_level_f64(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
-                            double *beta, int32_t *info, const Ws &w, cudaStream_t st);
+                            double *beta, int32_t *info, const Ws &w, cudaStream_t st,
+                            cudaEvent_t before_solve = nullptr);
 void launch_stats_gram_tc(const Geo &g, const int32_t *boxes, const double *centres,
                           const int32_t *info, const Ws &w, cudaStream_t st, int all);
 void launch_assemble_gram_f64(const Geo &g, const int32_t *boxes, const double *centres,
@@ -107,7 +110,8 @@ void launch_copy_gram_f32(const Geo &g, const int32_t *info, const Ws &w, double
 void launch_copy_gram_f64(const Geo &g, const int32_t *info, const Ws &w, double *G_out,
                           double *b_out, cudaStream_t st);
 void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
-                              double *beta, int32_t *info, const Ws &w, cudaStream_t st);
+                              double *beta, int32_t *info, const Ws &w, cudaStream_t st,
+                              cudaEvent_t before_solve = nullptr);
 void launch_refine_round(const Geo &g, const Par &p, int precision, const int32_t *boxes,
                          double *centres, double *beta, int32_t *info, const Ws &w, cudaStream_t st);
 void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,

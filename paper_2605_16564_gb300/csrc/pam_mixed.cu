@@ -1335,8 +1335,9 @@ void launch_solve_mixed(const Geo &g, const Par &p, const int32_t *boxes, const 
 
 void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes,
                               const double *centres, double *beta, int32_t *info, const Ws &w,
-                              cudaStream_t st) {
+                              cudaStream_t st, cudaEvent_t before_solve) {
     launch_stats_gram_tc(g, boxes, centres, info, w, st, 0);
+    if (before_solve) cudaStreamWaitEvent(st, before_solve, 0);  // an error surfaces in cudaGetLastError
     launch_solve_mixed(g, p, boxes, centres, beta, info, w, nullptr, 0, nullptr, 0, st);
 }
 

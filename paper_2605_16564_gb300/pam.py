@@ -56,7 +56,7 @@ class pam_params(C.Structure):
                 ("eps_tol_rel", C.c_double), ("eta", C.c_double), ("k_top", C.c_int),
                 ("m_max", C.c_int), ("levels", C.c_int), ("max_iters", C.c_int),
                 ("precision", C.c_int), ("warm_start", C.c_int), ("quad", C.c_int),
-                ("deferred_status", C.c_int)]
+                ("deferred_status", C.c_int), ("warm_start_event", C.c_void_p)]
 
 
 class pam_plan(C.Structure):
@@ -177,6 +177,17 @@ def _check(code, where):
 
 def _ptr(t):
     return C.c_void_p(t.data_ptr()) if t is not None else C.c_void_p(0)
+
+
+def _event_handle(event):
+    """cudaEvent_t of a torch.cuda.Event (created by its first record), an
+    integer handle as is, or None."""
+    if event is None:
+        return None
+    h = int(getattr(event, "cuda_event", event))
+    if h == 0:
+        raise ValueError("the event has not been recorded")
+    return h
 
 
 def _stream(stream):
@@ -562,15 +573,19 @@ class Fitter:
         self.model = alloc_model(self.plan, device)
         self.workspace = alloc_workspace(self.plan, device)
 
-    def fit(self, K, levels=None, stream=None, check=True, warm_start=False, deferred=False):
+    def fit(self, K, levels=None, stream=None, check=True, warm_start=False, deferred=False,
+            warm_start_event=None):
         """Step 2, then `levels` rounds of Step 3 (default: the planned levels).
         warm_start: the initial dictionary starts from the coefficients
         already in model.beta (e.g. seeded by pam_nn_seed).
+        warm_start_event: a torch.cuda.Event recorded after the warm start
+        was written on another stream; the level-0 solve waits for it.
         deferred: launch only, no host synchronisation (capturable in a CUDA
         graph); the status is read later with status()."""
         lv = self.params.levels if levels is None else levels
         self.params.warm_start = 1 if warm_start else 0
         self.params.deferred_status = 1 if deferred else 0
+        self.params.warm_start_event = _event_handle(warm_start_event)
         try:
             c1 = pam_fit_subdomains(self.problem, self.params, self.plan, K, self.model, self.workspace,
                                     stream, check)
@@ -579,6 +594,7 @@ class Fitter:
         finally:
             self.params.warm_start = 0
             self.params.deferred_status = 0
+            self.params.warm_start_event = None
         return c1 or c2
 
     def lambda_cv(self, K, grid, n_folds, stream=None, check=True):
@@ -705,10 +721,12 @@ class CellFitter(Fitter):
         self.model = alloc_model(self.plan, device)
         self.workspace = alloc_workspace(self.plan, device)
 
-    def fit(self, K, levels=None, stream=None, check=True, warm_start=False, deferred=False):
+    def fit(self, K, levels=None, stream=None, check=True, warm_start=False, deferred=False,
+            warm_start_event=None):
         lv = self.params.levels if levels is None else levels
         self.params.warm_start = 1 if warm_start else 0
         self.params.deferred_status = 1 if deferred else 0
+        self.params.warm_start_event = _event_handle(warm_start_event)
         try:
             c1 = pam_fit_cells(self.problem, self.params, self.plan, self.cells, K, self.model, self.workspace,
                                stream, check)
@@ -717,6 +735,7 @@ class CellFitter(Fitter):
         finally:
             self.params.warm_start = 0
             self.params.deferred_status = 0
+            self.params.warm_start_event = None
         return c1 or c2
 
     def errors_device(self, K, err, precision=None, stream=None, quad=None):

@@ -149,6 +149,19 @@ def test_layered_3d_learned_seed(precision):
     assert fit.fit(Kd, levels=0, check=False, warm_start=True) == 0
     it_warm = it()
     assert np.all((flags() & pam.FLAG_NOT_CERTIFIED) == 0)
+    # the same seeded fit with the inference on a side stream, joined by an
+    # event before the level-0 solve (pam_params.warm_start_event): the same
+    # bits, although model.beta holds NaN when the fit is enqueued
+    b_seq, i_seq = fit.model.beta.cpu().numpy().copy(), fit.model.info.cpu().numpy().copy()
+    fit.model.beta.fill_(float("nan"))
+    side, ev = torch.cuda.Stream(device=dev), torch.cuda.Event()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        lw.seed(fit, Kd)
+        ev.record(side)
+    assert fit.fit(Kd, levels=0, check=False, warm_start=True, warm_start_event=ev) == 0
+    np.testing.assert_array_equal(fit.model.beta.cpu().numpy(), b_seq)
+    np.testing.assert_array_equal(fit.model.info.cpu().numpy(), i_seq)
     print(f"precision {precision}: level-0 active-set steps cold {it_cold.mean():.2f} -> learned "
           f"{it_warm.mean():.2f} (max {it_cold.max()} -> {it_warm.max()})")
     assert it_warm.mean() <= 0.8 * it_cold.mean()
