@@ -62,6 +62,10 @@ WORKLOADS = {
                    field=lambda seed: fields.disc_field(64), seed=0),
 }
 
+# slices of the end-to-end evaluation whose device-to-host copies overlap
+# the evaluation of the next slices
+E2E_EVAL_CHUNKS = 4
+
 PHASES = ["prepare", "assemble", "gram", "solve", "residual", "mark", "eval", "errors", "stats",
           "gram_tc", "refine"]
 
@@ -532,7 +536,7 @@ def run_pam(args, rank, ws):
     outh = torch.empty(n_pts, dtype=torch.float64).pin_memory()
     errh = torch.empty(4, dtype=torch.float64).pin_memory()
     side = torch.cuda.Stream(device=dev)  # the evaluation points and the result travel beside the fit
-    pts_ready, out_ready = torch.cuda.Event(), torch.cuda.Event()
+    pts_ready = torch.cuda.Event()
 
     def e2e_body():
         cur = torch.cuda.current_stream()
@@ -543,11 +547,8 @@ def run_pam(args, rank, ws):
         Kd.copy_(Kh, non_blocking=True)
         fit_step(deferred=True)
         cur.wait_event(pts_ready)
-        fit.eval(ptsd, out=out)
-        out_ready.record(cur)
-        with torch.cuda.stream(side):
-            side.wait_event(out_ready)
-            outh.copy_(out, non_blocking=True)
+        # evaluated in slices, each copied back while the next evaluates
+        fit.eval_to_host(ptsd, out, outh, chunks=E2E_EVAL_CHUNKS, copy_stream=side, join=False)
         fit.errors_device(Kd, errd)
         errh.copy_(errd, non_blocking=True)
         cur.wait_stream(side)
@@ -934,7 +935,8 @@ def main():
         "roofline": r["roof"],
         "cpu_baseline": cpu,
         "e2e": {"value": r["n_cells"] * ws / r["e2e_s"], "unit": "cells/s",
-                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"], "launch": r["e2e_mode"]},
+                "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"], "launch": r["e2e_mode"],
+                "eval_slices": E2E_EVAL_CHUNKS},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
         "phase_ms_per_step": {k: round(v[0], 4) for k, v in r["phase_ms"].items()},

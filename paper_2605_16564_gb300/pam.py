@@ -637,6 +637,48 @@ class Fitter:
                  self.eval_workspace(pts.shape[0]), stream)
         return out
 
+    def eval_to_host(self, pts, out, out_host, chunks=4, copy_stream=None, join=True, log_space=False,
+                     precision=None):
+        """pam_eval of pts into the device buffer out in `chunks` contiguous
+        slices, each slice's values copied to the pinned host buffer out_host
+        on copy_stream as soon as they are ready, so that the copies overlap
+        the evaluation of the later slices (the values are those of one
+        pam_eval call: every point is evaluated on its own). Enqueued on the
+        current stream; join: later work on it waits for the copies (else
+        the caller joins copy_stream itself, and work enqueued meanwhile runs
+        beside the copies). Capturable in a CUDA graph."""
+        import torch
+        n = pts.shape[0]
+        cur = torch.cuda.current_stream()
+        cs = copy_stream if copy_stream is not None else self._copy_stream()
+        k = max(1, min(int(chunks), n)) if n > 0 else 0
+        evs = self._chunk_events(k)
+        self.eval_workspace(n)  # one workspace, sized for the whole set, serves every slice
+        for i in range(k):
+            a, b = n * i // k, n * (i + 1) // k
+            self.eval(pts[a:b], out=out[a:b], log_space=log_space, precision=precision)
+            evs[i].record(cur)
+            cs.wait_event(evs[i])
+            with torch.cuda.stream(cs):
+                out_host[a:b].copy_(out[a:b], non_blocking=True)
+        if join:
+            cur.wait_stream(cs)
+        return out_host
+
+    def _copy_stream(self):
+        import torch
+        if getattr(self, "_cs", None) is None:
+            self._cs = torch.cuda.Stream(device=self.device)
+        return self._cs
+
+    def _chunk_events(self, k):
+        import torch
+        evs = getattr(self, "_chunk_evs", [])
+        while len(evs) < k:
+            evs.append(torch.cuda.Event())
+        self._chunk_evs = evs
+        return evs
+
     def eval_glued(self, pts, band, out=None, log_space=False, precision=None, stream=None):
         """K*(x) blended across the subdomain interfaces (pam_eval_glued)."""
         import torch

@@ -115,3 +115,45 @@ def test_graph_replay_reproduces_the_eager_step(env, prec):
     for a, b in zip(_model(fit2), _model(fit)):
         np.testing.assert_array_equal(a, b)
     del g
+
+
+@pytest.mark.parametrize("prec,chunks", [("mixed", 1), ("mixed", 3), ("fp64", 7)])
+def test_chunked_evaluation_to_host_matches_one_call(env, prec, chunks):
+    # Fitter.eval_to_host: slices of the points evaluated one after another,
+    # each copied to pinned host memory on a side stream; the values are
+    # those of one pam_eval call, eager and replayed from a CUDA graph
+    torch, pam, dev = env
+    p = pam.PAM_PREC_FP64 if prec == "fp64" else pam.PAM_PREC_MIXED
+    fit, Kd = _fitter(env, p, fields.voronoi_field(n=128, n_sites=24, seed=13))
+    fit.fit(Kd)
+    pts = torch.from_numpy(fields.cell_centred_points((97, 83), (1.0, 1.0))).to(dev)
+    n = pts.shape[0]
+    ref = fit.eval(pts).cpu().numpy()
+    out = torch.empty(n, dtype=torch.float64, device=dev)
+    host = torch.zeros(n, dtype=torch.float64).pin_memory()
+    fit.eval_to_host(pts, out, host, chunks=chunks)
+    torch.cuda.current_stream().synchronize()  # the current stream waited for the copies
+    np.testing.assert_array_equal(host.numpy(), ref)
+
+    side = torch.cuda.Stream(device=dev)
+
+    def body():
+        side.wait_stream(torch.cuda.current_stream())
+        fit.eval_to_host(pts, out, host, chunks=chunks, copy_stream=side, join=False)
+        torch.cuda.current_stream().wait_stream(side)
+
+    s = torch.cuda.Stream(device=dev)
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):
+        body()
+    torch.cuda.current_stream().wait_stream(s)
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        body()
+    host.zero_()
+    out.zero_()
+    g.replay()
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(host.numpy(), ref)
+    del g
