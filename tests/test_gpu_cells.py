@@ -182,3 +182,33 @@ def test_cells_mesh_with_a_hole_that_empties_a_patch(env, precision):
     else:
         e_m, e_o = fit.errors(Kd), oracle.errors_cells(ref, x, vol, K)
         assert abs(e_m["l1"] - e_o["l1"]) <= L1_RTOL * e_o["l1"]
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+def test_cells_warm_start_written_on_a_side_stream(env, precision):
+    # pam_fit_cells with warm_start and pam_params.warm_start_event: the
+    # coefficients copied into model.beta on another stream after the fit is
+    # enqueued are the ones the level-0 solve starts from (the wait comes
+    # before the dictionary set-up on element lists): the same bits as the
+    # in-line warm start, although beta holds NaN when the fit is enqueued
+    torch, pam, dev = env
+    x, vol = fields.triangle_mesh(64, seed=62)
+    K = fields.voronoi_at(x, 12, 62)
+    geo, params = ((64, 64), (4, 4), 1, (4, 4)), dict(k_top=6, levels=0)
+    fit, Kd = _fit(env, x, vol, K, geo, precision=precision, **params)
+    seed = fit.model.beta.clone()
+    seed[:, ::2] = 0.0  # a partial warm start: half the coefficients
+    fit.model.beta.copy_(seed)
+    assert fit.fit(Kd, levels=0, warm_start=True, check=False) == 0
+    b_seq, i_seq = fit.model.beta.cpu().numpy().copy(), fit.model.info.cpu().numpy().copy()
+    fit.model.beta.fill_(float("nan"))
+    side, ev = torch.cuda.Stream(device=dev), torch.cuda.Event()
+    side.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(side):
+        torch.cuda._sleep(20_000_000)  # the copy lands well after the fit is enqueued
+        fit.model.beta.copy_(seed)
+        ev.record(side)
+    assert fit.fit(Kd, levels=0, warm_start=True, warm_start_event=ev, check=False) == 0
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(fit.model.beta.cpu().numpy(), b_seq)
+    np.testing.assert_array_equal(fit.model.info.cpu().numpy(), i_seq)
