@@ -53,7 +53,7 @@ typedef enum {
     PAM_ERR_CUDA = 3,          /* a CUDA runtime call failed */
     PAM_ERR_WORKSPACE = 4,     /* workspace smaller than pam_plan.workspace_bytes */
     PAM_ERR_NOT_CONVERGED = 5, /* some subdomain's solve was not certified (see info) */
-    PAM_ERR_UNSUPPORTED = 6,   /* valid request this build does not serve */
+    PAM_ERR_UNSUPPORTED = 6,   /* a valid request the library does not serve */
     PAM_ERR_TIMEOUT = 7        /* a bounded device wait gave up (tensor-core pipeline) */
 } pam_status;
 
@@ -470,7 +470,7 @@ pam_status pam_resume_cells(const pam_problem *prob, const pam_params *par, cons
                             size_t workspace_bytes, void *stream);
 
 /*
- * Learned warm start (spec addition; the paper has no learned part).
+ * Learned warm start (an addition: the paper has no learned part).
  * A convolutional network maps a subdomain patch of log10(K)/3 (clipped to
  * [-1, 1], NHWC) to n_out support logits and n_out coefficients / 4 of the
  * patch's initial dictionary. Two architectures (arch):

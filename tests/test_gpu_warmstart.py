@@ -3,7 +3,7 @@ patch workload: about 50k seeded 32 x 32 patches (224^2 = 50,176) labelled
 by the plain fit, the network trained on them with the project's kernels,
 and its inference batched over 4,096 held-out patches in one forward pass.
 What it gains: fewer active-set iterations for the same certified minimiser
-(the plain regression stays the fallback and the judge). Parity: on an
+(the plain regression stays the fallback and has the last word). Parity: on an
 evenly spaced sample of the held-out patches the oracle fits each patch,
 and the learned form matches it -- binary64: coefficients within 1e-9 and
 the same supports; fp32 form: the patch's L1 error within 1 % of the
