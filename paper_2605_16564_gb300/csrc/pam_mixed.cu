@@ -60,10 +60,39 @@ __device__ __forceinline__ void local_cell(const Geo &g, int s, const int32_t *b
 }
 
 // --------------------------------------------------------------------------
-// Row statistics of the Shepard normalisation (Eq. (10)): l2* = max_m l2_jm
-// and 1 / sum_m 2^(l2_jm - l2*), one thread per patch cell, one pass over
-// the centres.
+// Row statistics of the Shepard normalisation (Eq. (10)): a shift l2* and
+// 1 / sum_m 2^(l2_jm - l2*), so that W_jm = 2^(l2_jm - l2*) / sum. Every
+// l2_jm <= 0 and a patch cell lies within a few widths of the initial
+// lattice, so the plain sum of 2^(l2_jm) stays far above the fp32 underflow
+// and l2* = 0 serves: one pass with one exp and one add per centre, two
+// cells per thread (t and t + blockDim.x) sharing each centre read. A cell
+// whose plain sum falls below 2^-100 takes a second pass with the running
+// maximum as the shift (the sum rescaled whenever the maximum grows).
 // --------------------------------------------------------------------------
+__device__ __noinline__ void stats_max_shift(const float4 *sc, int M, const float x[3], float *lmax_out,
+                                             float *sum_out) {
+    float lmax = -INFINITY, sum = 0.0f;
+    for (int m = 0; m < M; ++m) {
+        const float l = logit2(sc[m], x[0], x[1], x[2]);
+        if (l > lmax) {
+            sum = fmaf(sum, tc::ex2(lmax - l), 1.0f);
+            lmax = l;
+        } else {
+            sum += tc::ex2(l - lmax);
+        }
+    }
+    *lmax_out = lmax;
+    *sum_out = sum;
+}
+
+__device__ __forceinline__ void stats_store(const Ws &w, size_t o, const float4 *sc, int M, const float x[3],
+                                            float sum) {
+    float shift = 0.0f;
+    if (!(sum > 0x1p-100f)) stats_max_shift(sc, M, x, &shift, &sum);
+    w.rowmax[o] = shift;
+    w.rowinv[o] = 1.0f / sum;
+}
+
 __global__ void __launch_bounds__(128) k_stats_f32(Geo g, const int32_t *boxes,
                                                    const double *centres, const int32_t *info,
                                                    Ws w, int all) {
@@ -78,24 +107,21 @@ __global__ void __launch_bounds__(128) k_stats_f32(Geo g, const int32_t *boxes,
     const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
     for (int m = threadIdx.x; m < M; m += blockDim.x) sc[m] = local_centre(cg[m], o);
     __syncthreads();
-    const int t = blockIdx.x * blockDim.x + threadIdx.x;
-    if (t >= N) return;
-    float x[3];
-    local_cell(g, s, box, t, x);
-    // one pass with a running maximum: the sum is rescaled whenever the
-    // maximum grows (sum = sum 2^(old - new) + 1), else gains 2^(l - max)
-    float lmax = -INFINITY, sum = 0.0f;
+    const int t0 = blockIdx.x * 2 * blockDim.x + threadIdx.x, t1 = t0 + blockDim.x;
+    if (t0 >= N) return;
+    const bool two = t1 < N;
+    float x0[3], x1[3];
+    local_cell(g, s, box, t0, x0);
+    local_cell(g, s, box, two ? t1 : t0, x1);
+    float s0 = 0.0f, s1 = 0.0f;
     for (int m = 0; m < M; ++m) {
-        const float l = logit2(sc[m], x[0], x[1], x[2]);
-        if (l > lmax) {
-            sum = fmaf(sum, tc::ex2(lmax - l), 1.0f);
-            lmax = l;
-        } else {
-            sum += tc::ex2(l - lmax);
-        }
+        const float4 c = sc[m];
+        s0 += tc::ex2(logit2(c, x0[0], x0[1], x0[2]));
+        s1 += tc::ex2(logit2(c, x1[0], x1[1], x1[2]));
     }
-    w.rowmax[(size_t)s * g.n_max + t] = lmax;
-    w.rowinv[(size_t)s * g.n_max + t] = 1.0f / sum;
+    const size_t row = (size_t)s * g.n_max;
+    stats_store(w, row + t0, sc, M, x0, s0);
+    if (two) stats_store(w, row + t1, sc, M, x1, s1);
 }
 
 // --------------------------------------------------------------------------
@@ -493,7 +519,7 @@ void launch_stats_f32(const Geo &g, const int32_t *boxes, const double *centres,
     PhaseScope ps(kPhStats, st);
     size_t sm = (size_t)g.m_cap * sizeof(float4);
     cudaFuncSetAttribute(k_stats_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    dim3 grid((g.n_max + 127) / 128, g.S);
+    dim3 grid((g.n_max + 255) / 256, g.S);  // two cells per thread
     k_stats_f32<<<grid, 128, sm, st>>>(g, boxes, centres, info, w, all);
     count_launches(1);
 }
