@@ -157,6 +157,13 @@ typedef struct {
 /* Library version string (static storage). */
 const char *pam_version(void);
 
+/* Sizes in bytes of the ABI's structs as this library was compiled, for a
+ * binding to check its own layouts against: out[0..5] = sizeof pam_problem,
+ * pam_params, pam_plan, pam_model, pam_cells, pam_tuning (n >= 6; fewer are
+ * written when n is smaller). Host only; returns the number of sizes the
+ * library knows (6). */
+int pam_struct_sizes(size_t *out, int n);
+
 /* Human-readable name of a status (static storage). */
 const char *pam_status_string(pam_status s);
 

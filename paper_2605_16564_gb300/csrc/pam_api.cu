@@ -228,6 +228,13 @@ extern "C" {
 
 const char *pam_version(void) { return "libpam 0.1 (sm_103a)"; }
 
+int pam_struct_sizes(size_t *out, int n) {
+    const size_t sz[6] = {sizeof(pam_problem), sizeof(pam_params), sizeof(pam_plan),
+                          sizeof(pam_model),   sizeof(pam_cells),  sizeof(pam_tuning)};
+    for (int i = 0; out && i < n && i < 6; ++i) out[i] = sz[i];
+    return 6;
+}
+
 void pam_timing_enable(int on) { g_timing = on != 0; }
 
 long long pam_kernel_launches(void) { return g_launches.load(); }

@@ -92,6 +92,7 @@ def lib():
         L = C.CDLL(LIB_PATH)
         P = C.POINTER
         L.pam_version.restype = C.c_char_p
+        L.pam_struct_sizes.argtypes = [P(C.c_size_t), C.c_int]
         L.pam_status_string.restype = C.c_char_p
         L.pam_status_string.argtypes = [C.c_int]
         L.pam_plan_create.argtypes = [P(pam_problem), P(pam_params), P(pam_plan)]

@@ -326,3 +326,27 @@ def test_partition_cells_on_faces_matches_the_oracle(pam):
     assert np.bincount(cells, minlength=x.shape[0]).min() >= 1
     with pytest.raises(pam.PamError):
         pam.pam_partition_cells(pr, np.array([[0.5, np.nextafter(0.75, 1.0)]]))
+
+
+def test_binding_struct_layouts_match_the_library(pam):
+    # the ctypes structs of the binding against sizeof in the compiled library
+    import ctypes as C
+    out = (C.c_size_t * 6)()
+    assert pam.lib().pam_struct_sizes(out, 6) == 6
+    mine = [C.sizeof(t) for t in (pam.pam_problem, pam.pam_params, pam.pam_plan, pam.pam_model,
+                                  pam.pam_cells, pam.pam_tuning)]
+    assert list(out) == mine
+    # pam_params: 4 doubles, 8 ints, the warm-start event pointer
+    assert C.sizeof(pam.pam_params) == 4 * 8 + 8 * 4 + 8
+    assert pam.pam_params.warm_start_event.offset == 64
+
+
+def test_event_handles(pam):
+    class Ev:
+        def __init__(self, h):
+            self.cuda_event = h
+    assert pam._event_handle(None) is None
+    assert pam._event_handle(12345) == 12345
+    assert pam._event_handle(Ev(777)) == 777
+    with pytest.raises(ValueError):
+        pam._event_handle(Ev(0))
