@@ -172,7 +172,8 @@ def accounting(fit, Kd, levels, pam, seed=None):
       pairs       sum N_i M_i: Gaussians evaluated once per (cell, centre);
       chol_flops  sum iters * s^3 / 3 over the active-set steps (fp32 form);
       eval_pairs  filled in by the caller (points x their owner's M)."""
-    out = dict(gram_flops=0.0, pairs=0.0, chol_flops=0.0, solve_bytes=0.0, m_final=None)
+    out = dict(gram_flops=0.0, pairs=0.0, chol_flops=0.0, solve_bytes=0.0, m_final=None, solves=0,
+               steps=0.0, passes=0.0, support_last=None)
     fit_levels = [0] + [1] * levels
     for r, _ in enumerate(fit_levels):
         if r == 0:
@@ -202,6 +203,10 @@ def accounting(fit, Kd, levels, pam, seed=None):
         # pass reads the support block (s^2) and the support's rows (s M) of
         # the fp32 Gram (s = the final support, the step count of the solve)
         out["solve_bytes"] += float(np.sum((iters + passes) * (sup * sup + sup * m) * 4.0))
+        out["solves"] += int(np.count_nonzero(solved))
+        out["steps"] += float(np.sum(iters))
+        out["passes"] += float(np.sum(passes))
+        out["support_last"] = float(sup.mean()) if len(sup) else 0.0
     out["m_final"] = fit.model.info.cpu().numpy()[:, pam.INFO_M].astype(float)
     return out
 
@@ -242,7 +247,7 @@ def roofline_entries(phase_ms, work, n_pts, mixed, peaks, peak_src):
                      "unit": "TFLOP/s", "frac": ach / FP64_NOMINAL_TFLOPS, "traffic": None,
                      "peak_source": "nominal GB300 fp64 dense rate"}
     if t("stats"):
-        ach = work["pairs"] / t("stats")  # one pass with a running maximum
+        ach = work["pairs"] / t("stats")  # one pass of plain sums of 2^l
         r["stats"] = {"kernel": "k_stats_f32", "bound": "alu", "achieved": ach / 1e12,
                       "peak": SFU_EX2_PER_S / 1e12, "unit": "Texp/s", "frac": ach / SFU_EX2_PER_S,
                       "traffic": None, "peak_source": "SFU ex2 16/clk/SM x 152 SMs x 2.07 GHz"}
@@ -264,6 +269,14 @@ def roofline_entries(phase_ms, work, n_pts, mixed, peaks, peak_src):
                                      "x (s^2 + s M) x 4 bytes per subdomain and level (latency-bound: one CTA "
                                      "per subdomain, see the clock-counter split)",
                       "cholesky_tflops": chol, "cholesky_frac_of_fp32": chol / FP32_TFLOPS}
+        if work.get("solves"):
+            # sweeps per subdomain: the solve's active-set steps (one support
+            # factorisation each) and exact-gradient refinement passes, per
+            # (subdomain, level) solve
+            r["solve"]["solves_per_step"] = work["solves"]
+            r["solve"]["active_set_steps_per_solve"] = work["steps"] / work["solves"]
+            r["solve"]["refinement_passes_per_solve"] = work["passes"] / work["solves"]
+            r["solve"]["mean_support_last_level"] = work["support_last"]
     return r
 
 
