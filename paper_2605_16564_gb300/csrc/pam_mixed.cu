@@ -93,7 +93,7 @@ __device__ __forceinline__ void stats_store(const Ws &w, size_t o, const float4 
     w.rowinv[o] = 1.0f / sum;
 }
 
-__global__ void __launch_bounds__(128) k_stats_f32(Geo g, const int32_t *boxes,
+__global__ void __launch_bounds__(256) k_stats_f32(Geo g, const int32_t *boxes,
                                                    const double *centres, const int32_t *info,
                                                    Ws w, int all) {
     const int s = blockIdx.y;
@@ -519,8 +519,11 @@ void launch_stats_f32(const Geo &g, const int32_t *boxes, const double *centres,
     PhaseScope ps(kPhStats, st);
     size_t sm = (size_t)g.m_cap * sizeof(float4);
     cudaFuncSetAttribute(k_stats_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    dim3 grid((g.n_max + 255) / 256, g.S);  // two cells per thread
-    k_stats_f32<<<grid, 128, sm, st>>>(g, boxes, centres, info, w, all);
+    // two cells per thread, 512 per block: every block converts the M
+    // centres once (binary64 offsets on the narrow fp64 pipe), so fewer,
+    // larger blocks per subdomain spend less of their time on it
+    dim3 grid((g.n_max + 511) / 512, g.S);
+    k_stats_f32<<<grid, 256, sm, st>>>(g, boxes, centres, info, w, all);
     count_launches(1);
 }
 
