@@ -208,17 +208,13 @@ __global__ void k_eval_bucket_f64(Geo g, const double *centres, const double *be
 }
 
 // ---------------------------------------------------------------- fp32 ------
-// Per-centre constants of the fp32 evaluation in scaled local coordinates:
-// with s = sqrt(log2(e) / 2) / sigma the base-2 logit is -|s x - s c|^2, so
-// a centre is staged as (-s c_x, -s c_y, -s c_z, s) and a (point, centre)
-// pair costs three fma for s x - s c and three operations for the square.
 __device__ __forceinline__ float4 local_centre_e(const dvec4 &c, const double o[3]) {
-    const float s = 0.84932180f / (float)c.w;  // fp32 (no fp64 divide)
     float4 r;
-    r.x = -s * (float)(c.x - o[0]);
-    r.y = -s * (float)(c.y - o[1]);
-    r.z = -s * (float)(c.z - o[2]);
-    r.w = s;
+    r.x = (float)(c.x - o[0]);
+    r.y = (float)(c.y - o[1]);
+    r.z = (float)(c.z - o[2]);
+    const float sg = (float)c.w;  // fp32 alpha (no fp64 divide)
+    r.w = -1.44269504f / (2.f * sg * sg);
     return r;
 }
 
@@ -226,8 +222,8 @@ __device__ __forceinline__ float4 local_centre_e(const dvec4 &c, const double o[
 __device__ __forceinline__ double exp_f32(float v) { return (double)tc::ex2(v * 1.44269504f); }
 
 __device__ __forceinline__ float logit2_e(const float4 &c, float x, float y, float z) {
-    const float u = fmaf(c.w, x, c.x), v = fmaf(c.w, y, c.y), w = fmaf(c.w, z, c.z);
-    return fmaf(-w, w, fmaf(-v, v, -(u * u)));
+    float dx = x - c.x, dy = y - c.y, dz = z - c.z;
+    return c.w * fmaf(dz, dz, fmaf(dy, dy, dx * dx));
 }
 
 __device__ __forceinline__ float shepard_f32_smem(const float4 *sc, const float *sb, int M,
