@@ -245,6 +245,7 @@ static int cd_sweeps(int m, const double *G, const double *b, double lam1,
                      double tol)
 {
     int s;
+    (void)b; /* enters through g = b - G beta, which the caller forms */
     for (s = 0; s < max_sweeps; ++s) {
         double maxd = 0.0;
         for (int j = 0; j < m; ++j) {
