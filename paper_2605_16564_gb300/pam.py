@@ -650,6 +650,10 @@ class Fitter:
         beside the copies). Capturable in a CUDA graph."""
         import torch
         n = pts.shape[0]
+        if out.shape[0] < n or out_host.shape[0] < n:
+            raise ValueError(f"eval_to_host: {n} points, out holds {out.shape[0]}, out_host {out_host.shape[0]}")
+        if out_host.device.type != "cpu" or out_host.dtype != out.dtype:
+            raise ValueError("eval_to_host: out_host must be a host tensor of out's dtype (pinned for overlap)")
         cur = torch.cuda.current_stream()
         cs = copy_stream if copy_stream is not None else self._copy_stream()
         k = max(1, min(int(chunks), n)) if n > 0 else 0

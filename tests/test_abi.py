@@ -350,3 +350,15 @@ def test_event_handles(pam):
     assert pam._event_handle(Ev(777)) == 777
     with pytest.raises(ValueError):
         pam._event_handle(Ev(0))
+
+
+def test_eval_to_host_checks_its_buffers_before_any_launch(pam):
+    import torch
+    pts = torch.zeros((10, 2), dtype=torch.float64)
+    out = torch.zeros(10, dtype=torch.float64)
+    with pytest.raises(ValueError):
+        pam.Fitter.eval_to_host(None, pts, out[:9], torch.zeros(10, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        pam.Fitter.eval_to_host(None, pts, out, torch.zeros(9, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        pam.Fitter.eval_to_host(None, pts, out, torch.zeros(10, dtype=torch.float32))
