@@ -363,13 +363,16 @@ pam_status pam_errors(const pam_problem *prob, const pam_plan *plan,
  * that reserve all device memory in their own pool at start-up, or
  * real-time loops where an allocation's latency or failure is not
  * acceptable. It computes the same four measures into d_err (device
- * double [4]) as pam_errors with PAM_PREC_FP64, summing fixed chunks of
- * 4096 grid cells.
+ * double [4]) as pam_errors with PAM_PREC_FP64 and quad = 0: each cell is
+ * measured at its centroid (the Gauss-Legendre rule, quad = 1, is not
+ * offered here), summing fixed chunks of 4096 grid cells. It reads the
+ * dictionary from global memory per cell, so it is slower than pam_errors.
  * Scratch: a file-scope device array of 4096 x 8 doubles (256 KiB) that
  * every GPU loading the library holds until the process exits; grids of
  * more than 16,777,216 cells return PAM_ERR_UNSUPPORTED. The first call on
  * each device looks up the array's device address with that device
- * current; make that first call before any stream capture. Every call
+ * current (again after the device's context was replaced, e.g. by
+ * cudaDeviceReset); make that first call before any stream capture. Every call
  * writes all the partial sums it reads, so no state carries over, but all
  * calls share the one array: calls that overlap on the GPU (different
  * streams, or different host threads on one device) race and must be

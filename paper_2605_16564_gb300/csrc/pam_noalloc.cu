@@ -16,6 +16,8 @@
 #include <cmath>
 #include <mutex>
 
+#include <cuda.h>  // CUcontext and CUresult only; the call is resolved through the runtime
+
 #include "pam_internal.cuh"
 
 namespace pam {
@@ -30,43 +32,78 @@ constexpr int kNaMaxDevices = 128;
 static __device__ __align__(256) double g_err_scratch[kNaMaxBlocks * 8];
 
 std::mutex g_na_mu;
-double *g_na_addr[kNaMaxDevices] = {};
+struct NaSlot {
+    CUcontext ctx;
+    double *addr;
+};
+NaSlot g_na_slot[kNaMaxDevices] = {};
 
-// Device address of g_err_scratch on the current device, looked up once per
-// device (host code cannot use the array's name as a device address).
+// The current context of this thread (nullptr if none or unavailable):
+// cuCtxGetCurrent, resolved once through the runtime so that the library
+// needs no link against the driver library.
+CUcontext current_context() {
+    using Fn = CUresult (*)(CUcontext *);
+    static Fn fn = [] {
+        void *p = nullptr;
+        cudaDriverEntryPointQueryResult q{};
+        if (cudaGetDriverEntryPointByVersion("cuCtxGetCurrent", &p, 4000, cudaEnableDefault, &q) != cudaSuccess ||
+            q != cudaDriverEntryPointSuccess)
+            p = nullptr;
+        return reinterpret_cast<Fn>(p);
+    }();
+    CUcontext c = nullptr;
+    if (fn && fn(&c) != CUDA_SUCCESS) c = nullptr;
+    return c;
+}
+
+// Device address of g_err_scratch in the current context: host code cannot
+// use the array's name as a device address. Looked up once per device, with
+// that device current, and again only when the device's context is not the
+// one of the lookup (after cudaDeviceReset the module is loaded anew and the
+// old address is stale).
 cudaError_t scratch_address(double **out) {
     int dev = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e != cudaSuccess) return e;
     if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
     std::lock_guard<std::mutex> lk(g_na_mu);
-    if (!g_na_addr[dev]) {
+    NaSlot &sl = g_na_slot[dev];
+    const CUcontext ctx = current_context();
+    if (!sl.addr || !ctx || ctx != sl.ctx) {
         void *p = nullptr;
-        e = cudaGetSymbolAddress(&p, g_err_scratch);
+        e = cudaGetSymbolAddress(&p, g_err_scratch);  // makes the device's context current if needed
         if (e != cudaSuccess) return e;
-        g_na_addr[dev] = static_cast<double *>(p);
+        sl.addr = static_cast<double *>(p);
+        sl.ctx = current_context();
     }
-    *out = g_na_addr[dev];
+    *out = sl.addr;
     return cudaSuccess;
 }
 
 // sum_m beta_m w_m(x) over the dictionary of subdomain s (Shepard weights,
-// maximum logit subtracted first), binary64.
+// maximum logit subtracted first), binary64. Each logit is formed exactly
+// as pam_errors forms it from its staged dictionary, |x - c|^2 times the
+// factor -1 / (2 sigma^2), so the two differ only in the order of the sums;
+// the centres are read from global memory per cell (no shared-memory
+// staging: a block's 4096 cells may span several subdomains), which makes
+// this path several times slower than pam_errors on large dictionaries.
 __device__ double na_shepard_value(const Geo &g, const double *centres, const double *beta, int s,
                                    int M, const double x[3]) {
     const dvec4 *cs = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
     const double *bs = beta + (size_t)s * g.m_cap;
     double lmax = -INFINITY;
     for (int m = 0; m < M; ++m) {
-        dvec4 c = cs[m];
-        double d0 = x[0] - c.x, d1 = x[1] - c.y, d2 = x[2] - c.z;
-        lmax = fmax(lmax, -(d0 * d0 + d1 * d1 + d2 * d2) / (2.0 * c.w * c.w));
+        const dvec4 c = cs[m];
+        const double f = -1.0 / (2.0 * c.w * c.w);
+        const double d0 = x[0] - c.x, d1 = x[1] - c.y, d2 = x[2] - c.z;
+        lmax = fmax(lmax, (d0 * d0 + d1 * d1 + d2 * d2) * f);
     }
     double num = 0.0, den = 0.0;
     for (int m = 0; m < M; ++m) {
-        dvec4 c = cs[m];
-        double d0 = x[0] - c.x, d1 = x[1] - c.y, d2 = x[2] - c.z;
-        double e = exp(-(d0 * d0 + d1 * d1 + d2 * d2) / (2.0 * c.w * c.w) - lmax);
+        const dvec4 c = cs[m];
+        const double f = -1.0 / (2.0 * c.w * c.w);
+        const double d0 = x[0] - c.x, d1 = x[1] - c.y, d2 = x[2] - c.z;
+        const double e = exp((d0 * d0 + d1 * d1 + d2 * d2) * f - lmax);
         num += bs[m] * e;
         den += e;
     }

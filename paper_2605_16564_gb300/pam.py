@@ -652,6 +652,9 @@ class Fitter:
         n = pts.shape[0]
         if out.shape[0] < n or out_host.shape[0] < n:
             raise ValueError(f"eval_to_host: {n} points, out holds {out.shape[0]}, out_host {out_host.shape[0]}")
+        if not out.is_cuda or out.device != torch.device(self.device) or out.dtype != torch.float64:
+            raise ValueError("eval_to_host: out must be a float64 tensor on the fitter's device (pam_eval writes "
+                             "binary64 values there)")
         if out_host.device.type != "cpu" or out_host.dtype != out.dtype:
             raise ValueError("eval_to_host: out_host must be a host tensor of out's dtype (pinned for overlap)")
         cur = torch.cuda.current_stream()
@@ -668,6 +671,8 @@ class Fitter:
                 out_host[a:b].copy_(out[a:b], non_blocking=True)
         if join:
             cur.wait_stream(cs)
+        else:
+            out.record_stream(cs)  # out stays allocated until the copies on cs have run
         return out_host
 
     def _copy_stream(self):

@@ -362,3 +362,9 @@ def test_eval_to_host_checks_its_buffers_before_any_launch(pam):
         pam.Fitter.eval_to_host(None, pts, out, torch.zeros(9, dtype=torch.float64))
     with pytest.raises(ValueError):
         pam.Fitter.eval_to_host(None, pts, out, torch.zeros(10, dtype=torch.float32))
+    # pam_eval writes binary64 values on the fitter's device: a host or
+    # float32 `out` is refused before anything is enqueued
+    with pytest.raises(ValueError):
+        pam.Fitter.eval_to_host(None, pts, out, torch.zeros(10, dtype=torch.float64))
+    with pytest.raises(ValueError):
+        pam.Fitter.eval_to_host(None, pts, out.float(), torch.zeros(10, dtype=torch.float32))

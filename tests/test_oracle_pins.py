@@ -594,3 +594,47 @@ def test_results_do_not_depend_on_the_thread_count():
     for key in ("M", "c", "beta", "info"):
         np.testing.assert_array_equal(a[key], b[key])
     np.testing.assert_array_equal(ea, oracle.evaluate(b, pts))
+
+
+@pytest.mark.parametrize("quad", [0, 1])
+def test_error_measures_of_piecewise_constant_surrogates_in_closed_form(quad):
+    # A surrogate with every coefficient of subdomain s equal to c_s is ln K* = c_s
+    # on s's core (Shepard weights sum to one), whatever the centres. On a
+    # hand-built K the four measures of the error reduction then have closed
+    # forms over the cells each core owns: L1 = sum|K - e^c| / sum|K|,
+    # L2 = sqrt(sum (K - e^c)^2 / sum K^2), the log-L1 = sum|ln K - c| / sum|ln K|
+    # and the maximum of |ln K - c| / ln 10 over all cells. Every node of the
+    # Gauss-Legendre rule sees the same constant, so quad = 1 gives the same
+    # values. A dropped /ln 10, a maximum over one subdomain's cells only, or the
+    # log-L1 normalised by sum|K| fails here.
+    n_cells, n_sub = (12, 10), (3, 2)
+    rng = np.random.default_rng(99)
+    K = 10.0 ** rng.choice([-2.0, -0.5, 0.0, 1.0, 3.0], size=n_cells[::-1])  # K[j, i]
+    boxes = oracle.partition(n_cells, n_sub, 0)
+    S, m_cap = boxes.shape[0], 5
+    c_s = np.log(np.array([0.3, 2.0, 7.0, 0.05, 40.0, 1.0]))
+    cen = np.zeros((S, m_cap, 4))
+    beta = np.zeros((S, m_cap))
+    M = np.full(S, m_cap, dtype=np.int32)
+    for s in range(S):
+        cen[s, :, 0] = rng.uniform(0, 1, m_cap)
+        cen[s, :, 1] = rng.uniform(0, 10 / 12, m_cap)
+        cen[s, :, 3] = rng.uniform(0.05, 0.3, m_cap)
+        beta[s, :] = c_s[s]
+    model = dict(boxes=boxes, M=M, c=cen, beta=beta, m_cap=m_cap, n_cells=n_cells, n_sub=n_sub)
+    lnKs = np.zeros(n_cells[::-1])
+    for s in range(S):
+        i0, j0, _, i1, j1, _ = boxes[s, :6]  # core box lo/hi (x, y, z)
+        lnKs[j0:j1, i0:i1] = c_s[s]
+    Ks = np.exp(lnKs)
+    lk = np.log(K)
+    want = dict(l1=np.abs(K - Ks).sum() / np.abs(K).sum(),
+                l2=np.sqrt(((K - Ks) ** 2).sum() / (K ** 2).sum()),
+                l1_log=np.abs(lk - lnKs).sum() / np.abs(lk).sum(),
+                max_log10=np.abs(lk - lnKs).max() / np.log(10.0))
+    got = oracle.errors(model, K, quad=quad)
+    for key, v in want.items():
+        assert got[key] == pytest.approx(v, rel=1e-13, abs=0), key
+    # the maximum sits in one subdomain: it is not the first one's
+    owner_max = np.unravel_index(np.argmax(np.abs(lk - lnKs)), lk.shape)
+    assert not (owner_max[0] < boxes[0, 4] and owner_max[1] < boxes[0, 3])

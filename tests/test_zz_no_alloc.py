@@ -4,20 +4,23 @@ Some host programs (a simulator that reserves the whole GPU memory in its own
 pool, a real-time loop that cannot afford an allocation) can hand the
 library their inputs and outputs but no scratch space. This entry point
 keeps its scratch in a fixed array inside the library; its results must
-agree with pam_errors, which takes a caller workspace, on consecutive calls.
-This file is collected last so that a failure here comes after every other
-test has run; it passes alone in a fresh process too.
+agree with pam_errors (midpoint rule, quad = 0), which takes a caller
+workspace, on consecutive calls, and with the FP64 oracle's error reduction
+of the same coefficients. This file is collected last so that a failure here
+comes after every other test has run; it passes alone in a fresh process too.
 """
 import ctypes as C
 
 import numpy as np
 import pytest
 
+import oracle
 from paper_2605_16564_gb300 import fields
 
 pytestmark = pytest.mark.gpu
 
-RTOL = 1e-12  # different summation order than pam_errors, same fp64 arithmetic
+RTOL = 1e-12  # different summation order than pam_errors, the same logits and exps
+RTOL_ORACLE = 1e-10  # the oracle: host exp/log and another summation order
 
 
 @pytest.fixture(scope="module")
@@ -47,7 +50,9 @@ def test_noalloc_errors_match_the_workspace_version_on_consecutive_calls(env):
     for K, n_cells, n_sub, overlap, g in cases:
         fit, Kd = _fitted(torch, pam, dev, K, n_cells, n_sub, overlap, g, k_top=8, levels=2)
         ref = torch.zeros(4, dtype=torch.float64, device=dev)
-        pam.pam_errors(fit.problem, fit.plan, fit.model, Kd, ref, fit.workspace, pam.PAM_PREC_FP64)
+        pam.pam_errors(fit.problem, fit.plan, fit.model, Kd, ref, fit.workspace, pam.PAM_PREC_FP64, quad=0)
+        orc = oracle.errors(fit.host_model(), K, quad=0)
+        want = np.array([orc["l1"], orc["l2"], orc["l1_log"], orc["max_log10"]])
         outs = []
         for _ in range(2):  # two calls in a row share the library's scratch array
             out = torch.full((4,), float("nan"), dtype=torch.float64, device=dev)
@@ -56,6 +61,7 @@ def test_noalloc_errors_match_the_workspace_version_on_consecutive_calls(env):
         r = ref.cpu().numpy()
         for o in outs:
             np.testing.assert_allclose(o, r, rtol=RTOL, atol=0)
+            np.testing.assert_allclose(o, want, rtol=RTOL_ORACLE, atol=0)
         np.testing.assert_array_equal(outs[0], outs[1])
 
 
