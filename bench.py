@@ -302,6 +302,24 @@ def workload_data(W, seed):
     return K, None, None
 
 
+def dictionary_agreement(pam, mixed, plain):
+    """Where the mixed form's refinement took other decisions than the plain
+    binary64 form's (which meets the oracle's to 1e-9): the fraction of
+    subdomains whose final dictionary differs (fp32 rounding moved a marking
+    decision), and how many of the mixed form's last solves fell back to
+    binary64 or stayed uncertified."""
+    S = len(plain["M"])
+    differ = 0
+    for s in range(S):
+        m = int(plain["M"][s])
+        if int(mixed["M"][s]) != m or not np.array_equal(mixed["c"][s, :m], plain["c"][s, :m]):
+            differ += 1
+    flags = mixed["info"][:, pam.INFO_FLAGS]
+    return {"subdomains": S, "dictionaries_differing": differ, "fraction_differing": differ / max(S, 1),
+            "mixed_solves_fallen_back_to_fp64": int(np.count_nonzero(flags & pam.FLAG_REFINE_DIVERGED)),
+            "mixed_solves_uncertified": int(np.count_nonzero(flags & pam.FLAG_NOT_CERTIFIED))}
+
+
 def make_fitter(pam, W, x, vol, dev, **params):
     if x is not None:
         return pam.CellFitter(W["shape"], W["n_sub"], W["overlap"], W["g"], x, vol, device=dev, **params)
@@ -428,7 +446,7 @@ def run_pam(args, rank, ws):
         choice, ms = fit.autotune(Kd, ptsd)
         names = ["gram_stages=3", "gram_stages=2", "factor_kb=builtin", "factor_kb=64", "factor_kb=48",
                  "factor_kb=32", "factor_kb=24", "factor_kb=16", "eval_block=128", "eval_block=256",
-                 "eval_block=512", "eval_block=1024"]
+                 "eval_block=512", "eval_block=1024", "solve_persistent=0", "solve_persistent=1"]
         tune = {"chosen": choice, "median_ms": {n: round(float(v), 4) for n, v in zip(names, ms) if v >= 0}}
         for _ in range(2):
             step()
@@ -611,6 +629,7 @@ def run_pam(args, rank, ws):
         plain = {"ms_per_step": pms, "cells_per_s": n_cells / (pms / 1e3), "l1": perr["l1"],
                  "speedup_chosen_over_plain": pms / step_ms,
                  "l1_ratio_chosen_over_plain": err["l1"] / perr["l1"]}
+        plain.update(dictionary_agreement(pam, fit.host_model(), pf.host_model()))
         del pf
 
     # --- per-subdomain lambda choice by k-fold cross-validation -------------

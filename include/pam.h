@@ -79,7 +79,13 @@ enum {
 enum {
     PAM_FLAG_NOT_CERTIFIED = 1, /* the last solve did not pass the optimality check */
     PAM_FLAG_CHOLESKY = 2,      /* a non-positive pivot (never expected: lambda2 > 0) */
-    PAM_FLAG_REFINE_DIVERGED = 4/* mixed form: refinement stalled; solved in fp64 instead */
+    PAM_FLAG_REFINE_DIVERGED = 4/* mixed form: the fp32 solve of this subdomain did not pass the
+                                   optimality check and the subdomain was solved again in binary64
+                                   (assembly, Gram and active-set solve of the plain form, so it
+                                   meets the plain form's certificate; NOT_CERTIFIED and CHOLESKY
+                                   then describe that solve). At most 32 subdomains per mixed solve
+                                   take this path; any others keep NOT_CERTIFIED. The cross-
+                                   validation fold solves of pam_lambda_cv never do (its refit does). */
 };
 
 /* The problem: grid, decomposition and initial dictionary (section 2 Step 1;
@@ -139,7 +145,9 @@ typedef struct {
     int m0;                  /* initial dictionary size prod g_init */
     int m_cap;               /* dictionary capacity per subdomain (<= PAM_MAX_M) */
     int64_t n_grid_cells;
-    size_t workspace_bytes;  /* device scratch the fit/refine/error calls need */
+    size_t workspace_bytes;  /* device scratch the fit/refine/error calls need; in the mixed
+                                form it includes the binary64 fallback's min(S, 32) slots
+                                (E, G and factor of one subdomain each) */
 } pam_plan;
 
 /* Device model, caller-owned (sizes from pam_plan):
@@ -270,8 +278,10 @@ pam_status pam_refine(const pam_problem *prob, const pam_params *par,
  * inspection: PAM_PREC_FP64 forms it in binary64; PAM_PREC_MIXED on the
  * tensor cores (W split into bf16 hi + lo, three products, fp32
  * accumulation; about 2^-16 relative per entry). Needs a model set up by
- * pam_fit_subdomains. Synchronises `stream` once; PAM_ERR_TIMEOUT if the
- * tensor-core pipeline stalled (no result then).
+ * pam_fit_subdomains. The workspace of a plan of either precision serves
+ * (no solve runs, so the mixed form's fallback slots are not needed).
+ * Synchronises `stream` once; PAM_ERR_TIMEOUT if the tensor-core pipeline
+ * stalled (no result then).
  */
 pam_status pam_gram(const pam_problem *prob, const pam_params *par, const pam_plan *plan,
                     const double *d_K, const pam_model *model, double *d_G, double *d_b,
@@ -542,7 +552,7 @@ pam_status pam_nn_adamw(float *d_params, const float *d_grads, float *d_m, float
 
 /*
  * Launch tuning and the autotuner (tile and launch shapes; no counterpart in
- * the paper). Three process-wide choices change the speed of the kernels
+ * the paper). Four process-wide choices change the speed of the kernels
  * but not their results:
  *   factor_kb    shared-memory budget (KiB) of the mixed solve's packed
  *                support factor; larger supports keep their factor in global
@@ -552,6 +562,10 @@ pam_status pam_nn_adamw(float *d_params, const float *d_grads, float *d_m, float
  *                shared memory allows)
  *   eval_block   threads per block of the evaluation kernels, 128, 256, 512
  *                or 1024 (0: 256)
+ *   solve_persistent  the mixed solve's launch: 0 one CTA per subdomain in
+ *                longest-first order (the built-in), 1 one CTA per resident
+ *                slot (two per SM), each taking the next subdomain of the
+ *                same order from a device counter until none is left
  * pam_tuning_set (NULL: all built-in) applies to every later launch of the
  * process; it is not synchronised with launches in flight on other threads.
  * pam_autotune measures, on a fitted model (after pam_fit_subdomains /
@@ -562,17 +576,19 @@ pam_status pam_nn_adamw(float *d_params, const float *d_grads, float *d_m, float
  * coefficients (the same minimiser: the coefficients are re-solved, as by
  * pam_resume, and the indicators rewritten), then the block sizes on
  * pam_eval of d_pts [n_pts][dim] into d_out [n_pts] (skipped when n_pts ==
- * 0; d_eval_workspace as for pam_eval). The binary64 form tunes the
- * evaluation only. The fastest candidates become the process tuning and
- * *out; h_ms (optional, [12]) receives the medians in ms in that order
- * (stages 3, 2; budgets; blocks), -1 where a candidate was not run.
+ * 0; d_eval_workspace as for pam_eval), then the solve's launch {0, 1}. The
+ * binary64 form tunes the evaluation only. The fastest candidates become
+ * the process tuning and *out; h_ms (optional, [14]) receives the medians in
+ * ms in that order (stages 3, 2; budgets; blocks; launches), -1 where a
+ * candidate was not run.
  * Synchronises `stream`; not to be captured in a CUDA graph.
  */
 typedef struct {
     int factor_kb;
     int gram_stages;
     int eval_block;
-    int reserved[5];
+    int solve_persistent;
+    int reserved[4];
 } pam_tuning;
 pam_status pam_tuning_set(const pam_tuning *t);
 pam_status pam_tuning_get(pam_tuning *t);

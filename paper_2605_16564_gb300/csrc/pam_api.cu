@@ -126,6 +126,7 @@ static size_t carve(const Geo &g, char *base, Ws *w) {
     w->rowmax = (float *)take(S * nm * sizeof(float));
     w->rowinv = (float *)take(S * nm * sizeof(float));
     w->b = (double *)take(S * mc * sizeof(double));
+    w->wsum = (float *)take(S * mc * sizeof(float));
     w->cost = (uint32_t *)take(S * sizeof(uint32_t));
     w->order = (int32_t *)take(S * sizeof(int32_t));
     // large regions: the fp64 form needs E, G and fp64 factors; the mixed
@@ -137,6 +138,14 @@ static size_t carve(const Geo &g, char *base, Ws *w) {
     w->Gf = (float *)w->G;
     w->E = f64 ? (double *)take(S * mc * nm * sizeof(double)) : nullptr;
     w->cxv = g.cells ? (double4_32a *)take(S * nm * sizeof(double4_32a)) : nullptr;
+    // the mixed form's binary64 fallback: a list and min(S, kFbSlots) slots
+    w->bytes_no_fb = off;
+    const size_t F = f64 ? 0 : (S < (size_t)kFbSlots ? S : (size_t)kFbSlots);
+    w->fb_slots = (int)F;
+    w->fb = F ? (int32_t *)take((2 + F) * sizeof(int32_t)) : nullptr;
+    w->fbE = F ? (double *)take(F * mc * nm * sizeof(double)) : nullptr;
+    w->fbG = F ? (double *)take(F * mc * mc * sizeof(double)) : nullptr;
+    w->fbL = F ? (double *)take(F * (mc * (mc + 1) / 2) * sizeof(double)) : nullptr;
     w->bytes = off;
     return off;
 }
@@ -190,7 +199,7 @@ Ws carve_workspace(const Geo &g, void *base) {
 }  // namespace pam
 
 namespace pam {
-static pam_tuning g_tuning = {0, 0, 0, {0, 0, 0, 0, 0}};  // factor_kb, gram_stages, eval_block
+static pam_tuning g_tuning = {0, 0, 0, 0, {0, 0, 0, 0}};  // factor_kb, gram_stages, eval_block, persistent
 const pam_tuning &tuning() { return g_tuning; }
 
 // Median of three timed runs of `body` (after one untimed run) on `st`, ms.
@@ -500,7 +509,7 @@ pam_status pam_gram(const pam_problem *prob, const pam_params *par, const pam_pl
     if (par->precision == PAM_PREC_MIXED && g.m_cap > kMixedMaxM) return PAM_ERR_UNSUPPORTED;
     if (!d_K || !model_ok(model) || !d_G || !d_b || !d_workspace) return PAM_ERR_INVALID_ARG;
     Ws w = carve_workspace(g, d_workspace);
-    if (workspace_bytes < w.bytes) return PAM_ERR_WORKSPACE;
+    if (workspace_bytes < w.bytes_no_fb) return PAM_ERR_WORKSPACE;  // no solve: the fallback slots are not used
     cudaStream_t s = (cudaStream_t)stream;
     PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 8 * sizeof(int32_t), s));
     launch_prepare(g, model->boxes, d_K, w, s);
@@ -989,6 +998,7 @@ pam_status pam_tuning_set(const pam_tuning *t) {
         t->eval_block != 1024)
         return PAM_ERR_INVALID_ARG;
     if (t->gram_stages != 0 && t->gram_stages != 2 && t->gram_stages != 3) return PAM_ERR_INVALID_ARG;
+    if (t->solve_persistent != 0 && t->solve_persistent != 1) return PAM_ERR_INVALID_ARG;
     g_tuning = *t;
     return PAM_OK;
 }
@@ -1006,7 +1016,7 @@ static pam_status autotune_run(Geo g, const Par &p, const pam_params *par, pam_m
     const bool mixed = par->precision == PAM_PREC_MIXED;
     if (mixed && (g.m_cap > kMixedMaxM || !mixed_solve_fits(g))) return PAM_ERR_UNSUPPORTED;
     if (h_ms)
-        for (int i = 0; i < 12; ++i) h_ms[i] = -1.0;
+        for (int i = 0; i < 14; ++i) h_ms[i] = -1.0;
     const pam_tuning keep = g_tuning;
     pam_tuning best = g_tuning;
     double t;
@@ -1032,7 +1042,7 @@ static pam_status autotune_run(Geo g, const Par &p, const pam_params *par, pam_m
             if (!mixed_solve_fits(g)) continue;
             if ((st = time_median(s, [&] {
                      launch_solve_mixed(g, p, model->boxes, model->centres, model->beta, model->info, w, nullptr, 1,
-                                        nullptr, 0, s);
+                                        nullptr, 0, s, 1);
                  }, &t)) != PAM_OK) { g_tuning = keep; return st; }
             if (h_ms) h_ms[2 + i] = t;
             if (t < bt) { bt = t; best.factor_kb = fkb[i]; }
@@ -1051,6 +1061,20 @@ static pam_status autotune_run(Geo g, const Par &p, const pam_params *par, pam_m
                  }, &t)) != PAM_OK) { g_tuning = keep; return st; }
             if (h_ms) h_ms[8 + i] = t;
             if (t < bt) { bt = t; best.eval_block = eb[i]; }
+        }
+    }
+    if (mixed) {
+        // the solve's launch: one CTA per subdomain, or resident CTAs taking
+        // subdomains from a counter (same order, same results)
+        double bt = INFINITY;
+        for (int i = 0; i < 2; ++i) {
+            g_tuning.solve_persistent = i;
+            if ((st = time_median(s, [&] {
+                     launch_solve_mixed(g, p, model->boxes, model->centres, model->beta, model->info, w, nullptr, 1,
+                                        nullptr, 0, s, 1);
+                 }, &t)) != PAM_OK) { g_tuning = keep; return st; }
+            if (h_ms) h_ms[12 + i] = t;
+            if (t < bt) { bt = t; best.solve_persistent = i; }
         }
     }
     g_tuning = best;

@@ -115,7 +115,7 @@ void launch_lambda_cv(const Geo &g, const Par &p, int precision, const int32_t *
             k_cv_scratch<<<(unsigned)((nb + 255) / 256), 256, 0, st>>>(nb, beta, beta_s, ni, info, info_s);
             count_launches(1);
             if (mixed) {
-                launch_solve_mixed(g, pf, boxes, centres, beta_s, info_s, w, nullptr, 1, cv + q, grid.n, st);
+                launch_solve_mixed(g, pf, boxes, centres, beta_s, info_s, w, nullptr, 1, cv + q, grid.n, st, 0);
             } else {
                 launch_solve_f64(g, pf, beta_s, info_s, w, nullptr, 1, st);
                 k_cv_heldout<<<(unsigned)S, 256, 0, st>>>(g, folds, f, beta_s, info_s, w, cv, grid.n, q);
@@ -128,7 +128,7 @@ void launch_lambda_cv(const Geo &g, const Par &p, int precision, const int32_t *
     // refit on all cells with each subdomain's chosen pair
     if (mixed) {
         launch_gram_tc(g, boxes, centres, info, w, st, 1, 0, 0);
-        launch_solve_mixed(g, p, boxes, centres, beta, info, w, lam_tab, 1, nullptr, 0, st);
+        launch_solve_mixed(g, p, boxes, centres, beta, info, w, lam_tab, 1, nullptr, 0, st, 1);
     } else {
         launch_bgram_f64(g, info, w, st, 1, 0, 0);
         launch_solve_f64(g, p, beta, info, w, lam_tab, 1, st);

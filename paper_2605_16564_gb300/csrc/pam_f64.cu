@@ -183,15 +183,28 @@ void launch_init_dictionary(const Geo &g, const int32_t *boxes, double *centres,
     count_launches(1);
 }
 
+// The slot loop of a kernel that serves both the per-subdomain launch (fb
+// null: block row = subdomain = slot, one pass) and the binary64 fallback (fb:
+// the listed subdomains; block row `row` of `rows` takes slots row, row +
+// rows, ..., so that a launch of a few rows costs next to nothing when the
+// list is empty). Items are separated by a barrier: an item's shared-memory
+// staging must not overtake the previous item's readers.
+template <class F>
+__device__ __forceinline__ void for_each_slot(const int32_t *fb, int slots, int row, int rows, F body) {
+    const int n = fb ? min(fb[0], slots) : rows;
+    for (int slot = row; slot < n; slot += rows) {
+        if (slot != row) __syncthreads();
+        body(slot, fb ? fb[2 + slot] : slot);
+    }
+}
+
 // --------------------------------------------------------------------------
 // Assembly, Eq. (6) and (10): E_jm = exp(l_jm - l_j*), inv_s_j = 1 / sum_m E_jm,
 // so that W_jm = E_jm inv_s_j; l_jm = -|x_j - c_m|^2 / (2 sigma_m^2).
 // One thread per patch cell, the dictionary staged in shared memory.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_assemble_f64(Geo g, const int32_t *boxes,
-                                                      const double *centres, const int32_t *info,
-                                                      Ws w, int all) {
-    int s = blockIdx.y;
+__device__ __forceinline__ void assemble_item(const Geo &g, const int32_t *boxes, const double *centres,
+                                              const int32_t *info, const Ws &w, int all, int slot, int s) {
     const int32_t *inf = info + s * kInfoN;
     if (!all && inf[PAM_INFO_STOPPED]) return;
     int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
@@ -215,7 +228,7 @@ __global__ void __launch_bounds__(128) k_assemble_f64(Geo g, const int32_t *boxe
         lmax = fmax(lmax, l);
     }
     double sum = 0.0;
-    double *E = w.E + (size_t)s * g.m_cap * g.n_max + t;
+    double *E = w.E + (size_t)slot * g.m_cap * g.n_max + t;
     for (int m = 0; m < M; ++m) {
         dvec4 c = sc[m];
         double d0 = x[0] - c.x, d1 = x[1] - c.y, d2 = x[2] - c.z;
@@ -226,6 +239,15 @@ __global__ void __launch_bounds__(128) k_assemble_f64(Geo g, const int32_t *boxe
     w.inv_s[(size_t)s * g.n_max + t] = 1.0 / sum;
 }
 
+// fb (optional): a fallback list; block row y takes its slots y, y + gridDim.y, ...
+// (E indexed by slot).
+__global__ void __launch_bounds__(128) k_assemble_f64(Geo g, const int32_t *boxes,
+                                                      const double *centres, const int32_t *info,
+                                                      Ws w, int all, const int32_t *fb) {
+    for_each_slot(fb, w.fb_slots, blockIdx.y, gridDim.y,
+                  [&](int slot, int s) { assemble_item(g, boxes, centres, info, w, all, slot, s); });
+}
+
 // Row mask of the cross-validation folds: with folds > 0 only the cells t
 // with t mod folds != fold enter G and b (the training rows of that fold).
 __device__ __forceinline__ bool cv_keep(int t, int folds, int fold) {
@@ -233,15 +255,15 @@ __device__ __forceinline__ bool cv_keep(int t, int folds, int fold) {
 }
 
 // b_m = sum_j W_jm y_j, one warp per (subdomain, centre).
-__global__ void k_bvec_f64(Geo g, const int32_t *info, Ws w, int all, int folds, int fold) {
-    int s = blockIdx.y;
+__device__ __forceinline__ void bvec_item(const Geo &g, const int32_t *info, const Ws &w, int all, int folds,
+                                          int fold, int slot, int s) {
     const int32_t *inf = info + s * kInfoN;
     if (!all && inf[PAM_INFO_STOPPED]) return;
     int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
     int m = blockIdx.x * (blockDim.x / 32) + threadIdx.x / 32;
     int lane = threadIdx.x & 31;
     if (m >= M) return;
-    const double *E = w.E + ((size_t)s * g.m_cap + m) * g.n_max;
+    const double *E = w.E + ((size_t)slot * g.m_cap + m) * g.n_max;
     const double *iv = w.inv_s + (size_t)s * g.n_max;
     const double *y = w.y + (size_t)s * g.n_max;
     double acc = 0.0;
@@ -251,11 +273,16 @@ __global__ void k_bvec_f64(Geo g, const int32_t *info, Ws w, int all, int folds,
     if (lane == 0) w.b[(size_t)s * g.m_cap + m] = acc;
 }
 
+__global__ void k_bvec_f64(Geo g, const int32_t *info, Ws w, int all, int folds, int fold,
+                           const int32_t *fb) {
+    for_each_slot(fb, w.fb_slots, blockIdx.y, gridDim.y,
+                  [&](int slot, int s) { bvec_item(g, info, w, all, folds, fold, slot, s); });
+}
+
 // G = W^T W on 64 x 64 tiles of the upper triangle, mirrored; fp64 FMA.
 constexpr int kGT = 64, kGK = 16;
-__global__ void __launch_bounds__(256) k_gram_f64(Geo g, const int32_t *info, Ws w, int all, int folds,
-                                                  int fold) {
-    int s = blockIdx.y;
+__device__ __forceinline__ void gram_item(const Geo &g, const int32_t *info, const Ws &w, int all, int folds,
+                                          int fold, int slot, int s) {
     const int32_t *inf = info + s * kInfoN;
     if (!all && inf[PAM_INFO_STOPPED]) return;
     int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
@@ -266,7 +293,7 @@ __global__ void __launch_bounds__(256) k_gram_f64(Geo g, const int32_t *info, Ws
     int I0 = ti * kGT, J0 = tj * kGT;
     if (I0 >= M || J0 >= M) return;
     __shared__ double As[kGK][kGT + 1], Bs[kGK][kGT + 1];
-    const double *E = w.E + (size_t)s * g.m_cap * g.n_max;
+    const double *E = w.E + (size_t)slot * g.m_cap * g.n_max;
     const double *iv = w.inv_s + (size_t)s * g.n_max;
     int tid = threadIdx.x, ty = tid / 16, tx = tid % 16;
     double acc[4][4] = {};
@@ -292,7 +319,7 @@ __global__ void __launch_bounds__(256) k_gram_f64(Geo g, const int32_t *info, Ws
         }
         __syncthreads();
     }
-    double *G = w.G + (size_t)s * g.m_cap * g.m_cap;
+    double *G = w.G + (size_t)slot * g.m_cap * g.m_cap;
     for (int i = 0; i < 4; ++i)
         for (int j = 0; j < 4; ++j) {
             int r = I0 + ty + 16 * i, c = J0 + tx + 16 * j;
@@ -301,6 +328,12 @@ __global__ void __launch_bounds__(256) k_gram_f64(Geo g, const int32_t *info, Ws
                 G[(size_t)c * g.m_cap + r] = acc[i][j];
             }
         }
+}
+
+__global__ void __launch_bounds__(256) k_gram_f64(Geo g, const int32_t *info, Ws w, int all, int folds,
+                                                  int fold, const int32_t *fb) {
+    for_each_slot(fb, w.fb_slots, blockIdx.y, gridDim.y,
+                  [&](int slot, int s) { gram_item(g, info, w, all, folds, fold, slot, s); });
 }
 
 // --------------------------------------------------------------------------
@@ -393,10 +426,8 @@ __device__ void cholesky_solve_packed(const double *A, int s, double *r) {
 // of p's; all: solve also the subdomains whose refinement has stopped. With
 // p.cv_folds > 0 the system is that of the training rows of fold p.cv_fold
 // and lambda_k = N_train lambda_k_hat.
-__global__ void __launch_bounds__(kSolveThreads) k_solve_f64(Geo g, Par p, double *beta,
-                                                             int32_t *info, Ws w, const double *lam_tab,
-                                                             int all) {
-    const int s = blockIdx.x;
+__device__ __forceinline__ void solve_item(const Geo &g, const Par &p, double *beta, int32_t *info, const Ws &w,
+                                           const double *lam_tab, int all, int slot, int s) {
     int32_t *inf = info + s * kInfoN;
     if (!all && inf[PAM_INFO_STOPPED]) return;
     const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS], mc = g.m_cap;
@@ -416,7 +447,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_f64(Geo g, Par p, doubl
     __shared__ SolveShared sh;
     __shared__ double inv_piv;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    const double *G = w.G + (size_t)s * mc * mc;
+    const double *G = w.G + (size_t)slot * mc * mc;
     const size_t smem_factor_elems = kFactorSmemBytes / sizeof(double);
 
     for (int j = tid; j < mc; j += blockDim.x) {
@@ -442,7 +473,7 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_f64(Geo g, Par p, doubl
     for (; it < p.max_iters; ++it) {
         compact_active(sg, M, idx, &sh.cnt);
         scnt = sh.cnt;
-        A = (tri(scnt, 0) <= smem_factor_elems) ? Asm : w.L + (size_t)s * ((size_t)mc * (mc + 1) / 2);
+        A = (tri(scnt, 0) <= smem_factor_elems) ? Asm : w.L + (size_t)slot * ((size_t)mc * (mc + 1) / 2);
         // A = G_SS + lambda2 I (packed lower), rhs = b_S - lambda1 s_S
         for (int pp = warp; pp < scnt; pp += nw) {
             const double *Gr = G + (size_t)idx[pp] * mc;
@@ -547,6 +578,13 @@ __global__ void __launch_bounds__(kSolveThreads) k_solve_f64(Geo g, Par p, doubl
     }
 }
 
+__global__ void __launch_bounds__(kSolveThreads) k_solve_f64(Geo g, Par p, double *beta,
+                                                             int32_t *info, Ws w, const double *lam_tab,
+                                                             int all, const int32_t *fb) {
+    for_each_slot(fb, w.fb_slots, blockIdx.x, gridDim.x,
+                  [&](int slot, int s) { solve_item(g, p, beta, info, w, lam_tab, all, slot, s); });
+}
+
 static size_t solve_smem_bytes(int mc) {
     return (size_t)mc * (4 * sizeof(double) + 2 * sizeof(int)) + kFactorSmemBytes;
 }
@@ -556,13 +594,13 @@ void launch_bgram_f64(const Geo &g, const int32_t *info, const Ws &w, cudaStream
     {
         PhaseScope ps(kPhAssemble, st);
         dim3 gb((g.m_cap + 7) / 8, g.S);
-        k_bvec_f64<<<gb, 256, 0, st>>>(g, info, w, all, folds, fold);
+        k_bvec_f64<<<gb, 256, 0, st>>>(g, info, w, all, folds, fold, nullptr);
         count_launches(1);
     }
     PhaseScope ps(kPhGram, st);
     int T = g.m_cap / kGT;
     dim3 gg(T * (T + 1) / 2, g.S);
-    k_gram_f64<<<gg, 256, 0, st>>>(g, info, w, all, folds, fold);
+    k_gram_f64<<<gg, 256, 0, st>>>(g, info, w, all, folds, fold, nullptr);
     count_launches(1);
 }
 
@@ -573,7 +611,7 @@ void launch_assemble_gram_f64(const Geo &g, const int32_t *boxes, const double *
     {
         PhaseScope ps(kPhAssemble, st);
         dim3 ga((g.n_max + 127) / 128, g.S);
-        k_assemble_f64<<<ga, 128, asm_smem, st>>>(g, boxes, centres, info, w, all);
+        k_assemble_f64<<<ga, 128, asm_smem, st>>>(g, boxes, centres, info, w, all, nullptr);
         count_launches(1);
     }
     launch_bgram_f64(g, info, w, st, all, 0, 0);
@@ -584,8 +622,63 @@ void launch_solve_f64(const Geo &g, const Par &p, double *beta, int32_t *info, c
     size_t ss = solve_smem_bytes(g.m_cap);
     cudaFuncSetAttribute(k_solve_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
     PhaseScope ps(kPhSolve, st);
-    k_solve_f64<<<g.S, kSolveThreads, ss, st>>>(g, p, beta, info, w, lam_tab, all);
+    k_solve_f64<<<g.S, kSolveThreads, ss, st>>>(g, p, beta, info, w, lam_tab, all, nullptr);
     count_launches(1);
+}
+
+__global__ void __launch_bounds__(128) k_residual_f64(Geo g, const double *beta, const int32_t *info, Ws w,
+                                                      const int32_t *fb);
+
+constexpr int kFbRows = 4;
+
+// Binary64 fallback of the mixed form: every subdomain on the fallback list
+// (written by the mixed solve: its fp32 iterate did not pass the optimality
+// check) is solved again by the binary64 path -- assembly of E and 1/Shepard
+// sum, b = W^T y, G = W^T W, the active-set solve -- on its slot of the
+// fallback regions, so that it reaches the unique minimiser of Eq. (2) to
+// the binary64 form's certificate; then its indicators are recomputed from
+// the new coefficients (midpoint rule; the Gauss-Legendre indicators are
+// recomputed for every subdomain by the refinement round anyway). The
+// launches are sized for all slots; blocks past the list return at once.
+void launch_fallback_f64(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
+                         double *beta, int32_t *info, const Ws &w, const double *lam_tab, cudaStream_t st) {
+    if (w.fb_slots <= 0) return;
+    PhaseScope ps(kPhSolve, st);
+    Ws wf = w;
+    wf.E = w.fbE;
+    wf.G = w.fbG;
+    wf.L = w.fbL;
+    // a few rows of blocks per kernel, each taking every rows-th listed
+    // subdomain: next to nothing to launch when the list is empty (the usual
+    // case), and up to kFbRows subdomains at a time otherwise
+    const unsigned F = (unsigned)(w.fb_slots < kFbRows ? w.fb_slots : kFbRows);
+    // the fallback kernels run between the mixed solve and the next level's
+    // tensor-core Gram, both near the shared-memory maximum: the same
+    // carveout keeps the SMs from reconfiguring around each (empty) launch
+    static bool carveout = [] {
+        cudaFuncSetAttribute(k_assemble_f64, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_bvec_f64, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_gram_f64, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_solve_f64, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        cudaFuncSetAttribute(k_residual_f64, cudaFuncAttributePreferredSharedMemoryCarveout, cudaSharedmemCarveoutMaxShared);
+        return true;
+    }();
+    (void)carveout;
+    const size_t asm_smem = (size_t)g.m_cap * sizeof(dvec4);
+    cudaFuncSetAttribute(k_assemble_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)asm_smem);
+    k_assemble_f64<<<dim3((g.n_max + 127) / 128, F), 128, asm_smem, st>>>(g, boxes, centres, info, wf, 1, w.fb);
+    k_bvec_f64<<<dim3((g.m_cap + 7) / 8, F), 256, 0, st>>>(g, info, wf, 1, 0, 0, w.fb);
+    const int T = g.m_cap / kGT;
+    k_gram_f64<<<dim3(T * (T + 1) / 2, F), 256, 0, st>>>(g, info, wf, 1, 0, 0, w.fb);
+    const size_t ss = solve_smem_bytes(g.m_cap);
+    cudaFuncSetAttribute(k_solve_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)ss);
+    k_solve_f64<<<F, kSolveThreads, ss, st>>>(g, p, beta, info, wf, lam_tab, 1, w.fb);
+    count_launches(4);
+    if (!p.quad) {
+        k_residual_f64<<<dim3((g.n_max + 127) / 128, F), 128, (size_t)g.m_cap * sizeof(double), st>>>(
+            g, beta, info, wf, w.fb);
+        count_launches(1);
+    }
 }
 
 void launch_solve_level_f64(const Geo &g, const Par &p, const int32_t *boxes,
@@ -622,9 +715,8 @@ void launch_copy_gram_f64(const Geo &g, const int32_t *info, const Ws &w, double
 // Step 3: residual indicators (Eq. (4), midpoint rule, K space),
 // R_T = |T| (exp(sum_m W_Tm beta_m) - K_T)^2.
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(128) k_residual_f64(Geo g, const double *beta,
-                                                      const int32_t *info, Ws w) {
-    int s = blockIdx.y;
+__device__ __forceinline__ void residual_item(const Geo &g, const double *beta, const int32_t *info, const Ws &w,
+                                              int slot, int s) {
     const int32_t *inf = info + s * kInfoN;
     if (inf[PAM_INFO_STOPPED]) return;
     int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
@@ -633,12 +725,18 @@ __global__ void __launch_bounds__(128) k_residual_f64(Geo g, const double *beta,
     __syncthreads();
     int t = blockIdx.x * blockDim.x + threadIdx.x;
     if (t >= N) return;
-    const double *E = w.E + (size_t)s * g.m_cap * g.n_max + t;
+    const double *E = w.E + (size_t)slot * g.m_cap * g.n_max + t;
     double acc = 0.0;
     for (int m = 0; m < M; ++m) acc += E[(size_t)m * g.n_max] * sb[m];
     size_t o = (size_t)s * g.n_max + t;
     double e = exp(acc * w.inv_s[o]) - w.kv[o];
     w.R[o] = cell_measure(g, s, t) * (e * e);
+}
+
+__global__ void __launch_bounds__(128) k_residual_f64(Geo g, const double *beta,
+                                                      const int32_t *info, Ws w, const int32_t *fb) {
+    for_each_slot(fb, w.fb_slots, blockIdx.y, gridDim.y,
+                  [&](int slot, int s) { residual_item(g, beta, info, w, slot, s); });
 }
 
 // --------------------------------------------------------------------------
@@ -909,7 +1007,7 @@ void launch_residual_f64(const Geo &g, const double *beta, const int32_t *info, 
     size_t sm = (size_t)g.m_cap * sizeof(double);
     dim3 grid((g.n_max + 127) / 128, g.S);
     PhaseScope ps(kPhResidual, st);
-    k_residual_f64<<<grid, 128, sm, st>>>(g, beta, info, w);
+    k_residual_f64<<<grid, 128, sm, st>>>(g, beta, info, w, nullptr);
     count_launches(1);
 }
 

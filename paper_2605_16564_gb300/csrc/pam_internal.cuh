@@ -60,14 +60,28 @@ struct Ws {
     float *Gf;        // [S][m_cap][m_cap] Gram in fp32 (mixed form)
     float *rowmax;    // [S][n_max]   row maximum of the logits (mixed form)
     float *rowinv;    // [S][n_max]   1 / Shepard sum (mixed form)
+    float *wsum;      // [S][m_cap]   sum_t W_tj of each centre (mixed form: bounds of the exact gradient)
     double *err_part; // [err_blocks][4] per-block partial sums of the error measures
     unsigned long long *kmax_bits; // [S] max K of each patch as ordered bits
     int32_t *status;  // [8] device status words
     uint32_t *cost;   // [S] clock cycles of each subdomain's last mixed solve (a scheduling hint)
     int32_t *order;   // [S] subdomains in decreasing cost, the mixed solve's block order
     double4_32a *cxv; // [S][n_max] gathered (x, y, z, |T|) of patch cells (element-list meshes only)
+    // binary64 fallback of the mixed form: the subdomains whose fp32 solve
+    // did not certify are solved again in binary64 on fb_slots slots
+    int32_t *fb;      // [2 + fb_slots]: fb[0] = subdomains listed, fb[2 + i] = the i-th
+    double *fbE;      // [fb_slots][m_cap][n_max] exp(l - l*) of the listed subdomains
+    double *fbG;      // [fb_slots][m_cap][m_cap] their binary64 Gram
+    double *fbL;      // [fb_slots][m_cap (m_cap+1)/2] their binary64 factors beyond shared memory
+    int fb_slots;     // 0 in the binary64 form
     size_t bytes;
+    size_t bytes_no_fb;  // the regions before the fallback's (all that pam_gram uses)
 };
+
+// Slots of the binary64 fallback: at most this many subdomains of one mixed
+// solve are solved again in binary64 (the rest stay flagged NOT_CERTIFIED).
+constexpr int kFbSlots = 32;
+
 
 enum StatusWord { kStBadK = 0, kStUncertified = 1, kStCholesky = 2, kStTimeout = 3 };
 
@@ -98,13 +112,15 @@ void launch_bgram_f64(const Geo &g, const int32_t *info, const Ws &w, cudaStream
                       int fold);
 void launch_solve_f64(const Geo &g, const Par &p, double *beta, int32_t *info, const Ws &w,
                       const double *lam_tab, int all, cudaStream_t st);
+void launch_fallback_f64(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
+                         double *beta, int32_t *info, const Ws &w, const double *lam_tab, cudaStream_t st);
 void launch_stats_f32(const Geo &g, const int32_t *boxes, const double *centres, const int32_t *info,
                       const Ws &w, cudaStream_t st, int all);
 void launch_gram_tc(const Geo &g, const int32_t *boxes, const double *centres, const int32_t *info,
                     const Ws &w, cudaStream_t st, int all, int folds, int fold);
 void launch_solve_mixed(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
                         double *beta, int32_t *info, const Ws &w, const double *lam_tab, int all, double *cv,
-                        int cv_stride, cudaStream_t st);
+                        int cv_stride, cudaStream_t st, int fallback);
 void launch_copy_gram_f32(const Geo &g, const int32_t *info, const Ws &w, double *G_out,
                           double *b_out, cudaStream_t st);
 void launch_copy_gram_f64(const Geo &g, const int32_t *info, const Ws &w, double *G_out,

@@ -17,6 +17,7 @@
 
 #include "pam_internal.cuh"
 #include "pam_tc.cuh"
+#include "pam_chol.cuh"
 
 namespace pam {
 
@@ -248,7 +249,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
                                     : (size_t)32 * kTcStageFloats * 4;
     float4 *sc = reinterpret_cast<float4 *>(smem + tiles_region);   // [Rcap]
     float *bpart = reinterpret_cast<float *>(sc + Rcap);             // [4][Rcap]
-    float4 *cellp = reinterpret_cast<float4 *>(bpart + 4 * Rcap);    // [nch * 32] (x, y, z, sh)
+    float *wpart = bpart + 4 * Rcap;                                 // [4][Rcap]
+    float4 *cellp = reinterpret_cast<float4 *>(wpart + 4 * Rcap);    // [nch * 32] (x, y, z, sh)
     const int nch = (N + kTcKC - 1) / kTcKC;
     float *celly = reinterpret_cast<float *>(cellp + (size_t)nch * kTcKC);  // [nch * 32] ln K
     __shared__ uint64_t full[kTcMaxStages], empty[kTcMaxStages], drain;
@@ -372,7 +374,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
         const int pw = pth >> 5, part = pw % tpr, r = (pw / tpr) * 32 + lane;
         const bool live = r < Rl;
         const float4 cc = live ? sc[r] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float bacc = 0.f;
+        float bacc = 0.f, wacc = 0.f;
         for (int c = 0; c < nch; ++c) {
             const int st = c % nst;
             bool bad = false;
@@ -392,7 +394,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
                 const float *cy = celly + c * kTcKC;
                 uint8_t *hi = tiles + (size_t)st * 2 * tile_bytes;
                 uint8_t *lo = hi + tile_bytes;
-                float bsum = 0.f;
+                float bsum = 0.f, wsm = 0.f;
                 for (int kk = 0; kk < nkg; ++kk) {
                     const int kg = part * nkg + kk;
                     float v[8];
@@ -404,6 +406,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
                         const float e = tc::ex2(fmaf(cc.w, fmaf(dz, dz, fmaf(dy, dy, dx * dx)), -cp.w));
                         v[q] = e;
                         bsum = fmaf(e, cy[k], bsum);
+                        wsm += e;
                     }
                     uint32_t hp[4], lp[4];
 #pragma unroll
@@ -417,6 +420,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
                     *reinterpret_cast<uint4 *>(lo + off) = make_uint4(lp[0], lp[1], lp[2], lp[3]);
                 }
                 bacc += bsum;
+                wacc += wsm;
             }
             tc::fence_proxy_async_smem();
             __syncwarp();
@@ -425,7 +429,10 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
             if (pth == 0) GP_ADD(4, clock64() - pp0);
 #endif
         }
-        if (live) bpart[part * Rcap + r] = bacc;
+        if (live) {
+            bpart[part * Rcap + r] = bacc;
+            wpart[part * Rcap + r] = wacc;
+        }
     }
     // wait for the last chunk's MMAs (they complete in issue order)
 #ifdef PAM_SOLVE_PROFILE
@@ -477,9 +484,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
         const int tpr = (4 * Rl <= 32 * kTcProdWarps) ? 4 : (2 * Rl <= 32 * kTcProdWarps ? 2 : 1);
         const int rend = min(Rl, 128 * (i1 - i0));
         for (int r = tid; r < rend; r += blockDim.x) {
-            float acc = 0.f;
-            for (int q = 0; q < tpr; ++q) acc += bpart[q * Rcap + r];
+            float acc = 0.f, ws = 0.f;
+            for (int q = 0; q < tpr; ++q) {
+                acc += bpart[q * Rcap + r];
+                ws += wpart[q * Rcap + r];
+            }
             w.b[(size_t)s * g.m_cap + row0 + r] = (double)acc;
+            w.wsum[(size_t)s * g.m_cap + row0 + r] = ws;  // sum_t W_tj: a row sum of G
         }
     }
     tc::fence_before_sync();
@@ -498,7 +509,7 @@ static size_t gram_tc_smem(const Geo &g, int stages) {
     const size_t cells = (size_t)((g.n_max + kTcKC - 1) / kTcKC) * kTcKC;
     size_t tiles = (size_t)stages * 2 * Rcap * kTcKC * 2;
     if (tiles < (size_t)32 * kTcStageFloats * 4) tiles = (size_t)32 * kTcStageFloats * 4;
-    return tiles + Rcap * sizeof(float4) + 4 * Rcap * sizeof(float) + cells * (sizeof(float4) + sizeof(float));
+    return tiles + Rcap * sizeof(float4) + 8 * Rcap * sizeof(float) + cells * (sizeof(float4) + sizeof(float));
 }
 
 void launch_gram_tc(const Geo &g, const int32_t *boxes, const double *centres, const int32_t *info,
@@ -582,8 +593,8 @@ constexpr int kMxMaxPdas = 200;
 constexpr int kMxPdasFull = 12;
 
 struct MxShared {
-    int cnt, bad, viol, flag, changed;
-    float inv_piv, dmax, xmax;
+    int cnt, bad, viol, flag, changed, nneed;
+    float inv_piv, dmax, xmax, dinf, yinf;
 };
 
 __device__ void mx_compact(const int *sg, int M, int *idx, int *cnt) {
@@ -601,32 +612,15 @@ __device__ void mx_compact(const int *sg, int M, int *idx, int *cnt) {
     __syncthreads();
 }
 
-__device__ __forceinline__ int tri_i(int p, int q) { return p * (p + 1) / 2 + q; }
-
-#ifdef PAM_SOLVE_PROFILE
-// Profiling builds only: clock64 totals per phase of the mixed solve.
-__device__ unsigned long long g_solve_prof[16];
-__device__ unsigned long long g_solve_blk[8192];
-#define PROF_T0() long long _pt = clock64()
-#define PROF_MARK(k)                                                          \
-    do {                                                                      \
-        if (threadIdx.x == 0) atomicAdd(&g_solve_prof[k], (unsigned long long)(clock64() - _pt)); \
-        _pt = clock64();                                                      \
-    } while (0)
-#else
-#define PROF_T0()
-#define PROF_MARK(k)
-#endif
-
 // Packed support matrix: A[tri(p, q)] = G~[idx[p]][idx[q]] (+ lambda2 on
 // the diagonal) for q <= p < s, flat over the packed entries so that every
-// thread keeps eight independent gathers from G~ in flight.
+// thread keeps sixteen independent gathers from G~ in flight.
 __device__ void mx_build(float *A, const float *G, const int *idx, int s, int mc, float lam2) {
     const int n = s * (s + 1) / 2, nt = blockDim.x;
-    for (int e0 = threadIdx.x; e0 < n; e0 += 8 * nt) {
-        float v[8];
+    for (int e0 = threadIdx.x; e0 < n; e0 += 16 * nt) {
+        float v[16];
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 16; ++u) {
             const int e = e0 + u * nt;
             v[u] = 0.f;
             if (e < n) {
@@ -638,191 +632,9 @@ __device__ void mx_build(float *A, const float *G, const int *idx, int s, int mc
             }
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
+        for (int u = 0; u < 16; ++u) {
             const int e = e0 + u * nt;
             if (e < n) A[e] = v[u];
-        }
-    }
-}
-
-// Blocked right-looking Cholesky of the packed lower s x s matrix A, in
-// place, with blocks of 32 columns. Warp 0 factors the 32 x 32 diagonal
-// block in registers (lane i holds row i, fully unrolled so every index is
-// static; rows past the end of a partial block are padded with the
-// identity); every other thread solves one panel row against it, again
-// from registers, reading L_kk as shared-memory broadcasts; then all
-// threads update the trailing triangle. Three block barriers per 32 columns.
-// dinv[k] receives 1 / L_kk for the triangular solves.
-__device__ __forceinline__ void mx_diag_block(float *A, int k0, int kw, int *flag, float *dinv) {
-    const unsigned full = 0xffffffffu;
-    const int lane = threadIdx.x & 31, i = k0 + lane;
-    const bool live = lane < kw;
-    float a[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j)
-        a[j] = (live && j <= lane) ? A[tri_i(i, k0 + j)] : (j == lane ? 1.f : 0.f);
-    float my_iv = 1.f;
-    bool bad = false;
-    // dn: lane k's pivot a_kk after the updates of columns < k, computed by
-    // lane k itself one step early (the same fma as its share of the bulk
-    // update), so that the column chain is shfl -> rsqrt -> fmul -> fma and
-    // the bulk shuffles stay off it
-    float dn = a[0];
-#pragma unroll
-    for (int k = 0; k < 32; ++k) {
-        float d = __shfl_sync(full, dn, k);
-        if (!(d > 0.f)) { bad = true; d = 1.f; }
-        const float iv = rsqrtf(d);
-        if (lane == k) { a[k] = d * iv; my_iv = iv; }
-        else a[k] *= iv;  // above the diagonal (lane < k) the value is never used
-        if (k + 1 < 32) dn = fmaf(-a[k], a[k], a[k + 1]);  // meaningful in lane k + 1
-#pragma unroll
-        for (int j = k + 1; j < 32; ++j) a[j] = fmaf(-a[k], __shfl_sync(full, a[k], j), a[j]);
-    }
-    if (live) {
-#pragma unroll
-        for (int j = 0; j < 32; ++j)
-            if (j <= lane) A[tri_i(i, k0 + j)] = a[j];
-        dinv[i] = my_iv;
-    }
-    if (__any_sync(full, bad && live)) {
-        if (lane == 0) *flag = 1;
-    }
-}
-
-// Panel row i: L[i, k0:k0+32] = A[i, k0:k0+32] L_kk^{-T} (kw == 32 only:
-// a partial block is the last one and has no rows below it).
-__device__ __forceinline__ void mx_panel_row(float *A, int k0, int i, const float *dinv) {
-    float *ri = A + tri_i(i, 0) + k0;
-    float r[32];
-#pragma unroll
-    for (int j = 0; j < 32; ++j) r[j] = ri[j];
-#pragma unroll
-    for (int q = 0; q < 32; ++q) {
-        const float *lq = A + tri_i(k0 + q, 0) + k0;
-        float a0 = r[q], a1 = 0.f, a2 = 0.f, a3 = 0.f;
-#pragma unroll
-        for (int rr = 0; rr < q; ++rr) {
-            if ((rr & 3) == 0) a0 = fmaf(-r[rr], lq[rr], a0);
-            else if ((rr & 3) == 1) a1 = fmaf(-r[rr], lq[rr], a1);
-            else if ((rr & 3) == 2) a2 = fmaf(-r[rr], lq[rr], a2);
-            else a3 = fmaf(-r[rr], lq[rr], a3);
-        }
-        r[q] = ((a0 + a1) + (a2 + a3)) * dinv[k0 + q];
-    }
-#pragma unroll
-    for (int j = 0; j < 32; ++j) ri[j] = r[j];
-}
-
-__device__ void mx_cholesky(float *A, int s, int *flag, float *dinv) {
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
-    PROF_T0();
-    for (int k0 = 0; k0 < s; k0 += 32) {
-        const int kw = min(32, s - k0);
-        if (warp == 0) mx_diag_block(A, k0, kw, flag, dinv);
-        __syncthreads();
-        PROF_MARK(12);
-        if (k0 + kw >= s) break;  // last block: nothing below it
-        for (int i = k0 + kw + tid; i < s; i += blockDim.x) mx_panel_row(A, k0, i, dinv);
-        __syncthreads();
-        PROF_MARK(13);
-        // trailing update of rows/cols >= k0 + kw
-        for (int i = k0 + kw + warp; i < s; i += nw) {
-            const float *li = A + tri_i(i, 0) + k0;
-            float *row = A + tri_i(i, 0);
-            for (int j = k0 + kw + lane; j <= i; j += 32) {
-                const float *lj = A + tri_i(j, 0) + k0;
-                float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll
-                for (int q = 0; q < 32; q += 2) {
-                    acc0 = fmaf(li[q], lj[q], acc0);
-                    acc1 = fmaf(li[q + 1], lj[q + 1], acc1);
-                }
-                row[j] -= acc0 + acc1;
-            }
-        }
-        __syncthreads();
-        PROF_MARK(14);
-    }
-}
-
-// Solves L L^T z = r in place (packed L from mx_cholesky, dinv = 1/diag):
-// per 32-row block, warp 0 solves the diagonal block with shuffles (fully
-// unrolled; the matrix loads do not depend on the recurrence) and all
-// threads apply the block's contribution to the remaining entries.
-__device__ void mx_chol_backward(const float *A, const float *dinv, int s, float *r);
-
-__device__ void mx_chol_solve(const float *A, const float *dinv, int s, float *r) {
-    const unsigned full = 0xffffffffu;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    // forward: L z = r
-    for (int k0 = 0; k0 < s; k0 += 32) {
-        const int kw = min(32, s - k0);
-        if (warp == 0) {
-            const int i = k0 + lane;
-            const bool live = lane < kw;
-            float ri = live ? r[i] : 0.f;
-            const float di = live ? dinv[i] : 1.f;
-#pragma unroll
-            for (int q = 0; q < 32; ++q) {
-                const float lik = (live && lane > q) ? A[tri_i(i, k0 + q)] : 0.f;
-                if (lane == q) ri *= di;
-                const float zq = __shfl_sync(full, ri, q);
-                ri = fmaf(-lik, zq, ri);
-            }
-            if (live) r[i] = ri;
-        }
-        __syncthreads();
-        if (k0 + kw < s) {
-            for (int i = k0 + kw + tid; i < s; i += blockDim.x) {
-                const float *li = A + tri_i(i, 0) + k0;
-                float acc0 = 0.f, acc1 = 0.f;
-#pragma unroll
-                for (int q = 0; q < 32; q += 2) {
-                    acc0 = fmaf(li[q], r[k0 + q], acc0);
-                    acc1 = fmaf(li[q + 1], r[k0 + q + 1], acc1);
-                }
-                r[i] -= acc0 + acc1;
-            }
-            __syncthreads();
-        }
-    }
-    mx_chol_backward(A, dinv, s, r);
-}
-
-// Backward half: L^T x = z in place.
-__device__ void mx_chol_backward(const float *A, const float *dinv, int s, float *r) {
-    const unsigned full = 0xffffffffu;
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int k0 = ((s - 1) / 32) * 32; k0 >= 0 && s > 0; k0 -= 32) {
-        const int kw = min(32, s - k0);
-        if (warp == 0) {
-            const int pr = k0 + lane;
-            const bool live = lane < kw;
-            float rp = live ? r[pr] : 0.f;
-            const float dp = live ? dinv[pr] : 1.f;
-#pragma unroll
-            for (int q = 31; q >= 0; --q) {
-                const float lqp = (q < kw && lane < q) ? A[tri_i(k0 + q, k0 + lane)] : 0.f;
-                if (lane == q) rp *= dp;
-                const float xq = __shfl_sync(full, rp, q);
-                rp = fmaf(-lqp, xq, rp);
-            }
-            if (live) r[pr] = rp;
-        }
-        __syncthreads();
-        if (k0 > 0) {
-            for (int pr = tid; pr < k0; pr += blockDim.x) {
-                float acc0 = 0.f, acc1 = 0.f;
-                int q = 0;
-                for (; q + 1 < kw; q += 2) {
-                    acc0 = fmaf(A[tri_i(k0 + q, pr)], r[k0 + q], acc0);
-                    acc1 = fmaf(A[tri_i(k0 + q + 1, pr)], r[k0 + q + 1], acc1);
-                }
-                if (q < kw) acc0 = fmaf(A[tri_i(k0 + q, pr)], r[k0 + q], acc0);
-                r[pr] -= acc0 + acc1;
-            }
-            __syncthreads();
         }
     }
 }
@@ -854,14 +666,10 @@ struct DFAcc {
 // in a fixed order. lam_tab (optional): per-subdomain (lambda1_hat,
 // lambda2_hat) pairs in place of p's; all: solve also the subdomains whose
 // refinement has stopped.
-__global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, const int32_t *boxes,
-                                                            const double *centres, double *beta,
-                                                            int32_t *info, Ws w, int kMxFactorBytes,
-                                                            int ordered, const double *lam_tab, int all,
-                                                            double *cv, int cv_stride) {
-    // blocks take the subdomains in decreasing cost of their previous solve,
-    // so the longest start first and the level does not wait on a late one
-    const int s = ordered ? w.order[blockIdx.x] : blockIdx.x;
+__device__ __forceinline__ void solve_mixed_item(const Geo &g, const Par &p, const int32_t *boxes,
+                                                 const double *centres, double *beta, int32_t *info,
+                                                 const Ws &w, int kMxFactorBytes, const double *lam_tab,
+                                                 int all, double *cv, int cv_stride, int fallback, int s) {
     const long long t_start = clock64();
     int32_t *inf = info + s * kInfoN;
     if (!all && inf[PAM_INFO_STOPPED]) return;
@@ -889,7 +697,9 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
     float *cinv = reinterpret_cast<float *>(cell + g.n_max);// [n_max]
     float *ce = cinv + g.n_max;                             // [n_max] y, then e = y - W x
     float *dinv = ce + g.n_max;                             // [mc] 1 / diag of the factor
-    float *Asm = dinv + mc;                                 // packed factor
+    float *ub = dinv + mc;                                  // [mc] bounds on |c_j| off the support
+    float *Lt = ub + mc;                                    // [32 x 32] factorisation scratch
+    float *Asm = Lt + kCholLtFloats;                        // packed factor
     __shared__ MxShared sh;
 
     const float *G = w.Gf + (size_t)s * mc * mc;
@@ -947,9 +757,19 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
     // packed matrix (diagonal 1e30, never a pivot problem): the factorisation
     // leaves L^-1 rhs there, and only the backward solve remains. (Not when
     // the support is the whole capacity: no room for the extra row.)
+    // the rows of G~ on the support: the build gathers from them now, the
+    // fp32 gradient streams them after the factorisation; one bulk L2
+    // prefetch per row keeps them on chip without holding registers
+    auto prefetch_rows = [&]() {
+        const uint32_t bytes = (uint32_t)((M * sizeof(float) + 15) & ~(size_t)15);
+        for (int pp = tid; pp < scnt; pp += blockDim.x)
+            asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;"
+                         ::"l"(G + (size_t)idx[pp] * mc), "r"(bytes) : "memory");
+    };
     auto factor_support = [&]() {
         mx_compact(sg, M, idx, &sh.cnt);
         scnt = sh.cnt;
+        prefetch_rows();
         const bool aug = scnt < mc;
         const int nrow = scnt + (aug ? 1 : 0);
         A = (tri_i(nrow, 0) * 4 <= kMxFactorBytes) ? Asm
@@ -965,7 +785,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
         if (aug && tid == 0) arow[scnt] = 1e30f;
         __syncthreads();
         PROF_MARK(9);
-        mx_cholesky(A, nrow, &sh.flag, dinv);
+        mx_cholesky(A, nrow, &sh.flag, dinv, Lt);
         PROF_MARK(10);
         if (!sh.flag) {
             if (aug) {
@@ -993,6 +813,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
         __syncthreads();
     };
     bool primal = false;
+    bool gfresh = false;  // gr = b~ - G~ x holds for the current x (the fp32 optimality test passed)
     const int max_pdas = p.max_iters < kMxMaxPdas ? p.max_iters : kMxMaxPdas;
     for (; it < max_pdas; ++it) {
         factor_support();
@@ -1015,7 +836,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
             if (mb) atomicAdd(&sh.bad, mb);
             if (mv) atomicAdd(&sh.viol, mv);
             __syncthreads();
-            if (sh.bad == 0 && sh.viol == 0) break;
+            if (sh.bad == 0 && sh.viol == 0) { gfresh = true; break; }
             if (it + 1 < kMxPdasFull) {
                 for (int j = tid; j < M; j += blockDim.x) {
                     if (sg[j] != 0) {
@@ -1058,7 +879,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
                 if (sg[j] == 0 && fabsf(gr[j]) > tol_pdas) { sg[j] = gr[j] > 0.f ? 1 : -1; x[j] = 0.f; ++mv; }
             if (mv) atomicAdd(&sh.viol, mv);
             __syncthreads();
-            if (sh.viol == 0) break;  // optimal
+            if (sh.viol == 0) { gfresh = true; break; }  // optimal
         } else {
             // step alpha towards the minimiser; the blocking coefficients (the
             // ones whose ratio attains alpha) reach zero and leave the support;
@@ -1090,9 +911,46 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
     // A coefficient inside that band has |beta_j| <= 1e-3 lambda1 / (G_jj +
     // lambda2) at the exact minimiser (changes W beta by <~1e-5); admitting it
     // only makes near-degenerate coordinates cycle in and out of the support.
+    //
+    // The exact gradient is computed only where it can decide something: on
+    // the support (the Newton step needs it) and at the centres off it whose
+    // upper bound ub_j >= |c_j| does not already show |c_j| <= kkt_tol. The
+    // first bound comes from the fp32 gradient of stage 1, c~ = b~ - G~ x:
+    // every W_tj >= 0 and each Shepard row sums to one, so sum_k G_jk =
+    // sum_t W_tj = wsum_j, and the per-entry errors of G~ (bf16 split
+    // 3 x 2^-17, fp32 accumulation N 2^-23, the exponent's rounding) and of
+    // b~ (fp32 accumulation) give |c_j - c~_j| <= wsum_j (eps_g ||x||_inf +
+    // eps_b ||y||_inf), taken with a factor 2 of margin. After an exact pass
+    // ub_j = |c_j|; a Newton step changes c by -G dx, so ub_j grows by
+    // wsum_j ||dx||_inf. Centres it settles keep |c_j| <= kkt_tol and cannot
+    // be violators: the certificate is the one of the full pass.
     const float kkt_tol = lam1 * (1.0f + 1e-3f);
     int certified = 0, refine_it = 0;
     const double *yv = w.y + (size_t)s * g.n_max;
+    const float *wsg = w.wsum + (size_t)s * mc;
+    if (!sh.flag) {
+        float xin = 0.f, yin = 0.f;
+        for (int pp = tid; pp < scnt; pp += blockDim.x) xin = fmaxf(xin, fabsf(x[idx[pp]]));
+        for (int t = tid; t < N; t += blockDim.x) yin = fmaxf(yin, fabsf((float)yv[t]));
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            xin = fmaxf(xin, __shfl_xor_sync(0xffffffffu, xin, o2));
+            yin = fmaxf(yin, __shfl_xor_sync(0xffffffffu, yin, o2));
+        }
+        if (tid == 0) { sh.dinf = 0.f; sh.yinf = 0.f; }
+        __syncthreads();
+        if (lane == 0) {
+            atomicMax(reinterpret_cast<int *>(&sh.dinf), __float_as_int(xin));
+            atomicMax(reinterpret_cast<int *>(&sh.yinf), __float_as_int(yin));
+        }
+        __syncthreads();
+        const float eps_g = 2.f * (3.7e-5f + 1.2e-7f * (float)N + 6e-8f * (float)scnt);
+        const float eps_b = 2.f * (1.2e-7f * (float)N + 5e-7f);
+        const float bnd = eps_g * sh.dinf + eps_b * sh.yinf;
+        for (int j = tid; j < M; j += blockDim.x)
+            ub[j] = (gfresh && sg[j] == 0) ? fmaf(wsg[j], bnd, fabsf(gr[j])) : INFINITY;
+        __syncthreads();
+    }
+    int *need = reinterpret_cast<int *>(rhs);  // the c pass's list (rhs is free until the Newton step)
     for (; refine_it < kMxMaxRefine && !sh.flag; ++refine_it) {
         // e = y - W x over the patch (only the support contributes); W x is
         // accumulated in double-float and subtracted in fp64: |y| ~ 10 would
@@ -1115,9 +973,23 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
         }
         __syncthreads();
         PROF_MARK(4);
-        // c_j = sum_t W_tj e_t for every centre (exact gradient of the data term)
+        // c_j = sum_t W_tj e_t (exact gradient of the data term) for the
+        // support and the centres whose bound leaves them undecided
+        if (threadIdx.x < 32) {
+            int base = 0;
+            for (int j0 = 0; j0 < M; j0 += 32) {
+                const int j = j0 + lane;
+                const bool on = j < M && (sg[j] != 0 || !(ub[j] <= kkt_tol));
+                const unsigned bal = __ballot_sync(0xffffffffu, on);
+                if (on) need[base + __popc(bal & ((1u << lane) - 1u))] = j;
+                base += __popc(bal);
+            }
+            if (lane == 0) sh.nneed = base;
+        }
+        __syncthreads();
         float cmax = 0.f;
-        for (int j = tid; j < M; j += blockDim.x) {
+        for (int q = tid; q < sh.nneed; q += blockDim.x) {
+            const int j = need[q];
             const float4 cj = sc[j];
             float acc = 0.f;
             for (int t = 0; t < N; ++t) {
@@ -1125,6 +997,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
                 acc = fmaf(tc::ex2(logit2(cj, cx.x, cx.y, cx.z) - cx.w) * cinv[t], ce[t], acc);
             }
             gr[j] = acc;
+            ub[j] = fabsf(acc);
             cmax = fmaxf(cmax, fabsf(acc));
         }
         if (tid == 0) { sh.viol = 0; sh.changed = 0; sh.dmax = 0.f; sh.xmax = 0.f; }
@@ -1135,7 +1008,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
         int mv = 0;
         for (int j = tid; j < M; j += blockDim.x) {
             if (sg[j] != 0) rmax = fmaxf(rmax, fabsf(gr[j] - lam2 * x[j] - lam1 * (float)sg[j]));
-            else if (fabsf(gr[j]) > kkt_tol) ++mv;
+            else if (ub[j] > kkt_tol) ++mv;  // computed this pass: ub_j = |c_j|
         }
         for (int o2 = 16; o2 > 0; o2 >>= 1) {
             rmax = fmaxf(rmax, __shfl_xor_sync(0xffffffffu, rmax, o2));
@@ -1153,7 +1026,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
         // violators join the support with the sign of their gradient
         int jn = 0;
         for (int j = tid; j < M; j += blockDim.x)
-            if (sg[j] == 0 && fabsf(gr[j]) > kkt_tol) { sg[j] = gr[j] > 0.f ? 1 : -1; x[j] = 0.f; ++jn; }
+            if (sg[j] == 0 && ub[j] > kkt_tol) { sg[j] = gr[j] > 0.f ? 1 : -1; x[j] = 0.f; ++jn; }
         if (jn) atomicOr(&sh.changed, 1);
         __syncthreads();
         if (sh.changed) {
@@ -1163,7 +1036,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
                 : (w.Lf + (size_t)s * ((size_t)mc * (mc + 1) / 2));
             mx_build(A, G, idx, scnt, mc, lam2);
             __syncthreads();
-            mx_cholesky(A, scnt, &sh.flag, dinv);
+            mx_cholesky(A, scnt, &sh.flag, dinv, Lt);
             if (sh.flag) break;
         }
         // Newton correction on the support
@@ -1174,15 +1047,29 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
         __syncthreads();
         mx_chol_solve(A, dinv, scnt, rhs);
         int dropped = 0;
+        float dx = 0.f;
+        if (tid == 0) sh.dinf = 0.f;
         for (int pp = tid; pp < scnt; pp += blockDim.x) {
             const int m = idx[pp];
             const float nx = x[m] + rhs[pp];
-            if (!(nx * (float)sg[m] > 0.f)) { sg[m] = 0; x[m] = 0.f; ++dropped; }
-            else x[m] = nx;
+            if (!(nx * (float)sg[m] > 0.f)) { dx = fmaxf(dx, fabsf(x[m])); sg[m] = 0; x[m] = 0.f; ++dropped; }
+            else { dx = fmaxf(dx, fabsf(rhs[pp])); x[m] = nx; }
         }
-        for (int o2 = 16; o2 > 0; o2 >>= 1) dropped += __shfl_xor_sync(0xffffffffu, dropped, o2);
-        if (lane == 0 && dropped) atomicOr(&sh.changed, 2);
+        for (int o2 = 16; o2 > 0; o2 >>= 1) {
+            dropped += __shfl_xor_sync(0xffffffffu, dropped, o2);
+            dx = fmaxf(dx, __shfl_xor_sync(0xffffffffu, dx, o2));
+        }
+        __syncthreads();  // sh.dinf reset before any warp adds to it
+        if (lane == 0) {
+            if (dropped) atomicOr(&sh.changed, 2);
+            atomicMax(reinterpret_cast<int *>(&sh.dinf), __float_as_int(dx));
+        }
         __syncthreads();
+        {   // c moves by -G dx: the bounds off the support grow by wsum_j ||dx||_inf
+            const float d = sh.dinf * 1.001f;
+            for (int j = tid; j < M; j += blockDim.x)
+                if (sg[j] == 0) ub[j] = fmaf(wsg[j], d, ub[j]);
+        }
         if (sh.changed & 2) {  // support shrank: recompact and refactor
             mx_compact(sg, M, idx, &sh.cnt);
             scnt = sh.cnt;
@@ -1190,7 +1077,7 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
                 : (w.Lf + (size_t)s * ((size_t)mc * (mc + 1) / 2));
             mx_build(A, G, idx, scnt, mc, lam2);
             __syncthreads();
-            mx_cholesky(A, scnt, &sh.flag, dinv);
+            mx_cholesky(A, scnt, &sh.flag, dinv, Lt);
         }
     }
 
@@ -1249,10 +1136,18 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
     if (tid == 0 && s < 8192) g_solve_blk[s] = (unsigned long long)(clock64() - t_blk0);
 #endif
     if (tid == 0) {
-        int flags = inf[PAM_INFO_FLAGS] & ~(PAM_FLAG_NOT_CERTIFIED | PAM_FLAG_CHOLESKY);
+        int flags = inf[PAM_INFO_FLAGS] & ~(PAM_FLAG_NOT_CERTIFIED | PAM_FLAG_CHOLESKY | PAM_FLAG_REFINE_DIVERGED);
         if (!certified) {
             flags |= PAM_FLAG_NOT_CERTIFIED;
-            atomicAdd(&w.status[kStUncertified], 1);
+            // an uncertified fit takes a slot of the binary64 fallback, which
+            // solves it again and sets the status if that fails too
+            const int slot = (fallback && !cv) ? atomicAdd(&w.fb[0], 1) : w.fb_slots;
+            if (slot < w.fb_slots) {
+                w.fb[2 + slot] = s;
+                flags |= PAM_FLAG_REFINE_DIVERGED;
+            } else {
+                atomicAdd(&w.status[kStUncertified], 1);
+            }
         }
         if (sh.flag) flags |= PAM_FLAG_CHOLESKY;
         inf[PAM_INFO_FLAGS] = flags;
@@ -1260,6 +1155,33 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
         inf[PAM_INFO_ITERS] = it + 100 * refine_it;  // active-set steps + 100 x refinement steps
         const long long dt = clock64() - t_start;
         w.cost[s] = dt > 0xffffffffLL ? 0xffffffffu : (uint32_t)dt;
+    }
+}
+
+// The subdomains go in decreasing cost of their previous solve, so the
+// longest start first and the level does not wait on a late one. persistent
+// = 0: one block per subdomain, block b taking the b-th of that order;
+// persistent = 1: one block per resident slot, each taking the next
+// subdomain of the order from the counter w.fb[1] until none is left.
+__global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, const int32_t *boxes,
+                                                            const double *centres, double *beta,
+                                                            int32_t *info, Ws w, int kMxFactorBytes,
+                                                            const double *lam_tab, int all, double *cv,
+                                                            int cv_stride, int fallback, int persistent) {
+    if (!persistent) {
+        solve_mixed_item(g, p, boxes, centres, beta, info, w, kMxFactorBytes, lam_tab, all, cv, cv_stride,
+                         fallback, w.order[blockIdx.x]);
+        return;
+    }
+    __shared__ int next;
+    for (int it = 0;; ++it) {
+        if (it) __syncthreads();  // the previous subdomain's readers are done with shared memory
+        if (threadIdx.x == 0) next = atomicAdd(&w.fb[1], 1);
+        __syncthreads();
+        const int k = next;
+        if (k >= g.S) break;
+        solve_mixed_item(g, p, boxes, centres, beta, info, w, kMxFactorBytes, lam_tab, all, cv, cv_stride,
+                         fallback, w.order[k]);
     }
 }
 
@@ -1278,7 +1200,11 @@ __device__ __forceinline__ int cost_bucket(uint32_t c) {
     return 8 * e + (int)((c >> (e - 3)) & 7u) - 16;  // 16..239, increasing with c
 }
 
-__global__ void __launch_bounds__(1024) k_solve_order(const uint32_t *cost, int S, int32_t *order) {
+__global__ void __launch_bounds__(1024) k_solve_order(const uint32_t *cost, int S, int32_t *order,
+                                                     int32_t *fb) {
+    // the solve that follows fills the fallback list afresh and (persistent
+    // launch) counts its subdomains from zero
+    if (fb && threadIdx.x == 0) { fb[0] = 0; fb[1] = 0; }
     constexpr int kB = 256;
     __shared__ int cnt[kB], base[kB];
     for (int i = threadIdx.x; i < kB; i += blockDim.x) cnt[i] = 0;
@@ -1298,8 +1224,8 @@ __global__ void __launch_bounds__(1024) k_solve_order(const uint32_t *cost, int 
 
 // Shared memory of the mixed solve besides the packed factor.
 static size_t solve_mixed_smem_rest(const Geo &g) {
-    return (size_t)g.m_cap * (5 * sizeof(float) + 2 * sizeof(int) + sizeof(float4)) +
-           (size_t)g.n_max * (sizeof(float4) + 2 * sizeof(float)) + 64;
+    return (size_t)g.m_cap * (6 * sizeof(float) + 2 * sizeof(int) + sizeof(float4)) +
+           (size_t)g.n_max * (sizeof(float4) + 2 * sizeof(float)) + kCholLtFloats * sizeof(float) + 64;
 }
 
 // Shared-memory budget of the packed support factor (larger supports keep
@@ -1337,9 +1263,11 @@ extern "C" void pam_debug_solve_blocks(unsigned long long *out, int n) {
 }
 extern "C" void pam_debug_solve_profile(unsigned long long *out, int reset) {
     cudaMemcpyFromSymbol(out, g_solve_prof, sizeof(g_solve_prof));
+    cudaMemcpyFromSymbol(out + 16, g_solve_cnt, sizeof(g_solve_cnt));
     if (reset) {
         unsigned long long z[16] = {};
         cudaMemcpyToSymbol(g_solve_prof, z, sizeof(z));
+        cudaMemcpyToSymbol(g_solve_cnt, z, sizeof(g_solve_cnt));
     }
 }
 #endif
@@ -1350,16 +1278,28 @@ bool mixed_solve_fits(const Geo &g) {
 
 void launch_solve_mixed(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
                         double *beta, int32_t *info, const Ws &w, const double *lam_tab, int all, double *cv,
-                        int cv_stride, cudaStream_t st) {
+                        int cv_stride, cudaStream_t st, int fallback) {
     size_t sm = solve_mixed_smem(g);
     cudaFuncSetAttribute(k_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     PhaseScope ps(kPhSolve, st);
-    const int ordered = 1;
-    k_solve_order<<<1, 1024, 0, st>>>(w.cost, g.S, w.order);
+    const int fb = fallback && !cv && w.fb_slots > 0;
+    k_solve_order<<<1, 1024, 0, st>>>(w.cost, g.S, w.order, w.fb);
     count_launches(1);
-    k_solve_mixed<<<g.S, kMxThreads, sm, st>>>(g, p, boxes, centres, beta, info, w, factor_smem_bytes(g),
-                                               ordered, lam_tab, all, cv, cv_stride);
+    const int persistent = tuning().solve_persistent == 1 && w.fb != nullptr;
+    unsigned grid = (unsigned)g.S;
+    if (persistent) {
+        // as many CTAs as fit the device at once with this launch's shared memory
+        int dev = 0, sms = 0, per = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_mixed, kMxThreads, sm);
+        const int resident = sms * (per > 0 ? per : 1);
+        grid = (unsigned)(resident < g.S ? resident : g.S);
+    }
+    k_solve_mixed<<<grid, kMxThreads, sm, st>>>(g, p, boxes, centres, beta, info, w, factor_smem_bytes(g),
+                                                lam_tab, all, cv, cv_stride, fb, persistent);
     count_launches(1);
+    if (fb) launch_fallback_f64(g, p, boxes, centres, beta, info, w, lam_tab, st);
 }
 
 void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes,
@@ -1367,7 +1307,7 @@ void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes,
                               cudaStream_t st, cudaEvent_t before_solve) {
     launch_stats_gram_tc(g, boxes, centres, info, w, st, 0);
     if (before_solve) cudaStreamWaitEvent(st, before_solve, 0);  // an error surfaces in cudaGetLastError
-    launch_solve_mixed(g, p, boxes, centres, beta, info, w, nullptr, 0, nullptr, 0, st);
+    launch_solve_mixed(g, p, boxes, centres, beta, info, w, nullptr, 0, nullptr, 0, st, 1);
 }
 
 // The mixed solve already wrote the indicators of its final coefficients.

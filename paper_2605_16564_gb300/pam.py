@@ -71,7 +71,7 @@ class pam_cells(C.Structure):
 
 class pam_tuning(C.Structure):
     _fields_ = [("factor_kb", C.c_int), ("gram_stages", C.c_int), ("eval_block", C.c_int),
-                ("reserved", C.c_int * 5)]
+                ("solve_persistent", C.c_int), ("reserved", C.c_int * 4)]
 
 
 class pam_model(C.Structure):
@@ -423,28 +423,29 @@ def pam_resume_cells(problem, params, plan, cells, K, model, workspace, stream=N
     return code
 
 
-def pam_tuning_set(factor_kb=0, gram_stages=0, eval_block=0, reset=False):
+def pam_tuning_set(factor_kb=0, gram_stages=0, eval_block=0, solve_persistent=0, reset=False):
     """Process-wide launch tuning (0 = built-in choice); reset=True restores all built-ins."""
     if reset:
         _check(lib().pam_tuning_set(None), "pam_tuning_set")
         return
-    t = pam_tuning(int(factor_kb), int(gram_stages), int(eval_block))
+    t = pam_tuning(int(factor_kb), int(gram_stages), int(eval_block), int(solve_persistent))
     _check(lib().pam_tuning_set(C.byref(t)), "pam_tuning_set")
 
 
 def pam_tuning_get():
     t = pam_tuning()
     _check(lib().pam_tuning_get(C.byref(t)), "pam_tuning_get")
-    return dict(factor_kb=t.factor_kb, gram_stages=t.gram_stages, eval_block=t.eval_block)
+    return dict(factor_kb=t.factor_kb, gram_stages=t.gram_stages, eval_block=t.eval_block,
+                solve_persistent=t.solve_persistent)
 
 
 def pam_autotune(problem, params, plan, K, model, workspace, pts=None, out=None, eval_workspace=None, stream=None,
                  cells=None):
     """Measures the tuning candidates on a fitted model (and pts, if given),
-    keeps the fastest process-wide; returns (choice dict, medians in ms [12]).
+    keeps the fastest process-wide; returns (choice dict, medians in ms [14]).
     cells: the pam_cells of a mesh given as cells (pam_autotune_cells)."""
     t = pam_tuning()
-    ms = np.zeros(12, dtype=np.float64)
+    ms = np.zeros(14, dtype=np.float64)
     n = pts.shape[0] if pts is not None else 0
     ebytes = eval_workspace.numel() * eval_workspace.element_size() if eval_workspace is not None else 0
     wbytes = workspace.numel() * workspace.element_size()
@@ -458,7 +459,8 @@ def pam_autotune(problem, params, plan, K, model, workspace, pts=None, out=None,
                                         _ptr(out), _ptr(eval_workspace), ebytes, _stream(stream), C.byref(t),
                                         ms.ctypes.data)
     _check(code, "pam_autotune")
-    return dict(factor_kb=t.factor_kb, gram_stages=t.gram_stages, eval_block=t.eval_block), ms
+    return dict(factor_kb=t.factor_kb, gram_stages=t.gram_stages, eval_block=t.eval_block,
+                solve_persistent=t.solve_persistent), ms
 
 
 def pam_selftest_wait(arrive, budget_cycles, flag, stream=None):

@@ -76,3 +76,18 @@ def test_roofline_objects_keep_their_contract():
     assert t["stats"]["traffic"] is None
     assert all(v["traffic"] is None for v in bench.attach_traffic({k: dict(v) for k, v in r.items()},
                                                                    "channel2d").values())
+
+
+def test_dictionary_agreement_counts_differing_subdomains_and_flags():
+    from paper_2605_16564_gb300 import pam
+    S, mc = 4, 6
+    c = np.random.default_rng(3).uniform(size=(S, mc, 4))
+    plain = dict(M=np.array([4, 5, 6, 4]), c=c.copy(), info=np.zeros((S, 8), dtype=np.int32))
+    mixed = dict(M=np.array([4, 5, 5, 4]), c=c.copy(), info=np.zeros((S, 8), dtype=np.int32))
+    mixed["c"][3, 2, 0] += 1e-12          # one centre moved: differs
+    mixed["c"][0, 5, 0] += 1.0            # past M: does not count
+    mixed["info"][1, pam.INFO_FLAGS] = pam.FLAG_REFINE_DIVERGED
+    mixed["info"][2, pam.INFO_FLAGS] = pam.FLAG_NOT_CERTIFIED
+    a = bench.dictionary_agreement(pam, mixed, plain)
+    assert a["dictionaries_differing"] == 2 and a["fraction_differing"] == 0.5
+    assert a["mixed_solves_fallen_back_to_fp64"] == 1 and a["mixed_solves_uncertified"] == 1

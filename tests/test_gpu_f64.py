@@ -206,6 +206,14 @@ def test_channel_field_1024_sampled_subdomains(torch_dev):
     pts = np.concatenate([ref["boxes"][s, 0:2] * h + rng.uniform(0, 1, size=(100, 2)) * 32 * h for s in which])
     out = fit.eval(torch.from_numpy(pts).to(dev)).cpu().numpy()
     assert np.abs(out - oracle.evaluate(ref, pts)).max() <= KSTAR_RTOL * (K.max() - K.min())
+    # the workload's own target: the non-matching 1536 x 1536 mesh, every
+    # point the sampled subdomains own
+    mesh = fields.cell_centred_points((1536, 1536), (1.0, 1.0))
+    ko, own = oracle.evaluate(ref, mesh, return_owner=True)
+    sel = np.isin(own, which)
+    assert sel.sum() == len(which) * 48 * 48
+    kg = fit.eval(torch.from_numpy(mesh).to(dev)).cpu().numpy()
+    assert np.abs(kg[sel] - ko[sel]).max() <= KSTAR_RTOL * (K.max() - K.min())
 
 
 @pytest.mark.parametrize("case", ["voronoi2d", "layered3d"])

@@ -8,6 +8,7 @@ import numpy as np
 import pytest
 
 import oracle
+from oracle_refit import oracle_on_gpu_dictionary
 from paper_2605_16564_gb300 import fields
 
 pytestmark = pytest.mark.gpu
@@ -73,6 +74,18 @@ def test_tensor_core_gram_voronoi_multi_strip(env):
     K = fields.voronoi_field(256, n_sites=32, seed=2)
     model, n = _gram_case(env, K, (256, 256), (8, 8), 2, (8, 8), 2, range(0, 64, 7), k_top=37, levels=3)
     assert model["M"].max() > 256 and n == 10
+
+
+def test_tensor_core_gram_two_strip_groups(env):
+    # after 3 refinement levels M reaches 64 + 3 * 111 = 397 > 384: the padded
+    # dictionary (416) needs four 128-row strips whose D blocks do not fit the
+    # 512 TMEM columns together, so two CTAs per subdomain each generate W for
+    # their own strip group (the benchmark's 3-D dictionaries, M = 392, take
+    # the same path)
+    K = fields.voronoi_field(256, n_sites=32, seed=2)
+    model, n = _gram_case(env, K, (256, 256), (8, 8), 2, (8, 8), 3, range(0, 64, 5), k_top=37, levels=3)
+    assert model["M"].max() > 384 and n == 13
+    assert sum(int(model["M"][s] > 384) for s in range(0, 64, 5)) >= 3
 
 
 def test_tensor_core_gram_3d_and_1d(env):
@@ -160,6 +173,14 @@ def test_mixed_full_fit_voronoi(env):
     ko = oracle.evaluate(ref, pts)
     ok = _log10_close(km, ko)
     assert ok.all(), (np.count_nonzero(~ok), np.abs(np.log10(km) - np.log10(ko)).max())
+    # the others: against the oracle's fit of the GPU's own refined dictionary
+    for s in sorted(set(range(64)) - set(same)):
+        b = boxes[s]
+        X, Y = np.meshgrid((np.arange(b[0], b[3]) + 0.5) * h, (np.arange(b[1], b[4]) + 0.5) * h)
+        ps = np.stack([X.ravel(), Y.ravel()], 1)
+        km = fit.eval(torch.from_numpy(ps).to(dev)).cpu().numpy()
+        ko = oracle_on_gpu_dictionary((256, 256), ref, got, s, K, ps)
+        assert _log10_close(km, ko).all(), (s, np.abs(np.log10(km) - np.log10(ko)).max())
     flags = got["info"][:, pam.INFO_FLAGS]
     assert np.count_nonzero(flags & pam.FLAG_NOT_CERTIFIED) == 0
 
@@ -189,6 +210,9 @@ def test_mixed_3d_layered_sample(env):
         if got["M"][s] == m and np.array_equal(got["c"][s, :m], ref["c"][s, :m]):
             same += 1
             bad += np.count_nonzero(~_log10_close(km, ko))
+        else:  # the oracle's fit of the GPU's own refined dictionary
+            kr = oracle_on_gpu_dictionary(shape, ref, got, s, K, pts)
+            bad += np.count_nonzero(~_log10_close(km, kr))
     assert same >= 0.75 * len(which), same
     assert bad == 0
     assert abs(l1m - l1o) <= L1_RTOL * l1o, (l1m / den, l1o / den)
@@ -228,9 +252,27 @@ def test_mixed_channel_field_1024_sample(env):
         if got["M"][s] == m and np.array_equal(got["c"][s, :m], ref["c"][s, :m]):
             same += 1
             bad += np.count_nonzero(~_log10_close(km, ko))
+        else:  # the oracle's fit of the GPU's own refined dictionary
+            kr = oracle_on_gpu_dictionary((1024, 1024), ref, got, s, K, pts)
+            bad += np.count_nonzero(~_log10_close(km, kr))
     assert same >= 0.75 * len(which), same
     assert bad == 0
     assert abs(l1m - l1o) <= L1_RTOL * l1o
+    # the workload's own target, the non-matching 1536 x 1536 mesh: every
+    # point the sampled subdomains own, per point against the oracle's fit
+    # (of the GPU's dictionary where the refinement decided differently)
+    mesh = fields.cell_centred_points((1536, 1536), (1.0, 1.0))
+    ko, own = oracle.evaluate(ref, mesh, return_owner=True)
+    kg = fit.eval(torch.from_numpy(mesh).to(dev)).cpu().numpy()
+    n_pts = 0
+    for s in which:
+        q = own == s
+        n_pts += int(q.sum())
+        m = ref["M"][s]
+        kr = ko[q] if (got["M"][s] == m and np.array_equal(got["c"][s, :m], ref["c"][s, :m])) else \
+            oracle_on_gpu_dictionary((1024, 1024), ref, got, s, K, mesh[q])
+        assert _log10_close(kg[q], kr).all(), (s, np.abs(np.log10(kg[q]) - np.log10(kr)).max())
+    assert n_pts == len(which) * 48 * 48
 
 
 def test_mixed_gauss_legendre_indicators(env):

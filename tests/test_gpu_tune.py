@@ -42,14 +42,16 @@ def test_autotune_choices_and_bitwise_invariance(env, precision):
     fit, Kd, base, out0 = _run(env, K, geo, pts, precision, **params)
     choice, ms = fit.autotune(Kd, torch.from_numpy(pts).to(dev))
     assert choice == pam.pam_tuning_get()
-    assert choice["eval_block"] in (128, 256, 512, 1024) and (ms[8:] > 0).all()
+    assert choice["eval_block"] in (128, 256, 512, 1024) and (ms[8:12] > 0).all()
     if precision == 1:
         assert choice["gram_stages"] in (2, 3) and choice["factor_kb"] in (0, 64, 48, 32, 24, 16)
-        assert (ms[:2] > 0).all() and (ms[2:8] != 0).all()
+        assert (ms[:2] > 0).all() and (ms[2:8] != 0).all() and (ms[12:14] > 0).all()
+        assert choice["solve_persistent"] in (0, 1)
     else:
-        assert (ms[:8] == -1).all()
+        assert (ms[:8] == -1).all() and (ms[12:14] == -1).all()
     # force the non-default candidates too: results must not move
-    for tuned in (choice, dict(factor_kb=16, gram_stages=2, eval_block=1024)):
+    for tuned in (choice, dict(factor_kb=16, gram_stages=2, eval_block=1024, solve_persistent=1),
+                  dict(solve_persistent=1)):
         pam.pam_tuning_set(**tuned)
         _, _, got, out = _run(env, K, geo, pts, precision, **params)
         for key in ("M", "c", "beta"):
