@@ -173,7 +173,7 @@ def accounting(fit, Kd, levels, pam, seed=None):
       chol_flops  sum iters * s^3 / 3 over the active-set steps (fp32 form);
       eval_pairs  filled in by the caller (points x their owner's M)."""
     out = dict(gram_flops=0.0, pairs=0.0, chol_flops=0.0, solve_bytes=0.0, m_final=None, solves=0,
-               steps=0.0, passes=0.0, support_last=None)
+               steps=0.0, passes=0.0, support_last=None, records=[])
     fit_levels = [0] + [1] * levels
     for r, _ in enumerate(fit_levels):
         if r == 0:
@@ -207,7 +207,28 @@ def accounting(fit, Kd, levels, pam, seed=None):
         out["steps"] += float(np.sum(iters))
         out["passes"] += float(np.sum(passes))
         out["support_last"] = float(sup.mean()) if len(sup) else 0.0
+        flags = info[solved, pam.INFO_FLAGS]
+        for k, sd in enumerate(np.flatnonzero(solved)):
+            out["records"].append({"level": r, "subdomain": int(sd), "cells": int(n[k]), "centres": int(m[k]),
+                                   "support": int(sup[k]), "active_set_steps": int(iters[k]),
+                                   "refinement_passes": int(passes[k]), "flags": int(flags[k])})
     out["m_final"] = fit.model.info.cpu().numpy()[:, pam.INFO_M].astype(float)
+    return out
+
+
+def solve_distribution(records):
+    """Per level: how the solves' support sizes and active-set steps are
+    spread (median, 90th percentile, maximum) and how many were flagged --
+    where the solve's tail comes from."""
+    out = {}
+    for lv in sorted({r["level"] for r in records}):
+        rs = [r for r in records if r["level"] == lv]
+        d = {"solves": len(rs)}
+        for key in ("centres", "support", "active_set_steps", "refinement_passes"):
+            v = np.array([r[key] for r in rs], dtype=float)
+            d[key] = {"p50": float(np.percentile(v, 50)), "p90": float(np.percentile(v, 90)), "max": float(v.max())}
+        d["flagged"] = int(sum(1 for r in rs if r["flags"]))
+        out[f"level{lv}"] = d
     return out
 
 
@@ -219,12 +240,13 @@ FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 
 
 # DRAM bytes (read + write) of one launch of each mixed-form kernel on the
-# layered 3-D workload: ncu --set full of the last level's launches on the
-# quarter-size workload (561 of the 2,244 subdomains, same subdomain shape),
-# scaled by 4 (profiles/kernels_layered3d_quarter_mixed.md). Only valid for
-# that workload and for the kernels as captured.
-# (k_stats_f32 has none: its launch shape changed after its last capture.)
-TRAFFIC_LAYERED3D = {"k_solve_mixed": 1.414e9, "k_gram_tc": 1.221e9, "k_eval_bucket_f32": 3.06e8}
+# layered 3-D workload: ncu of the last level's launch on the quarter-size
+# workload (561 of the 2,244 subdomains, same subdomain shape), scaled by 4
+# (profiles/solve_layered3d_quarter_mixed.md for the solve,
+# profiles/kernels_layered3d_quarter_mixed.md for the evaluation). Only valid
+# for that workload and for the kernels as captured (the statistics and the
+# tensor-core Gram changed after their last capture: none recorded).
+TRAFFIC_LAYERED3D = {"k_solve_mixed": 1.406e9, "k_eval_bucket_f32": 3.06e8}
 TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the level-3 launch (eval: its one launch), "
                 "captured on layered3d_quarter and scaled x4 by subdomains")
 
@@ -718,6 +740,11 @@ def run_pam(args, rank, ws):
     # --- roofline of every kernel family, the dominant one first ------------
     peaks, peak_src = _peaks()
     work = accounting(fit, Kd, W["params"]["levels"], pam, seed=(lambda: lw.seed(fit, Kd)) if lw else None)
+    if args.metrics_log and rank == 0:
+        # one JSON object per subdomain and level of the step's fit
+        with open(args.metrics_log, "w") as fh:
+            for rec in work["records"]:
+                fh.write(json.dumps(rec) + "\n")
     owners = owner_counts(W, pts)
     work["eval_pairs"] = float(np.sum(owners * work["m_final"]))
     roofs = attach_traffic(roofline_entries(phase_ms, work, n_pts, prec == pam.PAM_PREC_MIXED, peaks, peak_src),
@@ -729,7 +756,8 @@ def run_pam(args, rank, ws):
     return dict(value=value, step_ms=step_ms, times=times, err=err, phase_ms=phase_ms, launches=launches,
                 clocks=clk.summary(), e2e_s=e2e_s, h2d=h2d, d2h=d2h, plain=plain, roof=roof, roofs=roofs,
                 prec_name=prec_name, n_cells=n_cells, n_pts=n_pts, info=info, learned=learned, mode=mode,
-                e2e_mode=e2e_mode, lambda_cv=lcv, glue=glue, tune=tune)
+                e2e_mode=e2e_mode, lambda_cv=lcv, glue=glue, tune=tune,
+                solve_dist=solve_distribution(work["records"]))
 
 
 def glue_pairs_per_point(W, pts, band):
@@ -887,6 +915,9 @@ def main():
                     help="also time the per-subdomain 3-fold cross-validation of 3 lambda pairs (binary64)")
     ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of a CUDA graph replay")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch tuning")
+    ap.add_argument("--metrics-log", default=None,
+                    help="write one JSON line per subdomain and level (cells, centres, support, "
+                         "active-set steps, refinement passes, flags) of the step's fit to this file")
     ap.add_argument("--glue", type=float, default=0.0,
                     help="also time the glued evaluation (pam_eval_glued) with this band in cells")
     ap.add_argument("--quad", type=int, default=0, choices=[0, 1],
@@ -982,6 +1013,7 @@ def main():
         line["glued_eval"] = r["glue"]
     if r["tune"] is not None:
         line["tuning"] = r["tune"]
+    line["solves_per_level"] = r["solve_dist"]
     fit_ms = sum(v[0] for k, v in r["phase_ms"].items() if k not in ("eval", "errors"))
     line["fit_cells_per_s"] = r["n_cells"] * ws / (fit_ms / 1e3) if fit_ms else None
     print(json.dumps(line))

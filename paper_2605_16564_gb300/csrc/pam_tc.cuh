@@ -139,6 +139,31 @@ __device__ __forceinline__ void bulk_g2s(void *dst_smem, const void *src, uint32
                  : "memory");
 }
 
+// Block-wide staging of `bytes` bytes from global into shared memory by the
+// bulk-copy engine: thread 0 initialises the mbarrier `bar` (shared memory,
+// one per call site) and issues the copy, every thread waits with a bounded
+// wait. Returns false -- and nothing may be read from dst -- if an address is
+// not 16-byte aligned, bytes is zero or not a multiple of 16, or the wait
+// gave up (after a second bounded wait for the copy in flight); the caller
+// then loads from global memory. Call it from every thread of the block.
+__device__ __forceinline__ bool bulk_stage_block(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+    const bool ok_args = bytes > 0 && (bytes & 15u) == 0 &&
+                         ((reinterpret_cast<uintptr_t>(src) | (uintptr_t)smem_u32(dst)) & 15u) == 0;
+    if (!ok_args) return false;  // the same decision in every thread
+    if (threadIdx.x == 0) {
+        mbar_init(bar, 1);
+        mbar_fence_init();
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        mbar_arrive_expect_tx(bar, bytes);
+        bulk_g2s(dst, src, bytes, bar);
+    }
+    bool ok = mbar_wait(bar, 0, 2000000000LL);  // ~1 s at 2 GHz; a copy of a few KB takes microseconds
+    if (!ok) ok = mbar_wait(bar, 0, 2000000000LL);
+    return __syncthreads_and(ok ? 1 : 0) != 0;
+}
+
 // ---- fp32 helpers -------------------------------------------------------------
 // 2^x on the special-function unit (max relative error about 2^-22).
 __device__ __forceinline__ float ex2(float x) {

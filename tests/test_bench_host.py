@@ -72,7 +72,8 @@ def test_roofline_objects_keep_their_contract():
     assert r["gram_tc"]["bound"] == "tensor" and r["stats"]["bound"] == "alu"
     # recorded traffic: the layered 3-D workload only, and only for kernels captured as they are
     t = bench.attach_traffic({k: dict(v) for k, v in r.items()}, "layered3d")
-    assert t["solve"]["traffic"] == bench.TRAFFIC_LAYERED3D["k_solve_mixed"]
+    for name, v in t.items():
+        assert v["traffic"] == bench.TRAFFIC_LAYERED3D.get(v["kernel"])
     assert t["stats"]["traffic"] is None
     assert all(v["traffic"] is None for v in bench.attach_traffic({k: dict(v) for k, v in r.items()},
                                                                    "channel2d").values())
@@ -91,3 +92,14 @@ def test_dictionary_agreement_counts_differing_subdomains_and_flags():
     a = bench.dictionary_agreement(pam, mixed, plain)
     assert a["dictionaries_differing"] == 2 and a["fraction_differing"] == 0.5
     assert a["mixed_solves_fallen_back_to_fp64"] == 1 and a["mixed_solves_uncertified"] == 1
+
+
+def test_solve_distribution_summarises_each_level():
+    recs = [{"level": lv, "subdomain": s, "cells": 100, "centres": 32 + lv, "support": s % 7,
+             "active_set_steps": s % 5, "refinement_passes": s % 2, "flags": int(s == 3 and lv == 1)}
+            for lv in (0, 1) for s in range(10)]
+    d = bench.solve_distribution(recs)
+    assert set(d) == {"level0", "level1"}
+    assert d["level0"]["solves"] == 10 and d["level1"]["flagged"] == 1 and d["level0"]["flagged"] == 0
+    assert d["level1"]["centres"] == {"p50": 33.0, "p90": 33.0, "max": 33.0}
+    assert d["level0"]["support"]["max"] == 6.0 and d["level0"]["active_set_steps"]["p50"] == 2.0
