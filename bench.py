@@ -93,6 +93,57 @@ def barrier(ws: int):
         dist.barrier()
 
 
+def shard_ranges(costs, world: int):
+    """Contiguous blocks of subdomains, one per rank, with about equal
+    estimated cost (the prefix sums cut nearest to k/world of the total;
+    section 2's subdomains are independent, so a rank fits its block alone):
+    [(begin, end)] * world, covering every subdomain exactly once."""
+    c = np.concatenate([[0.0], np.cumsum(np.asarray(costs, dtype=float))])
+    S = len(c) - 1
+    cuts = [0]
+    for k in range(1, world):
+        target = c[-1] * k / world
+        i = int(np.searchsorted(c, target))
+        i = min(max(i, 1), S)
+        if abs(c[i - 1] - target) < abs(c[i] - target):
+            i -= 1
+        cuts.append(max(i, cuts[-1]))
+    cuts.append(S)
+    return [(cuts[k], cuts[k + 1]) for k in range(world)]
+
+
+def shard_costs(W):
+    """Estimated cost of each subdomain: N_i M_cap^2, N_i its patch cells and
+    M_cap the dictionary cap after the planned levels (the fit's Gram and
+    solve scale with N M^2; the final M_i are not known before the fit)."""
+    boxes = _patch_boxes(W)
+    n = np.prod(boxes[:, 9:12] - boxes[:, 6:9], axis=1).astype(float)
+    dim = len(W["shape"])
+    m_cap = int(np.prod(W["g"])) + W["params"]["levels"] * (dim + 1) * W["params"]["k_top"]
+    return n * float(m_cap) ** 2
+
+
+def _patch_boxes(W):
+    """Core and patch boxes [S, 12] of a workload (half-open cores, overlap clipped)."""
+    shape, n_sub, ov = W["shape"], W["n_sub"], W["overlap"]
+    dim = len(shape)
+    S = int(np.prod(n_sub))
+    boxes = np.zeros((S, 12), dtype=np.int64)
+    for sidx in range(S):
+        j, rem = [], sidx
+        for a in range(dim):
+            j.append(rem % n_sub[a])
+            rem //= n_sub[a]
+        for a in range(3):
+            if a < dim:
+                n, p = shape[a], n_sub[a]
+                lo, hi = (j[a] * n) // p, ((j[a] + 1) * n) // p
+                boxes[sidx, [a, 3 + a, 6 + a, 9 + a]] = [lo, hi, max(lo - ov, 0), min(hi + ov, n)]
+            else:
+                boxes[sidx, [a, 3 + a, 6 + a, 9 + a]] = [0, 1, 0, 1]
+    return boxes
+
+
 def shard_seed(base_seed: int, rank: int) -> int:
     """Each rank fits its own field: weak scaling over independent problems."""
     return base_seed + 1000 * rank
@@ -342,6 +393,89 @@ def dictionary_agreement(pam, mixed, plain):
             "mixed_solves_uncertified": int(np.count_nonzero(flags & pam.FLAG_NOT_CERTIFIED))}
 
 
+def combine_error_sums(sums, ws):
+    """The shards' raw error sums (pam_error_sums, a tensor [8]) added over the
+    ranks, the maximum taken for entry 6: the one collective of a sharded
+    field (section 8(e)), a handful of scalars after the step."""
+    if ws == 1:
+        return sums
+    import torch
+    import torch.distributed as dist
+    top = sums[6:7].clone()
+    dist.all_reduce(sums, op=dist.ReduceOp.SUM)
+    dist.all_reduce(top, op=dist.ReduceOp.MAX)
+    sums[6] = top[0]
+    return sums
+
+
+def run_field_shard(args, rank, ws):
+    """One field split over the ranks: rank r fits the contiguous block of
+    subdomains shard_ranges gives it (pam_params.sub_begin/sub_end), evaluates
+    the target points its block owns and reduces its error sums; the sums are
+    added over the ranks after the timed steps. Strong scaling: the whole
+    job's work is fixed."""
+    import torch
+    from paper_2605_16564_gb300 import build, pam
+    build.build()
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    W = WORKLOADS[args.workload]
+    if W.get("mesh"):
+        raise SystemExit("--shard field: grid workloads only")
+    K, _, _ = workload_data(W, W["seed"])  # the same field on every rank
+    b, e = shard_ranges(shard_costs(W), ws)[rank]
+    h = fields.cell_size(W["shape"])
+    pts = fields.cell_centred_points(W["eval_counts"], [n * h for n in W["shape"]])
+    own = owner_index(W, pts)
+    mine = np.ascontiguousarray(pts[(own >= b) & (own < e)])
+    prec = pam.PAM_PREC_MIXED if (args.precision in ("auto", "mixed") and _mixed_available(pam)) \
+        else pam.PAM_PREC_FP64
+    fit = make_fitter(pam, W, None, None, dev, precision=prec, sub_range=(b, e), **W["params"])
+    Kd = torch.from_numpy(np.ascontiguousarray(K)).to(dev)
+    ptsd = torch.from_numpy(mine).to(dev)
+    out = torch.empty(max(len(mine), 1), dtype=torch.float64, device=dev)
+    sums = torch.zeros(8, dtype=torch.float64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+
+    def step():
+        fit.fit(Kd, deferred=True)
+        if len(mine):
+            fit.eval(ptsd, out=out[:len(mine)])
+        pam.pam_error_sums(fit.problem, fit.plan, fit.model, Kd, sums, (b, e), fit.workspace, prec)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if fit.status() not in (0,):
+        raise SystemExit(f"rank {rank}: fit status {fit.status()}")
+    times = []
+    for _ in range(args.steps):
+        flush.fill_(1)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier(ws)
+        torch.cuda.synchronize()
+        e0.record()
+        step()
+        e1.record()
+        torch.cuda.synchronize()
+        times.append(e0.elapsed_time(e1))
+    ms = max_over_ranks(sum(times) / len(times), ws, dev)
+    tot = combine_error_sums(sums, ws).cpu().numpy()
+    if rank != 0:
+        return
+    err = pam.error_measures_from_sums(tot)
+    n_cells = int(np.prod(W["shape"]))
+    line = {"metric": METRIC, "value": n_cells / (ms / 1e3), "unit": "cells/s", "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
+            "vs_baseline": None, "dtype": "bf16x3+f32+f64" if prec == pam.PAM_PREC_MIXED else "f64",
+            "data": "synthetic",
+            "config": {"workload": args.workload, "parallelism": f"one field, {ws} contiguous subdomain blocks",
+                       "ranges_rank0": [b, e], "l2_flush": "256 MB buffer written between timed steps",
+                       "launch": "eager"},
+            "l1_rel": err["l1"], "l2_rel": err["l2"], "gpu_launches": None}
+    print(json.dumps(line))
+
+
 def make_fitter(pam, W, x, vol, dev, **params):
     if x is not None:
         return pam.CellFitter(W["shape"], W["n_sub"], W["overlap"], W["g"], x, vol, device=dev, **params)
@@ -399,14 +533,16 @@ def run_pam(args, rank, ws):
         learned = {"kind": "learned (PAM_NN_LAYERED3D network seeds the level-0 active set)",
                    "train_fields": 8, "train_samples": 8 * fit.plan.n_subdomains, "train_s": round(train_s, 2),
                    "seed_threshold": lw.threshold,
-                   "inference_stream": "a side stream beside the level-0 partition, cell data and Gram "
-                                       "products; the level-0 solve waits on its event",
+                   "inference_stream": "a high-priority side stream beside the level-0 partition, cell data "
+                                       "and Gram products; the level-0 solve waits on its event",
                    "level0_active_set_steps_cold": round(cold_it, 3),
                    "level0_active_set_steps_learned": round(warm_it, 3)}
 
     # the inference runs on a side stream beside the level-0 partition, cell
-    # data and Gram products; the level-0 solve waits for its event
-    seed_stream = torch.cuda.Stream(device=dev) if lw is not None else None
+    # data and Gram products; the level-0 solve waits for its event. The
+    # stream has the high priority, so that the network's small kernels are
+    # scheduled ahead of the set-up kernels they run beside
+    seed_stream = torch.cuda.Stream(device=dev, priority=-1) if lw is not None else None
     seeded = torch.cuda.Event() if lw is not None else None
 
     def fit_step(deferred=False):
@@ -915,6 +1051,9 @@ def main():
                     help="also time the per-subdomain 3-fold cross-validation of 3 lambda pairs (binary64)")
     ap.add_argument("--no-graph", action="store_true", help="time eager launches instead of a CUDA graph replay")
     ap.add_argument("--no-autotune", action="store_true", help="keep the built-in launch tuning")
+    ap.add_argument("--shard", choices=["replicas", "field"], default="replicas",
+                    help="replicas: every rank fits its own field (weak scaling, the default); field: one "
+                         "field's subdomains split into contiguous blocks over the ranks (strong scaling)")
     ap.add_argument("--metrics-log", default=None,
                     help="write one JSON line per subdomain and level (cells, centres, support, "
                          "active-set steps, refinement passes, flags) of the step's fit to this file")
@@ -971,6 +1110,9 @@ def main():
         print(json.dumps(line))
         return
 
+    if args.shard == "field":
+        run_field_shard(args, rank, ws)
+        return
     r = run_pam(args, rank, ws)
     if rank != 0:
         return

@@ -136,6 +136,15 @@ typedef struct {
                             zeroes the coefficients of a patch without elements). Ignored
                             otherwise and by the other calls. An invalid event gives
                             PAM_ERR_CUDA. */
+    /* pam_fit_subdomains / pam_fit_cells: fit only the subdomains [sub_begin,
+       sub_end) (0, 0 = all). The others get the initial lattice with beta = 0
+       and are marked stopped (info STOPPED = 1): no solve, no refinement. One
+       field sharded over several GPUs (section 2's subdomains are independent):
+       each rank fits a contiguous range, evaluates the points its range owns
+       and adds up the sums of pam_error_sums. PAM_ERR_INVALID_ARG unless
+       0 <= sub_begin <= sub_end <= S. */
+    int sub_begin;
+    int sub_end;
 } pam_params;
 
 /* Sizes derived from a problem and parameters by pam_plan_create. */
@@ -367,6 +376,22 @@ pam_status pam_errors(const pam_problem *prob, const pam_plan *plan,
                       void *stream);
 
 /*
+ * The sums behind pam_errors over the cells owned by the subdomains
+ * [sub_begin, sub_end) only, for one field sharded over several GPUs
+ * (section 2: the subdomains are independent; each rank fits its range with
+ * pam_params.sub_begin/sub_end): d_sums (device double [8]) receives
+ * sum |K - K*|, sum |K|, sum (K - K*)^2, sum K^2, sum |ln K - ln K*|,
+ * sum |ln K|, max |ln K - ln K*| and 0. Added over the ranks (the maximum
+ * taken for entry 6) they give pam_errors' measures: L1 = s0 / s1,
+ * L2 = sqrt(s2 / s3), log-L1 = s4 / s5, max log10 = s6 / ln 10. Arguments
+ * and workspace as pam_errors; PAM_ERR_INVALID_ARG unless
+ * 0 <= sub_begin <= sub_end <= S. Asynchronous.
+ */
+pam_status pam_error_sums(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
+                          const double *d_K, double *d_sums, int precision, int quad, int sub_begin,
+                          int sub_end, void *d_workspace, size_t workspace_bytes, void *stream);
+
+/*
  * pam_errors without a workspace and without allocating device memory.
  * The paper has no counterpart: this exists for callers that cannot
  * allocate on the GPU or hand the library scratch space -- host programs
@@ -577,8 +602,11 @@ pam_status pam_nn_adamw(float *d_params, const float *d_grads, float *d_m, float
  * pam_resume, and the indicators rewritten), then the block sizes on
  * pam_eval of d_pts [n_pts][dim] into d_out [n_pts] (skipped when n_pts ==
  * 0; d_eval_workspace as for pam_eval), then the solve's launch {0, 1}. The
- * binary64 form tunes the evaluation only. The fastest candidates become
- * the process tuning and *out; h_ms (optional, [14]) receives the medians in
+ * binary64 form tunes the evaluation only. Within each choice a candidate
+ * replaces the built-in (or the candidate kept so far) only when it measures
+ * at least 2 % faster (equivalent launches differ by about 1 % between
+ * runs); the choices become the process tuning and *out (eval_block 0 when
+ * the built-in 256 is kept); h_ms (optional, [14]) receives the medians in
  * ms in that order (stages 3, 2; budgets; blocks; launches), -1 where a
  * candidate was not run.
  * Synchronises `stream`; not to be captured in a CUDA graph.

@@ -839,7 +839,9 @@ __global__ void __launch_bounds__(kErrThreads) k_errors_owner(Geo g, const int32
 
 // Sums the per-owner rows in a fixed order: thread t adds the contiguous
 // rows [t*per, (t+1)*per) in order, then a fixed tree over the threads.
-__global__ void __launch_bounds__(256) k_errors_combine(const double *part, int rows, double *err) {
+// raw = 1: err[0..6] receive the seven sums themselves (err[7] = 0), for a
+// caller that adds them up over several shards before forming the ratios.
+__global__ void __launch_bounds__(256) k_errors_combine(const double *part, int rows, double *err, int raw) {
     __shared__ double red[7][256];
     const int t = threadIdx.x;
     const int per = (rows + 255) / 256;
@@ -855,7 +857,10 @@ __global__ void __launch_bounds__(256) k_errors_combine(const double *part, int 
                 red[q][t] = (q == 6) ? fmax(red[q][t], red[q][t + o]) : red[q][t] + red[q][t + o];
         __syncthreads();
     }
-    if (t == 0) {
+    if (t == 0 && raw) {
+        for (int q = 0; q < 7; ++q) err[q] = red[q][0];
+        err[7] = 0.0;
+    } else if (t == 0) {
         err[0] = red[0][0] / red[1][0];
         err[1] = sqrt(red[2][0] / red[3][0]);
         err[2] = red[5][0] > 0.0 ? red[4][0] / red[5][0] : red[4][0];
@@ -865,7 +870,7 @@ __global__ void __launch_bounds__(256) k_errors_combine(const double *part, int 
 
 void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
                    const int32_t *info, const double *K, double *err, int precision, int quad,
-                   const Ws &w, cudaStream_t st) {
+                   const Ws &w, cudaStream_t st, int row0, int row1) {
     PhaseScope ps(kPhErrors, st);
     if (precision == PAM_PREC_MIXED) {
         size_t sm = stage_f32_smem(g.m_cap);
@@ -876,7 +881,10 @@ void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, co
         cudaFuncSetAttribute(k_errors_owner<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_errors_owner<false><<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, quad, w.err_part);
     }
-    k_errors_combine<<<1, 256, 0, st>>>(w.err_part, g.S, err);
+    if (row1 < 0)  // the ratios over every subdomain
+        k_errors_combine<<<1, 256, 0, st>>>(w.err_part, g.S, err, 0);
+    else           // the raw sums over the subdomains [row0, row1)
+        k_errors_combine<<<1, 256, 0, st>>>(w.err_part + (size_t)row0 * 8, row1 - row0, err, 1);
     count_launches(2);
 }
 
@@ -954,7 +962,7 @@ void launch_errors_cells(const Geo &g, const int32_t *boxes, const double *centr
         cudaFuncSetAttribute(k_errors_cells<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_errors_cells<false><<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, w.err_part);
     }
-    k_errors_combine<<<1, 256, 0, st>>>(w.err_part, g.S, err);
+    k_errors_combine<<<1, 256, 0, st>>>(w.err_part, g.S, err, 0);
     count_launches(2);
 }
 

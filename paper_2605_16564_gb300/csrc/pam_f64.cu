@@ -170,7 +170,8 @@ __global__ void k_init_dictionary(Geo g, const int32_t *boxes, double *centres, 
         inf[PAM_INFO_ITERS] = 0;
         inf[PAM_INFO_FLAGS] = 0;
         const int n_cells = g.cells ? g.pstart[s + 1] - g.pstart[s] : ext[0] * ext[1] * ext[2];
-        inf[PAM_INFO_STOPPED] = n_cells == 0 ? 1 : 0;  // nothing to fit: no solve, no refinement
+        // nothing to fit, or outside the range this call fits: no solve, no refinement
+        inf[PAM_INFO_STOPPED] = (n_cells == 0 || s < g.sub_lo || s >= g.sub_hi) ? 1 : 0;
         inf[PAM_INFO_N_CELLS] = n_cells;
         inf[PAM_INFO_MARKED] = 0;
     }

@@ -29,6 +29,7 @@ struct Geo {
     int n_max;      // max patch cells (padded stride of per-cell arrays)
     int m0, m_cap;
     int prec;       // pam_precision of the fit calls (sizes the workspace)
+    int sub_lo, sub_hi;  // the subdomains a fit solves (the others start stopped)
     // a general mesh given as cells (section 2: elements with a sampling
     // point, a value and a measure); all NULL / 0 for a structured grid
     int cells;               // 1: the patches are element lists
@@ -104,8 +105,10 @@ void launch_init_dictionary(const Geo &g, const int32_t *boxes, double *centres,
 void launch_solve_level_f64(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
                             double *beta, int32_t *info, const Ws &w, cudaStream_t st,
                             cudaEvent_t before_solve = nullptr);
+// m_bound: an upper bound on every dictionary size of the launch (0: the
+// capacity); at most 64 takes the CUDA-core Gram of the initial lattices.
 void launch_stats_gram_tc(const Geo &g, const int32_t *boxes, const double *centres,
-                          const int32_t *info, const Ws &w, cudaStream_t st, int all);
+                          const int32_t *info, const Ws &w, cudaStream_t st, int all, int m_bound = 0);
 void launch_assemble_gram_f64(const Geo &g, const int32_t *boxes, const double *centres,
                               const int32_t *info, const Ws &w, cudaStream_t st, int all);
 void launch_bgram_f64(const Geo &g, const int32_t *info, const Ws &w, cudaStream_t st, int all, int folds,
@@ -127,7 +130,7 @@ void launch_copy_gram_f64(const Geo &g, const int32_t *info, const Ws &w, double
                           double *b_out, cudaStream_t st);
 void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
                               double *beta, int32_t *info, const Ws &w, cudaStream_t st,
-                              cudaEvent_t before_solve = nullptr);
+                              cudaEvent_t before_solve = nullptr, int m_bound = 0);
 void launch_refine_round(const Geo &g, const Par &p, int precision, const int32_t *boxes,
                          double *centres, double *beta, int32_t *info, const Ws &w, cudaStream_t st);
 void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
@@ -140,7 +143,7 @@ void launch_eval_glued(const Geo &g, const int32_t *boxes, const double *centres
 size_t glue_workspace_bytes(int S, int dim, int64_t n_pts);
 void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
                    const int32_t *info, const double *K, double *err, int precision, int quad,
-                   const Ws &w, cudaStream_t st);
+                   const Ws &w, cudaStream_t st, int row0 = 0, int row1 = -1);
 void launch_residual_quad(const Geo &g, int precision, const int32_t *boxes, const double *centres,
                           const double *beta, const int32_t *info, const Ws &w, cudaStream_t st);
 bool mixed_solve_fits(const Geo &g);

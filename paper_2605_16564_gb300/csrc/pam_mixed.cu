@@ -536,6 +536,109 @@ static size_t gram_tc_smem(const Geo &g, int stages) {
     return tiles + Rcap * sizeof(float4) + 8 * Rcap * sizeof(float) + cells * (sizeof(float4) + sizeof(float));
 }
 
+// --------------------------------------------------------------------------
+// Gram products of a small dictionary (M <= kSmallGramM: the initial
+// lattices) on the CUDA cores. At such sizes the contraction is too thin for
+// the tensor cores (one 128-row strip of N <= 64 columns per k-step: the
+// tcgen05 pipeline's set-up and per-instruction cost dominate), so one block
+// of 256 threads per subdomain generates W in chunks of 32 cells into shared
+// memory, with the same exponent as the tensor-core Gram (the Shepard
+// normaliser folded in: W = 2^(l - sh)), and accumulates the upper triangle
+// of W^T W in fp32, nine entries per thread at most, plus b = W^T y and the
+// weight sums. Products are exact fp32 (no bf16 split), so G~ is at least as
+// accurate as the tensor-core one.
+// --------------------------------------------------------------------------
+constexpr int kSmallGramM = 64;
+constexpr int kSgThreads = 256;
+constexpr int kSgSlots = (kSmallGramM * (kSmallGramM + 1) / 2 + kSgThreads - 1) / kSgThreads;  // 9
+
+__global__ void __launch_bounds__(kSgThreads) k_gram_small(Geo g, const int32_t *boxes, const double *centres,
+                                                          const int32_t *info, Ws w, int all) {
+    const int s = blockIdx.x;
+    const int32_t *inf = info + s * kInfoN;
+    if (!all && inf[PAM_INFO_STOPPED]) return;
+    const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
+    if (M > kSmallGramM) return;  // never: the launch is sized by the host's bound
+    const int tid = threadIdx.x;
+    const int32_t *box = boxes + s * 12;
+    __shared__ float4 sc[kSmallGramM];
+    __shared__ float Wt[kTcKC][kSmallGramM];
+    extern __shared__ float4 cxa[];  // [nch * 32] (x, y, z, sh) of every patch cell, then ln K
+    const int nch = (N + kTcKC - 1) / kTcKC;
+    float *cya = reinterpret_cast<float *>(cxa + (size_t)nch * kTcKC);
+    double o[3];
+    patch_origin(g, box, o);
+    const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
+    for (int m = tid; m < M; m += blockDim.x) sc[m] = local_centre(cg[m], o);
+    // this thread's entries (i, j), j >= i, of the upper triangle
+    const int T = M * (M + 1) / 2;
+    int ei[kSgSlots], ej[kSgSlots];
+    float acc[kSgSlots];
+#pragma unroll
+    for (int q = 0; q < kSgSlots; ++q) {
+        const int e = tid + q * kSgThreads;
+        int i = 0, rem = e;  // row-major over the upper triangle: row i holds M - i entries
+        while (i < M && rem >= M - i) { rem -= M - i; ++i; }
+        ei[q] = e < T ? i : 0;
+        ej[q] = e < T ? i + rem : 0;
+        acc[q] = 0.f;
+    }
+    const float *rowmax = w.rowmax + (size_t)s * g.n_max;
+    const float *rowinv = w.rowinv + (size_t)s * g.n_max;
+    const double *yv = w.y + (size_t)s * g.n_max;
+    // every cell's point, shift and ln K in shared memory once (the chunks
+    // below touch no global memory)
+    for (int t = tid; t < nch * kTcKC; t += blockDim.x) {
+        float x[3] = {0.f, 0.f, 0.f};
+        float sh = INFINITY, y = 0.f;
+        if (t < N) {
+            local_cell(g, s, box, t, x);
+            sh = rowmax[t] - log2f(rowinv[t]);
+            y = (float)yv[t];
+        }
+        cxa[t] = make_float4(x[0], x[1], x[2], sh);
+        cya[t] = y;
+    }
+    float bacc = 0.f, wacc = 0.f;
+    for (int t0 = 0; t0 < N; t0 += kTcKC) {
+        __syncthreads();  // the cells are staged; the previous chunk's readers are done
+        const float4 *cx = cxa + t0;
+        const float *cy = cya + t0;
+        for (int p = tid; p < kTcKC * M; p += blockDim.x) {
+            const int t = p / M, m = p - t * M;
+            const float4 c = cx[t];
+            Wt[t][m] = tc::ex2(logit2(sc[m], c.x, c.y, c.z) - c.w);  // 0 past the patch (sh = inf)
+        }
+        __syncthreads();
+        if (tid < M) {
+            for (int t = 0; t < kTcKC; ++t) {
+                bacc = fmaf(Wt[t][tid], cy[t], bacc);
+                wacc += Wt[t][tid];
+            }
+        }
+#pragma unroll
+        for (int q = 0; q < kSgSlots; ++q) {
+            if (tid + q * kSgThreads < T) {
+                float a = acc[q];
+                for (int t = 0; t < kTcKC; ++t) a = fmaf(Wt[t][ei[q]], Wt[t][ej[q]], a);
+                acc[q] = a;
+            }
+        }
+    }
+    float *G = w.Gf + (size_t)s * g.m_cap * g.m_cap;
+#pragma unroll
+    for (int q = 0; q < kSgSlots; ++q) {
+        if (tid + q * kSgThreads < T) {
+            G[(size_t)ei[q] * g.m_cap + ej[q]] = acc[q];
+            G[(size_t)ej[q] * g.m_cap + ei[q]] = acc[q];
+        }
+    }
+    if (tid < M) {
+        w.b[(size_t)s * g.m_cap + tid] = (double)bacc;
+        w.wsum[(size_t)s * g.m_cap + tid] = wacc;
+    }
+}
+
 void launch_gram_tc(const Geo &g, const int32_t *boxes, const double *centres, const int32_t *info,
                     const Ws &w, cudaStream_t st, int all, int folds, int fold) {
     PhaseScope ps(kPhGramTC, st);
@@ -563,8 +666,17 @@ void launch_stats_f32(const Geo &g, const int32_t *boxes, const double *centres,
 }
 
 void launch_stats_gram_tc(const Geo &g, const int32_t *boxes, const double *centres,
-                          const int32_t *info, const Ws &w, cudaStream_t st, int all) {
+                          const int32_t *info, const Ws &w, cudaStream_t st, int all, int m_bound) {
     launch_stats_f32(g, boxes, centres, info, w, st, all);
+    const size_t sm = (size_t)((g.n_max + kTcKC - 1) / kTcKC) * kTcKC * (sizeof(float4) + sizeof(float));
+    if (m_bound > 0 && m_bound <= kSmallGramM && sm + 16 * 1024 <= kSmemLimit) {
+        // every dictionary is at most m_bound centres (the initial lattices)
+        PhaseScope ps(kPhGramTC, st);
+        cudaFuncSetAttribute(k_gram_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_gram_small<<<g.S, kSgThreads, sm, st>>>(g, boxes, centres, info, w, all);
+        count_launches(1);
+        return;
+    }
     launch_gram_tc(g, boxes, centres, info, w, st, all, 0, 0);
 }
 
@@ -1330,8 +1442,8 @@ void launch_solve_mixed(const Geo &g, const Par &p, const int32_t *boxes, const 
 
 void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes,
                               const double *centres, double *beta, int32_t *info, const Ws &w,
-                              cudaStream_t st, cudaEvent_t before_solve) {
-    launch_stats_gram_tc(g, boxes, centres, info, w, st, 0);
+                              cudaStream_t st, cudaEvent_t before_solve, int m_bound) {
+    launch_stats_gram_tc(g, boxes, centres, info, w, st, 0, m_bound);
     if (before_solve) cudaStreamWaitEvent(st, before_solve, 0);  // an error surfaces in cudaGetLastError
     launch_solve_mixed(g, p, boxes, centres, beta, info, w, nullptr, 0, nullptr, 0, st, 1);
 }

@@ -37,7 +37,7 @@ EXPORTED = ["pam_version", "pam_status_string", "pam_plan_create", "pam_partitio
             "pam_eval_glued_workspace_size", "pam_eval_glued", "pam_partition_cells", "pam_plan_create_cells",
             "pam_fit_cells", "pam_refine_cells", "pam_errors_cells", "pam_model_save", "pam_model_load",
             "pam_resume", "pam_resume_cells", "pam_tuning_set", "pam_tuning_get", "pam_autotune",
-            "pam_autotune_cells", "pam_selftest_wait"]
+            "pam_autotune_cells", "pam_selftest_wait", "pam_error_sums"]
 
 
 class PamError(RuntimeError):
@@ -56,7 +56,8 @@ class pam_params(C.Structure):
                 ("eps_tol_rel", C.c_double), ("eta", C.c_double), ("k_top", C.c_int),
                 ("m_max", C.c_int), ("levels", C.c_int), ("max_iters", C.c_int),
                 ("precision", C.c_int), ("warm_start", C.c_int), ("quad", C.c_int),
-                ("deferred_status", C.c_int), ("warm_start_event", C.c_void_p)]
+                ("deferred_status", C.c_int), ("warm_start_event", C.c_void_p), ("sub_begin", C.c_int),
+                ("sub_end", C.c_int)]
 
 
 class pam_plan(C.Structure):
@@ -144,6 +145,9 @@ def lib():
                                      C.c_void_p]
         L.pam_errors.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_void_p,
                                  C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_error_sums.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p, C.c_void_p,
+                                     C.c_int, C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
+        L.pam_error_sums.restype = C.c_int
         L.pam_gram.argtypes = [P(pam_problem), P(pam_params), P(pam_plan), C.c_void_p, P(pam_model),
                                C.c_void_p, C.c_void_p, C.c_void_p, C.c_size_t, C.c_void_p]
         L.pam_nn_sizes.argtypes = [C.c_int, C.c_int, P(C.c_int64), P(C.c_size_t)]
@@ -211,12 +215,14 @@ def make_problem(n_cells, n_sub, overlap, g_init):
 
 def make_params(lambda1_hat=4.59e-4, lambda2_hat=4.64e-6, eps_tol_rel=1e-3, eta=0.5, k_top=37,
                 m_max=1 << 30, levels=3, max_iters=0, precision=PAM_PREC_FP64, warm_start=0, quad=0,
-                deferred_status=0):
+                deferred_status=0, sub_range=None):
     """quad: quadrature of the indicators R_T, 0 midpoint, 1 two-point Gauss-Legendre per axis.
     deferred_status: 1 = the fit calls never synchronise the host (read the
     status with pam_status_read), so they can be captured in a CUDA graph."""
     p = pam_params()
     p.warm_start = warm_start
+    if sub_range is not None:  # fit only the subdomains [begin, end) (a shard of one field)
+        p.sub_begin, p.sub_end = int(sub_range[0]), int(sub_range[1])
     p.quad = quad
     p.deferred_status = deferred_status
     p.lambda1_hat, p.lambda2_hat, p.eps_tol_rel, p.eta = lambda1_hat, lambda2_hat, eps_tol_rel, eta
@@ -330,6 +336,22 @@ def pam_errors(problem, plan, model, K, err, workspace, precision=PAM_PREC_FP64,
     _check(lib().pam_errors(C.byref(problem), C.byref(plan), C.byref(model.c_struct()), _ptr(K),
                             _ptr(err), int(precision), int(quad), _ptr(workspace),
                             workspace.numel() * workspace.element_size(), _stream(stream)), "pam_errors")
+
+
+def pam_error_sums(problem, plan, model, K, sums, sub_range, workspace, precision=PAM_PREC_FP64, stream=None,
+                   quad=0):
+    """The seven raw sums of the error measures over the cells owned by the
+    subdomains [begin, end) into the device tensor sums [8] (a shard's share)."""
+    _check(lib().pam_error_sums(C.byref(problem), C.byref(plan), C.byref(model.c_struct()), _ptr(K), _ptr(sums),
+                                int(precision), int(quad), int(sub_range[0]), int(sub_range[1]), _ptr(workspace),
+                                workspace.numel() * workspace.element_size(), _stream(stream)), "pam_error_sums")
+
+
+def error_measures_from_sums(s):
+    """pam_errors' four measures from the (summed) raw sums [8] (host array)."""
+    import math
+    return dict(l1=s[0] / s[1], l2=math.sqrt(s[2] / s[3]), l1_log=(s[4] / s[5]) if s[5] > 0 else s[4],
+                max_log10=s[6] / math.log(10.0))
 
 
 def pam_errors_noalloc(problem, plan, model, K, err, stream=None):

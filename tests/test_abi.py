@@ -339,7 +339,7 @@ def test_binding_struct_layouts_match_the_library(pam):
                                   pam.pam_cells, pam.pam_tuning)]
     assert list(out) == mine
     # pam_params: 4 doubles, 8 ints, the warm-start event pointer
-    assert C.sizeof(pam.pam_params) == 4 * 8 + 8 * 4 + 8
+    assert C.sizeof(pam.pam_params) == 4 * 8 + 8 * 4 + 8 + 2 * 4  # ..., the event, the subdomain range
     assert pam.pam_params.warm_start_event.offset == 64
 
 
@@ -370,3 +370,21 @@ def test_eval_to_host_checks_its_buffers_before_any_launch(pam):
         pam.Fitter.eval_to_host(None, pts, out, torch.zeros(10, dtype=torch.float64))
     with pytest.raises(ValueError):
         pam.Fitter.eval_to_host(None, pts, out.float(), torch.zeros(10, dtype=torch.float32))
+
+
+def test_subdomain_range_and_error_sums_are_checked(pam):
+    prob = pam.make_problem((32, 32), (2, 2), 1, (3, 3))
+    for bad in ((-1, 2), (3, 2), (0, 5)):
+        with pytest.raises(pam.PamError):
+            pam.pam_plan_create(prob, pam.make_params(k_top=2, levels=1, sub_range=bad))
+    plan = pam.pam_plan_create(prob, pam.make_params(k_top=2, levels=1, sub_range=(1, 3)))
+    assert plan.n_subdomains == 4
+    import ctypes as C
+    m = pam.pam_model()
+    for bad in ((-1, 2), (3, 2), (0, 5)):
+        code = pam.lib().pam_error_sums(C.byref(prob), C.byref(plan), C.byref(m), None, None, 0, 0, bad[0], bad[1],
+                                        None, 0, None)
+        assert code == pam.PAM_ERR_INVALID_ARG
+    s = np.array([6.0, 12.0, 8.0, 32.0, 3.0, 6.0, np.log(10.0) * 0.5, 0.0])
+    e = pam.error_measures_from_sums(s)
+    assert e == dict(l1=0.5, l2=0.5, l1_log=0.5, max_log10=pytest.approx(0.5))
