@@ -561,6 +561,15 @@ pam_status pam_nn_gradients(int arch, const float *d_params, const float *d_x, c
 pam_status pam_nn_layered_inputs(const pam_problem *prob, const pam_plan *plan, const double *d_K,
                                  float *d_x, int n_rows, void *stream);
 /*
+ * The same for either network: arch PAM_NN_LAYERED3D as above, or
+ * PAM_NN_PATCH2D for a 2-D problem whose patches are at most 32 x 32 cells
+ * (d_x [n_rows][32][32][1], entry [iy][ix] = clip(log10 K / 3, -1, 1) at patch
+ * cell (ix, iy), zero outside the patch and in rows s >= S): the learned warm
+ * start's inputs gathered on the device from the field itself.
+ */
+pam_status pam_nn_inputs(int arch, const pam_problem *prob, const pam_plan *plan, const double *d_K, float *d_x,
+                         int n_rows, void *stream);
+/*
  * Seeds the active set from a network output d_out [>= S][2 n_out]: for
  * every subdomain s and initial dictionary entry j < n_out,
  * model->beta[s][j] = b if |b| > threshold else 0, b = 4 d_out[s][n_out + j]

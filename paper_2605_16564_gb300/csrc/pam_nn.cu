@@ -650,14 +650,18 @@ pam_status pam_nn_gradients(int arch, const float *d_params, const float *d_x, c
     return PAM_OK;
 }
 
-pam_status pam_nn_layered_inputs(const pam_problem *prob, const pam_plan *plan, const double *d_K, float *d_x,
-                                 int n_rows, void *stream) {
-    if (!prob || !plan || !d_K || !d_x) return PAM_ERR_INVALID_ARG;
+pam_status pam_nn_inputs(int arch, const pam_problem *prob, const pam_plan *plan, const double *d_K, float *d_x,
+                         int n_rows, void *stream) {
+    const Arch *Ap = arch_of(arch);
+    if (!Ap || !prob || !plan || !d_K || !d_x) return PAM_ERR_INVALID_ARG;
     pam::Geo g;
     pam_status st;
     if (!pam::make_geo(prob, nullptr, &g, nullptr, &st)) return st;
-    if (g.dim != 3 || plan->n_subdomains != g.S || n_rows < g.S) return PAM_ERR_INVALID_ARG;
-    const Arch &A = kArch[PAM_NN_LAYERED3D];
+    // 2-D patches as pixels (one channel), layered 3-D patches with the z
+    // layers as channels
+    const int want_dim = arch == PAM_NN_LAYERED3D ? 3 : 2;
+    if (g.dim != want_dim || plan->n_subdomains != g.S || n_rows < g.S) return PAM_ERR_INVALID_ARG;
+    const Arch &A = *Ap;
     // every patch must fit the input grid: widest patch per axis
     const int lim[3] = {A.h0, A.h0, A.c0};
     for (int a = 0; a < 3; ++a) {
@@ -672,6 +676,11 @@ pam_status pam_nn_layered_inputs(const pam_problem *prob, const pam_plan *plan, 
     pam::count_launches(1);
     PAM_CUDA_TRY(cudaGetLastError());
     return PAM_OK;
+}
+
+pam_status pam_nn_layered_inputs(const pam_problem *prob, const pam_plan *plan, const double *d_K, float *d_x,
+                                 int n_rows, void *stream) {
+    return pam_nn_inputs(PAM_NN_LAYERED3D, prob, plan, d_K, d_x, n_rows, stream);
 }
 
 pam_status pam_nn_seed(const pam_plan *plan, int arch, const float *d_out, float threshold, pam_model *model,

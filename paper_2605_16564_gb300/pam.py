@@ -37,7 +37,7 @@ EXPORTED = ["pam_version", "pam_status_string", "pam_plan_create", "pam_partitio
             "pam_eval_glued_workspace_size", "pam_eval_glued", "pam_partition_cells", "pam_plan_create_cells",
             "pam_fit_cells", "pam_refine_cells", "pam_errors_cells", "pam_model_save", "pam_model_load",
             "pam_resume", "pam_resume_cells", "pam_tuning_set", "pam_tuning_get", "pam_autotune",
-            "pam_autotune_cells", "pam_selftest_wait", "pam_error_sums"]
+            "pam_autotune_cells", "pam_selftest_wait", "pam_error_sums", "pam_nn_inputs"]
 
 
 class PamError(RuntimeError):
@@ -162,8 +162,10 @@ def lib():
         L.pam_nn_layered_inputs.argtypes = [P(pam_problem), P(pam_plan), C.c_void_p, C.c_void_p, C.c_int,
                                             C.c_void_p]
         L.pam_nn_seed.argtypes = [P(pam_plan), C.c_int, C.c_void_p, C.c_float, P(pam_model), C.c_void_p]
+        L.pam_nn_inputs.argtypes = [C.c_int, P(pam_problem), P(pam_plan), C.c_void_p, C.c_void_p, C.c_int,
+                                    C.c_void_p]
         for name in ("pam_nn_sizes", "pam_nn_geometry", "pam_nn_layer_offsets", "pam_nn_forward",
-                     "pam_nn_gradients", "pam_nn_adamw", "pam_nn_layered_inputs", "pam_nn_seed"):
+                     "pam_nn_gradients", "pam_nn_adamw", "pam_nn_layered_inputs", "pam_nn_seed", "pam_nn_inputs"):
             getattr(L, name).restype = C.c_int
         L.pam_errors_noalloc.argtypes = [P(pam_problem), P(pam_plan), P(pam_model), C.c_void_p,
                                          C.c_void_p, C.c_void_p]
@@ -528,6 +530,12 @@ def pam_nn_layered_inputs(problem, plan, K, x, stream=None):
     """x [n_rows][16][16][8] fp32 (n_rows >= S) from the patches of K."""
     _check(lib().pam_nn_layered_inputs(C.byref(problem), C.byref(plan), _ptr(K), _ptr(x), int(x.shape[0]),
                                        _stream(stream)), "pam_nn_layered_inputs")
+
+
+def pam_nn_inputs(problem, plan, K, x, stream=None, arch=PAM_NN_PATCH2D):
+    """The network inputs x [n_rows][h][h][c] fp32 of every subdomain's patch of K (on the device)."""
+    _check(lib().pam_nn_inputs(int(arch), C.byref(problem), C.byref(plan), _ptr(K), _ptr(x), int(x.shape[0]),
+                               _stream(stream)), "pam_nn_inputs")
 
 
 def pam_nn_seed(plan, out, threshold, model, stream=None, arch=PAM_NN_LAYERED3D):

@@ -53,16 +53,25 @@ class PatchFit:
         self.fitter = pam.Fitter((T * PATCH, T * PATCH), (T, T), 0, (G, G), device=device, precision=precision,
                                  k_top=1, levels=0, max_iters=max_iters)
 
-    def fit(self, patches, beta0=None):
-        """Solve every patch; beta0 [P, 256] (numpy or tensor) seeds the solve.
-        Returns (beta [P,256] numpy, info [P,8] numpy, solve ms)."""
+    def device_field(self, patches):
+        """The tiled field of the patches on the device."""
         import torch
-        grid, T = tile(patches)
-        Kd = torch.from_numpy(grid).to(self.device)
+        grid, _ = tile(patches)
+        return torch.from_numpy(grid).to(self.device)
+
+    def fit(self, patches, beta0=None, Kd=None, seeded=False):
+        """Solve every patch; beta0 [P, 256] (numpy or tensor) seeds the solve,
+        or seeded=True: the model's coefficients were seeded on the device
+        (pam_nn_seed). Kd: the tiled field already on the device.
+        Returns (beta [P,256] numpy, info [P,8] numpy, solve ms)."""
+        if Kd is None:
+            Kd = self.device_field(patches)
         f = self.fitter
+        warm = seeded or beta0 is not None
         p = pam.make_params(k_top=1, levels=0, max_iters=self.max_iters, precision=self.precision,
-                            warm_start=0 if beta0 is None else 1)
-        if beta0 is not None:
+                            warm_start=1 if warm else 0)
+        if beta0 is not None and not seeded:
+            import torch
             b0 = torch.as_tensor(beta0, dtype=torch.float64).to(self.device)
             f.model.beta.zero_()
             f.model.beta[:, :N_OUT] = b0
@@ -244,17 +253,25 @@ def warm_start_coefficients(logits, beta, threshold=SEED_THRESHOLD):
 
 def learned_fit(net, patches, device, precision=pam.PAM_PREC_FP64, budget=48):
     """Fit with the network's warm start; patches not certified within
-    `budget` active-set iterations are refitted plainly from zero.
-    The inference is one batched forward pass over all the patches.
-    Returns dict(beta, info, solve_ms, refit, predict_ms)."""
+    `budget` active-set iterations are refitted plainly from zero. Inputs,
+    inference (one batched forward pass over all the patches) and the seed
+    (the predicted coefficients above SEED_THRESHOLD, pam_nn_seed) stay on
+    the device. Returns dict(beta, info, solve_ms, refit, predict_ms)."""
     import torch
+    fit = PatchFit(patches.shape[0], device, precision, max_iters=budget)
+    Kd = fit.device_field(patches)
+    f = fit.fitter
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
-    logits, b = net.predict(network_input(patches), batched=True)
+    rows = -(-patches.shape[0] // 32) * 32
+    X = torch.empty((rows, net.h0, net.h0, net.c0), dtype=torch.float32, device=device)
+    pam.pam_nn_inputs(f.problem, f.plan, Kd, X, arch=net.arch)
+    out = net.forward_device(X)
+    f.model.beta.zero_()
+    pam.pam_nn_seed(f.plan, out, SEED_THRESHOLD, f.model, arch=net.arch)
     torch.cuda.synchronize()
     t_pred = (time.perf_counter() - t0) * 1e3
-    beta0 = warm_start_coefficients(logits, b)
-    fit = PatchFit(patches.shape[0], device, precision, max_iters=budget)
-    beta, info, ms = fit.fit(patches, beta0)
+    beta, info, ms = fit.fit(patches, Kd=Kd, seeded=True)
     miss = np.nonzero(info[:, pam.INFO_FLAGS] & pam.FLAG_NOT_CERTIFIED)[0]
     refit_ms = 0.0
     if len(miss):

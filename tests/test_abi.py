@@ -164,6 +164,25 @@ def test_layered_inputs_reject_unsupported_problems(pam):
     assert L.pam_nn_layered_inputs(C.byref(pr3), C.byref(plan3), C.c_void_p(8), C.c_void_p(8), 32, None) == 6
 
 
+def test_network_inputs_check_the_arch_against_the_problem(pam):
+    import ctypes as C
+    L = pam.lib()
+    fake = C.c_void_p(8)  # never dereferenced: validation fails first
+    pr2 = pam.make_problem((64, 64), (2, 2), 0, (16, 16))
+    plan2 = pam.pam_plan_create(pr2, pam.make_params())
+    pr3 = pam.make_problem((30, 110, 85), (3, 11, 17), 1, (4, 4, 2))
+    plan3 = pam.pam_plan_create(pr3, pam.make_params())
+    wide = pam.make_problem((66, 64), (2, 2), 0, (16, 16))  # a 33-cell patch
+    plan_w = pam.pam_plan_create(wide, pam.make_params())
+    for arch, pr, plan, rows, want in [(0, pr3, plan3, 576, 1),   # a 3-D problem for the 2-D network
+                                       (1, pr2, plan2, 32, 1),    # and the converse
+                                       (2, pr2, plan2, 32, 1),    # no such network
+                                       (0, pr2, plan2, 3, 1),     # fewer rows than subdomains
+                                       (0, wide, plan_w, 32, 6)]:
+        assert L.pam_nn_inputs(arch, C.byref(pr), C.byref(plan), fake, fake, rows, None) == want, (arch, rows)
+    assert L.pam_nn_inputs(0, C.byref(pr2), C.byref(plan2), None, fake, 32, None) == 1
+
+
 def test_eval_glued_checks_the_band_and_sizes(pam):
     import ctypes as C
     fake = C.c_void_p(256)  # never dereferenced: validation fails first

@@ -71,6 +71,34 @@ def _sample_cells(T, which):
     return np.stack([((p // T) * 32 + r) * n + (p % T) * 32 + c for p in which]).reshape(len(which), -1)
 
 
+def test_device_inputs_and_seed_match_the_host_forms(trained):
+    # pam_nn_inputs(arch 0) gathers network_input's patches from the tiled
+    # field on the device (log10 in fp32 there: a rounding apart), and
+    # pam_nn_seed(arch 0) writes warm_start_coefficients of the same output
+    torch, pam, ws, dev, net, held = (trained[k] for k in ("torch", "pam", "ws", "dev", "net", "held"))
+    fit = ws.PatchFit(32 * 32, dev)
+    sub = held[:32 * 32]
+    Kd = fit.device_field(sub)
+    X = torch.full((1024, 32, 32, 1), 7.0, dtype=torch.float32, device=dev)
+    pam.pam_nn_inputs(fit.fitter.problem, fit.fitter.plan, Kd, X)
+    x = X.cpu().numpy()[..., 0]
+    np.testing.assert_allclose(x, ws.network_input(sub), rtol=0, atol=5e-7)
+    out = net.forward_device(X)
+    f = fit.fitter
+    f.model.beta.fill_(5.0)
+    pam.pam_nn_seed(f.plan, out, ws.SEED_THRESHOLD, f.model, arch=pam.PAM_NN_PATCH2D)
+    o = out.cpu().numpy()
+    want = ws.warm_start_coefficients(o[:, :ws.N_OUT], o[:, ws.N_OUT:] * ws.BETA_SCALE)
+    got = f.model.beta[:, :ws.N_OUT].cpu().numpy()
+    np.testing.assert_array_equal(got, want)
+    # fewer rows than subdomains: refused, nothing written
+    Xs = torch.full((992, 32, 32, 1), 7.0, dtype=torch.float32, device=dev)
+    with pytest.raises(pam.PamError):
+        pam.pam_nn_inputs(f.problem, f.plan, Kd, Xs)
+    torch.cuda.synchronize()
+    assert torch.all(Xs == 7.0)
+
+
 @pytest.mark.parametrize("precision", [0, 1])
 def test_warm_start_reaches_the_plain_minimiser_in_fewer_iterations(trained, precision):
     torch, pam, ws, dev, net, held = (trained[k] for k in ("torch", "pam", "ws", "dev", "net", "held"))
