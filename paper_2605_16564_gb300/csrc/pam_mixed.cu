@@ -543,14 +543,16 @@ static size_t gram_tc_smem(const Geo &g, int stages) {
 // tcgen05 pipeline's set-up and per-instruction cost dominate), so one block
 // of 256 threads per subdomain generates W in chunks of 32 cells into shared
 // memory, with the same exponent as the tensor-core Gram (the Shepard
-// normaliser folded in: W = 2^(l - sh)), and accumulates the upper triangle
-// of W^T W in fp32, nine entries per thread at most, plus b = W^T y and the
-// weight sums. Products are exact fp32 (no bf16 split), so G~ is at least as
-// accurate as the tensor-core one.
+// normaliser folded in: W = 2^(l - sh)), and accumulates W^T W in fp32 over
+// 4 x 4 tiles of the upper block triangle held in registers (two float4
+// loads per sixteen multiply-adds), the cells of a chunk split among
+// ks = 256 / tiles thread groups whose partial tiles are summed in shared
+// memory at the end. The threads that generate centre m's values also sum
+// b = W^T y and the weight sum of m. Products are exact fp32 (no bf16
+// split), so G~ is at least as accurate as the tensor-core one.
 // --------------------------------------------------------------------------
 constexpr int kSmallGramM = 64;
 constexpr int kSgThreads = 256;
-constexpr int kSgSlots = (kSmallGramM * (kSmallGramM + 1) / 2 + kSgThreads - 1) / kSgThreads;  // 9
 
 __global__ void __launch_bounds__(kSgThreads) k_gram_small(Geo g, const int32_t *boxes, const double *centres,
                                                           const int32_t *info, Ws w, int all) {
@@ -558,11 +560,12 @@ __global__ void __launch_bounds__(kSgThreads) k_gram_small(Geo g, const int32_t 
     const int32_t *inf = info + s * kInfoN;
     if (!all && inf[PAM_INFO_STOPPED]) return;
     const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
-    if (M > kSmallGramM) return;  // never: the launch is sized by the host's bound
+    if (M > kSmallGramM || M < 1) return;  // never: the launch is sized by the host's bound
     const int tid = threadIdx.x;
     const int32_t *box = boxes + s * 12;
     __shared__ float4 sc[kSmallGramM];
-    __shared__ float Wt[kTcKC][kSmallGramM];
+    __shared__ __align__(16) float Wt[kTcKC][kSmallGramM];
+    __shared__ float Gs[kSgThreads * 16];  // the partial tiles; then b and the weight sums
     extern __shared__ float4 cxa[];  // [nch * 32] (x, y, z, sh) of every patch cell, then ln K
     const int nch = (N + kTcKC - 1) / kTcKC;
     float *cya = reinterpret_cast<float *>(cxa + (size_t)nch * kTcKC);
@@ -570,19 +573,20 @@ __global__ void __launch_bounds__(kSgThreads) k_gram_small(Geo g, const int32_t 
     patch_origin(g, box, o);
     const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
     for (int m = tid; m < M; m += blockDim.x) sc[m] = local_centre(cg[m], o);
-    // this thread's entries (i, j), j >= i, of the upper triangle
-    const int T = M * (M + 1) / 2;
-    int ei[kSgSlots], ej[kSgSlots];
-    float acc[kSgSlots];
-#pragma unroll
-    for (int q = 0; q < kSgSlots; ++q) {
-        const int e = tid + q * kSgThreads;
-        int i = 0, rem = e;  // row-major over the upper triangle: row i holds M - i entries
-        while (i < M && rem >= M - i) { rem -= M - i; ++i; }
-        ei[q] = e < T ? i : 0;
-        ej[q] = e < T ? i + rem : 0;
-        acc[q] = 0.f;
-    }
+    // padding columns of W (M up to the next multiple of 4) stay zero
+    const int nb = (M + 3) >> 2, ntile = nb * (nb + 1) / 2;
+    for (int e = tid; e < kTcKC * kSmallGramM; e += blockDim.x) (&Wt[0][0])[e] = 0.f;
+    // this thread's tile (bi <= bj, row-major over the upper block triangle)
+    // and cell group kg of ks
+    const int ks = kSgThreads / ntile;  // >= 1: ntile <= 136
+    const int tile = tid % ntile, kg = tid / ntile;
+    int bi = 0, rem = tile;
+    while (rem >= nb - bi) { rem -= nb - bi; ++bi; }
+    const int bj = bi + rem;
+    const bool tiled = kg < ks;
+    // generators: R threads per centre, each its own cells of a chunk
+    const int R = kSgThreads / M, gm = tid % M, gq = tid / M;
+    const bool gen = gq < R;
     const float *rowmax = w.rowmax + (size_t)s * g.n_max;
     const float *rowinv = w.rowinv + (size_t)s * g.n_max;
     const double *yv = w.y + (size_t)s * g.n_max;
@@ -599,43 +603,70 @@ __global__ void __launch_bounds__(kSgThreads) k_gram_small(Geo g, const int32_t 
         cxa[t] = make_float4(x[0], x[1], x[2], sh);
         cya[t] = y;
     }
+    float acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0.f;
     float bacc = 0.f, wacc = 0.f;
+    const float4 cm = gen ? sc[gm] : make_float4(0.f, 0.f, 0.f, 0.f);
+    const float4 *W4 = reinterpret_cast<const float4 *>(&Wt[0][0]);
     for (int t0 = 0; t0 < N; t0 += kTcKC) {
         __syncthreads();  // the cells are staged; the previous chunk's readers are done
-        const float4 *cx = cxa + t0;
-        const float *cy = cya + t0;
-        for (int p = tid; p < kTcKC * M; p += blockDim.x) {
-            const int t = p / M, m = p - t * M;
-            const float4 c = cx[t];
-            Wt[t][m] = tc::ex2(logit2(sc[m], c.x, c.y, c.z) - c.w);  // 0 past the patch (sh = inf)
+        if (gen) {
+            for (int t = gq; t < kTcKC; t += R) {
+                const float4 c = cxa[t0 + t];
+                const float v = tc::ex2(logit2(cm, c.x, c.y, c.z) - c.w);  // 0 past the patch (sh = inf)
+                Wt[t][gm] = v;
+                bacc = fmaf(v, cya[t0 + t], bacc);
+                wacc += v;
+            }
         }
         __syncthreads();
-        if (tid < M) {
-            for (int t = 0; t < kTcKC; ++t) {
-                bacc = fmaf(Wt[t][tid], cy[t], bacc);
-                wacc += Wt[t][tid];
-            }
-        }
+        if (tiled) {
+            for (int t = kg; t < kTcKC; t += ks) {
+                const float4 a = W4[t * (kSmallGramM / 4) + bi], b = W4[t * (kSmallGramM / 4) + bj];
+                const float av[4] = {a.x, a.y, a.z, a.w}, bw[4] = {b.x, b.y, b.z, b.w};
 #pragma unroll
-        for (int q = 0; q < kSgSlots; ++q) {
-            if (tid + q * kSgThreads < T) {
-                float a = acc[q];
-                for (int t = 0; t < kTcKC; ++t) a = fmaf(Wt[t][ei[q]], Wt[t][ej[q]], a);
-                acc[q] = a;
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) acc[u][v] = fmaf(av[u], bw[v], acc[u][v]);
             }
         }
     }
+    // partial tiles out, then each entry sums its ks parts in a fixed order
+    // (the result does not depend on scheduling)
+    if (tiled) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) Gs[tid * 16 + u * 4 + v] = acc[u][v];
+    }
+    __syncthreads();
     float *G = w.Gf + (size_t)s * g.m_cap * g.m_cap;
-#pragma unroll
-    for (int q = 0; q < kSgSlots; ++q) {
-        if (tid + q * kSgThreads < T) {
-            G[(size_t)ei[q] * g.m_cap + ej[q]] = acc[q];
-            G[(size_t)ej[q] * g.m_cap + ei[q]] = acc[q];
-        }
+    for (int e = tid; e < M * M; e += blockDim.x) {
+        const int i = e / M, j = e - i * M;
+        const int a = i <= j ? i : j, b = i <= j ? j : i;
+        const int ta = a >> 2, tl = ta * nb - ta * (ta - 1) / 2 + (b >> 2) - ta;
+        const int off = tl * 16 + (a & 3) * 4 + (b & 3);
+        float v = 0.f;
+        for (int k = 0; k < ks; ++k) v += Gs[k * ntile * 16 + off];
+        G[(size_t)i * g.m_cap + j] = v;
     }
+    __syncthreads();  // Gs is free again: the generators' partial sums, R per centre
+    if (gen) {
+        Gs[gq * M + gm] = bacc;
+        Gs[kSgThreads + gq * M + gm] = wacc;
+    }
+    __syncthreads();
     if (tid < M) {
-        w.b[(size_t)s * g.m_cap + tid] = (double)bacc;
-        w.wsum[(size_t)s * g.m_cap + tid] = wacc;
+        float bs = 0.f, ws = 0.f;
+        for (int q = 0; q < R; ++q) {
+            bs += Gs[q * M + tid];
+            ws += Gs[kSgThreads + q * M + tid];
+        }
+        w.b[(size_t)s * g.m_cap + tid] = (double)bs;
+        w.wsum[(size_t)s * g.m_cap + tid] = ws;
     }
 }
 
@@ -669,7 +700,7 @@ void launch_stats_gram_tc(const Geo &g, const int32_t *boxes, const double *cent
                           const int32_t *info, const Ws &w, cudaStream_t st, int all, int m_bound) {
     launch_stats_f32(g, boxes, centres, info, w, st, all);
     const size_t sm = (size_t)((g.n_max + kTcKC - 1) / kTcKC) * kTcKC * (sizeof(float4) + sizeof(float));
-    if (m_bound > 0 && m_bound <= kSmallGramM && sm + 16 * 1024 <= kSmemLimit) {
+    if (m_bound > 0 && m_bound <= kSmallGramM && sm + 32 * 1024 <= kSmemLimit) {
         // every dictionary is at most m_bound centres (the initial lattices)
         PhaseScope ps(kPhGramTC, st);
         cudaFuncSetAttribute(k_gram_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
