@@ -297,6 +297,92 @@ __device__ void stage_f32(const Geo &g, const int32_t *boxes, const double *cent
     __syncthreads();
 }
 
+// Scaled form of the evaluation's logit. With a = sqrt(log2(e) / 2) / sigma
+// per centre and the centre stored as (a c, a), the base-2 logit
+// -|x - c|^2 / (2 sigma^2) log2(e) = -|a x - a c|^2 is three multiply-adds
+// (a x_i - a c_i) and a sum of squares: six operations per centre and point
+// against seven for the difference form. The rounding of a c_i costs
+// ~2 eps a^2 R |x - c| in the logit (R the distance from the patch centre,
+// the origin of the local coordinates): proportional to |x - c|, so it stays
+// below ~1e-5 wherever the weight is not negligible. Centre m is
+// su[m] = (a c, a), sb[m] = beta_m.
+static size_t stage_f32s_smem(int m_cap) {
+    return ((size_t)m_cap * (sizeof(float4) + sizeof(float)) + 31) / 32 * 32 + 32 +  // + alignment slack
+           (size_t)m_cap * (sizeof(dvec4) + sizeof(double));
+}
+
+__device__ __forceinline__ void put_centre_s(const dvec4 &c, double b, const double o[3], float4 *su, float *sb) {
+    const float sg = (float)c.w;
+    const float a = 0.84932180f / sg;  // sqrt(log2(e) / 2) / sigma
+    *su = make_float4(a * (float)(c.x - o[0]), a * (float)(c.y - o[1]), a * (float)(c.z - o[2]), a);
+    *sb = (float)b;
+}
+
+__device__ void stage_f32s(const Geo &g, const int32_t *boxes, const double *centres, const double *beta, int s,
+                           int M, float4 *su, float *sb, double o[3]) {
+    const int32_t *box = boxes + s * 12;
+    for (int a = 0; a < 3; ++a) o[a] = a < g.dim ? 0.5 * (double)(box[6 + a] + box[9 + a]) * g.h : 0.0;
+    dvec4 *raw_c = reinterpret_cast<dvec4 *>((reinterpret_cast<uintptr_t>(sb + g.m_cap) + 31) & ~(uintptr_t)31);
+    double *raw_b = reinterpret_cast<double *>(raw_c + g.m_cap);
+    if (stage_bulk(g, centres, beta, s, M, raw_c, raw_b)) {
+        for (int m = threadIdx.x; m < M; m += blockDim.x) put_centre_s(raw_c[m], raw_b[m], o, su + m, sb + m);
+        __syncthreads();
+        return;
+    }
+    const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
+    for (int m = threadIdx.x; m < M; m += blockDim.x)
+        put_centre_s(cg[m], beta[(size_t)s * g.m_cap + m], o, su + m, sb + m);
+    __syncthreads();
+}
+
+// minus the base-2 logit: |a x - a c|^2
+__device__ __forceinline__ float nlogit_s(const float4 &u, const float *p) {
+    const float dx = fmaf(u.w, p[0], -u.x), dy = fmaf(u.w, p[1], -u.y), dz = fmaf(u.w, p[2], -u.z);
+    return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+}
+
+// One point with the maximum logit subtracted (the plain sums underflowed).
+__device__ __noinline__ float shepard_f32s_shifted(const float4 *su, const float *sb, int M, float x, float y,
+                                                   float z) {
+    const float p[3] = {x, y, z};
+    float nmin = INFINITY;
+    for (int m = 0; m < M; ++m) nmin = fminf(nmin, nlogit_s(su[m], p));
+    float num = 0.f, den = 0.f;
+    for (int m = 0; m < M; ++m) {
+        const float e = tc::ex2(nmin - nlogit_s(su[m], p));
+        num = fmaf(sb[m], e, num);
+        den += e;
+    }
+    return num / den;
+}
+
+// P points at once: every centre read from shared memory serves all of them.
+template <int P>
+__device__ __forceinline__ void shepard_f32s(const float4 *su, const float *sb, int M, const float (&p)[P][3],
+                                             float (&v)[P]) {
+    float num[P], den[P];
+#pragma unroll
+    for (int k = 0; k < P; ++k) {
+        num[k] = 0.f;
+        den[k] = 0.f;
+    }
+    for (int m = 0; m < M; ++m) {
+        const float4 u = su[m];
+        const float bm = sb[m];
+#pragma unroll
+        for (int k = 0; k < P; ++k) {
+            const float e = tc::ex2(-nlogit_s(u, p[k]));
+            num[k] = fmaf(bm, e, num[k]);
+            den[k] += e;
+        }
+    }
+#pragma unroll
+    for (int k = 0; k < P; ++k)
+        v[k] = (den[k] > 7.9e-31f) ? num[k] / den[k] : shepard_f32s_shifted(su, sb, M, p[k][0], p[k][1], p[k][2]);
+}
+
+constexpr int kEvalPts = 4;  // points per thread and pass of the fp32 bucket evaluation
+
 __global__ void k_eval_bucket_f32(Geo g, const int32_t *boxes, const double *centres,
                                   const double *beta, const int32_t *info, const double *pts,
                                   const int32_t *perm, const int32_t *start, double *out,
@@ -306,24 +392,27 @@ __global__ void k_eval_bucket_f32(Geo g, const int32_t *boxes, const double *cen
     if (b == e) return;
     const int M = info[s * kInfoN + PAM_INFO_M];
     extern __shared__ uint8_t smb[];
-    float4 *sc = reinterpret_cast<float4 *>(smb);
-    float *sb = reinterpret_cast<float *>(sc + g.m_cap);
+    float4 *su = reinterpret_cast<float4 *>(smb);
+    float *sb = reinterpret_cast<float *>(su + g.m_cap);
     double o[3];
-    stage_f32(g, boxes, centres, beta, s, M, sc, sb, o);
-    // two points per thread and pass: i and i + blockDim.x
-    for (int i = b + threadIdx.x; i < e; i += 2 * blockDim.x) {
-        const int i1 = i + blockDim.x;
-        const bool two = i1 < e;
-        const int p0 = perm[i], p1 = two ? perm[i1] : p0;
-        float x0[3] = {0.f, 0.f, 0.f}, x1[3] = {0.f, 0.f, 0.f};
-        for (int a = 0; a < g.dim; ++a) {
-            x0[a] = (float)(pts[(int64_t)p0 * g.dim + a] - o[a]);
-            x1[a] = (float)(pts[(int64_t)p1 * g.dim + a] - o[a]);
+    stage_f32s(g, boxes, centres, beta, s, M, su, sb, o);
+    // kEvalPts points per thread and pass: i, i + blockDim.x, ...
+    const int bd = blockDim.x;
+    for (int i = b + threadIdx.x; i < e; i += kEvalPts * bd) {
+        int pi[kEvalPts];
+        float x[kEvalPts][3];
+#pragma unroll
+        for (int k = 0; k < kEvalPts; ++k) {
+            pi[k] = i + k * bd < e ? perm[i + k * bd] : -1;
+            const int64_t q = pi[k] >= 0 ? pi[k] : perm[i];  // idle slots repeat the first point
+#pragma unroll
+            for (int a = 0; a < 3; ++a) x[k][a] = a < g.dim ? (float)(pts[q * g.dim + a] - o[a]) : 0.f;
         }
-        float v0, v1;
-        shepard_f32_smem2(sc, sb, M, x0, x1, &v0, &v1);
-        out[p0] = log_space ? (double)v0 : exp_f32(v0);
-        if (two) out[p1] = log_space ? (double)v1 : exp_f32(v1);
+        float v[kEvalPts];
+        shepard_f32s<kEvalPts>(su, sb, M, x, v);
+#pragma unroll
+        for (int k = 0; k < kEvalPts; ++k)
+            if (pi[k] >= 0) out[pi[k]] = log_space ? (double)v[k] : exp_f32(v[k]);
     }
 }
 
@@ -344,7 +433,7 @@ void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, cons
     k_eval_scan<<<1, 1024, 0, st>>>(e.count, e.start, g.S);
     k_eval_scatter<<<nb, 256, 0, st>>>(e.owner, e.rank, e.start, e.perm, n_pts);
     if (precision == PAM_PREC_MIXED) {
-        size_t sm = stage_f32_smem(g.m_cap);
+        size_t sm = stage_f32s_smem(g.m_cap);
         cudaFuncSetAttribute(k_eval_bucket_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_eval_bucket_f32<<<g.S, eval_block(), sm, st>>>(g, boxes, centres, beta, info, pts, e.perm, e.start,
                                                 out, log_space);
@@ -670,24 +759,27 @@ __global__ void k_glue_bucket_f32(Geo g, const int32_t *boxes, const double *cen
     if (b == e) return;
     const int M = info[s * kInfoN + PAM_INFO_M];
     extern __shared__ uint8_t smb[];
-    float4 *sc = reinterpret_cast<float4 *>(smb);
-    float *sb = reinterpret_cast<float *>(sc + g.m_cap);
+    float4 *su = reinterpret_cast<float4 *>(smb);
+    float *sb = reinterpret_cast<float *>(su + g.m_cap);
     double o[3];
-    stage_f32(g, boxes, centres, beta, s, M, sc, sb, o);
-    for (int i = b + threadIdx.x; i < e; i += 2 * blockDim.x) {
-        const int i1 = i + blockDim.x;
-        const bool two = i1 < e;
-        const int q0 = perm[i], q1 = two ? perm[i1] : q0;
-        const int64_t p0 = q0 >> g.dim, p1 = q1 >> g.dim;
-        float x0[3] = {0.f, 0.f, 0.f}, x1[3] = {0.f, 0.f, 0.f};
-        for (int a = 0; a < g.dim; ++a) {
-            x0[a] = (float)(pts[p0 * g.dim + a] - o[a]);
-            x1[a] = (float)(pts[p1 * g.dim + a] - o[a]);
+    // the local evaluation of pam_eval's fp32 form, operation for operation
+    stage_f32s(g, boxes, centres, beta, s, M, su, sb, o);
+    const int bd = blockDim.x;
+    for (int i = b + threadIdx.x; i < e; i += kEvalPts * bd) {
+        int qi[kEvalPts];
+        float x[kEvalPts][3];
+#pragma unroll
+        for (int k = 0; k < kEvalPts; ++k) {
+            qi[k] = i + k * bd < e ? perm[i + k * bd] : -1;
+            const int64_t p = (int64_t)(qi[k] >= 0 ? qi[k] : perm[i]) >> g.dim;
+#pragma unroll
+            for (int a = 0; a < 3; ++a) x[k][a] = a < g.dim ? (float)(pts[p * g.dim + a] - o[a]) : 0.f;
         }
-        float v0, v1;
-        shepard_f32_smem2(sc, sb, M, x0, x1, &v0, &v1);
-        val[q0] = v0;
-        if (two) val[q1] = v1;
+        float v[kEvalPts];
+        shepard_f32s<kEvalPts>(su, sb, M, x, v);
+#pragma unroll
+        for (int k = 0; k < kEvalPts; ++k)
+            if (qi[k] >= 0) val[qi[k]] = v[k];
     }
 }
 
@@ -735,7 +827,7 @@ static void glue_launches(const Geo &g, const int32_t *boxes, const double *cent
     k_eval_scan<<<1, 1024, 0, st>>>(e.count, e.start, g.S);
     k_glue_scatter<D><<<nb, 256, 0, st>>>(n_pts, e.start, e);
     if (precision == PAM_PREC_MIXED) {
-        size_t sm = stage_f32_smem(g.m_cap);
+        size_t sm = stage_f32s_smem(g.m_cap);
         cudaFuncSetAttribute(k_glue_bucket_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
         k_glue_bucket_f32<<<g.S, eval_block(), sm, st>>>(g, boxes, centres, beta, info, pts, e.perm, e.start, e.valf);
         k_glue_combine<D, true><<<nb, 256, 0, st>>>(n_pts, e, out, log_space);
