@@ -228,6 +228,53 @@ static int tc_rows_cap(int m_cap) {
     return cap;
 }
 
+// Producer threads per generated row: 4, 2 or 1 (each covering 4 / tpr
+// k-groups of 8 cells of a chunk), the most that one thread per (row, part)
+// allows.
+__host__ __device__ __forceinline__ int tc_threads_per_row(int Rl) {
+    return (4 * Rl <= 32 * kTcProdWarps) ? 4 : (2 * Rl <= 32 * kTcProdWarps ? 2 : 1);
+}
+
+// One generated row of the producers: the centre's constants duplicated for
+// the packed two-cell arithmetic, and its running sums of W y and W (one per
+// half: even and odd cells).
+struct ProdRow {
+    float2 ncx, ncy, ncz, cw, b, w;
+};
+__device__ __forceinline__ ProdRow prod_row(const float4 &cc) {
+    ProdRow r;
+    r.ncx = make_float2(-cc.x, -cc.x);
+    r.ncy = make_float2(-cc.y, -cc.y);
+    r.ncz = make_float2(-cc.z, -cc.z);
+    r.cw = make_float2(cc.w, cc.w);
+    r.b = make_float2(0.f, 0.f);
+    r.w = make_float2(0.f, 0.f);
+    return r;
+}
+
+// W of one row at a cell pair (a = (x, x', y, y'), b = (z, z', -sh, -sh'),
+// yy = (ln K, ln K')): one cell per half of each packed operation -- the
+// same operations, in the same order, as the scalar exponent
+// cc.w |x - c|^2 - sh of each cell -- split into bf16 hi and lo pairs
+// (v = hi + lo to about 2^-16 relative).
+__device__ __forceinline__ void prod_pair(ProdRow &r, const float4 &a, const float4 &b, const float2 &yy,
+                                          uint32_t *hp, uint32_t *lp) {
+    const float2 dx = __fadd2_rn(make_float2(a.x, a.y), r.ncx);
+    const float2 dy = __fadd2_rn(make_float2(a.z, a.w), r.ncy);
+    const float2 dz = __fadd2_rn(make_float2(b.x, b.y), r.ncz);
+    float2 d2 = __fmul2_rn(dx, dx);
+    d2 = __ffma2_rn(dy, dy, d2);
+    d2 = __ffma2_rn(dz, dz, d2);
+    const float2 l = __ffma2_rn(r.cw, d2, make_float2(b.z, b.w));
+    const float2 e = make_float2(tc::ex2(l.x), tc::ex2(l.y));
+    r.b = __ffma2_rn(e, yy, r.b);
+    r.w = __fadd2_rn(e, r.w);
+    *hp = tc::pack_bf16(e.x, e.y);
+    const float2 h = make_float2(__uint_as_float(*hp << 16), __uint_as_float(*hp & 0xffff0000u));
+    const float2 rl = __ffma2_rn(h, make_float2(-1.f, -1.f), e);  // e - h, exact
+    *lp = tc::pack_bf16(rl.x, rl.y);
+}
+
 #ifdef PAM_SOLVE_PROFILE
 // Profiling builds only: clock64 totals of the Gram pipeline (per CTA, seen
 // from the MMA thread and from the first producer thread).
@@ -271,9 +318,12 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
     float4 *sc = reinterpret_cast<float4 *>(smem + tiles_region);   // [Rcap]
     float *bpart = reinterpret_cast<float *>(sc + Rcap);             // [4][Rcap]
     float *wpart = bpart + 4 * Rcap;                                 // [4][Rcap]
-    float4 *cellp = reinterpret_cast<float4 *>(wpart + 4 * Rcap);    // [nch * 32] (x, y, z, sh)
+    // the cells in pairs (2p, 2p + 1): cella[p] = (x, x', y, y'), cellb[p] =
+    // (z, z', -sh, -sh'), celly2[p] = (ln K, ln K') -- 20 bytes per cell
     const int nch = (N + kTcKC - 1) / kTcKC;
-    float *celly = reinterpret_cast<float *>(cellp + (size_t)nch * kTcKC);  // [nch * 32] ln K
+    float4 *cella = reinterpret_cast<float4 *>(wpart + 4 * Rcap);    // [nch * 16]
+    float4 *cellb = cella + (size_t)nch * (kTcKC / 2);               // [nch * 16]
+    float2 *celly2 = reinterpret_cast<float2 *>(cellb + (size_t)nch * (kTcKC / 2));  // [nch * 16]
     __shared__ uint64_t full[kTcMaxStages], empty[kTcMaxStages], drain;
     __shared__ uint32_t tmem_base;
     __shared__ int timed_out;
@@ -296,8 +346,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
             sh = rowmax[t] - log2f(rowinv[t]);
             y = (float)yv[t];
         }
-        cellp[t] = make_float4(x[0], x[1], x[2], sh);
-        celly[t] = y;
+        float *fa = reinterpret_cast<float *>(cella + (t >> 1)), *fb = reinterpret_cast<float *>(cellb + (t >> 1));
+        const int h = t & 1;
+        fa[h] = x[0];
+        fa[2 + h] = x[1];
+        fb[h] = x[2];
+        fb[2 + h] = -sh;  // -inf past the patch: the weight is 0
+        reinterpret_cast<float *>(celly2 + (t >> 1))[h] = y;
     }
     // rows past the live ones stay zero in every stage
     {
@@ -391,14 +446,13 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
     } else {
         // ---- producers ----
         const int pth = tid - 32 * kTcIssuers;  // 0 .. 32 * kTcProdWarps - 1
-        const int tpr = (4 * Rl <= 32 * kTcProdWarps) ? 4 : (2 * Rl <= 32 * kTcProdWarps ? 2 : 1);
+        const int tpr = tc_threads_per_row(Rl);
         const int nkg = 4 / tpr;
         // a warp covers 32 consecutive rows with one set of k-groups: its cell
         // reads are broadcasts and its stores one contiguous 512-byte run
         const int pw = pth >> 5, part = pw % tpr, r = (pw / tpr) * 32 + lane;
         const bool live = r < Rl;
-        const float4 cc = live ? sc[r] : make_float4(0.f, 0.f, 0.f, 0.f);
-        float bacc = 0.f, wacc = 0.f;
+        ProdRow row = prod_row(live ? sc[r] : make_float4(0.f, 0.f, 0.f, 0.f));
         for (int c = 0; c < nch; ++c) {
             const int st = c % nst;
             bool bad = false;
@@ -414,37 +468,22 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
             if (bad) *vto = 1;
             if (__any_sync(0xffffffffu, bad || *vto)) break;  // warp-uniform exit
             if (live) {
-                const float4 *cl = cellp + c * kTcKC;
-                const float *cy = celly + c * kTcKC;
+                const float4 *pa = cella + c * (kTcKC / 2), *pb = cellb + c * (kTcKC / 2);
+                const float2 *py = celly2 + c * (kTcKC / 2);
                 uint8_t *hi = tiles + (size_t)st * 2 * tile_bytes;
                 uint8_t *lo = hi + tile_bytes;
-                float bsum = 0.f, wsm = 0.f;
                 for (int kk = 0; kk < nkg; ++kk) {
                     const int kg = part * nkg + kk;
-                    float v[8];
-#pragma unroll
-                    for (int q = 0; q < 8; ++q) {
-                        const int k = kg * 8 + q;
-                        const float4 cp = cl[k];
-                        const float dx = cp.x - cc.x, dy = cp.y - cc.y, dz = cp.z - cc.z;
-                        const float e = tc::ex2(fmaf(cc.w, fmaf(dz, dz, fmaf(dy, dy, dx * dx)), -cp.w));
-                        v[q] = e;
-                        bsum = fmaf(e, cy[k], bsum);
-                        wsm += e;
-                    }
                     uint32_t hp[4], lp[4];
 #pragma unroll
                     for (int q = 0; q < 4; ++q) {
-                        hp[q] = tc::pack_bf16(v[2 * q], v[2 * q + 1]);
-                        const float h0 = __uint_as_float(hp[q] << 16), h1 = __uint_as_float(hp[q] & 0xffff0000u);
-                        lp[q] = tc::pack_bf16(v[2 * q] - h0, v[2 * q + 1] - h1);
+                        const int pq = kg * 4 + q;
+                        prod_pair(row, pa[pq], pb[pq], py[pq], &hp[q], &lp[q]);
                     }
                     const uint32_t off = (uint32_t)(kg * (Rt >> 3) + (r >> 3)) * 128u + (uint32_t)(r & 7) * 16u;
                     *reinterpret_cast<uint4 *>(hi + off) = make_uint4(hp[0], hp[1], hp[2], hp[3]);
                     *reinterpret_cast<uint4 *>(lo + off) = make_uint4(lp[0], lp[1], lp[2], lp[3]);
                 }
-                bacc += bsum;
-                wacc += wsm;
             }
             tc::fence_proxy_async_smem();
             __syncwarp();
@@ -454,8 +493,8 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
 #endif
         }
         if (live) {
-            bpart[part * Rcap + r] = bacc;
-            wpart[part * Rcap + r] = wacc;
+            bpart[part * Rcap + r] = row.b.x + row.b.y;
+            wpart[part * Rcap + r] = row.w.x + row.w.y;
         }
     }
     // wait for the last chunk's MMAs (they complete in issue order)
@@ -505,7 +544,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
             __syncwarp();
         }
         // b = W^T y for the group's rows: the parts of a row in a fixed order
-        const int tpr = (4 * Rl <= 32 * kTcProdWarps) ? 4 : (2 * Rl <= 32 * kTcProdWarps ? 2 : 1);
+        const int tpr = tc_threads_per_row(Rl);
         const int rend = min(Rl, 128 * (i1 - i0));
         for (int r = tid; r < rend; r += blockDim.x) {
             float acc = 0.f, ws = 0.f;
