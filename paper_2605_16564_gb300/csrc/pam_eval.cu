@@ -54,7 +54,9 @@ __global__ void k_eval_owner(Geo g, const double *pts, int64_t n, int32_t *owner
     int s = -2;  // lanes past the end take a key no real owner has
     if (p < n) {
         double x[3] = {0, 0, 0};
-        for (int a = 0; a < g.dim; ++a) x[a] = pts[p * g.dim + a];
+#pragma unroll
+        for (int a = 0; a < 3; ++a)
+            if (a < g.dim) x[a] = pts[p * g.dim + a];
         s = owner_of_point(g, x);
     }
     const unsigned peers = __match_any_sync(0xffffffffu, s);
@@ -298,87 +300,107 @@ __device__ void stage_f32(const Geo &g, const int32_t *boxes, const double *cent
 }
 
 // Scaled form of the evaluation's logit. With a = sqrt(log2(e) / 2) / sigma
-// per centre and the centre stored as (a c, a), the base-2 logit
-// -|x - c|^2 / (2 sigma^2) log2(e) = -|a x - a c|^2 is three multiply-adds
-// (a x_i - a c_i) and a sum of squares: six operations per centre and point
-// against seven for the difference form. The rounding of a c_i costs
-// ~2 eps a^2 R |x - c| in the logit (R the distance from the patch centre,
-// the origin of the local coordinates): proportional to |x - c|, so it stays
-// below ~1e-5 wherever the weight is not negligible. Centre m is
-// su[m] = (a c, a), sb[m] = beta_m.
+// per centre, the base-2 logit -|x - c|^2 / (2 sigma^2) log2(e) is
+// -|a x - a c|^2: three multiply-adds (a x_i - a c_i) and a sum of squares,
+// six operations per centre and point against seven for the difference form.
+// The rounding of a c_i costs ~2 eps a^2 R |x - c| in the logit (R the
+// distance from the patch centre, the origin of the local coordinates):
+// proportional to |x - c|, so it stays below ~1e-5 wherever the weight is
+// not negligible. Points go through the centres in pairs, one per half of
+// each packed fp32x2 operation (the same operations, in the same order, as
+// for a single point). Centre m is stored duplicated for that:
+// su[2m] = (-a c_x, -a c_x, -a c_y, -a c_y), su[2m + 1] = (-a c_z, -a c_z, a, a),
+// sb[m] = (beta_m, beta_m).
 static size_t stage_f32s_smem(int m_cap) {
-    return ((size_t)m_cap * (sizeof(float4) + sizeof(float)) + 31) / 32 * 32 + 32 +  // + alignment slack
+    return ((size_t)m_cap * (2 * sizeof(float4) + sizeof(float2)) + 31) / 32 * 32 + 32 +  // + alignment slack
            (size_t)m_cap * (sizeof(dvec4) + sizeof(double));
 }
 
-__device__ __forceinline__ void put_centre_s(const dvec4 &c, double b, const double o[3], float4 *su, float *sb) {
+__device__ __forceinline__ void put_centre_s(const dvec4 &c, double b, const double o[3], float4 *su, float2 *sb) {
     const float sg = (float)c.w;
     const float a = 0.84932180f / sg;  // sqrt(log2(e) / 2) / sigma
-    *su = make_float4(a * (float)(c.x - o[0]), a * (float)(c.y - o[1]), a * (float)(c.z - o[2]), a);
-    *sb = (float)b;
+    const float ax = a * (float)(c.x - o[0]), ay = a * (float)(c.y - o[1]), az = a * (float)(c.z - o[2]);
+    su[0] = make_float4(-ax, -ax, -ay, -ay);
+    su[1] = make_float4(-az, -az, a, a);
+    *sb = make_float2((float)b, (float)b);
 }
 
 __device__ void stage_f32s(const Geo &g, const int32_t *boxes, const double *centres, const double *beta, int s,
-                           int M, float4 *su, float *sb, double o[3]) {
+                           int M, float4 *su, float2 *sb, double o[3]) {
     const int32_t *box = boxes + s * 12;
     for (int a = 0; a < 3; ++a) o[a] = a < g.dim ? 0.5 * (double)(box[6 + a] + box[9 + a]) * g.h : 0.0;
     dvec4 *raw_c = reinterpret_cast<dvec4 *>((reinterpret_cast<uintptr_t>(sb + g.m_cap) + 31) & ~(uintptr_t)31);
     double *raw_b = reinterpret_cast<double *>(raw_c + g.m_cap);
     if (stage_bulk(g, centres, beta, s, M, raw_c, raw_b)) {
-        for (int m = threadIdx.x; m < M; m += blockDim.x) put_centre_s(raw_c[m], raw_b[m], o, su + m, sb + m);
+        for (int m = threadIdx.x; m < M; m += blockDim.x) put_centre_s(raw_c[m], raw_b[m], o, su + 2 * m, sb + m);
         __syncthreads();
         return;
     }
     const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
     for (int m = threadIdx.x; m < M; m += blockDim.x)
-        put_centre_s(cg[m], beta[(size_t)s * g.m_cap + m], o, su + m, sb + m);
+        put_centre_s(cg[m], beta[(size_t)s * g.m_cap + m], o, su + 2 * m, sb + m);
     __syncthreads();
 }
 
-// minus the base-2 logit: |a x - a c|^2
-__device__ __forceinline__ float nlogit_s(const float4 &u, const float *p) {
-    const float dx = fmaf(u.w, p[0], -u.x), dy = fmaf(u.w, p[1], -u.y), dz = fmaf(u.w, p[2], -u.z);
-    return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
-}
-
-// One point with the maximum logit subtracted (the plain sums underflowed).
-__device__ __noinline__ float shepard_f32s_shifted(const float4 *su, const float *sb, int M, float x, float y,
+// One point with the maximum logit subtracted (the plain sums underflowed):
+// minus the logit |a x - a c|^2 per centre, as the packed form computes it.
+__device__ __noinline__ float shepard_f32s_shifted(const float4 *su, const float2 *sb, int M, float x, float y,
                                                    float z) {
-    const float p[3] = {x, y, z};
+    auto nl = [&](int m) {
+        const float4 u = su[2 * m], v = su[2 * m + 1];
+        const float dx = fmaf(v.z, x, u.x), dy = fmaf(v.z, y, u.z), dz = fmaf(v.z, z, v.x);
+        return fmaf(dz, dz, fmaf(dy, dy, dx * dx));
+    };
     float nmin = INFINITY;
-    for (int m = 0; m < M; ++m) nmin = fminf(nmin, nlogit_s(su[m], p));
+    for (int m = 0; m < M; ++m) nmin = fminf(nmin, nl(m));
     float num = 0.f, den = 0.f;
     for (int m = 0; m < M; ++m) {
-        const float e = tc::ex2(nmin - nlogit_s(su[m], p));
-        num = fmaf(sb[m], e, num);
+        const float e = tc::ex2(nmin - nl(m));
+        num = fmaf(sb[m].x, e, num);
         den += e;
     }
     return num / den;
 }
 
-// P points at once: every centre read from shared memory serves all of them.
+// P points (P even) at once, in pairs: every centre read from shared memory
+// serves all of them.
 template <int P>
-__device__ __forceinline__ void shepard_f32s(const float4 *su, const float *sb, int M, const float (&p)[P][3],
+__device__ __forceinline__ void shepard_f32s(const float4 *su, const float2 *sb, int M, const float (&p)[P][3],
                                              float (&v)[P]) {
-    float num[P], den[P];
+    constexpr int H = P / 2;
+    float2 X[H], Y[H], Z[H], num[H], den[H];
 #pragma unroll
-    for (int k = 0; k < P; ++k) {
-        num[k] = 0.f;
-        den[k] = 0.f;
+    for (int k = 0; k < H; ++k) {
+        X[k] = make_float2(p[2 * k][0], p[2 * k + 1][0]);
+        Y[k] = make_float2(p[2 * k][1], p[2 * k + 1][1]);
+        Z[k] = make_float2(p[2 * k][2], p[2 * k + 1][2]);
+        num[k] = make_float2(0.f, 0.f);
+        den[k] = make_float2(0.f, 0.f);
     }
     for (int m = 0; m < M; ++m) {
-        const float4 u = su[m];
-        const float bm = sb[m];
+        const float4 u = su[2 * m], w = su[2 * m + 1];
+        const float2 bm = sb[m], a2 = make_float2(w.z, w.w);
 #pragma unroll
-        for (int k = 0; k < P; ++k) {
-            const float e = tc::ex2(-nlogit_s(u, p[k]));
-            num[k] = fmaf(bm, e, num[k]);
-            den[k] += e;
+        for (int k = 0; k < H; ++k) {
+            const float2 dx = __ffma2_rn(a2, X[k], make_float2(u.x, u.y));
+            const float2 dy = __ffma2_rn(a2, Y[k], make_float2(u.z, u.w));
+            const float2 dz = __ffma2_rn(a2, Z[k], make_float2(w.x, w.y));
+            float2 q = __fmul2_rn(dx, dx);
+            q = __ffma2_rn(dy, dy, q);
+            q = __ffma2_rn(dz, dz, q);
+            const float2 e = make_float2(tc::ex2(-q.x), tc::ex2(-q.y));
+            num[k] = __ffma2_rn(bm, e, num[k]);
+            den[k] = __fadd2_rn(e, den[k]);
         }
     }
 #pragma unroll
-    for (int k = 0; k < P; ++k)
-        v[k] = (den[k] > 7.9e-31f) ? num[k] / den[k] : shepard_f32s_shifted(su, sb, M, p[k][0], p[k][1], p[k][2]);
+    for (int k = 0; k < H; ++k) {
+        v[2 * k] = (den[k].x > 7.9e-31f) ? num[k].x / den[k].x
+                                         : shepard_f32s_shifted(su, sb, M, p[2 * k][0], p[2 * k][1], p[2 * k][2]);
+        v[2 * k + 1] = (den[k].y > 7.9e-31f)
+                           ? num[k].y / den[k].y
+                           : shepard_f32s_shifted(su, sb, M, p[2 * k + 1][0], p[2 * k + 1][1], p[2 * k + 1][2]);
+    }
 }
 
 constexpr int kEvalPts = 4;  // points per thread and pass of the fp32 bucket evaluation
@@ -393,7 +415,7 @@ __global__ void k_eval_bucket_f32(Geo g, const int32_t *boxes, const double *cen
     const int M = info[s * kInfoN + PAM_INFO_M];
     extern __shared__ uint8_t smb[];
     float4 *su = reinterpret_cast<float4 *>(smb);
-    float *sb = reinterpret_cast<float *>(su + g.m_cap);
+    float2 *sb = reinterpret_cast<float2 *>(su + 2 * g.m_cap);
     double o[3];
     stage_f32s(g, boxes, centres, beta, s, M, su, sb, o);
     // kEvalPts points per thread and pass: i, i + blockDim.x, ...
@@ -760,7 +782,7 @@ __global__ void k_glue_bucket_f32(Geo g, const int32_t *boxes, const double *cen
     const int M = info[s * kInfoN + PAM_INFO_M];
     extern __shared__ uint8_t smb[];
     float4 *su = reinterpret_cast<float4 *>(smb);
-    float *sb = reinterpret_cast<float *>(su + g.m_cap);
+    float2 *sb = reinterpret_cast<float2 *>(su + 2 * g.m_cap);
     double o[3];
     // the local evaluation of pam_eval's fp32 form, operation for operation
     stage_f32s(g, boxes, centres, beta, s, M, su, sb, o);
@@ -862,8 +884,84 @@ void launch_eval_glued(const Geo &g, const int32_t *boxes, const double *centres
 // --------------------------------------------------------------------------
 constexpr int kErrThreads = 256;
 
-template <bool F32>
-__global__ void __launch_bounds__(kErrThreads) k_errors_owner(Geo g, const int32_t *boxes,
+// The fp32 form's error sums: the surrogate as pam_eval evaluates it (the
+// scaled logit, points in pairs through the packed arithmetic), at the
+// cells' nodes taken two at a time -- two cells' centroids, or two
+// Gauss-Legendre nodes of one cell -- with ln K in fp32 (the surrogate
+// carries fp32 rounding already) and the sums in binary64.
+__global__ void __launch_bounds__(kErrThreads) k_errors_owner_f32(Geo g, const int32_t *boxes,
+                                                                  const double *centres, const double *beta,
+                                                                  const int32_t *info, const double *K, int quad,
+                                                                  double *part) {
+    const int s = blockIdx.x;
+    const int M = info[s * kInfoN + PAM_INFO_M];
+    const int32_t *box = boxes + s * 12;
+    extern __shared__ uint8_t smb[];
+    float4 *su = reinterpret_cast<float4 *>(smb);
+    float2 *sb = reinterpret_cast<float2 *>(su + 2 * g.m_cap);
+    double o[3];
+    stage_f32s(g, boxes, centres, beta, s, M, su, sb, o);
+    const int w0 = box[3] - box[0], w1 = box[4] - box[1], w2 = box[5] - box[2];
+    const int nq = quad ? (1 << g.dim) : 1;
+    const int64_t items = (int64_t)w0 * w1 * w2 * nq;  // (cell, node) pairs, node fastest
+    const double off = __dmul_rn(0.5, g.h) / sqrt(3.0), wq = 1.0 / (double)nq;
+    double acc[7] = {0, 0, 0, 0, 0, 0, 0};
+    for (int64_t pr = threadIdx.x; 2 * pr < items; pr += blockDim.x) {
+        float p[2][3];
+        double kk[2];
+        bool live[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int64_t it = 2 * pr + h < items ? 2 * pr + h : 2 * pr;  // an idle half repeats the first
+            live[h] = 2 * pr + h < items;
+            const int t = (int)(it / nq), q = (int)(it % nq);
+            const int i = box[0] + t % w0, j = box[1] + (t / w0) % w1, k = box[2] + t / (w0 * w1);
+            const int idx[3] = {i, j, k};
+#pragma unroll
+            for (int a = 0; a < 3; ++a) {
+                double x = 0.0;
+                if (a < g.dim) {
+                    x = __dmul_rn((double)idx[a] + 0.5, g.h);
+                    if (quad) x = __dadd_rn(x, ((q >> a) & 1) ? off : -off);
+                }
+                p[h][a] = a < g.dim ? (float)(x - o[a]) : 0.f;
+            }
+            kk[h] = K[(int64_t)i + (int64_t)g.n[0] * ((int64_t)j + (int64_t)g.n[1] * k)];
+            if (live[h] && q == 0) {  // the cell's own terms, once
+                acc[1] += fabs(kk[h]);
+                acc[3] += kk[h] * kk[h];
+                acc[5] += fabs((double)logf((float)kk[h]));
+            }
+        }
+        float v[2];
+        shepard_f32s<2>(su, sb, M, p, v);
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            if (!live[h]) continue;
+            const double lk = (double)logf((float)kk[h]), ks = exp_f32(v[h]);
+            acc[0] += wq * fabs(kk[h] - ks);
+            acc[2] += wq * ((kk[h] - ks) * (kk[h] - ks));
+            acc[4] += wq * fabs(lk - (double)v[h]);
+            acc[6] = fmax(acc[6], fabs(lk - (double)v[h]));
+        }
+    }
+    __shared__ double red[kErrThreads / 32][7];
+    for (int q = 0; q < 7; ++q) {
+        const double val = (q == 6) ? warp_max(acc[q]) : warp_sum(acc[q]);
+        if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5][q] = val;
+    }
+    __syncthreads();
+    if (threadIdx.x < 8) {
+        const int q = threadIdx.x;
+        double val = 0.0;
+        if (q < 7)
+            for (int wdx = 0; wdx < kErrThreads / 32; ++wdx)
+                val = (q == 6) ? fmax(val, red[wdx][q]) : val + red[wdx][q];
+        part[(size_t)s * 8 + q] = val;
+    }
+}
+
+__global__ void __launch_bounds__(kErrThreads) k_errors_owner_f64(Geo g, const int32_t *boxes,
                                                               const double *centres,
                                                               const double *beta,
                                                               const int32_t *info, const double *K,
@@ -874,11 +972,7 @@ __global__ void __launch_bounds__(kErrThreads) k_errors_owner(Geo g, const int32
     extern __shared__ uint8_t smb[];
     dvec4 *sc64 = reinterpret_cast<dvec4 *>(smb);
     double *sb64 = reinterpret_cast<double *>(sc64 + g.m_cap);
-    float4 *sc32 = reinterpret_cast<float4 *>(smb);
-    float *sb32 = reinterpret_cast<float *>(sc32 + g.m_cap);
-    double o[3];
-    if (F32) stage_f32(g, boxes, centres, beta, s, M, sc32, sb32, o);
-    else stage_f64(g, centres, beta, s, M, sc64, sb64);
+    stage_f64(g, centres, beta, s, M, sc64, sb64);
     const int w0 = box[3] - box[0], w1 = box[4] - box[1], w2 = box[5] - box[2];
     const int cnt = w0 * w1 * w2;
     double acc[7] = {0, 0, 0, 0, 0, 0, 0};
@@ -900,13 +994,8 @@ __global__ void __launch_bounds__(kErrThreads) k_errors_owner(Geo g, const int32
             double x[3] = {xc[0], xc[1], xc[2]};
             if (quad)
                 for (int a = 0; a < g.dim; ++a) x[a] = __dadd_rn(xc[a], ((q >> a) & 1) ? off : -off);
-            double v;
-            if (F32)
-                v = (double)shepard_f32_smem(sc32, sb32, M, (float)(x[0] - o[0]), (float)(x[1] - o[1]),
-                                             (float)(x[2] - o[2]));
-            else
-                v = shepard_f64_smem(sc64, sb64, M, x);
-            const double ks = F32 ? exp_f32((float)v) : exp(v);
+            const double v = shepard_f64_smem(sc64, sb64, M, x);
+            const double ks = exp(v);
             acc[0] += wq * fabs(kk - ks);
             acc[2] += wq * ((kk - ks) * (kk - ks));
             acc[4] += wq * fabs(lk - v);
@@ -965,13 +1054,13 @@ void launch_errors(const Geo &g, const int32_t *boxes, const double *centres, co
                    const Ws &w, cudaStream_t st, int row0, int row1) {
     PhaseScope ps(kPhErrors, st);
     if (precision == PAM_PREC_MIXED) {
-        size_t sm = stage_f32_smem(g.m_cap);
-        cudaFuncSetAttribute(k_errors_owner<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_errors_owner<true><<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, quad, w.err_part);
+        size_t sm = stage_f32s_smem(g.m_cap);
+        cudaFuncSetAttribute(k_errors_owner_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_errors_owner_f32<<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, quad, w.err_part);
     } else {
         size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));
-        cudaFuncSetAttribute(k_errors_owner<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_errors_owner<false><<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, quad, w.err_part);
+        cudaFuncSetAttribute(k_errors_owner_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+        k_errors_owner_f64<<<g.S, kErrThreads, sm, st>>>(g, boxes, centres, beta, info, K, quad, w.err_part);
     }
     if (row1 < 0)  // the ratios over every subdomain
         k_errors_combine<<<1, 256, 0, st>>>(w.err_part, g.S, err, 0);

@@ -228,22 +228,34 @@ __device__ __forceinline__ double cell_measure(const Geo &g, int s, int t) {
     return g.cxv ? g.cxv[(size_t)s * g.n_max + t].w : g.vol;
 }
 
-// Index of the core interval [floor(j n / p), floor((j+1) n / p)) holding
-// cell index i along an axis.
+// Core j of cell i along an axis of n cells split into p cores ([j n / p,
+// (j + 1) n / p) in floor division): j0 = floor(i p / n), plus one where
+// floor((j0 + 1) n / p) <= i, i.e. (j0 + 1) n < (i + 1) p. One integer
+// division, 32-bit where i p fits (always, below 2^16 cells per axis).
 __device__ __forceinline__ int core_of(int i, int n, int p) {
-    int j = (int)(((int64_t)i * p) / n);
-    if (j + 1 < p && (((int64_t)(j + 1) * n) / p) <= i) ++j;
+    const uint64_t ip = (uint64_t)i * (uint64_t)p;
+    int j = ip <= 0xffffffffull ? (int)((uint32_t)ip / (uint32_t)n) : (int)(ip / (uint64_t)n);
+    if (j + 1 < p && (uint64_t)(j + 1) * (uint64_t)n < ip + (uint64_t)p) ++j;
     return j;
 }
 
-// Owner subdomain of a point (half-open cores, outer face closed), -1 outside.
+// Owner subdomain of a point (half-open cores, outer face closed), -1 outside
+// or NaN. The cell index is floor(x n_max) in binary64; past the sign test
+// the range test is made on it in integers (u in [0, n] <=> i in [0, n), or
+// i = n with u = n), which spares the narrow binary64 pipe a comparison.
 __device__ __forceinline__ int owner_of_point(const Geo &g, const double x[3]) {
     int j[3] = {0, 0, 0};
-    for (int a = 0; a < g.dim; ++a) {
-        double u = x[a] * (double)g.nmax;
-        if (!(u >= 0.0) || u > (double)g.n[a]) return -1;
-        int i = (int)floor(u);
-        if (i >= g.n[a]) i = g.n[a] - 1;
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        if (a >= g.dim) break;
+        const double u = x[a] * (double)g.nmax;
+        if (!(u >= 0.0)) return -1;
+        int i = __double2int_rd(u);  // beyond the int range: INT_MAX
+        if (i > g.n[a]) return -1;
+        if (i == g.n[a]) {
+            if (u != (double)g.n[a]) return -1;
+            i = g.n[a] - 1;
+        }
         j[a] = core_of(i, g.n[a], g.p[a]);
     }
     return j[0] + g.p[0] * (j[1] + g.p[1] * j[2]);

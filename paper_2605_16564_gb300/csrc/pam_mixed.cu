@@ -91,11 +91,18 @@ __device__ __forceinline__ void local_cell(const Geo &g, int s, const int32_t *b
 // whose plain sum falls below 2^-100 takes a second pass with the running
 // maximum as the shift (the sum rescaled whenever the maximum grows).
 // --------------------------------------------------------------------------
-__device__ __noinline__ void stats_max_shift(const float4 *sc, int M, const float x[3], float *lmax_out,
+// Centre m of the statistics' shared-memory table, stored for the packed
+// two-cell arithmetic as (-c_x, -c_x, -c_y, -c_y), (-c_z, -c_z, alpha, alpha).
+__device__ __forceinline__ float4 stats_centre(const float4 *scp, int m) {
+    const float4 a = scp[2 * m], b = scp[2 * m + 1];
+    return make_float4(-a.x, -a.z, -b.x, b.z);
+}
+
+__device__ __noinline__ void stats_max_shift(const float4 *scp, int M, const float x[3], float *lmax_out,
                                              float *sum_out) {
     float lmax = -INFINITY, sum = 0.0f;
     for (int m = 0; m < M; ++m) {
-        const float l = logit2(sc[m], x[0], x[1], x[2]);
+        const float l = logit2(stats_centre(scp, m), x[0], x[1], x[2]);
         if (l > lmax) {
             sum = fmaf(sum, tc::ex2(lmax - l), 1.0f);
             lmax = l;
@@ -107,14 +114,17 @@ __device__ __noinline__ void stats_max_shift(const float4 *sc, int M, const floa
     *sum_out = sum;
 }
 
-__device__ __forceinline__ void stats_store(const Ws &w, size_t o, const float4 *sc, int M, const float x[3],
+__device__ __forceinline__ void stats_store(const Ws &w, size_t o, const float4 *scp, int M, const float x[3],
                                             float sum) {
     float shift = 0.0f;
-    if (!(sum > 0x1p-100f)) stats_max_shift(sc, M, x, &shift, &sum);
+    if (!(sum > 0x1p-100f)) stats_max_shift(scp, M, x, &shift, &sum);
     w.rowmax[o] = shift;
     w.rowinv[o] = 1.0f / sum;
 }
 
+// The two cells of a thread go through each centre together, one per half of
+// each packed fp32x2 operation: the same operations, in the same order, as
+// logit2 and the scalar sum of each cell.
 __global__ void __launch_bounds__(256) k_stats_f32(Geo g, const int32_t *boxes,
                                                    const double *centres, const int32_t *info,
                                                    Ws w, int all) {
@@ -123,11 +133,15 @@ __global__ void __launch_bounds__(256) k_stats_f32(Geo g, const int32_t *boxes,
     if (!all && inf[PAM_INFO_STOPPED]) return;
     const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
     const int32_t *box = boxes + s * 12;
-    extern __shared__ float4 sc[];
+    extern __shared__ float4 scp[];  // [2 * m_cap]
     double o[3];
     patch_origin(g, box, o);
     const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
-    for (int m = threadIdx.x; m < M; m += blockDim.x) sc[m] = local_centre(cg[m], o);
+    for (int m = threadIdx.x; m < M; m += blockDim.x) {
+        const float4 c = local_centre(cg[m], o);
+        scp[2 * m] = make_float4(-c.x, -c.x, -c.y, -c.y);
+        scp[2 * m + 1] = make_float4(-c.z, -c.z, c.w, c.w);
+    }
     __syncthreads();
     const int t0 = blockIdx.x * 2 * blockDim.x + threadIdx.x, t1 = t0 + blockDim.x;
     if (t0 >= N) return;
@@ -135,15 +149,22 @@ __global__ void __launch_bounds__(256) k_stats_f32(Geo g, const int32_t *boxes,
     float x0[3], x1[3];
     local_cell(g, s, box, t0, x0);
     local_cell(g, s, box, two ? t1 : t0, x1);
-    float s0 = 0.0f, s1 = 0.0f;
+    const float2 X = make_float2(x0[0], x1[0]), Y = make_float2(x0[1], x1[1]), Z = make_float2(x0[2], x1[2]);
+    float2 sum = make_float2(0.f, 0.f);
     for (int m = 0; m < M; ++m) {
-        const float4 c = sc[m];
-        s0 += tc::ex2(logit2(c, x0[0], x0[1], x0[2]));
-        s1 += tc::ex2(logit2(c, x1[0], x1[1], x1[2]));
+        const float4 a = scp[2 * m], b = scp[2 * m + 1];
+        const float2 dx = __fadd2_rn(X, make_float2(a.x, a.y));
+        const float2 dy = __fadd2_rn(Y, make_float2(a.z, a.w));
+        const float2 dz = __fadd2_rn(Z, make_float2(b.x, b.y));
+        float2 d2 = __fmul2_rn(dx, dx);
+        d2 = __ffma2_rn(dy, dy, d2);
+        d2 = __ffma2_rn(dz, dz, d2);
+        const float2 l = __fmul2_rn(make_float2(b.z, b.w), d2);
+        sum = __fadd2_rn(make_float2(tc::ex2(l.x), tc::ex2(l.y)), sum);
     }
     const size_t row = (size_t)s * g.n_max;
-    stats_store(w, row + t0, sc, M, x0, s0);
-    if (two) stats_store(w, row + t1, sc, M, x1, s1);
+    stats_store(w, row + t0, scp, M, x0, sum.x);
+    if (two) stats_store(w, row + t1, scp, M, x1, sum.y);
 }
 
 // --------------------------------------------------------------------------
@@ -725,7 +746,7 @@ void launch_gram_tc(const Geo &g, const int32_t *boxes, const double *centres, c
 void launch_stats_f32(const Geo &g, const int32_t *boxes, const double *centres, const int32_t *info,
                       const Ws &w, cudaStream_t st, int all) {
     PhaseScope ps(kPhStats, st);
-    size_t sm = (size_t)g.m_cap * sizeof(float4);
+    size_t sm = (size_t)g.m_cap * 2 * sizeof(float4);
     cudaFuncSetAttribute(k_stats_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     // two cells per thread, 512 per block: every block converts the M
     // centres once (binary64 offsets on the narrow fp64 pipe), so fewer,
