@@ -540,7 +540,9 @@ pam_status pam_nn_sizes(int arch, int batch, int64_t *n_params, size_t *workspac
 /* h_geo [3] = (input pixels per side, input channels, n_out). */
 pam_status pam_nn_geometry(int arch, int32_t *h_geo);
 pam_status pam_nn_layer_offsets(int arch, int64_t *h_offsets /* [6][4] */);
-/* d_x [batch][h][h][c] fp32; d_out [batch][2 n_out] fp32 (logits | beta/4). */
+/* d_x [batch][h][h][c] fp32; d_out [batch][2 n_out] fp32 (logits | beta/4).
+ * Convolutions with a power-of-two input channel count >= 8 read their input
+ * directly (no im2col matrix); the sums are those of the training pass. */
 pam_status pam_nn_forward(int arch, const float *d_params, const float *d_x, int batch, float *d_out,
                           void *d_workspace, size_t workspace_bytes, void *stream);
 /* Forward + loss + backward: d_grads (same layout as the parameters) and

@@ -87,10 +87,19 @@ static Layout layout(const Arch &A) {
 constexpr int kGT = 256;
 constexpr long long kGemmWait = 4000000000LL;
 
+// Implicit-convolution A operand (inference): with h > 0, A is the NHWC
+// activation [B][h][h][c] of a 3x3 pad-1 convolution (c = 2^c_log2 >= 8) and
+// row p, column k of the operand are those the im2col matrix would hold
+// (tap = k / c, channel k mod c; zero past 9 c and outside the image), read
+// 8 channels (16 bytes) at a time straight from the activation.
+struct ImplicitConv {
+    int h, c_log2, ho, stride;
+};
+
 __global__ void __launch_bounds__(kGT, 1) k_gemm_bf16(const bf16 *A, int lda, const bf16 *B, int ldb,
                                                       int M, int N, int K, float *C32, bf16 *C16,
                                                       int ldc, const float *bias, int relu,
-                                                      int32_t *status) {
+                                                      int32_t *status, ImplicitConv ic) {
     const int m0 = blockIdx.x * 128, n0 = blockIdx.y * 128;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int nt = min(128, ((N - n0) + 15) & ~15);  // MMA N of this tile
@@ -121,6 +130,21 @@ __global__ void __launch_bounds__(kGT, 1) k_gemm_bf16(const bf16 *A, int lda, co
     // the current one is synchronised and multiplied
     constexpr int kSeg = 1024 / kGT;
     uint4 pre[kSeg];
+    // implicit operand: this thread's A rows (u = 0, 1) as (image base, top-left input pixel)
+    const bf16 *img[2] = {A, A};
+    int iy0[2] = {0, 0}, ix0[2] = {0, 0};
+    if (ic.h > 0) {
+#pragma unroll
+        for (int u = 0; u < 2; ++u) {
+            const int r = ((tid + u * kGT) & 511) >> 2;
+            const int64_t pidx = (int64_t)m0 + r;
+            const int ox = (int)(pidx % ic.ho), oy = (int)((pidx / ic.ho) % ic.ho);
+            const int64_t b = pidx / ((int64_t)ic.ho * ic.ho);
+            img[u] = A + (b * ic.h * ic.h << ic.c_log2);
+            iy0[u] = oy * ic.stride - 1;
+            ix0[u] = ox * ic.stride - 1;
+        }
+    }
     auto load_chunk = [&](int kc) {
 #pragma unroll
         for (int u = 0; u < kSeg; ++u) {
@@ -128,7 +152,19 @@ __global__ void __launch_bounds__(kGT, 1) k_gemm_bf16(const bf16 *A, int lda, co
             const int isb = e >> 9, seg = e & 511, r = seg >> 2, kg = seg & 3;
             uint4 v = make_uint4(0, 0, 0, 0);
             if (isb == 0) {
-                if (m0 + r < M) v = *reinterpret_cast<const uint4 *>(A + (size_t)(m0 + r) * lda + kc * 32 + kg * 8);
+                if (m0 + r < M) {
+                    if (ic.h > 0) {
+                        const int k = kc * 32 + kg * 8, tap = k >> ic.c_log2;
+                        if (tap < 9) {
+                            const int ky = tap / 3, iy = iy0[u] + ky, ix = ix0[u] + (tap - 3 * ky);
+                            if (iy >= 0 && iy < ic.h && ix >= 0 && ix < ic.h)
+                                v = *reinterpret_cast<const uint4 *>(
+                                    img[u] + (((int64_t)(iy * ic.h + ix) << ic.c_log2) + (k & ((1 << ic.c_log2) - 1))));
+                        }
+                    } else {
+                        v = *reinterpret_cast<const uint4 *>(A + (size_t)(m0 + r) * lda + kc * 32 + kg * 8);
+                    }
+                }
             } else {
                 if (n0 + r < N) v = *reinterpret_cast<const uint4 *>(B + (size_t)(n0 + r) * ldb + kc * 32 + kg * 8);
             }
@@ -205,12 +241,22 @@ __global__ void __launch_bounds__(kGT, 1) k_gemm_bf16(const bf16 *A, int lda, co
 }
 
 static void gemm(const bf16 *A, int lda, const bf16 *B, int ldb, int M, int N, int K, float *C32,
-                 bf16 *C16, int ldc, const float *bias, int relu, int32_t *status, cudaStream_t st) {
+                 bf16 *C16, int ldc, const float *bias, int relu, int32_t *status, cudaStream_t st,
+                 ImplicitConv ic = {0, 0, 0, 0}) {
     // M tiles on x (up to 2^31 - 1 blocks): a 65,536-row forward pass has
     // 2^17 row tiles in its first convolution
     dim3 grid((M + 127) / 128, (N + 127) / 128);
-    k_gemm_bf16<<<grid, kGT, 32768 + 1024, st>>>(A, lda, B, ldb, M, N, K, C32, C16, ldc, bias, relu, status);
+    k_gemm_bf16<<<grid, kGT, 32768 + 1024, st>>>(A, lda, B, ldb, M, N, K, C32, C16, ldc, bias, relu, status, ic);
     count_launches(1);
+}
+
+// log2 c if c is a power of two of at least 8 (the implicit operand's
+// 16-byte reads stay inside one tap), else -1.
+static int implicit_c_log2(int c) {
+    if (c < 8 || (c & (c - 1))) return -1;
+    int l = 0;
+    while ((1 << l) < c) ++l;
+    return l;
 }
 
 // --------------------------------------------------------------- helpers --
@@ -485,7 +531,11 @@ static Ws carve(const Arch &A, int B, void *base) {
 }
 
 // Forward pass; activations stay in the workspace for the backward pass.
-static void forward(const Arch &A, const float *params, const float *x, int B, Ws &w, cudaStream_t st) {
+// implicit: inference only -- the convolutions read their input directly
+// (no im2col matrix; the backward pass needs it, so training passes false).
+// The operands, their order and the sums are the same either way.
+static void forward(const Arch &A, const float *params, const float *x, int B, Ws &w, cudaStream_t st,
+                    bool implicit = false, float *out = nullptr) {
     const Layout L = layout(A);
     const int64_t nx = (int64_t)B * A.h0 * A.h0 * A.c0;
     k_cast_bf16<<<grid_for(L.total), 256, 0, st>>>(params, w.pw, L.total);
@@ -496,6 +546,13 @@ static void forward(const Arch &A, const float *params, const float *x, int B, W
         const Conv &c = A.conv[l];
         const int64_t rows = (int64_t)B * c.hout * c.hout;
         const unsigned blocks = (unsigned)std::min<int64_t>(rows, 16384);
+        const int cl = implicit_c_log2(c.cin);
+        if (implicit && cl >= 0) {
+            gemm(in, 0, w.pw + L.w[l], c.kpad, (int)rows, c.cout, c.kpad, nullptr, w.act[l], c.cout,
+                 params + L.b[l], 1, w.status, st, ImplicitConv{c.hin, cl, c.hout, c.stride});
+            in = w.act[l];
+            continue;
+        }
         if (c.cin % 8 == 0) {
             const int kv = c.kpad / 8, thr = kv < 256 ? (kv + 31) / 32 * 32 : 256;
             k_im2col_v8<<<blocks, thr, 0, st>>>(in, B, c.hin, c.cin, c.hout, c.stride, c.kpad, w.cols[l]);
@@ -512,7 +569,8 @@ static void forward(const Arch &A, const float *params, const float *x, int B, W
     const int d0 = A.dense[0].out, d1 = A.dense[1].out;
     gemm(w.act[3], A.flat, w.pw + L.w[4], A.flat, B, d0, A.flat, nullptr, w.act[4], d0, params + L.b[4], 1,
          w.status, st);
-    gemm(w.act[4], d0, w.pw + L.w[5], d0, B, d1, d0, w.out, nullptr, d1, params + L.b[5], 0, w.status, st);
+    gemm(w.act[4], d0, w.pw + L.w[5], d0, B, d1, d0, out ? out : w.out, nullptr, d1, params + L.b[5], 0, w.status,
+         st);
 }
 
 // Backward of a layer y = relu(X W^T + b) (or linear for the output layer):
@@ -625,8 +683,7 @@ pam_status pam_nn_forward(int arch, const float *d_params, const float *d_x, int
     Ws w = carve(*A, batch, d_workspace);
     PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 16, s));
     cudaFuncSetAttribute(k_gemm_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, 32768 + 1024);
-    forward(*A, d_params, d_x, batch, w, s);
-    PAM_CUDA_TRY(cudaMemcpyAsync(d_out, w.out, (size_t)batch * A->dense[1].out * 4, cudaMemcpyDeviceToDevice, s));
+    forward(*A, d_params, d_x, batch, w, s, true, d_out);
     PAM_CUDA_TRY(cudaGetLastError());
     return PAM_OK;
 }
