@@ -793,7 +793,9 @@ __host__ __device__ __forceinline__ int mark_sort_len(int n) {
     return P;
 }
 
-__global__ void __launch_bounds__(kMarkThreads) k_mark_enrich(Geo g, Par p, const int32_t *boxes,
+// six blocks per SM (40 registers): the kernel is latency-bound (a sort and
+// short per-cell searches between block barriers), so resident blocks pay
+__global__ void __launch_bounds__(kMarkThreads, 6) k_mark_enrich(Geo g, Par p, const int32_t *boxes,
                                                               double *centres, double *beta,
                                                               int32_t *info, Ws w) {
     const int s = blockIdx.x;
