@@ -294,10 +294,10 @@ FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # layered 3-D workload: ncu of the last level's launch on the quarter-size
 # workload (561 of the 2,244 subdomains, same subdomain shape), scaled by 4
 # (profiles/solve_layered3d_quarter_mixed.md for the solve,
-# profiles/kernels_layered3d_quarter_mixed.md for the evaluation). Only valid
-# for that workload and for the kernels as captured (the statistics and the
-# tensor-core Gram changed after their last capture: none recorded).
-TRAFFIC_LAYERED3D = {"k_solve_mixed": 1.406e9, "k_eval_bucket_f32": 3.06e8}
+# profiles/gram_tc_layered3d_quarter_mixed.md for the tensor-core Gram and the
+# evaluation). Only valid for that workload and for the kernels as captured
+# (the statistics changed after their last capture: none recorded).
+TRAFFIC_LAYERED3D = {"k_solve_mixed": 1.406e9, "k_gram_tc": 1.224e9, "k_eval_bucket_f32": 2.94e8}
 TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the level-3 launch (eval: its one launch), "
                 "captured on layered3d_quarter and scaled x4 by subdomains")
 
