@@ -885,6 +885,26 @@ struct DFAcc {
     __device__ __forceinline__ double value() const { return (double)s + (double)c; }
 };
 
+// Two DFAcc sums in the halves of packed fp32x2 registers, each half the
+// same operations in the same order as DFAcc::add_prod (a subtraction y - x
+// as fma(x, -1, y), rounded once like __fsub_rn; -p as a times -b).
+struct DFAcc2 {
+    float2 s = make_float2(0.f, 0.f), c = make_float2(0.f, 0.f);
+    __device__ __forceinline__ void add_prod(float2 a, float2 b, float2 nb) {
+        const float2 m1 = make_float2(-1.f, -1.f);
+        const float2 p = __fmul2_rn(a, b);
+        const float2 pe = __ffma2_rn(a, b, __fmul2_rn(a, nb));  // a b - p, exact
+        const float2 t = __fadd2_rn(s, p);
+        const float2 bp = __ffma2_rn(s, m1, t);
+        const float2 err = __fadd2_rn(__ffma2_rn(__ffma2_rn(bp, m1, t), m1, s), __ffma2_rn(bp, m1, p));
+        s = t;
+        c = __fadd2_rn(c, __fadd2_rn(err, pe));
+    }
+    __device__ __forceinline__ double value() const {
+        return ((double)s.x + (double)c.x) + ((double)s.y + (double)c.y);
+    }
+};
+
 // Cross-validation form (cv != nullptr, p.cv_folds > 0): the system is that
 // of the training rows of fold p.cv_fold (G~ and b masked by the Gram, the
 // exact gradient over the training cells only), lambda_k = N_train
@@ -919,11 +939,27 @@ __device__ __forceinline__ void solve_mixed_item(const Geo &g, const Par &p, con
     float *rhs = bv + mc;                         // [mc]
     int *sg = reinterpret_cast<int *>(rhs + mc);  // [mc]
     int *idx = sg + mc;                           // [mc]
+    // cells in pairs (2p, 2p + 1) and the support in pairs (2q, 2q + 1), for
+    // the packed fp32x2 arithmetic of the exact-gradient passes
+    const int np2 = (g.n_max + 1) >> 1, ns2 = (mc >> 1) + 2;
     float4 *sc = reinterpret_cast<float4 *>(idx + mc);      // [mc] local centres
-    float4 *cell = sc + mc;                                 // [n_max] (x, y, z, rowmax)
-    float *cinv = reinterpret_cast<float *>(cell + g.n_max);// [n_max]
-    float *ce = cinv + g.n_max;                             // [n_max] y, then e = y - W x
-    float *dinv = ce + g.n_max;                             // [mc] 1 / diag of the factor
+    float4 *cella = sc + mc;                                // [np2] (x, x', y, y')
+    float4 *cellb = cella + np2;                            // [np2] (z, z', -rowmax, -rowmax')
+    float4 *supa = cellb + np2;                             // [ns2] (-c_x, -c_x', -c_y, -c_y')
+    float4 *supb = supa + ns2;                              // [ns2] (-c_z, -c_z', alpha, alpha')
+    float2 *supx = reinterpret_cast<float2 *>(supb + ns2);  // [ns2] (x_m, x_m')
+    float2 *supn = supx + ns2;                              // [ns2] (-x_m, -x_m')
+    float *cinv = reinterpret_cast<float *>(supn + ns2);    // [2 np2] 0 past the patch
+    float *ce = cinv + 2 * np2;                             // [2 np2] e = y - W x (0 past the patch)
+    const float2 *cinv2 = reinterpret_cast<const float2 *>(cinv), *ce2 = reinterpret_cast<const float2 *>(ce);
+    // cell t as (x, y, z, rowmax)
+    auto cell_at = [&](int t) {
+        const float *fa = reinterpret_cast<const float *>(cella + (t >> 1));
+        const float *fb = reinterpret_cast<const float *>(cellb + (t >> 1));
+        const int h = t & 1;
+        return make_float4(fa[h], fa[2 + h], fb[h], -fb[2 + h]);
+    };
+    float *dinv = ce + 2 * np2;                             // [mc] 1 / diag of the factor
     float *ub = dinv + mc;                                  // [mc] bounds on |c_j| off the support
     float *Lt = ub + mc;                                    // [32 x 32] factorisation scratch
     float *Asm = Lt + kCholLtFloats;                        // packed factor
@@ -955,11 +991,22 @@ __device__ __forceinline__ void solve_mixed_item(const Geo &g, const Par &p, con
         bv[j] = j < M ? (float)w.b[(size_t)s * mc + j] : 0.f;
         sg[j] = (j < M) ? ((b0 > 0.f) - (b0 < 0.f)) : 0;
     }
-    for (int t = tid; t < N; t += blockDim.x) {
-        float xl[3];
-        local_cell(g, s, box, t, xl);
-        cell[t] = make_float4(xl[0], xl[1], xl[2], rowmax[t]);
-        cinv[t] = rowinv[t];
+    for (int t = tid; t < 2 * np2; t += blockDim.x) {
+        float xl[3] = {0.f, 0.f, 0.f};
+        float nrm = -INFINITY, ci = 0.f;  // past the patch: weight 0
+        if (t < N) {
+            local_cell(g, s, box, t, xl);
+            nrm = -rowmax[t];
+            ci = rowinv[t];
+        }
+        float *fa = reinterpret_cast<float *>(cella + (t >> 1)), *fb = reinterpret_cast<float *>(cellb + (t >> 1));
+        const int h = t & 1;
+        fa[h] = xl[0];
+        fa[2 + h] = xl[1];
+        fb[h] = xl[2];
+        fb[2 + h] = nrm;
+        cinv[t] = ci;
+        ce[t] = 0.f;
     }
     if (tid == 0) sh.flag = 0;
     __syncthreads();
@@ -1185,12 +1232,37 @@ __device__ __forceinline__ void solve_mixed_item(const Geo &g, const Par &p, con
         // accumulated in double-float and subtracted in fp64: |y| ~ 10 would
         // otherwise leave ~1e-6 of cancellation noise in e, and W^T e inherits it
         held = 0.0;
+        PROF_MARK(15);  // the previous iteration's Newton step and refactorisation
+        // the support in pairs (an odd one out paired with alpha = 0, x = 0)
+        const int nsp = (scnt + 1) >> 1;
+        for (int q = tid; q < nsp; q += blockDim.x) {
+            const bool two = 2 * q + 1 < scnt;
+            const int m0 = idx[2 * q], m1 = two ? idx[2 * q + 1] : m0;
+            const float4 c0 = sc[m0], c1 = two ? sc[m1] : make_float4(0.f, 0.f, 0.f, 0.f);
+            const float x0 = x[m0], x1 = two ? x[m1] : 0.f;
+            supa[q] = make_float4(-c0.x, -c1.x, -c0.y, -c1.y);
+            supb[q] = make_float4(-c0.z, -c1.z, c0.w, c1.w);
+            supx[q] = make_float2(x0, x1);
+            supn[q] = make_float2(-x0, -x1);
+        }
+        __syncthreads();
         for (int t = tid; t < N; t += blockDim.x) {
-            const float4 cx = cell[t];
-            DFAcc acc;
-            for (int pp = 0; pp < scnt; ++pp) {
-                const int m = idx[pp];
-                acc.add_prod(tc::ex2(logit2(sc[m], cx.x, cx.y, cx.z) - cx.w), x[m]);
+            const float4 cx = cell_at(t);
+            const float2 X = make_float2(cx.x, cx.x), Y = make_float2(cx.y, cx.y), Z = make_float2(cx.z, cx.z);
+            const float2 nrm = make_float2(-cx.w, -cx.w);
+            DFAcc2 acc;
+#pragma unroll 2
+            for (int q = 0; q < nsp; ++q) {
+                // per half: ex2(logit2(c_m, x) - rowmax), as in the scalar form
+                const float4 a = supa[q], b = supb[q];
+                const float2 dx = __fadd2_rn(X, make_float2(a.x, a.y));
+                const float2 dy = __fadd2_rn(Y, make_float2(a.z, a.w));
+                const float2 dz = __fadd2_rn(Z, make_float2(b.x, b.y));
+                float2 d2 = __fmul2_rn(dx, dx);
+                d2 = __ffma2_rn(dy, dy, d2);
+                d2 = __ffma2_rn(dz, dz, d2);
+                const float2 l = __fadd2_rn(__fmul2_rn(make_float2(b.z, b.w), d2), nrm);
+                acc.add_prod(make_float2(tc::ex2(l.x), tc::ex2(l.y)), supx[q], supn[q]);
             }
             const float e = (float)(yv[t] - acc.value() * (double)cinv[t]);
             if (folds > 0 && t % folds == fold) {  // held out: not in the gradient
@@ -1217,17 +1289,42 @@ __device__ __forceinline__ void solve_mixed_item(const Geo &g, const Par &p, con
         }
         __syncthreads();
         float cmax = 0.f;
-        for (int q = tid; q < sh.nneed; q += blockDim.x) {
-            const int j = need[q];
+        const int ncp = (N + 1) >> 1;  // cell pairs (the odd one out pairs with weight 0)
+        // gq threads per centre (a power of two up to 8, as many as the list
+        // leaves room for), each over every gq-th cell pair, summed in a fixed
+        // butterfly order: short lists keep every thread busy
+        const int nneed = sh.nneed;
+        int gq = 1;
+        while (gq < 8 && nneed * gq * 2 <= (int)blockDim.x) gq <<= 1;
+        const int per_sweep = (int)blockDim.x / gq, sub = tid % gq;
+        for (int q0 = 0; q0 < nneed; q0 += per_sweep) {
+            const int q = q0 + tid / gq;
+            const bool act = q < nneed;
+            const int j = need[act ? q : 0];
             const float4 cj = sc[j];
-            float acc = 0.f;
-            for (int t = 0; t < N; ++t) {
-                const float4 cx = cell[t];
-                acc = fmaf(tc::ex2(logit2(cj, cx.x, cx.y, cx.z) - cx.w) * cinv[t], ce[t], acc);
+            const float2 ncx = make_float2(-cj.x, -cj.x), ncy = make_float2(-cj.y, -cj.y);
+            const float2 ncz = make_float2(-cj.z, -cj.z), cw = make_float2(cj.w, cj.w);
+            float2 acc2 = make_float2(0.f, 0.f);  // even and odd cells
+            for (int pc = sub; pc < ncp; pc += gq) {
+                // per half: fma(ex2(logit2(c_j, x_t) - rowmax_t) cinv_t, e_t, acc)
+                const float4 a = cella[pc], b = cellb[pc];
+                const float2 dx = __fadd2_rn(make_float2(a.x, a.y), ncx);
+                const float2 dy = __fadd2_rn(make_float2(a.z, a.w), ncy);
+                const float2 dz = __fadd2_rn(make_float2(b.x, b.y), ncz);
+                float2 d2 = __fmul2_rn(dx, dx);
+                d2 = __ffma2_rn(dy, dy, d2);
+                d2 = __ffma2_rn(dz, dz, d2);
+                const float2 l = __fadd2_rn(__fmul2_rn(cw, d2), make_float2(b.z, b.w));
+                const float2 wt = __fmul2_rn(make_float2(tc::ex2(l.x), tc::ex2(l.y)), cinv2[pc]);
+                acc2 = __ffma2_rn(wt, ce2[pc], acc2);
             }
-            gr[j] = acc;
-            ub[j] = fabsf(acc);
-            cmax = fmaxf(cmax, fabsf(acc));
+            float acc = acc2.x + acc2.y;
+            for (int o = 1; o < gq; o <<= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+            if (act && sub == 0) {
+                gr[j] = acc;
+                ub[j] = fabsf(acc);
+                cmax = fmaxf(cmax, fabsf(acc));
+            }
         }
         if (tid == 0) { sh.viol = 0; sh.changed = 0; sh.dmax = 0.f; sh.xmax = 0.f; }
         __syncthreads();
@@ -1320,7 +1417,7 @@ __device__ __forceinline__ void solve_mixed_item(const Geo &g, const Par &p, con
         if (!certified) {
             held = 0.0;
             for (int t = fold + folds * tid; t < N; t += folds * (int)blockDim.x) {
-                const float4 cx = cell[t];
+                const float4 cx = cell_at(t);
                 DFAcc acc;
                 for (int pp = 0; pp < scnt; ++pp) {
                     const int m = idx[pp];
@@ -1347,7 +1444,7 @@ __device__ __forceinline__ void solve_mixed_item(const Geo &g, const Par &p, con
     }
     // otherwise x changed after the last pass: e = y - W x once more
     for (int t = tid; t < N && !certified && !cv; t += blockDim.x) {
-        const float4 cx = cell[t];
+        const float4 cx = cell_at(t);
         DFAcc acc;
         for (int pp = 0; pp < scnt; ++pp) {
             const int m = idx[pp];
@@ -1453,8 +1550,10 @@ __global__ void __launch_bounds__(1024) k_solve_order(const uint32_t *cost, int 
 
 // Shared memory of the mixed solve besides the packed factor.
 static size_t solve_mixed_smem_rest(const Geo &g) {
+    const size_t np2 = (size_t)(g.n_max + 1) / 2, ns2 = (size_t)g.m_cap / 2 + 2;
     return (size_t)g.m_cap * (6 * sizeof(float) + 2 * sizeof(int) + sizeof(float4)) +
-           (size_t)g.n_max * (sizeof(float4) + 2 * sizeof(float)) + kCholLtFloats * sizeof(float) + 64;
+           np2 * 2 * (sizeof(float4) + 2 * sizeof(float)) + ns2 * 2 * (sizeof(float4) + sizeof(float2)) +
+           kCholLtFloats * sizeof(float) + 64;
 }
 
 // Shared-memory budget of the packed support factor (larger supports keep
