@@ -658,7 +658,9 @@ pam_status pam_selftest_wait(int arrive, long long budget_cycles, int32_t *d_fla
  * CUDA event pair around its launches on the caller's stream; reading sums
  * the elapsed times per family (and synchronises on the recorded events).
  * Families: PAM_PHASE_* (prepare, assemble, gram, solve, residual, mark,
- * eval, errors, stats, gram_tc, refine). Not thread-safe against concurrent
+ * eval, errors, stats, gram_tc, refine, eval_kernel: the evaluation's
+ * per-owner kernel alone, inside eval, which adds the owner lookup, scan and
+ * scatter). Not thread-safe against concurrent
  * enable/reset; intended for benchmarks. No counterpart in the paper.
  * Calls made while `stream` is being captured into a CUDA graph record the
  * pairs as event-record nodes of the graph: each replay re-records them, so
@@ -669,7 +671,7 @@ pam_status pam_selftest_wait(int arrive, long long budget_cycles, int32_t *d_fla
 enum {
     PAM_PHASE_PREPARE = 0, PAM_PHASE_ASSEMBLE, PAM_PHASE_GRAM, PAM_PHASE_SOLVE,
     PAM_PHASE_RESIDUAL, PAM_PHASE_MARK, PAM_PHASE_EVAL, PAM_PHASE_ERRORS,
-    PAM_PHASE_STATS, PAM_PHASE_GRAM_TC, PAM_PHASE_REFINE, PAM_PHASE_COUNT
+    PAM_PHASE_STATS, PAM_PHASE_GRAM_TC, PAM_PHASE_REFINE, PAM_PHASE_EVAL_KERNEL, PAM_PHASE_COUNT
 };
 void pam_timing_enable(int on);
 /* Kernels this library has launched since it was loaded (host-side count). */

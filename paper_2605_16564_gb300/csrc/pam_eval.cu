@@ -454,16 +454,19 @@ void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, cons
     k_eval_owner<<<nb, 256, 0, st>>>(g, pts, n_pts, e.owner, e.rank, e.count, out);
     k_eval_scan<<<1, 1024, 0, st>>>(e.count, e.start, g.S);
     k_eval_scatter<<<nb, 256, 0, st>>>(e.owner, e.rank, e.start, e.perm, n_pts);
-    if (precision == PAM_PREC_MIXED) {
-        size_t sm = stage_f32s_smem(g.m_cap);
-        cudaFuncSetAttribute(k_eval_bucket_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_eval_bucket_f32<<<g.S, eval_block(), sm, st>>>(g, boxes, centres, beta, info, pts, e.perm, e.start,
-                                                out, log_space);
-    } else {
-        size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));
-        cudaFuncSetAttribute(k_eval_bucket_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_eval_bucket_f64<<<g.S, eval_block(), sm, st>>>(g, centres, beta, info, pts, e.perm, e.start, out,
-                                                log_space);
+    {
+        PhaseScope pk(kPhEvalKernel, st);  // the per-owner kernel alone
+        if (precision == PAM_PREC_MIXED) {
+            size_t sm = stage_f32s_smem(g.m_cap);
+            cudaFuncSetAttribute(k_eval_bucket_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            k_eval_bucket_f32<<<g.S, eval_block(), sm, st>>>(g, boxes, centres, beta, info, pts, e.perm, e.start,
+                                                             out, log_space);
+        } else {
+            size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));
+            cudaFuncSetAttribute(k_eval_bucket_f64, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            k_eval_bucket_f64<<<g.S, eval_block(), sm, st>>>(g, centres, beta, info, pts, e.perm, e.start, out,
+                                                             log_space);
+        }
     }
     count_launches(4);
 }

@@ -167,7 +167,7 @@ const pam_tuning &tuning();
 // Kernel families timed by the optional event profiler (pam_timing_*).
 enum Phase {
     kPhPrepare = 0, kPhAssemble, kPhGram, kPhSolve, kPhResidual, kPhMark, kPhEval, kPhErrors,
-    kPhStats, kPhGramTC, kPhRefine, kPhCount
+    kPhStats, kPhGramTC, kPhRefine, kPhEvalKernel, kPhCount
 };
 
 // Counts kernel launches issued by the library (host side).

@@ -77,6 +77,15 @@ def test_roofline_objects_keep_their_contract():
     assert t["stats"]["traffic"] is None
     assert all(v["traffic"] is None for v in bench.attach_traffic({k: dict(v) for k, v in r.items()},
                                                                    "channel2d").values())
+    # with the evaluation kernel timed alone, its roofline uses that time
+    # and keeps the whole phase's fraction beside it
+    assert r["eval"]["timed"] == "the evaluation phase"
+    phases["eval_kernel"] = (1.12, 1)
+    r2 = bench.roofline_entries(phases, work, 8_976_000, True, peaks, "measured")
+    assert r2["eval"]["timed"] == "the kernel alone"
+    assert r2["eval"]["achieved"] == pytest.approx(3.5e12 / 1.12e-3 / 1e12)
+    assert r2["eval"]["phase_frac"] == pytest.approx(3.5e12 / 1.53e-3 / bench.SFU_EX2_PER_S)
+    assert "eval_kernel" not in r2
 
 
 def test_dictionary_agreement_counts_differing_subdomains_and_flags():
