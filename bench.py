@@ -63,8 +63,11 @@ WORKLOADS = {
 }
 
 # slices of the end-to-end evaluation whose device-to-host copies overlap
-# the evaluation of the next slices
-E2E_EVAL_CHUNKS = 4
+# the evaluation of the next slices (--e2e-slices; each slice repeats the
+# owner lookup and the per-owner staging of the dictionaries). Measured on
+# the layered 3-D workload: 1 slice 16.15 ms, 2 slices 15.90, 4 slices 16.14
+# per end-to-end step (the copies run at ~195-210 GB/s each way).
+E2E_EVAL_CHUNKS = 2
 
 # "eval_kernel" (the per-owner evaluation kernel alone) is timed inside "eval"
 PHASES = ["prepare", "assemble", "gram", "solve", "residual", "mark", "eval", "errors", "stats",
@@ -743,7 +746,7 @@ def run_pam(args, rank, ws):
         fit_step(deferred=True)
         cur.wait_event(pts_ready)
         # evaluated in slices, each copied back while the next evaluates
-        fit.eval_to_host(ptsd, out, outh, chunks=E2E_EVAL_CHUNKS, copy_stream=side, join=False)
+        fit.eval_to_host(ptsd, out, outh, chunks=args.e2e_slices, copy_stream=side, join=False)
         fit.errors_device(Kd, errd)
         errh.copy_(errd, non_blocking=True)
         cur.wait_stream(side)
@@ -1051,6 +1054,8 @@ def main():
     ap.add_argument("--cpu-sample", type=int, default=None,
                     help="subdomains in the oracle baseline sample (default: 192, 32 on the triangle mesh)")
     ap.add_argument("--skip-plain", action="store_true")
+    ap.add_argument("--e2e-slices", type=int, default=E2E_EVAL_CHUNKS,
+                    help="evaluation slices of the end-to-end leg, each copied back while the next evaluates")
     ap.add_argument("--skip-cpu", action="store_true")
     ap.add_argument("--no-learned", action="store_true", help="3-D mixed form without the learned warm start")
     ap.add_argument("--lambda-cv", action="store_true",
@@ -1147,7 +1152,7 @@ def main():
         "cpu_baseline": cpu,
         "e2e": {"value": r["n_cells"] * ws / r["e2e_s"], "unit": "cells/s",
                 "h2d_bytes_per_step": r["h2d"], "d2h_bytes_per_step": r["d2h"], "launch": r["e2e_mode"],
-                "eval_slices": E2E_EVAL_CHUNKS},
+                "eval_slices": args.e2e_slices},
         "gpu_launches": r["launches"],
         "clocks": r["clocks"],
         "phase_ms_per_step": {k: round(v[0], 4) for k, v in r["phase_ms"].items()},
