@@ -123,7 +123,7 @@ void launch_gram_tc(const Geo &g, const int32_t *boxes, const double *centres, c
                     const Ws &w, cudaStream_t st, int all, int folds, int fold);
 void launch_solve_mixed(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
                         double *beta, int32_t *info, const Ws &w, const double *lam_tab, int all, double *cv,
-                        int cv_stride, cudaStream_t st, int fallback);
+                        int cv_stride, cudaStream_t st, int fallback, int m_bound = 0);
 void launch_copy_gram_f32(const Geo &g, const int32_t *info, const Ws &w, double *G_out,
                           double *b_out, cudaStream_t st);
 void launch_copy_gram_f64(const Geo &g, const int32_t *info, const Ws &w, double *G_out,

@@ -814,6 +814,11 @@ void launch_copy_gram_f32(const Geo &g, const int32_t *info, const Ws &w, double
 // --------------------------------------------------------------------------
 
 constexpr int kMxThreads = 256;
+// At M <= 64 the solve is a chain of short factorisations and the
+// exact-gradient passes are short: more subdomains in flight pay more than
+// more threads per subdomain.
+constexpr int kSmallSolveM = 64;
+constexpr int kSmallSolveThreads = 64;
 constexpr int kMxFactorBytesDefault = 64 * 1024;
 constexpr int kMxMaxRefine = 12;
 constexpr int kMxMaxPdas = 200;
@@ -913,6 +918,7 @@ struct DFAcc2 {
 // in a fixed order. lam_tab (optional): per-subdomain (lambda1_hat,
 // lambda2_hat) pairs in place of p's; all: solve also the subdomains whose
 // refinement has stopped.
+template <bool SMALL>
 __device__ __forceinline__ void solve_mixed_item(const Geo &g, const Par &p, const int32_t *boxes,
                                                  const double *centres, double *beta, int32_t *info,
                                                  const Ws &w, int kMxFactorBytes, const double *lam_tab,
@@ -921,6 +927,9 @@ __device__ __forceinline__ void solve_mixed_item(const Geo &g, const Par &p, con
     int32_t *inf = info + s * kInfoN;
     if (!all && inf[PAM_INFO_STOPPED]) return;
     const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS], mc = g.m_cap;
+    // per-centre arrays in shared memory: the capacity, or (SMALL) the bound
+    // kSmallSolveM of every dictionary of the launch
+    const int mcs = SMALL ? kSmallSolveM : mc;
     const int folds = cv ? p.cv_folds : 0, fold = p.cv_fold;
     const int n_out = (folds > 0 && N > fold) ? (N - 1 - fold) / folds + 1 : 0;
     const double n_fit = (double)(N - n_out);
@@ -933,17 +942,17 @@ __device__ __forceinline__ void solve_mixed_item(const Geo &g, const Par &p, con
     const int32_t *box = boxes + s * 12;
 
     extern __shared__ __align__(16) uint8_t sm[];
-    float *x = reinterpret_cast<float *>(sm);     // [mc]
-    float *gr = x + mc;                           // [mc] b - G~ x (stage 1), exact c (stage 2)
-    float *bv = gr + mc;                          // [mc]
-    float *rhs = bv + mc;                         // [mc]
-    int *sg = reinterpret_cast<int *>(rhs + mc);  // [mc]
-    int *idx = sg + mc;                           // [mc]
+    float *x = reinterpret_cast<float *>(sm);      // [mcs]
+    float *gr = x + mcs;                           // [mcs] b - G~ x (stage 1), exact c (stage 2)
+    float *bv = gr + mcs;                          // [mcs]
+    float *rhs = bv + mcs;                         // [mcs]
+    int *sg = reinterpret_cast<int *>(rhs + mcs);  // [mcs]
+    int *idx = sg + mcs;                           // [mcs]
     // cells in pairs (2p, 2p + 1) and the support in pairs (2q, 2q + 1), for
     // the packed fp32x2 arithmetic of the exact-gradient passes
-    const int np2 = (g.n_max + 1) >> 1, ns2 = (mc >> 1) + 2;
-    float4 *sc = reinterpret_cast<float4 *>(idx + mc);      // [mc] local centres
-    float4 *cella = sc + mc;                                // [np2] (x, x', y, y')
+    const int np2 = (g.n_max + 1) >> 1, ns2 = (mcs >> 1) + 2;
+    float4 *sc = reinterpret_cast<float4 *>(idx + mcs);     // [mcs] local centres
+    float4 *cella = sc + mcs;                               // [np2] (x, x', y, y')
     float4 *cellb = cella + np2;                            // [np2] (z, z', -rowmax, -rowmax')
     float4 *supa = cellb + np2;                             // [ns2] (-c_x, -c_x', -c_y, -c_y')
     float4 *supb = supa + ns2;                              // [ns2] (-c_z, -c_z', alpha, alpha')
@@ -959,9 +968,9 @@ __device__ __forceinline__ void solve_mixed_item(const Geo &g, const Par &p, con
         const int h = t & 1;
         return make_float4(fa[h], fa[2 + h], fb[h], -fb[2 + h]);
     };
-    float *dinv = ce + 2 * np2;                             // [mc] 1 / diag of the factor
-    float *ub = dinv + mc;                                  // [mc] bounds on |c_j| off the support
-    float *Lt = ub + mc;                                    // [32 x 32] factorisation scratch
+    float *dinv = ce + 2 * np2;                             // [mcs] 1 / diag of the factor
+    float *ub = dinv + mcs;                                 // [mcs] bounds on |c_j| off the support
+    float *Lt = ub + mcs;                                   // [32 x 32] factorisation scratch
     float *Asm = Lt + kCholLtFloats;                        // packed factor
     __shared__ MxShared sh;
 
@@ -985,7 +994,7 @@ __device__ __forceinline__ void solve_mixed_item(const Geo &g, const Par &p, con
     // the dictionary (M x 32 bytes) comes into the factor's space, free until
     // the first factorisation, by one bulk copy, and is converted to local fp32
     stage_local_centres(sc, cg, M, o, Asm, M * 32 <= kMxFactorBytes);
-    for (int j = tid; j < mc; j += blockDim.x) {
+    for (int j = tid; j < mcs; j += blockDim.x) {
         float b0 = j < M ? (float)beta[(size_t)s * mc + j] : 0.f;
         x[j] = b0;
         bv[j] = j < M ? (float)w.b[(size_t)s * mc + j] : 0.f;
@@ -1433,7 +1442,7 @@ __device__ __forceinline__ void solve_mixed_item(const Geo &g, const Par &p, con
         __syncthreads();
         if (tid == 0) {
             double tot = 0.0;
-            for (int q = 0; q < kMxThreads / 32; ++q) tot += hpart[q];
+            for (int q = 0; q < (int)blockDim.x / 32; ++q) tot += hpart[q];
             cv[(size_t)s * cv_stride] += tot;
         }
     } else if (certified) {
@@ -1489,14 +1498,17 @@ __device__ __forceinline__ void solve_mixed_item(const Geo &g, const Par &p, con
 // = 0: one block per subdomain, block b taking the b-th of that order;
 // persistent = 1: one block per resident slot, each taking the next
 // subdomain of the order from the counter w.fb[1] until none is left.
-__global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, const int32_t *boxes,
-                                                            const double *centres, double *beta,
-                                                            int32_t *info, Ws w, int kMxFactorBytes,
-                                                            const double *lam_tab, int all, double *cv,
-                                                            int cv_stride, int fallback, int persistent) {
+// The body of both solve kernels: one subdomain per CTA (w.order[blockIdx.x],
+// longest first), or resident CTAs taking the next subdomain of the same
+// order from a counter (persistent).
+template <bool SMALL>
+__device__ __forceinline__ void solve_mixed_blocks(const Geo &g, const Par &p, const int32_t *boxes,
+                                                   const double *centres, double *beta, int32_t *info,
+                                                   const Ws &w, int kMxFactorBytes, const double *lam_tab, int all,
+                                                   double *cv, int cv_stride, int fallback, int persistent) {
     if (!persistent) {
-        solve_mixed_item(g, p, boxes, centres, beta, info, w, kMxFactorBytes, lam_tab, all, cv, cv_stride,
-                         fallback, w.order[blockIdx.x]);
+        solve_mixed_item<SMALL>(g, p, boxes, centres, beta, info, w, kMxFactorBytes, lam_tab, all, cv, cv_stride,
+                                fallback, w.order[blockIdx.x]);
         return;
     }
     __shared__ int next;
@@ -1506,9 +1518,32 @@ __global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, con
         __syncthreads();
         const int k = next;
         if (k >= g.S) break;
-        solve_mixed_item(g, p, boxes, centres, beta, info, w, kMxFactorBytes, lam_tab, all, cv, cv_stride,
-                         fallback, w.order[k]);
+        solve_mixed_item<SMALL>(g, p, boxes, centres, beta, info, w, kMxFactorBytes, lam_tab, all, cv, cv_stride,
+                                fallback, w.order[k]);
     }
+}
+
+__global__ void __launch_bounds__(kMxThreads, 2) k_solve_mixed(Geo g, Par p, const int32_t *boxes,
+                                                            const double *centres, double *beta,
+                                                            int32_t *info, Ws w, int kMxFactorBytes,
+                                                            const double *lam_tab, int all, double *cv,
+                                                            int cv_stride, int fallback, int persistent) {
+    solve_mixed_blocks<false>(g, p, boxes, centres, beta, info, w, kMxFactorBytes, lam_tab, all, cv, cv_stride,
+                              fallback, persistent);
+}
+
+// Small dictionaries (every M <= kSmallSolveM: the initial lattices): 64
+// threads per subdomain and per-centre arrays of kSmallSolveM entries, so
+// that five CTAs share an SM (k_solve_mixed_small below).
+// (No minimum-blocks bound: with one ptxas keeps the body in 150 registers
+// without spills, while a bound of 4-6 blocks spills; shared memory holds it
+// to five CTAs per SM either way.)
+__global__ void __launch_bounds__(kSmallSolveThreads) k_solve_mixed_small(Geo g, Par p, const int32_t *boxes,
+                                                                          const double *centres, double *beta,
+                                                                          int32_t *info, Ws w, int kMxFactorBytes,
+                                                                          int fallback) {
+    solve_mixed_blocks<true>(g, p, boxes, centres, beta, info, w, kMxFactorBytes, nullptr, 0, nullptr, 0, fallback,
+                             0);
 }
 
 // Block order of the next mixed solve: the subdomains sorted by the cost of
@@ -1549,9 +1584,10 @@ __global__ void __launch_bounds__(1024) k_solve_order(const uint32_t *cost, int 
 }
 
 // Shared memory of the mixed solve besides the packed factor.
-static size_t solve_mixed_smem_rest(const Geo &g) {
-    const size_t np2 = (size_t)(g.n_max + 1) / 2, ns2 = (size_t)g.m_cap / 2 + 2;
-    return (size_t)g.m_cap * (6 * sizeof(float) + 2 * sizeof(int) + sizeof(float4)) +
+static size_t solve_mixed_smem_rest(const Geo &g, int mcs = 0) {
+    if (mcs <= 0) mcs = g.m_cap;
+    const size_t np2 = (size_t)(g.n_max + 1) / 2, ns2 = (size_t)mcs / 2 + 2;
+    return (size_t)mcs * (6 * sizeof(float) + 2 * sizeof(int) + sizeof(float4)) +
            np2 * 2 * (sizeof(float4) + 2 * sizeof(float)) + ns2 * 2 * (sizeof(float4) + sizeof(float2)) +
            kCholLtFloats * sizeof(float) + 64;
 }
@@ -1606,11 +1642,25 @@ bool mixed_solve_fits(const Geo &g) {
 
 void launch_solve_mixed(const Geo &g, const Par &p, const int32_t *boxes, const double *centres,
                         double *beta, int32_t *info, const Ws &w, const double *lam_tab, int all, double *cv,
-                        int cv_stride, cudaStream_t st, int fallback) {
-    size_t sm = solve_mixed_smem(g);
-    cudaFuncSetAttribute(k_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+                        int cv_stride, cudaStream_t st, int fallback, int m_bound) {
     PhaseScope ps(kPhSolve, st);
     const int fb = fallback && !cv && w.fb_slots > 0;
+    if (m_bound > 0 && m_bound <= kSmallSolveM && !cv && !lam_tab && !all && kSmallSolveM <= g.m_cap) {
+        // every dictionary is at most kSmallSolveM centres: the small-CTA form
+        const int fbytes = ((kSmallSolveM + 2) * (kSmallSolveM + 1) / 2 * 4 + 1023) / 1024 * 1024;
+        const size_t sm = solve_mixed_smem_rest(g, kSmallSolveM) + (size_t)fbytes;
+        if (sm <= kSmemLimit) {
+            cudaFuncSetAttribute(k_solve_mixed_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+            k_solve_order<<<1, 1024, 0, st>>>(w.cost, g.S, w.order, w.fb);
+            k_solve_mixed_small<<<g.S, kSmallSolveThreads, sm, st>>>(g, p, boxes, centres, beta, info, w, fbytes,
+                                                                     fb);
+            count_launches(2);
+            if (fb) launch_fallback_f64(g, p, boxes, centres, beta, info, w, lam_tab, st);
+            return;
+        }
+    }
+    size_t sm = solve_mixed_smem(g);
+    cudaFuncSetAttribute(k_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_solve_order<<<1, 1024, 0, st>>>(w.cost, g.S, w.order, w.fb);
     count_launches(1);
     const int persistent = tuning().solve_persistent == 1 && w.fb != nullptr;
@@ -1635,7 +1685,7 @@ void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes,
                               cudaStream_t st, cudaEvent_t before_solve, int m_bound) {
     launch_stats_gram_tc(g, boxes, centres, info, w, st, 0, m_bound);
     if (before_solve) cudaStreamWaitEvent(st, before_solve, 0);  // an error surfaces in cudaGetLastError
-    launch_solve_mixed(g, p, boxes, centres, beta, info, w, nullptr, 0, nullptr, 0, st, 1);
+    launch_solve_mixed(g, p, boxes, centres, beta, info, w, nullptr, 0, nullptr, 0, st, 1, m_bound);
 }
 
 // The mixed solve already wrote the indicators of its final coefficients.
