@@ -301,7 +301,7 @@ FP32_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12
 # profiles/gram_tc_layered3d_quarter_mixed.md for the tensor-core Gram and the
 # evaluation). Only valid for that workload and for the kernels as captured
 # (the statistics changed after their last capture: none recorded).
-TRAFFIC_LAYERED3D = {"k_solve_mixed": 1.406e9, "k_gram_tc": 1.224e9, "k_eval_bucket_f32": 2.94e8}
+TRAFFIC_LAYERED3D = {"k_solve_mixed": 1.378e9, "k_gram_tc": 1.224e9, "k_eval_bucket_f32": 2.94e8}
 TRAFFIC_NOTE = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the level-3 launch (eval: its one launch), "
                 "captured on layered3d_quarter and scaled x4 by subdomains")
 
