@@ -812,15 +812,32 @@ __global__ void __launch_bounds__(kMarkThreads, 6) k_mark_enrich(Geo g, Par p, c
         if (tid == 0) inf[PAM_INFO_STOPPED] = 1;
         return;
     }
-    double kmax = __longlong_as_double((long long)w.kmax_bits[s]);
-    double eps;
-    const double a_tol = p.eps_tol_rel * kmax;
-    if (p.eps_tol_rel < 0.0) {
-        eps = -INFINITY;
-    } else {
-        eps = g.vol * (a_tol * a_tol);
+    // the block's binary64 scalars once, by thread 0 (the binary64 pipe is
+    // narrow on this part: per-thread copies of these showed as half of its
+    // time in the kernel)
+    __shared__ double s_atol, s_lo[3], s_hi[3];
+    __shared__ float s_ek, s_eloc;
+    if (tid == 0) {
+        const double kmax = __longlong_as_double((long long)w.kmax_bits[s]);
+        const double a_tol0 = p.eps_tol_rel * kmax;
+        s_atol = a_tol0;
+        s_ek = p.eps_tol_rel < 0.0 ? -INFINITY : (float)(g.vol * (a_tol0 * a_tol0));
+        const int32_t *bx = boxes + s * 12;
+        float ext0 = 0.f;
+        for (int a = 0; a < 3; ++a) {
+            s_lo[a] = 0.0;
+            s_hi[a] = 0.0;
+            if (a < g.dim) {
+                s_lo[a] = __dmul_rn((double)bx[6 + a], g.h);
+                s_hi[a] = __dmul_rn((double)bx[9 + a], g.h);
+                ext0 = fmaxf(ext0, (float)(s_hi[a] - s_lo[a]));
+            }
+        }
+        s_eloc = 2e-7f * ext0;
     }
-    const float ek = (float)eps;
+    __syncthreads();
+    const double a_tol = s_atol;
+    const float ek = s_ek;
     const double *R = w.R + (size_t)s * g.n_max;
     MK_T(mk0);
     // key = (fp32 R_T + 1 ulp step, ~index): strictly ordered, ties to the
@@ -879,18 +896,13 @@ __global__ void __launch_bounds__(kMarkThreads, 6) k_mark_enrich(Geo g, Par p, c
     const int nmu = (add + per - 1) / per;  // marked cells that receive centres
     double *cs = centres + (size_t)s * g.m_cap * 4;
     const int32_t *box = boxes + s * 12;
-    double lo[3] = {0, 0, 0}, hi[3] = {0, 0, 0};
-    for (int a = 0; a < g.dim; ++a) {
-        lo[a] = __dmul_rn((double)box[6 + a], g.h);
-        hi[a] = __dmul_rn((double)box[9 + a], g.h);
-    }
-    float ext = 0.f;
-    for (int a = 0; a < g.dim; ++a) ext = fmaxf(ext, (float)(hi[a] - lo[a]));
-    const float e_loc = 2e-7f * ext;
+    const double lo[3] = {s_lo[0], s_lo[1], s_lo[2]}, hi[3] = {s_hi[0], s_hi[1], s_hi[2]};
+    const float e_loc = s_eloc;
     // tables in the (now free) key space: local fp32 centres, marked-cell
-    // centroids (binary64), chosen parents
+    // centroids (binary64) and their local fp32 coordinates, chosen parents
     float4 *scl = reinterpret_cast<float4 *>(keys);          // [M]
-    double *cxt = reinterpret_cast<double *>(scl + M);        // [nmu][4]
+    float4 *cxl = scl + M;                                    // [nmu]
+    double *cxt = reinterpret_cast<double *>(cxl + nmu);      // [nmu][4]
     int *cbest = reinterpret_cast<int *>(cxt + 4 * nmu);      // [nmu]
     __syncthreads();  // every thread has read its keys
     for (int m = tid; m < M; m += blockDim.x)
@@ -900,6 +912,7 @@ __global__ void __launch_bounds__(kMarkThreads, 6) k_mark_enrich(Geo g, Par p, c
         double xt[3];
         cell_point(g, s, box, marked[r], xt);
         for (int a = 0; a < 3; ++a) cxt[4 * r + a] = xt[a];
+        cxl[r] = make_float4((float)(xt[0] - lo[0]), (float)(xt[1] - lo[1]), (float)(xt[2] - lo[2]), 0.f);
     }
     __syncthreads();
     MK_T(mk3);
@@ -914,8 +927,8 @@ __global__ void __launch_bounds__(kMarkThreads, 6) k_mark_enrich(Geo g, Par p, c
     // to the lower index.
     for (int r = warp; r < nmu; r += nwarp) {
         const double xt[3] = {cxt[4 * r], cxt[4 * r + 1], cxt[4 * r + 2]};
-        float xl[3];
-        for (int a = 0; a < 3; ++a) xl[a] = (float)(xt[a] - lo[a]);
+        const float4 xl4 = cxl[r];
+        const float xl[3] = {xl4.x, xl4.y, xl4.z};
         float bf = INFINITY;
         for (int m = lane; m < M; m += 32) {
             const float4 c = scl[m];
@@ -997,7 +1010,8 @@ void launch_mark_enrich(const Geo &g, const Par &p, const int32_t *boxes, double
     // the sort's keys, later the centre table, marked centroids and parents
     size_t sm = (size_t)mark_sort_len(g.n_max) * sizeof(unsigned long long);
     const int kt = p.k_top < kMaxKTop ? p.k_top : kMaxKTop;
-    const size_t tables = (size_t)g.m_cap * sizeof(float4) + (size_t)kt * (4 * sizeof(double) + sizeof(int));
+    const size_t tables = (size_t)g.m_cap * sizeof(float4) +
+                          (size_t)kt * (sizeof(float4) + 4 * sizeof(double) + sizeof(int));
     if (sm < tables) sm = tables;
     cudaFuncSetAttribute(k_mark_enrich, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     PhaseScope ps(kPhMark, st);
