@@ -62,6 +62,17 @@ __device__ __forceinline__ void patch_origin(const Geo &g, const int32_t *box, d
     for (int a = 0; a < 3; ++a) o[a] = a < g.dim ? (double)box[6 + a] * g.h : 0.0;
 }
 
+// The same, computed once per block and read from shared memory (the
+// binary64 pipe is narrow on this part; a block of 1024 threads would
+// otherwise repeat the products 1024 times). Called by the whole block.
+__device__ __forceinline__ void patch_origin_block(const Geo &g, const int32_t *box, double o[3]) {
+    __shared__ double so[3];
+    __syncthreads();  // a previous call's readers are done
+    if (threadIdx.x == 0) patch_origin(g, box, so);
+    __syncthreads();
+    for (int a = 0; a < 3; ++a) o[a] = so[a];
+}
+
 // Local coordinates of patch cell t: ((i - patch_lo) + 1/2) h, exact in fp32
 // up to one rounding; for a mesh given as cells, the gathered sampling point
 // minus the patch origin, rounded once to fp32.
@@ -135,7 +146,7 @@ __global__ void __launch_bounds__(256) k_stats_f32(Geo g, const int32_t *boxes,
     const int32_t *box = boxes + s * 12;
     extern __shared__ float4 scp[];  // [2 * m_cap]
     double o[3];
-    patch_origin(g, box, o);
+    patch_origin_block(g, box, o);
     const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
     for (int m = threadIdx.x; m < M; m += blockDim.x) {
         const float4 c = local_centre(cg[m], o);
@@ -350,7 +361,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
     __shared__ int timed_out;
 
     double o[3];
-    patch_origin(g, box, o);
+    patch_origin_block(g, box, o);
     const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
     // plain loads: a bulk copy of the centres into the (still free) tile
     // buffers measured 1 % slower over the step (2.110 -> 2.133 ms at the
@@ -630,7 +641,7 @@ __global__ void __launch_bounds__(kSgThreads) k_gram_small(Geo g, const int32_t 
     const int nch = (N + kTcKC - 1) / kTcKC;
     float *cya = reinterpret_cast<float *>(cxa + (size_t)nch * kTcKC);
     double o[3];
-    patch_origin(g, box, o);
+    patch_origin_block(g, box, o);
     const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * g.m_cap;
     for (int m = tid; m < M; m += blockDim.x) sc[m] = local_centre(cg[m], o);
     // padding columns of W (M up to the next multiple of 4) stay zero
@@ -989,7 +1000,7 @@ __device__ __forceinline__ void solve_mixed_item(const Geo &g, const Par &p, con
     const float *rowmax = w.rowmax + (size_t)s * g.n_max;
     const float *rowinv = w.rowinv + (size_t)s * g.n_max;
     double o[3];
-    patch_origin(g, box, o);
+    patch_origin_block(g, box, o);
     const dvec4 *cg = reinterpret_cast<const dvec4 *>(centres) + (size_t)s * mc;
     // the dictionary (M x 32 bytes) comes into the factor's space, free until
     // the first factorisation, by one bulk copy, and is converted to local fp32
