@@ -631,22 +631,25 @@ def run_pam(args, rank, ws):
                 got[name] = (tot.value, cnt.value)
         return got
 
-    # the timed step is a CUDA graph of the whole step (captured once, with
-    # the phase event pairs as graph nodes), else eager launches
-    graph, mode = None, "eager"
+    # the timed step is a CUDA graph of the whole step (captured once), else
+    # eager launches; the per-family phase times come from replays of a
+    # second capture of the same step with the phase event pairs as graph
+    # nodes, so that the timed replays carry no profiler nodes
+    graph, graph_ph, mode = None, None, "eager"
     L.pam_timing_reset()
     if not args.no_graph:
         try:
             l0 = L.pam_kernel_launches()
-            graph = capture(step_body, timed=True)
+            graph = capture(step_body, timed=False)
             launches_per_step = (L.pam_kernel_launches() - l0) // 2  # the eager pre-pass + the capture
+            graph_ph = capture(step_body, timed=True)
             for _ in range(args.warmup):
                 graph.replay()
             torch.cuda.synchronize()
             check_status()
             mode = "graph"
         except Exception as e:  # reported in the JSON line; the eager step is timed instead
-            graph = None
+            graph, graph_ph = None, None
             torch.cuda.synchronize()
             L.pam_timing_reset()
             mode = f"eager (graph capture failed: {type(e).__name__}: {str(e)[:160]})"
@@ -672,10 +675,16 @@ def run_pam(args, rank, ws):
             e1.record(stream)
             torch.cuda.synchronize()
             times.append(e0.elapsed_time(e1))
-            if graph is not None:  # this replay's phase times (host work between timed steps)
-                for k, (t, c) in read_phases().items():
-                    a = phase_tot.setdefault(k, [0.0, c])
-                    a[0] += t
+    if graph_ph is not None:
+        # the phase times: as many replays of the profiled capture, each
+        # after the same L2 flush, read one by one
+        for _ in range(args.steps):
+            flush.fill_(1)
+            graph_ph.replay()
+            torch.cuda.synchronize()
+            for k, (t, c) in read_phases().items():
+                a = phase_tot.setdefault(k, [0.0, c])
+                a[0] += t
     barrier(ws)
     phase_ms = {}
     if graph is not None:
@@ -688,7 +697,7 @@ def run_pam(args, rank, ws):
         L.pam_timing_enable(0)
         for k, (t, c) in read_phases().items():
             phase_ms[k] = (t / args.steps, c // args.steps)
-    del graph
+    del graph, graph_ph
     torch.cuda.synchronize()
     L.pam_timing_reset()
 
@@ -735,14 +744,20 @@ def run_pam(args, rank, ws):
     errh = torch.empty(4, dtype=torch.float64).pin_memory()
     side = torch.cuda.Stream(device=dev)  # the evaluation points and the result travel beside the fit
     pts_ready = torch.cuda.Event()
+    k_ready = torch.cuda.Event()
 
     def e2e_body():
         cur = torch.cuda.current_stream()
-        side.wait_stream(cur)
+        # the field first: the fit waits for it, and a points copy enqueued
+        # ahead of it on the same copy engine delayed it by the whole 215 MB
+        # (measured: 15.50 ms per end-to-end step that way, 14.47 with the
+        # field's copy alone on the path)
+        Kd.copy_(Kh, non_blocking=True)
+        k_ready.record(cur)
+        side.wait_event(k_ready)
         with torch.cuda.stream(side):
             ptsd.copy_(ptsh, non_blocking=True)
             pts_ready.record(side)
-        Kd.copy_(Kh, non_blocking=True)
         fit_step(deferred=True)
         cur.wait_event(pts_ready)
         # evaluated in slices, each copied back while the next evaluates
