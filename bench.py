@@ -704,11 +704,11 @@ def run_pam(args, rank, ws):
     step_ms = max_over_ranks(sum(times) / len(times), ws, dev)
     value = n_cells * ws / (step_ms / 1e3)
     info = fit.model.info.cpu().numpy()
-    if lw is not None:
-        # the same step without the learned seed (level 0 from beta = 0), for
-        # comparison, in the same launch mode
-        g2 = capture(lambda: step_body(seeded=False)) if mode == "graph" else None
-        plain_times = []
+    def time_variant(body):
+        # mean step time of `body` in the same launch mode and with the same
+        # L2 flush as the timed steps (a graph of its own, when graphs are used)
+        g2 = capture(body) if mode == "graph" else None
+        ts = []
         for i in range(args.warmup + args.steps):
             flush.fill_(1)
             e0 = torch.cuda.Event(enable_timing=True)
@@ -717,16 +717,35 @@ def run_pam(args, rank, ws):
             if g2 is not None:
                 g2.replay()
             else:
-                fit.fit(Kd)
-                fit.eval(ptsd, out=out)
-                fit.errors(Kd)
+                body()
             e1.record(stream)
             torch.cuda.synchronize()
             if i >= args.warmup:
-                plain_times.append(e0.elapsed_time(e1))
-        if g2 is not None:
-            check_status()
-            del g2
+                ts.append(e0.elapsed_time(e1))
+        check_status()
+        del g2
+        return sum(ts) / len(ts)
+
+    groups = None
+    if prec == pam.PAM_PREC_MIXED:
+        # the refinement levels as one pipeline of launches over every
+        # subdomain, against the two subdomain groups on two streams
+        tsave = pam.pam_tuning_get()
+        n_groups = 2 if tsave["level_groups"] == 2 or (
+            tsave["level_groups"] == 0 and fit.plan.n_subdomains >= 1024 and args.quad == 0) else 1
+        pam.pam_tuning_set(**dict(tsave, level_groups=1))
+        try:
+            one_ms = time_variant(step_body)
+        finally:
+            pam.pam_tuning_set(**tsave)
+        groups = {"groups": n_groups, "step_ms": round(step_ms, 3), "step_ms_one_pipeline": round(one_ms, 3),
+                  "note": "two groups (even and odd subdomains) run their refinement levels on two streams, "
+                          "so that one group's solve tail overlaps the other's work; the phase times come "
+                          "from one pipeline"}
+    if lw is not None:
+        # the same step without the learned seed (level 0 from beta = 0), for
+        # comparison, in the same launch mode
+        plain_ms = time_variant(lambda: step_body(seeded=False))
         t0 = torch.cuda.Event(enable_timing=True)
         t1 = torch.cuda.Event(enable_timing=True)
         t0.record(stream)
@@ -734,7 +753,7 @@ def run_pam(args, rank, ws):
         t1.record(stream)
         torch.cuda.synchronize()
         learned["step_ms_learned"] = round(step_ms, 3)
-        learned["step_ms_without_learned"] = round(sum(plain_times) / len(plain_times), 3)
+        learned["step_ms_without_learned"] = round(plain_ms, 3)
         learned["inference_ms"] = round(t0.elapsed_time(t1), 3)
 
     # --- end to end through the C ABI from pinned host buffers -------------
@@ -916,7 +935,7 @@ def run_pam(args, rank, ws):
     return dict(value=value, step_ms=step_ms, times=times, err=err, phase_ms=phase_ms, launches=launches,
                 clocks=clk.summary(), e2e_s=e2e_s, h2d=h2d, d2h=d2h, plain=plain, roof=roof, roofs=roofs,
                 prec_name=prec_name, n_cells=n_cells, n_pts=n_pts, info=info, learned=learned, mode=mode,
-                e2e_mode=e2e_mode, lambda_cv=lcv, glue=glue, tune=tune,
+                e2e_mode=e2e_mode, lambda_cv=lcv, glue=glue, tune=tune, groups=groups,
                 solve_dist=solve_distribution(work["records"]))
 
 
@@ -1174,6 +1193,7 @@ def main():
         "roofline_all": r["roofs"],
         "plain_fp64": r["plain"],
         "learned_warm_start": r["learned"],
+        "level_groups": r["groups"],
     }
     if r["lambda_cv"] is not None:
         line["lambda_cv"] = r["lambda_cv"]

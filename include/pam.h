@@ -588,7 +588,7 @@ pam_status pam_nn_adamw(float *d_params, const float *d_grads, float *d_m, float
 
 /*
  * Launch tuning and the autotuner (tile and launch shapes; no counterpart in
- * the paper). Four process-wide choices change the speed of the kernels
+ * the paper). Five process-wide choices change the speed of the kernels
  * but not their results:
  *   factor_kb    shared-memory budget (KiB) of the mixed solve's packed
  *                support factor; larger supports keep their factor in global
@@ -602,6 +602,20 @@ pam_status pam_nn_adamw(float *d_params, const float *d_grads, float *d_m, float
  *                longest-first order (the built-in), 1 one CTA per resident
  *                slot (two per SM), each taking the next subdomain of the
  *                same order from a device counter until none is left
+ *   level_groups the mixed form's refinement levels (pam_refine,
+ *                pam_refine_cells): 1 one pipeline of launches over every
+ *                subdomain, 2 the subdomains in two groups (even and odd
+ *                index), each running its levels on its own stream (the
+ *                caller's and one the library creates per host thread and
+ *                device, joined to the caller's stream before the call
+ *                returns), so that one group's solve tail overlaps the other
+ *                group's work; each group then has its share of the
+ *                binary64 fallback's slots (the even group the larger half),
+ *                and the results are the same bits as one pipeline's unless
+ *                a group runs out of slots where the one list would not.
+ *                0: two groups from 1,024 subdomains up
+ *                (midpoint indicators; one pipeline while the phase
+ *                profiler is on). The autotuner does not choose it.
  * pam_tuning_set (NULL: all built-in) applies to every later launch of the
  * process; it is not synchronised with launches in flight on other threads.
  * pam_autotune measures, on a fitted model (after pam_fit_subdomains /
@@ -627,7 +641,8 @@ typedef struct {
     int gram_stages;
     int eval_block;
     int solve_persistent;
-    int reserved[4];
+    int level_groups;
+    int reserved[3];
 } pam_tuning;
 pam_status pam_tuning_set(const pam_tuning *t);
 pam_status pam_tuning_get(pam_tuning *t);

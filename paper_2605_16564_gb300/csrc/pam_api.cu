@@ -21,7 +21,7 @@ static int64_t prod3(const int v[3]) { return (int64_t)v[0] * v[1] * v[2]; }
 bool make_geo(const pam_problem *prob, const pam_params *par, Geo *g, Par *p, pam_status *st) {
     *st = PAM_ERR_INVALID_ARG;
     if (!prob) return false;
-    memset(g, 0, sizeof(*g));
+    *g = Geo{};  // zeros, and every subdomain in one group (stride 1)
     if (prob->dim < 1 || prob->dim > 3) return false;
     g->dim = prob->dim;
     int64_t S = 1, nmax = 1;
@@ -149,7 +149,8 @@ static size_t carve(const Geo &g, char *base, Ws *w) {
     w->bytes_no_fb = off;
     const size_t F = f64 ? 0 : (S < (size_t)kFbSlots ? S : (size_t)kFbSlots);
     w->fb_slots = (int)F;
-    w->fb = F ? (int32_t *)take((2 + F) * sizeof(int32_t)) : nullptr;
+    // (4 + F: room for two lists when the subdomains run in two groups)
+    w->fb = F ? (int32_t *)take((4 + F) * sizeof(int32_t)) : nullptr;
     w->fbE = F ? (double *)take(F * mc * nm * sizeof(double)) : nullptr;
     w->fbG = F ? (double *)take(F * mc * mc * sizeof(double)) : nullptr;
     w->fbL = F ? (double *)take(F * (mc * (mc + 1) / 2) * sizeof(double)) : nullptr;
@@ -206,7 +207,7 @@ Ws carve_workspace(const Geo &g, void *base) {
 }  // namespace pam
 
 namespace pam {
-static pam_tuning g_tuning = {0, 0, 0, 0, {0, 0, 0, 0}};  // factor_kb, gram_stages, eval_block, persistent
+static pam_tuning g_tuning = {0, 0, 0, 0, 0, {0, 0, 0}};  // factor_kb, gram_stages, eval_block, persistent, groups
 const pam_tuning &tuning() { return g_tuning; }
 
 // Median of three timed runs of `body` (after one untimed run) on `st`, ms.
@@ -465,6 +466,72 @@ pam_status pam_status_read(const pam_plan *plan, void *d_workspace, size_t works
     return hs[kStUncertified] ? PAM_ERR_NOT_CONVERGED : PAM_OK;
 }
 
+// Subdomain groups of the refinement levels. Each level is marking ->
+// statistics -> Gram -> solve over every subdomain, and the solve's last
+// subdomains leave most of the SMs idle while they finish (its costs vary
+// severalfold from subdomain to subdomain and are not known before it runs).
+// Split into two groups (even and odd subdomain indices, so that both hold
+// the same mix of the field), each group runs its levels in order on its own
+// stream: one group's solve tail overlaps the other group's marking, Gram
+// and solve. The subdomains are independent (section 2), so the results are
+// the same bits as one pipeline's. Each group has its own part of the solve
+// order and its own half of the binary64 fallback's slots.
+constexpr int kGroupMinS = 1024;  // below this the solve has few waves to balance
+
+static int level_groups(const Geo &g, const Par &p, const pam_params *par, const Ws &w) {
+    if (par->precision != PAM_PREC_MIXED || p.quad || w.fb_slots < 2) return 1;
+    if (g_timing) return 1;  // the phase profiler times one pipeline, phase by phase
+    if (g_tuning.level_groups == 1 || g_tuning.level_groups == 2) return g_tuning.level_groups;
+    return g.S >= kGroupMinS ? 2 : 1;
+}
+
+static Geo group_geo(const Geo &g, int q) {
+    Geo v = g;
+    v.gb = q;
+    v.gs = 2;
+    v.gn = (g.S - q + 1) / 2;
+    return v;
+}
+
+static Ws group_ws(const Geo &g, const Ws &w, int q) {
+    Ws v = w;
+    const int f0 = (w.fb_slots + 1) / 2;  // the even group is the larger one when S is odd
+    if (q == 0) {
+        v.fb_slots = f0;
+        return v;
+    }
+    const size_t mc = (size_t)g.m_cap, nm = (size_t)g.n_max;
+    v.order = w.order + (g.S + 1) / 2;
+    v.fb_slots = w.fb_slots - f0;
+    v.fb = w.fb + 2 + f0;
+    v.fbE = w.fbE + (size_t)f0 * mc * nm;
+    v.fbG = w.fbG + (size_t)f0 * mc * mc;
+    v.fbL = w.fbL + (size_t)f0 * (mc * (mc + 1) / 2);
+    return v;
+}
+
+// The second group's stream and the fork / join events, one set per host
+// thread and device (created on first use, kept for the process).
+struct GroupStreams {
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+static pam_status group_streams(GroupStreams **out) {
+    thread_local std::vector<GroupStreams> per_dev;
+    int dev = 0;
+    PAM_CUDA_TRY(cudaGetDevice(&dev));
+    if ((int)per_dev.size() <= dev) per_dev.resize(dev + 1);
+    GroupStreams &gs = per_dev[dev];
+    if (!gs.st) {
+        PAM_CUDA_TRY(cudaStreamCreateWithFlags(&gs.st, cudaStreamNonBlocking));
+        PAM_CUDA_TRY(cudaEventCreateWithFlags(&gs.fork, cudaEventDisableTiming));
+        PAM_CUDA_TRY(cudaEventCreateWithFlags(&gs.join, cudaEventDisableTiming));
+    }
+    *out = &gs;
+    return PAM_OK;
+}
+
 // Step 3 launches shared by the grid and the element-list entry points.
 static pam_status refine_launches(const Geo &g, const Par &p, const pam_params *par, pam_model *model,
                                   int n_levels, const Ws &w, cudaStream_t s) {
@@ -472,13 +539,33 @@ static pam_status refine_launches(const Geo &g, const Par &p, const pam_params *
     const bool deferred = par->deferred_status != 0;
     // deferred: the status keeps accumulating from pam_fit_subdomains
     if (!deferred) PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 8 * sizeof(int32_t), s));
-    for (int lv = 0; lv < n_levels; ++lv) {
-        launch_refine_round(g, p, par->precision, model->boxes, model->centres, model->beta,
-                            model->info, w, s);
-        if (par->precision == PAM_PREC_MIXED)
-            launch_solve_level_mixed(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
-        else
-            launch_solve_level_f64(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
+    const int ng = n_levels > 0 ? level_groups(g, p, par, w) : 1;
+    if (ng == 2) {
+        GroupStreams *gs = nullptr;
+        if ((st = group_streams(&gs)) != PAM_OK) return st;
+        PAM_CUDA_TRY(cudaEventRecord(gs->fork, s));
+        PAM_CUDA_TRY(cudaStreamWaitEvent(gs->st, gs->fork, 0));
+        const Geo gq[2] = {group_geo(g, 0), group_geo(g, 1)};
+        const Ws wq[2] = {group_ws(g, w, 0), group_ws(g, w, 1)};
+        const cudaStream_t sq[2] = {s, gs->st};
+        for (int lv = 0; lv < n_levels; ++lv)
+            for (int q = 0; q < 2; ++q) {
+                launch_refine_round(gq[q], p, par->precision, model->boxes, model->centres, model->beta,
+                                    model->info, wq[q], sq[q]);
+                launch_solve_level_mixed(gq[q], p, model->boxes, model->centres, model->beta, model->info,
+                                         wq[q], sq[q]);
+            }
+        PAM_CUDA_TRY(cudaEventRecord(gs->join, gs->st));
+        PAM_CUDA_TRY(cudaStreamWaitEvent(s, gs->join, 0));
+    } else {
+        for (int lv = 0; lv < n_levels; ++lv) {
+            launch_refine_round(g, p, par->precision, model->boxes, model->centres, model->beta,
+                                model->info, w, s);
+            if (par->precision == PAM_PREC_MIXED)
+                launch_solve_level_mixed(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
+            else
+                launch_solve_level_f64(g, p, model->boxes, model->centres, model->beta, model->info, w, s);
+        }
     }
     PAM_CUDA_TRY(cudaGetLastError());
     if (deferred) return PAM_OK;
@@ -1029,6 +1116,7 @@ pam_status pam_tuning_set(const pam_tuning *t) {
         return PAM_ERR_INVALID_ARG;
     if (t->gram_stages != 0 && t->gram_stages != 2 && t->gram_stages != 3) return PAM_ERR_INVALID_ARG;
     if (t->solve_persistent != 0 && t->solve_persistent != 1) return PAM_ERR_INVALID_ARG;
+    if (t->level_groups < 0 || t->level_groups > 2) return PAM_ERR_INVALID_ARG;
     g_tuning = *t;
     return PAM_OK;
 }

@@ -798,7 +798,7 @@ __host__ __device__ __forceinline__ int mark_sort_len(int n) {
 __global__ void __launch_bounds__(kMarkThreads, 6) k_mark_enrich(Geo g, Par p, const int32_t *boxes,
                                                               double *centres, double *beta,
                                                               int32_t *info, Ws w) {
-    const int s = blockIdx.x;
+    const int s = group_sub(g, blockIdx.x);
     int32_t *inf = info + s * kInfoN;
     if (inf[PAM_INFO_STOPPED]) return;
     const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS], L = inf[PAM_INFO_LEVELS];
@@ -1015,7 +1015,7 @@ void launch_mark_enrich(const Geo &g, const Par &p, const int32_t *boxes, double
     if (sm < tables) sm = tables;
     cudaFuncSetAttribute(k_mark_enrich, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     PhaseScope ps(kPhMark, st);
-    k_mark_enrich<<<g.S, kMarkThreads, sm, st>>>(g, p, boxes, centres, beta, info, w);
+    k_mark_enrich<<<group_count(g), kMarkThreads, sm, st>>>(g, p, boxes, centres, beta, info, w);
     count_launches(1);
 }
 

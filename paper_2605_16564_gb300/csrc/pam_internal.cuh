@@ -30,6 +30,10 @@ struct Geo {
     int m0, m_cap;
     int prec;       // pam_precision of the fit calls (sizes the workspace)
     int sub_lo, sub_hi;  // the subdomains a fit solves (the others start stopped)
+    // the subdomains a launch of the refinement levels covers: gb + i gs for
+    // 0 <= i < gn (gn 0: all S); a group of them runs its levels on its own
+    // stream, beside the other groups
+    int gb = 0, gs = 1, gn = 0;
     // a general mesh given as cells (section 2: elements with a sampling
     // point, a value and a measure); all NULL / 0 for a structured grid
     int cells;               // 1: the patches are element lists
@@ -39,6 +43,9 @@ struct Geo {
     const int32_t *pcells;   // element indices, ascending within a patch
     const double4_32a *cxv;  // workspace [S][n_max]: (x, y, z, |T|) of each patch cell
 };
+
+__host__ __device__ __forceinline__ int group_count(const Geo &g) { return g.gn > 0 ? g.gn : g.S; }
+__host__ __device__ __forceinline__ int group_sub(const Geo &g, int i) { return g.gb + i * g.gs; }
 
 struct Par {
     double lam1_hat, lam2_hat, eps_tol_rel, eta;
@@ -70,7 +77,9 @@ struct Ws {
     double4_32a *cxv; // [S][n_max] gathered (x, y, z, |T|) of patch cells (element-list meshes only)
     // binary64 fallback of the mixed form: the subdomains whose fp32 solve
     // did not certify are solved again in binary64 on fb_slots slots
-    int32_t *fb;      // [2 + fb_slots]: fb[0] = subdomains listed, fb[2 + i] = the i-th
+    int32_t *fb;      // [2 + fb_slots]: fb[0] = subdomains listed, fb[1] = the persistent
+                      // solve's counter, fb[2 + i] = the i-th (two more words are carved:
+                      // a group's view starts its own list after the first group's slots)
     double *fbE;      // [fb_slots][m_cap][n_max] exp(l - l*) of the listed subdomains
     double *fbG;      // [fb_slots][m_cap][m_cap] their binary64 Gram
     double *fbL;      // [fb_slots][m_cap (m_cap+1)/2] their binary64 factors beyond shared memory

@@ -139,7 +139,7 @@ __device__ __forceinline__ void stats_store(const Ws &w, size_t o, const float4 
 __global__ void __launch_bounds__(256) k_stats_f32(Geo g, const int32_t *boxes,
                                                    const double *centres, const int32_t *info,
                                                    Ws w, int all) {
-    const int s = blockIdx.y;
+    const int s = group_sub(g, blockIdx.y);
     const int32_t *inf = info + s * kInfoN;
     if (!all && inf[PAM_INFO_STOPPED]) return;
     const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) k_gram_tc(Geo g, const int32_t 
                                                            const double *centres,
                                                            const int32_t *info, Ws w, int all,
                                                            int nst, int Rcap, int folds, int fold) {
-    const int s = blockIdx.y;
+    const int s = group_sub(g, blockIdx.y);
     const int32_t *inf = info + s * kInfoN;
     if (!all && inf[PAM_INFO_STOPPED]) return;
     const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
@@ -627,7 +627,7 @@ constexpr int kSgThreads = 256;
 
 __global__ void __launch_bounds__(kSgThreads) k_gram_small(Geo g, const int32_t *boxes, const double *centres,
                                                           const int32_t *info, Ws w, int all) {
-    const int s = blockIdx.x;
+    const int s = group_sub(g, blockIdx.x);
     const int32_t *inf = info + s * kInfoN;
     if (!all && inf[PAM_INFO_STOPPED]) return;
     const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
@@ -748,7 +748,7 @@ void launch_gram_tc(const Geo &g, const int32_t *boxes, const double *centres, c
     if (tuning().gram_stages == 2) stages = 2;  // a tuned shallower pipeline (3 only where it fits)
     size_t sm = gram_tc_smem(g, stages);
     cudaFuncSetAttribute(k_gram_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    dim3 grid((g.m_cap + 127) / 128, g.S);
+    dim3 grid((g.m_cap + 127) / 128, group_count(g));
     k_gram_tc<<<grid, kTcThreads, sm, st>>>(g, boxes, centres, info, w, all, stages, tc_rows_cap(g.m_cap),
                                             folds, fold);
     count_launches(1);
@@ -762,7 +762,7 @@ void launch_stats_f32(const Geo &g, const int32_t *boxes, const double *centres,
     // two cells per thread, 512 per block: every block converts the M
     // centres once (binary64 offsets on the narrow fp64 pipe), so fewer,
     // larger blocks per subdomain spend less of their time on it
-    dim3 grid((g.n_max + 511) / 512, g.S);
+    dim3 grid((g.n_max + 511) / 512, group_count(g));
     k_stats_f32<<<grid, 256, sm, st>>>(g, boxes, centres, info, w, all);
     count_launches(1);
 }
@@ -775,7 +775,7 @@ void launch_stats_gram_tc(const Geo &g, const int32_t *boxes, const double *cent
         // every dictionary is at most m_bound centres (the initial lattices)
         PhaseScope ps(kPhGramTC, st);
         cudaFuncSetAttribute(k_gram_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_gram_small<<<g.S, kSgThreads, sm, st>>>(g, boxes, centres, info, w, all);
+        k_gram_small<<<group_count(g), kSgThreads, sm, st>>>(g, boxes, centres, info, w, all);
         count_launches(1);
         return;
     }
@@ -1528,7 +1528,7 @@ __device__ __forceinline__ void solve_mixed_blocks(const Geo &g, const Par &p, c
         if (threadIdx.x == 0) next = atomicAdd(&w.fb[1], 1);
         __syncthreads();
         const int k = next;
-        if (k >= g.S) break;
+        if (k >= group_count(g)) break;
         solve_mixed_item<SMALL>(g, p, boxes, centres, beta, info, w, kMxFactorBytes, lam_tab, all, cv, cv_stride,
                                 fallback, w.order[k]);
     }
@@ -1572,7 +1572,8 @@ __device__ __forceinline__ int cost_bucket(uint32_t c) {
     return 8 * e + (int)((c >> (e - 3)) & 7u) - 16;  // 16..239, increasing with c
 }
 
-__global__ void __launch_bounds__(1024) k_solve_order(const uint32_t *cost, int S, int32_t *order,
+// The subdomains ordered are gb + i gs for 0 <= i < n (a launch's group).
+__global__ void __launch_bounds__(1024) k_solve_order(const uint32_t *cost, int n, int gb, int gs, int32_t *order,
                                                      int32_t *fb) {
     // the solve that follows fills the fallback list afresh and (persistent
     // launch) counts its subdomains from zero
@@ -1581,7 +1582,7 @@ __global__ void __launch_bounds__(1024) k_solve_order(const uint32_t *cost, int 
     __shared__ int cnt[kB], base[kB];
     for (int i = threadIdx.x; i < kB; i += blockDim.x) cnt[i] = 0;
     __syncthreads();
-    for (int i = threadIdx.x; i < S; i += blockDim.x) atomicAdd(&cnt[cost_bucket(cost[i])], 1);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&cnt[cost_bucket(cost[gb + i * gs])], 1);
     __syncthreads();
     if (threadIdx.x == 0) {
         int run = 0;
@@ -1591,7 +1592,10 @@ __global__ void __launch_bounds__(1024) k_solve_order(const uint32_t *cost, int 
         }
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < S; i += blockDim.x) order[atomicAdd(&base[cost_bucket(cost[i])], 1)] = i;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int sd = gb + i * gs;
+        order[atomicAdd(&base[cost_bucket(cost[sd])], 1)] = sd;
+    }
 }
 
 // Shared memory of the mixed solve besides the packed factor.
@@ -1662,8 +1666,8 @@ void launch_solve_mixed(const Geo &g, const Par &p, const int32_t *boxes, const 
         const size_t sm = solve_mixed_smem_rest(g, kSmallSolveM) + (size_t)fbytes;
         if (sm <= kSmemLimit) {
             cudaFuncSetAttribute(k_solve_mixed_small, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-            k_solve_order<<<1, 1024, 0, st>>>(w.cost, g.S, w.order, w.fb);
-            k_solve_mixed_small<<<g.S, kSmallSolveThreads, sm, st>>>(g, p, boxes, centres, beta, info, w, fbytes,
+            k_solve_order<<<1, 1024, 0, st>>>(w.cost, group_count(g), g.gb, g.gs, w.order, w.fb);
+            k_solve_mixed_small<<<group_count(g), kSmallSolveThreads, sm, st>>>(g, p, boxes, centres, beta, info, w, fbytes,
                                                                      fb);
             count_launches(2);
             if (fb) launch_fallback_f64(g, p, boxes, centres, beta, info, w, lam_tab, st);
@@ -1672,10 +1676,10 @@ void launch_solve_mixed(const Geo &g, const Par &p, const int32_t *boxes, const 
     }
     size_t sm = solve_mixed_smem(g);
     cudaFuncSetAttribute(k_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-    k_solve_order<<<1, 1024, 0, st>>>(w.cost, g.S, w.order, w.fb);
+    k_solve_order<<<1, 1024, 0, st>>>(w.cost, group_count(g), g.gb, g.gs, w.order, w.fb);
     count_launches(1);
     const int persistent = tuning().solve_persistent == 1 && w.fb != nullptr;
-    unsigned grid = (unsigned)g.S;
+    unsigned grid = (unsigned)group_count(g);
     if (persistent) {
         // as many CTAs as fit the device at once with this launch's shared memory
         int dev = 0, sms = 0, per = 0;
@@ -1683,7 +1687,7 @@ void launch_solve_mixed(const Geo &g, const Par &p, const int32_t *boxes, const 
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_solve_mixed, kMxThreads, sm);
         const int resident = sms * (per > 0 ? per : 1);
-        grid = (unsigned)(resident < g.S ? resident : g.S);
+        grid = (unsigned)(resident < (int)grid ? resident : (int)grid);
     }
     k_solve_mixed<<<grid, kMxThreads, sm, st>>>(g, p, boxes, centres, beta, info, w, factor_smem_bytes(g),
                                                 lam_tab, all, cv, cv_stride, fb, persistent);

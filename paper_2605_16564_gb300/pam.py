@@ -72,7 +72,7 @@ class pam_cells(C.Structure):
 
 class pam_tuning(C.Structure):
     _fields_ = [("factor_kb", C.c_int), ("gram_stages", C.c_int), ("eval_block", C.c_int),
-                ("solve_persistent", C.c_int), ("reserved", C.c_int * 4)]
+                ("solve_persistent", C.c_int), ("level_groups", C.c_int), ("reserved", C.c_int * 3)]
 
 
 class pam_model(C.Structure):
@@ -447,12 +447,12 @@ def pam_resume_cells(problem, params, plan, cells, K, model, workspace, stream=N
     return code
 
 
-def pam_tuning_set(factor_kb=0, gram_stages=0, eval_block=0, solve_persistent=0, reset=False):
+def pam_tuning_set(factor_kb=0, gram_stages=0, eval_block=0, solve_persistent=0, level_groups=0, reset=False):
     """Process-wide launch tuning (0 = built-in choice); reset=True restores all built-ins."""
     if reset:
         _check(lib().pam_tuning_set(None), "pam_tuning_set")
         return
-    t = pam_tuning(int(factor_kb), int(gram_stages), int(eval_block), int(solve_persistent))
+    t = pam_tuning(int(factor_kb), int(gram_stages), int(eval_block), int(solve_persistent), int(level_groups))
     _check(lib().pam_tuning_set(C.byref(t)), "pam_tuning_set")
 
 
@@ -460,7 +460,7 @@ def pam_tuning_get():
     t = pam_tuning()
     _check(lib().pam_tuning_get(C.byref(t)), "pam_tuning_get")
     return dict(factor_kb=t.factor_kb, gram_stages=t.gram_stages, eval_block=t.eval_block,
-                solve_persistent=t.solve_persistent)
+                solve_persistent=t.solve_persistent, level_groups=t.level_groups)
 
 
 def pam_autotune(problem, params, plan, K, model, workspace, pts=None, out=None, eval_workspace=None, stream=None,
@@ -484,7 +484,7 @@ def pam_autotune(problem, params, plan, K, model, workspace, pts=None, out=None,
                                         ms.ctypes.data)
     _check(code, "pam_autotune")
     return dict(factor_kb=t.factor_kb, gram_stages=t.gram_stages, eval_block=t.eval_block,
-                solve_persistent=t.solve_persistent), ms
+                solve_persistent=t.solve_persistent, level_groups=t.level_groups), ms
 
 
 def pam_selftest_wait(arrive, budget_cycles, flag, stream=None):

@@ -305,12 +305,13 @@ def test_model_blob_checks_without_a_gpu(pam):
 
 def test_tuning_set_get_and_checks(pam):
     pam.pam_tuning_set(reset=True)
-    assert pam.pam_tuning_get() == dict(factor_kb=0, gram_stages=0, eval_block=0, solve_persistent=0)
-    pam.pam_tuning_set(factor_kb=48, gram_stages=2, eval_block=512, solve_persistent=1)
-    want = dict(factor_kb=48, gram_stages=2, eval_block=512, solve_persistent=1)
+    assert pam.pam_tuning_get() == dict(factor_kb=0, gram_stages=0, eval_block=0, solve_persistent=0,
+                                        level_groups=0)
+    pam.pam_tuning_set(factor_kb=48, gram_stages=2, eval_block=512, solve_persistent=1, level_groups=2)
+    want = dict(factor_kb=48, gram_stages=2, eval_block=512, solve_persistent=1, level_groups=2)
     assert pam.pam_tuning_get() == want
     for bad in (dict(factor_kb=-1), dict(factor_kb=2), dict(gram_stages=4), dict(gram_stages=1), dict(eval_block=300),
-                dict(solve_persistent=2), dict(solve_persistent=-1)):
+                dict(solve_persistent=2), dict(solve_persistent=-1), dict(level_groups=3), dict(level_groups=-1)):
         with pytest.raises(pam.PamError):
             pam.pam_tuning_set(**bad)
     assert pam.pam_tuning_get() == want  # unchanged
