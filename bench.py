@@ -728,8 +728,8 @@ def run_pam(args, rank, ws):
 
     groups = None
     if prec == pam.PAM_PREC_MIXED:
-        # the refinement levels as one pipeline of launches over every
-        # subdomain, against the two subdomain groups on two streams
+        # the levels as one pipeline of launches over every subdomain,
+        # against the two subdomain groups on two streams
         tsave = pam.pam_tuning_get()
         n_groups = 2 if tsave["level_groups"] == 2 or (
             tsave["level_groups"] == 0 and fit.plan.n_subdomains >= 1024 and args.quad == 0) else 1
@@ -739,9 +739,9 @@ def run_pam(args, rank, ws):
         finally:
             pam.pam_tuning_set(**tsave)
         groups = {"groups": n_groups, "step_ms": round(step_ms, 3), "step_ms_one_pipeline": round(one_ms, 3),
-                  "note": "two groups (even and odd subdomains) run their refinement levels on two streams, "
-                          "so that one group's solve tail overlaps the other's work; the phase times come "
-                          "from one pipeline"}
+                  "note": "two groups (even and odd subdomains) run their levels (the initial lattices' "
+                          "solve and the refinement levels) on two streams, so that one group's solve tail "
+                          "overlaps the other's work; the phase times come from one pipeline"}
     if lw is not None:
         # the same step without the learned seed (level 0 from beta = 0), for
         # comparison, in the same launch mode

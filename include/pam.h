@@ -602,8 +602,10 @@ pam_status pam_nn_adamw(float *d_params, const float *d_grads, float *d_m, float
  *                longest-first order (the built-in), 1 one CTA per resident
  *                slot (two per SM), each taking the next subdomain of the
  *                same order from a device counter until none is left
- *   level_groups the mixed form's refinement levels (pam_refine,
- *                pam_refine_cells): 1 one pipeline of launches over every
+ *   level_groups the mixed form's levels (the initial lattices' statistics,
+ *                Gram and solve in pam_fit_subdomains / pam_fit_cells, the
+ *                refinement levels in pam_refine / pam_refine_cells; each
+ *                call forks and joins): 1 one pipeline of launches over every
  *                subdomain, 2 the subdomains in two groups (even and odd
  *                index), each running its levels on its own stream (the
  *                caller's and one the library creates per host thread and

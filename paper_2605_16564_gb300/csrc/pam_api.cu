@@ -353,6 +353,73 @@ static pam_status read_status(const Ws &w, cudaStream_t st, int32_t host[8]) {
 }
 
 // Step 2 launches shared by the grid and the element-list entry points.
+// Subdomain groups of the levels (the initial lattices' solve in
+// pam_fit_subdomains, the refinement levels in pam_refine). Each level is
+// (marking ->) statistics -> Gram -> solve over every subdomain, and the solve's last
+// subdomains leave most of the SMs idle while they finish (its costs vary
+// severalfold from subdomain to subdomain and are not known before it runs).
+// Split into two groups (even and odd subdomain indices, so that both hold
+// the same mix of the field), each group runs its levels in order on its own
+// stream: one group's solve tail overlaps the other group's marking, Gram
+// and solve. The subdomains are independent (section 2), so the results are
+// the same bits as one pipeline's. Each group has its own part of the solve
+// order and its own half of the binary64 fallback's slots.
+constexpr int kGroupMinS = 1024;  // below this the solve has few waves to balance
+
+static int level_groups(const Geo &g, const Par &p, const pam_params *par, const Ws &w) {
+    if (par->precision != PAM_PREC_MIXED || p.quad || w.fb_slots < 2) return 1;
+    if (g_timing) return 1;  // the phase profiler times one pipeline, phase by phase
+    if (g_tuning.level_groups == 1 || g_tuning.level_groups == 2) return g_tuning.level_groups;
+    return g.S >= kGroupMinS ? 2 : 1;
+}
+
+static Geo group_geo(const Geo &g, int q) {
+    Geo v = g;
+    v.gb = q;
+    v.gs = 2;
+    v.gn = (g.S - q + 1) / 2;
+    return v;
+}
+
+static Ws group_ws(const Geo &g, const Ws &w, int q) {
+    Ws v = w;
+    const int f0 = (w.fb_slots + 1) / 2;  // the even group is the larger one when S is odd
+    if (q == 0) {
+        v.fb_slots = f0;
+        return v;
+    }
+    const size_t mc = (size_t)g.m_cap, nm = (size_t)g.n_max;
+    v.order = w.order + (g.S + 1) / 2;
+    v.fb_slots = w.fb_slots - f0;
+    v.fb = w.fb + 2 + f0;
+    v.fbE = w.fbE + (size_t)f0 * mc * nm;
+    v.fbG = w.fbG + (size_t)f0 * mc * mc;
+    v.fbL = w.fbL + (size_t)f0 * (mc * (mc + 1) / 2);
+    return v;
+}
+
+// The second group's stream and the fork / join events, one set per host
+// thread and device (created on first use, kept for the process).
+struct GroupStreams {
+    cudaStream_t st = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+};
+
+static pam_status group_streams(GroupStreams **out) {
+    thread_local std::vector<GroupStreams> per_dev;
+    int dev = 0;
+    PAM_CUDA_TRY(cudaGetDevice(&dev));
+    if ((int)per_dev.size() <= dev) per_dev.resize(dev + 1);
+    GroupStreams &gs = per_dev[dev];
+    if (!gs.st) {
+        PAM_CUDA_TRY(cudaStreamCreateWithFlags(&gs.st, cudaStreamNonBlocking));
+        PAM_CUDA_TRY(cudaEventCreateWithFlags(&gs.fork, cudaEventDisableTiming));
+        PAM_CUDA_TRY(cudaEventCreateWithFlags(&gs.join, cudaEventDisableTiming));
+    }
+    *out = &gs;
+    return PAM_OK;
+}
+
 static pam_status fit_launches(const Geo &g, const Par &p, const pam_params *par, const double *d_K,
                                pam_model *model, const Ws &w, cudaStream_t s) {
     pam_status st;
@@ -376,7 +443,19 @@ static pam_status fit_launches(const Geo &g, const Par &p, const pam_params *par
     }
     launch_init_dictionary(g, model->boxes, model->centres, model->beta, model->info, s,
                            par->warm_start != 0);
-    if (par->precision == PAM_PREC_MIXED)
+    if (par->precision == PAM_PREC_MIXED && level_groups(g, p, par, w) == 2) {
+        // the initial lattices' statistics, Gram and solve in the two groups
+        GroupStreams *gs = nullptr;
+        if ((st = group_streams(&gs)) != PAM_OK) return st;
+        PAM_CUDA_TRY(cudaEventRecord(gs->fork, s));
+        PAM_CUDA_TRY(cudaStreamWaitEvent(gs->st, gs->fork, 0));
+        const cudaStream_t sq[2] = {s, gs->st};
+        for (int q = 0; q < 2; ++q)
+            launch_solve_level_mixed(group_geo(g, q), p, model->boxes, model->centres, model->beta, model->info,
+                                     group_ws(g, w, q), sq[q], seeded, g.m0);
+        PAM_CUDA_TRY(cudaEventRecord(gs->join, gs->st));
+        PAM_CUDA_TRY(cudaStreamWaitEvent(s, gs->join, 0));
+    } else if (par->precision == PAM_PREC_MIXED)
         launch_solve_level_mixed(g, p, model->boxes, model->centres, model->beta, model->info, w, s, seeded,
                                  g.m0);  // every dictionary is the initial lattice
     else
@@ -464,72 +543,6 @@ pam_status pam_status_read(const pam_plan *plan, void *d_workspace, size_t works
     if (hs[kStBadK]) return PAM_ERR_NONPOSITIVE_K;
     if (hs[kStTimeout]) return PAM_ERR_TIMEOUT;
     return hs[kStUncertified] ? PAM_ERR_NOT_CONVERGED : PAM_OK;
-}
-
-// Subdomain groups of the refinement levels. Each level is marking ->
-// statistics -> Gram -> solve over every subdomain, and the solve's last
-// subdomains leave most of the SMs idle while they finish (its costs vary
-// severalfold from subdomain to subdomain and are not known before it runs).
-// Split into two groups (even and odd subdomain indices, so that both hold
-// the same mix of the field), each group runs its levels in order on its own
-// stream: one group's solve tail overlaps the other group's marking, Gram
-// and solve. The subdomains are independent (section 2), so the results are
-// the same bits as one pipeline's. Each group has its own part of the solve
-// order and its own half of the binary64 fallback's slots.
-constexpr int kGroupMinS = 1024;  // below this the solve has few waves to balance
-
-static int level_groups(const Geo &g, const Par &p, const pam_params *par, const Ws &w) {
-    if (par->precision != PAM_PREC_MIXED || p.quad || w.fb_slots < 2) return 1;
-    if (g_timing) return 1;  // the phase profiler times one pipeline, phase by phase
-    if (g_tuning.level_groups == 1 || g_tuning.level_groups == 2) return g_tuning.level_groups;
-    return g.S >= kGroupMinS ? 2 : 1;
-}
-
-static Geo group_geo(const Geo &g, int q) {
-    Geo v = g;
-    v.gb = q;
-    v.gs = 2;
-    v.gn = (g.S - q + 1) / 2;
-    return v;
-}
-
-static Ws group_ws(const Geo &g, const Ws &w, int q) {
-    Ws v = w;
-    const int f0 = (w.fb_slots + 1) / 2;  // the even group is the larger one when S is odd
-    if (q == 0) {
-        v.fb_slots = f0;
-        return v;
-    }
-    const size_t mc = (size_t)g.m_cap, nm = (size_t)g.n_max;
-    v.order = w.order + (g.S + 1) / 2;
-    v.fb_slots = w.fb_slots - f0;
-    v.fb = w.fb + 2 + f0;
-    v.fbE = w.fbE + (size_t)f0 * mc * nm;
-    v.fbG = w.fbG + (size_t)f0 * mc * mc;
-    v.fbL = w.fbL + (size_t)f0 * (mc * (mc + 1) / 2);
-    return v;
-}
-
-// The second group's stream and the fork / join events, one set per host
-// thread and device (created on first use, kept for the process).
-struct GroupStreams {
-    cudaStream_t st = nullptr;
-    cudaEvent_t fork = nullptr, join = nullptr;
-};
-
-static pam_status group_streams(GroupStreams **out) {
-    thread_local std::vector<GroupStreams> per_dev;
-    int dev = 0;
-    PAM_CUDA_TRY(cudaGetDevice(&dev));
-    if ((int)per_dev.size() <= dev) per_dev.resize(dev + 1);
-    GroupStreams &gs = per_dev[dev];
-    if (!gs.st) {
-        PAM_CUDA_TRY(cudaStreamCreateWithFlags(&gs.st, cudaStreamNonBlocking));
-        PAM_CUDA_TRY(cudaEventCreateWithFlags(&gs.fork, cudaEventDisableTiming));
-        PAM_CUDA_TRY(cudaEventCreateWithFlags(&gs.join, cudaEventDisableTiming));
-    }
-    *out = &gs;
-    return PAM_OK;
 }
 
 // Step 3 launches shared by the grid and the element-list entry points.
