@@ -732,7 +732,7 @@ def run_pam(args, rank, ws):
         # against the two subdomain groups on two streams
         tsave = pam.pam_tuning_get()
         n_groups = 2 if tsave["level_groups"] == 2 or (
-            tsave["level_groups"] == 0 and fit.plan.n_subdomains >= 1024 and args.quad == 0) else 1
+            tsave["level_groups"] == 0 and fit.plan.n_subdomains >= 1024) else 1
         pam.pam_tuning_set(**dict(tsave, level_groups=1))
         try:
             one_ms = time_variant(step_body)

@@ -615,9 +615,9 @@ pam_status pam_nn_adamw(float *d_params, const float *d_grads, float *d_m, float
  *                binary64 fallback's slots (the even group the larger half),
  *                and the results are the same bits as one pipeline's unless
  *                a group runs out of slots where the one list would not.
- *                0: two groups from 1,024 subdomains up
- *                (midpoint indicators; one pipeline while the phase
- *                profiler is on). The autotuner does not choose it.
+ *                0: two groups from 1,024 subdomains up (one pipeline
+ *                while the phase profiler is on). The autotuner does not
+ *                choose it.
  * pam_tuning_set (NULL: all built-in) applies to every later launch of the
  * process; it is not synchronised with launches in flight on other threads.
  * pam_autotune measures, on a fitted model (after pam_fit_subdomains /

@@ -367,7 +367,7 @@ static pam_status read_status(const Ws &w, cudaStream_t st, int32_t host[8]) {
 constexpr int kGroupMinS = 1024;  // below this the solve has few waves to balance
 
 static int level_groups(const Geo &g, const Par &p, const pam_params *par, const Ws &w) {
-    if (par->precision != PAM_PREC_MIXED || p.quad || w.fb_slots < 2) return 1;
+    if (par->precision != PAM_PREC_MIXED || w.fb_slots < 2) return 1;
     if (g_timing) return 1;  // the phase profiler times one pipeline, phase by phase
     if (g_tuning.level_groups == 1 || g_tuning.level_groups == 2) return g_tuning.level_groups;
     return g.S >= kGroupMinS ? 2 : 1;

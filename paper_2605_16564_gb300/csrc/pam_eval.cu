@@ -1155,12 +1155,15 @@ void launch_errors_cells(const Geo &g, const int32_t *boxes, const double *centr
 // R_T = sum_q (|T| / 2^dim) (K*(x_q) - K_T)^2 over the nodes x_T +- h/(2
 // sqrt 3) per axis, K* from the subdomain's whole dictionary at each node
 // (Shepard weights, max-shifted). One block per running subdomain, a thread
-// per patch cell (patch order, x fastest).
+// per patch cell (patch order, x fastest). The fp32 form evaluates as
+// pam_eval does (the scaled logit, origin at the patch centre), four nodes
+// of a cell per pass through the centres in two packed pairs; the sum keeps
+// the node order in both forms.
 // --------------------------------------------------------------------------
 template <bool F32>
 __global__ void __launch_bounds__(256) k_residual_quad(Geo g, const int32_t *boxes, const double *centres,
                                                        const double *beta, const int32_t *info, Ws w) {
-    const int s = blockIdx.x;
+    const int s = group_sub(g, blockIdx.x);
     const int32_t *inf = info + s * kInfoN;
     if (inf[PAM_INFO_STOPPED]) return;
     const int M = inf[PAM_INFO_M], N = inf[PAM_INFO_N_CELLS];
@@ -1168,10 +1171,10 @@ __global__ void __launch_bounds__(256) k_residual_quad(Geo g, const int32_t *box
     extern __shared__ uint8_t smb[];
     dvec4 *sc64 = reinterpret_cast<dvec4 *>(smb);
     double *sb64 = reinterpret_cast<double *>(sc64 + g.m_cap);
-    float4 *sc32 = reinterpret_cast<float4 *>(smb);
-    float *sb32 = reinterpret_cast<float *>(sc32 + g.m_cap);
+    float4 *su = reinterpret_cast<float4 *>(smb);
+    float2 *sb = reinterpret_cast<float2 *>(su + 2 * g.m_cap);
     double o[3];
-    if (F32) stage_f32(g, boxes, centres, beta, s, M, sc32, sb32, o);
+    if (F32) stage_f32s(g, boxes, centres, beta, s, M, su, sb, o);
     else stage_f64(g, centres, beta, s, M, sc64, sb64);
     const int w0 = box[9] - box[6], w1 = box[10] - box[7];
     const int nq = 1 << g.dim;
@@ -1182,29 +1185,46 @@ __global__ void __launch_bounds__(256) k_residual_quad(Geo g, const int32_t *box
         for (int a = 0; a < g.dim; ++a) xc[a] = __dmul_rn((double)idx[a] + 0.5, g.h);
         const double kv = w.kv[(size_t)s * g.n_max + t];
         double r = 0.0;
-        // nodes in pairs (q, q + 1): in the fp32 form one pass over the
-        // centres serves both; the sum keeps the node order
-        for (int q = 0; q < nq; q += 2) {
-            double x0[3] = {0, 0, 0}, x1[3] = {0, 0, 0};
-            for (int a = 0; a < g.dim; ++a) {
-                x0[a] = __dadd_rn(xc[a], ((q >> a) & 1) ? off : -off);
-                x1[a] = __dadd_rn(xc[a], (((q + 1) >> a) & 1) ? off : -off);
+        if (F32) {
+            // K*(x_q) - K_T = K_T expm1(v_q - ln K_T) in fp32 (the surrogate's
+            // logit v_q carries fp32 rounding already): no binary64 exp per
+            // node, whose cost on this part's narrow fp64 pipe rivals the
+            // node's pass through the centres
+            const double yl = w.y[(size_t)s * g.n_max + t];
+            const double c = __dmul_rn(wq, __dmul_rn(kv, kv));
+            // the cell centre in local coordinates, the nodes at +-off from it in fp32
+            float pc[3];
+#pragma unroll
+            for (int a = 0; a < 3; ++a) pc[a] = a < g.dim ? (float)(xc[a] - o[a]) : 0.f;
+            const float offf = (float)off;
+            for (int q0 = 0; q0 < nq; q0 += 4) {
+                float p[4][3];
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    const int q = q0 + k < nq ? q0 + k : q0;  // 1-D: two nodes, the idle pair repeats them
+#pragma unroll
+                    for (int a = 0; a < 3; ++a)
+                        p[k][a] = a < g.dim ? pc[a] + (((q >> a) & 1) ? offf : -offf) : 0.f;
+                }
+                float v[4];
+                shepard_f32s<4>(su, sb, M, p, v);
+                for (int k = 0; k < 4 && q0 + k < nq; ++k) {
+                    const float e = expm1f((float)__dsub_rn((double)v[k], yl));
+                    r = __dadd_rn(r, __dmul_rn(c, (double)(e * e)));
+                }
             }
-            double v0, v1;
-            if (F32) {
-                const float p0[3] = {(float)(x0[0] - o[0]), (float)(x0[1] - o[1]), (float)(x0[2] - o[2])};
-                const float p1[3] = {(float)(x1[0] - o[0]), (float)(x1[1] - o[1]), (float)(x1[2] - o[2])};
-                float f0, f1;
-                shepard_f32_smem2(sc32, sb32, M, p0, p1, &f0, &f1);
-                v0 = f0;
-                v1 = f1;
-            } else {
-                v0 = shepard_f64_smem(sc64, sb64, M, x0);
-                v1 = shepard_f64_smem(sc64, sb64, M, x1);
+        } else {
+            for (int q = 0; q < nq; q += 2) {
+                double x0[3] = {0, 0, 0}, x1[3] = {0, 0, 0};
+                for (int a = 0; a < g.dim; ++a) {
+                    x0[a] = __dadd_rn(xc[a], ((q >> a) & 1) ? off : -off);
+                    x1[a] = __dadd_rn(xc[a], (((q + 1) >> a) & 1) ? off : -off);
+                }
+                const double v0 = shepard_f64_smem(sc64, sb64, M, x0), v1 = shepard_f64_smem(sc64, sb64, M, x1);
+                const double e0 = __dsub_rn(exp(v0), kv), e1 = __dsub_rn(exp(v1), kv);
+                r = __dadd_rn(r, __dmul_rn(wq, __dmul_rn(e0, e0)));
+                r = __dadd_rn(r, __dmul_rn(wq, __dmul_rn(e1, e1)));
             }
-            const double e0 = __dsub_rn(exp(v0), kv), e1 = __dsub_rn(exp(v1), kv);
-            r = __dadd_rn(r, __dmul_rn(wq, __dmul_rn(e0, e0)));
-            r = __dadd_rn(r, __dmul_rn(wq, __dmul_rn(e1, e1)));
         }
         w.R[(size_t)s * g.n_max + t] = r;
     }
@@ -1214,13 +1234,13 @@ void launch_residual_quad(const Geo &g, int precision, const int32_t *boxes, con
                           const double *beta, const int32_t *info, const Ws &w, cudaStream_t st) {
     PhaseScope ps(kPhResidual, st);
     if (precision == PAM_PREC_MIXED) {
-        size_t sm = stage_f32_smem(g.m_cap);
+        size_t sm = stage_f32s_smem(g.m_cap);
         cudaFuncSetAttribute(k_residual_quad<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_residual_quad<true><<<g.S, 256, sm, st>>>(g, boxes, centres, beta, info, w);
+        k_residual_quad<true><<<group_count(g), 256, sm, st>>>(g, boxes, centres, beta, info, w);
     } else {
         size_t sm = (size_t)g.m_cap * (sizeof(dvec4) + sizeof(double));
         cudaFuncSetAttribute(k_residual_quad<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_residual_quad<false><<<g.S, 256, sm, st>>>(g, boxes, centres, beta, info, w);
+        k_residual_quad<false><<<group_count(g), 256, sm, st>>>(g, boxes, centres, beta, info, w);
     }
     count_launches(1);
 }

@@ -57,6 +57,19 @@ def test_two_groups_match_one_pipeline_2d(env):
     np.testing.assert_array_equal(o1, o2)
 
 
+def test_two_groups_with_gauss_legendre_indicators(env):
+    # quad = 1: the indicators come from their own kernel at the start of
+    # each refinement round, launched per group
+    K = fields.voronoi_field(192, n_sites=24, seed=3)
+    geo = ((192, 192), (6, 6), 2, (6, 6))
+    pts = np.random.default_rng(7).uniform(0, 1, size=(10000, 2))
+    _, c1, one, o1 = _fit(env, K, geo, 1, pts, k_top=20, levels=2, quad=1)
+    _, c2, two, o2 = _fit(env, K, geo, 2, pts, k_top=20, levels=2, quad=1)
+    assert c1 == c2 == 0
+    _same(one, two)
+    np.testing.assert_array_equal(o1, o2)
+
+
 def test_two_groups_odd_count_3d(env):
     # 5 x 3 x 3 = 45 subdomains: 23 in the even group, 22 in the odd one
     shape = (40, 24, 18)
