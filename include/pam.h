@@ -648,6 +648,19 @@ typedef struct {
 } pam_tuning;
 pam_status pam_tuning_set(const pam_tuning *t);
 pam_status pam_tuning_get(pam_tuning *t);
+/*
+ * Host only: the subdomain groups the mixed form's levels would run in for
+ * a problem of n_subdomains subdomains under the current tuning (the phase
+ * profiler off). Returns the number of groups (1 or 2), or -1 for
+ * n_subdomains < 1. For each group q, out[7 q .. 7 q + 6] (caller-owned,
+ * 14 entries) = its first subdomain, the stride between its subdomains,
+ * their count, the offset of its solve order in the workspace's order
+ * region (entries), the offset of its fallback list in the list region
+ * (int32 words: two counters, then the slots' subdomains), its number of
+ * binary64 fallback slots and the first of them. One group: the whole
+ * range, offsets 0 and min(n_subdomains, 32) slots.
+ */
+int pam_group_layout(int n_subdomains, int32_t *out);
 pam_status pam_autotune(const pam_problem *prob, const pam_params *par, const pam_plan *plan, const double *d_K,
                         pam_model *model, void *d_workspace, size_t workspace_bytes, const double *d_pts,
                         int64_t n_pts, double *d_out, void *d_eval_workspace, size_t eval_workspace_bytes,

@@ -373,28 +373,39 @@ static int level_groups(const Geo &g, const Par &p, const pam_params *par, const
     return g.S >= kGroupMinS ? 2 : 1;
 }
 
+// Group q of ng: its subdomains gb + i gs (i < gn), the offset of its solve
+// order in the order region, of its fallback list in the list region (two
+// counters, then the slots' subdomains), its slots and the first of them.
+struct GroupLayout {
+    int gb, gs, gn, order_off, list_off, slots, slot0;
+};
+
+static GroupLayout group_layout(int S, int F, int q, int ng) {
+    if (ng == 1) return {0, 1, S, 0, 0, F, 0};
+    const int f0 = (F + 1) / 2;  // the even group is the larger one when S is odd
+    if (q == 0) return {0, 2, (S + 1) / 2, 0, 0, f0, 0};
+    return {1, 2, S / 2, (S + 1) / 2, 2 + f0, F - f0, f0};
+}
+
 static Geo group_geo(const Geo &g, int q) {
+    const GroupLayout l = group_layout(g.S, 0, q, 2);
     Geo v = g;
-    v.gb = q;
-    v.gs = 2;
-    v.gn = (g.S - q + 1) / 2;
+    v.gb = l.gb;
+    v.gs = l.gs;
+    v.gn = l.gn;
     return v;
 }
 
 static Ws group_ws(const Geo &g, const Ws &w, int q) {
-    Ws v = w;
-    const int f0 = (w.fb_slots + 1) / 2;  // the even group is the larger one when S is odd
-    if (q == 0) {
-        v.fb_slots = f0;
-        return v;
-    }
+    const GroupLayout l = group_layout(g.S, w.fb_slots, q, 2);
     const size_t mc = (size_t)g.m_cap, nm = (size_t)g.n_max;
-    v.order = w.order + (g.S + 1) / 2;
-    v.fb_slots = w.fb_slots - f0;
-    v.fb = w.fb + 2 + f0;
-    v.fbE = w.fbE + (size_t)f0 * mc * nm;
-    v.fbG = w.fbG + (size_t)f0 * mc * mc;
-    v.fbL = w.fbL + (size_t)f0 * (mc * (mc + 1) / 2);
+    Ws v = w;
+    v.order = w.order + l.order_off;
+    v.fb = w.fb + l.list_off;
+    v.fb_slots = l.slots;
+    v.fbE = w.fbE + (size_t)l.slot0 * mc * nm;
+    v.fbG = w.fbG + (size_t)l.slot0 * mc * mc;
+    v.fbL = w.fbL + (size_t)l.slot0 * (mc * (mc + 1) / 2);
     return v;
 }
 
@@ -1132,6 +1143,26 @@ pam_status pam_tuning_set(const pam_tuning *t) {
     if (t->level_groups < 0 || t->level_groups > 2) return PAM_ERR_INVALID_ARG;
     g_tuning = *t;
     return PAM_OK;
+}
+
+int pam_group_layout(int n_subdomains, int32_t *out) {
+    if (n_subdomains < 1 || !out) return -1;
+    Geo g{};
+    g.S = n_subdomains;
+    pam_params par{};
+    par.precision = PAM_PREC_MIXED;
+    Ws w{};
+    w.fb_slots = n_subdomains < kFbSlots ? n_subdomains : kFbSlots;
+    const bool timing = g_timing;
+    g_timing = false;
+    const int ng = level_groups(g, Par{}, &par, w);
+    g_timing = timing;
+    for (int q = 0; q < ng; ++q) {
+        const GroupLayout l = group_layout(g.S, w.fb_slots, q, ng);
+        const int32_t v[7] = {l.gb, l.gs, l.gn, l.order_off, l.list_off, l.slots, l.slot0};
+        for (int k = 0; k < 7; ++k) out[7 * q + k] = v[k];
+    }
+    return ng;
 }
 
 pam_status pam_tuning_get(pam_tuning *t) {

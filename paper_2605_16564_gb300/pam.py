@@ -37,7 +37,7 @@ EXPORTED = ["pam_version", "pam_status_string", "pam_plan_create", "pam_partitio
             "pam_eval_glued_workspace_size", "pam_eval_glued", "pam_partition_cells", "pam_plan_create_cells",
             "pam_fit_cells", "pam_refine_cells", "pam_errors_cells", "pam_model_save", "pam_model_load",
             "pam_resume", "pam_resume_cells", "pam_tuning_set", "pam_tuning_get", "pam_autotune",
-            "pam_autotune_cells", "pam_selftest_wait", "pam_error_sums", "pam_nn_inputs"]
+            "pam_autotune_cells", "pam_selftest_wait", "pam_error_sums", "pam_nn_inputs", "pam_group_layout"]
 
 
 class PamError(RuntimeError):
@@ -454,6 +454,19 @@ def pam_tuning_set(factor_kb=0, gram_stages=0, eval_block=0, solve_persistent=0,
         return
     t = pam_tuning(int(factor_kb), int(gram_stages), int(eval_block), int(solve_persistent), int(level_groups))
     _check(lib().pam_tuning_set(C.byref(t)), "pam_tuning_set")
+
+
+def pam_group_layout(n_subdomains):
+    """The subdomain groups of the mixed form's levels for n_subdomains
+    subdomains under the current tuning: a list of dicts, one per group."""
+    out = np.zeros(14, dtype=np.int32)
+    L = lib()
+    L.pam_group_layout.restype = C.c_int
+    n = L.pam_group_layout(int(n_subdomains), out.ctypes.data_as(C.c_void_p))
+    if n < 1:
+        raise PamError(PAM_ERR_INVALID_ARG, "pam_group_layout")
+    keys = ("first", "stride", "count", "order_offset", "list_offset", "slots", "first_slot")
+    return [dict(zip(keys, (int(v) for v in out[7 * q:7 * q + 7]))) for q in range(n)]
 
 
 def pam_tuning_get():

@@ -408,3 +408,47 @@ def test_subdomain_range_and_error_sums_are_checked(pam):
     s = np.array([6.0, 12.0, 8.0, 32.0, 3.0, 6.0, np.log(10.0) * 0.5, 0.0])
     e = pam.error_measures_from_sums(s)
     assert e == dict(l1=0.5, l2=0.5, l1_log=0.5, max_log10=pytest.approx(0.5))
+
+
+def _check_group_layout(groups, S):
+    F = min(S, 32)
+    subs, order, lists, slots = [], [], [], []
+    for g in groups:
+        subs += [g["first"] + i * g["stride"] for i in range(g["count"])]
+        order += list(range(g["order_offset"], g["order_offset"] + g["count"]))
+        lists += list(range(g["list_offset"], g["list_offset"] + 2 + g["slots"]))
+        slots += list(range(g["first_slot"], g["first_slot"] + g["slots"]))
+        assert g["slots"] >= 1
+        if S <= 32:  # every subdomain of the group can take a slot, as in one list
+            assert g["slots"] == g["count"]
+    # the groups partition the subdomains, the order region, the slots; the
+    # lists fit the 4 + F words carved for them, without overlap
+    assert sorted(subs) == list(range(S))
+    assert sorted(order) == list(range(S))
+    assert sorted(slots) == list(range(F))
+    assert len(set(lists)) == len(lists) and max(lists) < 4 + F
+
+
+def test_subdomain_group_layout(pam):
+    pam.pam_tuning_set(reset=True)
+    try:
+        for S in (1, 2, 3, 9, 25, 64, 1023):
+            groups = pam.pam_group_layout(S)
+            assert len(groups) == 1 and groups[0] == dict(first=0, stride=1, count=S, order_offset=0,
+                                                          list_offset=0, slots=min(S, 32), first_slot=0)
+        for S in (1024, 1025, 2244, 5001):
+            groups = pam.pam_group_layout(S)
+            assert len(groups) == 2 and [g["first"] for g in groups] == [0, 1]
+            _check_group_layout(groups, S)
+        pam.pam_tuning_set(level_groups=2)
+        for S in (2, 3, 9, 25, 33, 64, 1023):
+            groups = pam.pam_group_layout(S)
+            assert len(groups) == 2
+            _check_group_layout(groups, S)
+        assert len(pam.pam_group_layout(1)) == 1  # one subdomain: one fallback slot, one group
+        pam.pam_tuning_set(level_groups=1)
+        assert len(pam.pam_group_layout(2244)) == 1
+        with pytest.raises(pam.PamError):
+            pam.pam_group_layout(0)
+    finally:
+        pam.pam_tuning_set(reset=True)
