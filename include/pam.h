@@ -321,6 +321,24 @@ pam_status pam_eval(const pam_problem *prob, const pam_plan *plan,
                     size_t workspace_bytes, void *stream);
 
 /*
+ * pam_eval in two calls. pam_eval_bucket buckets the points by owner core in
+ * d_workspace and writes NaN to d_out for the points outside the grid; it
+ * reads no model, so it may run before or beside the fit (on another stream).
+ * pam_eval_bucketed then evaluates the model at the bucketed points into the
+ * other entries of d_out: the same values as pam_eval, bit for bit. Between
+ * the two calls the caller keeps d_pts, d_out and d_workspace unchanged and
+ * orders the second after the first (same stream, or an event); the same
+ * arguments and checks as pam_eval, the bucketing's precision irrelevant.
+ */
+pam_status pam_eval_bucket(const pam_problem *prob, const pam_plan *plan, const double *d_pts,
+                           int64_t n_pts, double *d_out, void *d_workspace, size_t workspace_bytes,
+                           void *stream);
+pam_status pam_eval_bucketed(const pam_problem *prob, const pam_plan *plan,
+                             const pam_model *model, const double *d_pts, int64_t n_pts,
+                             double *d_out, int log_space, int precision, void *d_workspace,
+                             size_t workspace_bytes, void *stream);
+
+/*
  * Glued evaluation (section 2, Step 4 remark: the piecewise surrogate of
  * pam_eval is discontinuous across subdomain interfaces, and a gluing or
  * averaging of neighbouring local surrogates makes it continuous; the paper

@@ -654,24 +654,58 @@ pam_status pam_eval_workspace_size(const pam_plan *plan, int64_t n_pts, size_t *
     return PAM_OK;
 }
 
-pam_status pam_eval(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
-                    const double *d_pts, int64_t n_pts, double *d_out, int log_space, int precision,
-                    void *d_workspace, size_t workspace_bytes, void *stream) {
-    Geo g;
+// The argument checks of the evaluation calls (model: NULL for the bucketing).
+static pam_status eval_args(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
+                            bool need_model, const double *d_pts, int64_t n_pts, double *d_out, int precision,
+                            void *d_workspace, size_t workspace_bytes, Geo *g) {
     pam_status st;
-    if (!make_geo(prob, nullptr, &g, nullptr, &st)) return st;
-    if (!plan || plan->n_subdomains != g.S || plan->m_cap > PAM_MAX_M || plan->m_cap < 1)
+    if (!make_geo(prob, nullptr, g, nullptr, &st)) return st;
+    if (!plan || plan->n_subdomains != g->S || plan->m_cap > PAM_MAX_M || plan->m_cap < 1)
         return PAM_ERR_INVALID_ARG;
-    g.m_cap = plan->m_cap;
-    g.n_max = plan->max_patch_cells;
-    if (n_pts < 0 || !model_ok(model)) return PAM_ERR_INVALID_ARG;
+    g->m_cap = plan->m_cap;
+    g->n_max = plan->max_patch_cells;
+    if (n_pts < 0 || (need_model && !model_ok(model))) return PAM_ERR_INVALID_ARG;
     if (precision != PAM_PREC_FP64 && precision != PAM_PREC_MIXED) return PAM_ERR_INVALID_ARG;
     if (n_pts > (int64_t)INT32_MAX) return PAM_ERR_UNSUPPORTED;
     if (n_pts == 0) return PAM_OK;
     if (!d_pts || !d_out || !d_workspace) return PAM_ERR_INVALID_ARG;
-    if (workspace_bytes < eval_workspace_bytes(g.S, n_pts)) return PAM_ERR_WORKSPACE;
+    if (workspace_bytes < eval_workspace_bytes(g->S, n_pts)) return PAM_ERR_WORKSPACE;
+    return PAM_OK;
+}
+
+pam_status pam_eval(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
+                    const double *d_pts, int64_t n_pts, double *d_out, int log_space, int precision,
+                    void *d_workspace, size_t workspace_bytes, void *stream) {
+    Geo g;
+    pam_status st = eval_args(prob, plan, model, true, d_pts, n_pts, d_out, precision, d_workspace,
+                              workspace_bytes, &g);
+    if (st != PAM_OK || n_pts == 0) return st;
     launch_eval(g, model->boxes, model->centres, model->beta, model->info, d_pts, n_pts, d_out,
                 log_space, precision, d_workspace, (cudaStream_t)stream);
+    PAM_CUDA_TRY(cudaGetLastError());
+    return PAM_OK;
+}
+
+pam_status pam_eval_bucket(const pam_problem *prob, const pam_plan *plan, const double *d_pts, int64_t n_pts,
+                           double *d_out, void *d_workspace, size_t workspace_bytes, void *stream) {
+    Geo g;
+    pam_status st = eval_args(prob, plan, nullptr, false, d_pts, n_pts, d_out, PAM_PREC_FP64, d_workspace,
+                              workspace_bytes, &g);
+    if (st != PAM_OK || n_pts == 0) return st;
+    launch_eval_bucket(g, d_pts, n_pts, d_out, d_workspace, (cudaStream_t)stream);
+    PAM_CUDA_TRY(cudaGetLastError());
+    return PAM_OK;
+}
+
+pam_status pam_eval_bucketed(const pam_problem *prob, const pam_plan *plan, const pam_model *model,
+                             const double *d_pts, int64_t n_pts, double *d_out, int log_space, int precision,
+                             void *d_workspace, size_t workspace_bytes, void *stream) {
+    Geo g;
+    pam_status st = eval_args(prob, plan, model, true, d_pts, n_pts, d_out, precision, d_workspace,
+                              workspace_bytes, &g);
+    if (st != PAM_OK || n_pts == 0) return st;
+    launch_eval_bucketed(g, model->boxes, model->centres, model->beta, model->info, d_pts, n_pts, d_out,
+                         log_space, precision, d_workspace, (cudaStream_t)stream);
     PAM_CUDA_TRY(cudaGetLastError());
     return PAM_OK;
 }

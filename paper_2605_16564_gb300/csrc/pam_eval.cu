@@ -444,9 +444,9 @@ static int eval_block() {
     return (b == 128 || b == 256 || b == 512 || b == 1024) ? b : 256;
 }
 
-void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
-                 const int32_t *info, const double *pts, int64_t n_pts, double *out, int log_space,
-                 int precision, void *ws, cudaStream_t st) {
+// The points bucketed by owner (they and the partition only, not the model:
+// a caller may run it beside the fit); NaN into out for points outside the grid.
+void launch_eval_bucket(const Geo &g, const double *pts, int64_t n_pts, double *out, void *ws, cudaStream_t st) {
     PhaseScope ps(kPhEval, st);
     EvalWs e = carve_eval_workspace(g.S, n_pts, ws);
     cudaMemsetAsync(e.count, 0, (size_t)g.S * sizeof(int32_t), st);
@@ -454,6 +454,15 @@ void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, cons
     k_eval_owner<<<nb, 256, 0, st>>>(g, pts, n_pts, e.owner, e.rank, e.count, out);
     k_eval_scan<<<1, 1024, 0, st>>>(e.count, e.start, g.S);
     k_eval_scatter<<<nb, 256, 0, st>>>(e.owner, e.rank, e.start, e.perm, n_pts);
+    count_launches(3);
+}
+
+// The surrogate at the bucketed points, one block per owner.
+void launch_eval_bucketed(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
+                          const int32_t *info, const double *pts, int64_t n_pts, double *out, int log_space,
+                          int precision, void *ws, cudaStream_t st) {
+    PhaseScope ps(kPhEval, st);
+    EvalWs e = carve_eval_workspace(g.S, n_pts, ws);
     {
         PhaseScope pk(kPhEvalKernel, st);  // the per-owner kernel alone
         if (precision == PAM_PREC_MIXED) {
@@ -468,7 +477,14 @@ void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, cons
                                                              log_space);
         }
     }
-    count_launches(4);
+    count_launches(1);
+}
+
+void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
+                 const int32_t *info, const double *pts, int64_t n_pts, double *out, int log_space,
+                 int precision, void *ws, cudaStream_t st) {
+    launch_eval_bucket(g, pts, n_pts, out, ws, st);
+    launch_eval_bucketed(g, boxes, centres, beta, info, pts, n_pts, out, log_space, precision, ws, st);
 }
 
 // --------------------------------------------------------------------------

@@ -142,6 +142,10 @@ void launch_solve_level_mixed(const Geo &g, const Par &p, const int32_t *boxes, 
                               cudaEvent_t before_solve = nullptr, int m_bound = 0);
 void launch_refine_round(const Geo &g, const Par &p, int precision, const int32_t *boxes,
                          double *centres, double *beta, int32_t *info, const Ws &w, cudaStream_t st);
+void launch_eval_bucket(const Geo &g, const double *pts, int64_t n_pts, double *out, void *ws, cudaStream_t st);
+void launch_eval_bucketed(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
+                          const int32_t *info, const double *pts, int64_t n_pts, double *out, int log_space,
+                          int precision, void *ws, cudaStream_t st);
 void launch_eval(const Geo &g, const int32_t *boxes, const double *centres, const double *beta,
                  const int32_t *info, const double *pts, int64_t n_pts, double *out, int log_space,
                  int precision, void *ws, cudaStream_t st);

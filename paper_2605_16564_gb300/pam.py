@@ -37,7 +37,8 @@ EXPORTED = ["pam_version", "pam_status_string", "pam_plan_create", "pam_partitio
             "pam_eval_glued_workspace_size", "pam_eval_glued", "pam_partition_cells", "pam_plan_create_cells",
             "pam_fit_cells", "pam_refine_cells", "pam_errors_cells", "pam_model_save", "pam_model_load",
             "pam_resume", "pam_resume_cells", "pam_tuning_set", "pam_tuning_get", "pam_autotune",
-            "pam_autotune_cells", "pam_selftest_wait", "pam_error_sums", "pam_nn_inputs", "pam_group_layout"]
+            "pam_autotune_cells", "pam_selftest_wait", "pam_error_sums", "pam_nn_inputs", "pam_group_layout",
+            "pam_eval_bucket", "pam_eval_bucketed"]
 
 
 class PamError(RuntimeError):
@@ -314,6 +315,22 @@ def pam_eval(problem, plan, model, pts, out, log_space=False, precision=PAM_PREC
     _check(lib().pam_eval(C.byref(problem), C.byref(plan), C.byref(model.c_struct()), _ptr(pts),
                           int(n), _ptr(out), int(bool(log_space)), int(precision), _ptr(workspace),
                           nbytes, _stream(stream)), "pam_eval")
+
+
+def pam_eval_bucket(problem, plan, pts, out, workspace=None, stream=None):
+    n = pts.shape[0] if pts is not None else 0
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().pam_eval_bucket(C.byref(problem), C.byref(plan), _ptr(pts), int(n), _ptr(out), _ptr(workspace),
+                                 nbytes, _stream(stream)), "pam_eval_bucket")
+
+
+def pam_eval_bucketed(problem, plan, model, pts, out, log_space=False, precision=PAM_PREC_FP64, workspace=None,
+                      stream=None):
+    n = pts.shape[0] if pts is not None else 0
+    nbytes = workspace.numel() * workspace.element_size() if workspace is not None else 0
+    _check(lib().pam_eval_bucketed(C.byref(problem), C.byref(plan), C.byref(model.c_struct()), _ptr(pts),
+                                   int(n), _ptr(out), int(bool(log_space)), int(precision), _ptr(workspace),
+                                   nbytes, _stream(stream)), "pam_eval_bucketed")
 
 
 def pam_eval_glued_workspace_size(problem, plan, n_pts):
@@ -674,6 +691,21 @@ class Fitter:
             self._eval_ws = ws
         return ws
 
+    def eval_bucket(self, pts, out, stream=None):
+        """pam_eval_bucket: the points bucketed by owner in this fitter's
+        evaluation workspace (no model read: it may run beside the fit on
+        another stream). eval_bucketed with the same pts and out completes the
+        evaluation; no other evaluation of more points may come in between
+        (the workspace would be replaced)."""
+        pam_eval_bucket(self.problem, self.plan, pts, out, self.eval_workspace(pts.shape[0]), stream)
+        return out
+
+    def eval_bucketed(self, pts, out, log_space=False, precision=None, stream=None):
+        prec = self.params.precision if precision is None else precision
+        pam_eval_bucketed(self.problem, self.plan, self.model, pts, out, log_space, prec,
+                          self.eval_workspace(pts.shape[0]), stream)
+        return out
+
     def eval(self, pts, out=None, log_space=False, precision=None, stream=None):
         import torch
         if out is None:
@@ -683,8 +715,33 @@ class Fitter:
                  self.eval_workspace(pts.shape[0]), stream)
         return out
 
+    def _slice_bounds(self, n, chunks):
+        k = max(1, min(int(chunks), n)) if n > 0 else 0
+        return [(n * i // k, n * (i + 1) // k) for i in range(k)]
+
+    def _slice_workspace(self, i, n_pts):
+        import torch
+        need = pam_eval_workspace_size(self.plan, n_pts)
+        wss = getattr(self, "_slice_ws", None)
+        if wss is None:
+            wss = self._slice_ws = []
+        while len(wss) <= i:
+            wss.append(None)
+        if wss[i] is None or wss[i].numel() < need:
+            wss[i] = torch.empty(max(need, 256), dtype=torch.uint8, device=self.device)
+        return wss[i]
+
+    def bucket_slices(self, pts, out, chunks=4):
+        """pam_eval_bucket of each slice eval_to_host(..., bucketed=True) will
+        evaluate (the same pts, out and chunks), each slice in a workspace of
+        its own, on the current stream: it reads no model, so it may run on
+        another stream beside the fit."""
+        for i, (a, b) in enumerate(self._slice_bounds(pts.shape[0], chunks)):
+            pam_eval_bucket(self.problem, self.plan, pts[a:b], out[a:b], self._slice_workspace(i, b - a))
+        return out
+
     def eval_to_host(self, pts, out, out_host, chunks=4, copy_stream=None, join=True, log_space=False,
-                     precision=None):
+                     precision=None, bucketed=False):
         """pam_eval of pts into the device buffer out in `chunks` contiguous
         slices, each slice's values copied to the pinned host buffer out_host
         on copy_stream as soon as they are ready, so that the copies overlap
@@ -692,7 +749,9 @@ class Fitter:
         pam_eval call: every point is evaluated on its own). Enqueued on the
         current stream; join: later work on it waits for the copies (else
         the caller joins copy_stream itself, and work enqueued meanwhile runs
-        beside the copies). Capturable in a CUDA graph."""
+        beside the copies). bucketed: the slices were bucketed already by
+        bucket_slices (same pts, out and chunks; ordered before this call), and
+        only pam_eval_bucketed runs here. Capturable in a CUDA graph."""
         import torch
         n = pts.shape[0]
         if out.shape[0] < n or out_host.shape[0] < n:
@@ -704,12 +763,18 @@ class Fitter:
             raise ValueError("eval_to_host: out_host must be a host tensor of out's dtype (pinned for overlap)")
         cur = torch.cuda.current_stream()
         cs = copy_stream if copy_stream is not None else self._copy_stream()
-        k = max(1, min(int(chunks), n)) if n > 0 else 0
+        bounds = self._slice_bounds(n, chunks)
+        k = len(bounds)
         evs = self._chunk_events(k)
-        self.eval_workspace(n)  # one workspace, sized for the whole set, serves every slice
-        for i in range(k):
-            a, b = n * i // k, n * (i + 1) // k
-            self.eval(pts[a:b], out=out[a:b], log_space=log_space, precision=precision)
+        if not bucketed:
+            self.eval_workspace(n)  # one workspace, sized for the whole set, serves every slice
+        prec = self.params.precision if precision is None else precision
+        for i, (a, b) in enumerate(bounds):
+            if bucketed:
+                pam_eval_bucketed(self.problem, self.plan, self.model, pts[a:b], out[a:b], log_space, prec,
+                                  self._slice_workspace(i, b - a))
+            else:
+                self.eval(pts[a:b], out=out[a:b], log_space=log_space, precision=precision)
             evs[i].record(cur)
             cs.wait_event(evs[i])
             with torch.cuda.stream(cs):

@@ -136,6 +136,28 @@ def test_null_arguments_are_rejected(pam):
     assert L.pam_eval(C.byref(pr), C.byref(plan), None, None, 0, None, 0, 0, None, 0, None) == 1
 
 
+def test_split_evaluation_checks_its_arguments(pam):
+    # host-side checks of pam_eval_bucket / pam_eval_bucketed (no device work)
+    import ctypes as C
+    L = pam.lib()
+    L.pam_eval_bucket.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p, C.c_void_p,
+                                  C.c_size_t, C.c_void_p]
+    L.pam_eval_bucketed.argtypes = [C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_void_p,
+                                    C.c_int, C.c_int, C.c_void_p, C.c_size_t, C.c_void_p]
+    pr = pam.make_problem((8, 8), (2, 2), 1, (2, 2))
+    plan = pam.pam_plan_create(pr, pam.make_params())
+    p, q = C.byref(pr), C.byref(plan)
+    fake = C.c_void_p(256)  # never dereferenced: every call below fails its checks first
+    need = pam.pam_eval_workspace_size(plan, 10)
+    assert L.pam_eval_bucket(p, q, None, 0, None, None, 0, None) == 0  # no points: a no-op
+    assert L.pam_eval_bucket(p, q, None, 10, fake, fake, need, None) == 1  # no points buffer
+    assert L.pam_eval_bucket(p, q, fake, 10, fake, None, need, None) == 1  # no workspace
+    assert L.pam_eval_bucket(p, q, fake, 10, fake, fake, need - 1, None) == 4  # workspace too small
+    assert L.pam_eval_bucket(p, q, fake, -1, fake, fake, need, None) == 1
+    assert L.pam_eval_bucketed(p, q, None, fake, 10, fake, 0, 1, fake, need, None) == 1  # no model
+    assert L.pam_eval_bucket(None, q, fake, 10, fake, fake, need, None) == 1
+
+
 def test_network_sizes_and_geometry(pam):
     # both architectures: parameter counts from the layer tables, geometry,
     # and rejection of unknown architectures and bad batches (host only)
