@@ -565,33 +565,20 @@ def run_pam(args, rank, ws):
             fit.fit(Kd, deferred=deferred)
 
     errd = torch.zeros(4, dtype=torch.float64, device=dev)
-    # the evaluation points are bucketed by owner (pam_eval_bucket: points and
-    # partition only) on a stream of their own beside the fit; the model is
-    # evaluated at them after it (pam_eval_bucketed)
-    bucket_stream = torch.cuda.Stream(device=dev)
-
-    def bucket_beside():
-        bucket_stream.wait_stream(torch.cuda.current_stream())
-        with torch.cuda.stream(bucket_stream):
-            fit.eval_bucket(ptsd, out)
 
     def step():
-        bucket_beside()
         fit_step()
-        torch.cuda.current_stream().wait_stream(bucket_stream)
-        fit.eval_bucketed(ptsd, out)
+        fit.eval(ptsd, out=out)
         return fit.errors(Kd)
 
     def step_body(seeded=True):
         # the same step without host synchronisation (deferred status), so
         # that it can be captured in a CUDA graph and replayed
-        bucket_beside()
         if seeded:
             fit_step(deferred=True)
         else:
             fit.fit(Kd, deferred=True)
-        torch.cuda.current_stream().wait_stream(bucket_stream)
-        fit.eval_bucketed(ptsd, out)
+        fit.eval(ptsd, out=out)
         fit.errors_device(Kd, errd)
 
     def check_status():
@@ -789,12 +776,11 @@ def run_pam(args, rank, ws):
         side.wait_event(k_ready)
         with torch.cuda.stream(side):
             ptsd.copy_(ptsh, non_blocking=True)
-            fit.bucket_slices(ptsd, out, chunks=args.e2e_slices)  # beside the fit, as the points arrive
             pts_ready.record(side)
         fit_step(deferred=True)
         cur.wait_event(pts_ready)
         # evaluated in slices, each copied back while the next evaluates
-        fit.eval_to_host(ptsd, out, outh, chunks=args.e2e_slices, copy_stream=side, join=False, bucketed=True)
+        fit.eval_to_host(ptsd, out, outh, chunks=args.e2e_slices, copy_stream=side, join=False)
         fit.errors_device(Kd, errd)
         errh.copy_(errd, non_blocking=True)
         cur.wait_stream(side)
