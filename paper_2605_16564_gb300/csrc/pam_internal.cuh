@@ -261,13 +261,26 @@ __device__ __forceinline__ int owner_of_point(const Geo &g, const double x[3]) {
 #pragma unroll
     for (int a = 0; a < 3; ++a) {
         if (a >= g.dim) break;
-        const double u = x[a] * (double)g.nmax;
-        if (!(u >= 0.0)) return -1;
-        int i = __double2int_rd(u);  // beyond the int range: INT_MAX
-        if (i > g.n[a]) return -1;
-        if (i == g.n[a]) {
-            if (u != (double)g.n[a]) return -1;
-            i = g.n[a] - 1;
+        // fp32 first: uf differs from the binary64 u = x n_max by at most
+        // 2^-22 |u| (the rounding of x to fp32 and of the product), so away
+        // from the integers and from both ends of the grid (margin d, twice
+        // that bound and more) floor(uf) is floor(u); the few points within
+        // d of one take the binary64 path. NaN fails every test and goes
+        // there too.
+        const float uf = (float)x[a] * (float)g.nmax;
+        const float fl = floorf(uf), d = fmaf(uf, 4.8e-7f, 1e-6f);
+        int i;
+        if (uf - fl >= d && fl + 1.f - uf >= d && uf >= d && uf <= (float)g.n[a] - d) {
+            i = (int)fl;
+        } else {
+            const double u = x[a] * (double)g.nmax;
+            if (!(u >= 0.0)) return -1;
+            i = __double2int_rd(u);  // beyond the int range: INT_MAX
+            if (i > g.n[a]) return -1;
+            if (i == g.n[a]) {
+                if (u != (double)g.n[a]) return -1;
+                i = g.n[a] - 1;
+            }
         }
         j[a] = core_of(i, g.n[a], g.p[a]);
     }
