@@ -138,15 +138,17 @@ __global__ void k_init_dictionary(Geo g, const int32_t *boxes, double *centres, 
     int m = blockIdx.x * blockDim.x + threadIdx.x;
     const int32_t *box = boxes + s * 12;
     if (m < g.m_cap) {
-        double lo[3] = {0, 0, 0}, sp[3] = {0, 0, 0};
-        double sigma = 0.0;
-        for (int a = 0; a < g.dim; ++a) {
-            lo[a] = __dmul_rn((double)box[a], g.h);
-            sp[a] = __ddiv_rn(__dmul_rn((double)(box[3 + a] - box[a]), g.h), (double)g.g[a]);
-            sigma = fmax(sigma, sp[a]);
-        }
         double *c = centres + ((size_t)s * g.m_cap + m) * 4;
         if (m < g.m0) {
+            // the lattice's origin, spacing and width (binary64 divisions:
+            // only the lattice's own threads compute them)
+            double lo[3] = {0, 0, 0}, sp[3] = {0, 0, 0};
+            double sigma = 0.0;
+            for (int a = 0; a < g.dim; ++a) {
+                lo[a] = __dmul_rn((double)box[a], g.h);
+                sp[a] = __ddiv_rn(__dmul_rn((double)(box[3 + a] - box[a]), g.h), (double)g.g[a]);
+                sigma = fmax(sigma, sp[a]);
+            }
             int idx[3] = {m % g.g[0], (m / g.g[0]) % g.g[1], m / (g.g[0] * g.g[1])};
             for (int a = 0; a < 3; ++a)
                 c[a] = a < g.dim ? __dadd_rn(lo[a], __dmul_rn((double)idx[a] + 0.5, sp[a])) : 0.0;
