@@ -809,6 +809,10 @@ __global__ void __launch_bounds__(kMarkThreads, 6) k_mark_enrich(Geo g, Par p, c
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = blockDim.x >> 5;
     __shared__ int marked[kMaxKTop];
     __shared__ int n_marked;
+    // the top-k selection: a digit histogram, counts, the selected keys
+    __shared__ int hist[256];
+    __shared__ int s_nz, s_nsel, s_digit, s_krem;
+    __shared__ unsigned long long sel[kMaxKTop];
     extern __shared__ __align__(16) unsigned long long keys[];  // [P], later the enrichment tables
     if (L >= p.levels || M >= m_limit) {
         if (tid == 0) inf[PAM_INFO_STOPPED] = 1;
@@ -859,31 +863,82 @@ __global__ void __launch_bounds__(kMarkThreads, 6) k_mark_enrich(Geo g, Par p, c
         }
         keys[t] = k;
     }
-    if (tid == 0) n_marked = 0;
+    if (tid == 0) { n_marked = 0; s_nz = 0; s_nsel = 0; }
     __syncthreads();
     const int k_top = p.k_top < kMaxKTop ? p.k_top : kMaxKTop;
     MK_T(mk1);
     MK_ADD(0, mk0, mk1);
-    // bitonic sort, descending (the keys are distinct, so the order is unique)
-    for (int k = 2; k <= P; k <<= 1) {
-        for (int j = k >> 1; j > 0; j >>= 1) {
-            for (int i = tid; i < (P >> 1); i += blockDim.x) {
-                const int l = 2 * i - (i & (j - 1)), r = l + j;
-                const unsigned long long a = keys[l], b = keys[r];
-                const bool desc = (l & k) == 0;
-                if (desc ? (a < b) : (a > b)) { keys[l] = b; keys[r] = a; }
+    // The k_top largest nonzero keys in descending order (the keys are
+    // distinct, so the set and its order are unique): the kk-th largest by a
+    // radix selection over eight 8-bit digits from the top, the keys at or
+    // above it gathered, then each ranked against the others.
+    {
+        int nz = 0;
+        for (int t = tid; t < P; t += blockDim.x) nz += keys[t] != 0ull;
+        for (int o = 16; o > 0; o >>= 1) nz += __shfl_xor_sync(0xffffffffu, nz, o);
+        if (lane == 0 && nz) atomicAdd(&s_nz, nz);
+    }
+    __syncthreads();
+    const int kk = k_top < s_nz ? k_top : s_nz;
+    unsigned long long thr = 1ull;  // every nonzero key when kk takes them all
+    if (kk > 0 && kk < s_nz) {
+        unsigned long long prefix = 0ull, mask = 0ull;
+        int krem = kk;
+        for (int shift = 56; shift >= 0; shift -= 8) {
+            for (int i = tid; i < 256; i += blockDim.x) hist[i] = 0;
+            __syncthreads();
+            for (int t = tid; t < P; t += blockDim.x) {
+                const unsigned long long k = keys[t];
+                if (k != 0ull && (k & mask) == prefix) atomicAdd(&hist[(int)((k >> shift) & 255ull)], 1);
             }
             __syncthreads();
+            if (warp == 0) {
+                // lane l sums the bins 255 - 8 l down to 248 - 8 l; the lane
+                // whose bins hold the krem-th key (counted from the top) finds
+                // its digit
+                int tot = 0;
+#pragma unroll
+                for (int q = 0; q < 8; ++q) tot += hist[255 - 8 * lane - q];
+                int inc = tot;
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int v = __shfl_up_sync(0xffffffffu, inc, o);
+                    if (lane >= o) inc += v;
+                }
+                int above = inc - tot;
+                if (above < krem && krem <= inc) {
+#pragma unroll
+                    for (int q = 0; q < 8; ++q) {
+                        const int c = hist[255 - 8 * lane - q];
+                        if (above + c >= krem) {
+                            s_digit = 255 - 8 * lane - q;
+                            s_krem = krem - above;
+                            break;
+                        }
+                        above += c;
+                    }
+                }
+            }
+            __syncthreads();
+            prefix |= (unsigned long long)s_digit << shift;
+            mask |= 255ull << shift;
+            krem = s_krem;
+        }
+        thr = prefix;  // all 64 bits fixed: the kk-th largest key itself
+    }
+    if (kk > 0) {
+        for (int t = tid; t < P; t += blockDim.x) {
+            const unsigned long long k = keys[t];
+            if (k != 0ull && k >= thr) sel[atomicAdd(&s_nsel, 1)] = k;
         }
     }
-    // the nonzero keys form a prefix: mark the first k_top of them
-    for (int r = tid; r < k_top && r < P; r += blockDim.x) {
-        const unsigned long long kr = keys[r];
-        if (kr != 0ull) {
-            marked[r] = (int)(0xffffffffu - (unsigned)(kr & 0xffffffffull));
-            if (r + 1 == k_top || r + 1 == P || keys[r + 1] == 0ull) n_marked = r + 1;
-        }
+    __syncthreads();
+    for (int i = tid; i < kk; i += blockDim.x) {
+        const unsigned long long k = sel[i];
+        int rank = 0;
+        for (int j = 0; j < kk; ++j) rank += sel[j] > k;
+        marked[rank] = (int)(0xffffffffu - (unsigned)(k & 0xffffffffull));
     }
+    if (tid == 0) n_marked = kk;
     __syncthreads();
     const int nm = n_marked;
     MK_T(mk2);
