@@ -619,7 +619,9 @@ pam_status pam_nn_adamw(float *d_params, const float *d_grads, float *d_m, float
  *   solve_persistent  the mixed solve's launch: 0 one CTA per subdomain in
  *                longest-first order (the built-in), 1 one CTA per resident
  *                slot (two per SM), each taking the next subdomain of the
- *                same order from a device counter until none is left
+ *                same order from a device counter until none is left; a
+ *                solve of one subdomain group (level_groups) always takes
+ *                the first form
  *   level_groups the mixed form's levels (the initial lattices' statistics,
  *                Gram and solve in pam_fit_subdomains / pam_fit_cells, the
  *                refinement levels in pam_refine / pam_refine_cells; each

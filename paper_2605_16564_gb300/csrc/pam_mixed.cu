@@ -1678,7 +1678,10 @@ void launch_solve_mixed(const Geo &g, const Par &p, const int32_t *boxes, const 
     cudaFuncSetAttribute(k_solve_mixed, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
     k_solve_order<<<1, 1024, 0, st>>>(w.cost, group_count(g), g.gb, g.gs, w.order, w.fb);
     count_launches(1);
-    const int persistent = tuning().solve_persistent == 1 && w.fb != nullptr;
+    // persistent CTAs would hold every resident slot until their queue is
+    // empty; in a subdomain group that would shut out the other group's
+    // kernels, whose overlap is the point of the groups
+    const int persistent = tuning().solve_persistent == 1 && w.fb != nullptr && g.gs == 1;
     unsigned grid = (unsigned)group_count(g);
     if (persistent) {
         // as many CTAs as fit the device at once with this launch's shared memory
