@@ -21,6 +21,9 @@
  *  - Pointers named d_* are DEVICE pointers, h_* HOST pointers. Every
  *    buffer is owned by the caller; the library allocates no memory.
  *    Scratch comes from a caller workspace of pam_plan.workspace_bytes.
+ *    (The mixed form's subdomain groups, pam_tuning.level_groups, create
+ *    one stream and two events per host thread and device on first use and
+ *    keep them for the process.)
  *  - Device work is enqueued on `stream` (a cudaStream_t, NULL = legacy
  *    default stream). Calls that return device-side status synchronise
  *    that stream once before returning; this is stated per call.
