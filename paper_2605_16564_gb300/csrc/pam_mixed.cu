@@ -1584,9 +1584,20 @@ __global__ void __launch_bounds__(1024) k_solve_order(const uint32_t *cost, int 
     __syncthreads();
     for (int i = threadIdx.x; i < n; i += blockDim.x) atomicAdd(&cnt[cost_bucket(cost[gb + i * gs])], 1);
     __syncthreads();
-    if (threadIdx.x == 0) {
-        int run = 0;
-        for (int q = kB - 1; q >= 0; --q) {
+    if (threadIdx.x < 32) {
+        // exclusive scan from the costliest bucket down: lane l takes buckets
+        // kB - 1 - 8 l down to kB - 8 - 8 l, the lanes' totals by a warp scan
+        const int lane = threadIdx.x;
+        int tot = 0;
+        for (int u = 0; u < kB / 32; ++u) tot += cnt[kB - 1 - (kB / 32) * lane - u];
+        int inc = tot;
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        int run = inc - tot;
+        for (int u = 0; u < kB / 32; ++u) {
+            const int q = kB - 1 - (kB / 32) * lane - u;
             base[q] = run;
             run += cnt[q];
         }
