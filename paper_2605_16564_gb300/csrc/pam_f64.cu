@@ -62,8 +62,7 @@ __global__ void k_prepare(Geo g, const int32_t *boxes, const double *K, Ws w) {
                 atomicAdd(&w.status[kStBadK], 1);
                 k = 1.0;
             }
-            w.y[o] = log(k);
-            w.kv[o] = k;
+            w.kv[o] = k;  // y = ln K: written by k_prepare_log, once per grid cell
             kmax = k;
         } else {
             w.y[o] = 0.0;
@@ -74,6 +73,57 @@ __global__ void k_prepare(Geo g, const int32_t *boxes, const double *K, Ws w) {
     double m = warp_max(kmax);
     if ((threadIdx.x & 31) == 0 && m > 0.0)
         atomicMax(&w.kmax_bits[s], (unsigned long long)__double_as_longlong(m));
+}
+
+// y = ln K of every patch cell, the binary64 log taken once per grid cell
+// and written to each patch that holds the cell (the patches overlap, so a
+// cell sits in about two on this grid; the log is most of the set-up's cost
+// on this part's narrow binary64 pipe). Along axis a the patches holding
+// cell i are those of the cores meeting [i - overlap, i + overlap], with the
+// boxes of pam_partition (core j: [j n / p, (j + 1) n / p), floor division,
+// patch: the core widened by the overlap and clipped). A bad K (<= 0, NaN,
+// Inf) gives y = 0, as k_prepare's substitute K = 1 did; k_prepare counts it.
+__global__ void k_prepare_log(Geo g, const double *K, Ws w) {
+    const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (gi >= (int64_t)g.n[0] * g.n[1] * g.n[2]) return;
+    const int idx[3] = {(int)(gi % g.n[0]), (int)((gi / g.n[0]) % g.n[1]),
+                        (int)(gi / ((int64_t)g.n[0] * g.n[1]))};
+    const double k = K[gi];
+    const double y = (k > 0.0 && k <= DBL_MAX) ? log(k) : 0.0;
+    int jlo[3], jhi[3];
+#pragma unroll
+    for (int a = 0; a < 3; ++a) {
+        const int ov = a < g.dim ? g.overlap : 0;
+        jlo[a] = core_of(max(0, idx[a] - ov), g.n[a], g.p[a]);
+        jhi[a] = core_of(min(g.n[a] - 1, idx[a] + ov), g.n[a], g.p[a]);
+    }
+    // the patch box along axis a of core j: [lo, hi) and the cell's offset
+    auto patch = [&](int a, int j, int *plo, int *pw) {
+        const int ov = a < g.dim ? g.overlap : 0, n = g.n[a], p = g.p[a];
+        const int lo = (int)(((int64_t)j * n) / p), hi = (int)(((int64_t)(j + 1) * n) / p);
+        *plo = lo - ov < 0 ? 0 : lo - ov;
+        *pw = (hi + ov > n ? n : hi + ov) - *plo;
+    };
+    for (int jz = jlo[2]; jz <= jhi[2]; ++jz) {
+        int pz, wz;
+        patch(2, jz, &pz, &wz);
+        const int oz = idx[2] - pz;
+        if (oz < 0 || oz >= wz) continue;
+        for (int jy = jlo[1]; jy <= jhi[1]; ++jy) {
+            int py, wy;
+            patch(1, jy, &py, &wy);
+            const int oy = idx[1] - py;
+            if (oy < 0 || oy >= wy) continue;
+            for (int jx = jlo[0]; jx <= jhi[0]; ++jx) {
+                int px, wx;
+                patch(0, jx, &px, &wx);
+                const int ox = idx[0] - px;
+                if (ox < 0 || ox >= wx) continue;
+                const int s = jx + g.p[0] * (jy + g.p[1] * jz);
+                w.y[(size_t)s * g.n_max + ox + wx * (oy + wy * oz)] = y;
+            }
+        }
+    }
 }
 
 // The same for a mesh given as cells: patch cell t of subdomain s is element
@@ -121,11 +171,15 @@ void launch_prepare(const Geo &g, const int32_t *boxes, const double *K, const W
     PhaseScope ps(kPhPrepare, st);
     cudaMemsetAsync(w.kmax_bits, 0, sizeof(unsigned long long) * g.S, st);
     dim3 grid((g.n_max + 255) / 256, g.S);
-    if (g.cells)
+    if (g.cells) {
         k_prepare_cells<<<grid, 256, 0, st>>>(g, K, w);
-    else
+        count_launches(1);
+    } else {
+        const int64_t n = (int64_t)g.n[0] * g.n[1] * g.n[2];
+        k_prepare_log<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, K, w);
         k_prepare<<<grid, 256, 0, st>>>(g, boxes, K, w);
-    count_launches(1);
+        count_launches(2);
+    }
 }
 
 // --------------------------------------------------------------------------
