@@ -366,9 +366,9 @@ static pam_status read_status(const Ws &w, cudaStream_t st, int32_t host[8]) {
 // order and its own half of the binary64 fallback's slots.
 constexpr int kGroupMinS = 1024;  // below this the solve has few waves to balance
 
-static int level_groups(const Geo &g, const Par &p, const pam_params *par, const Ws &w) {
+static int level_groups(const Geo &g, const pam_params *par, const Ws &w, bool timing = g_timing) {
     if (par->precision != PAM_PREC_MIXED || w.fb_slots < 2) return 1;
-    if (g_timing) return 1;  // the phase profiler times one pipeline, phase by phase
+    if (timing) return 1;  // the phase profiler times one pipeline, phase by phase
     if (g_tuning.level_groups == 1 || g_tuning.level_groups == 2) return g_tuning.level_groups;
     return g.S >= kGroupMinS ? 2 : 1;
 }
@@ -454,7 +454,7 @@ static pam_status fit_launches(const Geo &g, const Par &p, const pam_params *par
     }
     launch_init_dictionary(g, model->boxes, model->centres, model->beta, model->info, s,
                            par->warm_start != 0);
-    if (par->precision == PAM_PREC_MIXED && level_groups(g, p, par, w) == 2) {
+    if (par->precision == PAM_PREC_MIXED && level_groups(g, par, w) == 2) {
         // the initial lattices' statistics, Gram and solve in the two groups
         GroupStreams *gs = nullptr;
         if ((st = group_streams(&gs)) != PAM_OK) return st;
@@ -563,7 +563,7 @@ static pam_status refine_launches(const Geo &g, const Par &p, const pam_params *
     const bool deferred = par->deferred_status != 0;
     // deferred: the status keeps accumulating from pam_fit_subdomains
     if (!deferred) PAM_CUDA_TRY(cudaMemsetAsync(w.status, 0, 8 * sizeof(int32_t), s));
-    const int ng = n_levels > 0 ? level_groups(g, p, par, w) : 1;
+    const int ng = n_levels > 0 ? level_groups(g, par, w) : 1;
     if (ng == 2) {
         GroupStreams *gs = nullptr;
         if ((st = group_streams(&gs)) != PAM_OK) return st;
@@ -1187,10 +1187,7 @@ int pam_group_layout(int n_subdomains, int32_t *out) {
     par.precision = PAM_PREC_MIXED;
     Ws w{};
     w.fb_slots = n_subdomains < kFbSlots ? n_subdomains : kFbSlots;
-    const bool timing = g_timing;
-    g_timing = false;
-    const int ng = level_groups(g, Par{}, &par, w);
-    g_timing = timing;
+    const int ng = level_groups(g, &par, w, false);
     for (int q = 0; q < ng; ++q) {
         const GroupLayout l = group_layout(g.S, w.fb_slots, q, ng);
         const int32_t v[7] = {l.gb, l.gs, l.gn, l.order_off, l.list_off, l.slots, l.slot0};
