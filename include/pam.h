@@ -192,7 +192,7 @@ const char *pam_status_string(pam_status s);
  * m_cap = min(prod g_init + levels (dim+1) k_top, prod g_init + m_max),
  * rounded up to a multiple of 64; PAM_ERR_UNSUPPORTED if it exceeds
  * PAM_MAX_M, or if levels > 0 and a patch holds more than 16,384 cells
- * (marking sorts a patch's indicators in shared memory). Returns PAM_ERR_INVALID_ARG for an inconsistent problem
+ * (marking keeps a patch's indicator keys in shared memory). Returns PAM_ERR_INVALID_ARG for an inconsistent problem
  * (dim outside 1..3, n_sub[a] outside 1..n_cells[a], overlap < 0,
  * g_init < 1, lambda's < 0 or lambda2_hat == 0, eta outside (0,1),
  * k_top < 0, m_max < 0, levels < 0, precision unknown).

@@ -842,7 +842,7 @@ extern "C" void pam_debug_mark_profile(unsigned long long *out, int reset) {
 #endif
 constexpr int kMaxKTop = 1024;
 
-// Power of two >= n (the bitonic sort's padded length).
+// Power of two >= n: the length of the marking kernel's key buffer.
 __host__ __device__ __forceinline__ int mark_sort_len(int n) {
     int P = 1;
     while (P < n) P <<= 1;

@@ -1557,10 +1557,6 @@ __global__ void __launch_bounds__(kSmallSolveThreads) k_solve_mixed_small(Geo g,
                              0);
 }
 
-// Block order of the next mixed solve: the subdomains sorted by the cost of
-// their previous solve, descending, ties to the lower index (one block,
-// bitonic sort of (cost, ~index) keys in shared memory). Any order gives the
-// same results; this one only shortens the tail of the launch.
 // Longest-first order of the subdomains by the clock cost of their previous
 // solve, by buckets of 1/8 octave (the leading bit and the next three of the
 // cost): one pass of shared-memory counts, a scan from the costliest bucket
